@@ -1,0 +1,385 @@
+"""IG hot-path benchmark on synthetic NSL-KDD-shaped data (one JSON line).
+
+A step is one pass of the whole hot path over one workload: encode the
+training and test records (Eq. 5), fit (Eq. 1 -> Eq. 3 -> Eq. 2: pairwise
+intersections, dedup, coherence, canonical order, supports and scores) and
+score the test records (Eq. 4, Regulations 1-3).  Inputs (the discretised
+codes and labels) are resident on the device when the timed region starts;
+L2 is flushed (a 512 MiB write) before every timed step and each step is
+timed with CUDA events on the launching stream.
+
+value = subset tests per second, where the tests of one step are those the
+definitions require: |B^c| x n_(other class) for coherence (Eq. 3),
+|P^c| x n_c for supports (Eq. 2) and m_test x (|P+| + |P-|) for the
+evidence (Eq. 4), summed over both classes.
+
+Also reported: fit wall time, scored flows/s, an end-to-end figure through
+the C ABI with host buffers, the roofline of the dominant kernel, the CPU
+oracle timed on this host's cores, SM clocks sampled during the timed region
+and the number of kernels launched.
+
+--impl reference times the CPU oracle (the only other implementation of the
+method here) on a bounded sample of the same workload.
+
+Multi-GPU (torchrun): every rank fits its own independent problem of the same
+shape (seed offset by rank); there is no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import igdata  # noqa: E402
+
+METRIC = "IG fit wall-s & subset tests/s (G/s) vs roofline; scored flows/s, p99 ms"
+UNIT = "G subset-tests/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+# Integer-pipe peak of the subset test: LOP3 instructions per SM per clock
+# (measured on GB300, see the profiles directory) x SMs x max SM clock.
+LOP3_PER_SM_PER_CLK = 64
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="nsl15k", choices=sorted(igdata.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def nominal_tests(info: dict, m_test: int) -> dict:
+    """Subset tests the definitions require for one fit + score."""
+    nt, U, P = info["n_train"], info["n_candidates"], info["n_patterns"]
+    coh = U[1] * nt[0] + U[0] * nt[1]
+    sup = P[1] * nt[1] + P[0] * nt[0]
+    ev = m_test * (P[0] + P[1])
+    return {"coherence": coh, "support": sup, "evidence": ev,
+            "total": coh + sup + ev}
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f)
+    except OSError:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.tmp:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.tmp.flush()
+        rows = list(csv.reader(io.StringIO(open(self.tmp.name).read())))
+        os.unlink(self.tmp.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2507_14222_gb300 as ig
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    ig.build()
+    ig.load()
+
+    seed_offset = 0 if rank == 0 else 7919 * rank
+    w = {"tiny": lambda: igdata.tiny(1001 + seed_offset),
+         "nsl15k": lambda: igdata.nsl15k(1002 + seed_offset),
+         "nsl148k": lambda: igdata.nsl148k(1003 + seed_offset)}[args.workload]()
+    cards = w.cards
+    d_tr = torch.from_numpy(w.train_codes.view(np.int16)).cuda()
+    d_lab = torch.from_numpy(w.train_labels).cuda()
+    d_te = torch.from_numpy(w.test_codes.view(np.int16)).cuda()
+    m_test = w.test_codes.shape[0]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        rows = ig.ig_encode(d_tr, cards)
+        test_rows = ig.ig_encode(d_te, cards)
+        model = ig.ig_fit(rows, d_lab)
+        out = ig.ig_score(model, test_rows)
+        return model, out
+
+    info = None
+    for _ in range(args.warmup):
+        model, _out = step()
+        info = model.info()
+        model.free()
+    torch.cuda.synchronize()
+    tests = nominal_tests(info, m_test)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    fit_ms = []
+    ig.prof_reset()
+    ig.prof_enable(True)
+    launches0 = ig.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record(stream)
+            rows = ig.ig_encode(d_tr, cards)
+            test_rows = ig.ig_encode(d_te, cards)
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            model = ig.ig_fit(rows, d_lab)
+            f1.record(stream)
+            ig.ig_score(model, test_rows)
+            ends[i].record(stream)
+            model.free()
+            torch.cuda.synchronize()
+            fit_ms.append(f0.elapsed_time(f1))
+        torch.cuda.synchronize()
+    barrier()
+    launches = ig.launch_count() - launches0
+    ig.prof_enable(False)
+    stages = ig.prof_read()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * tests["total"] / (ms_per_step * 1e-3) / 1e9
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": {"workload": w.name, "train_records": int(w.train_codes.shape[0]),
+                   "test_records": int(m_test), "features": w.n_features,
+                   "items_L": w.n_items, "words_K": w.n_words,
+                   "l2": "flushed before every timed step (512 MiB write)",
+                   "parallelism": f"{world} independent problems" if world > 1 else "single"},
+        "fit_s": statistics.median(fit_ms) * 1e-3,
+        "flows_per_s": m_test / (ms_per_step * 1e-3),
+        "tests_per_step": tests,
+        "patterns": {"attack": info["n_patterns"][1], "normal": info["n_patterns"][0],
+                     "candidates": list(info["n_candidates"][::-1])},
+        "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in stages.items()},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    line["roofline"] = roofline(stages, info, m_test, w.n_words, line["clocks"])
+    if not args.no_e2e:
+        line["e2e"] = e2e_host_buffers(ig, w, tests, max(2, min(args.steps, 5)))
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def roofline(stages, info, m_test, K, clocks):
+    """Roofline of the dominant stage's kernel (largest share of step time)."""
+    name, (ms, launches) = max(stages.items(), key=lambda kv: kv[1][0])
+    nt, U, P = info["n_train"], info["n_candidates"], info["n_patterns"]
+    tests = {"coherence": U[1] * nt[0] + U[0] * nt[1],
+             "support": P[1] * nt[1] + P[0] * nt[0],
+             "evidence": m_test * (P[0] + P[1])}
+    out = {"kernel": name, "launches": int(launches),
+           "avg_launch_ms": ms / max(1, launches)}
+    if name in tests:
+        # Integer-pipe bound: each test is 2K LOP3 (one per 32-bit half).
+        # tests[name] counts both classes of one step, i.e. two launches.
+        steps = launches / 2.0
+        achieved = tests[name] * 2 * K * steps / (ms * 1e-3) / 1e12
+        sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
+        peak = LOP3_PER_SM_PER_CLK * 152 * sm_max * 1e6 / 1e12
+        out.update({"bound": "alu", "achieved": achieved, "peak": peak,
+                    "unit": "Tops/s (LOP3)", "frac": achieved / peak, "traffic": None,
+                    "peak_source": f"{LOP3_PER_SM_PER_CLK} LOP3/SM/clk x 152 SMs x {sm_max:.0f} MHz"})
+    else:
+        peaks = load_peaks()
+        hbm = (peaks or {}).get("hbm_gbs", FALLBACK_HBM_GBS)
+        out.update({"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s",
+                    "frac": None, "traffic": None,
+                    "peak_source": "measured" if peaks else "fallback"})
+    return out
+
+
+def e2e_host_buffers(ig, w, tests, steps):
+    """Same metric through the C ABI with numpy (host) buffers: the library
+    copies codes, rows and labels in and A, N, labels (and the encoded rows)
+    out inside every timed step."""
+    import torch
+    times = []
+    h2d = d2h = 0
+    for i in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rows = ig.ig_encode(w.train_codes, w.cards)
+        test_rows = ig.ig_encode(w.test_codes, w.cards)
+        model = ig.ig_fit(rows, w.train_labels)
+        A, N, lab = ig.ig_score(model, test_rows)
+        model.free()
+        torch.cuda.synchronize()
+        if i:  # the first pass is a warm-up
+            times.append(time.perf_counter() - t0)
+        h2d = (w.train_codes.nbytes + w.test_codes.nbytes + rows.nbytes
+               + w.train_labels.nbytes + test_rows.nbytes)
+        d2h = rows.nbytes + test_rows.nbytes + A.nbytes + N.nbytes + lab.nbytes
+    sec = statistics.median(times)
+    return {"value": tests["total"] / sec / 1e9, "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "s_per_step": sec}
+
+
+def _oracle_pass(train_codes, train_labels, test_codes, cards, threads):
+    import oracle
+    rows = oracle.encode(train_codes, cards)
+    test = oracle.encode(test_codes, cards)
+    t0 = time.perf_counter()
+    m = oracle.fit(rows, train_labels, threads=threads)
+    oracle.score(m, test, threads=threads)
+    sec = time.perf_counter() - t0
+    nt = [int((train_labels == c).sum()) for c in (0, 1)]
+    info = {"n_train": nt, "n_candidates": [m.n_candidates[0], m.n_candidates[1]],
+            "n_patterns": [m.patterns[0].shape[0], m.patterns[1].shape[0]]}
+    return sec, nominal_tests(info, test.shape[0])["total"]
+
+
+def cpu_baseline(w):
+    """The oracle as it stands, on this host's cores, over the whole workload
+    once (about 10-20 s of CPU time for the 15k workload)."""
+    import oracle
+    threads = oracle.default_threads()
+    sec, tests = _oracle_pass(w.train_codes, w.train_labels, w.test_codes, w.cards, threads)
+    return {"value": tests / sec / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"one full fit + score of {w.name} ({w.train_codes.shape[0]} train, "
+                      f"{w.test_codes.shape[0]} test)", "seconds": sec}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    threads = oracle.default_threads()
+    w = igdata.WORKLOADS[args.workload]()
+    # Bounded sample per step: the first 3,000 training and 1,000 test records.
+    n_tr = min(3000, w.train_codes.shape[0])
+    n_te = min(1000, w.test_codes.shape[0])
+    sample = (w.train_codes[:n_tr], w.train_labels[:n_tr], w.test_codes[:n_te], w.cards)
+    for _ in range(args.warmup):
+        _oracle_pass(*sample, threads)
+    secs, tests = [], 0
+    for _ in range(args.steps):
+        sec, tests = _oracle_pass(*sample, threads)
+        secs.append(sec)
+    total = sum(secs)
+    value = tests * args.steps / total / 1e9
+    desc = f"first {n_tr} train + {n_te} test records of {w.name} per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": w.name, "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads,
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * ig.h -- C ABI of the GB300 (sm_103a) Interpretable Generalization library.
+ *
+ * Interpretable Generalization (IG) learns, from labelled records encoded as
+ * itemsets, the "coherent" patterns of each class -- itemsets that occur in
+ * records of one class and inside no record of the other -- and scores new
+ * records by the patterns they contain (paper Section 3.1, Eq. 1-4 and
+ * Regulations 1-3; packed layout Eq. 5; subset test Eq. 6).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  * Records are itemsets over L items, bit-packed into K = ceil(L/64) 64-bit
+ *    words (Eq. 5): item j is bit (j mod 64) of word (j div 64).  Bits at
+ *    positions >= L must be zero: a set tail bit counts as an item.  A record
+ *    matrix is row-major uint64[n][K].  1 <= K <= IG_MAX_WORDS.
+ *  * Classes: label 1 = attack (class "+", evidence A), 0 = normal (class
+ *    "-", evidence N).
+ *  * Pattern lists are in canonical order: ascending as K-word unsigned
+ *    integers, word K-1 most significant; no duplicates; no empty pattern.
+ *  * Array arguments may be device pointers (CUDA memory of the current
+ *    device) or host pointers (pageable or pinned); the library detects which
+ *    with cudaPointerGetAttributes.  Host inputs are copied to the device and
+ *    host outputs copied back inside the call, which then returns only after
+ *    the copy-back has completed.  With device pointers all work is enqueued
+ *    on `stream` and the call may return before it has finished, except where
+ *    a size must be known on the host (noted per function).
+ *  * The caller owns every array it passes.  Arrays of data-dependent size
+ *    (pattern lists) belong to the library's ig_model and live until
+ *    ig_model_free.
+ *  * Every function returns IG_OK (0) or a negative status; the calling
+ *    thread's last error message is then readable via ig_last_error().
+ *    There is no CPU fallback: without a usable GPU every compute call
+ *    returns IG_E_CUDA.
+ */
+#ifndef IG_GB300_H
+#define IG_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* ig_stream_t;
+
+enum {
+  IG_OK = 0,
+  IG_E_INVAL = -1,     /* bad argument (size, K, label or code out of range) */
+  IG_E_NOMEM = -2,     /* device allocation failed */
+  IG_E_CUDA = -3,      /* CUDA runtime error (message has the CUDA text) */
+  IG_E_TIMEOUT = -4,   /* a bounded device-side wait ran out */
+  IG_E_OVERFLOW = -5,  /* a count exceeded the library's index range */
+  IG_E_INTERNAL = -6,  /* internal consistency check failed */
+  IG_E_IO = -7         /* file could not be read or written */
+};
+
+#define IG_MAX_WORDS 16 /* K limit: itemsets of up to 1024 items */
+
+/* Fitted model: the coherent dictionaries P+ and P- with their supports and
+ * scores, plus the Regulation 3 statistics.  Opaque; device-resident. */
+typedef struct ig_model ig_model;
+
+typedef struct {
+  /* Regulation 3 (Section 3.1): when reg3_enabled != 0, a record whose
+   * normal evidence N < mu_N - r * sigma_N is labelled attack even where
+   * Regulation 1 says normal.  mu_N and sigma_N are the mean and population
+   * standard deviation of N over the training normal records, computed in
+   * double precision in record order. */
+  double r;
+  int32_t reg3_enabled;
+  /* Subset-test kernel choice: 0 = library default, 1 = integer-pipe
+   * (LOP3) kernel.  Other values are reserved. */
+  int32_t subset_kernel;
+} ig_params;
+
+typedef struct {
+  int32_t K;                 /* words per pattern */
+  int32_t reg3_enabled;
+  int64_t n_train[2];        /* training records per class [normal, attack] */
+  int64_t n_candidates[2];   /* |B^c|: distinct non-empty candidates (Eq. 1) */
+  int64_t n_patterns[2];     /* |P^c|: coherent patterns (Eq. 3) */
+  int64_t n_pairs[2];        /* intersections formed: n_c (n_c - 1) / 2 */
+  double reg3_mu, reg3_sigma, reg3_r, reg3_threshold;
+} ig_model_info_t;
+
+/* Section 3.1 / Eq. 5: one-hot encoding of discretised records.
+ * codes: uint16[n][F], codes[i][f] < cards[f] (bin of feature f).
+ * cards: HOST array uint16[F], feature cardinalities; item of (f, v) is
+ *        sum(cards[0..f-1]) + v, so L = sum(cards).
+ * words_out: uint64[n][K] with K = ceil(L/64) (the K argument must equal it).
+ * Returns IG_E_INVAL if a code is out of range (checked on the device; the
+ * call synchronizes `stream` to read the check). n == 0 is valid. */
+int ig_encode(const uint16_t* codes, int64_t n, int32_t F,
+              const uint16_t* cards, uint64_t* words_out, int32_t K,
+              ig_stream_t stream);
+
+/* IG training (Section 3.1): for each class c, the candidates B^c of Eq. 1
+ * (pairwise intersections of class-c records plus the records themselves,
+ * as a set, the empty itemset dropped), the coherent subset P^c of Eq. 3
+ * (no record of the other class contains the pattern, tested as in Eq. 6),
+ * and for each coherent pattern its support f_c (number of class-c records
+ * containing it, duplicates counted) and score S_c = f_c * |b|^2 (Eq. 2),
+ * |b| = number of items.
+ * rows: uint64[n][K]; labels: uint8[n] in {0, 1}.  Both classes must be
+ * non-empty (IG_E_INVAL otherwise).  p may be NULL (defaults: Regulation 3
+ * off).  On success *out receives a new model (free with ig_model_free).
+ * Synchronizes `stream` at internal size checkpoints; returns after the
+ * model is complete. */
+int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
+           const ig_params* p, ig_model** out, ig_stream_t stream);
+
+/* Sizes and statistics of a fitted model. */
+int ig_model_info(const ig_model* m, ig_model_info_t* info);
+
+/* Device pointers to class `cls` (1 = attack P+, 0 = normal P-) of a model:
+ * words uint64[n_patterns][K] in canonical order, support uint32[n_patterns],
+ * score uint64[n_patterns].  Any output pointer may be NULL.  The arrays are
+ * owned by the model. */
+int ig_model_patterns(const ig_model* m, int32_t cls, const uint64_t** words,
+                      const uint32_t** support, const uint64_t** score);
+
+/* Copies class `cls` of a model into caller arrays (device or host; any may
+ * be NULL): words_out uint64[n_patterns][K], support_out uint32[n_patterns],
+ * score_out uint64[n_patterns].  Returns after the copies have completed. */
+int ig_model_copy_patterns(const ig_model* m, int32_t cls, uint64_t* words_out,
+                           uint32_t* support_out, uint64_t* score_out,
+                           ig_stream_t stream);
+
+/* IG inference (Eq. 4 and Regulations 1-3): for each record x,
+ * A(x) = sum of S+(b) over b in P+ contained in x, N(x) likewise over P-,
+ * both exact int64; label = 1 (attack) if A >= N (Regulation 1), or
+ * A == N == 0 (Regulation 2), or Regulation 3 fires; else 0.
+ * rows: uint64[m][K] with the model's K.  A_out, N_out: int64[m];
+ * label_out: uint8[m]; any of the three may be NULL.  m == 0 is valid. */
+int ig_score(const ig_model* model, const uint64_t* rows, int64_t m,
+             int64_t* A_out, int64_t* N_out, uint8_t* label_out,
+             ig_stream_t stream);
+
+/* Model persistence: a flat little-endian file (magic, version, K, counts,
+ * Regulation 3 statistics, then per class the canonical words, supports and
+ * scores).  ig_model_load places the model on the current device. */
+int ig_model_save(const ig_model* m, const char* path);
+int ig_model_load(const char* path, ig_model** out);
+void ig_model_free(ig_model* m);
+
+/* Message for the calling thread's most recent failed call ("" if none). */
+const char* ig_last_error(void);
+
+/* Per-stage device timing.  While enabled, the library records CUDA events
+ * around every kernel launch on the launching stream; ig_prof_read
+ * synchronizes and returns, for each stage s < IG_PROF_STAGES, the summed
+ * kernel time in milliseconds and the number of launches since the last
+ * reset.  Stage names are given by ig_prof_stage_name. */
+#define IG_PROF_STAGES 12
+int ig_prof_enable(int32_t on);
+int ig_prof_reset(void);
+int ig_prof_read(double* ms, int64_t* launches);
+const char* ig_prof_stage_name(int32_t stage);
+
+/* Number of kernels this library has launched in the process so far. */
+int64_t ig_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IG_GB300_H */

@@ -1,0 +1,296 @@
+"""Python binding of the GB300 IG library (include/ig.h).
+
+Argument marshalling only: every step of Interpretable Generalization --
+encoding (Section 3.1, Eq. 5), candidate generation (Eq. 1), coherence
+(Eq. 3 / Eq. 6), supports and scores (Eq. 2), evidence (Eq. 4) and labels
+(Regulations 1-3) -- runs in the library's CUDA kernels.  PyTorch provides
+device memory and the current stream.  The functions take either CUDA
+tensors (work is enqueued on the current stream) or numpy arrays (host
+buffers: the library copies in and out itself).
+
+Packed words are carried in torch.int64 / numpy.uint64 arrays: the library
+reads and writes the same 64 bits either way.
+
+There is no fallback: if the compiled library is missing or no GPU is usable,
+every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import buildlib as _build
+
+NORMAL = 0
+ATTACK = 1
+
+IG_OK = 0
+_ERRORS = {-1: "IG_E_INVAL", -2: "IG_E_NOMEM", -3: "IG_E_CUDA",
+           -4: "IG_E_TIMEOUT", -5: "IG_E_OVERFLOW", -6: "IG_E_INTERNAL",
+           -7: "IG_E_IO"}
+PROF_STAGES = 12
+
+
+class IGError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class ig_params(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_double), ("reg3_enabled", ctypes.c_int32),
+                ("subset_kernel", ctypes.c_int32)]
+
+
+class ig_model_info_t(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("reg3_enabled", ctypes.c_int32),
+                ("n_train", ctypes.c_int64 * 2),
+                ("n_candidates", ctypes.c_int64 * 2),
+                ("n_patterns", ctypes.c_int64 * 2),
+                ("n_pairs", ctypes.c_int64 * 2),
+                ("reg3_mu", ctypes.c_double), ("reg3_sigma", ctypes.c_double),
+                ("reg3_r", ctypes.c_double),
+                ("reg3_threshold", ctypes.c_double)]
+
+
+# Every symbol of include/ig.h with its ctypes signature.
+_P, _I64, _I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+SIGNATURES = {
+    "ig_encode": (ctypes.c_int, [_P, _I64, _I32, _P, _P, _I32, _P]),
+    "ig_fit": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _P, _P]),
+    "ig_model_info": (ctypes.c_int, [_P, _P]),
+    "ig_model_patterns": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
+    "ig_model_copy_patterns": (ctypes.c_int, [_P, _I32, _P, _P, _P, _P]),
+    "ig_score": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P]),
+    "ig_model_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "ig_model_load": (ctypes.c_int, [ctypes.c_char_p, _P]),
+    "ig_model_free": (None, [_P]),
+    "ig_last_error": (ctypes.c_char_p, []),
+    "ig_prof_enable": (ctypes.c_int, [_I32]),
+    "ig_prof_reset": (ctypes.c_int, []),
+    "ig_prof_read": (ctypes.c_int, [_P, _P]),
+    "ig_prof_stage_name": (ctypes.c_char_p, [_I32]),
+    "ig_launch_count": (ctypes.c_int64, []),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Loads libig_gb300.so (built by build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"IG CUDA library not built ({path} missing): run "
+            "paper_2507_14222_gb300.buildlib.build() first")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def build(force: bool = False) -> str:
+    return _build.build(force=force)
+
+
+def _check(rc: int):
+    if rc != IG_OK:
+        raise IGError(rc, load().ig_last_error().decode(errors="replace"))
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(x):
+    """Data pointer of a contiguous torch tensor or numpy array."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+def _rows_shape(rows):
+    if rows.ndim != 2:
+        raise ValueError("rows must be [n, K]")
+    return int(rows.shape[0]), int(rows.shape[1])
+
+
+def ig_encode(codes, cards, stream=None):
+    """One-hot packing (Section 3.1, Eq. 5) of codes[n, F] with cards[F].
+
+    codes: CUDA tensor (uint16/int16) or numpy uint16 array.  Returns the
+    packed rows as a CUDA int64 tensor or a numpy uint64 array, matching the
+    input's kind.
+    """
+    lib = load()
+    cards = np.ascontiguousarray(np.asarray(cards, dtype=np.uint16))
+    n, F = int(codes.shape[0]), int(codes.shape[1])
+    K = (int(cards.astype(np.int64).sum()) + 63) // 64
+    if _is_torch(codes):
+        import torch
+        out = torch.empty((n, K), dtype=torch.int64, device=codes.device)
+    else:
+        codes = np.ascontiguousarray(codes, dtype=np.uint16)
+        out = np.empty((n, K), dtype=np.uint64)
+    _check(lib.ig_encode(_ptr(codes), n, F, _ptr(cards), _ptr(out), K,
+                         _stream(stream) if _is_torch(codes) else None))
+    return out
+
+
+class Model:
+    """A fitted IG model (coherent dictionaries P+ / P-) owned by the library."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = ig_model_info_t()
+        _check(load().ig_model_info(self._h, ctypes.byref(inf)))
+        return {"K": inf.K, "reg3_enabled": bool(inf.reg3_enabled),
+                "n_train": tuple(inf.n_train),
+                "n_candidates": tuple(inf.n_candidates),
+                "n_patterns": tuple(inf.n_patterns),
+                "n_pairs": tuple(inf.n_pairs),
+                "reg3": (inf.reg3_mu, inf.reg3_sigma, inf.reg3_r,
+                         inf.reg3_threshold)}
+
+    def patterns(self, cls: int, device: str | None = None):
+        """(words uint64[P, K], support uint32[P], score uint64[P]) of class cls.
+
+        With device=None the arrays come back as numpy arrays (host copies);
+        otherwise as tensors on that CUDA device.
+        """
+        inf = self.info()
+        P, K = inf["n_patterns"][cls], inf["K"]
+        if device is None:
+            w = np.empty((P, K), np.uint64)
+            f = np.empty(P, np.uint32)
+            s = np.empty(P, np.uint64)
+            stream = None
+        else:
+            import torch
+            w = torch.empty((P, K), dtype=torch.int64, device=device)
+            f = torch.empty(P, dtype=torch.int32, device=device)
+            s = torch.empty(P, dtype=torch.int64, device=device)
+            stream = _stream(None)
+        _check(load().ig_model_copy_patterns(self._h, cls, _ptr(w), _ptr(f),
+                                             _ptr(s), stream))
+        return w, f, s
+
+    def save(self, path: str):
+        _check(load().ig_model_save(self._h, path.encode()))
+
+    def free(self):
+        if self._h:
+            load().ig_model_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def ig_fit(rows, labels, r: float | None = None, subset_kernel: int = 0,
+           stream=None) -> Model:
+    """IG training (Section 3.1: Eq. 1, Eq. 3, Eq. 2; Regulation 3 if r given).
+
+    rows: [n, K] packed records (CUDA int64 tensor or numpy uint64 array);
+    labels: [n] uint8, 1 = attack, 0 = normal.
+    """
+    lib = load()
+    n, K = _rows_shape(rows)
+    if not _is_torch(rows):
+        rows = np.ascontiguousarray(rows, dtype=np.uint64)
+    if not _is_torch(labels):
+        labels = np.ascontiguousarray(labels, dtype=np.uint8)
+    prm = ig_params(float(r) if r is not None else 0.0, 1 if r is not None else 0,
+                    int(subset_kernel))
+    h = ctypes.c_void_p()
+    _check(lib.ig_fit(_ptr(rows), _ptr(labels), n, K, ctypes.byref(prm),
+                      ctypes.byref(h), _stream(stream) if _is_torch(rows) else None))
+    return Model(h)
+
+
+def ig_score(model: Model, rows, stream=None):
+    """IG inference (Eq. 4, Regulations 1-3): returns (A, N, labels)."""
+    lib = load()
+    m, K = _rows_shape(rows)
+    if _is_torch(rows):
+        import torch
+        A = torch.empty(m, dtype=torch.int64, device=rows.device)
+        N = torch.empty(m, dtype=torch.int64, device=rows.device)
+        lab = torch.empty(m, dtype=torch.uint8, device=rows.device)
+        stream = _stream(stream)
+    else:
+        rows = np.ascontiguousarray(rows, dtype=np.uint64)
+        A = np.empty(m, np.int64)
+        N = np.empty(m, np.int64)
+        lab = np.empty(m, np.uint8)
+        stream = None
+    _check(lib.ig_score(model.handle, _ptr(rows), m, _ptr(A), _ptr(N), _ptr(lab),
+                        stream))
+    return A, N, lab
+
+
+def ig_model_load(path: str) -> Model:
+    h = ctypes.c_void_p()
+    _check(load().ig_model_load(path.encode(), ctypes.byref(h)))
+    return Model(h)
+
+
+def prof_enable(on: bool = True):
+    _check(load().ig_prof_enable(1 if on else 0))
+
+
+def prof_reset():
+    _check(load().ig_prof_reset())
+
+
+def prof_read() -> dict:
+    """{stage name: (total ms, timed launches)} since the last reset."""
+    lib = load()
+    ms = (ctypes.c_double * PROF_STAGES)()
+    n = (ctypes.c_int64 * PROF_STAGES)()
+    _check(lib.ig_prof_read(ms, n))
+    return {lib.ig_prof_stage_name(i).decode(): (ms[i], n[i])
+            for i in range(PROF_STAGES)}
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(load().ig_launch_count())
+
+
+# Short aliases.
+encode, fit, score, model_load = ig_encode, ig_fit, ig_score, ig_model_load

@@ -1,0 +1,814 @@
+// C ABI of the IG library (declared in include/ig.h): argument checks,
+// staging of host buffers, the orchestration of IG training (Section 3.1:
+// Eq. 1 -> Eq. 3 -> Eq. 2 per class, then the Regulation 3 statistics) and
+// inference (Eq. 4, Regulations 1-3), model persistence and stage timing.
+// Every step of the computation runs in the kernels of encode.cu, dedup.cu,
+// subset.cu and sort.cu; this file only sizes buffers and launches them.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/ig.h"
+#include "common.cuh"
+#include "internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int fail_cuda(cudaError_t e, const char* where) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(IG_E_NOMEM, "%s: device allocation failed (%s)", where,
+                cudaGetErrorString(e));
+  return fail(IG_E_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define IG_CUDA(expr, where)                          \
+  do {                                                \
+    cudaError_t e_ = (expr);                          \
+    if (e_ != cudaSuccess) return fail_cuda(e_, where); \
+  } while (0)
+
+#define IG_CHECK(expr)           \
+  do {                           \
+    int rc_ = (expr);            \
+    if (rc_ != IG_OK) return rc_; \
+  } while (0)
+
+// ---- per-stage timing -------------------------------------------------------
+const char* kStageNames[IG_PROF_STAGES] = {
+    "encode",        "split",          "pair_insert", "rehash",
+    "compact",       "coherence",      "select",      "canonical_sort",
+    "support",       "pattern_score",  "evidence",    "labels"};
+enum Stage {
+  S_ENCODE, S_SPLIT, S_PAIR, S_REHASH, S_COMPACT, S_COHERENCE,
+  S_SELECT, S_SORT, S_SUPPORT, S_PSCORE, S_EVIDENCE, S_LABELS
+};
+
+struct Prof {
+  std::mutex mu;
+  bool on = false;
+  double ms[IG_PROF_STAGES] = {};
+  int64_t launches[IG_PROF_STAGES] = {};
+  struct Pending {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+};
+Prof g_prof;
+
+cudaEvent_t prof_event() {
+  if (!g_prof.pool.empty()) {
+    cudaEvent_t e = g_prof.pool.back();
+    g_prof.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets the launches of one stage with CUDA events on their stream.
+struct ProfScope {
+  int stage;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  ProfScope(int st, cudaStream_t stream) : stage(st), s(stream) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    if (!g_prof.on) return;
+    a = prof_event();
+    cudaEventRecord(a, s);
+  }
+  ~ProfScope() {
+    if (!a) return;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    cudaEvent_t b = prof_event();
+    cudaEventRecord(b, s);
+    g_prof.pending.push_back({stage, a, b});
+  }
+};
+
+void prof_drain_locked() {
+  for (auto& p : g_prof.pending) {
+    cudaEventSynchronize(p.b);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      g_prof.ms[p.stage] += ms;
+      g_prof.launches[p.stage] += 1;
+    }
+    g_prof.pool.push_back(p.a);
+    g_prof.pool.push_back(p.b);
+  }
+  g_prof.pending.clear();
+}
+
+// ---- device buffers ---------------------------------------------------------
+// Stream-ordered allocation; freed on the same stream when the owner goes
+// out of scope (or kept by release()).
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  cudaStream_t s = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { reset(); }
+  void reset() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+  }
+  cudaError_t alloc(size_t count, cudaStream_t stream) {
+    reset();
+    s = stream;
+    if (count == 0) count = 1;
+    return cudaMallocAsync(reinterpret_cast<void**>(&p), count * sizeof(T), stream);
+  }
+  T* release() {
+    T* q = p;
+    p = nullptr;
+    return q;
+  }
+};
+
+// True for CUDA device (or managed) memory; the calling thread's current
+// device is then switched to the device that owns it, so that every later
+// allocation and launch of the call happens there.
+bool is_device_pointer(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) return false;
+  int cur = -1;
+  if (cudaGetDevice(&cur) == cudaSuccess && cur != attr.device && attr.device >= 0)
+    cudaSetDevice(attr.device);
+  return true;
+}
+
+// An input array as a device pointer: either the caller's own device array,
+// or a stream-ordered device copy of the caller's host array.
+template <class T>
+struct InputView {
+  const T* d = nullptr;
+  DevBuf<T> copy;
+  int bind(const T* p, size_t count, cudaStream_t s, const char* what) {
+    if (count == 0) {
+      d = p;
+      return IG_OK;
+    }
+    if (is_device_pointer(p)) {
+      d = p;
+      return IG_OK;
+    }
+    IG_CUDA(copy.alloc(count, s), what);
+    IG_CUDA(cudaMemcpyAsync(copy.p, p, count * sizeof(T), cudaMemcpyHostToDevice, s), what);
+    d = copy.p;
+    return IG_OK;
+  }
+};
+
+// An output array: written in place when it is on the device, otherwise
+// produced in a device buffer and copied back by finish().
+template <class T>
+struct OutputView {
+  T* user = nullptr;
+  T* d = nullptr;
+  size_t count = 0;
+  bool host = false;
+  DevBuf<T> buf;
+  int bind(T* p, size_t n, cudaStream_t s, const char* what) {
+    user = p;
+    count = n;
+    if (p && is_device_pointer(p)) {
+      d = p;
+      return IG_OK;
+    }
+    host = p != nullptr;
+    IG_CUDA(buf.alloc(n, s), what);
+    d = buf.p;
+    return IG_OK;
+  }
+  int finish(cudaStream_t s, const char* what) {
+    if (host && count)
+      IG_CUDA(cudaMemcpyAsync(user, d, count * sizeof(T), cudaMemcpyDeviceToHost, s), what);
+    return IG_OK;
+  }
+};
+
+int read_status(int* d_status, cudaStream_t s, const char* where) {
+  int st = 0;
+  IG_CUDA(cudaMemcpyAsync(&st, d_status, sizeof(int), cudaMemcpyDeviceToHost, s), where);
+  IG_CUDA(cudaStreamSynchronize(s), where);
+  if (st & igk::ST_BAD_INPUT)
+    return fail(IG_E_INVAL, "%s: input value out of range (code >= card or label > 1)", where);
+  if (st & igk::ST_TIMEOUT) return fail(IG_E_TIMEOUT, "%s: a bounded device wait ran out", where);
+  if (st & igk::ST_TABLE_FULL) return fail(IG_E_INTERNAL, "%s: hash table full", where);
+  return IG_OK;
+}
+
+std::atomic<long long> g_launches{0};
+
+}  // namespace
+
+void igk::count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int igk::num_sms() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 148;
+  if (!cached[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = v > 0 ? v : 148;
+  }
+  return cached[dev];
+}
+
+struct ig_model {
+  int K = 0, KT = 0;
+  int64_t n_train[2] = {0, 0}, n_cand[2] = {0, 0}, n_pat[2] = {0, 0}, n_pairs[2] = {0, 0};
+  uint64_t* words[2] = {nullptr, nullptr};     // stride K (API view)
+  uint64_t* words_kt[2] = {nullptr, nullptr};  // stride KT, pad_rows rows
+  uint32_t* support[2] = {nullptr, nullptr};
+  uint64_t* score[2] = {nullptr, nullptr};     // pad_rows entries
+  int reg3 = 0;
+  double mu = 0, sigma = 0, r = 0, thr = 0;
+};
+
+static void model_release(ig_model* m) {
+  if (!m) return;
+  for (int c = 0; c < 2; ++c) {
+    if (m->words[c] && m->words[c] != m->words_kt[c]) cudaFree(m->words[c]);
+    if (m->words_kt[c]) cudaFree(m->words_kt[c]);
+    if (m->support[c]) cudaFree(m->support[c]);
+    if (m->score[c]) cudaFree(m->score[c]);
+  }
+  delete m;
+}
+
+namespace {
+
+// Candidate generation (Eq. 1) for one class: every row-tile band of the
+// pair triangle is inserted into the hash table after making sure that the
+// table could absorb every pair of the band as a new key at load <= 0.7;
+// the table doubles (with a rehash) when it could not.
+int build_candidates(const uint64_t* X, int64_t n, int KT, cudaStream_t s,
+                     int* d_status, unsigned long long* h_count,
+                     DevBuf<uint64_t>& cand, int64_t* U_out) {
+  using igk::HashTable;
+  const int64_t T = igk::kPairTile;
+  const int64_t nt = igk::ceil_div(n, T);
+  auto band_pairs = [&](int64_t r) { return (nt - r) * T * T; };
+  const double kLoad = 0.7;
+
+  DevBuf<uint32_t> tags;
+  DevBuf<uint64_t> keys;
+  DevBuf<unsigned long long> count;
+  IG_CUDA(count.alloc(1, s), "ig_fit: table counter");
+  IG_CUDA(cudaMemsetAsync(count.p, 0, sizeof(unsigned long long), s), "ig_fit");
+
+  uint64_t cap = 1u << 16;
+  const int64_t want = std::max<int64_t>(band_pairs(0) * 2, 16 * n);
+  while (double(cap) * kLoad < double(want)) cap <<= 1;
+  auto make_table = [&](uint64_t c, DevBuf<uint32_t>& tg, DevBuf<uint64_t>& ky) -> int {
+    IG_CUDA(tg.alloc(c, s), "ig_fit: hash table");
+    IG_CUDA(ky.alloc(c * KT, s), "ig_fit: hash table");
+    IG_CUDA(cudaMemsetAsync(tg.p, 0, c * sizeof(uint32_t), s), "ig_fit");
+    return IG_OK;
+  };
+  IG_CHECK(make_table(cap, tags, keys));
+
+  uint64_t stored = 0;
+  int64_t r = 0;
+  while (r < nt) {
+    // Grow until at least the next band fits as all-new keys.
+    while (double(stored) + double(band_pairs(r)) > kLoad * double(cap)) {
+      uint64_t ncap = cap << 1;
+      DevBuf<uint32_t> ntags;
+      DevBuf<uint64_t> nkeys;
+      DevBuf<unsigned long long> ncount;
+      IG_CHECK(make_table(ncap, ntags, nkeys));
+      IG_CUDA(ncount.alloc(1, s), "ig_fit: table counter");
+      IG_CUDA(cudaMemsetAsync(ncount.p, 0, sizeof(unsigned long long), s), "ig_fit");
+      {
+        ProfScope ps(S_REHASH, s);
+        IG_CUDA(igk::launch_rehash(HashTable{tags.p, keys.p, cap, count.p},
+                                   HashTable{ntags.p, nkeys.p, ncap, ncount.p}, KT,
+                                   d_status, s),
+                "ig_fit: rehash");
+      }
+      std::swap(tags.p, ntags.p);
+      std::swap(keys.p, nkeys.p);
+      std::swap(count.p, ncount.p);
+      cap = ncap;
+    }
+    int64_t r2 = r;
+    double budget = kLoad * double(cap) - double(stored);
+    while (r2 < nt && double(band_pairs(r2)) <= budget) {
+      budget -= double(band_pairs(r2));
+      ++r2;
+    }
+    {
+      ProfScope ps(S_PAIR, s);
+      IG_CUDA(igk::launch_pair_insert(X, n, KT, r, r2, HashTable{tags.p, keys.p, cap, count.p},
+                                      d_status, s),
+              "ig_fit: pair intersection");
+    }
+    r = r2;
+    IG_CUDA(cudaMemcpyAsync(h_count, count.p, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, s),
+            "ig_fit");
+    IG_CUDA(cudaStreamSynchronize(s), "ig_fit");
+    stored = *h_count;
+  }
+  IG_CHECK(read_status(d_status, s, "ig_fit: candidate generation"));
+  const int64_t U = int64_t(stored);
+  if (U > int64_t(0xffffffffll)) return fail(IG_E_OVERFLOW, "ig_fit: too many candidates");
+  IG_CUDA(cand.alloc(size_t(igk::pad_rows(U)) * KT, s), "ig_fit: candidates");
+  DevBuf<unsigned long long> out_count;
+  IG_CUDA(out_count.alloc(1, s), "ig_fit");
+  IG_CUDA(cudaMemsetAsync(out_count.p, 0, sizeof(unsigned long long), s), "ig_fit");
+  {
+    ProfScope ps(S_COMPACT, s);
+    IG_CUDA(igk::launch_compact(HashTable{tags.p, keys.p, cap, count.p}, KT, cand.p,
+                                out_count.p, s),
+            "ig_fit: compact");
+  }
+  IG_CUDA(cudaMemcpyAsync(h_count, out_count.p, sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, s),
+          "ig_fit");
+  IG_CUDA(cudaStreamSynchronize(s), "ig_fit");
+  if (int64_t(*h_count) != U) return fail(IG_E_INTERNAL, "ig_fit: compaction count mismatch");
+  *U_out = U;
+  return IG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ig_last_error(void) { return g_last_error.c_str(); }
+
+int ig_encode(const uint16_t* codes, int64_t n, int32_t F, const uint16_t* cards,
+              uint64_t* words_out, int32_t K, ig_stream_t stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (n < 0 || F <= 0 || !cards || (n > 0 && (!codes || !words_out)))
+    return fail(IG_E_INVAL, "ig_encode: bad arguments");
+  std::vector<uint32_t> offsets(F + 1, 0);
+  for (int f = 0; f < F; ++f) {
+    if (cards[f] == 0) return fail(IG_E_INVAL, "ig_encode: feature %d has cardinality 0", f);
+    offsets[f + 1] = offsets[f] + cards[f];
+  }
+  const int64_t L = offsets[F];
+  if (K != int32_t((L + 63) / 64))
+    return fail(IG_E_INVAL, "ig_encode: K = %d but ceil(L/64) = %lld", K, (long long)((L + 63) / 64));
+  if (K < 1 || K > IG_MAX_WORDS) return fail(IG_E_INVAL, "ig_encode: K = %d out of range", K);
+  if (n == 0) return IG_OK;
+  InputView<uint16_t> in;
+  IG_CHECK(in.bind(codes, size_t(n) * F, s, "ig_encode: codes"));
+  OutputView<uint64_t> out;
+  IG_CHECK(out.bind(words_out, size_t(n) * K, s, "ig_encode: output"));
+  DevBuf<uint32_t> d_off;
+  DevBuf<int> d_status;
+  IG_CUDA(d_off.alloc(F + 1, s), "ig_encode");
+  IG_CUDA(d_status.alloc(1, s), "ig_encode");
+  IG_CUDA(cudaMemcpyAsync(d_off.p, offsets.data(), sizeof(uint32_t) * (F + 1),
+                          cudaMemcpyHostToDevice, s),
+          "ig_encode");
+  IG_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), s), "ig_encode");
+  {
+    ProfScope ps(S_ENCODE, s);
+    IG_CUDA(igk::launch_encode(in.d, n, F, d_off.p, nullptr, out.d, K, d_status.p, s),
+            "ig_encode: kernel");
+  }
+  IG_CHECK(out.finish(s, "ig_encode: copy back"));
+  return read_status(d_status.p, s, "ig_encode");
+}
+
+int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
+           const ig_params* params, ig_model** out, ig_stream_t stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!out) return fail(IG_E_INVAL, "ig_fit: out is NULL");
+  *out = nullptr;
+  if (!rows || !labels || n < 2) return fail(IG_E_INVAL, "ig_fit: need at least two records");
+  if (K < 1 || K > IG_MAX_WORDS) return fail(IG_E_INVAL, "ig_fit: K = %d out of range", K);
+  if (n > int64_t(0x7fffffff)) return fail(IG_E_OVERFLOW, "ig_fit: too many records");
+  ig_params prm{0.0, 0, 0};
+  if (params) prm = *params;
+  if (prm.subset_kernel != 0 && prm.subset_kernel != 1)
+    return fail(IG_E_INVAL, "ig_fit: unknown subset_kernel %d", prm.subset_kernel);
+  if (prm.reg3_enabled && !std::isfinite(prm.r))
+    return fail(IG_E_INVAL, "ig_fit: Regulation 3 needs a finite r");
+  const int KT = igk::padded_words(K);
+
+  InputView<uint64_t> in_rows;
+  InputView<uint8_t> in_lab;
+  IG_CHECK(in_rows.bind(rows, size_t(n) * K, s, "ig_fit: rows"));
+  IG_CHECK(in_lab.bind(labels, size_t(n), s, "ig_fit: labels"));
+
+  DevBuf<int> d_status;
+  DevBuf<unsigned long long> d_counts;
+  IG_CUDA(d_status.alloc(1, s), "ig_fit");
+  IG_CUDA(d_counts.alloc(2, s), "ig_fit");
+  IG_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), s), "ig_fit");
+  // Pinned host words for size read-backs: [0..1] class counts, [2] scratch.
+  static thread_local unsigned long long* h_pinned = nullptr;
+  if (!h_pinned) IG_CUDA(cudaMallocHost(&h_pinned, 4 * sizeof(unsigned long long)), "ig_fit");
+
+  // Section 3.2: class-stacked row matrices (normal -> X[0], attack -> X[1]).
+  DevBuf<uint64_t> X[2];
+  for (int c = 0; c < 2; ++c) IG_CUDA(X[c].alloc(size_t(igk::pad_rows(n)) * KT, s), "ig_fit: rows");
+  {
+    ProfScope ps(S_SPLIT, s);
+    IG_CUDA(igk::launch_split(in_rows.d, in_lab.d, n, K, KT, X[0].p, X[1].p, d_counts.p,
+                              d_status.p, s),
+            "ig_fit: split");
+  }
+  IG_CUDA(cudaMemcpyAsync(h_pinned, d_counts.p, 2 * sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, s),
+          "ig_fit");
+  IG_CHECK(read_status(d_status.p, s, "ig_fit: labels"));
+  const int64_t nc[2] = {int64_t(h_pinned[0]), int64_t(h_pinned[1])};
+  if (nc[0] == 0 || nc[1] == 0) return fail(IG_E_INVAL, "ig_fit: both classes must be non-empty");
+
+  ig_model* m = new ig_model;
+  struct ModelGuard {
+    ig_model* m;
+    ~ModelGuard() { model_release(m); }
+  } guard{m};
+  m->K = K;
+  m->KT = KT;
+
+  for (int c = 1; c >= 0; --c) {
+    const int o = 1 - c;
+    m->n_train[c] = nc[c];
+    m->n_pairs[c] = nc[c] * (nc[c] - 1) / 2;
+    // Eq. 1: B^c, deduplicated on the device.
+    DevBuf<uint64_t> cand;
+    int64_t U = 0;
+    IG_CHECK(build_candidates(X[c].p, nc[c], KT, s, d_status.p, h_pinned + 2, cand, &U));
+    m->n_cand[c] = U;
+    // Eq. 3 (tested as Eq. 6): drop candidates inside any opposite record.
+    DevBuf<uint32_t> covered;
+    IG_CUDA(covered.alloc(size_t(U), s), "ig_fit");
+    IG_CUDA(cudaMemsetAsync(covered.p, 0, sizeof(uint32_t) * U, s), "ig_fit");
+    {
+      ProfScope ps(S_COHERENCE, s);
+      igk::SubsetArgs a{igk::MODE_ANY, KT, cand.p, U, KT, X[o].p, nullptr, nc[o],
+                        covered.p, nullptr, d_status.p};
+      IG_CUDA(igk::launch_subset(a, s), "ig_fit: coherence");
+    }
+    DevBuf<uint64_t> surv;
+    DevBuf<unsigned long long> d_kept;
+    IG_CUDA(surv.alloc(size_t(igk::pad_rows(U)) * KT, s), "ig_fit");
+    IG_CUDA(d_kept.alloc(1, s), "ig_fit");
+    IG_CUDA(cudaMemsetAsync(d_kept.p, 0, sizeof(unsigned long long), s), "ig_fit");
+    {
+      ProfScope ps(S_SELECT, s);
+      IG_CUDA(igk::launch_select_unflagged(cand.p, U, KT, covered.p, surv.p, d_kept.p, s),
+              "ig_fit: select");
+    }
+    IG_CUDA(cudaMemcpyAsync(h_pinned + 2, d_kept.p, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, s),
+            "ig_fit");
+    IG_CHECK(read_status(d_status.p, s, "ig_fit: coherence"));
+    const int64_t P = int64_t(h_pinned[2]);
+    m->n_pat[c] = P;
+    cand.reset();
+    covered.reset();
+    // Canonical order of P^c.
+    IG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&m->words_kt[c]),
+                            sizeof(uint64_t) * std::max<int64_t>(1, igk::pad_rows(P)) * KT, s),
+            "ig_fit: patterns");
+    {
+      ProfScope ps(S_SORT, s);
+      IG_CUDA(igk::canonical_sort(surv.p, P, KT, m->words_kt[c], d_status.p, s),
+              "ig_fit: canonical sort");
+    }
+    surv.reset();
+    // Eq. 2: support f_c and score S_c = f_c * |b|^2.
+    IG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&m->support[c]),
+                            sizeof(uint32_t) * std::max<int64_t>(1, P), s),
+            "ig_fit: supports");
+    IG_CUDA(cudaMemsetAsync(m->support[c], 0, sizeof(uint32_t) * std::max<int64_t>(1, P), s),
+            "ig_fit");
+    {
+      ProfScope ps(S_SUPPORT, s);
+      igk::SubsetArgs a{igk::MODE_COUNT, KT, m->words_kt[c], P, KT, X[c].p, nullptr, nc[c],
+                        m->support[c], nullptr, d_status.p};
+      IG_CUDA(igk::launch_subset(a, s), "ig_fit: support");
+    }
+    const size_t npad = size_t(std::max<int64_t>(1, igk::pad_rows(P)));
+    IG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&m->score[c]), sizeof(uint64_t) * npad, s),
+            "ig_fit: scores");
+    IG_CUDA(cudaMemsetAsync(m->score[c], 0, sizeof(uint64_t) * npad, s), "ig_fit");
+    {
+      ProfScope ps(S_PSCORE, s);
+      IG_CUDA(igk::launch_pattern_score(m->words_kt[c], P, KT, m->support[c], m->score[c], s),
+              "ig_fit: score");
+    }
+    if (K == KT) {
+      m->words[c] = m->words_kt[c];
+    } else {
+      IG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&m->words[c]),
+                              sizeof(uint64_t) * std::max<int64_t>(1, P) * K, s),
+              "ig_fit");
+      if (P)
+        IG_CUDA(cudaMemcpy2DAsync(m->words[c], K * sizeof(uint64_t), m->words_kt[c],
+                                  KT * sizeof(uint64_t), K * sizeof(uint64_t), P,
+                                  cudaMemcpyDeviceToDevice, s),
+                "ig_fit");
+    }
+  }
+
+  // Regulation 3: mean and population std of N over the training normals,
+  // in double precision and record order.
+  if (prm.reg3_enabled) {
+    DevBuf<unsigned long long> d_n;
+    IG_CUDA(d_n.alloc(size_t(nc[0]), s), "ig_fit");
+    IG_CUDA(cudaMemsetAsync(d_n.p, 0, sizeof(unsigned long long) * nc[0], s), "ig_fit");
+    {
+      ProfScope ps(S_EVIDENCE, s);
+      igk::SubsetArgs a{igk::MODE_SUM, KT, X[0].p, nc[0], KT, m->words_kt[0], m->score[0],
+                        m->n_pat[0], nullptr, d_n.p, d_status.p};
+      IG_CUDA(igk::launch_subset(a, s), "ig_fit: Regulation 3 evidence");
+    }
+    std::vector<unsigned long long> hn(static_cast<size_t>(nc[0]));
+    IG_CUDA(cudaMemcpyAsync(hn.data(), d_n.p, sizeof(unsigned long long) * nc[0],
+                            cudaMemcpyDeviceToHost, s),
+            "ig_fit");
+    IG_CHECK(read_status(d_status.p, s, "ig_fit: Regulation 3"));
+    double sum = 0.0;
+    for (int64_t i = 0; i < nc[0]; ++i) sum += double(int64_t(hn[i]));
+    const double mean = sum / double(nc[0]);
+    double ss = 0.0;
+    for (int64_t i = 0; i < nc[0]; ++i) {
+      const double d = double(int64_t(hn[i])) - mean;
+      ss += d * d;
+    }
+    m->reg3 = 1;
+    m->mu = mean;
+    m->sigma = std::sqrt(ss / double(nc[0]));
+    m->r = prm.r;
+    const double scaled = prm.r * m->sigma;
+    m->thr = m->mu - scaled;
+  }
+  IG_CHECK(read_status(d_status.p, s, "ig_fit"));
+  guard.m = nullptr;
+  *out = m;
+  return IG_OK;
+}
+
+int ig_model_info(const ig_model* m, ig_model_info_t* info) {
+  if (!m || !info) return fail(IG_E_INVAL, "ig_model_info: NULL argument");
+  info->K = m->K;
+  info->reg3_enabled = m->reg3;
+  for (int c = 0; c < 2; ++c) {
+    info->n_train[c] = m->n_train[c];
+    info->n_candidates[c] = m->n_cand[c];
+    info->n_patterns[c] = m->n_pat[c];
+    info->n_pairs[c] = m->n_pairs[c];
+  }
+  info->reg3_mu = m->mu;
+  info->reg3_sigma = m->sigma;
+  info->reg3_r = m->r;
+  info->reg3_threshold = m->thr;
+  return IG_OK;
+}
+
+int ig_model_patterns(const ig_model* m, int32_t cls, const uint64_t** words,
+                      const uint32_t** support, const uint64_t** score) {
+  if (!m || (cls != 0 && cls != 1)) return fail(IG_E_INVAL, "ig_model_patterns: bad arguments");
+  if (words) *words = m->words[cls];
+  if (support) *support = m->support[cls];
+  if (score) *score = m->score[cls];
+  return IG_OK;
+}
+
+int ig_model_copy_patterns(const ig_model* m, int32_t cls, uint64_t* words_out,
+                           uint32_t* support_out, uint64_t* score_out,
+                           ig_stream_t stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!m || (cls != 0 && cls != 1)) return fail(IG_E_INVAL, "ig_model_copy_patterns: bad arguments");
+  const int64_t P = m->n_pat[cls];
+  if (P == 0) return IG_OK;
+  if (words_out)
+    IG_CUDA(cudaMemcpyAsync(words_out, m->words[cls], sizeof(uint64_t) * P * m->K,
+                            cudaMemcpyDefault, s), "ig_model_copy_patterns");
+  if (support_out)
+    IG_CUDA(cudaMemcpyAsync(support_out, m->support[cls], sizeof(uint32_t) * P,
+                            cudaMemcpyDefault, s), "ig_model_copy_patterns");
+  if (score_out)
+    IG_CUDA(cudaMemcpyAsync(score_out, m->score[cls], sizeof(uint64_t) * P, cudaMemcpyDefault, s),
+            "ig_model_copy_patterns");
+  IG_CUDA(cudaStreamSynchronize(s), "ig_model_copy_patterns");
+  return IG_OK;
+}
+
+int ig_score(const ig_model* m, const uint64_t* rows, int64_t n_rows, int64_t* A_out,
+             int64_t* N_out, uint8_t* label_out, ig_stream_t stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!m || n_rows < 0 || (n_rows > 0 && !rows)) return fail(IG_E_INVAL, "ig_score: bad arguments");
+  if (n_rows == 0) return IG_OK;
+  InputView<uint64_t> in;
+  IG_CHECK(in.bind(rows, size_t(n_rows) * m->K, s, "ig_score: rows"));
+  OutputView<unsigned long long> A, N;
+  OutputView<uint8_t> lab;
+  IG_CHECK(A.bind(reinterpret_cast<unsigned long long*>(A_out), size_t(n_rows), s, "ig_score"));
+  IG_CHECK(N.bind(reinterpret_cast<unsigned long long*>(N_out), size_t(n_rows), s, "ig_score"));
+  if (label_out) IG_CHECK(lab.bind(label_out, size_t(n_rows), s, "ig_score"));
+  DevBuf<int> d_status;
+  IG_CUDA(d_status.alloc(1, s), "ig_score");
+  IG_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), s), "ig_score");
+  IG_CUDA(cudaMemsetAsync(A.d, 0, sizeof(unsigned long long) * n_rows, s), "ig_score");
+  IG_CUDA(cudaMemsetAsync(N.d, 0, sizeof(unsigned long long) * n_rows, s), "ig_score");
+  for (int c = 1; c >= 0; --c) {  // A from P+, then N from P- (Eq. 4)
+    ProfScope ps(S_EVIDENCE, s);
+    igk::SubsetArgs a{igk::MODE_SUM, m->KT, in.d, n_rows, m->K, m->words_kt[c], m->score[c],
+                      m->n_pat[c], nullptr, c == 1 ? A.d : N.d, d_status.p};
+    IG_CUDA(igk::launch_subset(a, s), "ig_score: evidence");
+  }
+  if (label_out) {
+    ProfScope ps(S_LABELS, s);
+    IG_CUDA(igk::launch_labels(A.d, N.d, n_rows, m->reg3, m->thr, lab.d, s), "ig_score: labels");
+  }
+  IG_CHECK(A.finish(s, "ig_score"));
+  IG_CHECK(N.finish(s, "ig_score"));
+  if (label_out) IG_CHECK(lab.finish(s, "ig_score"));
+  return read_status(d_status.p, s, "ig_score");
+}
+
+// ---- persistence ------------------------------------------------------------
+static const char kMagic[8] = {'I', 'G', 'G', 'B', '3', '0', '0', 0};
+static const uint32_t kVersion = 1;
+
+int ig_model_save(const ig_model* m, const char* path) {
+  if (!m || !path) return fail(IG_E_INVAL, "ig_model_save: NULL argument");
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(IG_E_IO, "ig_model_save: cannot open %s", path);
+  bool ok = true;
+  auto put = [&](const void* p, size_t n) { ok = ok && fwrite(p, 1, n, f) == n; };
+  uint32_t hdr[4] = {kVersion, uint32_t(m->K), uint32_t(m->reg3), 0};
+  double st[4] = {m->mu, m->sigma, m->r, m->thr};
+  put(kMagic, 8);
+  put(hdr, sizeof(hdr));
+  put(st, sizeof(st));
+  put(m->n_train, sizeof(m->n_train));
+  put(m->n_cand, sizeof(m->n_cand));
+  put(m->n_pairs, sizeof(m->n_pairs));
+  put(m->n_pat, sizeof(m->n_pat));
+  for (int c = 0; c < 2 && ok; ++c) {
+    const int64_t P = m->n_pat[c];
+    std::vector<uint64_t> w(size_t(P) * m->K);
+    std::vector<uint32_t> sup(static_cast<size_t>(P));
+    std::vector<uint64_t> sc(static_cast<size_t>(P));
+    if (P) {
+      if (cudaMemcpy(w.data(), m->words[c], w.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+          cudaMemcpy(sup.data(), m->support[c], sup.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+          cudaMemcpy(sc.data(), m->score[c], sc.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        fclose(f);
+        return fail(IG_E_CUDA, "ig_model_save: copy from device failed");
+      }
+    }
+    put(w.data(), w.size() * 8);
+    put(sup.data(), sup.size() * 4);
+    put(sc.data(), sc.size() * 8);
+  }
+  if (fclose(f) != 0) ok = false;
+  return ok ? IG_OK : fail(IG_E_IO, "ig_model_save: write to %s failed", path);
+}
+
+int ig_model_load(const char* path, ig_model** out) {
+  if (!path || !out) return fail(IG_E_INVAL, "ig_model_load: NULL argument");
+  *out = nullptr;
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(IG_E_IO, "ig_model_load: cannot open %s", path);
+  bool ok = true;
+  auto get = [&](void* p, size_t n) { ok = ok && fread(p, 1, n, f) == n; };
+  char magic[8];
+  uint32_t hdr[4];
+  double st[4];
+  ig_model* m = new ig_model;
+  get(magic, 8);
+  get(hdr, sizeof(hdr));
+  get(st, sizeof(st));
+  get(m->n_train, sizeof(m->n_train));
+  get(m->n_cand, sizeof(m->n_cand));
+  get(m->n_pairs, sizeof(m->n_pairs));
+  get(m->n_pat, sizeof(m->n_pat));
+  if (!ok || memcmp(magic, kMagic, 8) != 0 || hdr[0] != kVersion || hdr[1] < 1 ||
+      hdr[1] > IG_MAX_WORDS || m->n_pat[0] < 0 || m->n_pat[1] < 0) {
+    fclose(f);
+    model_release(m);
+    return fail(IG_E_IO, "ig_model_load: %s is not an IG model file", path);
+  }
+  m->K = int(hdr[1]);
+  m->KT = igk::padded_words(m->K);
+  m->reg3 = int(hdr[2]);
+  m->mu = st[0];
+  m->sigma = st[1];
+  m->r = st[2];
+  m->thr = st[3];
+  for (int c = 0; c < 2 && ok; ++c) {
+    const int64_t P = m->n_pat[c];
+    std::vector<uint64_t> w(size_t(P) * m->K), wk(size_t(std::max<int64_t>(1, igk::pad_rows(P))) * m->KT, 0);
+    std::vector<uint32_t> sup(static_cast<size_t>(P));
+    std::vector<uint64_t> sc(size_t(std::max<int64_t>(1, igk::pad_rows(P))), 0);
+    get(w.data(), w.size() * 8);
+    get(sup.data(), sup.size() * 4);
+    get(sc.data(), size_t(P) * 8);
+    if (!ok) break;
+    for (int64_t i = 0; i < P; ++i)
+      for (int k = 0; k < m->K; ++k) wk[size_t(i) * m->KT + k] = w[size_t(i) * m->K + k];
+    bool cu = cudaMalloc(&m->words_kt[c], wk.size() * 8) == cudaSuccess &&
+              cudaMemcpy(m->words_kt[c], wk.data(), wk.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMalloc(&m->support[c], std::max<size_t>(1, sup.size()) * 4) == cudaSuccess &&
+              (sup.empty() || cudaMemcpy(m->support[c], sup.data(), sup.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess) &&
+              cudaMalloc(&m->score[c], sc.size() * 8) == cudaSuccess &&
+              cudaMemcpy(m->score[c], sc.data(), sc.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (cu && m->K == m->KT) {
+      m->words[c] = m->words_kt[c];
+    } else if (cu) {
+      cu = cudaMalloc(&m->words[c], std::max<size_t>(1, w.size()) * 8) == cudaSuccess &&
+           (w.empty() || cudaMemcpy(m->words[c], w.data(), w.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess);
+    }
+    if (!cu) {
+      fclose(f);
+      model_release(m);
+      return fail(IG_E_CUDA, "ig_model_load: device allocation or copy failed");
+    }
+  }
+  fclose(f);
+  if (!ok) {
+    model_release(m);
+    return fail(IG_E_IO, "ig_model_load: %s is truncated", path);
+  }
+  *out = m;
+  return IG_OK;
+}
+
+void ig_model_free(ig_model* m) {
+  if (!m) return;
+  cudaDeviceSynchronize();
+  model_release(m);
+}
+
+int ig_prof_enable(int32_t on) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  g_prof.on = on != 0;
+  return IG_OK;
+}
+
+int ig_prof_reset(void) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  prof_drain_locked();
+  for (int i = 0; i < IG_PROF_STAGES; ++i) {
+    g_prof.ms[i] = 0;
+    g_prof.launches[i] = 0;
+  }
+  return IG_OK;
+}
+
+int ig_prof_read(double* ms, int64_t* launches) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  prof_drain_locked();
+  for (int i = 0; i < IG_PROF_STAGES; ++i) {
+    if (ms) ms[i] = g_prof.ms[i];
+    if (launches) launches[i] = g_prof.launches[i];
+  }
+  return IG_OK;
+}
+
+int64_t ig_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char* ig_prof_stage_name(int32_t stage) {
+  if (stage < 0 || stage >= IG_PROF_STAGES) return "";
+  return kStageNames[stage];
+}
+
+}  // extern "C"

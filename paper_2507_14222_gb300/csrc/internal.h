@@ -1,0 +1,109 @@
+// Host-side launchers of the IG kernels, called by the C ABI layer
+// (ig_capi.cu).  Internal row arrays use a padded stride of KT words,
+// KT = the smallest of {1, 2, 4, 8, 16} >= K; the padding words are zero.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace igk {
+
+// Rows of every internally staged row array are allocated in multiples of
+// this many rows, so that whole TMA tiles can always be copied in bounds.
+constexpr int64_t kRowPad = 256;
+
+inline int padded_words(int K) {
+  int kt = 1;
+  while (kt < K) kt *= 2;
+  return kt;
+}
+
+inline int64_t pad_rows(int64_t n) { return ((n + kRowPad - 1) / kRowPad) * kRowPad; }
+
+int num_sms();
+
+// Adds n to the library's count of kernel launches (ig_launch_count).
+void count_launches(int n);
+
+// ---- encode.cu --------------------------------------------------------------
+// Eq. 5 one-hot packing; offsets[f] = sum of cards before f (device array).
+cudaError_t launch_encode(const uint16_t* codes, int64_t n, int F,
+                          const uint32_t* offsets, const uint16_t* cards,
+                          uint64_t* out, int K, int* status, cudaStream_t s);
+
+// Stable split of rows (stride K) by label into class arrays (stride KT):
+// normal rows to x0, attack rows to x1.  counts[0..1] receive the sizes.
+cudaError_t launch_split(const uint64_t* rows, const uint8_t* labels, int64_t n,
+                         int K, int KT, uint64_t* x0, uint64_t* x1,
+                         unsigned long long* counts, int* status, cudaStream_t s);
+
+// ---- dedup.cu -----------------------------------------------------------------
+struct HashTable {
+  uint32_t* tags = nullptr;   // 0 empty, 1 being written, else 0x8.. | fingerprint
+  uint64_t* keys = nullptr;   // cap * KT words
+  uint64_t cap = 0;           // power of two
+  unsigned long long* count = nullptr;  // device counter of stored keys
+};
+
+constexpr int kPairTile = 64;  // records per side of a pair tile
+
+// Inserts x_i AND x_j for every i <= j (i == j gives the record itself) with
+// i in tile rows [row_lo, row_hi) of the upper triangle, skipping empty
+// intersections.
+cudaError_t launch_pair_insert(const uint64_t* X, int64_t n, int KT,
+                               int64_t row_lo, int64_t row_hi, HashTable t,
+                               int* status, cudaStream_t s);
+cudaError_t launch_rehash(HashTable from, HashTable to, int KT, int* status,
+                          cudaStream_t s);
+// Appends every stored key to out (stride KT); out_count must start at 0.
+cudaError_t launch_compact(HashTable t, int KT, uint64_t* out,
+                           unsigned long long* out_count, cudaStream_t s);
+
+// ---- subset.cu --------------------------------------------------------------
+enum SubsetMode { MODE_ANY = 0, MODE_COUNT = 1, MODE_SUM = 2 };
+
+// MODE_ANY:   flag[i] = 1 if own row i is contained in some stream row.
+// MODE_COUNT: cnt[i] += number of stream rows containing own row i.
+// MODE_SUM:   sum[i] += sum of score[j] over stream rows j contained in own
+//             row i.
+// own: n_own rows of stride own_stride (any K <= KT, extra words read as 0).
+// stream: n_stream rows of stride KT, allocated to pad_rows(n_stream) rows.
+struct SubsetArgs {
+  int mode;
+  int KT;
+  const uint64_t* own;
+  int64_t n_own;
+  int own_stride;
+  const uint64_t* stream;
+  const uint64_t* stream_score;  // MODE_SUM only, padded like stream
+  int64_t n_stream;
+  uint32_t* out_u32;             // ANY / COUNT
+  unsigned long long* out_u64;   // SUM
+  int* status;
+};
+cudaError_t launch_subset(const SubsetArgs& a, cudaStream_t s);
+
+// Keeps the rows whose flag is zero: out gets them (stride KT), out_count
+// the number kept (must start at 0).
+cudaError_t launch_select_unflagged(const uint64_t* rows, int64_t n, int KT,
+                                    const uint32_t* flag, uint64_t* out,
+                                    unsigned long long* out_count,
+                                    cudaStream_t s);
+
+// S = f * popcount(row)^2 (Eq. 2).
+cudaError_t launch_pattern_score(const uint64_t* rows, int64_t n, int KT,
+                                 const uint32_t* f, uint64_t* S, cudaStream_t s);
+
+// Regulations 1-3 -> label (1 attack).
+cudaError_t launch_labels(const unsigned long long* A, const unsigned long long* N,
+                          int64_t m, int reg3, double threshold, uint8_t* out,
+                          cudaStream_t s);
+
+// ---- sort.cu ----------------------------------------------------------------
+// Canonical order of n keys (stride KT): ascending as KT-word unsigned
+// integers, word KT-1 most significant.  keys_out receives the sorted rows.
+// Synchronizes the stream once (to learn which digits vary).
+cudaError_t canonical_sort(const uint64_t* keys, int64_t n, int KT,
+                           uint64_t* keys_out, int* status, cudaStream_t s);
+
+}  // namespace igk

@@ -1,0 +1,321 @@
+"""CUDA library vs CPU oracle, element by element (all integer: bit-exact).
+
+Covers the C ABI end to end -- ig_encode, ig_fit, ig_score, persistence --
+on the seeded workloads (500-record, 15k and 148k NSL-KDD-shaped), random
+dense itemsets of every word count K in 1..16 with ragged sizes around the
+64-record pair tile, brute-force tiny cases, and the degenerate cases of the
+method (identical classes, disjoint classes, a single record per class,
+duplicate records, empty intersections, an empty class).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import igdata
+import oracle
+from tests import brute
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2507_14222_gb300 as ig  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ig.build()
+    ig.load()
+
+
+def dev(a):
+    """numpy -> CUDA tensor holding the same bytes."""
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint64:
+        a = a.view(np.int64)
+    elif a.dtype == np.uint16:
+        a = a.view(np.int16)
+    elif a.dtype == np.uint32:
+        a = a.view(np.int32)
+    return torch.from_numpy(a).cuda()
+
+
+def host(t, dtype):
+    return t.cpu().numpy().view(dtype)
+
+
+def gpu_fit(rows, labels, r=None):
+    return ig.ig_fit(dev(rows), dev(np.asarray(labels, np.uint8)), r=r)
+
+
+def assert_model_equal(m, om):
+    info = m.info()
+    for cls in (0, 1):
+        words, f, s = m.patterns(cls)
+        want = om.patterns[cls]
+        assert words.shape == want.shape, (cls, words.shape, want.shape)
+        assert np.array_equal(words, want), f"class {cls}: pattern sets differ"
+        assert np.array_equal(f, om.support[cls]), f"class {cls}: supports differ"
+        assert np.array_equal(s, om.score[cls]), f"class {cls}: scores differ"
+        assert info["n_candidates"][cls] == om.n_candidates[cls]
+
+
+def assert_scores_equal(m, om, rows):
+    A, N, lab = ig.ig_score(m, dev(rows))
+    oA, oN, olab = oracle.score(om, rows)
+    assert np.array_equal(host(A, np.int64), oA)
+    assert np.array_equal(host(N, np.int64), oN)
+    assert np.array_equal(host(lab, np.uint8), olab)
+
+
+# ---- encoding ---------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["tiny", "nsl15k"])
+def test_encode_parity(name):
+    w = igdata.WORKLOADS[name]()
+    for codes in (w.train_codes, w.test_codes):
+        got = ig.ig_encode(dev(codes), w.cards)
+        assert np.array_equal(host(got, np.uint64), oracle.encode(codes, w.cards))
+
+
+def test_encode_ragged_and_wide():
+    rng = np.random.default_rng(3)
+    cards = rng.integers(1, 40, size=37).astype(np.uint16)   # L not a multiple of 64
+    codes = np.stack([rng.integers(0, c, size=129) for c in cards], 1).astype(np.uint16)
+    got = ig.ig_encode(dev(codes), cards)
+    assert np.array_equal(host(got, np.uint64), oracle.encode(codes, cards))
+    empty = ig.ig_encode(dev(codes[:0]), cards)
+    assert tuple(empty.shape) == (0, (int(cards.astype(int).sum()) + 63) // 64)
+
+
+def test_encode_rejects_out_of_range_code():
+    codes = np.array([[0, 1], [2, 5]], np.uint16)
+    with pytest.raises(ig.IGError) as e:
+        ig.ig_encode(dev(codes), [3, 5])
+    assert e.value.code == -1
+
+
+# ---- fit and score on brute-force and random cases --------------------------
+
+@pytest.mark.parametrize("seed", range(10))
+def test_fit_against_brute_force(seed):
+    rng = np.random.default_rng(100 + seed)
+    L = 12
+    K, positions = (1, list(range(L))) if seed % 2 else (2, list(range(58, 58 + L)))
+    pool = [int(v) for v in rng.integers(1, 1 << L, size=7)]
+    XA = [pool[i] for i in rng.integers(0, 7, size=3 + seed)]
+    XN = [pool[i] for i in rng.integers(0, 7, size=2 + (seed * 3) % 7)]
+    want = brute.fit(XA, XN, L)
+    rows = np.concatenate([brute.pack(XA, positions, K), brute.pack(XN, positions, K)])
+    labels = np.array([1] * len(XA) + [0] * len(XN), np.uint8)
+    m = gpu_fit(rows, labels)
+    for cls in (0, 1):
+        words, f, s = m.patterns(cls)
+        B, P, ff, S = want[cls]
+        assert np.array_equal(words, brute.pack(P, positions, K).reshape(-1, K))
+        assert f.tolist() == ff and s.tolist() == S
+        assert m.info()["n_candidates"][cls] == len(B)
+    tests = list(range(0, 1 << L, 5))
+    A, N, lab = ig.ig_score(m, dev(brute.pack(tests, positions, K)))
+    for i, t in enumerate(tests):
+        a = brute.evidence(want[1][1], want[1][3], t)
+        n = brute.evidence(want[0][1], want[0][3], t)
+        assert (int(A[i]), int(N[i]), int(lab[i])) == (a, n, brute.label(a, n))
+
+
+RANDOM_CASES = [
+    # (n_items, n_attack, n_normal, density, duplicate pool or 0)
+    (40, 1, 1, "half", 0),
+    (64, 2, 3, "half", 0),
+    (70, 63, 65, "three_quarters", 0),
+    (128, 64, 64, "half", 0),
+    (150, 65, 129, "three_quarters", 12),
+    (250, 130, 70, "three_quarters", 0),
+    (300, 200, 190, "half", 40),
+    (520, 129, 63, "three_quarters", 0),
+    (600, 100, 90, "three_quarters", 0),
+    (1024, 150, 140, "three_quarters", 20),
+    (1000, 70, 80, "three_quarters", 0),
+]
+
+
+@pytest.mark.parametrize("case", RANDOM_CASES, ids=lambda c: f"L{c[0]}-{c[1]}x{c[2]}")
+def test_fit_and_score_random(case):
+    L, na, nn, density, pool = case
+    rng = np.random.default_rng(L * 7 + na)
+    if pool:
+        base = igdata.random_words(rng, pool, L, density)
+        rows = base[rng.integers(0, pool, size=na + nn)]
+    else:
+        rows = igdata.random_words(rng, na + nn, L, density)
+    labels = np.zeros(na + nn, np.uint8)
+    labels[rng.permutation(na + nn)[:na]] = 1
+    m = gpu_fit(rows, labels)
+    om = oracle.fit(rows, labels)
+    assert_model_equal(m, om)
+    test = igdata.random_words(rng, 97, L, "three_quarters")
+    assert_scores_equal(m, om, np.concatenate([test, rows]))
+
+
+def test_identical_classes():
+    rng = np.random.default_rng(11)
+    X = igdata.random_words(rng, 40, 200, "half")
+    rows = np.concatenate([X, X[::-1]])
+    labels = np.array([1] * 40 + [0] * 40, np.uint8)
+    m = gpu_fit(rows, labels)
+    assert m.info()["n_patterns"] == (0, 0)
+    A, N, lab = ig.ig_score(m, dev(rows))
+    assert int(A.abs().sum()) == 0 and int(N.abs().sum()) == 0
+    assert bool((lab == 1).all())                      # Regulation 2
+
+
+def test_disjoint_classes_all_candidates_coherent():
+    rng = np.random.default_rng(12)
+    XA = igdata.random_words(rng, 70, 64, "half")                 # items 0..63
+    XN = np.zeros((75, 2), np.uint64)
+    XN[:, 1] = igdata.random_words(rng, 75, 64, "half")[:, 0]     # items 64..127
+    XA = np.concatenate([XA, np.zeros((70, 1), np.uint64)], 1)
+    rows = np.concatenate([XA, XN])
+    labels = np.array([1] * 70 + [0] * 75, np.uint8)
+    m = gpu_fit(rows, labels)
+    info = m.info()
+    assert info["n_patterns"] == info["n_candidates"]
+    assert_model_equal(m, oracle.fit(rows, labels))
+
+
+def test_single_record_classes_and_duplicates():
+    rows = np.array([[0b1011], [0b0110]], np.uint64)
+    m = gpu_fit(rows, [1, 0])
+    assert m.patterns(1)[0].tolist() == [[0b1011]]
+    assert m.patterns(0)[0].tolist() == [[0b0110]]
+    # All records identical within each class: one candidate, the record.
+    rows = np.array([[5]] * 9 + [[6]] * 4, np.uint64)
+    m = gpu_fit(rows, [1] * 9 + [0] * 4)
+    assert m.patterns(1)[1].tolist() == [9] and m.patterns(0)[1].tolist() == [4]
+    # Records whose pairwise intersections are all empty.
+    rows = np.array([[1 << i] for i in range(20)], np.uint64)
+    labels = [1] * 10 + [0] * 10
+    assert_model_equal(gpu_fit(rows, labels), oracle.fit(rows, np.array(labels, np.uint8)))
+
+
+def test_empty_class_rejected():
+    rows = np.array([[1], [2], [3]], np.uint64)
+    with pytest.raises(ig.IGError) as e:
+        gpu_fit(rows, [1, 1, 1])
+    assert e.value.code == -1
+
+
+def test_bad_label_rejected():
+    rows = np.array([[1], [2], [3]], np.uint64)
+    with pytest.raises(ig.IGError) as e:
+        gpu_fit(rows, [1, 2, 0])
+    assert e.value.code == -1
+
+
+def test_hash_table_growth():
+    # ~1.1M distinct, nearly all coherent intersections among 1,500 dense
+    # records: the dedup table has to double several times.
+    rng = np.random.default_rng(13)
+    XA = igdata.random_words(rng, 1500, 256, "three_quarters")
+    XN = igdata.random_words(rng, 30, 256, "three_quarters")
+    rows = np.concatenate([XA, XN])
+    labels = np.array([1] * 1500 + [0] * 30, np.uint8)
+    m = gpu_fit(rows, labels)
+    om = oracle.fit(rows, labels)
+    assert om.n_candidates[1] > 1_000_000
+    assert_model_equal(m, om)
+
+
+# ---- seeded workloads -------------------------------------------------------
+
+def _workload_fit(w, r=None):
+    d_codes = dev(w.train_codes)
+    rows = ig.ig_encode(d_codes, w.cards)
+    m = ig.ig_fit(rows, dev(w.train_labels), r=r)
+    return m, oracle.encode(w.train_codes, w.cards)
+
+
+def test_tiny_workload_parity():
+    w = igdata.tiny()
+    m, rows = _workload_fit(w)
+    om = oracle.fit(rows, w.train_labels)
+    assert_model_equal(m, om)
+    assert_scores_equal(m, om, oracle.encode(w.test_codes, w.cards))
+
+
+def test_tiny_workload_regulation3():
+    w = igdata.tiny()
+    m, rows = _workload_fit(w, r=0.568)
+    om = oracle.fit(rows, w.train_labels, r=0.568)
+    mu, sigma, r, thr = m.info()["reg3"]
+    assert (mu, sigma, r, thr) == om.reg3          # same fp64 formula and order
+    assert_scores_equal(m, om, oracle.encode(w.test_codes, w.cards))
+
+
+@pytest.fixture(scope="module")
+def nsl15k():
+    w = igdata.nsl15k()
+    m, rows = _workload_fit(w)
+    om = oracle.fit(rows, w.train_labels)
+    return w, m, om
+
+
+def test_nsl15k_fit_parity(nsl15k):
+    w, m, om = nsl15k
+    assert_model_equal(m, om)
+    assert sum(m.info()["n_patterns"]) > 100_000
+
+
+def test_nsl15k_score_parity(nsl15k):
+    w, m, om = nsl15k
+    assert_scores_equal(m, om, oracle.encode(w.test_codes, w.cards))
+
+
+def test_nsl15k_deterministic_and_permutation_invariant(nsl15k):
+    w, m, om = nsl15k
+    perm = np.random.default_rng(5).permutation(w.train_codes.shape[0])
+    rows = ig.ig_encode(dev(w.train_codes[perm]), w.cards)
+    m2 = ig.ig_fit(rows, dev(w.train_labels[perm]))
+    for cls in (0, 1):
+        a, b = m.patterns(cls), m2.patterns(cls)
+        assert all(np.array_equal(x, y) for x, y in zip(a, b))
+
+
+def test_host_buffer_path(nsl15k):
+    w, m, om = nsl15k
+    rows = ig.ig_encode(w.train_codes, w.cards)          # numpy in -> numpy out
+    assert isinstance(rows, np.ndarray)
+    mh = ig.ig_fit(rows, w.train_labels)
+    assert_model_equal(mh, om)
+    test = ig.ig_encode(w.test_codes[:3000], w.cards)
+    A, N, lab = ig.ig_score(mh, test)
+    oA, oN, olab = oracle.score(om, test)
+    assert np.array_equal(A, oA) and np.array_equal(N, oN) and np.array_equal(lab, olab)
+
+
+def test_save_load_roundtrip(nsl15k, tmp_path):
+    w, m, om = nsl15k
+    path = str(tmp_path / "model.ig")
+    m.save(path)
+    m2 = ig.ig_model_load(path)
+    assert_model_equal(m2, om)
+    test = oracle.encode(w.test_codes[:500], w.cards)
+    assert_scores_equal(m2, om, test)
+
+
+def test_nsl148k_parity_sampled_scores():
+    # Full-size fit compared in full; scores on a seeded sample of the
+    # 133,200 test records (the oracle's evidence loop is the slow part).
+    w = igdata.nsl148k()
+    m, rows = _workload_fit(w)
+    om = oracle.fit(rows, w.train_labels)
+    assert_model_equal(m, om)
+    test_rows = ig.ig_encode(dev(w.test_codes), w.cards)
+    A, N, lab = ig.ig_score(m, test_rows)
+    idx = np.random.default_rng(7).choice(w.test_codes.shape[0], 1500, replace=False)
+    oA, oN, olab = oracle.score(om, oracle.encode(w.test_codes[idx], w.cards))
+    assert np.array_equal(host(A, np.int64)[idx], oA)
+    assert np.array_equal(host(N, np.int64)[idx], oN)
+    assert np.array_equal(host(lab, np.uint8)[idx], olab)
