@@ -138,6 +138,25 @@ int ig_score(const ig_model* model, const uint64_t* rows, int64_t m,
              int64_t* A_out, int64_t* N_out, uint8_t* label_out,
              ig_stream_t stream);
 
+/* Scoring that allocates no device memory (the paper has no counterpart:
+ * this is a library convenience).  It is for callers that cannot have the
+ * library allocate on their behalf -- a latency-bound flow-scoring loop where
+ * a cudaMalloc/cudaFree could stall the device or fail under memory pressure,
+ * or a process whose device memory is reserved up front by another
+ * allocator.  Results equal ig_score's.
+ * rows, and each non-NULL output, must be device memory; at most
+ * IG_SCORE_NOALLOC_MAX_ROWS rows per call (IG_E_INVAL beyond that, and for
+ * host pointers).  The A/N accumulators and the status word live in one
+ * fixed device array inside the library (about 4 MiB, held on every GPU that
+ * loads the library until the process exits); it is cleared by each call, and
+ * calls whose work overlaps on the GPU race on it.  The first call on each
+ * device looks up that array's device address; make that first call before
+ * any stream capture.  Synchronizes `stream` before returning. */
+#define IG_SCORE_NOALLOC_MAX_ROWS 262144
+int ig_score_noalloc(const ig_model* model, const uint64_t* rows, int64_t m,
+                     int64_t* A_out, int64_t* N_out, uint8_t* label_out,
+                     ig_stream_t stream);
+
 /* Model persistence: a flat little-endian file (magic, version, K, counts,
  * Regulation 3 statistics, then per class the canonical words, supports and
  * scores).  ig_model_load places the model on the current device. */

@@ -73,7 +73,9 @@ SIGNATURES = {
     "ig_prof_read": (ctypes.c_int, [_P, _P]),
     "ig_prof_stage_name": (ctypes.c_char_p, [_I32]),
     "ig_launch_count": (ctypes.c_int64, []),
+    "ig_score_noalloc": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P]),
 }
+SCORE_NOALLOC_MAX_ROWS = 262144
 
 _lib = None
 
@@ -260,6 +262,27 @@ def ig_score(model: Model, rows, stream=None):
         stream = None
     _check(lib.ig_score(model.handle, _ptr(rows), m, _ptr(A), _ptr(N), _ptr(lab),
                         stream))
+    return A, N, lab
+
+
+def ig_score_noalloc(model: Model, rows, stream=None):
+    """ig_score without any device allocation inside the library.
+
+    For callers that cannot let the library allocate device memory (a
+    latency-bound scoring loop, or a process whose device memory is already
+    reserved by another allocator).  rows must be a CUDA tensor with at most
+    SCORE_NOALLOC_MAX_ROWS rows; the outputs are allocated here by PyTorch,
+    the caller's allocator.  Returns (A, N, labels) like ig_score.
+    """
+    import torch
+    if not _is_torch(rows) or not rows.is_cuda:
+        raise ValueError("ig_score_noalloc takes CUDA tensors only")
+    m, _ = _rows_shape(rows)
+    A = torch.empty(m, dtype=torch.int64, device=rows.device)
+    N = torch.empty(m, dtype=torch.int64, device=rows.device)
+    lab = torch.empty(m, dtype=torch.uint8, device=rows.device)
+    _check(load().ig_score_noalloc(model.handle, _ptr(rows), m, _ptr(A), _ptr(N),
+                                   _ptr(lab), _stream(stream)))
     return A, N, lab
 
 

@@ -271,6 +271,20 @@ static void model_release(ig_model* m) {
   delete m;
 }
 
+void igk::model_view(const ig_model* m, igk::ModelView* v) {
+  v->K = m->K;
+  v->KT = m->KT;
+  for (int c = 0; c < 2; ++c) {
+    v->words_kt[c] = m->words_kt[c];
+    v->score[c] = m->score[c];
+    v->n_pat[c] = m->n_pat[c];
+  }
+  v->reg3 = m->reg3;
+  v->thr = m->thr;
+}
+
+int igk::report_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
 namespace {
 
 // Candidate generation (Eq. 1) for one class: every row-tile band of the

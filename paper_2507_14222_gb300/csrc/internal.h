@@ -25,6 +25,24 @@ int num_sms();
 // Adds n to the library's count of kernel launches (ig_launch_count).
 void count_launches(int n);
 
+// Read-only view of a fitted model's device arrays (for entry points defined
+// outside ig_capi.cu).
+struct ModelView {
+  int K, KT;
+  const uint64_t* words_kt[2];  // stride KT, pad_rows rows
+  const uint64_t* score[2];     // pad_rows entries
+  int64_t n_pat[2];
+  int reg3;
+  double thr;
+};
+}  // namespace igk
+struct ig_model;
+namespace igk {
+void model_view(const ig_model* m, ModelView* v);
+
+// Records msg as the calling thread's last error and returns code.
+int report_error(int code, const char* msg);
+
 // ---- encode.cu --------------------------------------------------------------
 // Eq. 5 one-hot packing; offsets[f] = sum of cards before f (device array).
 cudaError_t launch_encode(const uint16_t* codes, int64_t n, int F,
