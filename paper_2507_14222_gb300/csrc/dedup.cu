@@ -3,70 +3,80 @@
 //
 // Every pair i <= j of one class's records is ANDed (i == j yields the record
 // itself, the "union X^c" term of Eq. 1) and the non-empty results are
-// inserted into an open-addressing hash table keyed on all KT words, so
-// B^c is formed as a set on the device without materialising the O(n^2)
-// intersections.
+// inserted into an open-addressing hash set, so B^c is formed as a set on
+// the device without materialising the O(n^2) intersections.
 //
-// Table layout: tags[cap] (uint32: 0 empty, 1 claimed and being written,
-// otherwise 0x80000000 | 31 fingerprint bits) and keys[cap][KT].  A slot is
-// claimed by CAS on its tag, its key written, then the tag is published with
-// a release store; readers load tags with acquire semantics, so a published
-// fingerprint guarantees the key words are visible.  Linear probing; the
-// host keeps the load factor below 0.7 so every probe sequence ends at an
-// empty slot, and waits on a claimed slot are bounded.
+// A slot is one 64-bit word: 0 = empty, otherwise
+//   bit 63 = 1 | 19 fingerprint bits (62..44) | i (43..22) | j (21..0),
+// naming the pair whose intersection is the stored key.  The key itself is
+// never stored: it is recomputed as X[i] AND X[j] from the class's records,
+// which are read-only while the table is built.  A key is therefore claimed
+// and published by a single 64-bit CAS -- there is no half-written state,
+// no acquire/release protocol and no waiting on another thread's slot.
+//
+// Overflow cannot happen: before claiming an empty slot a thread takes a
+// reservation (atomicAdd on `reserved`) and gives up if the table already
+// holds `limit` keys (half its capacity), recording its tile band.  The host
+// then doubles the table, rehashes it, and replays the bands from the first
+// failed one (inserts are idempotent).
 #include "common.cuh"
 #include "internal.h"
 
 namespace igk {
 
-constexpr uint32_t kTagBusy = 1u;
-constexpr uint32_t kTagReady = 0x80000000u;
+constexpr int kIdxBits = 22;
+constexpr uint64_t kIdxMask = (1ull << kIdxBits) - 1;
+constexpr uint64_t kFpMask = 0xfffff00000000000ull;  // bit 63 + 19 fingerprint bits
 
-struct TableView {
-  uint32_t* tags;
-  uint64_t* keys;
-  uint64_t mask;
-  unsigned long long* count;
-};
+__device__ __forceinline__ uint64_t slot_value(uint64_t h, uint32_t i, uint32_t j) {
+  return (1ull << 63) | ((h >> 45) << 44) | (uint64_t(i) << kIdxBits) | uint64_t(j);
+}
 
-// Returns 1 if inserted, 0 if already present, -1 on a bounded-wait timeout
-// or a full table (status set).
 template <int KT>
-__device__ int table_insert(const TableView& t, const uint64_t (&b)[KT],
-                            uint64_t h, int* status) {
-  const uint32_t fp = kTagReady | uint32_t(h >> 33);
-  uint64_t slot = h & t.mask;
-  for (uint64_t probe = 0; probe <= t.mask; ++probe) {
-    uint32_t tag = ld_acquire_u32(t.tags + slot);
-    if (tag == 0u) {
-      uint32_t old = atomicCAS(t.tags + slot, 0u, kTagBusy);
-      if (old == 0u) {
-        uint64_t* dst = t.keys + slot * KT;
+__device__ __forceinline__ void pair_key(const uint64_t* __restrict__ X, uint64_t v,
+                                         uint64_t (&k)[KT]) {
+  const uint64_t* a = X + ((v >> kIdxBits) & kIdxMask) * KT;
+  const uint64_t* b = X + (v & kIdxMask) * KT;
 #pragma unroll
-        for (int k = 0; k < KT; ++k) dst[k] = b[k];
-        st_release_u32(t.tags + slot, fp);
+  for (int w = 0; w < KT; ++w) k[w] = __ldg(a + w) & __ldg(b + w);
+}
+
+// Returns 1 if inserted, 0 if already present, -1 if no reservation was
+// granted (the band is recorded for replay).
+template <int KT>
+__device__ int table_insert(const PairTable& t, const uint64_t* __restrict__ X,
+                            const uint64_t (&b)[KT], uint64_t h, uint32_t i, uint32_t j,
+                            int band, int* status) {
+  const uint64_t val = slot_value(h, i, j);
+  uint64_t slot = h & t.mask;
+  bool reserved = false;
+  for (uint64_t probe = 0; probe <= t.mask; ++probe) {
+    unsigned long long cur = ld_relaxed_u64(t.slots + slot);
+    if (cur == 0ull) {
+      if (!reserved) {
+        if (atomicAdd(t.reserved, 1ull) >= t.limit) {
+          atomicMin(t.failed_band, band);
+          return -1;
+        }
+        reserved = true;
+      }
+      cur = atomicCAS(reinterpret_cast<unsigned long long*>(t.slots + slot), 0ull,
+                      (unsigned long long)val);
+      if (cur == 0ull) {
         atomicAdd(t.count, 1ull);
         return 1;
       }
-      tag = old;
     }
-    if (tag == kTagBusy) {
-      uint32_t spins = 0;
-      do {
-        __nanosleep(32);
-        tag = ld_acquire_u32(t.tags + slot);
-      } while (tag == kTagBusy && ++spins < kSlotSpinLimit);
-      if (tag == kTagBusy) {
-        set_status(status, ST_TIMEOUT);
-        return -1;
-      }
-    }
-    if (tag == fp) {
-      const uint64_t* src = t.keys + slot * KT;
+    if ((cur & kFpMask) == (val & kFpMask)) {
+      uint64_t k2[KT];
+      pair_key<KT>(X, cur, k2);
       bool same = true;
 #pragma unroll
-      for (int k = 0; k < KT; ++k) same &= (ld_relaxed_u64(src + k) == b[k]);
-      if (same) return 0;
+      for (int w = 0; w < KT; ++w) same &= (k2[w] == b[w]);
+      if (same) {
+        if (reserved) atomicAdd(t.reserved, ~0ull);  // give the reservation back
+        return 0;
+      }
     }
     slot = (slot + 1) & t.mask;
   }
@@ -76,18 +86,18 @@ __device__ int table_insert(const TableView& t, const uint64_t (&b)[KT],
 
 constexpr int kPairThreads = 256;
 
-// Grid: x = column tile bj, y = row tile bi - row_lo.  Tiles with bj < bi
+// Grid: x = column tile bj, y = row tile bi - band_lo.  Tiles with bj < bi
 // lie below the diagonal and exit at once.  Shared rows use an odd stride of
 // KT + 1 words so that lanes reading consecutive rows hit distinct banks.
 template <int KT>
 __global__ void __launch_bounds__(kPairThreads)
-    pair_insert_kernel(const uint64_t* __restrict__ X, int64_t n, int64_t row_lo,
-                       TableView t, int* status) {
+    pair_insert_kernel(const uint64_t* __restrict__ X, int64_t n, int64_t band_lo,
+                       PairTable t, int* status) {
   constexpr int T = kPairTile;
   constexpr int SKT = KT + 1;
   __shared__ uint64_t A[T * SKT];
   __shared__ uint64_t B[T * SKT];
-  const int64_t bi = row_lo + blockIdx.y, bj = blockIdx.x;
+  const int64_t bi = band_lo + blockIdx.y, bj = blockIdx.x;
   if (bj < bi) return;
   const int64_t i0 = bi * T, j0 = bj * T;
   for (int e = threadIdx.x; e < T * KT; e += kPairThreads) {
@@ -120,75 +130,74 @@ __global__ void __launch_bounds__(kPairThreads)
 #pragma unroll
     for (int k = 0; k < KT; ++k) same &= (__shfl_sync(active, b[k], leader) == b[k]);
     if (leader != lane && same) continue;
-    table_insert<KT>(t, b, h, status);
+    table_insert<KT>(t, X, b, h, uint32_t(i0 + i), uint32_t(j0 + j), int(bi), status);
   }
 }
 
 template <int KT>
-__global__ void rehash_kernel(TableView from, TableView to, int* status) {
+__global__ void rehash_kernel(const uint64_t* __restrict__ X, const uint64_t* __restrict__ from,
+                              uint64_t from_cap, PairTable to, int* status) {
   int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (s > int64_t(from.mask)) return;
-  uint32_t tag = from.tags[s];
-  if (!(tag & kTagReady)) return;
+  if (s >= int64_t(from_cap)) return;
+  const uint64_t v = from[s];
+  if (v == 0ull) return;
   uint64_t b[KT];
-#pragma unroll
-  for (int k = 0; k < KT; ++k) b[k] = from.keys[s * KT + k];
-  table_insert<KT>(to, b, hash_key<KT>(b), status);
+  pair_key<KT>(X, v, b);
+  table_insert<KT>(to, X, b, hash_key<KT>(b), uint32_t((v >> kIdxBits) & kIdxMask),
+                   uint32_t(v & kIdxMask), 0, status);
 }
 
-// Warp-aggregated append of every published key.
+// Warp-aggregated append of every stored key, recomputed from its pair.
 template <int KT>
-__global__ void compact_kernel(TableView t, uint64_t* __restrict__ out,
+__global__ void compact_kernel(const uint64_t* __restrict__ X, const uint64_t* __restrict__ slots,
+                               uint64_t cap, uint64_t* __restrict__ out,
                                unsigned long long* out_count) {
   const int lane = threadIdx.x & 31;
-  const int64_t cap = int64_t(t.mask) + 1;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31);
-       base < cap; base += stride) {
+       base < int64_t(cap); base += stride) {
     int64_t s = base + lane;
-    bool ready = s < cap && (t.tags[s] & kTagReady);
-    unsigned m = __ballot_sync(0xffffffffu, ready);
+    const uint64_t v = s < int64_t(cap) ? slots[s] : 0ull;
+    unsigned m = __ballot_sync(0xffffffffu, v != 0ull);
     if (m == 0) continue;
     unsigned long long pos0 = 0;
     if (lane == 0) pos0 = atomicAdd(out_count, (unsigned long long)__popc(m));
     pos0 = __shfl_sync(0xffffffffu, pos0, 0);
-    if (ready) {
+    if (v != 0ull) {
       uint64_t pos = pos0 + __popc(m & ((1u << lane) - 1u));
+      uint64_t b[KT];
+      pair_key<KT>(X, v, b);
 #pragma unroll
-      for (int k = 0; k < KT; ++k) out[pos * KT + k] = t.keys[s * KT + k];
+      for (int k = 0; k < KT; ++k) out[pos * KT + k] = b[k];
     }
   }
 }
 
-static TableView view(const HashTable& t) {
-  return TableView{t.tags, t.keys, t.cap - 1, t.count};
-}
-
-cudaError_t launch_pair_insert(const uint64_t* X, int64_t n, int KT,
-                               int64_t row_lo, int64_t row_hi, HashTable t,
-                               int* status, cudaStream_t s) {
+cudaError_t launch_pair_insert(const uint64_t* X, int64_t n, int KT, int64_t band_lo,
+                               PairTable t, int* status, cudaStream_t s) {
   int64_t nt = ceil_div(n, kPairTile);
-  if (row_hi <= row_lo || nt == 0) return cudaSuccess;
-  dim3 grid(unsigned(nt), unsigned(row_hi - row_lo));
-  IG_DISPATCH_KT(KT, (pair_insert_kernel<KTC><<<grid, kPairThreads, 0, s>>>(
-                         X, n, row_lo, view(t), status)));
+  if (band_lo >= nt) return cudaSuccess;
+  dim3 grid{unsigned(nt), unsigned(nt - band_lo), 1u};
+  IG_DISPATCH_KT(KT, (pair_insert_kernel<KTC><<<grid, kPairThreads, 0, s>>>(X, n, band_lo, t,
+                                                                             status)));
   count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_rehash(HashTable from, HashTable to, int KT, int* status,
-                          cudaStream_t s) {
-  unsigned blocks = unsigned(ceil_div(int64_t(from.cap), 256));
-  IG_DISPATCH_KT(KT, (rehash_kernel<KTC><<<blocks, 256, 0, s>>>(view(from), view(to), status)));
+cudaError_t launch_rehash(const uint64_t* X, const uint64_t* from, uint64_t from_cap,
+                          PairTable to, int KT, int* status, cudaStream_t s) {
+  unsigned blocks = unsigned(ceil_div(int64_t(from_cap), 256));
+  IG_DISPATCH_KT(KT, (rehash_kernel<KTC><<<blocks, 256, 0, s>>>(X, from, from_cap, to, status)));
   count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_compact(HashTable t, int KT, uint64_t* out,
-                           unsigned long long* out_count, cudaStream_t s) {
-  int64_t blocks = ceil_div(int64_t(t.cap), 256);
-  if (blocks > 4 * 1024) blocks = 4 * 1024;
-  IG_DISPATCH_KT(KT, (compact_kernel<KTC><<<unsigned(blocks), 256, 0, s>>>(view(t), out, out_count)));
+cudaError_t launch_compact(const uint64_t* X, const uint64_t* slots, uint64_t cap, int KT,
+                           uint64_t* out, unsigned long long* out_count, cudaStream_t s) {
+  int64_t blocks = ceil_div(int64_t(cap), 256);
+  if (blocks > 8 * 1024) blocks = 8 * 1024;
+  IG_DISPATCH_KT(KT, (compact_kernel<KTC><<<unsigned(blocks), 256, 0, s>>>(X, slots, cap, out,
+                                                                            out_count)));
   count_launches(1);
   return cudaGetLastError();
 }

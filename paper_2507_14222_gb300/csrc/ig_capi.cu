@@ -287,81 +287,82 @@ int igk::report_error(int code, const char* msg) { return fail(code, "%s", msg);
 
 namespace {
 
-// Candidate generation (Eq. 1) for one class: every row-tile band of the
-// pair triangle is inserted into the hash table after making sure that the
-// table could absorb every pair of the band as a new key at load <= 0.7;
-// the table doubles (with a rehash) when it could not.
-int build_candidates(const uint64_t* X, int64_t n, int KT, cudaStream_t s,
-                     int* d_status, unsigned long long* h_count,
-                     DevBuf<uint64_t>& cand, int64_t* U_out) {
-  using igk::HashTable;
-  const int64_t T = igk::kPairTile;
-  const int64_t nt = igk::ceil_div(n, T);
-  auto band_pairs = [&](int64_t r) { return (nt - r) * T * T; };
-  const double kLoad = 0.7;
+// Candidate generation (Eq. 1) for one class, deduplicated on the device.
+// One launch covers every pair band; if the table runs out of room the
+// launch records the lowest band that failed, and the table is doubled,
+// rehashed and the bands from that one on are replayed (inserts are
+// idempotent).  The table starts at twice a guess of |B^c| (an eighth of the
+// pairs, at least 16 keys per record), so typical workloads need one launch.
+struct TableCounters {
+  unsigned long long count;
+  unsigned long long reserved;
+  int failed_band;
+  int pad;
+};
 
-  DevBuf<uint32_t> tags;
-  DevBuf<uint64_t> keys;
-  DevBuf<unsigned long long> count;
-  IG_CUDA(count.alloc(1, s), "ig_fit: table counter");
-  IG_CUDA(cudaMemsetAsync(count.p, 0, sizeof(unsigned long long), s), "ig_fit");
+int build_candidates(const uint64_t* X, int64_t n, int KT, cudaStream_t s, int* d_status,
+                     TableCounters* h_counters, DevBuf<uint64_t>& cand, int64_t* U_out) {
+  if (n > int64_t(65535) * igk::kPairTile)
+    return fail(IG_E_OVERFLOW, "ig_fit: more than 4,194,240 records in one class");
+  const int64_t pairs = n * (n + 1) / 2;
+  uint64_t cap = 1u << 12;
+  const int64_t guess = std::max<int64_t>(pairs / 8, 16 * n);
+  while (cap < uint64_t(2 * guess)) cap <<= 1;
 
-  uint64_t cap = 1u << 16;
-  const int64_t want = std::max<int64_t>(band_pairs(0) * 2, 16 * n);
-  while (double(cap) * kLoad < double(want)) cap <<= 1;
-  auto make_table = [&](uint64_t c, DevBuf<uint32_t>& tg, DevBuf<uint64_t>& ky) -> int {
-    IG_CUDA(tg.alloc(c, s), "ig_fit: hash table");
-    IG_CUDA(ky.alloc(c * KT, s), "ig_fit: hash table");
-    IG_CUDA(cudaMemsetAsync(tg.p, 0, c * sizeof(uint32_t), s), "ig_fit");
-    return IG_OK;
+  DevBuf<uint64_t> slots;
+  DevBuf<TableCounters> ctr;
+  IG_CUDA(ctr.alloc(1, s), "ig_fit: table counters");
+  IG_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(TableCounters), s), "ig_fit");
+  IG_CUDA(slots.alloc(cap, s), "ig_fit: hash table");
+  IG_CUDA(cudaMemsetAsync(slots.p, 0, cap * sizeof(uint64_t), s), "ig_fit");
+  auto table = [&](uint64_t* sl, uint64_t c, TableCounters* t) {
+    igk::PairTable pt;
+    pt.slots = sl;
+    pt.mask = c - 1;
+    pt.count = &t->count;
+    pt.reserved = &t->reserved;
+    pt.limit = c / 2;
+    pt.failed_band = &t->failed_band;
+    return pt;
   };
-  IG_CHECK(make_table(cap, tags, keys));
-
-  uint64_t stored = 0;
-  int64_t r = 0;
-  while (r < nt) {
-    // Grow until at least the next band fits as all-new keys.
-    while (double(stored) + double(band_pairs(r)) > kLoad * double(cap)) {
-      uint64_t ncap = cap << 1;
-      DevBuf<uint32_t> ntags;
-      DevBuf<uint64_t> nkeys;
-      DevBuf<unsigned long long> ncount;
-      IG_CHECK(make_table(ncap, ntags, nkeys));
-      IG_CUDA(ncount.alloc(1, s), "ig_fit: table counter");
-      IG_CUDA(cudaMemsetAsync(ncount.p, 0, sizeof(unsigned long long), s), "ig_fit");
-      {
-        ProfScope ps(S_REHASH, s);
-        IG_CUDA(igk::launch_rehash(HashTable{tags.p, keys.p, cap, count.p},
-                                   HashTable{ntags.p, nkeys.p, ncap, ncount.p}, KT,
-                                   d_status, s),
-                "ig_fit: rehash");
-      }
-      std::swap(tags.p, ntags.p);
-      std::swap(keys.p, nkeys.p);
-      std::swap(count.p, ncount.p);
-      cap = ncap;
-    }
-    int64_t r2 = r;
-    double budget = kLoad * double(cap) - double(stored);
-    while (r2 < nt && double(band_pairs(r2)) <= budget) {
-      budget -= double(band_pairs(r2));
-      ++r2;
-    }
+  const int kNoBand = 0x7f7f7f7f;  // failed_band after a 0x7f byte fill
+  int64_t band_lo = 0;
+  for (;;) {
+    // reserved = count, failed_band = none, then insert the bands.
+    IG_CUDA(cudaMemcpyAsync(&ctr.p->reserved, &ctr.p->count, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToDevice, s),
+            "ig_fit");
+    IG_CUDA(cudaMemsetAsync(&ctr.p->failed_band, 0x7f, sizeof(int), s), "ig_fit");
     {
       ProfScope ps(S_PAIR, s);
-      IG_CUDA(igk::launch_pair_insert(X, n, KT, r, r2, HashTable{tags.p, keys.p, cap, count.p},
-                                      d_status, s),
+      IG_CUDA(igk::launch_pair_insert(X, n, KT, band_lo, table(slots.p, cap, ctr.p), d_status, s),
               "ig_fit: pair intersection");
     }
-    r = r2;
-    IG_CUDA(cudaMemcpyAsync(h_count, count.p, sizeof(unsigned long long),
-                            cudaMemcpyDeviceToHost, s),
+    IG_CUDA(cudaMemcpyAsync(h_counters, ctr.p, sizeof(TableCounters), cudaMemcpyDeviceToHost, s),
             "ig_fit");
     IG_CUDA(cudaStreamSynchronize(s), "ig_fit");
-    stored = *h_count;
+    if (h_counters->failed_band == kNoBand) break;
+    // Grow: a table twice the size holds the keys stored so far at a
+    // quarter load; replay from the first band that ran out of room.
+    const uint64_t ncap = cap << 1;
+    DevBuf<uint64_t> nslots;
+    DevBuf<TableCounters> nctr;
+    IG_CUDA(nslots.alloc(ncap, s), "ig_fit: hash table");
+    IG_CUDA(nctr.alloc(1, s), "ig_fit: table counters");
+    IG_CUDA(cudaMemsetAsync(nslots.p, 0, ncap * sizeof(uint64_t), s), "ig_fit");
+    IG_CUDA(cudaMemsetAsync(nctr.p, 0, sizeof(TableCounters), s), "ig_fit");
+    {
+      ProfScope ps(S_REHASH, s);
+      IG_CUDA(igk::launch_rehash(X, slots.p, cap, table(nslots.p, ncap, nctr.p), KT, d_status, s),
+              "ig_fit: rehash");
+    }
+    std::swap(slots.p, nslots.p);
+    std::swap(ctr.p, nctr.p);
+    cap = ncap;
+    band_lo = h_counters->failed_band;
   }
   IG_CHECK(read_status(d_status, s, "ig_fit: candidate generation"));
-  const int64_t U = int64_t(stored);
+  const int64_t U = int64_t(h_counters->count);
   if (U > int64_t(0xffffffffll)) return fail(IG_E_OVERFLOW, "ig_fit: too many candidates");
   IG_CUDA(cand.alloc(size_t(igk::pad_rows(U)) * KT, s), "ig_fit: candidates");
   DevBuf<unsigned long long> out_count;
@@ -369,15 +370,8 @@ int build_candidates(const uint64_t* X, int64_t n, int KT, cudaStream_t s,
   IG_CUDA(cudaMemsetAsync(out_count.p, 0, sizeof(unsigned long long), s), "ig_fit");
   {
     ProfScope ps(S_COMPACT, s);
-    IG_CUDA(igk::launch_compact(HashTable{tags.p, keys.p, cap, count.p}, KT, cand.p,
-                                out_count.p, s),
-            "ig_fit: compact");
+    IG_CUDA(igk::launch_compact(X, slots.p, cap, KT, cand.p, out_count.p, s), "ig_fit: compact");
   }
-  IG_CUDA(cudaMemcpyAsync(h_count, out_count.p, sizeof(unsigned long long),
-                          cudaMemcpyDeviceToHost, s),
-          "ig_fit");
-  IG_CUDA(cudaStreamSynchronize(s), "ig_fit");
-  if (int64_t(*h_count) != U) return fail(IG_E_INTERNAL, "ig_fit: compaction count mismatch");
   *U_out = U;
   return IG_OK;
 }
@@ -450,13 +444,18 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
   IG_CUDA(d_status.alloc(1, s), "ig_fit");
   IG_CUDA(d_counts.alloc(2, s), "ig_fit");
   IG_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), s), "ig_fit");
-  // Pinned host words for size read-backs: [0..1] class counts, [2] scratch.
+  // Pinned host words for size read-backs: [0..1] class counts, [2] scratch,
+  // [4..7] hash-table counters.
   static thread_local unsigned long long* h_pinned = nullptr;
-  if (!h_pinned) IG_CUDA(cudaMallocHost(&h_pinned, 4 * sizeof(unsigned long long)), "ig_fit");
+  if (!h_pinned) IG_CUDA(cudaMallocHost(&h_pinned, 8 * sizeof(unsigned long long)), "ig_fit");
+  TableCounters* h_counters = reinterpret_cast<TableCounters*>(h_pinned + 4);
 
   // Section 3.2: class-stacked row matrices (normal -> X[0], attack -> X[1]).
   DevBuf<uint64_t> X[2];
-  for (int c = 0; c < 2; ++c) IG_CUDA(X[c].alloc(size_t(igk::pad_rows(n)) * KT, s), "ig_fit: rows");
+  // One spare tile of rows beyond the padding: record windows of the
+  // coherence rounds may start at any multiple of 32 rows.
+  for (int c = 0; c < 2; ++c)
+    IG_CUDA(X[c].alloc(size_t(igk::pad_rows(n) + igk::kRowPad) * KT, s), "ig_fit: rows");
   {
     ProfScope ps(S_SPLIT, s);
     IG_CUDA(igk::launch_split(in_rows.d, in_lab.d, n, K, KT, X[0].p, X[1].p, d_counts.p,
@@ -485,45 +484,61 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
     // Eq. 1: B^c, deduplicated on the device.
     DevBuf<uint64_t> cand;
     int64_t U = 0;
-    IG_CHECK(build_candidates(X[c].p, nc[c], KT, s, d_status.p, h_pinned + 2, cand, &U));
+    IG_CHECK(build_candidates(X[c].p, nc[c], KT, s, d_status.p, h_counters, cand, &U));
     m->n_cand[c] = U;
     // Eq. 3 (tested as Eq. 6): drop candidates inside any opposite record.
+    // The opposite records are tested in growing windows; after each window
+    // the candidates already found inside a record are dropped, so the long
+    // tail of records is only tested against the candidates still standing.
+    // Row counts stay on the device between rounds.
     DevBuf<uint32_t> covered;
-    IG_CUDA(covered.alloc(size_t(U), s), "ig_fit");
-    IG_CUDA(cudaMemsetAsync(covered.p, 0, sizeof(uint32_t) * U, s), "ig_fit");
-    {
-      ProfScope ps(S_COHERENCE, s);
-      igk::SubsetArgs a{igk::MODE_ANY, KT, cand.p, U, KT, X[o].p, nullptr, nc[o],
-                        covered.p, nullptr, d_status.p};
-      IG_CUDA(igk::launch_subset(a, s), "ig_fit: coherence");
-    }
     DevBuf<uint64_t> surv;
     DevBuf<unsigned long long> d_kept;
+    IG_CUDA(covered.alloc(size_t(U), s), "ig_fit");
     IG_CUDA(surv.alloc(size_t(igk::pad_rows(U)) * KT, s), "ig_fit");
-    IG_CUDA(d_kept.alloc(1, s), "ig_fit");
-    IG_CUDA(cudaMemsetAsync(d_kept.p, 0, sizeof(unsigned long long), s), "ig_fit");
-    {
-      ProfScope ps(S_SELECT, s);
-      IG_CUDA(igk::launch_select_unflagged(cand.p, U, KT, covered.p, surv.p, d_kept.p, s),
-              "ig_fit: select");
+    IG_CUDA(d_kept.alloc(2, s), "ig_fit");
+    const int64_t windows[] = {0, 32, 128, 512, 2048};
+    const int nwin = int(sizeof(windows) / sizeof(windows[0]));
+    uint64_t* cur = cand.p;
+    uint64_t* nxt = surv.p;
+    const unsigned long long* cur_n_dev = nullptr;
+    for (int wi = 0; wi < nwin && windows[wi] < nc[o]; ++wi) {
+      const int64_t lo = windows[wi];
+      const int64_t hi = (wi + 1 < nwin && windows[wi + 1] < nc[o]) ? windows[wi + 1] : nc[o];
+      unsigned long long* kept = d_kept.p + (wi & 1);
+      IG_CUDA(cudaMemsetAsync(covered.p, 0, sizeof(uint32_t) * U, s), "ig_fit");
+      IG_CUDA(cudaMemsetAsync(kept, 0, sizeof(unsigned long long), s), "ig_fit");
+      {
+        ProfScope ps(S_COHERENCE, s);
+        igk::SubsetArgs a{igk::MODE_ANY, KT,      cur,     U,          KT,       X[o].p + lo * KT,
+                          nullptr,        hi - lo, covered.p, nullptr, d_status.p, cur_n_dev};
+        IG_CUDA(igk::launch_subset(a, s), "ig_fit: coherence");
+      }
+      {
+        ProfScope ps(S_SELECT, s);
+        IG_CUDA(igk::launch_select_unflagged(cur, U, KT, covered.p, nxt, kept, s, cur_n_dev),
+                "ig_fit: select");
+      }
+      cur_n_dev = kept;
+      std::swap(cur, nxt);
     }
-    IG_CUDA(cudaMemcpyAsync(h_pinned + 2, d_kept.p, sizeof(unsigned long long),
+    IG_CUDA(cudaMemcpyAsync(h_pinned + 2, cur_n_dev, sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, s),
             "ig_fit");
     IG_CHECK(read_status(d_status.p, s, "ig_fit: coherence"));
     const int64_t P = int64_t(h_pinned[2]);
     m->n_pat[c] = P;
-    cand.reset();
     covered.reset();
-    // Canonical order of P^c.
+    // Canonical order of P^c (the other buffer serves as sort workspace).
+    uint64_t* spare = (cur == cand.p) ? surv.p : cand.p;
     IG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&m->words_kt[c]),
                             sizeof(uint64_t) * std::max<int64_t>(1, igk::pad_rows(P)) * KT, s),
             "ig_fit: patterns");
     {
       ProfScope ps(S_SORT, s);
-      IG_CUDA(igk::canonical_sort(surv.p, P, KT, m->words_kt[c], d_status.p, s),
-              "ig_fit: canonical sort");
+      IG_CUDA(igk::canonical_sort(cur, P, KT, m->words_kt[c], spare, s), "ig_fit: canonical sort");
     }
+    cand.reset();
     surv.reset();
     // Eq. 2: support f_c and score S_c = f_c * |b|^2.
     IG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&m->support[c]),

@@ -56,26 +56,31 @@ cudaError_t launch_split(const uint64_t* rows, const uint8_t* labels, int64_t n,
                          unsigned long long* counts, int* status, cudaStream_t s);
 
 // ---- dedup.cu -----------------------------------------------------------------
-struct HashTable {
-  uint32_t* tags = nullptr;   // 0 empty, 1 being written, else 0x8.. | fingerprint
-  uint64_t* keys = nullptr;   // cap * KT words
-  uint64_t cap = 0;           // power of two
-  unsigned long long* count = nullptr;  // device counter of stored keys
+// Hash set of candidate itemsets keyed by the pair (i, j) whose intersection
+// they are (see dedup.cu for the slot format).
+struct PairTable {
+  uint64_t* slots = nullptr;                // cap words, 0 = empty
+  uint64_t mask = 0;                        // cap - 1, cap a power of two
+  unsigned long long* count = nullptr;      // keys stored
+  unsigned long long* reserved = nullptr;   // keys stored + claims in flight
+  unsigned long long limit = 0;             // most keys the table may hold
+  int* failed_band = nullptr;               // lowest band that ran out of room
 };
 
-constexpr int kPairTile = 64;  // records per side of a pair tile
+constexpr int kPairTile = 64;  // records per side of a pair tile (one band = one tile row)
 
-// Inserts x_i AND x_j for every i <= j (i == j gives the record itself) with
-// i in tile rows [row_lo, row_hi) of the upper triangle, skipping empty
-// intersections.
-cudaError_t launch_pair_insert(const uint64_t* X, int64_t n, int KT,
-                               int64_t row_lo, int64_t row_hi, HashTable t,
-                               int* status, cudaStream_t s);
-cudaError_t launch_rehash(HashTable from, HashTable to, int KT, int* status,
-                          cudaStream_t s);
-// Appends every stored key to out (stride KT); out_count must start at 0.
-cudaError_t launch_compact(HashTable t, int KT, uint64_t* out,
-                           unsigned long long* out_count, cudaStream_t s);
+// Inserts x_i AND x_j for every i <= j (i == j gives the record itself),
+// skipping empty intersections, for every pair tile in bands >= band_lo of
+// the upper triangle; one launch.
+cudaError_t launch_pair_insert(const uint64_t* X, int64_t n, int KT, int64_t band_lo,
+                               PairTable t, int* status, cudaStream_t s);
+// Re-inserts every key of the table `from` (from_cap slots) into `to`.
+cudaError_t launch_rehash(const uint64_t* X, const uint64_t* from, uint64_t from_cap,
+                          PairTable to, int KT, int* status, cudaStream_t s);
+// Appends every stored key (recomputed from its pair) to out (stride KT);
+// out_count must start at 0.
+cudaError_t launch_compact(const uint64_t* X, const uint64_t* slots, uint64_t cap, int KT,
+                           uint64_t* out, unsigned long long* out_count, cudaStream_t s);
 
 // ---- subset.cu --------------------------------------------------------------
 enum SubsetMode { MODE_ANY = 0, MODE_COUNT = 1, MODE_SUM = 2 };
@@ -98,15 +103,19 @@ struct SubsetArgs {
   uint32_t* out_u32;             // ANY / COUNT
   unsigned long long* out_u64;   // SUM
   int* status;
+  // Optional: the number of own rows, read on the device (n_own is then
+  // only an upper bound used to size the grid).
+  const unsigned long long* n_own_dev = nullptr;
 };
 cudaError_t launch_subset(const SubsetArgs& a, cudaStream_t s);
 
 // Keeps the rows whose flag is zero: out gets them (stride KT), out_count
-// the number kept (must start at 0).
+// the number kept (must start at 0).  With n_dev given, the row count is
+// read on the device and n is only an upper bound.
 cudaError_t launch_select_unflagged(const uint64_t* rows, int64_t n, int KT,
                                     const uint32_t* flag, uint64_t* out,
-                                    unsigned long long* out_count,
-                                    cudaStream_t s);
+                                    unsigned long long* out_count, cudaStream_t s,
+                                    const unsigned long long* n_dev = nullptr);
 
 // S = f * popcount(row)^2 (Eq. 2).
 cudaError_t launch_pattern_score(const uint64_t* rows, int64_t n, int KT,
@@ -118,10 +127,10 @@ cudaError_t launch_labels(const unsigned long long* A, const unsigned long long*
                           cudaStream_t s);
 
 // ---- sort.cu ----------------------------------------------------------------
-// Canonical order of n keys (stride KT): ascending as KT-word unsigned
-// integers, word KT-1 most significant.  keys_out receives the sorted rows.
-// Synchronizes the stream once (to learn which digits vary).
-cudaError_t canonical_sort(const uint64_t* keys, int64_t n, int KT,
-                           uint64_t* keys_out, int* status, cudaStream_t s);
+// Canonical order of n distinct keys (stride KT): ascending as KT-word
+// unsigned integers, word KT-1 most significant.  keys_out (n rows) receives
+// the sorted rows; `work` must hold n rows as well.
+cudaError_t canonical_sort(const uint64_t* keys, int64_t n, int KT, uint64_t* keys_out,
+                           uint64_t* work, cudaStream_t s);
 
 }  // namespace igk

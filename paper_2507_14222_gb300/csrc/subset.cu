@@ -44,6 +44,7 @@ struct SubsetParams {
   uint32_t* out_u32;
   unsigned long long* out_u64;
   int* status;
+  const unsigned long long* n_own_dev;
 };
 
 template <int H>
@@ -77,14 +78,19 @@ __global__ void __launch_bounds__(kSubThreads)
   uint64_t* score_s = rows_s + kStages * TR * KT;
   uint64_t* bars = score_s + (MODE == MODE_SUM ? kStages * TR : 0);
 
+  // CTAs past the own rows (when their count is read on the device) exit
+  // before touching any barrier or copy.
+  const int64_t n_own = p.n_own_dev ? int64_t(*p.n_own_dev) : p.n_own;
+  const int64_t own_base = int64_t(blockIdx.x) * (kSubThreads * Q);
+  if (own_base >= n_own) return;
+
   // Own rows -> registers (words beyond own_stride read as zero).
   uint32_t own[Q][H];
   bool valid[Q];
-  const int64_t own_base = int64_t(blockIdx.x) * (kSubThreads * Q);
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     int64_t row = own_base + q * kSubThreads + threadIdx.x;
-    valid[q] = row < p.n_own;
+    valid[q] = row < n_own;
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
       uint64_t w = (valid[q] && k < p.own_stride) ? p.own[row * p.own_stride + k] : 0ull;
@@ -214,8 +220,8 @@ static cudaError_t launch_subset_t(const SubsetArgs& a, cudaStream_t s) {
   if (splits < 1) splits = 1;
   const int64_t per_split = ceil_div(stream_tiles, splits) * S::TR;
   splits = ceil_div(a.n_stream, per_split);
-  SubsetParams p{a.own, a.n_own, a.own_stride, a.stream, a.stream_score,
-                 a.n_stream, per_split, a.out_u32, a.out_u64, a.status};
+  SubsetParams p{a.own,     a.n_own,   a.own_stride, a.stream,  a.stream_score, a.n_stream,
+                 per_split, a.out_u32, a.out_u64,    a.status, a.n_own_dev};
   const size_t smem = size_t(kStages) * (S::TR * KT * 8 + (MODE == MODE_SUM ? S::TR * 8 : 0)) +
                       kStages * sizeof(uint64_t);
   if (gx > 0x7fffffff) return cudaErrorInvalidValue;
@@ -239,7 +245,9 @@ template <int KT>
 __global__ void select_unflagged_kernel(const uint64_t* __restrict__ rows, int64_t n,
                                         const uint32_t* __restrict__ flag,
                                         uint64_t* __restrict__ out,
-                                        unsigned long long* out_count) {
+                                        unsigned long long* out_count,
+                                        const unsigned long long* n_dev) {
+  if (n_dev) n = int64_t(*n_dev);
   const int lane = threadIdx.x & 31;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31);
@@ -261,13 +269,13 @@ __global__ void select_unflagged_kernel(const uint64_t* __restrict__ rows, int64
 
 cudaError_t launch_select_unflagged(const uint64_t* rows, int64_t n, int KT,
                                     const uint32_t* flag, uint64_t* out,
-                                    unsigned long long* out_count,
-                                    cudaStream_t s) {
+                                    unsigned long long* out_count, cudaStream_t s,
+                                    const unsigned long long* n_dev) {
   if (n == 0) return cudaSuccess;
   int64_t blocks = ceil_div(n, 256);
   if (blocks > 8 * 1024) blocks = 8 * 1024;
   IG_DISPATCH_KT(KT, (select_unflagged_kernel<KTC><<<unsigned(blocks), 256, 0, s>>>(
-                         rows, n, flag, out, out_count)));
+                         rows, n, flag, out, out_count, n_dev)));
   count_launches(1);
   return cudaGetLastError();
 }
