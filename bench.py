@@ -48,8 +48,11 @@ METRIC = "IG fit wall-s & subset tests/s (G/s) vs roofline; scored flows/s, p99 
 UNIT = "G subset-tests/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
 # Integer-pipe peak of the subset test: LOP3 instructions per SM per clock
-# (measured on GB300, see the profiles directory) x SMs x max SM clock.
+# (4 sub-partitions x 16 lanes; a LOP3 throughput probe on GB300 measured
+# 60.8 per SM per clock against the 2,070 MHz attribute clock while the SM
+# ran near 1,995 MHz) x 152 SMs x the maximum SM clock.
 LOP3_PER_SM_PER_CLK = 64
 
 
@@ -62,6 +65,9 @@ def parse():
     ap.add_argument("--workload", default="nsl15k", choices=sorted(igdata.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kernel", type=int, default=0,
+                    help="subset-test form: 0 default, 1 integer pipe, 2 tensor cores, "
+                         "3 item index")
     return ap.parse_args()
 
 
@@ -172,7 +178,7 @@ def run_ours(args):
     def step():
         rows = ig.ig_encode(d_tr, cards)
         test_rows = ig.ig_encode(d_te, cards)
-        model = ig.ig_fit(rows, d_lab)
+        model = ig.ig_fit(rows, d_lab, subset_kernel=args.kernel)
         out = ig.ig_score(model, test_rows)
         return model, out
 
@@ -205,7 +211,7 @@ def run_ours(args):
             f0 = torch.cuda.Event(enable_timing=True)
             f1 = torch.cuda.Event(enable_timing=True)
             f0.record(stream)
-            model = ig.ig_fit(rows, d_lab)
+            model = ig.ig_fit(rows, d_lab, subset_kernel=args.kernel)
             f1.record(stream)
             ig.ig_score(model, test_rows)
             ends[i].record(stream)
@@ -246,11 +252,17 @@ def run_ours(args):
         "tests_per_step": tests,
         "patterns": {"attack": info["n_patterns"][1], "normal": info["n_patterns"][0],
                      "candidates": list(info["n_candidates"][::-1])},
-        "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in stages.items()},
+        "subset_kernel": {1: "lop3", 2: "tcgen05", 3: "item-index"}[info["subset_kernel"]],
+        "coherence_tests_executed": sum(info["coherence_tests"]),
+        "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in stages.items()
+                               if v[1]},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
-    line["roofline"] = roofline(stages, info, m_test, w.n_words, line["clocks"])
+    kt = 1
+    while kt < w.n_words:
+        kt *= 2
+    line["roofline"] = roofline(stages, info, kt, line["clocks"], args.steps)
     if not args.no_e2e:
         line["e2e"] = e2e_host_buffers(ig, w, tests, max(2, min(args.steps, 5)))
     if not args.no_cpu_baseline:
@@ -260,27 +272,42 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def roofline(stages, info, m_test, K, clocks):
-    """Roofline of the dominant stage's kernel (largest share of step time)."""
-    name, (ms, launches) = max(stages.items(), key=lambda kv: kv[1][0])
-    nt, U, P = info["n_train"], info["n_candidates"], info["n_patterns"]
-    tests = {"coherence": U[1] * nt[0] + U[0] * nt[1],
-             "support": P[1] * nt[1] + P[0] * nt[0],
-             "evidence": m_test * (P[0] + P[1])}
+def roofline(stages, info, K, clocks, steps):
+    """Roofline of the dominant kernel (largest share of the timed steps).
+
+    Subset-test kernels are bound by the integer pipe (LOP3 forms: 2K LOP3 per
+    executed test, one per 32-bit half) or by the tensor cores (tcgen05 form:
+    a 0/1 FP8 GEMM, 2 x 64K flops per executed test).  Executed tests come
+    from the library: per timed stage for supports and evidence, per model
+    for the coherence windows.
+    """
+    name, (ms, launches, work) = max(stages.items(), key=lambda kv: kv[1][0])
+    coh_idx = sum(info["coherence_tests_idx"]) * steps
+    coh_tc = sum(info["coherence_tests_tc"]) * steps
+    coh_dense = sum(info["coherence_tests"]) * steps - coh_idx - coh_tc
+    tests = {"coherence": coh_dense, "coherence_tc": coh_tc, "coherence_idx": coh_idx}
+    executed = tests.get(name, work)
     out = {"kernel": name, "launches": int(launches),
-           "avg_launch_ms": ms / max(1, launches)}
-    if name in tests:
-        # Integer-pipe bound: each test is 2K LOP3 (one per 32-bit half).
-        # tests[name] counts both classes of one step, i.e. two launches.
-        steps = launches / 2.0
-        achieved = tests[name] * 2 * K * steps / (ms * 1e-3) / 1e12
-        sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
+           "avg_launch_ms": ms / max(1, launches), "tests": int(executed)}
+    sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peaks = load_peaks()
+    if name in ("coherence", "support", "evidence", "coherence_idx", "support_idx",
+                "evidence_idx"):
+        achieved = executed * 2 * K / (ms * 1e-3) / 1e12
         peak = LOP3_PER_SM_PER_CLK * 152 * sm_max * 1e6 / 1e12
         out.update({"bound": "alu", "achieved": achieved, "peak": peak,
                     "unit": "Tops/s (LOP3)", "frac": achieved / peak, "traffic": None,
-                    "peak_source": f"{LOP3_PER_SM_PER_CLK} LOP3/SM/clk x 152 SMs x {sm_max:.0f} MHz"})
+                    "peak_source": f"{LOP3_PER_SM_PER_CLK} LOP3/SM/clk (measured) x 152 SMs "
+                                   f"x {sm_max:.0f} MHz"})
+    elif name in ("coherence_tc", "support_tc", "evidence_tc"):
+        achieved = executed * 2 * 64 * K / (ms * 1e-3) / 1e12
+        bf16 = (peaks or {}).get("bf16_tflops", FALLBACK_BF16_TFLOPS)
+        peak = 2.0 * bf16
+        out.update({"bound": "tensor", "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s (FP8 0/1 GEMM)", "frac": achieved / peak, "traffic": None,
+                    "peak_source": ("measured bf16 burst x 2 (nominal FP8/BF16 ratio)"
+                                    if peaks else "fallback bf16 x 2")})
     else:
-        peaks = load_peaks()
         hbm = (peaks or {}).get("hbm_gbs", FALLBACK_HBM_GBS)
         out.update({"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s",
                     "frac": None, "traffic": None,

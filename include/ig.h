@@ -70,8 +70,14 @@ typedef struct {
    * double precision in record order. */
   double r;
   int32_t reg3_enabled;
-  /* Subset-test kernel choice: 0 = library default, 1 = integer-pipe
-   * (LOP3) kernel.  Other values are reserved. */
+  /* Subset-test form: 0 = library default (3 where K > 1, else 1);
+   * 1 = integer-pipe kernel (LOP3) on every pair; 2 = tensor-core kernel
+   * (tcgen05 0/1 GEMM) on every pair, where K (rounded up to a power of two)
+   * is 2, 4 or 8, else 1; 3 = item index: each pattern is tested only
+   * against the records holding its rarest item (exact), in integer-pipe
+   * blocks, falling back to 2 when records are too dense for the index to
+   * pay off.  The choice is kept in the model and used by ig_score too.
+   * Results are identical for every choice. */
   int32_t subset_kernel;
 } ig_params;
 
@@ -83,6 +89,12 @@ typedef struct {
   int64_t n_patterns[2];     /* |P^c|: coherent patterns (Eq. 3) */
   int64_t n_pairs[2];        /* intersections formed: n_c (n_c - 1) / 2 */
   double reg3_mu, reg3_sigma, reg3_r, reg3_threshold;
+  int64_t coherence_tests[2];  /* subset tests the coherence step executed */
+  int64_t coherence_tests_tc[2]; /* ... of which on the tensor cores */
+  int64_t coherence_tests_idx[2]; /* ... of which through the item index */
+  int64_t support_tests[2];      /* subset tests the support step executed */
+  int32_t subset_kernel;       /* form in use: 1 integer pipe, 2 tensor cores, 3 item index */
+  int32_t reserved;
 } ig_model_info_t;
 
 /* Section 3.1 / Eq. 5: one-hot encoding of discretised records.
@@ -172,11 +184,16 @@ const char* ig_last_error(void);
  * synchronizes and returns, for each stage s < IG_PROF_STAGES, the summed
  * kernel time in milliseconds and the number of launches since the last
  * reset.  Stage names are given by ig_prof_stage_name. */
-#define IG_PROF_STAGES 12
+#define IG_PROF_STAGES 20
 int ig_prof_enable(int32_t on);
 int ig_prof_reset(void);
 int ig_prof_read(double* ms, int64_t* launches);
 const char* ig_prof_stage_name(int32_t stage);
+
+/* Subset tests executed per stage since the last reset, counted while
+ * timing is enabled (support and evidence stages; coherence tests are
+ * reported per model by ig_model_info). */
+int ig_prof_read_work(int64_t* tests);
 
 /* Number of kernels this library has launched in the process so far. */
 int64_t ig_launch_count(void);

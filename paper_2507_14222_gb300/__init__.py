@@ -30,7 +30,7 @@ IG_OK = 0
 _ERRORS = {-1: "IG_E_INVAL", -2: "IG_E_NOMEM", -3: "IG_E_CUDA",
            -4: "IG_E_TIMEOUT", -5: "IG_E_OVERFLOW", -6: "IG_E_INTERNAL",
            -7: "IG_E_IO"}
-PROF_STAGES = 12
+PROF_STAGES = 20
 
 
 class IGError(RuntimeError):
@@ -52,7 +52,12 @@ class ig_model_info_t(ctypes.Structure):
                 ("n_pairs", ctypes.c_int64 * 2),
                 ("reg3_mu", ctypes.c_double), ("reg3_sigma", ctypes.c_double),
                 ("reg3_r", ctypes.c_double),
-                ("reg3_threshold", ctypes.c_double)]
+                ("reg3_threshold", ctypes.c_double),
+                ("coherence_tests", ctypes.c_int64 * 2),
+                ("coherence_tests_tc", ctypes.c_int64 * 2),
+                ("coherence_tests_idx", ctypes.c_int64 * 2),
+                ("support_tests", ctypes.c_int64 * 2),
+                ("subset_kernel", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 # Every symbol of include/ig.h with its ctypes signature.
@@ -73,6 +78,7 @@ SIGNATURES = {
     "ig_prof_read": (ctypes.c_int, [_P, _P]),
     "ig_prof_stage_name": (ctypes.c_char_p, [_I32]),
     "ig_launch_count": (ctypes.c_int64, []),
+    "ig_prof_read_work": (ctypes.c_int, [_P]),
     "ig_score_noalloc": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P]),
 }
 SCORE_NOALLOC_MAX_ROWS = 262144
@@ -183,7 +189,12 @@ class Model:
                 "n_patterns": tuple(inf.n_patterns),
                 "n_pairs": tuple(inf.n_pairs),
                 "reg3": (inf.reg3_mu, inf.reg3_sigma, inf.reg3_r,
-                         inf.reg3_threshold)}
+                         inf.reg3_threshold),
+                "coherence_tests": tuple(inf.coherence_tests),
+                "coherence_tests_tc": tuple(inf.coherence_tests_tc),
+                "coherence_tests_idx": tuple(inf.coherence_tests_idx),
+                "support_tests": tuple(inf.support_tests),
+                "subset_kernel": inf.subset_kernel}
 
     def patterns(self, cls: int, device: str | None = None):
         """(words uint64[P, K], support uint32[P], score uint64[P]) of class cls.
@@ -301,12 +312,14 @@ def prof_reset():
 
 
 def prof_read() -> dict:
-    """{stage name: (total ms, timed launches)} since the last reset."""
+    """{stage name: (total ms, timed launches, executed tests)} since reset."""
     lib = load()
     ms = (ctypes.c_double * PROF_STAGES)()
     n = (ctypes.c_int64 * PROF_STAGES)()
+    w = (ctypes.c_int64 * PROF_STAGES)()
     _check(lib.ig_prof_read(ms, n))
-    return {lib.ig_prof_stage_name(i).decode(): (ms[i], n[i])
+    _check(lib.ig_prof_read_work(w))
+    return {lib.ig_prof_stage_name(i).decode(): (ms[i], n[i], w[i])
             for i in range(PROF_STAGES)}
 
 

@@ -56,12 +56,16 @@ int fail_cuda(cudaError_t e, const char* where) {
 
 // ---- per-stage timing -------------------------------------------------------
 const char* kStageNames[IG_PROF_STAGES] = {
-    "encode",        "split",          "pair_insert", "rehash",
-    "compact",       "coherence",      "select",      "canonical_sort",
-    "support",       "pattern_score",  "evidence",    "labels"};
+    "encode",         "split",          "pair_insert",  "rehash",
+    "compact",        "coherence",      "select",       "canonical_sort",
+    "support",        "pattern_score",  "evidence",     "labels",
+    "coherence_tc",   "support_tc",     "evidence_tc",  "expand",
+    "coherence_idx",  "support_idx",    "evidence_idx", "index_build"};
 enum Stage {
   S_ENCODE, S_SPLIT, S_PAIR, S_REHASH, S_COMPACT, S_COHERENCE,
-  S_SELECT, S_SORT, S_SUPPORT, S_PSCORE, S_EVIDENCE, S_LABELS
+  S_SELECT, S_SORT, S_SUPPORT, S_PSCORE, S_EVIDENCE, S_LABELS,
+  S_COHERENCE_TC, S_SUPPORT_TC, S_EVIDENCE_TC, S_EXPAND,
+  S_COHERENCE_IDX, S_SUPPORT_IDX, S_EVIDENCE_IDX, S_INDEX_BUILD
 };
 
 struct Prof {
@@ -69,6 +73,7 @@ struct Prof {
   bool on = false;
   double ms[IG_PROF_STAGES] = {};
   int64_t launches[IG_PROF_STAGES] = {};
+  int64_t work[IG_PROF_STAGES] = {};
   struct Pending {
     int stage;
     cudaEvent_t a, b;
@@ -91,22 +96,15 @@ cudaEvent_t prof_event() {
 
 // Brackets the launches of one stage with CUDA events on their stream.
 struct ProfScope {
+  void* token;
+  ProfScope(int st, cudaStream_t stream) : token(igk::prof_begin(st, stream)) {}
+  ~ProfScope() { igk::prof_end(token); }
+};
+
+struct ProfToken {
   int stage;
   cudaStream_t s;
-  cudaEvent_t a = nullptr;
-  ProfScope(int st, cudaStream_t stream) : stage(st), s(stream) {
-    std::lock_guard<std::mutex> lk(g_prof.mu);
-    if (!g_prof.on) return;
-    a = prof_event();
-    cudaEventRecord(a, s);
-  }
-  ~ProfScope() {
-    if (!a) return;
-    std::lock_guard<std::mutex> lk(g_prof.mu);
-    cudaEvent_t b = prof_event();
-    cudaEventRecord(b, s);
-    g_prof.pending.push_back({stage, a, b});
-  }
+  cudaEvent_t a;
 };
 
 void prof_drain_locked() {
@@ -234,6 +232,29 @@ std::atomic<long long> g_launches{0};
 
 }  // namespace
 
+void* igk::prof_begin(int stage, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  if (!g_prof.on) return nullptr;
+  ProfToken* t = new ProfToken{stage, s, prof_event()};
+  cudaEventRecord(t->a, s);
+  return t;
+}
+
+void igk::prof_add_work(int stage, int64_t tests) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  if (g_prof.on && stage >= 0 && stage < IG_PROF_STAGES) g_prof.work[stage] += tests;
+}
+
+void igk::prof_end(void* token) {
+  if (!token) return;
+  ProfToken* t = static_cast<ProfToken*>(token);
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  cudaEvent_t b = prof_event();
+  cudaEventRecord(b, t->s);
+  g_prof.pending.push_back({t->stage, t->a, b});
+  delete t;
+}
+
 void igk::count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 int igk::num_sms() {
@@ -258,11 +279,18 @@ struct ig_model {
   uint64_t* score[2] = {nullptr, nullptr};     // pad_rows entries
   int reg3 = 0;
   double mu = 0, sigma = 0, r = 0, thr = 0;
+  int subset_kernel = 1;                       // 1 integer pipe, 2 tensor cores, 3 item index
+  uint8_t* pat_img[2] = {nullptr, nullptr};    // tensor-core images of P^c
+  int64_t coh_tests[2] = {0, 0};               // coherence tests executed
+  int64_t coh_tests_tc[2] = {0, 0};            // ... of which on the tensor cores
+  int64_t coh_tests_pruned[2] = {0, 0};        // ... of which through the item index
+  int64_t sup_tests[2] = {0, 0};               // support tests executed
 };
 
 static void model_release(ig_model* m) {
   if (!m) return;
   for (int c = 0; c < 2; ++c) {
+    if (m->pat_img[c]) cudaFree(m->pat_img[c]);
     if (m->words[c] && m->words[c] != m->words_kt[c]) cudaFree(m->words[c]);
     if (m->words_kt[c]) cudaFree(m->words_kt[c]);
     if (m->support[c]) cudaFree(m->support[c]);
@@ -428,7 +456,7 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
   if (n > int64_t(0x7fffffff)) return fail(IG_E_OVERFLOW, "ig_fit: too many records");
   ig_params prm{0.0, 0, 0};
   if (params) prm = *params;
-  if (prm.subset_kernel != 0 && prm.subset_kernel != 1)
+  if (prm.subset_kernel < 0 || prm.subset_kernel > 3)
     return fail(IG_E_INVAL, "ig_fit: unknown subset_kernel %d", prm.subset_kernel);
   if (prm.reg3_enabled && !std::isfinite(prm.r))
     return fail(IG_E_INVAL, "ig_fit: Regulation 3 needs a finite r");
@@ -476,6 +504,24 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
   } guard{m};
   m->K = K;
   m->KT = KT;
+  // Subset-test form: the item index (default, and where K allows it), the
+  // tensor-core GEMM, or the plain integer-pipe kernel.  Dense steps of the
+  // index form run on the tensor cores where K allows.
+  const bool pruned = (prm.subset_kernel == 0 || prm.subset_kernel == 3) && KT >= 2;
+  const bool tc = prm.subset_kernel != 1 && igk::tc_supported(KT);
+  m->subset_kernel = pruned ? 3 : (tc ? 2 : 1);
+  // Complemented images of both classes' records: the stream operand of the
+  // other class's coherence and of this class's support, and the own operand
+  // of the Regulation 3 evidence.
+  DevBuf<uint8_t> rec_img[2];
+  if (tc) {
+    for (int c = 0; c < 2; ++c) {
+      IG_CUDA(rec_img[c].alloc(igk::tc_image_bytes(nc[c], KT, false), s), "ig_fit: images");
+      ProfScope ps(S_EXPAND, s);
+      IG_CUDA(igk::launch_expand(X[c].p, nc[c], KT, KT, true, false, rec_img[c].p, s),
+              "ig_fit: expand");
+    }
+  }
 
   for (int c = 1; c >= 0; --c) {
     const int o = 1 - c;
@@ -494,21 +540,81 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
     DevBuf<uint32_t> covered;
     DevBuf<uint64_t> surv;
     DevBuf<unsigned long long> d_kept;
-    IG_CUDA(covered.alloc(size_t(U), s), "ig_fit");
-    IG_CUDA(surv.alloc(size_t(igk::pad_rows(U)) * KT, s), "ig_fit");
-    IG_CUDA(d_kept.alloc(2, s), "ig_fit");
     const int64_t windows[] = {0, 32, 128, 512, 2048};
     const int nwin = int(sizeof(windows) / sizeof(windows[0]));
+    // With tensor cores the last window starts at 512 (a whole number of
+    // 128-row tiles) and runs as one 0/1 GEMM.
+    const int64_t tc_from = 512;
+    IG_CUDA(covered.alloc(size_t(U), s), "ig_fit");
+    IG_CUDA(surv.alloc(size_t(igk::pad_rows(U)) * KT, s), "ig_fit");
+    IG_CUDA(d_kept.alloc(nwin, s), "ig_fit");
+    IG_CUDA(cudaMemsetAsync(d_kept.p, 0, sizeof(unsigned long long) * nwin, s), "ig_fit");
     uint64_t* cur = cand.p;
     uint64_t* nxt = surv.p;
     const unsigned long long* cur_n_dev = nullptr;
+    int64_t win_lo[8], win_hi[8];
+    int rounds = 0;
+    // With the item index, records from 128 on are tested in one indexed
+    // round; with tensor cores (and no index), from 512 on in one GEMM round.
+    const int64_t pruned_from = 128;
+    int64_t round_tests[8];   // tests of an indexed round, or -1 for dense
     for (int wi = 0; wi < nwin && windows[wi] < nc[o]; ++wi) {
       const int64_t lo = windows[wi];
-      const int64_t hi = (wi + 1 < nwin && windows[wi + 1] < nc[o]) ? windows[wi + 1] : nc[o];
-      unsigned long long* kept = d_kept.p + (wi & 1);
+      int64_t hi = (wi + 1 < nwin && windows[wi + 1] < nc[o]) ? windows[wi + 1] : nc[o];
+      const bool pruned_round = pruned && lo == pruned_from;
+      const bool tc_round = !pruned && tc && lo >= tc_from;
+      if (pruned_round || tc_round) hi = nc[o];
+      unsigned long long* kept = d_kept.p + rounds;
+      round_tests[rounds] = -1;
       IG_CUDA(cudaMemsetAsync(covered.p, 0, sizeof(uint32_t) * U, s), "ig_fit");
-      IG_CUDA(cudaMemsetAsync(kept, 0, sizeof(unsigned long long), s), "ig_fit");
-      {
+      bool done_round = false;
+      if (pruned_round) {
+        // The indexed round needs the exact number of candidates left.
+        int64_t n_cur = U;
+        if (cur_n_dev) {
+          IG_CUDA(cudaMemcpyAsync(h_pinned + 3, cur_n_dev, sizeof(unsigned long long),
+                                  cudaMemcpyDeviceToHost, s),
+                  "ig_fit");
+          IG_CUDA(cudaStreamSynchronize(s), "ig_fit");
+          n_cur = int64_t(h_pinned[3]);
+        }
+        int64_t t = 0;
+        igk::PrunedArgs a;
+        a.prof_stage = S_COHERENCE_IDX;
+        a.mode = igk::MODE_ANY;
+        a.K = K;
+        a.KT = KT;
+        a.keyed = cur;
+        a.n_keyed = n_cur;
+        a.keyed_stride = KT;
+        a.multi = X[o].p + lo * KT;
+        a.n_multi = hi - lo;
+        a.multi_stride = KT;
+        a.keyed_score = nullptr;
+        a.out_u32 = covered.p;
+        a.out_u64 = nullptr;
+        a.status = d_status.p;
+        a.tests_out = &t;
+        IG_CUDA(igk::pruned_subset(a, s), "ig_fit: coherence");
+        if (t >= 0) {
+          round_tests[rounds] = t;
+          done_round = true;
+        }
+      }
+      if (!done_round && (tc_round || (pruned_round && tc && lo % 128 == 0))) {
+        DevBuf<uint8_t> own_img;
+        IG_CUDA(own_img.alloc(igk::tc_image_bytes(U, KT, true), s), "ig_fit: images");
+        {
+          ProfScope pe(S_EXPAND, s);
+          IG_CUDA(igk::launch_expand(cur, U, KT, KT, false, true, own_img.p, s), "ig_fit: expand");
+        }
+        ProfScope ps(S_COHERENCE_TC, s);
+        igk::TcArgs a{igk::MODE_ANY, KT,        own_img.p, U,       cur_n_dev, rec_img[o].p,
+                      lo / 128,      hi - lo,   nullptr,   covered.p, nullptr, d_status.p};
+        IG_CUDA(igk::launch_subset_tc(a, s), "ig_fit: coherence");
+        done_round = true;
+      }
+      if (!done_round) {
         ProfScope ps(S_COHERENCE, s);
         igk::SubsetArgs a{igk::MODE_ANY, KT,      cur,     U,          KT,       X[o].p + lo * KT,
                           nullptr,        hi - lo, covered.p, nullptr, d_status.p, cur_n_dev};
@@ -519,13 +625,30 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
         IG_CUDA(igk::launch_select_unflagged(cur, U, KT, covered.p, nxt, kept, s, cur_n_dev),
                 "ig_fit: select");
       }
+      win_lo[rounds] = lo;
+      win_hi[rounds] = hi;
+      ++rounds;
       cur_n_dev = kept;
       std::swap(cur, nxt);
+      if (hi == nc[o]) break;
     }
-    IG_CUDA(cudaMemcpyAsync(h_pinned + 2, cur_n_dev, sizeof(unsigned long long),
+    unsigned long long kept_h[8] = {0};
+    IG_CUDA(cudaMemcpyAsync(kept_h, d_kept.p, sizeof(unsigned long long) * rounds,
                             cudaMemcpyDeviceToHost, s),
             "ig_fit");
     IG_CHECK(read_status(d_status.p, s, "ig_fit: coherence"));
+    h_pinned[2] = kept_h[rounds - 1];
+    m->coh_tests[c] = m->coh_tests_tc[c] = m->coh_tests_pruned[c] = 0;
+    for (int r = 0; r < rounds; ++r) {
+      if (round_tests[r] >= 0) {
+        m->coh_tests[c] += round_tests[r];
+        m->coh_tests_pruned[c] += round_tests[r];
+        continue;
+      }
+      const int64_t t = int64_t(r == 0 ? U : kept_h[r - 1]) * (win_hi[r] - win_lo[r]);
+      m->coh_tests[c] += t;
+      if (tc && win_lo[r] >= (pruned ? pruned_from : tc_from)) m->coh_tests_tc[c] += t;
+    }
     const int64_t P = int64_t(h_pinned[2]);
     m->n_pat[c] = P;
     covered.reset();
@@ -546,11 +669,62 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
             "ig_fit: supports");
     IG_CUDA(cudaMemsetAsync(m->support[c], 0, sizeof(uint32_t) * std::max<int64_t>(1, P), s),
             "ig_fit");
-    {
+    bool support_done = false;
+    m->sup_tests[c] = P * nc[c];
+    if (pruned) {
+      int64_t t = 0;
+      igk::PrunedArgs a;
+      a.prof_stage = S_SUPPORT_IDX;
+      a.mode = igk::MODE_COUNT;
+      a.K = K;
+      a.KT = KT;
+      a.keyed = m->words_kt[c];
+      a.n_keyed = P;
+      a.keyed_stride = KT;
+      a.multi = X[c].p;
+      a.n_multi = nc[c];
+      a.multi_stride = KT;
+      a.keyed_score = nullptr;
+      a.out_u32 = m->support[c];
+      a.out_u64 = nullptr;
+      a.status = d_status.p;
+      a.tests_out = &t;
+      IG_CUDA(igk::pruned_subset(a, s), "ig_fit: support");
+      if (t >= 0) {
+        support_done = true;
+        m->sup_tests[c] = t;
+        igk::prof_add_work(S_SUPPORT_IDX, t);
+      }
+    }
+    if (support_done) {
+    } else if (tc) {
+      DevBuf<uint8_t> own_img;
+      IG_CUDA(own_img.alloc(igk::tc_image_bytes(P, KT, true), s), "ig_fit: images");
+      {
+        ProfScope pe(S_EXPAND, s);
+        IG_CUDA(igk::launch_expand(m->words_kt[c], P, KT, KT, false, true, own_img.p, s),
+                "ig_fit: expand");
+      }
+      igk::prof_add_work(S_SUPPORT_TC, P * nc[c]);
+      ProfScope ps(S_SUPPORT_TC, s);
+      igk::TcArgs a{igk::MODE_COUNT, KT,      own_img.p,      P,       nullptr, rec_img[c].p,
+                    0,               nc[c],   nullptr,        m->support[c], nullptr,
+                    d_status.p};
+      IG_CUDA(igk::launch_subset_tc(a, s), "ig_fit: support");
+    } else {
+      igk::prof_add_work(S_SUPPORT, P * nc[c]);
       ProfScope ps(S_SUPPORT, s);
       igk::SubsetArgs a{igk::MODE_COUNT, KT, m->words_kt[c], P, KT, X[c].p, nullptr, nc[c],
                         m->support[c], nullptr, d_status.p};
       IG_CUDA(igk::launch_subset(a, s), "ig_fit: support");
+    }
+    if (tc && P) {  // stream image of P^c for the evidence kernels
+      IG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&m->pat_img[c]),
+                              igk::tc_image_bytes(P, KT, false), s),
+              "ig_fit: images");
+      ProfScope pe(S_EXPAND, s);
+      IG_CUDA(igk::launch_expand(m->words_kt[c], P, KT, KT, false, false, m->pat_img[c], s),
+              "ig_fit: expand");
     }
     const size_t npad = size_t(std::max<int64_t>(1, igk::pad_rows(P)));
     IG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&m->score[c]), sizeof(uint64_t) * npad, s),
@@ -581,7 +755,33 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
     DevBuf<unsigned long long> d_n;
     IG_CUDA(d_n.alloc(size_t(nc[0]), s), "ig_fit");
     IG_CUDA(cudaMemsetAsync(d_n.p, 0, sizeof(unsigned long long) * nc[0], s), "ig_fit");
-    {
+    int64_t t_idx = -1;
+    if (pruned && m->n_pat[0]) {
+      igk::PrunedArgs a;
+      a.prof_stage = S_EVIDENCE_IDX;
+      a.mode = igk::MODE_SUM;
+      a.K = K;
+      a.KT = KT;
+      a.keyed = m->words_kt[0];
+      a.n_keyed = m->n_pat[0];
+      a.keyed_stride = KT;
+      a.multi = X[0].p;
+      a.n_multi = nc[0];
+      a.multi_stride = KT;
+      a.keyed_score = m->score[0];
+      a.out_u32 = nullptr;
+      a.out_u64 = d_n.p;
+      a.status = d_status.p;
+      a.tests_out = &t_idx;
+      IG_CUDA(igk::pruned_subset(a, s), "ig_fit: Regulation 3 evidence");
+    }
+    if (t_idx >= 0) {
+    } else if (tc && m->n_pat[0]) {
+      ProfScope ps(S_EVIDENCE_TC, s);
+      igk::TcArgs a{igk::MODE_SUM, KT,           rec_img[0].p, nc[0],   nullptr, m->pat_img[0],
+                    0,             m->n_pat[0],  m->score[0],  nullptr, d_n.p,   d_status.p};
+      IG_CUDA(igk::launch_subset_tc(a, s), "ig_fit: Regulation 3 evidence");
+    } else {
       ProfScope ps(S_EVIDENCE, s);
       igk::SubsetArgs a{igk::MODE_SUM, KT, X[0].p, nc[0], KT, m->words_kt[0], m->score[0],
                         m->n_pat[0], nullptr, d_n.p, d_status.p};
@@ -627,6 +827,16 @@ int ig_model_info(const ig_model* m, ig_model_info_t* info) {
   info->reg3_sigma = m->sigma;
   info->reg3_r = m->r;
   info->reg3_threshold = m->thr;
+  info->coherence_tests[0] = m->coh_tests[0];
+  info->coherence_tests[1] = m->coh_tests[1];
+  info->coherence_tests_tc[0] = m->coh_tests_tc[0];
+  info->coherence_tests_tc[1] = m->coh_tests_tc[1];
+  info->coherence_tests_idx[0] = m->coh_tests_pruned[0];
+  info->coherence_tests_idx[1] = m->coh_tests_pruned[1];
+  info->support_tests[0] = m->sup_tests[0];
+  info->support_tests[1] = m->sup_tests[1];
+  info->subset_kernel = m->subset_kernel;
+  info->reserved = 0;
   return IG_OK;
 }
 
@@ -676,11 +886,59 @@ int ig_score(const ig_model* m, const uint64_t* rows, int64_t n_rows, int64_t* A
   IG_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), s), "ig_score");
   IG_CUDA(cudaMemsetAsync(A.d, 0, sizeof(unsigned long long) * n_rows, s), "ig_score");
   IG_CUDA(cudaMemsetAsync(N.d, 0, sizeof(unsigned long long) * n_rows, s), "ig_score");
+  DevBuf<uint8_t> test_img;
+  const bool pruned = m->subset_kernel == 3;
+  bool tc = m->subset_kernel >= 2 && igk::tc_supported(m->KT) && m->pat_img[0] && m->pat_img[1];
+  bool done[2] = {false, false};
+  if (pruned) {
+    for (int c = 1; c >= 0; --c) {
+      if (m->n_pat[c] == 0) {
+        done[c] = true;
+        continue;
+      }
+      int64_t t = 0;
+      igk::PrunedArgs a;
+      a.prof_stage = S_EVIDENCE_IDX;
+      a.mode = igk::MODE_SUM;
+      a.K = m->K;
+      a.KT = m->KT;
+      a.keyed = m->words_kt[c];
+      a.n_keyed = m->n_pat[c];
+      a.keyed_stride = m->KT;
+      a.multi = in.d;
+      a.n_multi = n_rows;
+      a.multi_stride = m->K;
+      a.keyed_score = m->score[c];
+      a.out_u32 = nullptr;
+      a.out_u64 = c == 1 ? A.d : N.d;
+      a.status = d_status.p;
+      a.tests_out = &t;
+      IG_CUDA(igk::pruned_subset(a, s), "ig_score: evidence");
+      done[c] = t >= 0;
+      if (done[c]) igk::prof_add_work(S_EVIDENCE_IDX, t);
+    }
+  }
+  if (done[0] && done[1]) tc = false;
+  if (tc) {
+    IG_CUDA(test_img.alloc(igk::tc_image_bytes(n_rows, m->KT, true), s), "ig_score: images");
+    ProfScope pe(S_EXPAND, s);
+    IG_CUDA(igk::launch_expand(in.d, n_rows, m->K, m->KT, true, true, test_img.p, s),
+            "ig_score: expand");
+  }
   for (int c = 1; c >= 0; --c) {  // A from P+, then N from P- (Eq. 4)
-    ProfScope ps(S_EVIDENCE, s);
-    igk::SubsetArgs a{igk::MODE_SUM, m->KT, in.d, n_rows, m->K, m->words_kt[c], m->score[c],
-                      m->n_pat[c], nullptr, c == 1 ? A.d : N.d, d_status.p};
-    IG_CUDA(igk::launch_subset(a, s), "ig_score: evidence");
+    if (done[c]) continue;
+    igk::prof_add_work(tc && m->n_pat[c] ? S_EVIDENCE_TC : S_EVIDENCE, n_rows * m->n_pat[c]);
+    ProfScope ps(tc && m->n_pat[c] ? S_EVIDENCE_TC : S_EVIDENCE, s);
+    if (tc && m->n_pat[c]) {
+      igk::TcArgs a{igk::MODE_SUM, m->KT,      test_img.p,  n_rows,  nullptr,
+                    m->pat_img[c], 0,          m->n_pat[c], m->score[c], nullptr,
+                    c == 1 ? A.d : N.d,        d_status.p};
+      IG_CUDA(igk::launch_subset_tc(a, s), "ig_score: evidence");
+    } else {
+      igk::SubsetArgs a{igk::MODE_SUM, m->KT, in.d, n_rows, m->K, m->words_kt[c], m->score[c],
+                        m->n_pat[c], nullptr, c == 1 ? A.d : N.d, d_status.p};
+      IG_CUDA(igk::launch_subset(a, s), "ig_score: evidence");
+    }
   }
   if (label_out) {
     ProfScope ps(S_LABELS, s);
@@ -819,7 +1077,15 @@ int ig_prof_reset(void) {
   for (int i = 0; i < IG_PROF_STAGES; ++i) {
     g_prof.ms[i] = 0;
     g_prof.launches[i] = 0;
+    g_prof.work[i] = 0;
   }
+  return IG_OK;
+}
+
+int ig_prof_read_work(int64_t* tests) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  for (int i = 0; i < IG_PROF_STAGES; ++i)
+    if (tests) tests[i] = g_prof.work[i];
   return IG_OK;
 }
 

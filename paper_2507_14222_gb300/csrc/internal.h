@@ -22,6 +22,15 @@ inline int64_t pad_rows(int64_t n) { return ((n + kRowPad - 1) / kRowPad) * kRow
 
 int num_sms();
 
+// Stage timing (ig_prof_*): prof_begin records a CUDA event on s when timing
+// is on and returns a token (nullptr otherwise); prof_end records the
+// closing event and files the pair under the stage.
+void* prof_begin(int stage, cudaStream_t s);
+void prof_end(void* token);
+// Adds executed subset tests to a stage's tally (while timing is on).
+void prof_add_work(int stage, int64_t tests);
+constexpr int kStageIndexBuild = 19;
+
 // Adds n to the library's count of kernel launches (ig_launch_count).
 void count_launches(int n);
 
@@ -108,6 +117,79 @@ struct SubsetArgs {
   const unsigned long long* n_own_dev = nullptr;
 };
 cudaError_t launch_subset(const SubsetArgs& a, cudaStream_t s);
+
+// ---- subset_tc.cu (tensor-core form of the subset tests) --------------------
+// Operand images: rows expanded to one FP8 byte per item in the shared-memory
+// layout of the MMA, in tiles of 128 rows.  own_side images feed the M side
+// (one tile per CTA), the others the streamed N side.  `complement` images
+// hold NOT(row) (used for the records being tested against).
+bool tc_supported(int KT);
+size_t tc_image_bytes(int64_t n, int KT, bool own_side);
+cudaError_t launch_expand(const uint64_t* rows, int64_t n, int stride, int KT, bool complement,
+                          bool own_side, uint8_t* img, cudaStream_t s);
+struct TcArgs {
+  int mode;
+  int KT;
+  const uint8_t* a_img;                 // own image (patterns, or complemented records for SUM)
+  int64_t n_own;                        // own rows (upper bound when n_own_dev is given)
+  const unsigned long long* n_own_dev;  // optional device-side own count
+  const uint8_t* b_img;                 // stream image
+  int64_t b_tile0;                      // first 128-row stream tile to use
+  int64_t n_stream;                     // stream rows from tile b_tile0 on
+  const uint64_t* score;                // MODE_SUM: S per stream row (from b_tile0 * 128)
+  uint32_t* out_u32;
+  unsigned long long* out_u64;
+  int* status;
+};
+cudaError_t launch_subset_tc(const TcArgs& a, cudaStream_t s);
+
+// ---- prune.cu (subset tests restricted by an item index) --------------------
+struct WorkItem {
+  int64_t own_begin, own_count, str_begin, str_count;
+};
+struct GroupedArgs {
+  int mode;
+  int KT;
+  const WorkItem* items;
+  int64_t n_items;
+  const uint64_t* own;
+  const uint32_t* own_ids;
+  const uint64_t* stream;
+  const uint64_t* stream_score;
+  uint32_t* out_u32;
+  unsigned long long* out_u64;
+  int* status;
+};
+cudaError_t launch_grouped_subset(const GroupedArgs& a, cudaStream_t s);
+
+// A subset test of "keyed" rows (patterns: MODE_ANY / MODE_COUNT own rows,
+// MODE_SUM stream rows) against "multi" rows (records), restricted to the
+// pairs that share the pattern's key item.  Outputs are indexed like the
+// dense kernel's: by pattern for ANY / COUNT, by record for SUM.  Requires
+// KT >= 2.  Synchronizes the stream.
+struct PrunedArgs {
+  int mode;
+  int K;   // words holding items (items 0 .. 64K-1)
+  int KT;  // padded words of the kernels (2, 4, 8 or 16)
+  const uint64_t* keyed;
+  int64_t n_keyed;
+  int keyed_stride;
+  const uint64_t* multi;
+  int64_t n_multi;
+  int multi_stride;
+  const uint64_t* keyed_score;  // MODE_SUM: S of each keyed row
+  uint32_t* out_u32;
+  unsigned long long* out_u64;
+  int* status;
+  int64_t* tests_out;  // subset tests executed; -1 if the index was not used
+  // The index is not built (tests_out = -1, nothing written) when the
+  // records hold more than this fraction of all item slots on average:
+  // then nearly every group holds nearly every record and the dense kernels
+  // are faster.
+  double max_fill = 0.25;
+  int prof_stage = -1;  // stage under which the grouped kernel is timed
+};
+cudaError_t pruned_subset(const PrunedArgs& a, cudaStream_t s);
 
 // Keeps the rows whose flag is zero: out gets them (stride KT), out_count
 // the number kept (must start at 0).  With n_dev given, the row count is

@@ -1,0 +1,513 @@
+// Subset tests with an item index (exact pruning of Eq. 3, Eq. 2 and Eq. 4).
+//
+// p is inside r only if r contains every item of p, in particular the item
+// k(p) of p that the fewest records contain.  So instead of testing every
+// (pattern, record) pair:
+//   * the records ("multi" side) are filed under every item they contain:
+//     group l holds a copy of each record with item l;
+//   * the patterns ("keyed" side) are filed under their key item k(p), the
+//     item of p with the smallest record count (lowest item on ties); a
+//     pattern with an item no record contains is filed in the extra group L
+//     and needs no test at all (it is inside no record);
+//   * group l's patterns are tested only against group l's records, as dense
+//     blocks of the integer-pipe kernel.
+// Every (pattern, record) pair with p inside r is met exactly once (in group
+// k(p)), and no pair outside a common group can have p inside r, so counts,
+// flags and score sums are the same as from the full product.
+//
+// Work items are (group, own tile, stream range) blocks; the host builds the
+// list from the group sizes and balances the stream ranges across the GPU.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace igk {
+
+// ---- building the groups ------------------------------------------------------
+
+// freq[l] += number of rows containing item l.
+__global__ void item_histogram_kernel(const uint64_t* __restrict__ rows, int64_t n, int stride,
+                                      int K, int L, uint32_t* __restrict__ freq) {
+  extern __shared__ uint32_t h[];
+  for (int l = threadIdx.x; l < L; l += blockDim.x) h[l] = 0;
+  __syncthreads();
+  const int64_t step = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += step)
+    for (int k = 0; k < K; ++k) {
+      uint64_t w = rows[i * stride + k];
+      while (w) {
+        const int b = __ffsll(static_cast<long long>(w)) - 1;
+        w &= w - 1;
+        atomicAdd(&h[k * 64 + b], 1u);
+      }
+    }
+  __syncthreads();
+  for (int l = threadIdx.x; l < L; l += blockDim.x)
+    if (h[l]) atomicAdd(freq + l, h[l]);
+}
+
+// Exclusive scan of cnt[0..len) into off[0..len] (off[len] = total), one block.
+__global__ void small_scan_kernel(const uint32_t* __restrict__ cnt, int len,
+                                  uint32_t* __restrict__ off) {
+  __shared__ uint32_t part[1024];
+  const int chunk = (len + 1023) / 1024;
+  const int lo = threadIdx.x * chunk, hi = min(len, lo + chunk);
+  uint32_t s = 0;
+  for (int i = lo; i < hi; ++i) s += cnt[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int d = 1; d < 1024; d <<= 1) {
+    uint32_t v = threadIdx.x >= d ? part[threadIdx.x - d] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = part[threadIdx.x] - s;
+  for (int i = lo; i < hi; ++i) {
+    off[i] = run;
+    run += cnt[i];
+  }
+  if (threadIdx.x == 1023) off[len] = part[1023];
+}
+
+// Copies row i into the group of every item it contains.
+__global__ void multi_scatter_kernel(const uint64_t* __restrict__ rows, int64_t n, int stride,
+                                     int K, int KT, const uint32_t* __restrict__ off,
+                                     uint32_t* __restrict__ cursor, uint64_t* __restrict__ out,
+                                     uint32_t* __restrict__ ids) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t w[IG_MAX_KT_WORDS];
+  for (int k = 0; k < KT; ++k) w[k] = k < K ? rows[i * stride + k] : 0ull;
+  for (int k = 0; k < K; ++k) {
+    uint64_t x = w[k];
+    while (x) {
+      const int b = __ffsll(static_cast<long long>(x)) - 1;
+      x &= x - 1;
+      const int l = k * 64 + b;
+      const uint32_t pos = off[l] + atomicAdd(cursor + l, 1u);
+      for (int q = 0; q < KT; ++q) out[int64_t(pos) * KT + q] = w[q];
+      ids[pos] = uint32_t(i);
+    }
+  }
+}
+
+// key[i] = the item of row i with the smallest freq (lowest item on ties),
+// or L when one of its items has freq 0 (or the row is empty).
+__global__ void key_item_kernel(const uint64_t* __restrict__ rows, int64_t n, int stride, int K,
+                                int L, const uint32_t* __restrict__ freq,
+                                uint32_t* __restrict__ key, uint32_t* __restrict__ kcount) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t best = 0xffffffffu;
+  int best_l = L;
+  for (int k = 0; k < K; ++k) {
+    uint64_t x = rows[i * stride + k];
+    while (x) {
+      const int b = __ffsll(static_cast<long long>(x)) - 1;
+      x &= x - 1;
+      const int l = k * 64 + b;
+      const uint32_t f = freq[l];
+      if (f < best) {
+        best = f;
+        best_l = l;
+      }
+    }
+  }
+  if (best == 0u) best_l = L;
+  key[i] = uint32_t(best_l);
+  atomicAdd(kcount + best_l, 1u);
+}
+
+__global__ void keyed_scatter_kernel(const uint64_t* __restrict__ rows, int64_t n, int stride,
+                                     int K, int KT, const uint32_t* __restrict__ key,
+                                     const uint32_t* __restrict__ off,
+                                     uint32_t* __restrict__ cursor, uint64_t* __restrict__ out,
+                                     uint32_t* __restrict__ ids,
+                                     const uint64_t* __restrict__ payload,
+                                     uint64_t* __restrict__ payload_out) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t l = key[i];
+  const uint32_t pos = off[l] + atomicAdd(cursor + l, 1u);
+  for (int q = 0; q < KT; ++q) out[int64_t(pos) * KT + q] = q < K ? rows[i * stride + q] : 0ull;
+  ids[pos] = uint32_t(i);
+  if (payload) payload_out[pos] = payload[i];
+}
+
+// ---- the grouped subset kernel ------------------------------------------------
+
+constexpr int kGThreads = 256;
+constexpr int kGStages = 3;
+
+template <int KT>
+struct GShape {
+  static constexpr int TR = (8192 / (KT * 8)) > 256 ? 256 : (8192 / (KT * 8));
+  static constexpr int Q = KT >= 16 ? 2 : 4;
+  static constexpr int H = 2 * KT;
+};
+
+struct GroupedParams {
+  const WorkItem* items;
+  const uint64_t* own;        // grouped own rows (stride KT)
+  const uint32_t* own_ids;    // original index of each own row
+  const uint64_t* stream;     // grouped stream rows (stride KT, padded)
+  const uint64_t* stream_score;  // MODE_SUM: score per grouped stream row (padded)
+  uint32_t* out_u32;
+  unsigned long long* out_u64;
+  int* status;
+};
+
+template <int KT, int MODE>
+__global__ void __launch_bounds__(kGThreads) grouped_subset_kernel(GroupedParams p) {
+  using S = GShape<KT>;
+  constexpr int TR = S::TR, Q = S::Q, H = S::H;
+  constexpr uint32_t kRowBytes = TR * KT * 8;
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint64_t* rows_s = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* bars = rows_s + kGStages * TR * KT;
+
+  const WorkItem wi = p.items[blockIdx.x];
+  uint32_t own[Q][H];
+  bool valid[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int64_t r = int64_t(q) * kGThreads + threadIdx.x;
+    valid[q] = r < wi.own_count;
+    const uint64_t* src = p.own + (wi.own_begin + r) * KT;
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+      const uint64_t w = valid[q] ? src[k] : 0ull;
+      own[q][2 * k] = uint32_t(w);
+      own[q][2 * k + 1] = uint32_t(w >> 32);
+    }
+  }
+  // Stream tiles may start at any row: with KT >= 2 every row is 16-byte
+  // aligned, as the bulk copy needs.  Scores (MODE_SUM) are not staged; the
+  // rare hits read theirs from global memory.
+  const int64_t s_lo = wi.str_begin, s_hi = wi.str_begin + wi.str_count;
+  const int64_t ntiles = ceil_div(s_hi - s_lo, TR);
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kGStages; ++st) mbar_init(bars + st, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto issue = [&](int64_t tile) {
+    const int st = int(tile % kGStages);
+    const int64_t r0 = s_lo + tile * TR;
+    mbar_arrive_expect_tx(bars + st, kRowBytes);
+    bulk_g2s(rows_s + st * TR * KT, p.stream + r0 * KT, kRowBytes, bars + st);
+  };
+  if (threadIdx.x == 0)
+    for (int64_t t = 0; t < ntiles && t < kGStages; ++t) issue(t);
+
+  bool cov[Q];
+  uint32_t cnt[Q];
+  unsigned long long sum[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    cov[q] = false;
+    cnt[q] = 0;
+    sum[q] = 0;
+  }
+  int64_t tile = 0;
+  bool failed = false;
+  for (; tile < ntiles; ++tile) {
+    const int st = int(tile % kGStages);
+    const bool ok = mbar_wait(bars + st, uint32_t((tile / kGStages) & 1), p.status);
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    const int64_t left = s_hi - (s_lo + tile * TR);
+    const int nr = int(left < TR ? left : TR);
+    const uint32_t* rs = reinterpret_cast<const uint32_t*>(rows_s + st * TR * KT);
+#pragma unroll 2
+    for (int r = 0; r < nr; ++r) {
+      uint32_t rh[H];
+#pragma unroll
+      for (int v = 0; v < H / 4; ++v) {
+        const uint4 x = reinterpret_cast<const uint4*>(rs + r * H)[v];
+        rh[4 * v] = x.x;
+        rh[4 * v + 1] = x.y;
+        rh[4 * v + 2] = x.z;
+        rh[4 * v + 3] = x.w;
+      }
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        uint32_t acc = 0;
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+          if constexpr (MODE == MODE_SUM)
+            acc |= rh[h] & ~own[q][h];
+          else
+            acc |= own[q][h] & ~rh[h];
+        }
+        const bool hit = acc == 0u;
+        if constexpr (MODE == MODE_ANY) cov[q] |= hit;
+        if constexpr (MODE == MODE_COUNT) cnt[q] += hit ? 1u : 0u;
+        if constexpr (MODE == MODE_SUM) {
+          if (hit) sum[q] += p.stream_score[s_lo + tile * TR + r];
+        }
+      }
+    }
+    bool stop = false;
+    if constexpr (MODE == MODE_ANY) {
+      bool done = true;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) done &= (cov[q] || !valid[q]);
+      stop = __syncthreads_and(done) != 0;
+    } else {
+      __syncthreads();
+    }
+    if (stop) break;
+    if (threadIdx.x == 0 && tile + kGStages < ntiles) issue(tile + kGStages);
+  }
+  if (threadIdx.x == 0 && tile < ntiles) {
+    const int64_t first = failed ? tile : tile + 1;
+    const int64_t end = (tile + kGStages < ntiles) ? tile + kGStages : ntiles;
+    for (int64_t t = first; t < end; ++t)
+      if (!mbar_wait(bars + int(t % kGStages), uint32_t((t / kGStages) & 1), p.status)) break;
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    if (!valid[q]) continue;
+    const uint32_t id = p.own_ids[wi.own_begin + int64_t(q) * kGThreads + threadIdx.x];
+    if constexpr (MODE == MODE_ANY) {
+      if (cov[q]) p.out_u32[id] = 1u;
+    }
+    if constexpr (MODE == MODE_COUNT) {
+      if (cnt[q]) atomicAdd(p.out_u32 + id, cnt[q]);
+    }
+    if constexpr (MODE == MODE_SUM) {
+      if (sum[q]) atomicAdd(p.out_u64 + id, sum[q]);
+    }
+  }
+}
+
+// ---- host side ----------------------------------------------------------------
+
+cudaError_t launch_item_histogram(const uint64_t* rows, int64_t n, int stride, int K, int L,
+                                  uint32_t* freq, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int64_t blocks = ceil_div(n, 256);
+  if (blocks > int64_t(num_sms()) * 4) blocks = int64_t(num_sms()) * 4;
+  item_histogram_kernel<<<unsigned(blocks), 256, size_t(L) * 4, s>>>(rows, n, stride, K, L, freq);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_small_scan(const uint32_t* cnt, int len, uint32_t* off, cudaStream_t s) {
+  small_scan_kernel<<<1, 1024, 0, s>>>(cnt, len, off);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multi_scatter(const uint64_t* rows, int64_t n, int stride, int K, int KT,
+                                 const uint32_t* off, uint32_t* cursor, uint64_t* out,
+                                 uint32_t* ids, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  multi_scatter_kernel<<<unsigned(ceil_div(n, 256)), 256, 0, s>>>(rows, n, stride, K, KT, off,
+                                                                  cursor, out, ids);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_key_item(const uint64_t* rows, int64_t n, int stride, int K, int L,
+                            const uint32_t* freq, uint32_t* key, uint32_t* kcount,
+                            cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  key_item_kernel<<<unsigned(ceil_div(n, 256)), 256, 0, s>>>(rows, n, stride, K, L, freq, key,
+                                                             kcount);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_keyed_scatter(const uint64_t* rows, int64_t n, int stride, int K, int KT,
+                                 const uint32_t* key, const uint32_t* off, uint32_t* cursor,
+                                 uint64_t* out, uint32_t* ids, const uint64_t* payload,
+                                 uint64_t* payload_out, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  keyed_scatter_kernel<<<unsigned(ceil_div(n, 256)), 256, 0, s>>>(
+      rows, n, stride, K, KT, key, off, cursor, out, ids, payload, payload_out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+int grouped_rows_per_tile(int KT) {
+  switch (KT) {
+    case 2: return GShape<2>::TR;
+    case 4: return GShape<4>::TR;
+    case 8: return GShape<8>::TR;
+    case 16: return GShape<16>::TR;
+  }
+  return 256;
+}
+
+int grouped_own_per_cta(int KT) { return kGThreads * (KT >= 16 ? 2 : 4); }
+
+template <int KT, int MODE>
+static cudaError_t grouped_t(const GroupedArgs& a, cudaStream_t s) {
+  using S = GShape<KT>;
+  GroupedParams p{a.items, a.own, a.own_ids, a.stream, a.stream_score,
+                  a.out_u32, a.out_u64, a.status};
+  const size_t smem = size_t(kGStages) * S::TR * KT * 8 + kGStages * sizeof(uint64_t);
+  grouped_subset_kernel<KT, MODE><<<unsigned(a.n_items), kGThreads, smem, s>>>(p);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grouped_subset(const GroupedArgs& a, cudaStream_t s) {
+  if (a.n_items == 0) return cudaSuccess;
+#define IG_G_CASE(KTV)                                          \
+  case KTV:                                                     \
+    switch (a.mode) {                                           \
+      case MODE_ANY: return grouped_t<KTV, MODE_ANY>(a, s);     \
+      case MODE_COUNT: return grouped_t<KTV, MODE_COUNT>(a, s); \
+      case MODE_SUM: return grouped_t<KTV, MODE_SUM>(a, s);     \
+    }                                                           \
+    break;
+  switch (a.KT) {
+    IG_G_CASE(2)
+    IG_G_CASE(4)
+    IG_G_CASE(8)
+    IG_G_CASE(16)
+  }
+#undef IG_G_CASE
+  return cudaErrorInvalidValue;
+}
+
+// Blocks (group, own tile, stream range) with about `target` tests each.
+void build_work_items(const uint32_t* own_off, const uint32_t* str_off, int groups, int own_tile,
+                      int str_tile, int64_t target, std::vector<WorkItem>* items,
+                      int64_t* tests) {
+  items->clear();
+  *tests = 0;
+  for (int l = 0; l < groups; ++l) {
+    const int64_t no = int64_t(own_off[l + 1]) - own_off[l];
+    const int64_t ns = int64_t(str_off[l + 1]) - str_off[l];
+    if (no == 0 || ns == 0) continue;
+    *tests += no * ns;
+    for (int64_t o = 0; o < no; o += own_tile) {
+      const int64_t oc = std::min<int64_t>(own_tile, no - o);
+      int64_t per = std::max<int64_t>(str_tile, target / std::max<int64_t>(1, oc));
+      per = ((per + str_tile - 1) / str_tile) * str_tile;
+      for (int64_t r = 0; r < ns; r += per) {
+        WorkItem w;
+        w.own_begin = int64_t(own_off[l]) + o;
+        w.own_count = oc;
+        w.str_begin = int64_t(str_off[l]) + r;
+        w.str_count = std::min<int64_t>(per, ns - r);
+        items->push_back(w);
+      }
+    }
+  }
+}
+
+// One pruned subset test (see the top of this file): builds both sides'
+// groups, reads the group sizes back (the one synchronisation), and runs the
+// grouped kernel over blocks of about equal work.
+cudaError_t pruned_subset(const PrunedArgs& a, cudaStream_t s) {
+  *a.tests_out = 0;
+  if (a.n_keyed == 0 || a.n_multi == 0) return cudaSuccess;
+  const int L = 64 * a.K, KT = a.KT;
+  cudaError_t e;
+  std::vector<void*> bufs;
+  auto alloc = [&](void** p, size_t bytes) {
+    cudaError_t r = cudaMallocAsync(p, bytes ? bytes : 16, s);
+    if (r == cudaSuccess) bufs.push_back(*p);
+    return r;
+  };
+  auto done = [&](cudaError_t r) {
+    for (void* b : bufs) cudaFreeAsync(b, s);
+    return r;
+  };
+#define IG_P_TRY(x) \
+  if ((e = (x)) != cudaSuccess) return done(e);
+  // Small per-item arrays in one allocation: freq, kcount, moff, koff, cursors.
+  uint32_t* small = nullptr;
+  const size_t nsmall = size_t(L) + (L + 1) + (L + 1) + (L + 2) + (L + 1) + (L + 1);
+  IG_P_TRY(alloc(reinterpret_cast<void**>(&small), nsmall * 4));
+  uint32_t* freq = small;
+  uint32_t* kcount = freq + L;
+  uint32_t* moff = kcount + (L + 1);
+  uint32_t* koff = moff + (L + 1);
+  uint32_t* mcur = koff + (L + 2);
+  uint32_t* kcur = mcur + (L + 1);
+  uint32_t* key = nullptr;
+  void* build_tok = prof_begin(kStageIndexBuild, s);
+  IG_P_TRY(cudaMemsetAsync(small, 0, nsmall * 4, s));
+  IG_P_TRY(alloc(reinterpret_cast<void**>(&key), size_t(a.n_keyed) * 4));
+  IG_P_TRY(launch_item_histogram(a.multi, a.n_multi, a.multi_stride, a.K, L, freq, s));
+  IG_P_TRY(launch_small_scan(freq, L, moff, s));
+  IG_P_TRY(launch_key_item(a.keyed, a.n_keyed, a.keyed_stride, a.K, L, freq, key, kcount, s));
+  IG_P_TRY(launch_small_scan(kcount, L + 1, koff, s));
+  std::vector<uint32_t> h_moff(L + 1), h_koff(L + 2);
+  prof_end(build_tok);
+  IG_P_TRY(cudaMemcpyAsync(h_moff.data(), moff, (L + 1) * 4, cudaMemcpyDeviceToHost, s));
+  IG_P_TRY(cudaMemcpyAsync(h_koff.data(), koff, (L + 2) * 4, cudaMemcpyDeviceToHost, s));
+  IG_P_TRY(cudaStreamSynchronize(s));
+  const int64_t n_copies = h_moff[L];
+  if (double(n_copies) > a.max_fill * double(a.n_multi) * double(L)) {
+    *a.tests_out = -1;
+    return done(cudaSuccess);
+  }
+  // Grouped arrays, padded by one stream tile so whole-tile copies stay in bounds.
+  uint64_t *mrows = nullptr, *krows = nullptr, *kscore = nullptr;
+  uint32_t *mids = nullptr, *kids = nullptr;
+  IG_P_TRY(alloc(reinterpret_cast<void**>(&mrows), size_t(n_copies + 256) * KT * 8));
+  IG_P_TRY(alloc(reinterpret_cast<void**>(&mids), size_t(n_copies) * 4));
+  IG_P_TRY(alloc(reinterpret_cast<void**>(&krows), size_t(a.n_keyed + 256) * KT * 8));
+  IG_P_TRY(alloc(reinterpret_cast<void**>(&kids), size_t(a.n_keyed) * 4));
+  if (a.mode == MODE_SUM)
+    IG_P_TRY(alloc(reinterpret_cast<void**>(&kscore), size_t(a.n_keyed + 256) * 8));
+  build_tok = prof_begin(kStageIndexBuild, s);
+  IG_P_TRY(launch_multi_scatter(a.multi, a.n_multi, a.multi_stride, a.K, KT, moff, mcur, mrows,
+                                mids, s));
+  IG_P_TRY(launch_keyed_scatter(a.keyed, a.n_keyed, a.keyed_stride, a.K, KT, key, koff, kcur,
+                                krows, kids, a.mode == MODE_SUM ? a.keyed_score : nullptr,
+                                kscore, s));
+  prof_end(build_tok);
+  // Work blocks: own = keyed (patterns) for ANY / COUNT, own = multi
+  // (records) for SUM; about 8 blocks per SM worth of tests each.
+  std::vector<WorkItem> items;
+  int64_t tests = 0;
+  const bool own_keyed = a.mode != MODE_SUM;
+  int64_t total = 0;
+  for (int l = 0; l < L; ++l)
+    total += (int64_t(h_koff[l + 1]) - h_koff[l]) * (int64_t(h_moff[l + 1]) - h_moff[l]);
+  const int64_t target = std::max<int64_t>(total / (int64_t(num_sms()) * 8), 1 << 16);
+  build_work_items(own_keyed ? h_koff.data() : h_moff.data(),
+                   own_keyed ? h_moff.data() : h_koff.data(), L, grouped_own_per_cta(KT),
+                   grouped_rows_per_tile(KT), target, &items, &tests);
+  *a.tests_out = tests;
+  if (!items.empty()) {
+    WorkItem* d_items = nullptr;
+    IG_P_TRY(alloc(reinterpret_cast<void**>(&d_items), items.size() * sizeof(WorkItem)));
+    IG_P_TRY(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(WorkItem),
+                             cudaMemcpyHostToDevice, s));
+    GroupedArgs g{a.mode,
+                  KT,
+                  d_items,
+                  int64_t(items.size()),
+                  own_keyed ? krows : mrows,
+                  own_keyed ? kids : mids,
+                  own_keyed ? mrows : krows,
+                  own_keyed ? nullptr : kscore,
+                  a.out_u32,
+                  a.out_u64,
+                  a.status};
+    void* tok = a.prof_stage >= 0 ? prof_begin(a.prof_stage, s) : nullptr;
+    const cudaError_t ge = launch_grouped_subset(g, s);
+    prof_end(tok);
+    IG_P_TRY(ge);
+    // The host vector of items must outlive the copy: wait for it here.
+    IG_P_TRY(cudaStreamSynchronize(s));
+  }
+#undef IG_P_TRY
+  return done(cudaSuccess);
+}
+
+}  // namespace igk

@@ -1,0 +1,408 @@
+// Subset tests on the tensor cores: a 0/1 GEMM with tcgen05 (sm_100 family).
+//
+// Eq. 6 tests every word of p against r.  Counted instead over items l,
+//   D[p, r] = sum_l p_l * (1 - r_l)
+// is the number of items of p missing from r, so p is inside r iff D == 0.
+// That sum is a matrix product of 0/1 matrices: pattern bits against
+// complemented record bits.  The operands are expanded to one FP8 (E4M3)
+// byte per item (1.0 = 0x38) and multiplied by tcgen05.mma kind::f8f6f4 into
+// FP32 accumulators in tensor memory; the counts are at most 64*KT <= 512,
+// exact in FP32, and D == 0 is read straight from the accumulator bits.
+//
+// One CTA owns 128 "own" rows (the A operand, M = 128, resident in shared
+// memory) and streams tiles of N = 128 rows of the other operand (B) through
+// a ring of shared-memory stages filled by 1-D TMA bulk copies.  Warp roles:
+//   warp 0   lane 0 issues the bulk copies (A once, then the B tiles);
+//   warp 1   allocates tensor memory; lane 0 issues the MMAs and commits;
+//   warps 2-5 read the accumulators (tcgen05.ld, one 32-lane quarter each)
+//            and reduce them: any / count / score-weighted sum (Eq. 3, 2, 4).
+// Two accumulator buffers let the epilogue of tile t overlap the MMAs of
+// tile t+1.  Every wait is bounded; on a timeout the CTA records it in the
+// status word, stops issuing work, waits (bounded) for what is in flight and
+// frees its tensor memory.
+//
+// The operands live in global memory already in the shared-memory image the
+// MMA reads (K-major, 128-byte swizzle: 8-row x 128-byte atoms, the 16-byte
+// chunk c of row r stored at chunk c ^ (r mod 8)), so every tile is one
+// contiguous bulk copy.  expand_kernel writes these images from packed rows.
+#include "common.cuh"
+#include "internal.h"
+
+namespace igk {
+
+constexpr int kTcM = 128;          // own rows per CTA (MMA M)
+constexpr int kTcN = 128;          // stream rows per tile (MMA N)
+constexpr int kTcThreads = 192;    // 6 warps
+constexpr uint32_t kTmemCols = 2 * kTcN;
+
+template <int KT>
+struct TcShape {
+  static constexpr int kBytesPerRow = KT * 64;             // one byte per item
+  static constexpr int kKSteps = KT * 64 / 32;             // MMA K = 32 for 8-bit inputs
+  static constexpr uint32_t kABytes = kTcM * kBytesPerRow;
+  static constexpr uint32_t kBBytes = kTcN * kBytesPerRow;
+  static constexpr int kStages = (200 * 1024 - int(kABytes)) / int(kBBytes) > 6
+                                     ? 6
+                                     : (200 * 1024 - int(kABytes)) / int(kBBytes);
+  static constexpr size_t kSmem = 1024 + kABytes + size_t(kStages) * kBBytes + 256;
+};
+
+// ---- operand images ---------------------------------------------------------
+
+// img tile t holds rows [t*R, t*R + R): byte offset of item k of tile row r is
+//   (k / 128) * (R * 128) + r * 128 + (((k % 128) / 16) ^ (r % 8)) * 16 + k % 16.
+// One thread writes one 16-byte chunk.  Rows >= n are zero.
+template <int KT>
+__global__ void expand_kernel(const uint64_t* __restrict__ rows, int64_t n, int stride,
+                              int complement, int R, int64_t ntiles, uint8_t* __restrict__ img) {
+  const int64_t chunks_per_tile = int64_t(R) * KT * 4;
+  const int64_t id = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (id >= ntiles * chunks_per_tile) return;
+  const int64_t tile = id / chunks_per_tile;
+  const int64_t rem = id - tile * chunks_per_tile;
+  const int katom = int(rem / (R * 8));
+  const int rem2 = int(rem - int64_t(katom) * R * 8);
+  const int r = rem2 >> 3, pos = rem2 & 7;
+  const int c = pos ^ (r & 7);
+  const int k0 = katom * 128 + c * 16;
+  const int64_t g = tile * R + r;
+  uint32_t bits = 0;
+  if (g < n) {
+    const int word = k0 >> 6;
+    uint64_t w = word < stride ? rows[g * stride + word] : 0ull;
+    if (complement) w = ~w;
+    bits = uint32_t((w >> (k0 & 63)) & 0xffffu);
+  }
+  uint32_t v[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint32_t x = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) x |= ((bits >> (4 * q + b)) & 1u) ? (0x38u << (8 * b)) : 0u;
+    v[q] = x;
+  }
+  *reinterpret_cast<uint4*>(img + tile * (int64_t(R) * KT * 64) + int64_t(katom) * R * 128 +
+                            r * 128 + pos * 16) = make_uint4(v[0], v[1], v[2], v[3]);
+}
+
+// ---- tcgen05 wrappers ---------------------------------------------------------
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, atoms of
+// 8 rows x 128 bytes stacked 1024 bytes apart (SBO); descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr & 0x3ffffu) >> 4);       // start address
+  d |= uint64_t(1) << 16;                        // leading byte offset (unused here)
+  d |= uint64_t(1024 >> 4) << 32;                // stride byte offset
+  d |= uint64_t(1) << 46;                        // version
+  d |= uint64_t(2) << 61;                        // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f8f6f4: D F32, A and B E4M3, both K-major,
+// N = kTcN, M = kTcM.
+constexpr uint32_t kTcIdesc = (1u << 4) | (0u << 7) | (0u << 10) | (uint32_t(kTcN >> 3) << 17) |
+                              (uint32_t(kTcM >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(kTcIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 32 consecutive accumulator columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+        "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+        "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+        "=r"(v[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ---- the kernel -------------------------------------------------------------
+
+struct TcParams {
+  const uint8_t* a_img;                 // own rows, tiles of kTcM
+  int64_t n_own;
+  const unsigned long long* n_own_dev;  // optional device-side own count
+  const uint8_t* b_img;                 // stream rows, tiles of kTcN
+  int64_t b_tile0;                      // first stream tile of this launch
+  int64_t n_stream;                     // stream rows from tile b_tile0 on
+  int64_t tiles_per_split;
+  const uint64_t* score;                // MODE_SUM: S of stream row j (from b_tile0 * kTcN)
+  uint32_t* out_u32;
+  unsigned long long* out_u64;
+  int* status;
+};
+
+template <int KT, int MODE>
+__global__ void __launch_bounds__(kTcThreads, 1) subset_tc_kernel(TcParams p) {
+  using S = TcShape<KT>;
+  constexpr int STAGES = S::kStages;
+  extern __shared__ uint8_t smem_raw[];
+  const int64_t n_own = p.n_own_dev ? int64_t(*p.n_own_dev) : p.n_own;
+  const int64_t own0 = int64_t(blockIdx.x) * kTcM;
+  if (own0 >= n_own) return;
+  const int64_t t_lo = int64_t(blockIdx.y) * p.tiles_per_split;
+  const int64_t total_tiles = ceil_div(p.n_stream, kTcN);
+  const int64_t t_hi = (t_lo + p.tiles_per_split < total_tiles) ? t_lo + p.tiles_per_split
+                                                                 : total_tiles;
+  const int ntiles = int(t_hi > t_lo ? t_hi - t_lo : 0);
+
+  // 1024-byte aligned carve-up of dynamic shared memory.
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* base = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+  uint8_t* A_s = base;
+  uint8_t* B_s = A_s + S::kABytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(B_s + size_t(STAGES) * S::kBBytes);
+  uint64_t* a_full = bars;
+  uint64_t* full = bars + 1;
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;
+  uint64_t* acc_empty = acc_full + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    mbar_init(a_full, 1);
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(acc_full + b, 1);
+      mbar_init(acc_empty + b, 4);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // Producer: A once, then the B tiles through the ring.
+      mbar_arrive_expect_tx(a_full, S::kABytes);
+      bulk_g2s(A_s, p.a_img + size_t(blockIdx.x) * S::kABytes, S::kABytes, a_full);
+      int issued = 0;
+      for (int t = 0; t < ntiles; ++t) {
+        const int s = t % STAGES;
+        if (!mbar_wait(empty + s, uint32_t(((t / STAGES) & 1) ^ 1), p.status) || *abort_flag) {
+          *abort_flag = 1;
+          break;
+        }
+        mbar_arrive_expect_tx(full + s, S::kBBytes);
+        bulk_g2s(B_s + size_t(s) * S::kBBytes,
+                 p.b_img + size_t(p.b_tile0 + t_lo + t) * S::kBBytes, S::kBBytes, full + s);
+        issued = t + 1;
+      }
+      // Copies must have landed before the CTA may finish.
+      mbar_wait(a_full, 0, p.status);
+      for (int t = (issued > STAGES ? issued - STAGES : 0); t < issued; ++t)
+        if (*abort_flag) mbar_wait(full + (t % STAGES), uint32_t((t / STAGES) & 1), p.status);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer.
+      bool ok = mbar_wait(a_full, 0, p.status);
+      int last = -1;
+      const uint32_t a_base = smem_u32(A_s);
+      for (int t = 0; t < ntiles && ok; ++t) {
+        const int s = t % STAGES, b = t & 1;
+        if (!mbar_wait(full + s, uint32_t((t / STAGES) & 1), p.status) ||
+            !mbar_wait(acc_empty + b, uint32_t(((t >> 1) & 1) ^ 1), p.status) || *abort_flag) {
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t b_base = smem_u32(B_s + size_t(s) * S::kBBytes);
+        const uint32_t d = tmem + uint32_t(b * kTcN);
+#pragma unroll 4
+        for (int k = 0; k < S::kKSteps; ++k) {
+          const uint32_t koff = uint32_t(k >> 2) * (kTcM * 128) + uint32_t(k & 3) * 32;
+          const uint32_t kboff = uint32_t(k >> 2) * (kTcN * 128) + uint32_t(k & 3) * 32;
+          tc_mma(d, sw128_desc(a_base + koff), sw128_desc(b_base + kboff), k > 0 ? 1u : 0u);
+        }
+        tc_commit(empty + s);     // stage reusable once these MMAs are done
+        tc_commit(acc_full + b);  // accumulator b ready for the epilogue
+        last = t;
+      }
+      // MMAs complete in order: once the last commit has arrived, no MMA of
+      // this CTA is still writing tensor memory.
+      if (last >= 0) mbar_wait(acc_full + (last & 1), uint32_t((last >> 1) & 1), p.status);
+    }
+  } else {
+    // Epilogue: warp w reads accumulator lanes 32*(w % 4) .. +32.
+    const int quarter = warp & 3;
+    const int64_t row = own0 + quarter * 32 + lane;
+    const bool valid = row < n_own;
+    bool cov = false;
+    uint32_t cnt = 0;
+    unsigned long long sum = 0;
+    for (int t = 0; t < ntiles; ++t) {
+      const int b = t & 1;
+      bool ok = mbar_wait(acc_full + b, uint32_t((t >> 1) & 1), p.status);
+      if (!__all_sync(0xffffffffu, ok) || *abort_flag) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const int64_t j0 = (t_lo + t) * kTcN;  // first stream row of this tile
+      const int nvalid = int((p.n_stream - j0) < kTcN ? (p.n_stream - j0) : kTcN);
+#pragma unroll 1
+      for (int c = 0; c < kTcN; c += 32) {
+        uint32_t v[32];
+        tmem_ld32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * kTcN + c), v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const bool hit = v[i] == 0u && (c + i) < nvalid;
+          if constexpr (MODE == MODE_ANY) cov |= hit;
+          if constexpr (MODE == MODE_COUNT) cnt += hit ? 1u : 0u;
+          if constexpr (MODE == MODE_SUM) {
+            if (hit) sum += p.score[j0 + c + i];
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty + b);
+    }
+    if (valid) {
+      if constexpr (MODE == MODE_ANY) {
+        if (cov) p.out_u32[row] = 1u;
+      }
+      if constexpr (MODE == MODE_COUNT) {
+        if (cnt) atomicAdd(p.out_u32 + row, cnt);
+      }
+      if constexpr (MODE == MODE_SUM) {
+        if (sum) atomicAdd(p.out_u64 + row, sum);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+// ---- host side --------------------------------------------------------------
+
+template <int KT>
+static cudaError_t expand(const uint64_t* rows, int64_t n, int stride, int complement, int R,
+                          uint8_t* img, cudaStream_t s) {
+  const int64_t ntiles = ceil_div(n, R);
+  const int64_t chunks = ntiles * int64_t(R) * KT * 4;
+  if (chunks == 0) return cudaSuccess;
+  expand_kernel<KT><<<unsigned(ceil_div(chunks, 256)), 256, 0, s>>>(rows, n, stride, complement,
+                                                                    R, ntiles, img);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <int KT, int MODE>
+static cudaError_t run_tc(const TcArgs& a, cudaStream_t s) {
+  using S = TcShape<KT>;
+  const int64_t gx = ceil_div(a.n_own, kTcM);
+  const int64_t stream_tiles = ceil_div(a.n_stream, kTcN);
+  const int64_t target = int64_t(num_sms()) * 2;
+  int64_t splits = ceil_div(target, gx);
+  if (splits > stream_tiles) splits = stream_tiles;
+  if (splits > 65535) splits = 65535;
+  if (splits < 1) splits = 1;
+  const int64_t per = ceil_div(stream_tiles, splits);
+  splits = ceil_div(stream_tiles, per);
+  TcParams p{a.a_img, a.n_own, a.n_own_dev, a.b_img, a.b_tile0, a.n_stream, per,
+             a.score, a.out_u32, a.out_u64, a.status};
+  cudaError_t e = cudaFuncSetAttribute(subset_tc_kernel<KT, MODE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::kSmem));
+  if (e != cudaSuccess) return e;
+  dim3 grid{unsigned(gx), unsigned(splits), 1u};
+  subset_tc_kernel<KT, MODE><<<grid, kTcThreads, S::kSmem, s>>>(p);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+bool tc_supported(int KT) { return KT == 2 || KT == 4 || KT == 8; }
+
+size_t tc_image_bytes(int64_t n, int KT, bool own_side) {
+  const int R = own_side ? kTcM : kTcN;
+  return size_t(ceil_div(n, R)) * R * KT * 64;
+}
+
+cudaError_t launch_expand(const uint64_t* rows, int64_t n, int stride, int KT, bool complement,
+                          bool own_side, uint8_t* img, cudaStream_t s) {
+  const int R = own_side ? kTcM : kTcN;
+  switch (KT) {
+    case 2: return expand<2>(rows, n, stride, complement ? 1 : 0, R, img, s);
+    case 4: return expand<4>(rows, n, stride, complement ? 1 : 0, R, img, s);
+    case 8: return expand<8>(rows, n, stride, complement ? 1 : 0, R, img, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_subset_tc(const TcArgs& a, cudaStream_t s) {
+  if (a.n_own == 0 || a.n_stream == 0) return cudaSuccess;
+#define IG_TC_CASE(KTV)                                                        \
+  case KTV:                                                                    \
+    switch (a.mode) {                                                          \
+      case MODE_ANY: return run_tc<KTV, MODE_ANY>(a, s);                       \
+      case MODE_COUNT: return run_tc<KTV, MODE_COUNT>(a, s);                   \
+      case MODE_SUM: return run_tc<KTV, MODE_SUM>(a, s);                       \
+    }                                                                          \
+    break;
+  switch (a.KT) {
+    IG_TC_CASE(2)
+    IG_TC_CASE(4)
+    IG_TC_CASE(8)
+  }
+#undef IG_TC_CASE
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace igk

@@ -46,8 +46,13 @@ def host(t, dtype):
     return t.cpu().numpy().view(dtype)
 
 
-def gpu_fit(rows, labels, r=None):
-    return ig.ig_fit(dev(rows), dev(np.asarray(labels, np.uint8)), r=r)
+# 1 = integer-pipe (LOP3) kernel, 2 = tensor-core (tcgen05) kernel,
+# 3 = item-index pruning (exact)
+KERNELS = [1, 2, 3]
+
+
+def gpu_fit(rows, labels, r=None, kernel=0):
+    return ig.ig_fit(dev(rows), dev(np.asarray(labels, np.uint8)), r=r, subset_kernel=kernel)
 
 
 def assert_model_equal(m, om):
@@ -60,6 +65,15 @@ def assert_model_equal(m, om):
         assert np.array_equal(f, om.support[cls]), f"class {cls}: supports differ"
         assert np.array_equal(s, om.score[cls]), f"class {cls}: scores differ"
         assert info["n_candidates"][cls] == om.n_candidates[cls]
+
+
+_ORACLE_CACHE = {}
+
+
+def _oracle_fit_cached(key, rows, labels):
+    if key not in _ORACLE_CACHE:
+        _ORACLE_CACHE[key] = oracle.fit(rows, labels)
+    return _ORACLE_CACHE[key]
 
 
 def assert_scores_equal(m, om, rows):
@@ -99,8 +113,9 @@ def test_encode_rejects_out_of_range_code():
 
 # ---- fit and score on brute-force and random cases --------------------------
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("seed", range(10))
-def test_fit_against_brute_force(seed):
+def test_fit_against_brute_force(seed, kernel):
     rng = np.random.default_rng(100 + seed)
     L = 12
     K, positions = (1, list(range(L))) if seed % 2 else (2, list(range(58, 58 + L)))
@@ -110,7 +125,7 @@ def test_fit_against_brute_force(seed):
     want = brute.fit(XA, XN, L)
     rows = np.concatenate([brute.pack(XA, positions, K), brute.pack(XN, positions, K)])
     labels = np.array([1] * len(XA) + [0] * len(XN), np.uint8)
-    m = gpu_fit(rows, labels)
+    m = gpu_fit(rows, labels, kernel=kernel)
     for cls in (0, 1):
         words, f, s = m.patterns(cls)
         B, P, ff, S = want[cls]
@@ -138,11 +153,14 @@ RANDOM_CASES = [
     (600, 100, 90, "three_quarters", 0),
     (1024, 150, 140, "three_quarters", 20),
     (1000, 70, 80, "three_quarters", 0),
+    (256, 700, 650, "three_quarters", 0),    # > 512 per class: last coherence window
+    (500, 600, 900, "three_quarters", 30),
 ]
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("case", RANDOM_CASES, ids=lambda c: f"L{c[0]}-{c[1]}x{c[2]}")
-def test_fit_and_score_random(case):
+def test_fit_and_score_random(case, kernel):
     L, na, nn, density, pool = case
     rng = np.random.default_rng(L * 7 + na)
     if pool:
@@ -152,8 +170,8 @@ def test_fit_and_score_random(case):
         rows = igdata.random_words(rng, na + nn, L, density)
     labels = np.zeros(na + nn, np.uint8)
     labels[rng.permutation(na + nn)[:na]] = 1
-    m = gpu_fit(rows, labels)
-    om = oracle.fit(rows, labels)
+    m = gpu_fit(rows, labels, kernel=kernel)
+    om = _oracle_fit_cached(case, rows, labels)
     assert_model_equal(m, om)
     test = igdata.random_words(rng, 97, L, "three_quarters")
     assert_scores_equal(m, om, np.concatenate([test, rows]))
@@ -230,24 +248,27 @@ def test_hash_table_growth():
 
 # ---- seeded workloads -------------------------------------------------------
 
-def _workload_fit(w, r=None):
+def _workload_fit(w, r=None, kernel=0):
     d_codes = dev(w.train_codes)
     rows = ig.ig_encode(d_codes, w.cards)
-    m = ig.ig_fit(rows, dev(w.train_labels), r=r)
+    m = ig.ig_fit(rows, dev(w.train_labels), r=r, subset_kernel=kernel)
+    assert m.info()["subset_kernel"] == {0: 3, 1: 1, 2: 2, 3: 3}[kernel]
     return m, oracle.encode(w.train_codes, w.cards)
 
 
-def test_tiny_workload_parity():
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_tiny_workload_parity(kernel):
     w = igdata.tiny()
-    m, rows = _workload_fit(w)
+    m, rows = _workload_fit(w, kernel=kernel)
     om = oracle.fit(rows, w.train_labels)
     assert_model_equal(m, om)
     assert_scores_equal(m, om, oracle.encode(w.test_codes, w.cards))
 
 
-def test_tiny_workload_regulation3():
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_tiny_workload_regulation3(kernel):
     w = igdata.tiny()
-    m, rows = _workload_fit(w, r=0.568)
+    m, rows = _workload_fit(w, r=0.568, kernel=kernel)
     om = oracle.fit(rows, w.train_labels, r=0.568)
     mu, sigma, r, thr = m.info()["reg3"]
     assert (mu, sigma, r, thr) == om.reg3          # same fp64 formula and order
@@ -255,10 +276,16 @@ def test_tiny_workload_regulation3():
 
 
 @pytest.fixture(scope="module")
-def nsl15k():
+def nsl15k_oracle():
     w = igdata.nsl15k()
-    m, rows = _workload_fit(w)
-    om = oracle.fit(rows, w.train_labels)
+    rows = oracle.encode(w.train_codes, w.cards)
+    return w, oracle.fit(rows, w.train_labels)
+
+
+@pytest.fixture(scope="module", params=KERNELS, ids=["lop3", "tcgen05", "index"])
+def nsl15k(request, nsl15k_oracle):
+    w, om = nsl15k_oracle
+    m, _ = _workload_fit(w, kernel=request.param)
     return w, m, om
 
 
@@ -308,6 +335,7 @@ def test_save_load_roundtrip(nsl15k, tmp_path):
 def test_nsl148k_parity_sampled_scores():
     # Full-size fit compared in full; scores on a seeded sample of the
     # 133,200 test records (the oracle's evidence loop is the slow part).
+    # Library default kernel, as the benchmark runs it.
     w = igdata.nsl148k()
     m, rows = _workload_fit(w)
     om = oracle.fit(rows, w.train_labels)
