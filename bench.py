@@ -253,7 +253,12 @@ def run_ours(args):
         "patterns": {"attack": info["n_patterns"][1], "normal": info["n_patterns"][0],
                      "candidates": list(info["n_candidates"][::-1])},
         "subset_kernel": {1: "lop3", 2: "tcgen05", 3: "item-index"}[info["subset_kernel"]],
-        "coherence_tests_executed": sum(info["coherence_tests"]),
+        "executed_tests_per_step": {
+            "coherence": sum(info["coherence_tests"]),
+            "support": sum(info["support_tests"]),
+            "evidence": stages.get("evidence_idx", (0, 0, 0))[2] // max(1, args.steps)
+                        + stages.get("evidence_tc", (0, 0, 0))[2] // max(1, args.steps)
+                        + stages.get("evidence", (0, 0, 0))[2] // max(1, args.steps)},
         "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in stages.items()
                                if v[1]},
         "gpu_launches": int(launches),

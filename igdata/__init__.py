@@ -243,9 +243,9 @@ def random_words(rng: np.random.Generator, n: int, n_items: int,
                  density: str = "half") -> np.ndarray:
     """Arbitrary (not one-hot) itemsets as uint64[n, ceil(n_items/64)].
 
-    Uniform random words, thinned ("quarter": AND of two draws) or thickened
-    ("three_quarters": OR of two draws); every bit at a position >= n_items
-    is cleared.  Used for small adversarial cases that the one-hot
+    Uniform random words, thinned ("quarter": AND of two draws, "eighth":
+    AND of three) or thickened ("three_quarters": OR of two draws); every bit
+    at a position >= n_items is cleared.  Used for small adversarial cases that the one-hot
     generators cannot produce.
     """
     K = (n_items + 63) // 64
@@ -256,6 +256,9 @@ def random_words(rng: np.random.Generator, n: int, n_items: int,
 
     w = draw()
     if density == "quarter":
+        w &= draw()
+    elif density == "eighth":
+        w &= draw()
         w &= draw()
     elif density == "three_quarters":
         w |= draw()

@@ -152,6 +152,13 @@ struct DevBuf {
 // True for CUDA device (or managed) memory; the calling thread's current
 // device is then switched to the device that owns it, so that every later
 // allocation and launch of the call happens there.
+// Owns a record index for the duration of a call.
+struct IndexHolder {
+  igk::RecordIndex idx;
+  cudaStream_t s = nullptr;
+  ~IndexHolder() { igk::release_record_index(&idx, s); }
+};
+
 bool is_device_pointer(const void* p) {
   if (!p) return false;
   cudaPointerAttributes attr;
@@ -510,12 +517,24 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
   const bool pruned = (prm.subset_kernel == 0 || prm.subset_kernel == 3) && KT >= 2;
   const bool tc = prm.subset_kernel != 1 && igk::tc_supported(KT);
   m->subset_kernel = pruned ? 3 : (tc ? 2 : 1);
-  // Complemented images of both classes' records: the stream operand of the
-  // other class's coherence and of this class's support, and the own operand
-  // of the Regulation 3 evidence.
+  // Item indexes of both classes' records: used by the other class's
+  // coherence, this class's support and (normal class) Regulation 3.
+  IndexHolder rec_idx[2];
+  if (pruned) {
+    for (int c = 0; c < 2; ++c) {
+      rec_idx[c].s = s;
+      IG_CUDA(igk::build_record_index(X[c].p, nc[c], KT, K, KT, 0.25, &rec_idx[c].idx, s),
+              "ig_fit: record index");
+    }
+  }
+  // Complemented images of both classes' records for the tensor cores: the
+  // stream operand of the other class's coherence and of this class's
+  // support, and the own operand of the Regulation 3 evidence.  With the
+  // item index they are only needed where an index could not be used.
   DevBuf<uint8_t> rec_img[2];
   if (tc) {
     for (int c = 0; c < 2; ++c) {
+      if (pruned && rec_idx[c].idx.usable) continue;
       IG_CUDA(rec_img[c].alloc(igk::tc_image_bytes(nc[c], KT, false), s), "ig_fit: images");
       ProfScope ps(S_EXPAND, s);
       IG_CUDA(igk::launch_expand(X[c].p, nc[c], KT, KT, true, false, rec_img[c].p, s),
@@ -578,30 +597,28 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
           IG_CUDA(cudaStreamSynchronize(s), "ig_fit");
           n_cur = int64_t(h_pinned[3]);
         }
-        int64_t t = 0;
-        igk::PrunedArgs a;
-        a.prof_stage = S_COHERENCE_IDX;
-        a.mode = igk::MODE_ANY;
-        a.K = K;
-        a.KT = KT;
-        a.keyed = cur;
-        a.n_keyed = n_cur;
-        a.keyed_stride = KT;
-        a.multi = X[o].p + lo * KT;
-        a.n_multi = hi - lo;
-        a.multi_stride = KT;
-        a.keyed_score = nullptr;
-        a.out_u32 = covered.p;
-        a.out_u64 = nullptr;
-        a.status = d_status.p;
-        a.tests_out = &t;
-        IG_CUDA(igk::pruned_subset(a, s), "ig_fit: coherence");
+        int64_t t = -1;
+        if (rec_idx[o].idx.usable) {
+          igk::IndexedArgs a;
+          a.mode = igk::MODE_ANY;
+          a.index = &rec_idx[o].idx;
+          a.keyed = cur;
+          a.n_keyed = n_cur;
+          a.keyed_stride = KT;
+          a.keyed_score = nullptr;
+          a.out_u32 = covered.p;
+          a.out_u64 = nullptr;
+          a.status = d_status.p;
+          a.tests_out = &t;
+          a.prof_stage = S_COHERENCE_IDX;
+          IG_CUDA(igk::indexed_subset(a, s), "ig_fit: coherence");
+        }
         if (t >= 0) {
           round_tests[rounds] = t;
           done_round = true;
         }
       }
-      if (!done_round && (tc_round || (pruned_round && tc && lo % 128 == 0))) {
+      if (!done_round && rec_img[o].p && (tc_round || (pruned_round && tc && lo % 128 == 0))) {
         DevBuf<uint8_t> own_img;
         IG_CUDA(own_img.alloc(igk::tc_image_bytes(U, KT, true), s), "ig_fit: images");
         {
@@ -672,24 +689,22 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
     bool support_done = false;
     m->sup_tests[c] = P * nc[c];
     if (pruned) {
-      int64_t t = 0;
-      igk::PrunedArgs a;
-      a.prof_stage = S_SUPPORT_IDX;
-      a.mode = igk::MODE_COUNT;
-      a.K = K;
-      a.KT = KT;
-      a.keyed = m->words_kt[c];
-      a.n_keyed = P;
-      a.keyed_stride = KT;
-      a.multi = X[c].p;
-      a.n_multi = nc[c];
-      a.multi_stride = KT;
-      a.keyed_score = nullptr;
-      a.out_u32 = m->support[c];
-      a.out_u64 = nullptr;
-      a.status = d_status.p;
-      a.tests_out = &t;
-      IG_CUDA(igk::pruned_subset(a, s), "ig_fit: support");
+      int64_t t = -1;
+      if (rec_idx[c].idx.usable) {
+        igk::IndexedArgs a;
+        a.mode = igk::MODE_COUNT;
+        a.index = &rec_idx[c].idx;
+        a.keyed = m->words_kt[c];
+        a.n_keyed = P;
+        a.keyed_stride = KT;
+        a.keyed_score = nullptr;
+        a.out_u32 = m->support[c];
+        a.out_u64 = nullptr;
+        a.status = d_status.p;
+        a.tests_out = &t;
+        a.prof_stage = S_SUPPORT_IDX;
+        IG_CUDA(igk::indexed_subset(a, s), "ig_fit: support");
+      }
       if (t >= 0) {
         support_done = true;
         m->sup_tests[c] = t;
@@ -697,7 +712,7 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
       }
     }
     if (support_done) {
-    } else if (tc) {
+    } else if (tc && rec_img[c].p) {
       DevBuf<uint8_t> own_img;
       IG_CUDA(own_img.alloc(igk::tc_image_bytes(P, KT, true), s), "ig_fit: images");
       {
@@ -718,7 +733,7 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
                         m->support[c], nullptr, d_status.p};
       IG_CUDA(igk::launch_subset(a, s), "ig_fit: support");
     }
-    if (tc && P) {  // stream image of P^c for the evidence kernels
+    if (tc && P && !pruned) {  // stream image of P^c for the evidence kernels
       IG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&m->pat_img[c]),
                               igk::tc_image_bytes(P, KT, false), s),
               "ig_fit: images");
@@ -756,27 +771,23 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
     IG_CUDA(d_n.alloc(size_t(nc[0]), s), "ig_fit");
     IG_CUDA(cudaMemsetAsync(d_n.p, 0, sizeof(unsigned long long) * nc[0], s), "ig_fit");
     int64_t t_idx = -1;
-    if (pruned && m->n_pat[0]) {
-      igk::PrunedArgs a;
-      a.prof_stage = S_EVIDENCE_IDX;
+    if (pruned && m->n_pat[0] && rec_idx[0].idx.usable) {
+      igk::IndexedArgs a;
       a.mode = igk::MODE_SUM;
-      a.K = K;
-      a.KT = KT;
+      a.index = &rec_idx[0].idx;
       a.keyed = m->words_kt[0];
       a.n_keyed = m->n_pat[0];
       a.keyed_stride = KT;
-      a.multi = X[0].p;
-      a.n_multi = nc[0];
-      a.multi_stride = KT;
       a.keyed_score = m->score[0];
       a.out_u32 = nullptr;
       a.out_u64 = d_n.p;
       a.status = d_status.p;
       a.tests_out = &t_idx;
-      IG_CUDA(igk::pruned_subset(a, s), "ig_fit: Regulation 3 evidence");
+      a.prof_stage = S_EVIDENCE_IDX;
+      IG_CUDA(igk::indexed_subset(a, s), "ig_fit: Regulation 3 evidence");
     }
     if (t_idx >= 0) {
-    } else if (tc && m->n_pat[0]) {
+    } else if (tc && m->n_pat[0] && rec_img[0].p && m->pat_img[0]) {
       ProfScope ps(S_EVIDENCE_TC, s);
       igk::TcArgs a{igk::MODE_SUM, KT,           rec_img[0].p, nc[0],   nullptr, m->pat_img[0],
                     0,             m->n_pat[0],  m->score[0],  nullptr, d_n.p,   d_status.p};
@@ -890,32 +901,33 @@ int ig_score(const ig_model* m, const uint64_t* rows, int64_t n_rows, int64_t* A
   const bool pruned = m->subset_kernel == 3;
   bool tc = m->subset_kernel >= 2 && igk::tc_supported(m->KT) && m->pat_img[0] && m->pat_img[1];
   bool done[2] = {false, false};
-  if (pruned) {
+  IndexHolder test_idx;
+  test_idx.s = s;
+  if (pruned)
+    IG_CUDA(igk::build_record_index(in.d, n_rows, m->K, m->K, m->KT, 0.25, &test_idx.idx, s),
+            "ig_score: record index");
+  if (pruned && test_idx.idx.usable) {
     for (int c = 1; c >= 0; --c) {
       if (m->n_pat[c] == 0) {
         done[c] = true;
         continue;
       }
       int64_t t = 0;
-      igk::PrunedArgs a;
-      a.prof_stage = S_EVIDENCE_IDX;
+      igk::IndexedArgs a;
       a.mode = igk::MODE_SUM;
-      a.K = m->K;
-      a.KT = m->KT;
+      a.index = &test_idx.idx;
       a.keyed = m->words_kt[c];
       a.n_keyed = m->n_pat[c];
       a.keyed_stride = m->KT;
-      a.multi = in.d;
-      a.n_multi = n_rows;
-      a.multi_stride = m->K;
       a.keyed_score = m->score[c];
       a.out_u32 = nullptr;
       a.out_u64 = c == 1 ? A.d : N.d;
       a.status = d_status.p;
       a.tests_out = &t;
-      IG_CUDA(igk::pruned_subset(a, s), "ig_score: evidence");
-      done[c] = t >= 0;
-      if (done[c]) igk::prof_add_work(S_EVIDENCE_IDX, t);
+      a.prof_stage = S_EVIDENCE_IDX;
+      IG_CUDA(igk::indexed_subset(a, s), "ig_score: evidence");
+      done[c] = true;
+      igk::prof_add_work(S_EVIDENCE_IDX, t);
     }
   }
   if (done[0] && done[1]) tc = false;

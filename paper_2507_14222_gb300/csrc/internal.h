@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace igk {
 
 // Rows of every internally staged row array are allocated in multiples of
@@ -162,34 +164,46 @@ struct GroupedArgs {
 };
 cudaError_t launch_grouped_subset(const GroupedArgs& a, cudaStream_t s);
 
+// Record index ("multi" side): every record filed under each item it
+// holds, with the item counts.  Built once, used by any number of indexed
+// subset tests.  Not built (usable = false) when the records fill more than
+// max_fill of all item slots: then nearly every group holds nearly every
+// record and the dense kernels are faster.  Synchronizes the stream.
+struct RecordIndex {
+  int K = 0, KT = 0, L = 0;
+  int64_t n_rows = 0, n_copies = 0;
+  bool usable = false;
+  uint64_t* rows = nullptr;   // grouped copies, stride KT (+256 rows of padding)
+  uint32_t* ids = nullptr;    // original record of each copy
+  uint32_t* small = nullptr;  // freq[L] | off[L+1] | cursor[L]
+  uint32_t* freq = nullptr;
+  uint32_t* off = nullptr;
+  std::vector<uint32_t> h_off;
+};
+cudaError_t build_record_index(const uint64_t* rows, int64_t n, int stride, int K, int KT,
+                               double max_fill, RecordIndex* idx, cudaStream_t s);
+void release_record_index(RecordIndex* idx, cudaStream_t s);
+
 // A subset test of "keyed" rows (patterns: MODE_ANY / MODE_COUNT own rows,
-// MODE_SUM stream rows) against "multi" rows (records), restricted to the
-// pairs that share the pattern's key item.  Outputs are indexed like the
-// dense kernel's: by pattern for ANY / COUNT, by record for SUM.  Requires
-// KT >= 2.  Synchronizes the stream.
-struct PrunedArgs {
+// MODE_SUM stream rows) against the records of an index, restricted to the
+// pairs that share the pattern's key item (its item held by the fewest
+// records).  Outputs are indexed like the dense kernels': by pattern for
+// ANY / COUNT, by record for SUM.  Requires KT >= 2.  Synchronizes the
+// stream once.
+struct IndexedArgs {
   int mode;
-  int K;   // words holding items (items 0 .. 64K-1)
-  int KT;  // padded words of the kernels (2, 4, 8 or 16)
+  const RecordIndex* index;
   const uint64_t* keyed;
   int64_t n_keyed;
   int keyed_stride;
-  const uint64_t* multi;
-  int64_t n_multi;
-  int multi_stride;
   const uint64_t* keyed_score;  // MODE_SUM: S of each keyed row
   uint32_t* out_u32;
   unsigned long long* out_u64;
   int* status;
-  int64_t* tests_out;  // subset tests executed; -1 if the index was not used
-  // The index is not built (tests_out = -1, nothing written) when the
-  // records hold more than this fraction of all item slots on average:
-  // then nearly every group holds nearly every record and the dense kernels
-  // are faster.
-  double max_fill = 0.25;
+  int64_t* tests_out;   // subset tests executed
   int prof_stage = -1;  // stage under which the grouped kernel is timed
 };
-cudaError_t pruned_subset(const PrunedArgs& a, cudaStream_t s);
+cudaError_t indexed_subset(const IndexedArgs& a, cudaStream_t s);
 
 // Keeps the rows whose flag is zero: out gets them (stride KT), out_count
 // the number kept (must start at 0).  With n_dev given, the row count is

@@ -72,22 +72,48 @@ __global__ void small_scan_kernel(const uint32_t* __restrict__ cnt, int len,
   if (threadIdx.x == 1023) off[len] = part[1023];
 }
 
-// Copies row i into the group of every item it contains.
-__global__ void multi_scatter_kernel(const uint64_t* __restrict__ rows, int64_t n, int stride,
-                                     int K, int KT, const uint32_t* __restrict__ off,
-                                     uint32_t* __restrict__ cursor, uint64_t* __restrict__ out,
-                                     uint32_t* __restrict__ ids) {
+// Copies row i into the group of every item it contains.  A block first
+// counts its copies per item in shared memory, reserves one range per item
+// in the group with a single global atomic, then places its copies with
+// shared-memory atomics only (the order inside a group does not matter).
+constexpr int kScatterThreads = 256;
+
+__global__ void __launch_bounds__(kScatterThreads)
+    multi_scatter_kernel(const uint64_t* __restrict__ rows, int64_t n, int stride, int K, int KT,
+                         int L, const uint32_t* __restrict__ off, uint32_t* __restrict__ cursor,
+                         uint64_t* __restrict__ out, uint32_t* __restrict__ ids) {
+  extern __shared__ uint32_t sh[];
+  uint32_t* cnt = sh;       // [L]
+  uint32_t* base = sh + L;  // [L]
+  for (int l = threadIdx.x; l < L; l += blockDim.x) cnt[l] = 0;
+  __syncthreads();
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const bool valid = i < n;
+  for (int k = 0; valid && k < K; ++k) {
+    uint64_t x = rows[i * stride + k];
+    while (x) {
+      const int b = __ffsll(static_cast<long long>(x)) - 1;
+      x &= x - 1;
+      atomicAdd(&cnt[k * 64 + b], 1u);
+    }
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < L; l += blockDim.x) {
+    const uint32_t c = cnt[l];
+    base[l] = c ? off[l] + atomicAdd(cursor + l, c) : 0u;
+    cnt[l] = 0;
+  }
+  __syncthreads();
+  if (!valid) return;
   uint64_t w[IG_MAX_KT_WORDS];
-  for (int k = 0; k < KT; ++k) w[k] = k < K ? rows[i * stride + k] : 0ull;
+  for (int q = 0; q < KT; ++q) w[q] = q < K ? rows[i * stride + q] : 0ull;
   for (int k = 0; k < K; ++k) {
     uint64_t x = w[k];
     while (x) {
       const int b = __ffsll(static_cast<long long>(x)) - 1;
       x &= x - 1;
       const int l = k * 64 + b;
-      const uint32_t pos = off[l] + atomicAdd(cursor + l, 1u);
+      const uint32_t pos = base[l] + atomicAdd(&cnt[l], 1u);
       for (int q = 0; q < KT; ++q) out[int64_t(pos) * KT + q] = w[q];
       ids[pos] = uint32_t(i);
     }
@@ -121,17 +147,31 @@ __global__ void key_item_kernel(const uint64_t* __restrict__ rows, int64_t n, in
   atomicAdd(kcount + best_l, 1u);
 }
 
-__global__ void keyed_scatter_kernel(const uint64_t* __restrict__ rows, int64_t n, int stride,
-                                     int K, int KT, const uint32_t* __restrict__ key,
-                                     const uint32_t* __restrict__ off,
-                                     uint32_t* __restrict__ cursor, uint64_t* __restrict__ out,
-                                     uint32_t* __restrict__ ids,
-                                     const uint64_t* __restrict__ payload,
-                                     uint64_t* __restrict__ payload_out) {
+// Files row i under its key (block-aggregated like multi_scatter_kernel).
+__global__ void __launch_bounds__(kScatterThreads)
+    keyed_scatter_kernel(const uint64_t* __restrict__ rows, int64_t n, int stride, int K, int KT,
+                         int groups, const uint32_t* __restrict__ key,
+                         const uint32_t* __restrict__ off, uint32_t* __restrict__ cursor,
+                         uint64_t* __restrict__ out, uint32_t* __restrict__ ids,
+                         const uint64_t* __restrict__ payload, uint64_t* __restrict__ payload_out) {
+  extern __shared__ uint32_t sh[];
+  uint32_t* cnt = sh;            // [groups]
+  uint32_t* base = sh + groups;  // [groups]
+  for (int l = threadIdx.x; l < groups; l += blockDim.x) cnt[l] = 0;
+  __syncthreads();
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint32_t l = key[i];
-  const uint32_t pos = off[l] + atomicAdd(cursor + l, 1u);
+  const bool valid = i < n;
+  const uint32_t l = valid ? key[i] : 0u;
+  if (valid) atomicAdd(&cnt[l], 1u);
+  __syncthreads();
+  for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+    const uint32_t c = cnt[g];
+    base[g] = c ? off[g] + atomicAdd(cursor + g, c) : 0u;
+    cnt[g] = 0;
+  }
+  __syncthreads();
+  if (!valid) return;
+  const uint32_t pos = base[l] + atomicAdd(&cnt[l], 1u);
   for (int q = 0; q < KT; ++q) out[int64_t(pos) * KT + q] = q < K ? rows[i * stride + q] : 0ull;
   ids[pos] = uint32_t(i);
   if (payload) payload_out[pos] = payload[i];
@@ -306,11 +346,11 @@ cudaError_t launch_small_scan(const uint32_t* cnt, int len, uint32_t* off, cudaS
 }
 
 cudaError_t launch_multi_scatter(const uint64_t* rows, int64_t n, int stride, int K, int KT,
-                                 const uint32_t* off, uint32_t* cursor, uint64_t* out,
+                                 int L, const uint32_t* off, uint32_t* cursor, uint64_t* out,
                                  uint32_t* ids, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  multi_scatter_kernel<<<unsigned(ceil_div(n, 256)), 256, 0, s>>>(rows, n, stride, K, KT, off,
-                                                                  cursor, out, ids);
+  multi_scatter_kernel<<<unsigned(ceil_div(n, kScatterThreads)), kScatterThreads,
+                         size_t(2) * L * 4, s>>>(rows, n, stride, K, KT, L, off, cursor, out, ids);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -326,12 +366,13 @@ cudaError_t launch_key_item(const uint64_t* rows, int64_t n, int stride, int K, 
 }
 
 cudaError_t launch_keyed_scatter(const uint64_t* rows, int64_t n, int stride, int K, int KT,
-                                 const uint32_t* key, const uint32_t* off, uint32_t* cursor,
-                                 uint64_t* out, uint32_t* ids, const uint64_t* payload,
-                                 uint64_t* payload_out, cudaStream_t s) {
+                                 int groups, const uint32_t* key, const uint32_t* off,
+                                 uint32_t* cursor, uint64_t* out, uint32_t* ids,
+                                 const uint64_t* payload, uint64_t* payload_out, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  keyed_scatter_kernel<<<unsigned(ceil_div(n, 256)), 256, 0, s>>>(
-      rows, n, stride, K, KT, key, off, cursor, out, ids, payload, payload_out);
+  keyed_scatter_kernel<<<unsigned(ceil_div(n, kScatterThreads)), kScatterThreads,
+                         size_t(2) * groups * 4, s>>>(rows, n, stride, K, KT, groups, key, off,
+                                                      cursor, out, ids, payload, payload_out);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -406,13 +447,79 @@ void build_work_items(const uint32_t* own_off, const uint32_t* str_off, int grou
   }
 }
 
-// One pruned subset test (see the top of this file): builds both sides'
-// groups, reads the group sizes back (the one synchronisation), and runs the
-// grouped kernel over blocks of about equal work.
-cudaError_t pruned_subset(const PrunedArgs& a, cudaStream_t s) {
+// ---- record index -------------------------------------------------------------
+
+void release_record_index(RecordIndex* idx, cudaStream_t s) {
+  for (void* p : {static_cast<void*>(idx->rows), static_cast<void*>(idx->ids),
+                  static_cast<void*>(idx->small)})
+    if (p) cudaFreeAsync(p, s);
+  idx->rows = nullptr;
+  idx->ids = nullptr;
+  idx->small = nullptr;
+  idx->usable = false;
+}
+
+cudaError_t build_record_index(const uint64_t* rows, int64_t n, int stride, int K, int KT,
+                               double max_fill, RecordIndex* idx, cudaStream_t s) {
+  *idx = RecordIndex();
+  idx->K = K;
+  idx->KT = KT;
+  idx->L = 64 * K;
+  idx->n_rows = n;
+  const int L = idx->L;
+  cudaError_t e;
+#define IG_I_TRY(x)                  \
+  if ((e = (x)) != cudaSuccess) {     \
+    release_record_index(idx, s);    \
+    return e;                        \
+  }
+  // freq[L], off[L+1], cursor[L] in one allocation.
+  IG_I_TRY(cudaMallocAsync(reinterpret_cast<void**>(&idx->small), size_t(3 * L + 1) * 4, s));
+  idx->freq = idx->small;
+  idx->off = idx->freq + L;
+  uint32_t* cursor = idx->off + (L + 1);
+  IG_I_TRY(cudaMemsetAsync(idx->small, 0, size_t(3 * L + 1) * 4, s));
+  if (n > 0) {
+    void* tok = prof_begin(kStageIndexBuild, s);
+    IG_I_TRY(launch_item_histogram(rows, n, stride, K, L, idx->freq, s));
+    IG_I_TRY(launch_small_scan(idx->freq, L, idx->off, s));
+    prof_end(tok);
+  }
+  idx->h_off.assign(L + 1, 0u);
+  IG_I_TRY(cudaMemcpyAsync(idx->h_off.data(), idx->off, (L + 1) * 4, cudaMemcpyDeviceToHost, s));
+  IG_I_TRY(cudaStreamSynchronize(s));
+  idx->n_copies = idx->h_off[L];
+  idx->usable = n > 0 && double(idx->n_copies) <= max_fill * double(n) * double(L);
+  if (!idx->usable) return cudaSuccess;
+  // Grouped copies, padded by one stream tile so whole-tile copies stay in bounds.
+  IG_I_TRY(cudaMallocAsync(reinterpret_cast<void**>(&idx->rows),
+                           size_t(idx->n_copies + 256) * KT * 8, s));
+  IG_I_TRY(cudaMallocAsync(reinterpret_cast<void**>(&idx->ids), size_t(idx->n_copies) * 4, s));
+  void* tok = prof_begin(kStageIndexBuild, s);
+  IG_I_TRY(launch_multi_scatter(rows, n, stride, K, KT, L, idx->off, cursor, idx->rows, idx->ids,
+                                s));
+  prof_end(tok);
+#undef IG_I_TRY
+  return cudaSuccess;
+}
+
+namespace {
+// Pinned staging for work lists: reused once the copy out of it (recorded
+// by `done`) has finished.
+struct Staging {
+  WorkItem* buf = nullptr;
+  size_t cap = 0;
+  cudaEvent_t done = nullptr;
+};
+thread_local Staging g_staging;
+}  // namespace
+
+cudaError_t indexed_subset(const IndexedArgs& a, cudaStream_t s) {
   *a.tests_out = 0;
-  if (a.n_keyed == 0 || a.n_multi == 0) return cudaSuccess;
-  const int L = 64 * a.K, KT = a.KT;
+  const RecordIndex& idx = *a.index;
+  if (a.n_keyed == 0 || idx.n_rows == 0) return cudaSuccess;
+  const int L = idx.L, KT = idx.KT, K = idx.K;
+  const int groups = L + 1;
   cudaError_t e;
   std::vector<void*> bufs;
   auto alloc = [&](void** p, size_t bytes) {
@@ -426,50 +533,30 @@ cudaError_t pruned_subset(const PrunedArgs& a, cudaStream_t s) {
   };
 #define IG_P_TRY(x) \
   if ((e = (x)) != cudaSuccess) return done(e);
-  // Small per-item arrays in one allocation: freq, kcount, moff, koff, cursors.
-  uint32_t* small = nullptr;
-  const size_t nsmall = size_t(L) + (L + 1) + (L + 1) + (L + 2) + (L + 1) + (L + 1);
-  IG_P_TRY(alloc(reinterpret_cast<void**>(&small), nsmall * 4));
-  uint32_t* freq = small;
-  uint32_t* kcount = freq + L;
-  uint32_t* moff = kcount + (L + 1);
-  uint32_t* koff = moff + (L + 1);
-  uint32_t* mcur = koff + (L + 2);
-  uint32_t* kcur = mcur + (L + 1);
+  uint32_t* small = nullptr;  // kcount[groups], koff[groups+1], cursor[groups]
+  IG_P_TRY(alloc(reinterpret_cast<void**>(&small), size_t(3 * groups + 1) * 4));
+  uint32_t* kcount = small;
+  uint32_t* koff = kcount + groups;
+  uint32_t* kcur = koff + (groups + 1);
   uint32_t* key = nullptr;
-  void* build_tok = prof_begin(kStageIndexBuild, s);
-  IG_P_TRY(cudaMemsetAsync(small, 0, nsmall * 4, s));
   IG_P_TRY(alloc(reinterpret_cast<void**>(&key), size_t(a.n_keyed) * 4));
-  IG_P_TRY(launch_item_histogram(a.multi, a.n_multi, a.multi_stride, a.K, L, freq, s));
-  IG_P_TRY(launch_small_scan(freq, L, moff, s));
-  IG_P_TRY(launch_key_item(a.keyed, a.n_keyed, a.keyed_stride, a.K, L, freq, key, kcount, s));
-  IG_P_TRY(launch_small_scan(kcount, L + 1, koff, s));
-  std::vector<uint32_t> h_moff(L + 1), h_koff(L + 2);
-  prof_end(build_tok);
-  IG_P_TRY(cudaMemcpyAsync(h_moff.data(), moff, (L + 1) * 4, cudaMemcpyDeviceToHost, s));
-  IG_P_TRY(cudaMemcpyAsync(h_koff.data(), koff, (L + 2) * 4, cudaMemcpyDeviceToHost, s));
-  IG_P_TRY(cudaStreamSynchronize(s));
-  const int64_t n_copies = h_moff[L];
-  if (double(n_copies) > a.max_fill * double(a.n_multi) * double(L)) {
-    *a.tests_out = -1;
-    return done(cudaSuccess);
-  }
-  // Grouped arrays, padded by one stream tile so whole-tile copies stay in bounds.
-  uint64_t *mrows = nullptr, *krows = nullptr, *kscore = nullptr;
-  uint32_t *mids = nullptr, *kids = nullptr;
-  IG_P_TRY(alloc(reinterpret_cast<void**>(&mrows), size_t(n_copies + 256) * KT * 8));
-  IG_P_TRY(alloc(reinterpret_cast<void**>(&mids), size_t(n_copies) * 4));
+  IG_P_TRY(cudaMemsetAsync(small, 0, size_t(3 * groups + 1) * 4, s));
+  void* tok = prof_begin(kStageIndexBuild, s);
+  IG_P_TRY(launch_key_item(a.keyed, a.n_keyed, a.keyed_stride, K, L, idx.freq, key, kcount, s));
+  IG_P_TRY(launch_small_scan(kcount, groups, koff, s));
+  uint64_t *krows = nullptr, *kscore = nullptr;
+  uint32_t* kids = nullptr;
   IG_P_TRY(alloc(reinterpret_cast<void**>(&krows), size_t(a.n_keyed + 256) * KT * 8));
   IG_P_TRY(alloc(reinterpret_cast<void**>(&kids), size_t(a.n_keyed) * 4));
   if (a.mode == MODE_SUM)
     IG_P_TRY(alloc(reinterpret_cast<void**>(&kscore), size_t(a.n_keyed + 256) * 8));
-  build_tok = prof_begin(kStageIndexBuild, s);
-  IG_P_TRY(launch_multi_scatter(a.multi, a.n_multi, a.multi_stride, a.K, KT, moff, mcur, mrows,
-                                mids, s));
-  IG_P_TRY(launch_keyed_scatter(a.keyed, a.n_keyed, a.keyed_stride, a.K, KT, key, koff, kcur,
-                                krows, kids, a.mode == MODE_SUM ? a.keyed_score : nullptr,
+  IG_P_TRY(launch_keyed_scatter(a.keyed, a.n_keyed, a.keyed_stride, K, KT, groups, key, koff,
+                                kcur, krows, kids, a.mode == MODE_SUM ? a.keyed_score : nullptr,
                                 kscore, s));
-  prof_end(build_tok);
+  prof_end(tok);
+  std::vector<uint32_t> h_koff(groups + 1);
+  IG_P_TRY(cudaMemcpyAsync(h_koff.data(), koff, (groups + 1) * 4, cudaMemcpyDeviceToHost, s));
+  IG_P_TRY(cudaStreamSynchronize(s));
   // Work blocks: own = keyed (patterns) for ANY / COUNT, own = multi
   // (records) for SUM; about 8 blocks per SM worth of tests each.
   std::vector<WorkItem> items;
@@ -477,34 +564,44 @@ cudaError_t pruned_subset(const PrunedArgs& a, cudaStream_t s) {
   const bool own_keyed = a.mode != MODE_SUM;
   int64_t total = 0;
   for (int l = 0; l < L; ++l)
-    total += (int64_t(h_koff[l + 1]) - h_koff[l]) * (int64_t(h_moff[l + 1]) - h_moff[l]);
+    total += (int64_t(h_koff[l + 1]) - h_koff[l]) * (int64_t(idx.h_off[l + 1]) - idx.h_off[l]);
   const int64_t target = std::max<int64_t>(total / (int64_t(num_sms()) * 8), 1 << 16);
-  build_work_items(own_keyed ? h_koff.data() : h_moff.data(),
-                   own_keyed ? h_moff.data() : h_koff.data(), L, grouped_own_per_cta(KT),
+  build_work_items(own_keyed ? h_koff.data() : idx.h_off.data(),
+                   own_keyed ? idx.h_off.data() : h_koff.data(), L, grouped_own_per_cta(KT),
                    grouped_rows_per_tile(KT), target, &items, &tests);
   *a.tests_out = tests;
   if (!items.empty()) {
+    Staging& st = g_staging;
+    if (st.done) IG_P_TRY(cudaEventSynchronize(st.done));
+    if (st.cap < items.size()) {
+      if (st.buf) cudaFreeHost(st.buf);
+      st.buf = nullptr;
+      st.cap = 0;
+      IG_P_TRY(cudaMallocHost(reinterpret_cast<void**>(&st.buf), items.size() * 2 * sizeof(WorkItem)));
+      st.cap = items.size() * 2;
+    }
+    if (!st.done) IG_P_TRY(cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming));
+    std::copy(items.begin(), items.end(), st.buf);
     WorkItem* d_items = nullptr;
     IG_P_TRY(alloc(reinterpret_cast<void**>(&d_items), items.size() * sizeof(WorkItem)));
-    IG_P_TRY(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(WorkItem),
+    IG_P_TRY(cudaMemcpyAsync(d_items, st.buf, items.size() * sizeof(WorkItem),
                              cudaMemcpyHostToDevice, s));
+    IG_P_TRY(cudaEventRecord(st.done, s));
     GroupedArgs g{a.mode,
                   KT,
                   d_items,
                   int64_t(items.size()),
-                  own_keyed ? krows : mrows,
-                  own_keyed ? kids : mids,
-                  own_keyed ? mrows : krows,
+                  own_keyed ? krows : idx.rows,
+                  own_keyed ? kids : idx.ids,
+                  own_keyed ? idx.rows : krows,
                   own_keyed ? nullptr : kscore,
                   a.out_u32,
                   a.out_u64,
                   a.status};
-    void* tok = a.prof_stage >= 0 ? prof_begin(a.prof_stage, s) : nullptr;
+    void* gtok = a.prof_stage >= 0 ? prof_begin(a.prof_stage, s) : nullptr;
     const cudaError_t ge = launch_grouped_subset(g, s);
-    prof_end(tok);
+    prof_end(gtok);
     IG_P_TRY(ge);
-    // The host vector of items must outlive the copy: wait for it here.
-    IG_P_TRY(cudaStreamSynchronize(s));
   }
 #undef IG_P_TRY
   return done(cudaSuccess);

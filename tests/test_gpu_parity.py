@@ -155,6 +155,9 @@ RANDOM_CASES = [
     (1000, 70, 80, "three_quarters", 0),
     (256, 700, 650, "three_quarters", 0),    # > 512 per class: last coherence window
     (500, 600, 900, "three_quarters", 30),
+    (256, 300, 280, "eighth", 0),            # sparse: the item index is used
+    (512, 260, 400, "eighth", 25),
+    (1024, 200, 150, "eighth", 0),
 ]
 
 
