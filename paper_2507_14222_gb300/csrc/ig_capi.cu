@@ -12,6 +12,9 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <condition_variable>
+#include <functional>
+#include <thread>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -152,6 +155,61 @@ struct DevBuf {
 // True for CUDA device (or managed) memory; the calling thread's current
 // device is then switched to the device that owns it, so that every later
 // allocation and launch of the call happens there.
+// Pinned host words for size read-backs, one block per host thread.
+unsigned long long* thread_pinned() {
+  static thread_local unsigned long long* p = nullptr;
+  if (!p && cudaMallocHost(&p, 8 * sizeof(unsigned long long)) != cudaSuccess) p = nullptr;
+  return p;
+}
+
+// One persistent helper thread that runs a task while the caller runs
+// another (used to fit the two classes concurrently).  Detached and never
+// destroyed: it idles on a condition variable until the process exits.
+class Worker {
+ public:
+  Worker() {
+    std::thread([this] { loop(); }).detach();
+  }
+  void run(std::function<void()> f) {
+    std::lock_guard<std::mutex> lk(mu_);
+    task_ = std::move(f);
+    pending_ = true;
+    finished_ = false;
+    cv_.notify_all();
+  }
+  void wait() {
+    std::unique_lock<std::mutex> lk(mu_);
+    cv_.wait(lk, [this] { return finished_; });
+  }
+
+ private:
+  void loop() {
+    for (;;) {
+      std::function<void()> f;
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [this] { return pending_; });
+        f = std::move(task_);
+        pending_ = false;
+      }
+      f();
+      std::lock_guard<std::mutex> lk(mu_);
+      finished_ = true;
+      cv_.notify_all();
+    }
+  }
+  std::mutex mu_;
+  std::condition_variable cv_;
+  std::function<void()> task_;
+  bool pending_ = false, finished_ = false;
+};
+
+std::mutex g_worker_mu;
+Worker& worker() {
+  static Worker* w = new Worker();
+  return *w;
+}
+
 // Owns a record index for the duration of a call.
 struct IndexHolder {
   igk::RecordIndex idx;
@@ -542,8 +600,14 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
     }
   }
 
-  for (int c = 1; c >= 0; --c) {
+  // The two classes are fitted concurrently, each on its own stream (class
+  // + on a worker thread, class - on the calling thread), so that the
+  // kernels of one class run while the other waits for a size read-back.
+  auto fit_class = [&](int c, cudaStream_t s) -> int {
     const int o = 1 - c;
+    unsigned long long* h_pinned = thread_pinned();
+    if (!h_pinned) return fail(IG_E_CUDA, "ig_fit: pinned host allocation failed");
+    TableCounters* h_counters = reinterpret_cast<TableCounters*>(h_pinned + 4);
     m->n_train[c] = nc[c];
     m->n_pairs[c] = nc[c] * (nc[c] - 1) / 2;
     // Eq. 1: B^c, deduplicated on the device.
@@ -762,6 +826,44 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
                                   cudaMemcpyDeviceToDevice, s),
                 "ig_fit");
     }
+    return IG_OK;
+  };
+  {
+    int dev = 0;
+    IG_CUDA(cudaGetDevice(&dev), "ig_fit");
+    cudaStream_t cs[2] = {nullptr, nullptr};
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    for (int i = 0; i < 2; ++i)
+      IG_CUDA(cudaStreamCreateWithFlags(&cs[i], cudaStreamNonBlocking), "ig_fit");
+    for (int i = 0; i < 3; ++i)
+      IG_CUDA(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming), "ig_fit");
+    IG_CUDA(cudaEventRecord(ev[2], s), "ig_fit");
+    for (int i = 0; i < 2; ++i) IG_CUDA(cudaStreamWaitEvent(cs[i], ev[2], 0), "ig_fit");
+    int rc[2] = {IG_OK, IG_OK};
+    std::string msg[2];
+    {
+      std::lock_guard<std::mutex> lk(g_worker_mu);
+      Worker& w = worker();
+      w.run([&] {
+        cudaSetDevice(dev);
+        rc[1] = fit_class(1, cs[1]);
+        if (rc[1] != IG_OK) msg[1] = g_last_error;
+      });
+      rc[0] = fit_class(0, cs[0]);
+      if (rc[0] != IG_OK) msg[0] = g_last_error;
+      w.wait();
+    }
+    for (int i = 0; i < 2; ++i) {
+      cudaEventRecord(ev[i], cs[i]);
+      cudaStreamWaitEvent(s, ev[i], 0);
+      cudaStreamDestroy(cs[i]);
+    }
+    for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
+    for (int i = 1; i >= 0; --i)
+      if (rc[i] != IG_OK) {
+        g_last_error = msg[i];
+        return rc[i];
+      }
   }
 
   // Regulation 3: mean and population std of N over the training normals,

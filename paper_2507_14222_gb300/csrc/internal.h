@@ -148,16 +148,18 @@ cudaError_t launch_subset_tc(const TcArgs& a, cudaStream_t s);
 // ---- prune.cu (subset tests restricted by an item index) --------------------
 struct WorkItem {
   int64_t own_begin, own_count, str_begin, str_count;
+  int64_t own_keyed;  // 1: registers hold patterns (keyed rows), 0: records
 };
 struct GroupedArgs {
   int mode;
   int KT;
   const WorkItem* items;
   int64_t n_items;
-  const uint64_t* own;
-  const uint32_t* own_ids;
-  const uint64_t* stream;
-  const uint64_t* stream_score;
+  const uint64_t* keyed;
+  const uint32_t* keyed_ids;
+  const uint64_t* keyed_score;
+  const uint64_t* multi;
+  const uint32_t* multi_ids;
   uint32_t* out_u32;
   unsigned long long* out_u64;
   int* status;

@@ -191,15 +191,23 @@ struct GShape {
 
 struct GroupedParams {
   const WorkItem* items;
-  const uint64_t* own;        // grouped own rows (stride KT)
-  const uint32_t* own_ids;    // original index of each own row
-  const uint64_t* stream;     // grouped stream rows (stride KT, padded)
-  const uint64_t* stream_score;  // MODE_SUM: score per grouped stream row (padded)
-  uint32_t* out_u32;
-  unsigned long long* out_u64;
+  const uint64_t* keyed;        // patterns, grouped by key (stride KT, padded)
+  const uint32_t* keyed_ids;    // original pattern of each grouped row
+  const uint64_t* keyed_score;  // MODE_SUM: S of each grouped pattern (padded)
+  const uint64_t* multi;        // record copies, grouped by item (stride KT, padded)
+  const uint32_t* multi_ids;    // original record of each copy
+  uint32_t* out_u32;            // ANY / COUNT: per pattern
+  unsigned long long* out_u64;  // SUM: per record
   int* status;
 };
 
+// One work item: the rows [own_begin, +own_count) of one side of a group sit
+// in registers (Q per thread), the rows [str_begin, +str_count) of the other
+// side stream through shared memory.  The side in registers is the larger
+// one, so that the lanes are busy.  When it is the side the result belongs
+// to (patterns for ANY / COUNT, records for SUM) the result accumulates in
+// registers; otherwise every hit updates the streamed row's result directly
+// (atomics: hits are few).
 template <int KT, int MODE>
 __global__ void __launch_bounds__(kGThreads) grouped_subset_kernel(GroupedParams p) {
   using S = GShape<KT>;
@@ -210,23 +218,33 @@ __global__ void __launch_bounds__(kGThreads) grouped_subset_kernel(GroupedParams
   uint64_t* bars = rows_s + kGStages * TR * KT;
 
   const WorkItem wi = p.items[blockIdx.x];
+  const bool own_keyed = wi.own_keyed != 0;
+  // Results stay in registers when the own side is the result side.
+  const bool own_result = (MODE == MODE_SUM) ? !own_keyed : own_keyed;
+  const uint64_t* own_rows = own_keyed ? p.keyed : p.multi;
+  const uint64_t* str_rows = own_keyed ? p.multi : p.keyed;
+  const uint32_t* str_ids = own_keyed ? p.multi_ids : p.keyed_ids;
+
   uint32_t own[Q][H];
   bool valid[Q];
+  unsigned long long own_score[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int64_t r = int64_t(q) * kGThreads + threadIdx.x;
     valid[q] = r < wi.own_count;
-    const uint64_t* src = p.own + (wi.own_begin + r) * KT;
+    const uint64_t* src = own_rows + (wi.own_begin + r) * KT;
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
       const uint64_t w = valid[q] ? src[k] : 0ull;
       own[q][2 * k] = uint32_t(w);
       own[q][2 * k + 1] = uint32_t(w >> 32);
     }
+    own_score[q] = 0;
+    if constexpr (MODE == MODE_SUM)
+      if (valid[q] && own_keyed) own_score[q] = p.keyed_score[wi.own_begin + r];
   }
   // Stream tiles may start at any row: with KT >= 2 every row is 16-byte
-  // aligned, as the bulk copy needs.  Scores (MODE_SUM) are not staged; the
-  // rare hits read theirs from global memory.
+  // aligned, as the bulk copy needs.
   const int64_t s_lo = wi.str_begin, s_hi = wi.str_begin + wi.str_count;
   const int64_t ntiles = ceil_div(s_hi - s_lo, TR);
   if (threadIdx.x == 0) {
@@ -238,7 +256,7 @@ __global__ void __launch_bounds__(kGThreads) grouped_subset_kernel(GroupedParams
     const int st = int(tile % kGStages);
     const int64_t r0 = s_lo + tile * TR;
     mbar_arrive_expect_tx(bars + st, kRowBytes);
-    bulk_g2s(rows_s + st * TR * KT, p.stream + r0 * KT, kRowBytes, bars + st);
+    bulk_g2s(rows_s + st * TR * KT, str_rows + r0 * KT, kRowBytes, bars + st);
   };
   if (threadIdx.x == 0)
     for (int64_t t = 0; t < ntiles && t < kGStages; ++t) issue(t);
@@ -264,38 +282,67 @@ __global__ void __launch_bounds__(kGThreads) grouped_subset_kernel(GroupedParams
     const int64_t left = s_hi - (s_lo + tile * TR);
     const int nr = int(left < TR ? left : TR);
     const uint32_t* rs = reinterpret_cast<const uint32_t*>(rows_s + st * TR * KT);
+    if (own_keyed) {
+      // pattern (own) inside record (streamed)?
 #pragma unroll 2
-    for (int r = 0; r < nr; ++r) {
-      uint32_t rh[H];
+      for (int r = 0; r < nr; ++r) {
+        uint32_t rh[H];
 #pragma unroll
-      for (int v = 0; v < H / 4; ++v) {
-        const uint4 x = reinterpret_cast<const uint4*>(rs + r * H)[v];
-        rh[4 * v] = x.x;
-        rh[4 * v + 1] = x.y;
-        rh[4 * v + 2] = x.z;
-        rh[4 * v + 3] = x.w;
-      }
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        uint32_t acc = 0;
-#pragma unroll
-        for (int h = 0; h < H; ++h) {
-          if constexpr (MODE == MODE_SUM)
-            acc |= rh[h] & ~own[q][h];
-          else
-            acc |= own[q][h] & ~rh[h];
+        for (int v = 0; v < H / 4; ++v) {
+          const uint4 x = reinterpret_cast<const uint4*>(rs + r * H)[v];
+          rh[4 * v] = x.x;
+          rh[4 * v + 1] = x.y;
+          rh[4 * v + 2] = x.z;
+          rh[4 * v + 3] = x.w;
         }
-        const bool hit = acc == 0u;
-        if constexpr (MODE == MODE_ANY) cov[q] |= hit;
-        if constexpr (MODE == MODE_COUNT) cnt[q] += hit ? 1u : 0u;
-        if constexpr (MODE == MODE_SUM) {
-          if (hit) sum[q] += p.stream_score[s_lo + tile * TR + r];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          uint32_t acc = 0;
+#pragma unroll
+          for (int h = 0; h < H; ++h) acc |= own[q][h] & ~rh[h];
+          const bool hit = acc == 0u && valid[q];
+          if constexpr (MODE == MODE_ANY) cov[q] |= hit;
+          if constexpr (MODE == MODE_COUNT) cnt[q] += hit ? 1u : 0u;
+          if constexpr (MODE == MODE_SUM) {
+            if (hit) atomicAdd(p.out_u64 + str_ids[s_lo + tile * TR + r], own_score[q]);
+          }
+        }
+      }
+    } else {
+      // pattern (streamed) inside record (own)?
+#pragma unroll 2
+      for (int r = 0; r < nr; ++r) {
+        uint32_t rh[H];
+#pragma unroll
+        for (int v = 0; v < H / 4; ++v) {
+          const uint4 x = reinterpret_cast<const uint4*>(rs + r * H)[v];
+          rh[4 * v] = x.x;
+          rh[4 * v + 1] = x.y;
+          rh[4 * v + 2] = x.z;
+          rh[4 * v + 3] = x.w;
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          uint32_t acc = 0;
+#pragma unroll
+          for (int h = 0; h < H; ++h) acc |= rh[h] & ~own[q][h];
+          const bool hit = acc == 0u && valid[q];
+          if constexpr (MODE == MODE_SUM) {
+            if (hit) sum[q] += p.keyed_score[s_lo + tile * TR + r];
+          } else {
+            if (hit) {
+              const uint32_t sid = str_ids[s_lo + tile * TR + r];
+              if constexpr (MODE == MODE_ANY) p.out_u32[sid] = 1u;
+              if constexpr (MODE == MODE_COUNT) atomicAdd(p.out_u32 + sid, 1u);
+            }
+          }
         }
       }
     }
     bool stop = false;
     if constexpr (MODE == MODE_ANY) {
-      bool done = true;
+      // Early exit once every pattern held in registers is covered.
+      bool done = own_result;
 #pragma unroll
       for (int q = 0; q < Q; ++q) done &= (cov[q] || !valid[q]);
       stop = __syncthreads_and(done) != 0;
@@ -311,10 +358,12 @@ __global__ void __launch_bounds__(kGThreads) grouped_subset_kernel(GroupedParams
     for (int64_t t = first; t < end; ++t)
       if (!mbar_wait(bars + int(t % kGStages), uint32_t((t / kGStages) & 1), p.status)) break;
   }
+  if (!own_result) return;
+  const uint32_t* own_ids = own_keyed ? p.keyed_ids : p.multi_ids;
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     if (!valid[q]) continue;
-    const uint32_t id = p.own_ids[wi.own_begin + int64_t(q) * kGThreads + threadIdx.x];
+    const uint32_t id = own_ids[wi.own_begin + int64_t(q) * kGThreads + threadIdx.x];
     if constexpr (MODE == MODE_ANY) {
       if (cov[q]) p.out_u32[id] = 1u;
     }
@@ -392,7 +441,7 @@ int grouped_own_per_cta(int KT) { return kGThreads * (KT >= 16 ? 2 : 4); }
 template <int KT, int MODE>
 static cudaError_t grouped_t(const GroupedArgs& a, cudaStream_t s) {
   using S = GShape<KT>;
-  GroupedParams p{a.items, a.own, a.own_ids, a.stream, a.stream_score,
+  GroupedParams p{a.items, a.keyed, a.keyed_ids, a.keyed_score, a.multi, a.multi_ids,
                   a.out_u32, a.out_u64, a.status};
   const size_t smem = size_t(kGStages) * S::TR * KT * 8 + kGStages * sizeof(uint64_t);
   grouped_subset_kernel<KT, MODE><<<unsigned(a.n_items), kGThreads, smem, s>>>(p);
@@ -420,27 +469,35 @@ cudaError_t launch_grouped_subset(const GroupedArgs& a, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
-// Blocks (group, own tile, stream range) with about `target` tests each.
-void build_work_items(const uint32_t* own_off, const uint32_t* str_off, int groups, int own_tile,
-                      int str_tile, int64_t target, std::vector<WorkItem>* items,
-                      int64_t* tests) {
+// Blocks (group, own tile, stream range) with about `target` tests each;
+// in every group the larger side goes to registers (own).
+void build_work_items(const uint32_t* keyed_off, const uint32_t* multi_off, int groups,
+                      int own_tile, int str_tile, int64_t target, bool mode_sum,
+                      std::vector<WorkItem>* items, int64_t* tests) {
   items->clear();
   *tests = 0;
   for (int l = 0; l < groups; ++l) {
-    const int64_t no = int64_t(own_off[l + 1]) - own_off[l];
-    const int64_t ns = int64_t(str_off[l + 1]) - str_off[l];
-    if (no == 0 || ns == 0) continue;
-    *tests += no * ns;
+    const int64_t nk = int64_t(keyed_off[l + 1]) - keyed_off[l];
+    const int64_t nm = int64_t(multi_off[l + 1]) - multi_off[l];
+    if (nk == 0 || nm == 0) continue;
+    *tests += nk * nm;
+    // The result side stays in registers unless the other side is at least
+    // twice as large (then per-hit atomics are the cheaper way to fill lanes).
+    const bool own_keyed = mode_sum ? (nk >= 2 * nm) : (2 * nk >= nm);
+    const int64_t no = own_keyed ? nk : nm, ns = own_keyed ? nm : nk;
+    const int64_t o0 = own_keyed ? keyed_off[l] : multi_off[l];
+    const int64_t s0 = own_keyed ? multi_off[l] : keyed_off[l];
     for (int64_t o = 0; o < no; o += own_tile) {
       const int64_t oc = std::min<int64_t>(own_tile, no - o);
       int64_t per = std::max<int64_t>(str_tile, target / std::max<int64_t>(1, oc));
       per = ((per + str_tile - 1) / str_tile) * str_tile;
       for (int64_t r = 0; r < ns; r += per) {
         WorkItem w;
-        w.own_begin = int64_t(own_off[l]) + o;
+        w.own_begin = o0 + o;
         w.own_count = oc;
-        w.str_begin = int64_t(str_off[l]) + r;
+        w.str_begin = s0 + r;
         w.str_count = std::min<int64_t>(per, ns - r);
+        w.own_keyed = own_keyed ? 1 : 0;
         items->push_back(w);
       }
     }
@@ -557,18 +614,15 @@ cudaError_t indexed_subset(const IndexedArgs& a, cudaStream_t s) {
   std::vector<uint32_t> h_koff(groups + 1);
   IG_P_TRY(cudaMemcpyAsync(h_koff.data(), koff, (groups + 1) * 4, cudaMemcpyDeviceToHost, s));
   IG_P_TRY(cudaStreamSynchronize(s));
-  // Work blocks: own = keyed (patterns) for ANY / COUNT, own = multi
-  // (records) for SUM; about 8 blocks per SM worth of tests each.
+  // Work blocks of about 8 blocks per SM worth of tests each.
   std::vector<WorkItem> items;
   int64_t tests = 0;
-  const bool own_keyed = a.mode != MODE_SUM;
   int64_t total = 0;
   for (int l = 0; l < L; ++l)
     total += (int64_t(h_koff[l + 1]) - h_koff[l]) * (int64_t(idx.h_off[l + 1]) - idx.h_off[l]);
   const int64_t target = std::max<int64_t>(total / (int64_t(num_sms()) * 8), 1 << 16);
-  build_work_items(own_keyed ? h_koff.data() : idx.h_off.data(),
-                   own_keyed ? idx.h_off.data() : h_koff.data(), L, grouped_own_per_cta(KT),
-                   grouped_rows_per_tile(KT), target, &items, &tests);
+  build_work_items(h_koff.data(), idx.h_off.data(), L, grouped_own_per_cta(KT),
+                   grouped_rows_per_tile(KT), target, a.mode == MODE_SUM, &items, &tests);
   *a.tests_out = tests;
   if (!items.empty()) {
     Staging& st = g_staging;
@@ -587,17 +641,8 @@ cudaError_t indexed_subset(const IndexedArgs& a, cudaStream_t s) {
     IG_P_TRY(cudaMemcpyAsync(d_items, st.buf, items.size() * sizeof(WorkItem),
                              cudaMemcpyHostToDevice, s));
     IG_P_TRY(cudaEventRecord(st.done, s));
-    GroupedArgs g{a.mode,
-                  KT,
-                  d_items,
-                  int64_t(items.size()),
-                  own_keyed ? krows : idx.rows,
-                  own_keyed ? kids : idx.ids,
-                  own_keyed ? idx.rows : krows,
-                  own_keyed ? nullptr : kscore,
-                  a.out_u32,
-                  a.out_u64,
-                  a.status};
+    GroupedArgs g{a.mode, KT,      d_items,   int64_t(items.size()), krows,   kids,
+                  kscore, idx.rows, idx.ids, a.out_u32,             a.out_u64, a.status};
     void* gtok = a.prof_stage >= 0 ? prof_begin(a.prof_stage, s) : nullptr;
     const cudaError_t ge = launch_grouped_subset(g, s);
     prof_end(gtok);
