@@ -62,7 +62,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="nsl15k", choices=sorted(igdata.WORKLOADS))
+    ap.add_argument("--workload", default="nsl15k",
+                    choices=sorted(igdata.WORKLOADS) + ["batched", "served"])
+    ap.add_argument("--served-patterns", type=int, default=1_000_000,
+                    help="patterns per class of the served workload")
+    ap.add_argument("--served-flows", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel", type=int, default=0,
@@ -162,6 +166,10 @@ def run_ours(args):
         dist.init_process_group("nccl")
     ig.build()
     ig.load()
+    if args.workload == "batched":
+        return run_batched(args, ig, torch, rank, world, local)
+    if args.workload == "served":
+        return run_served(args, ig, torch, rank, world, local)
 
     seed_offset = 0 if rank == 0 else 7919 * rank
     w = {"tiny": lambda: igdata.tiny(1001 + seed_offset),
@@ -275,6 +283,177 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_batched(args, ig, torch, rank, world, local):
+    """64 independent problems per step: batched fit vs one ig_fit per problem.
+
+    Both forms run in the same process on the same inputs; their models must
+    be byte-identical.  Scoring runs per problem in both.
+    """
+    probs = igdata.batched(igdata.BATCHED_PROBLEMS, 2000 + 7919 * rank)
+    dev = []
+    for w in probs:
+        dev.append((torch.from_numpy(w.train_codes.view(np.int16)).cuda(),
+                    torch.from_numpy(w.train_labels).cuda(),
+                    torch.from_numpy(w.test_codes.view(np.int16)).cuda(), w.cards))
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def encode_all():
+        return [(ig.ig_encode(c, cards), lab, ig.ig_encode(t, cards)) for c, lab, t, cards in dev]
+
+    def step(batched):
+        enc = encode_all()
+        if batched:
+            models = ig.ig_fit_batched([(r, lab) for r, lab, _ in enc],
+                                       subset_kernel=args.kernel)
+        else:
+            models = [ig.ig_fit(r, lab, subset_kernel=args.kernel) for r, lab, _ in enc]
+        for mdl, (_, _, te) in zip(models, enc):
+            ig.ig_score(mdl, te)
+        return models
+
+    def timed(batched, steps):
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            models = step(batched)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+            last = models
+        return ms, last
+
+    for _ in range(args.warmup):
+        for mdl in step(True):
+            mdl.free()
+    infos = None
+    launches0 = ig.launch_count()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms_b, models_b = timed(True, args.steps)
+    launches = ig.launch_count() - launches0
+    ms_s, models_s = timed(False, max(1, min(args.steps, 3)))
+    identical = True
+    total_tests = 0
+    for w, mb, ms_ in zip(probs, models_b, models_s):
+        ib = mb.info()
+        total_tests += nominal_tests(ib, w.test_codes.shape[0])["total"]
+        for cls in (0, 1):
+            identical &= all(np.array_equal(x, y) for x, y in zip(mb.patterns(cls),
+                                                                   ms_.patterns(cls)))
+        mb.free()
+        ms_.free()
+    total_ms = sum(ms_b)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": world * total_tests / (ms_per_step * 1e-3) / 1e9,
+        "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"ig-batched-{len(probs)}-problems",
+                   "records": [int(w.train_codes.shape[0] + w.test_codes.shape[0])
+                               for w in probs][:8] + ["..."],
+                   "l2": "flushed before every timed step (512 MiB write)"},
+        "per_problem_launch_ms_per_step": statistics.median(ms_s),
+        "speedup_vs_per_problem": statistics.median(ms_s) / statistics.median(ms_b),
+        "identical_to_per_problem": bool(identical),
+        "gpu_launches": int(launches), "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_served(args, ig, torch, rank, world, local):
+    """Served scoring: a continuous-batching server over resident pattern sets.
+
+    1. Saturated throughput: every request submitted at once.
+    2. A Poisson request stream at 0.8x that rate, replayed in real time:
+       flows/s and per-request latency (submission -> results in host memory).
+    Every flow's (A, N, label) is checked against one ig_score call over all
+    flows.
+    """
+    import threading
+    sw = igdata.served(args.served_patterns, args.served_flows, 1005 + 7919 * rank)
+    words = [ig.ig_encode(torch.from_numpy(sw.patterns[c].view(np.int16)).cuda(), sw.cards)
+             for c in (0, 1)]
+    model = ig.ig_model_from_patterns(words[0], sw.support[0], words[1], sw.support[1])
+    flows = ig.ig_encode(sw.flow_codes, sw.cards)              # host rows
+    ref = ig.ig_score(model, torch.from_numpy(flows.view(np.int64)).cuda())
+    torch.cuda.synchronize()
+    ref = [t.cpu().numpy() for t in ref]
+    offs = np.concatenate([[0], np.cumsum(sw.request_sizes)])
+    reqs = [flows[offs[i]:offs[i + 1]] for i in range(len(sw.request_sizes))]
+    server = ig.Server(model, slots=3, max_batch_flows=65536,
+                       memory_budget_bytes=1 << 30)
+
+    def run(gaps_s):
+        out = [None] * len(reqs)
+        tickets = [None] * len(reqs)
+        t0 = time.perf_counter()
+
+        def submitter():
+            due = t0
+            for i, r in enumerate(reqs):
+                if gaps_s is not None:
+                    due += gaps_s[i]
+                    delay = due - time.perf_counter()
+                    if delay > 0:
+                        time.sleep(delay)
+                tickets[i] = server.submit(r)
+        th = threading.Thread(target=submitter)
+        th.start()
+        for i in range(len(reqs)):
+            while tickets[i] is None:
+                time.sleep(0.0001)
+            out[i] = server.wait(tickets[i])
+        th.join()
+        return out, time.perf_counter() - t0
+
+    run(None)                                   # warm-up pass
+    sat, sat_s = run(None)
+    sat_fps = sw.request_sizes.sum() / sat_s
+    rate_req = 0.8 * sat_fps / sw.request_sizes.mean()
+    b0, f0 = server.stats()
+    with ClockSampler(local) as clk:
+        paced, paced_s = run(sw.unit_gaps / rate_req)
+    b1, f1 = server.stats()
+    lat = np.array([o[3] for o in paced])
+    got = [np.concatenate([o[k] for o in paced]) for k in range(3)]
+    identical = all(np.array_equal(g, r) for g, r in zip(got, ref))
+    server.close()
+    if rank != 0:
+        return
+    flows_done = int(sw.request_sizes.sum())
+    line = {
+        "metric": METRIC, "value": flows_done / paced_s, "unit": "flows/s",
+        "n_gpus": world, "steps": 1, "warmup": 1,
+        "ms_per_step": paced_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": sw.name, "patterns_per_class": args.served_patterns,
+                   "flows": flows_done, "requests": int(len(reqs)),
+                   "request_sizes": "log-uniform in [1, 4096]",
+                   "arrivals": "Poisson at 0.8x the saturated rate",
+                   "server": {"slots": 3, "max_batch_flows": 65536,
+                              "memory_budget_bytes": 1 << 30}},
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "saturated_flows_per_s": sat_fps,
+        "saturated_p50_ms": float(np.percentile([o[3] for o in sat], 50)),
+        "batches": int(b1 - b0), "mean_flows_per_batch": (f1 - f0) / max(1, b1 - b0),
+        "identical_to_one_shot": bool(identical), "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
 
 
 def roofline(stages, info, K, clocks, steps):

@@ -150,6 +150,32 @@ def _prototype_records(rng, protos, weights, rho, pmfs, n):
     return codes
 
 
+class _NslSampler:
+    """Draws NSL-KDD-shaped records of either class (see nsl_like)."""
+
+    def __init__(self, rng: np.random.Generator):
+        self.rng = rng
+        self.cards = NSL_CARDS
+        F = len(self.cards)
+        exps = rng.uniform(NSL_S_LO, NSL_S_HI, size=F)
+        self.pmfs = class_pmfs(rng, self.cards, exps, shared_frac=NSL_SHARED_FRAC)
+        mean_pmfs = [0.5 * (self.pmfs[NORMAL][f] + self.pmfs[ATTACK][f]) for f in range(F)]
+        mean_pmfs = [p / p.sum() for p in mean_pmfs]
+        self.protos = draw_codes(rng, mean_pmfs, NSL_PROTOTYPES)
+        base = zipf_pmf(NSL_PROTOTYPES, NSL_PROTO_S)
+        common = base[rng.permutation(NSL_PROTOTYPES)]
+        self.weights = {}
+        for c in (NORMAL, ATTACK):
+            w = NSL_PROTO_SHARED * common + (1.0 - NSL_PROTO_SHARED) * base[
+                rng.permutation(NSL_PROTOTYPES)]
+            self.weights[c] = w / w.sum()
+        self.rho = rng.uniform(NSL_RHO_LO, NSL_RHO_HI, size=F)
+
+    def draw(self, c: int, n: int) -> np.ndarray:
+        return _prototype_records(self.rng, self.protos, self.weights[c], self.rho,
+                                  self.pmfs[c], n)
+
+
 def nsl_like(n_records: int, train_frac: float, seed: int, name: str,
              normal_frac: float = 0.53) -> Workload:
     """NSL-KDD-shaped records: 41 features, 464 items, K = 8 words.
@@ -158,21 +184,8 @@ def nsl_like(n_records: int, train_frac: float, seed: int, name: str,
     overall, and the same fraction (rounded) within the training split.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
+    sampler = _NslSampler(rng)
     cards = NSL_CARDS
-    F = len(cards)
-    exps = rng.uniform(NSL_S_LO, NSL_S_HI, size=F)
-    pmfs = class_pmfs(rng, cards, exps, shared_frac=NSL_SHARED_FRAC)
-    mean_pmfs = [0.5 * (pmfs[NORMAL][f] + pmfs[ATTACK][f]) for f in range(F)]
-    mean_pmfs = [p / p.sum() for p in mean_pmfs]
-    protos = draw_codes(rng, mean_pmfs, NSL_PROTOTYPES)
-    base = zipf_pmf(NSL_PROTOTYPES, NSL_PROTO_S)
-    common = base[rng.permutation(NSL_PROTOTYPES)]
-    weights = {}
-    for c in (NORMAL, ATTACK):
-        w = NSL_PROTO_SHARED * common + (1.0 - NSL_PROTO_SHARED) * base[
-            rng.permutation(NSL_PROTOTYPES)]
-        weights[c] = w / w.sum()
-    rho = rng.uniform(NSL_RHO_LO, NSL_RHO_HI, size=F)
 
     n_train = int(round(train_frac * n_records))
     n_normal = int(round(normal_frac * n_records))
@@ -182,9 +195,7 @@ def nsl_like(n_records: int, train_frac: float, seed: int, name: str,
     te_attack = (n_records - n_train) - te_normal
 
     def split(n_norm, n_att):
-        codes = np.concatenate([
-            _prototype_records(rng, protos, weights[NORMAL], rho, pmfs[NORMAL], n_norm),
-            _prototype_records(rng, protos, weights[ATTACK], rho, pmfs[ATTACK], n_att)])
+        codes = np.concatenate([sampler.draw(NORMAL, n_norm), sampler.draw(ATTACK, n_att)])
         labels = np.concatenate([np.full(n_norm, NORMAL, np.uint8),
                                  np.full(n_att, ATTACK, np.uint8)])
         order = rng.permutation(codes.shape[0])
@@ -278,3 +289,73 @@ WORKLOADS = {
     "nsl15k": nsl15k,
     "nsl148k": nsl148k,
 }
+
+BATCHED_PROBLEMS = 64
+
+
+def batched(count: int = BATCHED_PROBLEMS, base_seed: int = 2000) -> list:
+    """The batched workload: `count` independent problems (batched_problem)."""
+    return [batched_problem(i, base_seed) for i in range(count)]
+
+
+MISSING = 0xFFFF  # code of a missing value: the feature contributes no item
+
+
+@dataclass
+class ServedWorkload:
+    """Pattern sets to serve, flows to score and a request stream."""
+
+    name: str
+    cards: np.ndarray
+    patterns: dict         # class -> uint16[P, F] codes, MISSING where dropped
+    support: dict          # class -> uint32[P]
+    flow_codes: np.ndarray  # uint16[total_flows, F]
+    request_sizes: np.ndarray  # int64[R], summing to total_flows
+    unit_gaps: np.ndarray   # float64[R], Exp(1) inter-arrival gaps (unit rate)
+    meta: dict = field(default_factory=dict)
+
+
+def served(per_class: int = 1_000_000, total_flows: int = 1_000_000, seed: int = 1005,
+           keep_frac: float = 0.5, max_request: int = 4096) -> ServedWorkload:
+    """The served-scoring workload (NSL-KDD-shaped, K = 8).
+
+    Each pattern is a record of its class drawn from the NSL-KDD-shaped
+    generator with every feature kept with probability keep_frac and the
+    others marked MISSING (at least one kept); patterns are distinct as code
+    rows, per_class of them per class.  Supports are uniform in 1..1000.
+    Flows are records of both classes (53% normal).  Requests carry
+    log-uniform sizes in [1, max_request] flows until total_flows are used;
+    their arrival gaps are unit-rate exponentials (a Poisson stream, scaled
+    to the wanted rate by the caller).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sampler = _NslSampler(rng)
+    patterns, support = {}, {}
+    for c in (NORMAL, ATTACK):
+        have = np.empty((0, len(NSL_CARDS)), np.uint16)
+        while have.shape[0] < per_class:
+            need = int((per_class - have.shape[0]) * 1.3) + 1024
+            codes = sampler.draw(c, need)
+            keep = rng.random(codes.shape) < keep_frac
+            keep[np.arange(need), rng.integers(0, codes.shape[1], need)] = True
+            codes = np.where(keep, codes, np.uint16(MISSING)).astype(np.uint16)
+            have = np.unique(np.concatenate([have, codes]), axis=0)
+        patterns[c] = np.ascontiguousarray(have[rng.permutation(have.shape[0])[:per_class]])
+        support[c] = rng.integers(1, 1001, size=per_class).astype(np.uint32)
+    n_normal = int(round(0.53 * total_flows))
+    flows = np.concatenate([sampler.draw(NORMAL, n_normal),
+                            sampler.draw(ATTACK, total_flows - n_normal)])
+    flows = np.ascontiguousarray(flows[rng.permutation(total_flows)])
+    sizes = []
+    left = total_flows
+    while left > 0:
+        m = int(round(np.exp(rng.uniform(0.0, np.log(max_request)))))
+        m = max(1, min(m, left))
+        sizes.append(m)
+        left -= m
+    sizes = np.asarray(sizes, np.int64)
+    gaps = rng.exponential(1.0, size=sizes.shape[0])
+    return ServedWorkload(f"ig-served-{per_class}x2-patterns-{total_flows}-flows",
+                          np.asarray(NSL_CARDS, np.uint16), patterns, support, flows,
+                          sizes, gaps, {"seed": seed, "keep_frac": keep_frac,
+                                        "max_request": max_request})

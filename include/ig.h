@@ -98,7 +98,8 @@ typedef struct {
 } ig_model_info_t;
 
 /* Section 3.1 / Eq. 5: one-hot encoding of discretised records.
- * codes: uint16[n][F], codes[i][f] < cards[f] (bin of feature f).
+ * codes: uint16[n][F], codes[i][f] < cards[f] (bin of feature f), or
+ *        0xFFFF for a missing value (no item for that feature).
  * cards: HOST array uint16[F], feature cardinalities; item of (f, v) is
  *        sum(cards[0..f-1]) + v, so L = sum(cards).
  * words_out: uint64[n][K] with K = ceil(L/64) (the K argument must equal it).
@@ -122,6 +123,36 @@ int ig_encode(const uint16_t* codes, int64_t n, int32_t F,
  * model is complete. */
 int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
            const ig_params* p, ig_model** out, ig_stream_t stream);
+
+/* One problem of a batched fit: records and labels as for ig_fit. */
+typedef struct {
+  const uint64_t* rows;   /* uint64[n][K], device or host */
+  const uint8_t* labels;  /* uint8[n] */
+  int64_t n;
+  int32_t K;
+  int32_t reserved;
+} ig_problem;
+
+/* Batched IG training: fits n_problems independent problems (each exactly
+ * as ig_fit would, Section 3.1), of any sizes and word counts, concurrently
+ * on up to `lanes` streams (0 = 8); the largest problems start first and
+ * every lane pulls the next problem when it finishes one.  out[i] receives
+ * problem i's model.  Work is ordered after what `stream` holds when the
+ * call starts and before what is enqueued on it afterwards; the call returns
+ * when all models are complete.  On an error every model is freed, out[] is
+ * cleared, and the first error is reported (naming the problem). */
+int ig_fit_batched(const ig_problem* problems, int32_t n_problems, const ig_params* p,
+                   int32_t lanes, ig_model** out, ig_stream_t stream);
+
+/* Builds a model from given pattern sets (Section 3.1's dictionaries P^-
+ * and P^+, learned elsewhere), e.g. to serve them: for class c (0 = normal,
+ * 1 = attack) words[c] is uint64[n_patterns[c]][K] (any order; non-empty,
+ * distinct rows) and support[c] uint32[n_patterns[c]] the supports f_c.  The
+ * model holds the patterns in canonical order with their supports and the
+ * scores S = f * |b|^2 of Eq. 2; Regulation 3 is off.  IG_E_INVAL for an
+ * empty or repeated pattern.  Returns when the model is complete. */
+int ig_model_from_patterns(int32_t K, const uint64_t* const* words, const uint32_t* const* support,
+                           const int64_t* n_patterns, ig_model** out, ig_stream_t stream);
 
 /* Sizes and statistics of a fitted model. */
 int ig_model_info(const ig_model* m, ig_model_info_t* info);
@@ -168,6 +199,42 @@ int ig_score(const ig_model* model, const uint64_t* rows, int64_t m,
 int ig_score_noalloc(const ig_model* model, const uint64_t* rows, int64_t m,
                      int64_t* A_out, int64_t* N_out, uint8_t* label_out,
                      ig_stream_t stream);
+
+/* ---- Serving ------------------------------------------------------------
+ * A scoring server over a device-resident model (Eq. 4 and Regulations 1-3
+ * per flow, exactly as ig_score; the paper has no serving layer -- it notes
+ * that per-flow inference on learned patterns takes milliseconds).
+ * Requests are host arrays of packed flows.  The server batches the requests
+ * waiting in its queue -- in arrival order, as many as fit max_batch_flows
+ * and the device-memory budget for work in flight, without waiting for more
+ * -- and runs up to `slots` batches at once on separate streams, so batches
+ * admitted while others run overlap on the device.  A flow's results do not
+ * depend on the batch it shares. */
+typedef struct ig_server ig_server;
+typedef struct {
+  int32_t slots;                /* batches in flight at once (0 = 3) */
+  int32_t reserved;
+  int64_t max_batch_flows;      /* flows per batch, and per request (0 = 65536) */
+  int64_t memory_budget_bytes;  /* device bytes for batches in flight (0 = a
+                                   quarter of the free memory at creation) */
+} ig_server_config;
+
+/* The model must outlive the server.  cfg may be NULL. */
+int ig_server_create(const ig_model* model, const ig_server_config* cfg, ig_server** out);
+/* Queues a request: rows uint64[m][K] on the host (read when the request is
+ * batched), results written to the host arrays A_out, N_out (int64[m]) and
+ * label_out (uint8[m]; any may be NULL) before the request completes.  The
+ * arrays must stay valid until ig_server_wait returns for *ticket. */
+int ig_server_submit(ig_server* sv, const uint64_t* rows, int64_t m, int64_t* A_out,
+                     int64_t* N_out, uint8_t* label_out, uint64_t* ticket);
+/* Blocks until the request completes; *latency_ms (may be NULL) receives the
+ * time from its submission to its completion.  Each ticket is waited once. */
+int ig_server_wait(ig_server* sv, uint64_t ticket, double* latency_ms);
+/* Batches run and flows scored so far. */
+int ig_server_stats(ig_server* sv, int64_t* batches, int64_t* flows);
+/* Stops the server after the batches in flight; requests still queued are
+ * dropped (destroy only once every submitted request has been waited). */
+void ig_server_destroy(ig_server* sv);
 
 /* Model persistence: a flat little-endian file (magic, version, K, counts,
  * Regulation 3 statistics, then per class the canonical words, supports and

@@ -109,7 +109,8 @@ extern "C" {
 
 // Section 3.1 and Eq. 5: the token (feature f, value v) is item
 // offset_f + v, where offset_f is the sum of the cardinalities of the features
-// before f.  Returns 0, or -1 if a code is out of range or K is too small.
+// before f; the code 0xFFFF marks a missing value (no token).  Returns 0, or
+// -1 if a code is out of range or K is too small.
 int oracle_encode(const uint16_t* codes, int64_t n, int32_t F,
                   const uint16_t* cards, int32_t K, uint64_t* out) {
   int64_t L = 0;
@@ -120,6 +121,10 @@ int oracle_encode(const uint16_t* codes, int64_t n, int32_t F,
     int64_t offset = 0;
     for (int f = 0; f < F; ++f) {
       uint16_t v = codes[i * F + f];
+      if (v == 0xFFFF) {  // missing value: the feature contributes no item
+        offset += cards[f];
+        continue;
+      }
       if (v >= cards[f]) return -1;
       int64_t item = offset + v;
       out[i * K + item / 64] |= uint64_t(1) << (item % 64);

@@ -80,6 +80,13 @@ SIGNATURES = {
     "ig_launch_count": (ctypes.c_int64, []),
     "ig_prof_read_work": (ctypes.c_int, [_P]),
     "ig_score_noalloc": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P]),
+    "ig_fit_batched": (ctypes.c_int, [_P, _I32, _P, _I32, _P, _P]),
+    "ig_model_from_patterns": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P]),
+    "ig_server_create": (ctypes.c_int, [_P, _P, _P]),
+    "ig_server_submit": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P]),
+    "ig_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, _P]),
+    "ig_server_stats": (ctypes.c_int, [_P, _P, _P]),
+    "ig_server_destroy": (None, [_P]),
 }
 SCORE_NOALLOC_MAX_ROWS = 262144
 
@@ -255,6 +262,40 @@ def ig_fit(rows, labels, r: float | None = None, subset_kernel: int = 0,
     return Model(h)
 
 
+class ig_problem(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_void_p), ("labels", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("K", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def ig_fit_batched(problems, r: float | None = None, subset_kernel: int = 0,
+                   lanes: int = 0, stream=None) -> list:
+    """Fits independent problems [(rows, labels), ...] concurrently.
+
+    Each problem is fitted exactly as ig_fit would; returns one Model per
+    problem, in order.  Arrays may be CUDA tensors or numpy arrays.
+    """
+    lib = load()
+    keep = []
+    arr = (ig_problem * max(1, len(problems)))()
+    any_torch = False
+    for i, (rows, labels) in enumerate(problems):
+        n, K = _rows_shape(rows)
+        if _is_torch(rows):
+            any_torch = True
+        else:
+            rows = np.ascontiguousarray(rows, dtype=np.uint64)
+        if not _is_torch(labels):
+            labels = np.ascontiguousarray(labels, dtype=np.uint8)
+        keep.append((rows, labels))
+        arr[i] = ig_problem(_ptr(rows), _ptr(labels), n, K, 0)
+    prm = ig_params(float(r) if r is not None else 0.0, 1 if r is not None else 0,
+                    int(subset_kernel))
+    outs = (ctypes.c_void_p * max(1, len(problems)))()
+    _check(lib.ig_fit_batched(arr, len(problems), ctypes.byref(prm), int(lanes), outs,
+                              _stream(stream) if any_torch else None))
+    return [Model(ctypes.c_void_p(outs[i])) for i in range(len(problems))]
+
+
 def ig_score(model: Model, rows, stream=None):
     """IG inference (Eq. 4, Regulations 1-3): returns (A, N, labels)."""
     lib = load()
@@ -295,6 +336,95 @@ def ig_score_noalloc(model: Model, rows, stream=None):
     _check(load().ig_score_noalloc(model.handle, _ptr(rows), m, _ptr(A), _ptr(N),
                                    _ptr(lab), _stream(stream)))
     return A, N, lab
+
+
+def ig_model_from_patterns(words_normal, support_normal, words_attack, support_attack,
+                           stream=None) -> Model:
+    """A model holding given pattern sets (class 0 normal, 1 attack).
+
+    words_*: [P, K] packed patterns (numpy uint64 or CUDA int64 tensors, any
+    order, distinct, non-empty); support_*: [P] supports.  Scores follow
+    Eq. 2.
+    """
+    lib = load()
+    ws, fs = [], []
+    any_torch = False
+    for w, f in ((words_normal, support_normal), (words_attack, support_attack)):
+        if _is_torch(w):
+            any_torch = True
+        else:
+            w = np.ascontiguousarray(w, dtype=np.uint64)
+        if not _is_torch(f):
+            f = np.ascontiguousarray(f, dtype=np.uint32)
+        ws.append(w)
+        fs.append(f)
+    K = int(ws[0].shape[1]) if ws[0].ndim == 2 else int(ws[1].shape[1])
+    wp = (ctypes.c_void_p * 2)(*[_ptr(w).value for w in ws])
+    fp = (ctypes.c_void_p * 2)(*[_ptr(f).value for f in fs])
+    n = (ctypes.c_int64 * 2)(int(ws[0].shape[0]), int(ws[1].shape[0]))
+    h = ctypes.c_void_p()
+    _check(lib.ig_model_from_patterns(K, wp, fp, n, ctypes.byref(h),
+                                      _stream(stream) if any_torch else None))
+    return Model(h)
+
+
+class ig_server_config(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("max_batch_flows", ctypes.c_int64), ("memory_budget_bytes", ctypes.c_int64)]
+
+
+class Server:
+    """Continuous-batching scoring server over a model (see include/ig.h).
+
+    submit() queues host (numpy) flows and returns a handle; wait() blocks
+    until the request's (A, N, labels) are filled and returns its latency in
+    milliseconds.
+    """
+
+    def __init__(self, model: Model, slots: int = 0, max_batch_flows: int = 0,
+                 memory_budget_bytes: int = 0):
+        self.model = model
+        cfg = ig_server_config(int(slots), 0, int(max_batch_flows), int(memory_budget_bytes))
+        h = ctypes.c_void_p()
+        _check(load().ig_server_create(model.handle, ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._pending = {}
+
+    def submit(self, rows) -> int:
+        rows = np.ascontiguousarray(rows, dtype=np.uint64)
+        m = rows.shape[0]
+        A = np.empty(m, np.int64)
+        N = np.empty(m, np.int64)
+        lab = np.empty(m, np.uint8)
+        t = ctypes.c_uint64()
+        _check(load().ig_server_submit(self._h, _ptr(rows), m, _ptr(A), _ptr(N), _ptr(lab),
+                                       ctypes.byref(t)))
+        self._pending[t.value] = (rows, A, N, lab)
+        return t.value
+
+    def wait(self, ticket: int):
+        """-> (A, N, labels, latency_ms)."""
+        lat = ctypes.c_double()
+        rc = load().ig_server_wait(self._h, ctypes.c_uint64(ticket), ctypes.byref(lat))
+        rows, A, N, lab = self._pending.pop(ticket)
+        _check(rc)
+        return A, N, lab, lat.value
+
+    def stats(self):
+        b, f = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().ig_server_stats(self._h, ctypes.byref(b), ctypes.byref(f)))
+        return b.value, f.value
+
+    def close(self):
+        if self._h:
+            load().ig_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def ig_model_load(path: str) -> Model:

@@ -21,7 +21,7 @@ LIB = os.path.join(BUILD, "libig_gb300.so")
 
 SOURCES = ["encode.cu", "dedup.cu", "subset.cu", "sort.cu", "ig_capi.cu",
            "score_noalloc.cu", "subset_tc.cu",
-           "prune.cu"]
+           "prune.cu", "server.cu"]
 HEADERS = ["common.cuh", "internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",

@@ -21,6 +21,7 @@ __global__ void encode_kernel(const uint16_t* __restrict__ codes, int64_t n,
     uint32_t lo = offsets[f], hi = offsets[f + 1];
     if (hi <= uint32_t(k) * 64u || lo >= uint32_t(k + 1) * 64u) continue;
     uint32_t v = c[f];
+    if (v == 0xffffu) continue;  // missing value: no item for this feature
     if (v >= hi - lo) {
       bad = true;
       continue;

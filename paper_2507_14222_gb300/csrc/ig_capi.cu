@@ -204,11 +204,25 @@ class Worker {
   bool pending_ = false, finished_ = false;
 };
 
-std::mutex g_worker_mu;
-Worker& worker() {
-  static Worker* w = new Worker();
-  return *w;
+// Idle helper threads, reused across calls (created on demand).
+std::mutex g_pool_mu;
+std::vector<Worker*> g_pool;
+
+Worker* acquire_worker() {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (g_pool.empty()) return new Worker();
+  Worker* w = g_pool.back();
+  g_pool.pop_back();
+  return w;
 }
+
+void release_worker(Worker* w) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  g_pool.push_back(w);
+}
+
+// Smallest scoring batch that uses the item index (item-index models).
+constexpr int64_t kIndexMinRows = 512;
 
 // Owns a record index for the duration of a call.
 struct IndexHolder {
@@ -842,16 +856,16 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
     int rc[2] = {IG_OK, IG_OK};
     std::string msg[2];
     {
-      std::lock_guard<std::mutex> lk(g_worker_mu);
-      Worker& w = worker();
-      w.run([&] {
+      Worker* w = acquire_worker();
+      w->run([&] {
         cudaSetDevice(dev);
         rc[1] = fit_class(1, cs[1]);
         if (rc[1] != IG_OK) msg[1] = g_last_error;
       });
       rc[0] = fit_class(0, cs[0]);
       if (rc[0] != IG_OK) msg[0] = g_last_error;
-      w.wait();
+      w->wait();
+      release_worker(w);
     }
     for (int i = 0; i < 2; ++i) {
       cudaEventRecord(ev[i], cs[i]);
@@ -921,6 +935,162 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
     m->thr = m->mu - scaled;
   }
   IG_CHECK(read_status(d_status.p, s, "ig_fit"));
+  guard.m = nullptr;
+  *out = m;
+  return IG_OK;
+}
+
+int ig_fit_batched(const ig_problem* problems, int32_t n_problems, const ig_params* params,
+                   int32_t lanes, ig_model** out, ig_stream_t stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (n_problems < 0 || (n_problems > 0 && (!problems || !out)))
+    return fail(IG_E_INVAL, "ig_fit_batched: bad arguments");
+  for (int32_t i = 0; i < n_problems; ++i) out[i] = nullptr;
+  if (n_problems == 0) return IG_OK;
+  if (lanes <= 0) lanes = 8;
+  if (lanes > n_problems) lanes = n_problems;
+  // Largest problems first (pairs grow as n^2), each lane pulling the next.
+  std::vector<int32_t> order(n_problems);
+  for (int32_t i = 0; i < n_problems; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return problems[a].n > problems[b].n || (problems[a].n == problems[b].n && a < b);
+  });
+  int dev = 0;
+  IG_CUDA(cudaGetDevice(&dev), "ig_fit_batched");
+  cudaEvent_t ready = nullptr;
+  IG_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming), "ig_fit_batched");
+  IG_CUDA(cudaEventRecord(ready, s), "ig_fit_batched");
+  std::atomic<int32_t> next{0};
+  std::mutex err_mu;
+  int first_rc = IG_OK;
+  std::string first_msg;
+  std::vector<cudaStream_t> ls(lanes, nullptr);
+  std::vector<cudaEvent_t> done(lanes, nullptr);
+  for (int l = 0; l < lanes; ++l) {
+    IG_CUDA(cudaStreamCreateWithFlags(&ls[l], cudaStreamNonBlocking), "ig_fit_batched");
+    IG_CUDA(cudaEventCreateWithFlags(&done[l], cudaEventDisableTiming), "ig_fit_batched");
+    IG_CUDA(cudaStreamWaitEvent(ls[l], ready, 0), "ig_fit_batched");
+  }
+  auto lane = [&](int l) {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int32_t k = next.fetch_add(1);
+      if (k >= n_problems) break;
+      const ig_problem& pr = problems[order[k]];
+      const int rc = ig_fit(pr.rows, pr.labels, pr.n, pr.K, params, &out[order[k]],
+                            reinterpret_cast<ig_stream_t>(ls[l]));
+      if (rc != IG_OK) {
+        std::lock_guard<std::mutex> lk(err_mu);
+        if (first_rc == IG_OK) {
+          first_rc = rc;
+          first_msg = std::string("problem ") + std::to_string(order[k]) + ": " + g_last_error;
+        }
+      }
+    }
+    cudaEventRecord(done[l], ls[l]);
+  };
+  std::vector<Worker*> ws;
+  for (int l = 1; l < lanes; ++l) {
+    Worker* w = acquire_worker();
+    w->run([&, l] { lane(l); });
+    ws.push_back(w);
+  }
+  lane(0);
+  for (Worker* w : ws) {
+    w->wait();
+    release_worker(w);
+  }
+  for (int l = 0; l < lanes; ++l) {
+    cudaStreamWaitEvent(s, done[l], 0);
+    cudaEventDestroy(done[l]);
+    cudaStreamDestroy(ls[l]);
+  }
+  cudaEventDestroy(ready);
+  if (first_rc != IG_OK) {
+    for (int32_t i = 0; i < n_problems; ++i) {
+      ig_model_free(out[i]);
+      out[i] = nullptr;
+    }
+    g_last_error = first_msg;
+    return first_rc;
+  }
+  return IG_OK;
+}
+
+int ig_model_from_patterns(int32_t K, const uint64_t* const* words, const uint32_t* const* support,
+                           const int64_t* n_patterns, ig_model** out, ig_stream_t stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!out || !words || !support || !n_patterns)
+    return fail(IG_E_INVAL, "ig_model_from_patterns: NULL argument");
+  *out = nullptr;
+  if (K < 1 || K > IG_MAX_WORDS)
+    return fail(IG_E_INVAL, "ig_model_from_patterns: K = %d out of range", K);
+  const int KT = igk::padded_words(K);
+  ig_model* m = new ig_model;
+  struct ModelGuard {
+    ig_model* m;
+    ~ModelGuard() { model_release(m); }
+  } guard{m};
+  m->K = K;
+  m->KT = KT;
+  DevBuf<int> d_status;
+  IG_CUDA(d_status.alloc(1, s), "ig_model_from_patterns");
+  IG_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), s), "ig_model_from_patterns");
+  for (int c = 0; c < 2; ++c) {
+    const int64_t P = n_patterns[c];
+    if (P < 0 || (P > 0 && (!words[c] || !support[c])))
+      return fail(IG_E_INVAL, "ig_model_from_patterns: bad class %d arrays", c);
+    if (P > int64_t(0xffffffffll)) return fail(IG_E_OVERFLOW, "ig_model_from_patterns: too many");
+    m->n_pat[c] = P;
+    const size_t npad = size_t(std::max<int64_t>(1, igk::pad_rows(P)));
+    InputView<uint64_t> in_w;
+    InputView<uint32_t> in_f;
+    IG_CHECK(in_w.bind(words[c], size_t(P) * K, s, "ig_model_from_patterns: words"));
+    IG_CHECK(in_f.bind(support[c], size_t(P), s, "ig_model_from_patterns: supports"));
+    DevBuf<uint64_t> raw, work;
+    IG_CUDA(raw.alloc(npad * KT, s), "ig_model_from_patterns");
+    IG_CUDA(work.alloc(npad * KT, s), "ig_model_from_patterns");
+    IG_CUDA(cudaMemsetAsync(raw.p, 0, npad * KT * 8, s), "ig_model_from_patterns");
+    if (P)
+      IG_CUDA(cudaMemcpy2DAsync(raw.p, KT * 8, in_w.d, K * 8, K * 8, P, cudaMemcpyDeviceToDevice, s),
+              "ig_model_from_patterns");
+    IG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&m->words_kt[c]), npad * KT * 8, s),
+            "ig_model_from_patterns");
+    IG_CUDA(cudaMemsetAsync(m->words_kt[c], 0, npad * KT * 8, s), "ig_model_from_patterns");
+    IG_CUDA(cudaMemcpyAsync(work.p, raw.p, npad * KT * 8, cudaMemcpyDeviceToDevice, s),
+            "ig_model_from_patterns");
+    {
+      ProfScope ps(S_SORT, s);
+      IG_CUDA(igk::canonical_sort(work.p, P, KT, m->words_kt[c], work.p, s),
+              "ig_model_from_patterns: sort");
+    }
+    IG_CUDA(igk::launch_check_strict(m->words_kt[c], P, KT, d_status.p, s),
+            "ig_model_from_patterns");
+    IG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&m->support[c]),
+                            sizeof(uint32_t) * std::max<int64_t>(1, P), s),
+            "ig_model_from_patterns");
+    IG_CUDA(igk::launch_place_payload(m->words_kt[c], P, KT, raw.p, in_f.d, m->support[c],
+                                      d_status.p, s),
+            "ig_model_from_patterns");
+    IG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&m->score[c]), sizeof(uint64_t) * npad, s),
+            "ig_model_from_patterns");
+    IG_CUDA(cudaMemsetAsync(m->score[c], 0, sizeof(uint64_t) * npad, s), "ig_model_from_patterns");
+    IG_CUDA(igk::launch_pattern_score(m->words_kt[c], P, KT, m->support[c], m->score[c], s),
+            "ig_model_from_patterns: score");
+    if (K == KT) {
+      m->words[c] = m->words_kt[c];
+    } else {
+      IG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&m->words[c]),
+                              sizeof(uint64_t) * std::max<int64_t>(1, P) * K, s),
+              "ig_model_from_patterns");
+      if (P)
+        IG_CUDA(cudaMemcpy2DAsync(m->words[c], K * 8, m->words_kt[c], KT * 8, K * 8, P,
+                                  cudaMemcpyDeviceToDevice, s),
+                "ig_model_from_patterns");
+    }
+    IG_CHECK(read_status(d_status.p, s, "ig_model_from_patterns"));
+  }
+  m->subset_kernel = KT >= 2 ? 3 : 1;
   guard.m = nullptr;
   *out = m;
   return IG_OK;
@@ -1000,7 +1170,9 @@ int ig_score(const ig_model* m, const uint64_t* rows, int64_t n_rows, int64_t* A
   IG_CUDA(cudaMemsetAsync(A.d, 0, sizeof(unsigned long long) * n_rows, s), "ig_score");
   IG_CUDA(cudaMemsetAsync(N.d, 0, sizeof(unsigned long long) * n_rows, s), "ig_score");
   DevBuf<uint8_t> test_img;
-  const bool pruned = m->subset_kernel == 3;
+  // The item index pays for its build (and its host round trips) only on
+  // batches of some size; smaller batches stream the patterns densely.
+  const bool pruned = m->subset_kernel == 3 && n_rows >= kIndexMinRows;
   bool tc = m->subset_kernel >= 2 && igk::tc_supported(m->KT) && m->pat_img[0] && m->pat_img[1];
   bool done[2] = {false, false};
   IndexHolder test_idx;

@@ -225,10 +225,19 @@ cudaError_t launch_labels(const unsigned long long* A, const unsigned long long*
                           cudaStream_t s);
 
 // ---- sort.cu ----------------------------------------------------------------
-// Canonical order of n distinct keys (stride KT): ascending as KT-word
+// Canonical order of n keys (stride KT): ascending as KT-word
 // unsigned integers, word KT-1 most significant.  keys_out (n rows) receives
 // the sorted rows; `work` must hold n rows as well.
 cudaError_t canonical_sort(const uint64_t* keys, int64_t n, int KT, uint64_t* keys_out,
                            uint64_t* work, cudaStream_t s);
+
+// payload_sorted[pos of keys[i] in sorted] = payload[i] (binary search;
+// ST_BAD_INPUT if a key is missing).  sorted and keys: n rows, stride KT.
+cudaError_t launch_place_payload(const uint64_t* sorted, int64_t n, int KT, const uint64_t* keys,
+                                 const uint32_t* payload, uint32_t* payload_sorted, int* status,
+                                 cudaStream_t s);
+// ST_BAD_INPUT if a sorted list holds an empty row or a repeated row.
+cudaError_t launch_check_strict(const uint64_t* sorted, int64_t n, int KT, int* status,
+                                cudaStream_t s);
 
 }  // namespace igk

@@ -4,13 +4,14 @@
 // across runs (the paper's requirement that GPU and CPU pattern evidence
 // agree exactly, Section 4).
 //
-// The keys are distinct (they come from a set), which keeps the sort simple:
 //  1. each block sorts a tile of T keys held in shared memory with a bitonic
 //     network over 16-bit indices (full KT-word comparisons);
 //  2. merge passes double the sorted run length: every key finds its output
 //     slot directly as (its index in its own run) + (number of keys of the
-//     partner run below it), the latter by binary search.  With distinct keys
-//     these slots form a permutation, so no merge-path partitioning is needed.
+//     partner run before it), the latter by binary search -- keys of the
+//     right run count equal keys of the left run as before them -- so the
+//     slots form a permutation without merge-path partitioning, also when
+//     keys repeat.
 #include "common.cuh"
 #include "internal.h"
 
@@ -85,12 +86,18 @@ __global__ void merge_pass_kernel(const uint64_t* __restrict__ in, uint64_t* __r
   uint64_t key[KT];
 #pragma unroll
   for (int k = 0; k < KT; ++k) key[k] = in[e * KT + k];
+  // A key of the left run goes before equal keys of the right run: it counts
+  // the partner's keys strictly below it, a right-run key those not above it
+  // (a stable merge, so equal keys cannot collide on one slot).
+  const bool left = (r & 1) == 0;
   int64_t below = 0;
   if (o_lo < n) {
     int64_t lo = o_lo, hi = o_hi;
     while (lo < hi) {
       const int64_t mid = (lo + hi) >> 1;
-      if (key_less<KT>(in + mid * KT, key))
+      const bool before = left ? key_less<KT>(in + mid * KT, key)
+                               : !key_less<KT>(key, in + mid * KT);
+      if (before)
         lo = mid + 1;
       else
         hi = mid;
@@ -126,6 +133,67 @@ static cudaError_t sort_t(const uint64_t* keys, int64_t n, uint64_t* keys_out, u
     other = t;
   }
   return cudaSuccess;
+}
+
+// payload_sorted[position of keys[i] in sorted] = payload[i], found by
+// binary search (sorted holds the same rows in canonical order, distinct).
+template <int KT>
+__global__ void place_payload_kernel(const uint64_t* __restrict__ sorted, int64_t n,
+                                     const uint64_t* __restrict__ keys,
+                                     const uint32_t* __restrict__ payload,
+                                     uint32_t* __restrict__ payload_sorted, int* status) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t key[KT];
+#pragma unroll
+  for (int k = 0; k < KT; ++k) key[k] = keys[i * KT + k];
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (key_less<KT>(sorted + mid * KT, key))
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  if (lo >= n || key_less<KT>(key, sorted + lo * KT)) {
+    set_status(status, ST_BAD_INPUT);
+    return;
+  }
+  payload_sorted[lo] = payload[i];
+}
+
+// Flags (ST_BAD_INPUT) an empty row or two equal neighbours in a sorted list.
+template <int KT>
+__global__ void check_strict_kernel(const uint64_t* __restrict__ sorted, int64_t n, int* status) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  bool empty = true, same = i + 1 < n;
+#pragma unroll
+  for (int k = 0; k < KT; ++k) {
+    const uint64_t w = sorted[i * KT + k];
+    empty &= w == 0ull;
+    if (i + 1 < n) same &= w == sorted[(i + 1) * KT + k];
+  }
+  if (empty || same) set_status(status, ST_BAD_INPUT);
+}
+
+cudaError_t launch_place_payload(const uint64_t* sorted, int64_t n, int KT, const uint64_t* keys,
+                                 const uint32_t* payload, uint32_t* payload_sorted, int* status,
+                                 cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  IG_DISPATCH_KT(KT, (place_payload_kernel<KTC><<<unsigned(ceil_div(n, 256)), 256, 0, s>>>(
+                         sorted, n, keys, payload, payload_sorted, status)));
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_strict(const uint64_t* sorted, int64_t n, int KT, int* status,
+                                cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  IG_DISPATCH_KT(KT, (check_strict_kernel<KTC><<<unsigned(ceil_div(n, 256)), 256, 0, s>>>(
+                         sorted, n, status)));
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t canonical_sort(const uint64_t* keys, int64_t n, int KT, uint64_t* keys_out,

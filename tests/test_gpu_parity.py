@@ -104,6 +104,15 @@ def test_encode_ragged_and_wide():
     assert tuple(empty.shape) == (0, (int(cards.astype(int).sum()) + 63) // 64)
 
 
+def test_encode_missing_values():
+    rng = np.random.default_rng(4)
+    cards = np.array([16] * 32, np.uint16)
+    codes = rng.integers(0, 16, size=(300, 32)).astype(np.uint16)
+    codes[rng.random(codes.shape) < 0.4] = 0xFFFF
+    got = ig.ig_encode(dev(codes), cards)
+    assert np.array_equal(host(got, np.uint64), oracle.encode(codes, cards))
+
+
 def test_encode_rejects_out_of_range_code():
     codes = np.array([[0, 1], [2, 5]], np.uint16)
     with pytest.raises(ig.IGError) as e:
@@ -350,3 +359,31 @@ def test_nsl148k_parity_sampled_scores():
     assert np.array_equal(host(A, np.int64)[idx], oA)
     assert np.array_equal(host(N, np.int64)[idx], oN)
     assert np.array_equal(host(lab, np.uint8)[idx], olab)
+
+
+# ---- batched problems -------------------------------------------------------
+
+def test_batched_fit_matches_single_fits_and_oracle():
+    probs = igdata.batched(14)
+    enc = []
+    for w in probs:
+        enc.append((ig.ig_encode(dev(w.train_codes), w.cards), dev(w.train_labels)))
+    batched = ig.ig_fit_batched(enc, lanes=5)
+    widths = set()
+    for i, (w, mb) in enumerate(zip(probs, batched)):
+        single = ig.ig_fit(*enc[i])
+        for cls in (0, 1):
+            assert all(np.array_equal(x, y) for x, y in zip(mb.patterns(cls), single.patterns(cls)))
+        widths.add(w.meta["width"])
+        if w.train_codes.shape[0] <= 2500:          # oracle on the smaller problems
+            om = oracle.fit(oracle.encode(w.train_codes, w.cards), w.train_labels)
+            assert_model_equal(mb, om)
+            assert_scores_equal(mb, om, oracle.encode(w.test_codes, w.cards))
+    assert len(widths) >= 3
+
+
+def test_batched_fit_reports_failing_problem():
+    good = (np.array([[1], [2], [3]], np.uint64), np.array([1, 0, 1], np.uint8))
+    bad = (np.array([[1], [2]], np.uint64), np.array([1, 1], np.uint8))   # one class only
+    with pytest.raises(ig.IGError, match="problem 1"):
+        ig.ig_fit_batched([good, bad, good])

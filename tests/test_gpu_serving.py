@@ -1,0 +1,112 @@
+"""Serving: patterns given from outside, the continuous-batching server, and
+the batched fit -- all against ig_score / ig_fit and the CPU oracle.
+"""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import igdata
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2507_14222_gb300 as ig  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def served():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ig.build()
+    sw = igdata.served(per_class=30000, total_flows=24000, seed=77)
+    words = [ig.ig_encode(sw.patterns[c], sw.cards) for c in (0, 1)]   # host path
+    model = ig.ig_model_from_patterns(words[0], sw.support[0], words[1], sw.support[1])
+    flows = ig.ig_encode(sw.flow_codes, sw.cards)
+    return sw, words, model, flows
+
+
+def test_model_from_patterns_matches_oracle(served):
+    sw, words, model, flows = served
+    pats, sups, scos = {}, {}, {}
+    for c in (0, 1):
+        order = np.lexsort(words[c].T)   # canonical: word K-1 most significant
+        w, f, s = model.patterns(c)
+        assert np.array_equal(w, words[c][order])
+        assert np.array_equal(f, sw.support[c][order])
+        items = np.unpackbits(w.view(np.uint8), axis=1).sum(1).astype(np.uint64)
+        assert np.array_equal(s, f.astype(np.uint64) * items * items)     # Eq. 2
+        pats[c], sups[c], scos[c] = w, f, s
+    om = oracle.Model(8, pats, sups, scos, {0: 0, 1: 0}, None)
+    A, N, lab = ig.ig_score(model, flows[:3000])
+    oA, oN, olab = oracle.score(om, flows[:3000])
+    assert np.array_equal(A, oA) and np.array_equal(N, oN) and np.array_equal(lab, olab)
+
+
+def test_model_from_patterns_rejects_duplicates():
+    rows = np.array([[3], [5], [3]], np.uint64)
+    with pytest.raises(ig.IGError) as e:
+        ig.ig_model_from_patterns(rows, np.ones(3, np.uint32), rows[:1], np.ones(1, np.uint32))
+    assert e.value.code == -1
+
+
+@pytest.mark.parametrize("rows", [7, 900])   # dense (small batch) and item-index scoring
+def test_small_and_large_batches_agree(served, rows):
+    sw, words, model, flows = served
+    A, N, lab = ig.ig_score(model, flows[:rows])
+    A2, N2, lab2 = ig.ig_score(model, torch.from_numpy(flows[:rows].view(np.int64)).cuda())
+    assert np.array_equal(A, A2.cpu().numpy()) and np.array_equal(N, N2.cpu().numpy())
+    assert np.array_equal(lab, lab2.cpu().numpy())
+
+
+def _serve(model, reqs, pause_s, slots=3, cap=8192, budget=64 << 20):
+    server = ig.Server(model, slots=slots, max_batch_flows=cap, memory_budget_bytes=budget)
+    tickets = []
+
+    def submit_all():
+        for r in reqs:
+            tickets.append(server.submit(r))
+            if pause_s:
+                time.sleep(pause_s)
+    th = threading.Thread(target=submit_all)
+    th.start()
+    th.join()
+    outs = [server.wait(t) for t in tickets]
+    stats = server.stats()
+    server.close()
+    return outs, stats
+
+
+@pytest.mark.parametrize("pause_s", [0.0, 0.0003], ids=["burst", "paced"])
+def test_server_results_same_alone_and_in_the_mix(served, pause_s):
+    sw, words, model, flows = served
+    refA, refN, reflab = ig.ig_score(model, flows)
+    offs = np.concatenate([[0], np.cumsum(sw.request_sizes)])
+    reqs = [flows[offs[i]:offs[i + 1]] for i in range(len(sw.request_sizes))]
+    outs, (batches, scored) = _serve(model, reqs, pause_s)
+    assert scored == flows.shape[0]
+    if pause_s == 0.0:
+        assert batches < len(reqs)                # a burst is batched together
+    for i, (A, N, lab, ms) in enumerate(outs):
+        sl = slice(offs[i], offs[i + 1])
+        assert np.array_equal(A, refA[sl]) and np.array_equal(N, refN[sl])
+        assert np.array_equal(lab, reflab[sl])
+        assert ms >= 0
+    # Alone: a request scored by itself gives the same numbers.
+    for i in (0, len(reqs) // 2, len(reqs) - 1):
+        A, N, lab = ig.ig_score(model, reqs[i])
+        assert np.array_equal(A, outs[i][0]) and np.array_equal(lab, outs[i][2])
+
+
+def test_server_memory_admission(served):
+    # A budget of a few requests' worth still serves everything, exactly.
+    sw, words, model, flows = served
+    offs = np.concatenate([[0], np.cumsum(sw.request_sizes)])
+    reqs = [flows[offs[i]:offs[i + 1]] for i in range(len(sw.request_sizes))]
+    outs, (batches, scored) = _serve(model, reqs, 0.0, budget=4096 * 9000)
+    refA, _, reflab = ig.ig_score(model, flows)
+    assert scored == flows.shape[0]
+    assert np.array_equal(np.concatenate([o[0] for o in outs]), refA)
+    assert np.array_equal(np.concatenate([o[2] for o in outs]), reflab)

@@ -127,6 +127,12 @@ def test_encode_closed_form():
         oracle.encode(np.array([[3, 0, 0]], np.uint16), cards)
 
 
+def test_encode_missing_value_has_no_item():
+    cards = np.array([3, 70, 11], np.uint16)
+    codes = np.array([[2, 0xFFFF, 10], [0xFFFF, 0xFFFF, 0xFFFF]], np.uint16)
+    assert _ints(oracle.encode(codes, cards)) == [(1 << 2) | (1 << 83), 0]
+
+
 def test_encode_one_hot_properties():
     w = igdata.nsl15k()
     rows = oracle.encode(w.train_codes[:500], w.cards)
