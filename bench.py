@@ -336,9 +336,13 @@ def run_batched(args, ig, torch, rank, world, local):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    ig.prof_reset()
+    ig.prof_enable(True)
     with ClockSampler(local) as clk:
         ms_b, models_b = timed(True, args.steps)
     launches = ig.launch_count() - launches0
+    ig.prof_enable(False)
+    stages = ig.prof_read()
     ms_s, models_s = timed(False, max(1, min(args.steps, 3)))
     identical = True
     total_tests = 0
@@ -370,6 +374,8 @@ def run_batched(args, ig, torch, rank, world, local):
         "per_problem_launch_ms_per_step": statistics.median(ms_s),
         "speedup_vs_per_problem": statistics.median(ms_s) / statistics.median(ms_b),
         "identical_to_per_problem": bool(identical),
+        "stages_ms_per_step (summed over concurrent lanes)":
+            {k: round(v[0] / args.steps, 3) for k, v in stages.items() if v[1]},
         "gpu_launches": int(launches), "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)

@@ -364,11 +364,16 @@ struct ig_model {
   int64_t coh_tests_tc[2] = {0, 0};            // ... of which on the tensor cores
   int64_t coh_tests_pruned[2] = {0, 0};        // ... of which through the item index
   int64_t sup_tests[2] = {0, 0};               // support tests executed
+  igk::KeyedIndex* pidx[2] = {nullptr, nullptr};  // patterns by key item, for scoring
 };
 
 static void model_release(ig_model* m) {
   if (!m) return;
   for (int c = 0; c < 2; ++c) {
+    if (m->pidx[c]) {
+      igk::release_keyed_index(m->pidx[c], nullptr);
+      delete m->pidx[c];
+    }
     if (m->pat_img[c]) cudaFree(m->pat_img[c]);
     if (m->words[c] && m->words[c] != m->words_kt[c]) cudaFree(m->words[c]);
     if (m->words_kt[c]) cudaFree(m->words_kt[c]);
@@ -376,6 +381,35 @@ static void model_release(ig_model* m) {
     if (m->score[c]) cudaFree(m->score[c]);
   }
   delete m;
+}
+
+// Files both classes' patterns under their key items for scoring: the key
+// of a pattern is its item held by the fewest records according to freq
+// (device, 64K entries).  Any choice keeps scoring exact; this one keeps the
+// item-index work small for records like those freq was counted on.
+static cudaError_t build_pattern_indexes(ig_model* m, const uint32_t* freq, cudaStream_t s) {
+  for (int c = 0; c < 2; ++c) {
+    if (m->n_pat[c] == 0) continue;
+    igk::KeyedIndex* k = new igk::KeyedIndex;
+    cudaError_t e = igk::build_keyed_index(m->words_kt[c], m->n_pat[c], m->KT, m->K, m->KT, freq,
+                                           m->score[c], k, s);
+    if (e != cudaSuccess) {
+      delete k;
+      return e;
+    }
+    m->pidx[c] = k;
+  }
+  return cudaSuccess;
+}
+
+// Item counts over the patterns of both classes (for models whose records
+// are not at hand).
+static cudaError_t pattern_item_freq(const ig_model* m, uint32_t* freq, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(freq, 0, sizeof(uint32_t) * 64 * m->K, s);
+  for (int c = 0; c < 2 && e == cudaSuccess; ++c)
+    if (m->n_pat[c])
+      e = igk::launch_item_histogram(m->words_kt[c], m->n_pat[c], m->KT, m->K, 64 * m->K, freq, s);
+  return e;
 }
 
 void igk::model_view(const ig_model* m, igk::ModelView* v) {
@@ -449,9 +483,22 @@ int build_candidates(const uint64_t* X, int64_t n, int KT, cudaStream_t s, int* 
             "ig_fit");
     IG_CUDA(cudaStreamSynchronize(s), "ig_fit");
     if (h_counters->failed_band == kNoBand) break;
-    // Grow: a table twice the size holds the keys stored so far at a
-    // quarter load; replay from the first band that ran out of room.
-    const uint64_t ncap = cap << 1;
+    // Grow, then replay from the first band that ran out of room.  The bands
+    // before it held `pairs_before` pairs and gave `count` keys; the new table
+    // is sized for twice the count projected at that rate over all pairs
+    // (at least doubling), so that one growth is usually enough.
+    const int64_t failed = h_counters->failed_band;
+    const int64_t T = igk::kPairTile, nt = igk::ceil_div(n, T);
+    int64_t pairs_before = 0, pairs_all = 0;  // tile-granular pair counts
+    for (int64_t r = 0; r < nt; ++r) {
+      const int64_t band = (nt - r) * T * T;
+      pairs_all += band;
+      if (r < failed) pairs_before += band;
+    }
+    const double rate = double(h_counters->count) / double(std::max<int64_t>(1, pairs_before));
+    const double projected = std::min(double(pairs), rate * double(pairs_all)) * 1.25;
+    uint64_t ncap = cap << 1;
+    while (double(ncap) < 2.0 * projected && ncap < (uint64_t(1) << 36)) ncap <<= 1;
     DevBuf<uint64_t> nslots;
     DevBuf<TableCounters> nctr;
     IG_CUDA(nslots.alloc(ncap, s), "ig_fit: hash table");
@@ -934,6 +981,19 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
     const double scaled = prm.r * m->sigma;
     m->thr = m->mu - scaled;
   }
+  // Scoring's pattern index, keyed by the training records' item counts.
+  if (pruned && rec_idx[0].idx.usable && rec_idx[1].idx.usable) {
+    const int L = 64 * K;
+    std::vector<uint32_t> f(L);
+    for (int l = 0; l < L; ++l)
+      f[l] = (rec_idx[0].idx.h_off[l + 1] - rec_idx[0].idx.h_off[l]) +
+             (rec_idx[1].idx.h_off[l + 1] - rec_idx[1].idx.h_off[l]);
+    DevBuf<uint32_t> d_f;
+    IG_CUDA(d_f.alloc(L, s), "ig_fit");
+    IG_CUDA(cudaMemcpyAsync(d_f.p, f.data(), sizeof(uint32_t) * L, cudaMemcpyHostToDevice, s),
+            "ig_fit");
+    IG_CUDA(build_pattern_indexes(m, d_f.p, s), "ig_fit: pattern index");
+  }
   IG_CHECK(read_status(d_status.p, s, "ig_fit"));
   guard.m = nullptr;
   *out = m;
@@ -1091,6 +1151,12 @@ int ig_model_from_patterns(int32_t K, const uint64_t* const* words, const uint32
     IG_CHECK(read_status(d_status.p, s, "ig_model_from_patterns"));
   }
   m->subset_kernel = KT >= 2 ? 3 : 1;
+  if (KT >= 2) {
+    DevBuf<uint32_t> d_f;
+    IG_CUDA(d_f.alloc(64 * K, s), "ig_model_from_patterns");
+    IG_CUDA(pattern_item_freq(m, d_f.p, s), "ig_model_from_patterns");
+    IG_CUDA(build_pattern_indexes(m, d_f.p, s), "ig_model_from_patterns: pattern index");
+  }
   guard.m = nullptr;
   *out = m;
   return IG_OK;
@@ -1187,6 +1253,18 @@ int ig_score(const ig_model* m, const uint64_t* rows, int64_t n_rows, int64_t* A
         continue;
       }
       int64_t t = 0;
+      // Small batches reuse the model's pattern index; larger ones re-key
+      // the patterns by the batch's own item counts (fewer tests, and
+      // patterns holding an item absent from the batch drop out at once).
+      if (m->pidx[c] && n_rows * 8 < m->n_pat[c]) {
+        IG_CUDA(igk::indexed_subset_prebuilt(igk::MODE_SUM, test_idx.idx, *m->pidx[c], nullptr,
+                                             c == 1 ? A.d : N.d, d_status.p, &t, S_EVIDENCE_IDX,
+                                             s),
+                "ig_score: evidence");
+        done[c] = true;
+        igk::prof_add_work(S_EVIDENCE_IDX, t);
+        continue;
+      }
       igk::IndexedArgs a;
       a.mode = igk::MODE_SUM;
       a.index = &test_idx.idx;
@@ -1340,6 +1418,18 @@ int ig_model_load(const char* path, ig_model** out) {
   if (!ok) {
     model_release(m);
     return fail(IG_E_IO, "ig_model_load: %s is truncated", path);
+  }
+  if (m->KT >= 2) {
+    uint32_t* d_f = nullptr;
+    cudaError_t e = cudaMalloc(&d_f, sizeof(uint32_t) * 64 * m->K);
+    if (e == cudaSuccess) e = pattern_item_freq(m, d_f, nullptr);
+    if (e == cudaSuccess) e = build_pattern_indexes(m, d_f, nullptr);
+    if (d_f) cudaFree(d_f);
+    if (e != cudaSuccess) {
+      model_release(m);
+      return fail_cuda(e, "ig_model_load: pattern index");
+    }
+    m->subset_kernel = 3;
   }
   *out = m;
   return IG_OK;

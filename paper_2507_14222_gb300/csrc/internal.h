@@ -148,7 +148,8 @@ cudaError_t launch_subset_tc(const TcArgs& a, cudaStream_t s);
 // ---- prune.cu (subset tests restricted by an item index) --------------------
 struct WorkItem {
   int64_t own_begin, own_count, str_begin, str_count;
-  int64_t own_keyed;  // 1: registers hold patterns (keyed rows), 0: records
+  int32_t own_keyed;  // 1: registers hold patterns (keyed rows), 0: records
+  int32_t q;          // own rows per thread (1, 2 or 4); 256 * q rows per block
 };
 struct GroupedArgs {
   int mode;
@@ -206,6 +207,30 @@ struct IndexedArgs {
   int prof_stage = -1;  // stage under which the grouped kernel is timed
 };
 cudaError_t indexed_subset(const IndexedArgs& a, cudaStream_t s);
+
+// The pattern side of the item index, built once and reusable: patterns
+// filed under their key item (the item with the smallest `freq`; group L
+// holds patterns with an item of freq 0).  Synchronizes the stream once.
+struct KeyedIndex {
+  int K = 0, KT = 0, L = 0;
+  int64_t n = 0;
+  uint64_t* rows = nullptr;   // grouped patterns, stride KT (+256 rows of padding)
+  uint32_t* ids = nullptr;    // original pattern of each grouped row
+  uint64_t* score = nullptr;  // S of each grouped pattern (when built with scores)
+  uint32_t* off = nullptr;    // group offsets, L + 2 entries
+  std::vector<uint32_t> h_off;
+};
+cudaError_t build_keyed_index(const uint64_t* keyed, int64_t n, int stride, int K, int KT,
+                              const uint32_t* freq, const uint64_t* score, KeyedIndex* out,
+                              cudaStream_t s);
+void release_keyed_index(KeyedIndex* k, cudaStream_t s);
+// indexed_subset with a prebuilt pattern side; no synchronization.
+cudaError_t indexed_subset_prebuilt(int mode, const RecordIndex& idx, const KeyedIndex& kx,
+                                    uint32_t* out_u32, unsigned long long* out_u64, int* status,
+                                    int64_t* tests_out, int prof_stage, cudaStream_t s);
+// freq[l] += number of the n rows holding item l (rows of stride `stride`, K words).
+cudaError_t launch_item_histogram(const uint64_t* rows, int64_t n, int stride, int K, int L,
+                                  uint32_t* freq, cudaStream_t s);
 
 // Keeps the rows whose flag is zero: out gets them (stride KT), out_count
 // the number kept (must start at 0).  With n_dev given, the row count is

@@ -208,16 +208,15 @@ struct GroupedParams {
 // to (patterns for ANY / COUNT, records for SUM) the result accumulates in
 // registers; otherwise every hit updates the streamed row's result directly
 // (atomics: hits are few).
-template <int KT, int MODE>
-__global__ void __launch_bounds__(kGThreads) grouped_subset_kernel(GroupedParams p) {
+template <int KT, int MODE, int Q>
+__device__ __forceinline__ void grouped_body(const GroupedParams& p, const WorkItem& wi,
+                                             uint8_t* smem) {
   using S = GShape<KT>;
-  constexpr int TR = S::TR, Q = S::Q, H = S::H;
+  constexpr int TR = S::TR, H = S::H;
   constexpr uint32_t kRowBytes = TR * KT * 8;
-  extern __shared__ __align__(128) uint8_t smem[];
   uint64_t* rows_s = reinterpret_cast<uint64_t*>(smem);
   uint64_t* bars = rows_s + kGStages * TR * KT;
 
-  const WorkItem wi = p.items[blockIdx.x];
   const bool own_keyed = wi.own_keyed != 0;
   // Results stay in registers when the own side is the result side.
   const bool own_result = (MODE == MODE_SUM) ? !own_keyed : own_keyed;
@@ -376,6 +375,20 @@ __global__ void __launch_bounds__(kGThreads) grouped_subset_kernel(GroupedParams
   }
 }
 
+// Each block holds 256 * q own rows, q = 1, 2 or 4 chosen per work item
+// from the size of its group (q never exceeds GShape<KT>::Q).
+template <int KT, int MODE>
+__global__ void __launch_bounds__(kGThreads) grouped_subset_kernel(GroupedParams p) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const WorkItem wi = p.items[blockIdx.x];
+  if (wi.q <= 1)
+    grouped_body<KT, MODE, 1>(p, wi, smem);
+  else if (wi.q == 2 || GShape<KT>::Q == 2)
+    grouped_body<KT, MODE, 2>(p, wi, smem);
+  else
+    grouped_body<KT, MODE, (GShape<KT>::Q >= 4 ? 4 : 2)>(p, wi, smem);
+}
+
 // ---- host side ----------------------------------------------------------------
 
 cudaError_t launch_item_histogram(const uint64_t* rows, int64_t n, int stride, int K, int L,
@@ -474,6 +487,7 @@ cudaError_t launch_grouped_subset(const GroupedArgs& a, cudaStream_t s) {
 void build_work_items(const uint32_t* keyed_off, const uint32_t* multi_off, int groups,
                       int own_tile, int str_tile, int64_t target, bool mode_sum,
                       std::vector<WorkItem>* items, int64_t* tests) {
+  const int max_q = own_tile / 256;
   items->clear();
   *tests = 0;
   for (int l = 0; l < groups; ++l) {
@@ -487,8 +501,12 @@ void build_work_items(const uint32_t* keyed_off, const uint32_t* multi_off, int 
     const int64_t no = own_keyed ? nk : nm, ns = own_keyed ? nm : nk;
     const int64_t o0 = own_keyed ? keyed_off[l] : multi_off[l];
     const int64_t s0 = own_keyed ? multi_off[l] : keyed_off[l];
-    for (int64_t o = 0; o < no; o += own_tile) {
-      const int64_t oc = std::min<int64_t>(own_tile, no - o);
+    // Rows per thread from the group's size: small groups use narrow blocks.
+    int q = 1;
+    while (q < max_q && 256 * q < no) q *= 2;
+    const int64_t tile = std::min<int64_t>(own_tile, 256 * q);
+    for (int64_t o = 0; o < no; o += tile) {
+      const int64_t oc = std::min<int64_t>(tile, no - o);
       int64_t per = std::max<int64_t>(str_tile, target / std::max<int64_t>(1, oc));
       per = ((per + str_tile - 1) / str_tile) * str_tile;
       for (int64_t r = 0; r < ns; r += per) {
@@ -498,6 +516,7 @@ void build_work_items(const uint32_t* keyed_off, const uint32_t* multi_off, int 
         w.str_begin = s0 + r;
         w.str_count = std::min<int64_t>(per, ns - r);
         w.own_keyed = own_keyed ? 1 : 0;
+        w.q = q;
         items->push_back(w);
       }
     }
@@ -571,85 +590,118 @@ struct Staging {
 thread_local Staging g_staging;
 }  // namespace
 
+void release_keyed_index(KeyedIndex* k, cudaStream_t s) {
+  for (void* p : {static_cast<void*>(k->rows), static_cast<void*>(k->ids),
+                  static_cast<void*>(k->score), static_cast<void*>(k->off)})
+    if (p) cudaFreeAsync(p, s);
+  k->rows = nullptr;
+  k->ids = nullptr;
+  k->score = nullptr;
+  k->off = nullptr;
+  k->n = 0;
+}
+
+cudaError_t build_keyed_index(const uint64_t* keyed, int64_t n, int stride, int K, int KT,
+                              const uint32_t* freq, const uint64_t* score, KeyedIndex* out,
+                              cudaStream_t s) {
+  *out = KeyedIndex();
+  out->K = K;
+  out->KT = KT;
+  out->L = 64 * K;
+  out->n = n;
+  const int L = out->L, groups = L + 1;
+  cudaError_t e;
+  uint32_t *kcount = nullptr, *key = nullptr;
+#define IG_K_TRY(x)                            \
+  if ((e = (x)) != cudaSuccess) {               \
+    if (kcount) cudaFreeAsync(kcount, s);      \
+    if (key) cudaFreeAsync(key, s);            \
+    release_keyed_index(out, s);               \
+    return e;                                  \
+  }
+  // kcount[groups] and cursor[groups] scratch; off[groups+1] kept.
+  IG_K_TRY(cudaMallocAsync(reinterpret_cast<void**>(&kcount), size_t(2 * groups) * 4, s));
+  IG_K_TRY(cudaMallocAsync(reinterpret_cast<void**>(&out->off), size_t(groups + 1) * 4, s));
+  IG_K_TRY(cudaMallocAsync(reinterpret_cast<void**>(&key), size_t(std::max<int64_t>(1, n)) * 4, s));
+  IG_K_TRY(cudaMemsetAsync(kcount, 0, size_t(2 * groups) * 4, s));
+  IG_K_TRY(cudaMallocAsync(reinterpret_cast<void**>(&out->rows), size_t(n + 256) * KT * 8, s));
+  IG_K_TRY(cudaMallocAsync(reinterpret_cast<void**>(&out->ids), size_t(std::max<int64_t>(1, n)) * 4, s));
+  if (score)
+    IG_K_TRY(cudaMallocAsync(reinterpret_cast<void**>(&out->score), size_t(n + 256) * 8, s));
+  void* tok = prof_begin(kStageIndexBuild, s);
+  IG_K_TRY(launch_key_item(keyed, n, stride, K, L, freq, key, kcount, s));
+  IG_K_TRY(launch_small_scan(kcount, groups, out->off, s));
+  IG_K_TRY(launch_keyed_scatter(keyed, n, stride, K, KT, groups, key, out->off, kcount + groups,
+                                out->rows, out->ids, score, out->score, s));
+  prof_end(tok);
+  out->h_off.assign(groups + 1, 0u);
+  IG_K_TRY(cudaMemcpyAsync(out->h_off.data(), out->off, (groups + 1) * 4, cudaMemcpyDeviceToHost, s));
+  IG_K_TRY(cudaStreamSynchronize(s));
+  cudaFreeAsync(kcount, s);
+  cudaFreeAsync(key, s);
+#undef IG_K_TRY
+  return cudaSuccess;
+}
+
+cudaError_t indexed_subset_prebuilt(int mode, const RecordIndex& idx, const KeyedIndex& kx,
+                                    uint32_t* out_u32, unsigned long long* out_u64, int* status,
+                                    int64_t* tests_out, int prof_stage, cudaStream_t s) {
+  *tests_out = 0;
+  if (kx.n == 0 || idx.n_rows == 0) return cudaSuccess;
+  const int L = idx.L, KT = idx.KT;
+  std::vector<WorkItem> items;
+  int64_t tests = 0, total = 0;
+  for (int l = 0; l < L; ++l)
+    total += (int64_t(kx.h_off[l + 1]) - kx.h_off[l]) * (int64_t(idx.h_off[l + 1]) - idx.h_off[l]);
+  const int64_t target = std::max<int64_t>(total / (int64_t(num_sms()) * 8), 1 << 16);
+  build_work_items(kx.h_off.data(), idx.h_off.data(), L, grouped_own_per_cta(KT),
+                   grouped_rows_per_tile(KT), target, mode == MODE_SUM, &items, &tests);
+  *tests_out = tests;
+  if (items.empty()) return cudaSuccess;
+  cudaError_t e;
+  Staging& st = g_staging;
+  if (st.done && (e = cudaEventSynchronize(st.done)) != cudaSuccess) return e;
+  if (st.cap < items.size()) {
+    if (st.buf) cudaFreeHost(st.buf);
+    st.buf = nullptr;
+    st.cap = 0;
+    if ((e = cudaMallocHost(reinterpret_cast<void**>(&st.buf), items.size() * 2 * sizeof(WorkItem))) !=
+        cudaSuccess)
+      return e;
+    st.cap = items.size() * 2;
+  }
+  if (!st.done && (e = cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming)) != cudaSuccess)
+    return e;
+  std::copy(items.begin(), items.end(), st.buf);
+  WorkItem* d_items = nullptr;
+  if ((e = cudaMallocAsync(reinterpret_cast<void**>(&d_items), items.size() * sizeof(WorkItem), s)) !=
+      cudaSuccess)
+    return e;
+  e = cudaMemcpyAsync(d_items, st.buf, items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaEventRecord(st.done, s);
+  if (e == cudaSuccess) {
+    GroupedArgs g{mode,    KT,       d_items, int64_t(items.size()), kx.rows, kx.ids,
+                  kx.score, idx.rows, idx.ids, out_u32,               out_u64, status};
+    void* tok = prof_stage >= 0 ? prof_begin(prof_stage, s) : nullptr;
+    e = launch_grouped_subset(g, s);
+    prof_end(tok);
+  }
+  cudaFreeAsync(d_items, s);
+  return e;
+}
+
 cudaError_t indexed_subset(const IndexedArgs& a, cudaStream_t s) {
   *a.tests_out = 0;
   const RecordIndex& idx = *a.index;
   if (a.n_keyed == 0 || idx.n_rows == 0) return cudaSuccess;
-  const int L = idx.L, KT = idx.KT, K = idx.K;
-  const int groups = L + 1;
-  cudaError_t e;
-  std::vector<void*> bufs;
-  auto alloc = [&](void** p, size_t bytes) {
-    cudaError_t r = cudaMallocAsync(p, bytes ? bytes : 16, s);
-    if (r == cudaSuccess) bufs.push_back(*p);
-    return r;
-  };
-  auto done = [&](cudaError_t r) {
-    for (void* b : bufs) cudaFreeAsync(b, s);
-    return r;
-  };
-#define IG_P_TRY(x) \
-  if ((e = (x)) != cudaSuccess) return done(e);
-  uint32_t* small = nullptr;  // kcount[groups], koff[groups+1], cursor[groups]
-  IG_P_TRY(alloc(reinterpret_cast<void**>(&small), size_t(3 * groups + 1) * 4));
-  uint32_t* kcount = small;
-  uint32_t* koff = kcount + groups;
-  uint32_t* kcur = koff + (groups + 1);
-  uint32_t* key = nullptr;
-  IG_P_TRY(alloc(reinterpret_cast<void**>(&key), size_t(a.n_keyed) * 4));
-  IG_P_TRY(cudaMemsetAsync(small, 0, size_t(3 * groups + 1) * 4, s));
-  void* tok = prof_begin(kStageIndexBuild, s);
-  IG_P_TRY(launch_key_item(a.keyed, a.n_keyed, a.keyed_stride, K, L, idx.freq, key, kcount, s));
-  IG_P_TRY(launch_small_scan(kcount, groups, koff, s));
-  uint64_t *krows = nullptr, *kscore = nullptr;
-  uint32_t* kids = nullptr;
-  IG_P_TRY(alloc(reinterpret_cast<void**>(&krows), size_t(a.n_keyed + 256) * KT * 8));
-  IG_P_TRY(alloc(reinterpret_cast<void**>(&kids), size_t(a.n_keyed) * 4));
-  if (a.mode == MODE_SUM)
-    IG_P_TRY(alloc(reinterpret_cast<void**>(&kscore), size_t(a.n_keyed + 256) * 8));
-  IG_P_TRY(launch_keyed_scatter(a.keyed, a.n_keyed, a.keyed_stride, K, KT, groups, key, koff,
-                                kcur, krows, kids, a.mode == MODE_SUM ? a.keyed_score : nullptr,
-                                kscore, s));
-  prof_end(tok);
-  std::vector<uint32_t> h_koff(groups + 1);
-  IG_P_TRY(cudaMemcpyAsync(h_koff.data(), koff, (groups + 1) * 4, cudaMemcpyDeviceToHost, s));
-  IG_P_TRY(cudaStreamSynchronize(s));
-  // Work blocks of about 8 blocks per SM worth of tests each.
-  std::vector<WorkItem> items;
-  int64_t tests = 0;
-  int64_t total = 0;
-  for (int l = 0; l < L; ++l)
-    total += (int64_t(h_koff[l + 1]) - h_koff[l]) * (int64_t(idx.h_off[l + 1]) - idx.h_off[l]);
-  const int64_t target = std::max<int64_t>(total / (int64_t(num_sms()) * 8), 1 << 16);
-  build_work_items(h_koff.data(), idx.h_off.data(), L, grouped_own_per_cta(KT),
-                   grouped_rows_per_tile(KT), target, a.mode == MODE_SUM, &items, &tests);
-  *a.tests_out = tests;
-  if (!items.empty()) {
-    Staging& st = g_staging;
-    if (st.done) IG_P_TRY(cudaEventSynchronize(st.done));
-    if (st.cap < items.size()) {
-      if (st.buf) cudaFreeHost(st.buf);
-      st.buf = nullptr;
-      st.cap = 0;
-      IG_P_TRY(cudaMallocHost(reinterpret_cast<void**>(&st.buf), items.size() * 2 * sizeof(WorkItem)));
-      st.cap = items.size() * 2;
-    }
-    if (!st.done) IG_P_TRY(cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming));
-    std::copy(items.begin(), items.end(), st.buf);
-    WorkItem* d_items = nullptr;
-    IG_P_TRY(alloc(reinterpret_cast<void**>(&d_items), items.size() * sizeof(WorkItem)));
-    IG_P_TRY(cudaMemcpyAsync(d_items, st.buf, items.size() * sizeof(WorkItem),
-                             cudaMemcpyHostToDevice, s));
-    IG_P_TRY(cudaEventRecord(st.done, s));
-    GroupedArgs g{a.mode, KT,      d_items,   int64_t(items.size()), krows,   kids,
-                  kscore, idx.rows, idx.ids, a.out_u32,             a.out_u64, a.status};
-    void* gtok = a.prof_stage >= 0 ? prof_begin(a.prof_stage, s) : nullptr;
-    const cudaError_t ge = launch_grouped_subset(g, s);
-    prof_end(gtok);
-    IG_P_TRY(ge);
-  }
-#undef IG_P_TRY
-  return done(cudaSuccess);
+  KeyedIndex kx;
+  cudaError_t e = build_keyed_index(a.keyed, a.n_keyed, a.keyed_stride, idx.K, idx.KT, idx.freq,
+                                    a.mode == MODE_SUM ? a.keyed_score : nullptr, &kx, s);
+  if (e != cudaSuccess) return e;
+  e = indexed_subset_prebuilt(a.mode, idx, kx, a.out_u32, a.out_u64, a.status, a.tests_out,
+                              a.prof_stage, s);
+  release_keyed_index(&kx, s);
+  return e;
 }
 
 }  // namespace igk
