@@ -303,11 +303,24 @@ def run_batched(args, ig, torch, rank, world, local):
     def encode_all():
         return [(ig.ig_encode(c, cards), lab, ig.ig_encode(t, cards)) for c, lab, t, cards in dev]
 
+
+    # Tiling and subset-test form per (K, size) group, tuned once per GPU
+    # (cached), outside the timed region.
+    from paper_2507_14222_gb300 import autotune
+    tuner = autotune.Autotuner()
+    enc0 = encode_all_once = [(ig.ig_encode(c, cards), lab, ig.ig_encode(t, cards))
+                              for c, lab, t, cards in dev]
+    tuned = tuner.tune(enc0) if args.kernel == 0 else {}
+    per_params = [tuner.params_for(int(r.shape[1]), int(r.shape[0])) if args.kernel == 0
+                  else None for r, _, _ in enc0]
+    del encode_all_once
+
     def step(batched):
         enc = encode_all()
         if batched:
             models = ig.ig_fit_batched([(r, lab) for r, lab, _ in enc],
-                                       subset_kernel=args.kernel)
+                                       subset_kernel=args.kernel,
+                                       per_problem_params=per_params)
         else:
             models = [ig.ig_fit(r, lab, subset_kernel=args.kernel) for r, lab, _ in enc]
         for mdl, (_, _, te) in zip(models, enc):
@@ -374,6 +387,7 @@ def run_batched(args, ig, torch, rank, world, local):
         "per_problem_launch_ms_per_step": statistics.median(ms_s),
         "speedup_vs_per_problem": statistics.median(ms_s) / statistics.median(ms_b),
         "identical_to_per_problem": bool(identical),
+        "autotuned": tuned,
         "stages_ms_per_step (summed over concurrent lanes)":
             {k: round(v[0] / args.steps, 3) for k, v in stages.items() if v[1]},
         "gpu_launches": int(launches), "clocks": clk.summary(),

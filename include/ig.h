@@ -79,6 +79,13 @@ typedef struct {
    * pay off.  The choice is kept in the model and used by ig_score too.
    * Results are identical for every choice. */
   int32_t subset_kernel;
+  /* Tiling of the item-index form (results never depend on them; 0 picks
+   * the default): the most own rows per thread of a block (1, 2 or 4, i.e.
+   * blocks of up to 256, 512 or 1,024 rows; default 4), and the factor by
+   * which one side of an item group must outnumber the other before that
+   * side is held in registers instead of the result side (default 2). */
+  int32_t index_max_q;
+  int32_t index_flip_factor;
 } ig_params;
 
 typedef struct {
@@ -131,6 +138,7 @@ typedef struct {
   int64_t n;
   int32_t K;
   int32_t reserved;
+  const ig_params* params; /* this problem's parameters, or NULL for the batch's */
 } ig_problem;
 
 /* Batched IG training: fits n_problems independent problems (each exactly

@@ -41,7 +41,13 @@ class IGError(RuntimeError):
 
 class ig_params(ctypes.Structure):
     _fields_ = [("r", ctypes.c_double), ("reg3_enabled", ctypes.c_int32),
-                ("subset_kernel", ctypes.c_int32)]
+                ("subset_kernel", ctypes.c_int32), ("index_max_q", ctypes.c_int32),
+                ("index_flip_factor", ctypes.c_int32)]
+
+
+def make_params(r=None, subset_kernel=0, index_max_q=0, index_flip_factor=0) -> ig_params:
+    return ig_params(float(r) if r is not None else 0.0, 1 if r is not None else 0,
+                     int(subset_kernel), int(index_max_q), int(index_flip_factor))
 
 
 class ig_model_info_t(ctypes.Structure):
@@ -242,7 +248,7 @@ class Model:
 
 
 def ig_fit(rows, labels, r: float | None = None, subset_kernel: int = 0,
-           stream=None) -> Model:
+           stream=None, index_max_q: int = 0, index_flip_factor: int = 0) -> Model:
     """IG training (Section 3.1: Eq. 1, Eq. 3, Eq. 2; Regulation 3 if r given).
 
     rows: [n, K] packed records (CUDA int64 tensor or numpy uint64 array);
@@ -254,8 +260,7 @@ def ig_fit(rows, labels, r: float | None = None, subset_kernel: int = 0,
         rows = np.ascontiguousarray(rows, dtype=np.uint64)
     if not _is_torch(labels):
         labels = np.ascontiguousarray(labels, dtype=np.uint8)
-    prm = ig_params(float(r) if r is not None else 0.0, 1 if r is not None else 0,
-                    int(subset_kernel))
+    prm = make_params(r, subset_kernel, index_max_q, index_flip_factor)
     h = ctypes.c_void_p()
     _check(lib.ig_fit(_ptr(rows), _ptr(labels), n, K, ctypes.byref(prm),
                       ctypes.byref(h), _stream(stream) if _is_torch(rows) else None))
@@ -264,15 +269,18 @@ def ig_fit(rows, labels, r: float | None = None, subset_kernel: int = 0,
 
 class ig_problem(ctypes.Structure):
     _fields_ = [("rows", ctypes.c_void_p), ("labels", ctypes.c_void_p),
-                ("n", ctypes.c_int64), ("K", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("n", ctypes.c_int64), ("K", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("params", ctypes.c_void_p)]
 
 
 def ig_fit_batched(problems, r: float | None = None, subset_kernel: int = 0,
-                   lanes: int = 0, stream=None) -> list:
+                   lanes: int = 0, stream=None, per_problem_params=None) -> list:
     """Fits independent problems [(rows, labels), ...] concurrently.
 
     Each problem is fitted exactly as ig_fit would; returns one Model per
     problem, in order.  Arrays may be CUDA tensors or numpy arrays.
+    per_problem_params: optional list of ig_params (or None entries) that
+    override the batch parameters problem by problem.
     """
     lib = load()
     keep = []
@@ -287,9 +295,13 @@ def ig_fit_batched(problems, r: float | None = None, subset_kernel: int = 0,
         if not _is_torch(labels):
             labels = np.ascontiguousarray(labels, dtype=np.uint8)
         keep.append((rows, labels))
-        arr[i] = ig_problem(_ptr(rows), _ptr(labels), n, K, 0)
-    prm = ig_params(float(r) if r is not None else 0.0, 1 if r is not None else 0,
-                    int(subset_kernel))
+        pp = per_problem_params[i] if per_problem_params else None
+        if pp is not None:
+            keep.append(pp)
+        arr[i] = ig_problem(_ptr(rows), _ptr(labels), n, K, 0,
+                            ctypes.cast(ctypes.pointer(pp), ctypes.c_void_p) if pp is not None
+                            else None)
+    prm = make_params(r, subset_kernel)
     outs = (ctypes.c_void_p * max(1, len(problems)))()
     _check(lib.ig_fit_batched(arr, len(problems), ctypes.byref(prm), int(lanes), outs,
                               _stream(stream) if any_torch else None))

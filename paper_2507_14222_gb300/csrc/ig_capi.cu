@@ -365,6 +365,7 @@ struct ig_model {
   int64_t coh_tests_pruned[2] = {0, 0};        // ... of which through the item index
   int64_t sup_tests[2] = {0, 0};               // support tests executed
   igk::KeyedIndex* pidx[2] = {nullptr, nullptr};  // patterns by key item, for scoring
+  int index_max_q = 4, index_flip = 2;            // item-index tiling
 };
 
 static void model_release(ig_model* m) {
@@ -580,8 +581,12 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
   if (!rows || !labels || n < 2) return fail(IG_E_INVAL, "ig_fit: need at least two records");
   if (K < 1 || K > IG_MAX_WORDS) return fail(IG_E_INVAL, "ig_fit: K = %d out of range", K);
   if (n > int64_t(0x7fffffff)) return fail(IG_E_OVERFLOW, "ig_fit: too many records");
-  ig_params prm{0.0, 0, 0};
+  ig_params prm{0.0, 0, 0, 0, 0};
   if (params) prm = *params;
+  if (prm.index_max_q != 0 && prm.index_max_q != 1 && prm.index_max_q != 2 &&
+      prm.index_max_q != 4)
+    return fail(IG_E_INVAL, "ig_fit: index_max_q must be 0, 1, 2 or 4");
+  if (prm.index_flip_factor < 0) return fail(IG_E_INVAL, "ig_fit: negative index_flip_factor");
   if (prm.subset_kernel < 0 || prm.subset_kernel > 3)
     return fail(IG_E_INVAL, "ig_fit: unknown subset_kernel %d", prm.subset_kernel);
   if (prm.reg3_enabled && !std::isfinite(prm.r))
@@ -636,6 +641,8 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
   const bool pruned = (prm.subset_kernel == 0 || prm.subset_kernel == 3) && KT >= 2;
   const bool tc = prm.subset_kernel != 1 && igk::tc_supported(KT);
   m->subset_kernel = pruned ? 3 : (tc ? 2 : 1);
+  m->index_max_q = prm.index_max_q ? prm.index_max_q : 4;
+  m->index_flip = prm.index_flip_factor ? prm.index_flip_factor : 2;
   // Item indexes of both classes' records: used by the other class's
   // coherence, this class's support and (normal class) Regulation 3.
   IndexHolder rec_idx[2];
@@ -736,6 +743,8 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
           a.status = d_status.p;
           a.tests_out = &t;
           a.prof_stage = S_COHERENCE_IDX;
+          a.max_q = m->index_max_q;
+          a.flip_factor = m->index_flip;
           IG_CUDA(igk::indexed_subset(a, s), "ig_fit: coherence");
         }
         if (t >= 0) {
@@ -828,6 +837,8 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
         a.status = d_status.p;
         a.tests_out = &t;
         a.prof_stage = S_SUPPORT_IDX;
+        a.max_q = m->index_max_q;
+        a.flip_factor = m->index_flip;
         IG_CUDA(igk::indexed_subset(a, s), "ig_fit: support");
       }
       if (t >= 0) {
@@ -947,6 +958,8 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
       a.status = d_status.p;
       a.tests_out = &t_idx;
       a.prof_stage = S_EVIDENCE_IDX;
+      a.max_q = m->index_max_q;
+      a.flip_factor = m->index_flip;
       IG_CUDA(igk::indexed_subset(a, s), "ig_fit: Regulation 3 evidence");
     }
     if (t_idx >= 0) {
@@ -1037,8 +1050,8 @@ int ig_fit_batched(const ig_problem* problems, int32_t n_problems, const ig_para
       const int32_t k = next.fetch_add(1);
       if (k >= n_problems) break;
       const ig_problem& pr = problems[order[k]];
-      const int rc = ig_fit(pr.rows, pr.labels, pr.n, pr.K, params, &out[order[k]],
-                            reinterpret_cast<ig_stream_t>(ls[l]));
+      const int rc = ig_fit(pr.rows, pr.labels, pr.n, pr.K, pr.params ? pr.params : params,
+                            &out[order[k]], reinterpret_cast<ig_stream_t>(ls[l]));
       if (rc != IG_OK) {
         std::lock_guard<std::mutex> lk(err_mu);
         if (first_rc == IG_OK) {
@@ -1259,7 +1272,7 @@ int ig_score(const ig_model* m, const uint64_t* rows, int64_t n_rows, int64_t* A
       if (m->pidx[c] && n_rows * 8 < m->n_pat[c]) {
         IG_CUDA(igk::indexed_subset_prebuilt(igk::MODE_SUM, test_idx.idx, *m->pidx[c], nullptr,
                                              c == 1 ? A.d : N.d, d_status.p, &t, S_EVIDENCE_IDX,
-                                             s),
+                                             m->index_max_q, m->index_flip, s),
                 "ig_score: evidence");
         done[c] = true;
         igk::prof_add_work(S_EVIDENCE_IDX, t);
@@ -1277,6 +1290,8 @@ int ig_score(const ig_model* m, const uint64_t* rows, int64_t n_rows, int64_t* A
       a.status = d_status.p;
       a.tests_out = &t;
       a.prof_stage = S_EVIDENCE_IDX;
+      a.max_q = m->index_max_q;
+      a.flip_factor = m->index_flip;
       IG_CUDA(igk::indexed_subset(a, s), "ig_score: evidence");
       done[c] = true;
       igk::prof_add_work(S_EVIDENCE_IDX, t);

@@ -205,6 +205,8 @@ struct IndexedArgs {
   int* status;
   int64_t* tests_out;   // subset tests executed
   int prof_stage = -1;  // stage under which the grouped kernel is timed
+  int max_q = 4;        // most own rows per thread of a block (1, 2, 4)
+  int flip_factor = 2;  // side ratio before the non-result side goes to registers
 };
 cudaError_t indexed_subset(const IndexedArgs& a, cudaStream_t s);
 
@@ -227,7 +229,8 @@ void release_keyed_index(KeyedIndex* k, cudaStream_t s);
 // indexed_subset with a prebuilt pattern side; no synchronization.
 cudaError_t indexed_subset_prebuilt(int mode, const RecordIndex& idx, const KeyedIndex& kx,
                                     uint32_t* out_u32, unsigned long long* out_u64, int* status,
-                                    int64_t* tests_out, int prof_stage, cudaStream_t s);
+                                    int64_t* tests_out, int prof_stage, int max_q,
+                                    int flip_factor, cudaStream_t s);
 // freq[l] += number of the n rows holding item l (rows of stride `stride`, K words).
 cudaError_t launch_item_histogram(const uint64_t* rows, int64_t n, int stride, int K, int L,
                                   uint32_t* freq, cudaStream_t s);

@@ -485,9 +485,9 @@ cudaError_t launch_grouped_subset(const GroupedArgs& a, cudaStream_t s) {
 // Blocks (group, own tile, stream range) with about `target` tests each;
 // in every group the larger side goes to registers (own).
 void build_work_items(const uint32_t* keyed_off, const uint32_t* multi_off, int groups,
-                      int own_tile, int str_tile, int64_t target, bool mode_sum,
-                      std::vector<WorkItem>* items, int64_t* tests) {
-  const int max_q = own_tile / 256;
+                      int own_tile, int str_tile, int64_t target, bool mode_sum, int max_q_param,
+                      int flip, std::vector<WorkItem>* items, int64_t* tests) {
+  const int max_q = std::max(1, std::min(own_tile / 256, max_q_param));
   items->clear();
   *tests = 0;
   for (int l = 0; l < groups; ++l) {
@@ -497,7 +497,7 @@ void build_work_items(const uint32_t* keyed_off, const uint32_t* multi_off, int 
     *tests += nk * nm;
     // The result side stays in registers unless the other side is at least
     // twice as large (then per-hit atomics are the cheaper way to fill lanes).
-    const bool own_keyed = mode_sum ? (nk >= 2 * nm) : (2 * nk >= nm);
+    const bool own_keyed = mode_sum ? (nk >= int64_t(flip) * nm) : (int64_t(flip) * nk >= nm);
     const int64_t no = own_keyed ? nk : nm, ns = own_keyed ? nm : nk;
     const int64_t o0 = own_keyed ? keyed_off[l] : multi_off[l];
     const int64_t s0 = own_keyed ? multi_off[l] : keyed_off[l];
@@ -645,7 +645,8 @@ cudaError_t build_keyed_index(const uint64_t* keyed, int64_t n, int stride, int 
 
 cudaError_t indexed_subset_prebuilt(int mode, const RecordIndex& idx, const KeyedIndex& kx,
                                     uint32_t* out_u32, unsigned long long* out_u64, int* status,
-                                    int64_t* tests_out, int prof_stage, cudaStream_t s) {
+                                    int64_t* tests_out, int prof_stage, int max_q,
+                                    int flip_factor, cudaStream_t s) {
   *tests_out = 0;
   if (kx.n == 0 || idx.n_rows == 0) return cudaSuccess;
   const int L = idx.L, KT = idx.KT;
@@ -655,7 +656,8 @@ cudaError_t indexed_subset_prebuilt(int mode, const RecordIndex& idx, const Keye
     total += (int64_t(kx.h_off[l + 1]) - kx.h_off[l]) * (int64_t(idx.h_off[l + 1]) - idx.h_off[l]);
   const int64_t target = std::max<int64_t>(total / (int64_t(num_sms()) * 8), 1 << 16);
   build_work_items(kx.h_off.data(), idx.h_off.data(), L, grouped_own_per_cta(KT),
-                   grouped_rows_per_tile(KT), target, mode == MODE_SUM, &items, &tests);
+                   grouped_rows_per_tile(KT), target, mode == MODE_SUM, max_q,
+                   std::max(1, flip_factor), &items, &tests);
   *tests_out = tests;
   if (items.empty()) return cudaSuccess;
   cudaError_t e;
@@ -699,7 +701,7 @@ cudaError_t indexed_subset(const IndexedArgs& a, cudaStream_t s) {
                                     a.mode == MODE_SUM ? a.keyed_score : nullptr, &kx, s);
   if (e != cudaSuccess) return e;
   e = indexed_subset_prebuilt(a.mode, idx, kx, a.out_u32, a.out_u64, a.status, a.tests_out,
-                              a.prof_stage, s);
+                              a.prof_stage, a.max_q, a.flip_factor, s);
   release_keyed_index(&kx, s);
   return e;
 }

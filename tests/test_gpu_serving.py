@@ -110,3 +110,43 @@ def test_server_memory_admission(served):
     assert scored == flows.shape[0]
     assert np.array_equal(np.concatenate([o[0] for o in outs]), refA)
     assert np.array_equal(np.concatenate([o[2] for o in outs]), reflab)
+
+
+def test_autotuner_choices_keep_results(tmp_path):
+    from paper_2507_14222_gb300 import autotune
+    probs = igdata.batched(6)
+    enc = []
+    for w in probs:
+        codes = torch.from_numpy(w.train_codes.view(np.int16)).cuda()
+        tests = torch.from_numpy(w.test_codes.view(np.int16)).cuda()
+        enc.append((ig.ig_encode(codes, w.cards), torch.from_numpy(w.train_labels).cuda(),
+                    ig.ig_encode(tests, w.cards)))
+    tuner = autotune.Autotuner(str(tmp_path / "tune.json"))
+    chosen = tuner.tune(enc, repeats=1)
+    assert chosen and all(c in autotune.CANDIDATES for c in chosen.values())
+    assert (tmp_path / "tune.json").exists()
+    again = autotune.Autotuner(str(tmp_path / "tune.json"))     # read back from the cache
+    params = [again.params_for(int(r.shape[1]), int(r.shape[0])) for r, _, _ in enc]
+    assert all(p is not None for p in params)
+    tuned = ig.ig_fit_batched([(r, lab) for r, lab, _ in enc], per_problem_params=params)
+    for (r, lab, t), mt in zip(enc, tuned):
+        plain = ig.ig_fit(r, lab)
+        for cls in (0, 1):
+            assert all(np.array_equal(x, y) for x, y in zip(mt.patterns(cls), plain.patterns(cls)))
+        a1 = ig.ig_score(mt, t)
+        a2 = ig.ig_score(plain, t)
+        assert all(torch.equal(x, y) for x, y in zip(a1, a2))
+
+
+@pytest.mark.parametrize("cfg", [dict(index_max_q=1), dict(index_max_q=2),
+                                 dict(index_flip_factor=1), dict(index_flip_factor=1 << 20)])
+def test_index_tiling_knobs_keep_results(cfg):
+    w = igdata.nsl15k()
+    rows = ig.ig_encode(torch.from_numpy(w.train_codes.view(np.int16)).cuda(), w.cards)
+    lab = torch.from_numpy(w.train_labels).cuda()
+    test = ig.ig_encode(torch.from_numpy(w.test_codes.view(np.int16)).cuda(), w.cards)
+    base = ig.ig_fit(rows, lab)
+    tuned = ig.ig_fit(rows, lab, **cfg)
+    for cls in (0, 1):
+        assert all(np.array_equal(x, y) for x, y in zip(tuned.patterns(cls), base.patterns(cls)))
+    assert all(torch.equal(x, y) for x, y in zip(ig.ig_score(tuned, test), ig.ig_score(base, test)))
