@@ -253,9 +253,10 @@ cudaError_t launch_labels(const unsigned long long* A, const unsigned long long*
                           cudaStream_t s);
 
 // ---- sort.cu ----------------------------------------------------------------
-// Canonical order of n keys (stride KT): ascending as KT-word
-// unsigned integers, word KT-1 most significant.  keys_out (n rows) receives
-// the sorted rows; `work` must hold n rows as well.
+// Canonical order of n keys (stride KT): ascending as KT-word unsigned
+// integers, word KT-1 most significant; equal keys may repeat.  keys_out (n
+// rows) receives the sorted rows and must not overlap keys; `work` is
+// unused (the sort allocates its own 40 bytes per key).
 cudaError_t canonical_sort(const uint64_t* keys, int64_t n, int KT, uint64_t* keys_out,
                            uint64_t* work, cudaStream_t s);
 

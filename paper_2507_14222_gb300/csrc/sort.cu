@@ -4,27 +4,26 @@
 // across runs (the paper's requirement that GPU and CPU pattern evidence
 // agree exactly, Section 4).
 //
-//  1. each block sorts a tile of T keys held in shared memory with a bitonic
-//     network over 16-bit indices (full KT-word comparisons);
-//  2. merge passes double the sorted run length: every key finds its output
-//     slot directly as (its index in its own run) + (number of keys of the
-//     partner run before it), the latter by binary search -- keys of the
-//     right run count equal keys of the left run as before them -- so the
-//     slots form a permutation without merge-path partitioning, also when
-//     keys repeat.
+//  1. every key gets an order-preserving 128-bit prefix (its ten highest
+//     items) and is represented by (prefix, index) while it is sorted, so the
+//     passes move 20 bytes per key and their searches run over arrays that
+//     fit in L2; full keys are read only when two prefixes tie;
+//  2. each block sorts a tile of 2,048 elements in shared memory with a
+//     bitonic network;
+//  3. merge passes double the sorted run length: every element finds its
+//     output slot directly as (its index in its own run) + (number of
+//     partner-run elements before it), the latter by binary search --
+//     right-run elements count equal left-run elements as before them -- so
+//     the slots form a permutation without merge-path partitioning, also
+//     when keys repeat;
+//  4. the keys are gathered in the final order.
 #include "common.cuh"
 #include "internal.h"
 
 namespace igk {
 
 constexpr int kSortBlockThreads = 512;
-
-template <int KT>
-struct SortShape {
-  // 64 KiB of keys per tile, at most 4096 keys (16-bit indices).
-  static constexpr int T = (8192 / KT) > 4096 ? 4096 : (8192 / KT);
-  static constexpr size_t kSmem = size_t(T) * KT * 8 + size_t(T) * 2;
-};
+constexpr int kSortTile = 2048;  // elements per block-sorted tile
 
 template <int KT>
 __device__ __forceinline__ bool key_less(const uint64_t* a, const uint64_t* b) {
@@ -36,46 +35,112 @@ __device__ __forceinline__ bool key_less(const uint64_t* a, const uint64_t* b) {
   return false;
 }
 
+// Order-preserving prefix of a key: its ten highest items, from the top,
+// each as (item + 1) in a 12-bit field (0 = no further item), five per
+// word.  Comparing (p0, p1) lexicographically agrees with comparing the keys
+// (word KT-1 most significant): two keys first differ at the highest bit
+// where one has an item and the other not, and that is the first position
+// where their descending item lists differ.  Keys with equal prefixes are
+// compared in full.
+template <int KT>
+__global__ void prefix_kernel(const uint64_t* __restrict__ keys, int64_t n,
+                              uint64_t* __restrict__ p0, uint64_t* __restrict__ p1,
+                              uint32_t* __restrict__ idx) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t a = 0, b = 0;
+  int taken = 0;
+  for (int w = KT - 1; w >= 0 && taken < 10; --w) {
+    uint64_t x = keys[i * KT + w];
+    while (x && taken < 10) {
+      const int bit = 63 - __clzll(static_cast<long long>(x));
+      x &= ~(1ull << bit);
+      const uint64_t field = uint64_t(w * 64 + bit + 1);
+      if (taken < 5)
+        a |= field << (12 * (4 - taken));
+      else
+        b |= field << (12 * (9 - taken));
+      ++taken;
+    }
+  }
+  p0[i] = a;
+  p1[i] = b;
+  idx[i] = uint32_t(i);
+}
+
+template <int KT>
+__device__ __forceinline__ bool elem_less(const uint64_t* keys, uint64_t a0, uint64_t a1,
+                                          uint32_t ai, uint64_t b0, uint64_t b1, uint32_t bi) {
+  if (a0 != b0) return a0 < b0;
+  if (a1 != b1) return a1 < b1;
+  return key_less<KT>(keys + int64_t(ai) * KT, keys + int64_t(bi) * KT);
+}
+
+struct SortArrays {
+  uint64_t* p0;
+  uint64_t* p1;
+  uint32_t* idx;
+};
+
+// Bitonic network over a tile of kSortTile elements in shared memory.
 template <int KT>
 __global__ void __launch_bounds__(kSortBlockThreads)
-    block_sort_kernel(const uint64_t* keys, int64_t n, uint64_t* out) {
-  constexpr int T = SortShape<KT>::T;
-  extern __shared__ __align__(16) uint64_t sk[];
-  uint16_t* idx = reinterpret_cast<uint16_t*>(sk + T * KT);
-  const int64_t base = int64_t(blockIdx.x) * T;
-  const int nv = int((n - base) < T ? (n - base) : T);
-  for (int e = threadIdx.x; e < nv * KT; e += blockDim.x) sk[e] = keys[base * KT + e];
-  for (int r = threadIdx.x; r < T; r += blockDim.x) idx[r] = uint16_t(r);
+    block_sort_kernel(const uint64_t* __restrict__ keys, int64_t n, SortArrays in,
+                      SortArrays out) {
+  __shared__ uint64_t s0[kSortTile];
+  __shared__ uint64_t s1[kSortTile];
+  __shared__ uint32_t si[kSortTile];
+  const int64_t base = int64_t(blockIdx.x) * kSortTile;
+  const int nv = int((n - base) < kSortTile ? (n - base) : kSortTile);
+  for (int r = threadIdx.x; r < kSortTile; r += blockDim.x) {
+    if (r < nv) {
+      s0[r] = in.p0[base + r];
+      s1[r] = in.p1[base + r];
+      si[r] = in.idx[base + r];
+    } else {  // +infinity: after every key
+      s0[r] = ~0ull;
+      s1[r] = ~0ull;
+      si[r] = 0xffffffffu;
+    }
+  }
   __syncthreads();
-  // Indices >= nv stand for +infinity (the tile's missing tail).
-  auto greater = [&](int a, int b) -> bool {
-    if (a >= nv) return b < nv;
-    if (b >= nv) return false;
-    return key_less<KT>(sk + b * KT, sk + a * KT);
+  auto greater = [&](int x, int y) -> bool {
+    if (si[x] == 0xffffffffu) return si[y] != 0xffffffffu;
+    if (si[y] == 0xffffffffu) return false;
+    return elem_less<KT>(keys, s0[y], s1[y], si[y], s0[x], s1[x], si[x]);
   };
-  for (int k = 2; k <= T; k <<= 1) {
+  for (int k = 2; k <= kSortTile; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int t = threadIdx.x; t < T / 2; t += blockDim.x) {
+      for (int t = threadIdx.x; t < kSortTile / 2; t += blockDim.x) {
         const int i = (t / j) * 2 * j + (t % j), l = i + j;
-        const int a = idx[i], b = idx[l];
         const bool up = (i & k) == 0;
-        if (up ? greater(a, b) : greater(b, a)) {
-          idx[i] = uint16_t(b);
-          idx[l] = uint16_t(a);
+        if (up ? greater(i, l) : greater(l, i)) {
+          const uint64_t a0 = s0[i], a1 = s1[i];
+          const uint32_t ai = si[i];
+          s0[i] = s0[l];
+          s1[i] = s1[l];
+          si[i] = si[l];
+          s0[l] = a0;
+          s1[l] = a1;
+          si[l] = ai;
         }
       }
       __syncthreads();
     }
   }
-  for (int e = threadIdx.x; e < nv * KT; e += blockDim.x) {
-    const int r = e / KT, k = e - r * KT;
-    out[base * KT + e] = sk[idx[r] * KT + k];
+  for (int r = threadIdx.x; r < nv; r += blockDim.x) {
+    out.p0[base + r] = s0[r];
+    out.p1[base + r] = s1[r];
+    out.idx[base + r] = si[r];
   }
 }
 
+// Merge pass: element e of run r goes to (its index in its run) + (number
+// of partner-run elements before it); left-run elements go before equal
+// right-run elements, so the slots form a permutation even when keys repeat.
 template <int KT>
-__global__ void merge_pass_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
-                                  int64_t n, int64_t run) {
+__global__ void merge_pass_kernel(const uint64_t* __restrict__ keys, SortArrays in,
+                                  SortArrays out, int64_t n, int64_t run) {
   const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= n) return;
   const int64_t r = e / run;
@@ -83,20 +148,18 @@ __global__ void merge_pass_kernel(const uint64_t* __restrict__ in, uint64_t* __r
   const int64_t pair_lo = (r & ~int64_t(1)) * run;
   const int64_t o_lo = (r ^ 1) * run;
   const int64_t o_hi = o_lo + run < n ? o_lo + run : n;
-  uint64_t key[KT];
-#pragma unroll
-  for (int k = 0; k < KT; ++k) key[k] = in[e * KT + k];
-  // A key of the left run goes before equal keys of the right run: it counts
-  // the partner's keys strictly below it, a right-run key those not above it
-  // (a stable merge, so equal keys cannot collide on one slot).
+  const uint64_t k0 = in.p0[e], k1 = in.p1[e];
+  const uint32_t ki = in.idx[e];
   const bool left = (r & 1) == 0;
   int64_t below = 0;
   if (o_lo < n) {
     int64_t lo = o_lo, hi = o_hi;
     while (lo < hi) {
       const int64_t mid = (lo + hi) >> 1;
-      const bool before = left ? key_less<KT>(in + mid * KT, key)
-                               : !key_less<KT>(key, in + mid * KT);
+      const uint64_t m0 = in.p0[mid], m1 = in.p1[mid];
+      const uint32_t mi = in.idx[mid];
+      const bool before = left ? elem_less<KT>(keys, m0, m1, mi, k0, k1, ki)
+                               : !elem_less<KT>(keys, k0, k1, ki, m0, m1, mi);
       if (before)
         lo = mid + 1;
       else
@@ -105,34 +168,52 @@ __global__ void merge_pass_kernel(const uint64_t* __restrict__ in, uint64_t* __r
     below = lo - o_lo;
   }
   const int64_t pos = pair_lo + (e - own_lo) + below;
-#pragma unroll
-  for (int k = 0; k < KT; ++k) out[pos * KT + k] = key[k];
+  out.p0[pos] = k0;
+  out.p1[pos] = k1;
+  out.idx[pos] = ki;
+}
+
+__global__ void gather_rows_kernel(const uint64_t* __restrict__ keys, int KT,
+                                   const uint32_t* __restrict__ idx, int64_t n,
+                                   uint64_t* __restrict__ out) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n * KT) return;
+  const int64_t i = t / KT;
+  const int k = int(t - i * KT);
+  out[t] = keys[int64_t(idx[i]) * KT + k];
 }
 
 template <int KT>
-static cudaError_t sort_t(const uint64_t* keys, int64_t n, uint64_t* keys_out, uint64_t* work,
-                          cudaStream_t s) {
-  using S = SortShape<KT>;
-  cudaError_t e = cudaFuncSetAttribute(block_sort_kernel<KT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::kSmem));
+static cudaError_t sort_t(const uint64_t* keys, int64_t n, uint64_t* keys_out, cudaStream_t s) {
+  // Two sets of (p0, p1, idx) arrays, ping-ponged by the passes.
+  void* mem = nullptr;
+  cudaError_t e = cudaMallocAsync(&mem, size_t(n) * 40, s);
   if (e != cudaSuccess) return e;
-  int passes = 0;
-  for (int64_t run = S::T; run < n; run *= 2) ++passes;
-  uint64_t* cur = (passes % 2 == 0) ? keys_out : work;
-  uint64_t* other = (cur == keys_out) ? work : keys_out;
-  const int64_t tiles = ceil_div(n, S::T);
-  block_sort_kernel<KT><<<unsigned(tiles), kSortBlockThreads, S::kSmem, s>>>(keys, n, cur);
+  uint8_t* m = static_cast<uint8_t*>(mem);
+  SortArrays A{reinterpret_cast<uint64_t*>(m), reinterpret_cast<uint64_t*>(m + 8 * n),
+               reinterpret_cast<uint32_t*>(m + 32 * n)};
+  SortArrays B{reinterpret_cast<uint64_t*>(m + 16 * n), reinterpret_cast<uint64_t*>(m + 24 * n),
+               reinterpret_cast<uint32_t*>(m + 36 * n)};
+  const unsigned g = unsigned(ceil_div(n, 256));
+  prefix_kernel<KT><<<g, 256, 0, s>>>(keys, n, A.p0, A.p1, A.idx);
   count_launches(1);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  for (int64_t run = S::T; run < n; run *= 2) {
-    merge_pass_kernel<KT><<<unsigned(ceil_div(n, 256)), 256, 0, s>>>(cur, other, n, run);
+  block_sort_kernel<KT><<<unsigned(ceil_div(n, kSortTile)), kSortBlockThreads, 0, s>>>(keys, n, A,
+                                                                                       B);
+  count_launches(1);
+  SortArrays cur = B, other = A;
+  for (int64_t run = kSortTile; run < n; run *= 2) {
+    merge_pass_kernel<KT><<<g, 256, 0, s>>>(keys, cur, other, n, run);
     count_launches(1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    uint64_t* t = cur;
+    const SortArrays t = cur;
     cur = other;
     other = t;
   }
-  return cudaSuccess;
+  gather_rows_kernel<<<unsigned(ceil_div(n * KT, 256)), 256, 0, s>>>(keys, KT, cur.idx, n,
+                                                                     keys_out);
+  count_launches(1);
+  e = cudaGetLastError();
+  cudaFreeAsync(mem, s);
+  return e;
 }
 
 // payload_sorted[position of keys[i] in sorted] = payload[i], found by
@@ -197,9 +278,10 @@ cudaError_t launch_check_strict(const uint64_t* sorted, int64_t n, int KT, int* 
 }
 
 cudaError_t canonical_sort(const uint64_t* keys, int64_t n, int KT, uint64_t* keys_out,
-                           uint64_t* work, cudaStream_t s) {
+                           uint64_t* /*work*/, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  IG_DISPATCH_KT(KT, return sort_t<KTC>(keys, n, keys_out, work, s));
+  if (n >= int64_t(0xffffffffll)) return cudaErrorInvalidValue;
+  IG_DISPATCH_KT(KT, return sort_t<KTC>(keys, n, keys_out, s));
   return cudaErrorInvalidValue;
 }
 
