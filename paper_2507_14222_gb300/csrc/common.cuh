@@ -18,6 +18,7 @@ enum : int {
   ST_TIMEOUT = 1,     // a bounded wait (mbarrier or hash slot) ran out
   ST_TABLE_FULL = 2,  // a hash probe sequence visited every slot
   ST_BAD_INPUT = 4,   // input value out of range (code >= card, label > 1)
+  ST_COUNT = 8,       // a table held more keys than its count (nothing written past it)
 };
 
 // Upper bounds on spin loops.  Each mbarrier poll is a try_wait, which
@@ -116,15 +117,21 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 // Hash of a KT-word key: one multiply-xorshift round per word (so the word
 // position matters), then the full mixing function so that keys differing
 // in a single sparse bit land far apart.
+// The same hash taken one word at a time (hash_begin, hash_word per word in
+// order, hash_end), for callers that do not hold the key in registers.
+__device__ __forceinline__ uint64_t hash_begin() { return 0x243f6a8885a308d3ull; }
+__device__ __forceinline__ uint64_t hash_word(uint64_t h, uint64_t w) {
+  h = (h ^ w) * 0x9e3779b97f4a7c15ull;
+  return h ^ (h >> 32);
+}
+__device__ __forceinline__ uint64_t hash_end(uint64_t h) { return mix64(h); }
+
 template <int KT>
 __device__ __forceinline__ uint64_t hash_key(const uint64_t (&w)[KT]) {
-  uint64_t h = 0x243f6a8885a308d3ull;
+  uint64_t h = hash_begin();
 #pragma unroll
-  for (int k = 0; k < KT; ++k) {
-    h = (h ^ w[k]) * 0x9e3779b97f4a7c15ull;
-    h ^= h >> 32;
-  }
-  return mix64(h);
+  for (int k = 0; k < KT; ++k) h = hash_word(h, w[k]);
+  return hash_end(h);
 }
 
 __host__ __device__ constexpr int64_t ceil_div(int64_t a, int64_t b) {

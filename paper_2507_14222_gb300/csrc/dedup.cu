@@ -14,11 +14,17 @@
 // and published by a single 64-bit CAS -- there is no half-written state,
 // no acquire/release protocol and no waiting on another thread's slot.
 //
-// Overflow cannot happen: before claiming an empty slot a thread takes a
-// reservation (atomicAdd on `reserved`) and gives up if the table already
-// holds `limit` keys (half its capacity), recording its tile band.  The host
-// then doubles the table, rehashes it, and replays the bands from the first
-// failed one (inserts are idempotent).
+// Overflow cannot happen and every insert ends: an insert probes at most
+// `max_probe` slots, and a pair tile that starts when the table already holds
+// `limit` keys (half its capacity) inserts nothing.  Either way the tile's
+// band is recorded; the host then grows the table, rehashes it, and replays
+// the bands from the first failed one (inserts are idempotent).  Bounding the
+// probe keeps lookups exact: slots are written once and never cleared, so a
+// stored key sits within `max_probe` slots of its home, before any empty one.
+//
+// Each CTA counts the keys it adds in shared memory and adds that to the
+// table's count once, when it ends: a per-key atomic on one global counter
+// would serialise every new key in one L2 slice.
 #include "common.cuh"
 #include "internal.h"
 
@@ -41,46 +47,48 @@ __device__ __forceinline__ void pair_key(const uint64_t* __restrict__ X, uint64_
   for (int w = 0; w < KT; ++w) k[w] = __ldg(a + w) & __ldg(b + w);
 }
 
+// A key given as the AND of two rows, read word by word where it is needed
+// instead of being held in registers: rows in shared memory (pair tiles) or
+// in global memory (rehash).
+struct SharedPairKey {
+  const uint64_t* a;
+  const uint64_t* b;
+  __device__ __forceinline__ uint64_t operator()(int w) const { return a[w] & b[w]; }
+};
+struct GlobalPairKey {
+  const uint64_t* a;
+  const uint64_t* b;
+  __device__ __forceinline__ uint64_t operator()(int w) const {
+    return __ldg(a + w) & __ldg(b + w);
+  }
+};
+
 // Returns 1 if inserted, 0 if already present, -1 if no reservation was
 // granted (the band is recorded for replay).
-template <int KT>
-__device__ int table_insert(const PairTable& t, const uint64_t* __restrict__ X,
-                            const uint64_t (&b)[KT], uint64_t h, uint32_t i, uint32_t j,
-                            int band, int* status) {
+template <int KT, class Key>
+__device__ int table_insert(const PairTable& t, const uint64_t* __restrict__ X, const Key& key,
+                            uint64_t h, uint32_t i, uint32_t j, int band, int* status) {
   const uint64_t val = slot_value(h, i, j);
   uint64_t slot = h & t.mask;
-  bool reserved = false;
-  for (uint64_t probe = 0; probe <= t.mask; ++probe) {
+  for (uint64_t probe = 0; probe < t.max_probe; ++probe) {
     unsigned long long cur = ld_relaxed_u64(t.slots + slot);
     if (cur == 0ull) {
-      if (!reserved) {
-        if (atomicAdd(t.reserved, 1ull) >= t.limit) {
-          atomicMin(t.failed_band, band);
-          return -1;
-        }
-        reserved = true;
-      }
       cur = atomicCAS(reinterpret_cast<unsigned long long*>(t.slots + slot), 0ull,
                       (unsigned long long)val);
-      if (cur == 0ull) {
-        atomicAdd(t.count, 1ull);
-        return 1;
-      }
+      if (cur == 0ull) return 1;
     }
     if ((cur & kFpMask) == (val & kFpMask)) {
-      uint64_t k2[KT];
-      pair_key<KT>(X, cur, k2);
+      const uint64_t* ca = X + ((cur >> kIdxBits) & kIdxMask) * KT;
+      const uint64_t* cb = X + (cur & kIdxMask) * KT;
       bool same = true;
 #pragma unroll
-      for (int w = 0; w < KT; ++w) same &= (k2[w] == b[w]);
-      if (same) {
-        if (reserved) atomicAdd(t.reserved, ~0ull);  // give the reservation back
-        return 0;
-      }
+      for (int w = 0; w < KT; ++w) same &= ((__ldg(ca + w) & __ldg(cb + w)) == key(w));
+      if (same) return 0;
     }
     slot = (slot + 1) & t.mask;
   }
-  set_status(status, ST_TABLE_FULL);
+  if (t.max_probe > t.mask) set_status(status, ST_TABLE_FULL);  // every slot taken
+  atomicMin(t.failed_band, band);
   return -1;
 }
 
@@ -89,6 +97,10 @@ constexpr int kPairThreads = 256;
 // Grid: x = column tile bj, y = row tile bi - band_lo.  Tiles with bj < bi
 // lie below the diagonal and exit at once.  Shared rows use an odd stride of
 // KT + 1 words so that lanes reading consecutive rows hit distinct banks.
+// The intersection is never held in registers: each use re-reads its words
+// from the two shared rows.  (More resident CTAs do not help: their shared
+// memory comes out of the L1 that caches the class's records, which every
+// key comparison reads.)
 template <int KT>
 __global__ void __launch_bounds__(kPairThreads)
     pair_insert_kernel(const uint64_t* __restrict__ X, int64_t n, int64_t band_lo,
@@ -97,8 +109,14 @@ __global__ void __launch_bounds__(kPairThreads)
   constexpr int SKT = KT + 1;
   __shared__ uint64_t A[T * SKT];
   __shared__ uint64_t B[T * SKT];
+  __shared__ unsigned int n_new;
+  __shared__ int table_full;
   const int64_t bi = band_lo + blockIdx.y, bj = blockIdx.x;
   if (bj < bi) return;
+  if (threadIdx.x == 0) {
+    n_new = 0;
+    table_full = ld_relaxed_u64(reinterpret_cast<const uint64_t*>(t.count)) >= t.limit;
+  }
   const int64_t i0 = bi * T, j0 = bj * T;
   for (int e = threadIdx.x; e < T * KT; e += kPairThreads) {
     int r = e / KT, k = e - r * KT;
@@ -106,52 +124,74 @@ __global__ void __launch_bounds__(kPairThreads)
     B[r * SKT + k] = (j0 + r < n) ? X[(j0 + r) * KT + k] : 0ull;
   }
   __syncthreads();
+  if (table_full) {  // uniform: the whole tile waits for the grown table
+    if (threadIdx.x == 0) atomicMin(t.failed_band, int(bi));
+    return;
+  }
   const int lane = threadIdx.x & 31;
   for (int p = threadIdx.x; p < T * T; p += kPairThreads) {
     const int i = p / T, j = p - (p / T) * T;
     bool valid = (i0 + i < n) && (j0 + j < n) && (bi < bj || i <= j);
-    uint64_t b[KT];
+    const SharedPairKey key{A + i * SKT, B + j * SKT};
     uint64_t any = 0;
+    uint64_t h = hash_begin();
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
-      b[k] = A[i * SKT + k] & B[j * SKT + k];
-      any |= b[k];
+      const uint64_t w = key(k);
+      any |= w;
+      h = hash_word(h, w);
     }
+    h = hash_end(h);
     bool has = valid && any != 0;
     unsigned active = __ballot_sync(0xffffffffu, has);
     if (!has) continue;
-    uint64_t h = hash_key<KT>(b);
     // Lanes holding the same key insert it once: the lowest lane of each
     // group of equal hashes is its leader; a lane whose key equals its
     // leader's skips the insert.
-    unsigned peers = __match_any_sync(active, h);
-    int leader = __ffs(peers) - 1;
-    bool same = true;
+    // Most hashes are unique in the warp, and those lanes skip the compare.
+    const unsigned peers = __match_any_sync(active, h);
+    if (__popc(peers) > 1) {
+      const int leader = __ffs(peers) - 1;
+      bool same = true;
 #pragma unroll
-    for (int k = 0; k < KT; ++k) same &= (__shfl_sync(active, b[k], leader) == b[k]);
-    if (leader != lane && same) continue;
-    table_insert<KT>(t, X, b, h, uint32_t(i0 + i), uint32_t(j0 + j), int(bi), status);
+      for (int k = 0; k < KT; ++k) {
+        const uint64_t w = key(k);
+        same &= (__shfl_sync(peers, w, leader) == w);
+      }
+      if (leader != lane && same) continue;
+    }
+    if (table_insert<KT>(t, X, key, h, uint32_t(i0 + i), uint32_t(j0 + j), int(bi), status) == 1)
+      atomicAdd(&n_new, 1u);
   }
+  __syncthreads();
+  if (threadIdx.x == 0 && n_new != 0) atomicAdd(t.count, (unsigned long long)n_new);
 }
 
 template <int KT>
 __global__ void rehash_kernel(const uint64_t* __restrict__ X, const uint64_t* __restrict__ from,
                               uint64_t from_cap, PairTable to, int* status) {
-  int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (s >= int64_t(from_cap)) return;
-  const uint64_t v = from[s];
-  if (v == 0ull) return;
-  uint64_t b[KT];
-  pair_key<KT>(X, v, b);
-  table_insert<KT>(to, X, b, hash_key<KT>(b), uint32_t((v >> kIdxBits) & kIdxMask),
-                   uint32_t(v & kIdxMask), 0, status);
+  __shared__ unsigned int n_new;
+  if (threadIdx.x == 0) n_new = 0;
+  __syncthreads();
+  const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const uint64_t v = s < int64_t(from_cap) ? from[s] : 0ull;
+  if (v != 0ull) {
+    uint64_t b[KT];
+    pair_key<KT>(X, v, b);
+    const GlobalPairKey key{X + ((v >> kIdxBits) & kIdxMask) * KT, X + (v & kIdxMask) * KT};
+    if (table_insert<KT>(to, X, key, hash_key<KT>(b), uint32_t((v >> kIdxBits) & kIdxMask),
+                         uint32_t(v & kIdxMask), 0, status) == 1)
+      atomicAdd(&n_new, 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && n_new != 0) atomicAdd(to.count, (unsigned long long)n_new);
 }
 
 // Warp-aggregated append of every stored key, recomputed from its pair.
 template <int KT>
 __global__ void compact_kernel(const uint64_t* __restrict__ X, const uint64_t* __restrict__ slots,
-                               uint64_t cap, uint64_t* __restrict__ out,
-                               unsigned long long* out_count) {
+                               uint64_t cap, uint64_t* __restrict__ out, int64_t out_rows,
+                               unsigned long long* out_count, int* status) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31);
@@ -165,6 +205,10 @@ __global__ void compact_kernel(const uint64_t* __restrict__ X, const uint64_t* _
     pos0 = __shfl_sync(0xffffffffu, pos0, 0);
     if (v != 0ull) {
       uint64_t pos = pos0 + __popc(m & ((1u << lane) - 1u));
+      if (pos >= uint64_t(out_rows)) {
+        set_status(status, ST_COUNT);
+        continue;
+      }
       uint64_t b[KT];
       pair_key<KT>(X, v, b);
 #pragma unroll
@@ -193,11 +237,12 @@ cudaError_t launch_rehash(const uint64_t* X, const uint64_t* from, uint64_t from
 }
 
 cudaError_t launch_compact(const uint64_t* X, const uint64_t* slots, uint64_t cap, int KT,
-                           uint64_t* out, unsigned long long* out_count, cudaStream_t s) {
+                           uint64_t* out, int64_t out_rows, unsigned long long* out_count,
+                           int* status, cudaStream_t s) {
   int64_t blocks = ceil_div(int64_t(cap), 256);
   if (blocks > 8 * 1024) blocks = 8 * 1024;
-  IG_DISPATCH_KT(KT, (compact_kernel<KTC><<<unsigned(blocks), 256, 0, s>>>(X, slots, cap, out,
-                                                                            out_count)));
+  IG_DISPATCH_KT(KT, (compact_kernel<KTC><<<unsigned(blocks), 256, 0, s>>>(
+                         X, slots, cap, out, out_rows, out_count, status)));
   count_launches(1);
   return cudaGetLastError();
 }

@@ -304,6 +304,7 @@ int read_status(int* d_status, cudaStream_t s, const char* where) {
     return fail(IG_E_INVAL, "%s: input value out of range (code >= card or label > 1)", where);
   if (st & igk::ST_TIMEOUT) return fail(IG_E_TIMEOUT, "%s: a bounded device wait ran out", where);
   if (st & igk::ST_TABLE_FULL) return fail(IG_E_INTERNAL, "%s: hash table full", where);
+  if (st & igk::ST_COUNT) return fail(IG_E_INTERNAL, "%s: hash table key count mismatch", where);
   return IG_OK;
 }
 
@@ -437,10 +438,14 @@ namespace {
 // pairs, at least 16 keys per record), so typical workloads need one launch.
 struct TableCounters {
   unsigned long long count;
-  unsigned long long reserved;
   int failed_band;
   int pad;
 };
+
+// Slots one pair insert may probe before its band is replayed on a grown
+// table.  At the load factors used (at most one half) linear probing
+// almost never comes near it.
+constexpr uint64_t kMaxProbe = 512;
 
 int build_candidates(const uint64_t* X, int64_t n, int KT, cudaStream_t s, int* d_status,
                      TableCounters* h_counters, DevBuf<uint64_t>& cand, int64_t* U_out) {
@@ -457,27 +462,25 @@ int build_candidates(const uint64_t* X, int64_t n, int KT, cudaStream_t s, int* 
   IG_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(TableCounters), s), "ig_fit");
   IG_CUDA(slots.alloc(cap, s), "ig_fit: hash table");
   IG_CUDA(cudaMemsetAsync(slots.p, 0, cap * sizeof(uint64_t), s), "ig_fit");
-  auto table = [&](uint64_t* sl, uint64_t c, TableCounters* t) {
+  auto table = [&](uint64_t* sl, uint64_t c, TableCounters* t, uint64_t max_probe) {
     igk::PairTable pt;
     pt.slots = sl;
     pt.mask = c - 1;
     pt.count = &t->count;
-    pt.reserved = &t->reserved;
     pt.limit = c / 2;
+    pt.max_probe = max_probe;
     pt.failed_band = &t->failed_band;
     return pt;
   };
   const int kNoBand = 0x7f7f7f7f;  // failed_band after a 0x7f byte fill
   int64_t band_lo = 0;
   for (;;) {
-    // reserved = count, failed_band = none, then insert the bands.
-    IG_CUDA(cudaMemcpyAsync(&ctr.p->reserved, &ctr.p->count, sizeof(unsigned long long),
-                            cudaMemcpyDeviceToDevice, s),
-            "ig_fit");
+    // failed_band = none, then insert the bands.
     IG_CUDA(cudaMemsetAsync(&ctr.p->failed_band, 0x7f, sizeof(int), s), "ig_fit");
     {
       ProfScope ps(S_PAIR, s);
-      IG_CUDA(igk::launch_pair_insert(X, n, KT, band_lo, table(slots.p, cap, ctr.p), d_status, s),
+      IG_CUDA(igk::launch_pair_insert(X, n, KT, band_lo, table(slots.p, cap, ctr.p, kMaxProbe),
+                                      d_status, s),
               "ig_fit: pair intersection");
     }
     IG_CUDA(cudaMemcpyAsync(h_counters, ctr.p, sizeof(TableCounters), cudaMemcpyDeviceToHost, s),
@@ -508,7 +511,10 @@ int build_candidates(const uint64_t* X, int64_t n, int KT, cudaStream_t s, int* 
     IG_CUDA(cudaMemsetAsync(nctr.p, 0, sizeof(TableCounters), s), "ig_fit");
     {
       ProfScope ps(S_REHASH, s);
-      IG_CUDA(igk::launch_rehash(X, slots.p, cap, table(nslots.p, ncap, nctr.p), KT, d_status, s),
+      // The grown table is at most a quarter full: every rehashed key finds
+      // a slot (probing is unbounded here).
+      IG_CUDA(igk::launch_rehash(X, slots.p, cap, table(nslots.p, ncap, nctr.p, ncap), KT,
+                                 d_status, s),
               "ig_fit: rehash");
     }
     std::swap(slots.p, nslots.p);
@@ -525,7 +531,8 @@ int build_candidates(const uint64_t* X, int64_t n, int KT, cudaStream_t s, int* 
   IG_CUDA(cudaMemsetAsync(out_count.p, 0, sizeof(unsigned long long), s), "ig_fit");
   {
     ProfScope ps(S_COMPACT, s);
-    IG_CUDA(igk::launch_compact(X, slots.p, cap, KT, cand.p, out_count.p, s), "ig_fit: compact");
+    IG_CUDA(igk::launch_compact(X, slots.p, cap, KT, cand.p, U, out_count.p, d_status, s),
+            "ig_fit: compact");
   }
   *U_out = U;
   return IG_OK;

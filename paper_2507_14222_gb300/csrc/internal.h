@@ -72,9 +72,9 @@ cudaError_t launch_split(const uint64_t* rows, const uint8_t* labels, int64_t n,
 struct PairTable {
   uint64_t* slots = nullptr;                // cap words, 0 = empty
   uint64_t mask = 0;                        // cap - 1, cap a power of two
-  unsigned long long* count = nullptr;      // keys stored
-  unsigned long long* reserved = nullptr;   // keys stored + claims in flight
-  unsigned long long limit = 0;             // most keys the table may hold
+  unsigned long long* count = nullptr;      // keys stored (added per CTA when it ends)
+  unsigned long long limit = 0;             // a pair tile starting at count >= limit fails
+  uint64_t max_probe = 0;                   // slots one insert may probe before it fails
   int* failed_band = nullptr;               // lowest band that ran out of room
 };
 
@@ -88,10 +88,12 @@ cudaError_t launch_pair_insert(const uint64_t* X, int64_t n, int KT, int64_t ban
 // Re-inserts every key of the table `from` (from_cap slots) into `to`.
 cudaError_t launch_rehash(const uint64_t* X, const uint64_t* from, uint64_t from_cap,
                           PairTable to, int KT, int* status, cudaStream_t s);
-// Appends every stored key (recomputed from its pair) to out (stride KT);
-// out_count must start at 0.
+// Appends every stored key (recomputed from its pair) to out (stride KT,
+// room for out_rows keys; a key beyond them is not written and sets
+// ST_COUNT); out_count must start at 0.
 cudaError_t launch_compact(const uint64_t* X, const uint64_t* slots, uint64_t cap, int KT,
-                           uint64_t* out, unsigned long long* out_count, cudaStream_t s);
+                           uint64_t* out, int64_t out_rows, unsigned long long* out_count,
+                           int* status, cudaStream_t s);
 
 // ---- subset.cu --------------------------------------------------------------
 enum SubsetMode { MODE_ANY = 0, MODE_COUNT = 1, MODE_SUM = 2 };
