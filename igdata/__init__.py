@@ -359,3 +359,49 @@ def served(per_class: int = 1_000_000, total_flows: int = 1_000_000, seed: int =
                           np.asarray(NSL_CARDS, np.uint16), patterns, support, flows,
                           sizes, gaps, {"seed": seed, "keep_frac": keep_frac,
                                         "max_request": max_request})
+
+
+@dataclass
+class RawFlows:
+    """Raw (undiscretised) flow attributes for the preprocessing helpers."""
+
+    values: np.ndarray       # float64[n, F]; NaN = missing
+    categorical: np.ndarray  # bool[F]
+    labels: np.ndarray       # uint8[n], 1 = attack
+
+
+def raw_flows(n: int, seed: int = 1006, missing_frac: float = 0.001) -> RawFlows:
+    """NSL-KDD-shaped raw attributes: 41 columns -- three categorical (3, 70
+    and 11 values, as integer-valued floats), then 38 numeric ones of three
+    kinds drawn per class: zero-inflated log-normal byte/duration counts,
+    rates in [0, 1] with two decimals, and small Poisson counts.  A fraction
+    `missing_frac` of all entries is NaN.  Labels are 53% normal."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    labels = (rng.random(n) >= 0.53).astype(np.uint8)
+    F = 41
+    vals = np.empty((n, F), np.float64)
+    cat = np.zeros(F, bool)
+    cat[:3] = True
+    for f, card in enumerate((3, 70, 11)):
+        pmf = [rng.dirichlet(np.full(card, 0.3)) for _ in range(2)]
+        for c in (0, 1):
+            idx = np.flatnonzero(labels == c)
+            vals[idx, f] = rng.choice(card, size=idx.size, p=pmf[c]).astype(np.float64)
+    for f in range(3, F):
+        kind = f % 3
+        for c in (0, 1):
+            idx = np.flatnonzero(labels == c)
+            m = idx.size
+            if kind == 0:
+                zero = rng.random() * 0.9
+                mean, sd = rng.uniform(2.0, 8.0), rng.uniform(0.5, 2.0)
+                v = np.round(rng.lognormal(mean, sd, m))
+                v[rng.random(m) < zero] = 0.0
+            elif kind == 1:
+                a, b = rng.uniform(0.2, 3.0, 2)
+                v = np.round(rng.beta(a, b, m), 2)
+            else:
+                v = rng.poisson(rng.uniform(0.1, 20.0), m).astype(np.float64)
+            vals[idx, f] = v
+    vals[rng.random((n, F)) < missing_frac] = np.nan
+    return RawFlows(vals, cat, labels)

@@ -93,6 +93,11 @@ SIGNATURES = {
     "ig_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, _P]),
     "ig_server_stats": (ctypes.c_int, [_P, _P, _P]),
     "ig_server_destroy": (None, [_P]),
+    "ig_discretize": (ctypes.c_int, [_P, _I64, _P, _I64, _I32, _P, _I32, _P, _P]),
+    "ig_filter_contradictions": (ctypes.c_int, [_P, _P, _I64, _I32, _I32, _P, _P]),
+    "ig_evaluate": (ctypes.c_int, [_P, _P, _P, _P, _I64, _P]),
+    "ig_reg3_sweep": (ctypes.c_int, [_P, _P, _P, _I64, ctypes.c_double, ctypes.c_double,
+                                     _P, _I32, _P]),
 }
 SCORE_NOALLOC_MAX_ROWS = 262144
 
@@ -472,3 +477,88 @@ def launch_count() -> int:
 
 # Short aliases.
 encode, fit, score, model_load = ig_encode, ig_fit, ig_score, ig_model_load
+
+
+# ---- host helpers (include/ig_helpers.h): host arrays only ------------------
+
+class ig_metrics_t(ctypes.Structure):
+    _fields_ = [("tp", ctypes.c_int64), ("fp", ctypes.c_int64),
+                ("tn", ctypes.c_int64), ("fn", ctypes.c_int64),
+                ("accuracy", ctypes.c_double), ("precision", ctypes.c_double),
+                ("recall", ctypes.c_double), ("f1", ctypes.c_double),
+                ("auc", ctypes.c_double)]
+
+
+def _host(x, dtype):
+    """A C-contiguous numpy copy (or view) of x on the host."""
+    if _is_torch(x):
+        x = x.detach().cpu().numpy()
+    return np.ascontiguousarray(np.asarray(x), dtype=dtype)
+
+
+def _metrics_dict(m: ig_metrics_t) -> dict:
+    return {k: getattr(m, k) for k, _ in ig_metrics_t._fields_}
+
+
+def ig_discretize(fit_values, categorical, p: int, values=None):
+    """Section 3.1 discretiser: (codes uint16[n, F], cards uint16[F]).
+
+    fit_values: float[n_fit, F] (NaN = missing) -- statistics and vocabulary;
+    values: rows to code (default: fit_values); categorical: bool[F]."""
+    fit = _host(fit_values, np.float64)
+    vals = fit if values is None else _host(values, np.float64)
+    if fit.ndim != 2 or vals.ndim != 2 or vals.shape[1] != fit.shape[1]:
+        raise ValueError("fit_values and values must be [n, F] with the same F")
+    F = fit.shape[1]
+    cat = _host(categorical, np.uint8)
+    if cat.shape != (F,):
+        raise ValueError("categorical must have one entry per column")
+    codes = np.empty(vals.shape, np.uint16)
+    cards = np.empty(F, np.uint16)
+    _check(load().ig_discretize(_ptr(fit), fit.shape[0], _ptr(vals), vals.shape[0], F,
+                                _ptr(cat), int(p), _ptr(codes), _ptr(cards)))
+    return codes, cards
+
+
+def ig_filter_contradictions(rows, labels, mode: int = 0):
+    """Anti-contradiction filter: bool[n] mask of the records kept."""
+    r = _host(rows, np.uint64)
+    lab = _host(labels, np.uint8)
+    if r.ndim != 2 or lab.shape != (r.shape[0],):
+        raise ValueError("rows must be [n, K] and labels [n]")
+    keep = np.empty(r.shape[0], np.uint8)
+    _check(load().ig_filter_contradictions(_ptr(r), _ptr(lab), r.shape[0], r.shape[1],
+                                           int(mode), _ptr(keep), None))
+    return keep.astype(bool)
+
+
+def ig_evaluate(y_true, y_pred, A=None, N=None) -> dict:
+    """Accuracy, precision, recall, F1 and (with A, N) the AUC of A - N."""
+    yt = _host(y_true, np.uint8)
+    yp = _host(y_pred, np.uint8)
+    if yp.shape != yt.shape or yt.ndim != 1:
+        raise ValueError("y_true and y_pred must be 1-D of one length")
+    a = n_ = None
+    if (A is None) != (N is None):
+        raise ValueError("give both A and N, or neither")
+    if A is not None:
+        a, n_ = _host(A, np.int64), _host(N, np.int64)
+        if a.shape != yt.shape or n_.shape != yt.shape:
+            raise ValueError("A and N must have one entry per record")
+    out = ig_metrics_t()
+    _check(load().ig_evaluate(_ptr(yt), _ptr(yp), _ptr(a) if a is not None else None,
+                              _ptr(n_) if n_ is not None else None, yt.shape[0],
+                              ctypes.byref(out)))
+    return _metrics_dict(out)
+
+
+def ig_reg3_sweep(A, N, y_true, mu: float, sigma: float, rs) -> list:
+    """Metrics of Regulations 1-3 for each r in rs (one dict per r)."""
+    a, n_, yt = _host(A, np.int64), _host(N, np.int64), _host(y_true, np.uint8)
+    if not (a.shape == n_.shape == yt.shape) or yt.ndim != 1:
+        raise ValueError("A, N and y_true must be 1-D of one length")
+    r = _host(rs, np.float64).reshape(-1)
+    out = (ig_metrics_t * max(1, r.shape[0]))()
+    _check(load().ig_reg3_sweep(_ptr(a), _ptr(n_), _ptr(yt), yt.shape[0], float(mu),
+                                float(sigma), _ptr(r), r.shape[0], out))
+    return [dict(_metrics_dict(out[k]), r=float(r[k])) for k in range(r.shape[0])]

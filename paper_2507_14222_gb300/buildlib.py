@@ -21,11 +21,13 @@ LIB = os.path.join(BUILD, "libig_gb300.so")
 
 SOURCES = ["encode.cu", "dedup.cu", "subset.cu", "sort.cu", "ig_capi.cu",
            "score_noalloc.cu", "subset_tc.cu",
-           "prune.cu", "server.cu"]
+           "prune.cu", "server.cu", "helpers.cu"]
 HEADERS = ["common.cuh", "internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Host code is compiled without floating-point contraction, so that its
+# double arithmetic (Regulation 3, the helpers) rounds the same on every host.
 FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
-                "-I" + INCLUDE]
+                "-Xcompiler", "-ffp-contract=off", "-I" + INCLUDE]
 
 
 def nvcc_path() -> str:
@@ -43,8 +45,9 @@ def _stamp() -> str:
     for name in SOURCES + HEADERS:
         with open(os.path.join(CSRC, name), "rb") as f:
             h.update(name.encode() + f.read())
-    with open(os.path.join(INCLUDE, "ig.h"), "rb") as f:
-        h.update(f.read())
+    for name in sorted(os.listdir(INCLUDE)):
+        with open(os.path.join(INCLUDE, name), "rb") as f:
+            h.update(name.encode() + f.read())
     h.update(" ".join(FLAGS).encode())
     return h.hexdigest()
 
