@@ -512,9 +512,26 @@ def roofline(stages, info, K, clocks, steps):
                     "peak_source": ("measured bf16 burst x 2 (nominal FP8/BF16 ratio)"
                                     if peaks else "fallback bf16 x 2")})
     else:
+        # Byte models (per timed step x steps) of the memory-bound stages:
+        #   pair_insert: a hash set of K-word keys -- every pair compares its
+        #     key with one stored key (8K B) and every distinct key is
+        #     written once (8K B);
+        #   compact: every distinct key written once (8K B);
+        #   canonical_sort: every distinct key read and written once.
+        # The pairs include each record with itself (the records of Eq. 1).
+        U = sum(info["n_candidates"]) * steps
+        pairs = (sum(info["n_pairs"]) + sum(info["n_train"])) * steps
+        model_bytes = {
+            "pair_insert": (pairs + U) * 8 * K,
+            "compact": U * 8 * K,
+            "canonical_sort": 2 * U * 8 * K,
+        }
         hbm = (peaks or {}).get("hbm_gbs", FALLBACK_HBM_GBS)
-        out.update({"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s",
-                    "frac": None, "traffic": None,
+        nbytes = model_bytes.get(name)
+        achieved = nbytes / (ms * 1e-3) / 1e9 if nbytes else None
+        out.update({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm if achieved else None, "traffic": None,
+                    "algorithmic_bytes_per_step": (nbytes // steps) if nbytes else None,
                     "peak_source": "measured" if peaks else "fallback"})
     return out
 
