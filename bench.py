@@ -28,6 +28,7 @@ from __future__ import annotations
 
 import argparse
 import csv
+import hashlib
 import io
 import json
 import os
@@ -171,10 +172,10 @@ def run_ours(args):
     if args.workload == "served":
         return run_served(args, ig, torch, rank, world, local)
 
-    seed_offset = 0 if rank == 0 else 7919 * rank
-    w = {"tiny": lambda: igdata.tiny(1001 + seed_offset),
-         "nsl15k": lambda: igdata.nsl15k(1002 + seed_offset),
-         "nsl148k": lambda: igdata.nsl148k(1003 + seed_offset)}[args.workload]()
+    from paper_2507_14222_gb300 import replicas
+    w = {"tiny": lambda: igdata.tiny(replicas.replica_seed(1001, rank)),
+         "nsl15k": lambda: igdata.nsl15k(replicas.replica_seed(1002, rank)),
+         "nsl148k": lambda: igdata.nsl148k(replicas.replica_seed(1003, rank))}[args.workload]()
     cards = w.cards
     d_tr = torch.from_numpy(w.train_codes.view(np.int16)).cuda()
     d_lab = torch.from_numpy(w.train_labels).cuda()
@@ -198,17 +199,13 @@ def run_ours(args):
     torch.cuda.synchronize()
     tests = nominal_tests(info, m_test)
 
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     fit_ms = []
     ig.prof_reset()
     ig.prof_enable(True)
     launches0 = ig.launch_count()
-    barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         for i in range(args.steps):
@@ -227,18 +224,16 @@ def run_ours(args):
             torch.cuda.synchronize()
             fit_ms.append(f0.elapsed_time(f1))
         torch.cuda.synchronize()
-    barrier()
+    replicas.barrier()
     launches = ig.launch_count() - launches0
     ig.prof_enable(False)
     stages = ig.prof_read()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    # Slowest rank's time; every rank's own tests (their problems differ).
+    total_ms, job_tests = replicas.job_totals(sum(step_ms), tests["total"] * args.steps,
+                                              device="cuda")
     ms_per_step = total_ms / args.steps
-    value = world * tests["total"] / (ms_per_step * 1e-3) / 1e9
+    value = job_tests / args.steps / (ms_per_step * 1e-3) / 1e9
 
     if rank != 0:
         if world > 1:
@@ -291,7 +286,8 @@ def run_batched(args, ig, torch, rank, world, local):
     Both forms run in the same process on the same inputs; their models must
     be byte-identical.  Scoring runs per problem in both.
     """
-    probs = igdata.batched(igdata.BATCHED_PROBLEMS, 2000 + 7919 * rank)
+    from paper_2507_14222_gb300 import replicas
+    probs = igdata.batched(igdata.BATCHED_PROBLEMS, replicas.replica_seed(2000, rank))
     dev = []
     for w in probs:
         dev.append((torch.from_numpy(w.train_codes.view(np.int16)).cuda(),
@@ -303,17 +299,15 @@ def run_batched(args, ig, torch, rank, world, local):
     def encode_all():
         return [(ig.ig_encode(c, cards), lab, ig.ig_encode(t, cards)) for c, lab, t, cards in dev]
 
-
     # Tiling and subset-test form per (K, size) group, tuned once per GPU
     # (cached), outside the timed region.
     from paper_2507_14222_gb300 import autotune
     tuner = autotune.Autotuner()
-    enc0 = encode_all_once = [(ig.ig_encode(c, cards), lab, ig.ig_encode(t, cards))
-                              for c, lab, t, cards in dev]
+    enc0 = encode_all()
     tuned = tuner.tune(enc0) if args.kernel == 0 else {}
     per_params = [tuner.params_for(int(r.shape[1]), int(r.shape[0])) if args.kernel == 0
                   else None for r, _, _ in enc0]
-    del encode_all_once
+    del enc0
 
     def step(batched):
         enc = encode_all()
@@ -346,8 +340,7 @@ def run_batched(args, ig, torch, rank, world, local):
             mdl.free()
     infos = None
     launches0 = ig.launch_count()
-    if world > 1:
-        torch.distributed.barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
     ig.prof_reset()
     ig.prof_enable(True)
@@ -367,16 +360,12 @@ def run_batched(args, ig, torch, rank, world, local):
                                                                    ms_.patterns(cls)))
         mb.free()
         ms_.free()
-    total_ms = sum(ms_b)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, job_tests = replicas.job_totals(sum(ms_b), total_tests, device="cuda")
     ms_per_step = total_ms / args.steps
     if rank != 0:
         return
     line = {
-        "metric": METRIC, "value": world * total_tests / (ms_per_step * 1e-3) / 1e9,
+        "metric": METRIC, "value": job_tests / (ms_per_step * 1e-3) / 1e9,
         "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
@@ -405,7 +394,9 @@ def run_served(args, ig, torch, rank, world, local):
     flows.
     """
     import threading
-    sw = igdata.served(args.served_patterns, args.served_flows, 1005 + 7919 * rank)
+    from paper_2507_14222_gb300 import replicas
+    sw = igdata.served(args.served_patterns, args.served_flows,
+                       replicas.replica_seed(1005, rank))
     words = [ig.ig_encode(torch.from_numpy(sw.patterns[c].view(np.int16)).cuda(), sw.cards)
              for c in (0, 1)]
     model = ig.ig_model_from_patterns(words[0], sw.support[0], words[1], sw.support[1])
@@ -453,11 +444,13 @@ def run_served(args, ig, torch, rank, world, local):
     got = [np.concatenate([o[k] for o in paced]) for k in range(3)]
     identical = all(np.array_equal(g, r) for g, r in zip(got, ref))
     server.close()
+    flows_done = int(sw.request_sizes.sum())
+    paced_ms, job_flows = replicas.job_totals(paced_s * 1e3, flows_done, device="cuda")
+    paced_s = paced_ms * 1e-3
     if rank != 0:
         return
-    flows_done = int(sw.request_sizes.sum())
     line = {
-        "metric": METRIC, "value": flows_done / paced_s, "unit": "flows/s",
+        "metric": METRIC, "value": job_flows / paced_s, "unit": "flows/s",
         "n_gpus": world, "steps": 1, "warmup": 1,
         "ms_per_step": paced_s * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
@@ -476,64 +469,107 @@ def run_served(args, ig, torch, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
-def roofline(stages, info, K, clocks, steps):
-    """Roofline of the dominant kernel (largest share of the timed steps).
+# Stages that time exactly one kernel (the others -- split, select,
+# canonical_sort, index_build -- bracket several kernels and the gaps
+# between them, so they cannot stand for one kernel's roofline).
+SINGLE_KERNEL_STAGES = {
+    "pair_insert": "pair_insert_kernel", "compact": "compact_kernel",
+    "coherence": "subset_kernel<K, ANY>", "support": "subset_kernel<K, COUNT>",
+    "evidence": "subset_kernel<K, SUM>",
+    "coherence_idx": "grouped_subset_kernel<K, ANY>",
+    "support_idx": "grouped_subset_kernel<K, COUNT>",
+    "evidence_idx": "grouped_subset_kernel<K, SUM>",
+    "coherence_tc": "subset_tc_kernel<ANY>", "support_tc": "subset_tc_kernel<COUNT>",
+    "evidence_tc": "subset_tc_kernel<SUM>",
+}
+
+
+def stage_roofline(name, ms, launches, work, info, K, clocks, steps):
+    """Roofline of one single-kernel stage over the timed steps.
 
     Subset-test kernels are bound by the integer pipe (LOP3 forms: 2K LOP3 per
     executed test, one per 32-bit half) or by the tensor cores (tcgen05 form:
     a 0/1 FP8 GEMM, 2 x 64K flops per executed test).  Executed tests come
     from the library: per timed stage for supports and evidence, per model
-    for the coherence windows.
+    for the coherence windows.  Memory-bound stages use byte models.
     """
-    name, (ms, launches, work) = max(stages.items(), key=lambda kv: kv[1][0])
     coh_idx = sum(info["coherence_tests_idx"]) * steps
     coh_tc = sum(info["coherence_tests_tc"]) * steps
     coh_dense = sum(info["coherence_tests"]) * steps - coh_idx - coh_tc
     tests = {"coherence": coh_dense, "coherence_tc": coh_tc, "coherence_idx": coh_idx}
     executed = tests.get(name, work)
-    out = {"kernel": name, "launches": int(launches),
-           "avg_launch_ms": ms / max(1, launches), "tests": int(executed)}
+    out = {"kernel": SINGLE_KERNEL_STAGES[name].replace("K,", f"{K},"), "stage": name,
+           "launches": int(launches), "avg_launch_ms": ms / max(1, launches)}
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
     peaks = load_peaks()
     if name in ("coherence", "support", "evidence", "coherence_idx", "support_idx",
                 "evidence_idx"):
         achieved = executed * 2 * K / (ms * 1e-3) / 1e12
         peak = LOP3_PER_SM_PER_CLK * 152 * sm_max * 1e6 / 1e12
-        out.update({"bound": "alu", "achieved": achieved, "peak": peak,
-                    "unit": "Tops/s (LOP3)", "frac": achieved / peak, "traffic": None,
+        out.update({"tests": int(executed), "bound": "alu", "achieved": achieved,
+                    "peak": peak, "unit": "Tops/s (LOP3)", "frac": achieved / peak,
                     "peak_source": f"{LOP3_PER_SM_PER_CLK} LOP3/SM/clk (measured) x 152 SMs "
                                    f"x {sm_max:.0f} MHz"})
     elif name in ("coherence_tc", "support_tc", "evidence_tc"):
         achieved = executed * 2 * 64 * K / (ms * 1e-3) / 1e12
         bf16 = (peaks or {}).get("bf16_tflops", FALLBACK_BF16_TFLOPS)
         peak = 2.0 * bf16
-        out.update({"bound": "tensor", "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s (FP8 0/1 GEMM)", "frac": achieved / peak, "traffic": None,
+        out.update({"tests": int(executed), "bound": "tensor", "achieved": achieved,
+                    "peak": peak, "unit": "TFLOP/s (FP8 0/1 GEMM)", "frac": achieved / peak,
                     "peak_source": ("measured bf16 burst x 2 (nominal FP8/BF16 ratio)"
                                     if peaks else "fallback bf16 x 2")})
     else:
         # Byte models (per timed step x steps) of the memory-bound stages:
         #   pair_insert: a hash set of K-word keys -- every pair compares its
         #     key with one stored key (8K B) and every distinct key is
-        #     written once (8K B);
-        #   compact: every distinct key written once (8K B);
-        #   canonical_sort: every distinct key read and written once.
-        # The pairs include each record with itself (the records of Eq. 1).
+        #     written once (8K B); the pairs include each record with itself
+        #     (the records of Eq. 1);
+        #   compact: every distinct key written once (8K B).
         U = sum(info["n_candidates"]) * steps
         pairs = (sum(info["n_pairs"]) + sum(info["n_train"])) * steps
-        model_bytes = {
-            "pair_insert": (pairs + U) * 8 * K,
-            "compact": U * 8 * K,
-            "canonical_sort": 2 * U * 8 * K,
-        }
+        nbytes = {"pair_insert": (pairs + U) * 8 * K, "compact": U * 8 * K}[name]
         hbm = (peaks or {}).get("hbm_gbs", FALLBACK_HBM_GBS)
-        nbytes = model_bytes.get(name)
-        achieved = nbytes / (ms * 1e-3) / 1e9 if nbytes else None
+        achieved = nbytes / (ms * 1e-3) / 1e9
         out.update({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved / hbm if achieved else None, "traffic": None,
-                    "algorithmic_bytes_per_step": (nbytes // steps) if nbytes else None,
+                    "frac": achieved / hbm,
+                    "algorithmic_bytes_per_launch": nbytes // max(1, launches),
                     "peak_source": "measured" if peaks else "fallback"})
+    out["traffic"] = dram_traffic(out["kernel"], K)
     return out
+
+
+def dram_traffic(kernel, K):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None if none was taken or the kernel's source changed since."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as f:
+            table = json.load(f)
+    except (OSError, ValueError):
+        return None
+    rec = table.get(kernel)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return rec["bytes_per_launch"] if digest == rec["source_sha256_16"] else None
+
+
+def roofline(stages, info, K, clocks, steps):
+    """Rooflines of every single-kernel stage that ran; the dominant one
+    (largest device time over the timed steps) is the headline."""
+    lines = {name: stage_roofline(name, ms, launches, work, info, K, clocks, steps)
+             for name, (ms, launches, work) in stages.items()
+             if name in SINGLE_KERNEL_STAGES and launches and ms > 0}
+    top = max(lines, key=lambda n: stages[n][0])
+    head = dict(lines[top])
+    head["all_kernels"] = {n: {"ms_per_step": round(stages[n][0] / steps, 4),
+                               "frac": round(r["frac"], 4), "bound": r["bound"]}
+                           for n, r in lines.items()}
+    return head
 
 
 def e2e_host_buffers(ig, w, tests, steps):

@@ -55,6 +55,11 @@ struct SharedPairKey {
   const uint64_t* b;
   __device__ __forceinline__ uint64_t operator()(int w) const { return a[w] & b[w]; }
 };
+template <int KT>
+struct RegKey {
+  const uint64_t (&w)[KT];
+  __device__ __forceinline__ uint64_t operator()(int k) const { return w[k]; }
+};
 struct GlobalPairKey {
   const uint64_t* a;
   const uint64_t* b;
@@ -97,10 +102,10 @@ constexpr int kPairThreads = 256;
 // Grid: x = column tile bj, y = row tile bi - band_lo.  Tiles with bj < bi
 // lie below the diagonal and exit at once.  Shared rows use an odd stride of
 // KT + 1 words so that lanes reading consecutive rows hit distinct banks.
-// The intersection is never held in registers: each use re-reads its words
-// from the two shared rows.  (More resident CTAs do not help: their shared
-// memory comes out of the L1 that caches the class's records, which every
-// key comparison reads.)
+// Each thread forms its intersection once in registers (about 64 in all);
+// more resident CTAs would not help anyway, since their shared memory comes
+// out of the L1 that caches the class's records, which every key comparison
+// reads.
 template <int KT>
 __global__ void __launch_bounds__(kPairThreads)
     pair_insert_kernel(const uint64_t* __restrict__ X, int64_t n, int64_t band_lo,
@@ -132,15 +137,16 @@ __global__ void __launch_bounds__(kPairThreads)
   for (int p = threadIdx.x; p < T * T; p += kPairThreads) {
     const int i = p / T, j = p - (p / T) * T;
     bool valid = (i0 + i < n) && (j0 + j < n) && (bi < bj || i <= j);
-    const SharedPairKey key{A + i * SKT, B + j * SKT};
+    uint64_t kw[KT];
     uint64_t any = 0;
     uint64_t h = hash_begin();
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
-      const uint64_t w = key(k);
-      any |= w;
-      h = hash_word(h, w);
+      kw[k] = A[i * SKT + k] & B[j * SKT + k];
+      any |= kw[k];
+      h = hash_word(h, kw[k]);
     }
+    const RegKey<KT> key{kw};
     h = hash_end(h);
     bool has = valid && any != 0;
     unsigned active = __ballot_sync(0xffffffffu, has);
