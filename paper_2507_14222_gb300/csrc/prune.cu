@@ -226,11 +226,16 @@ __device__ __forceinline__ void grouped_body(const GroupedParams& p, const WorkI
 
   uint32_t own[Q][H];
   bool valid[Q];
+  // warp_rows[q]: some lane of this warp holds own row q (warp-uniform; the
+  // rows of a block fill q = 0 first, so these form a prefix).  A warp skips
+  // the tests of a q that none of its lanes holds.
+  bool warp_rows[Q];
   unsigned long long own_score[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int64_t r = int64_t(q) * kGThreads + threadIdx.x;
     valid[q] = r < wi.own_count;
+    warp_rows[q] = int64_t(q) * kGThreads + (threadIdx.x & ~31u) < wi.own_count;
     const uint64_t* src = own_rows + (wi.own_begin + r) * KT;
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
@@ -281,7 +286,9 @@ __device__ __forceinline__ void grouped_body(const GroupedParams& p, const WorkI
     const int64_t left = s_hi - (s_lo + tile * TR);
     const int nr = int(left < TR ? left : TR);
     const uint32_t* rs = reinterpret_cast<const uint32_t*>(rows_s + st * TR * KT);
-    if (own_keyed) {
+    if (!warp_rows[0]) {
+      // no own row in this warp: nothing to test
+    } else if (own_keyed) {
       // pattern (own) inside record (streamed)?
 #pragma unroll 2
       for (int r = 0; r < nr; ++r) {
@@ -296,6 +303,7 @@ __device__ __forceinline__ void grouped_body(const GroupedParams& p, const WorkI
         }
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
+          if (!warp_rows[q]) break;
           uint32_t acc = 0;
 #pragma unroll
           for (int h = 0; h < H; ++h) acc |= own[q][h] & ~rh[h];
@@ -322,6 +330,7 @@ __device__ __forceinline__ void grouped_body(const GroupedParams& p, const WorkI
         }
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
+          if (!warp_rows[q]) break;
           uint32_t acc = 0;
 #pragma unroll
           for (int h = 0; h < H; ++h) acc |= rh[h] & ~own[q][h];
@@ -485,19 +494,36 @@ cudaError_t launch_grouped_subset(const GroupedArgs& a, cudaStream_t s) {
 // Blocks (group, own tile, stream range) with about `target` tests each;
 // in every group the larger side goes to registers (own).
 void build_work_items(const uint32_t* keyed_off, const uint32_t* multi_off, int groups,
-                      int own_tile, int str_tile, int64_t target, bool mode_sum, int max_q_param,
-                      int flip, std::vector<WorkItem>* items, int64_t* tests) {
+                      int own_tile, int str_tile, int64_t n_blocks_goal, bool mode_sum,
+                      int max_q_param, int flip, std::vector<WorkItem>* items, int64_t* tests) {
   const int max_q = std::max(1, std::min(own_tile / 256, max_q_param));
   items->clear();
   *tests = 0;
+  // The result side stays in registers unless the other side is at least
+  // twice as large (then per-hit atomics are the cheaper way to fill lanes).
+  auto orient = [&](int64_t nk, int64_t nm) {
+    return mode_sum ? (nk >= int64_t(flip) * nm) : (int64_t(flip) * nk >= nm);
+  };
+  // A block's cost is the lane-tests it executes: every stream row meets
+  // 32 * ceil(own rows / 32) lanes (warps without an own row skip the tests).
+  // Stream ranges are cut so that every block costs about the same, and
+  // there are about n_blocks_goal of them.
+  auto lanes = [](int64_t oc) { return ((oc + 31) / 32) * 32; };
+  int64_t total = 0;
+  for (int l = 0; l < groups; ++l) {
+    const int64_t nk = int64_t(keyed_off[l + 1]) - keyed_off[l];
+    const int64_t nm = int64_t(multi_off[l + 1]) - multi_off[l];
+    if (nk == 0 || nm == 0) continue;
+    const bool ok = orient(nk, nm);
+    total += lanes(ok ? nk : nm) * (ok ? nm : nk);
+  }
+  const int64_t target = std::max<int64_t>(total / std::max<int64_t>(1, n_blocks_goal), 1 << 16);
   for (int l = 0; l < groups; ++l) {
     const int64_t nk = int64_t(keyed_off[l + 1]) - keyed_off[l];
     const int64_t nm = int64_t(multi_off[l + 1]) - multi_off[l];
     if (nk == 0 || nm == 0) continue;
     *tests += nk * nm;
-    // The result side stays in registers unless the other side is at least
-    // twice as large (then per-hit atomics are the cheaper way to fill lanes).
-    const bool own_keyed = mode_sum ? (nk >= int64_t(flip) * nm) : (int64_t(flip) * nk >= nm);
+    const bool own_keyed = orient(nk, nm);
     const int64_t no = own_keyed ? nk : nm, ns = own_keyed ? nm : nk;
     const int64_t o0 = own_keyed ? keyed_off[l] : multi_off[l];
     const int64_t s0 = own_keyed ? multi_off[l] : keyed_off[l];
@@ -507,7 +533,7 @@ void build_work_items(const uint32_t* keyed_off, const uint32_t* multi_off, int 
     const int64_t tile = std::min<int64_t>(own_tile, 256 * q);
     for (int64_t o = 0; o < no; o += tile) {
       const int64_t oc = std::min<int64_t>(tile, no - o);
-      int64_t per = std::max<int64_t>(str_tile, target / std::max<int64_t>(1, oc));
+      int64_t per = std::max<int64_t>(str_tile, target / lanes(oc));
       per = ((per + str_tile - 1) / str_tile) * str_tile;
       for (int64_t r = 0; r < ns; r += per) {
         WorkItem w;
@@ -651,12 +677,9 @@ cudaError_t indexed_subset_prebuilt(int mode, const RecordIndex& idx, const Keye
   if (kx.n == 0 || idx.n_rows == 0) return cudaSuccess;
   const int L = idx.L, KT = idx.KT;
   std::vector<WorkItem> items;
-  int64_t tests = 0, total = 0;
-  for (int l = 0; l < L; ++l)
-    total += (int64_t(kx.h_off[l + 1]) - kx.h_off[l]) * (int64_t(idx.h_off[l + 1]) - idx.h_off[l]);
-  const int64_t target = std::max<int64_t>(total / (int64_t(num_sms()) * 8), 1 << 16);
+  int64_t tests = 0;
   build_work_items(kx.h_off.data(), idx.h_off.data(), L, grouped_own_per_cta(KT),
-                   grouped_rows_per_tile(KT), target, mode == MODE_SUM, max_q,
+                   grouped_rows_per_tile(KT), int64_t(num_sms()) * 8, mode == MODE_SUM, max_q,
                    std::max(1, flip_factor), &items, &tests);
   *tests_out = tests;
   if (items.empty()) return cudaSuccess;
