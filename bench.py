@@ -270,7 +270,7 @@ def run_ours(args):
     kt = 1
     while kt < w.n_words:
         kt *= 2
-    line["roofline"] = roofline(stages, info, kt, line["clocks"], args.steps)
+    line["roofline"] = roofline(stages, info, kt, line["clocks"], args.steps, w.name)
     if not args.no_e2e:
         line["e2e"] = e2e_host_buffers(ig, w, tests, max(2, min(args.steps, 5)))
     if not args.no_cpu_baseline:
@@ -484,7 +484,7 @@ SINGLE_KERNEL_STAGES = {
 }
 
 
-def stage_roofline(name, ms, launches, work, info, K, clocks, steps):
+def stage_roofline(name, ms, launches, work, info, K, clocks, steps, workload=None):
     """Roofline of one single-kernel stage over the timed steps.
 
     Subset-test kernels are bound by the integer pipe (LOP3 forms: 2K LOP3 per
@@ -534,13 +534,13 @@ def stage_roofline(name, ms, launches, work, info, K, clocks, steps):
                     "frac": achieved / hbm,
                     "algorithmic_bytes_per_launch": nbytes // max(1, launches),
                     "peak_source": "measured" if peaks else "fallback"})
-    out["traffic"] = dram_traffic(out["kernel"], K)
+    out["traffic"] = dram_traffic(out["kernel"], workload)
     return out
 
 
-def dram_traffic(kernel, K):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
-    None if none was taken or the kernel's source changed since."""
+def dram_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    summary, or None if none was taken or the kernel's source changed since."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as f:
@@ -548,7 +548,7 @@ def dram_traffic(kernel, K):
     except (OSError, ValueError):
         return None
     rec = table.get(kernel)
-    if not rec:
+    if not rec or rec.get("workload") != workload:
         return None
     src = os.path.join(ROOT, rec["source"])
     try:
@@ -558,10 +558,10 @@ def dram_traffic(kernel, K):
     return rec["bytes_per_launch"] if digest == rec["source_sha256_16"] else None
 
 
-def roofline(stages, info, K, clocks, steps):
+def roofline(stages, info, K, clocks, steps, workload=None):
     """Rooflines of every single-kernel stage that ran; the dominant one
     (largest device time over the timed steps) is the headline."""
-    lines = {name: stage_roofline(name, ms, launches, work, info, K, clocks, steps)
+    lines = {name: stage_roofline(name, ms, launches, work, info, K, clocks, steps, workload)
              for name, (ms, launches, work) in stages.items()
              if name in SINGLE_KERNEL_STAGES and launches and ms > 0}
     top = max(lines, key=lambda n: stages[n][0])
