@@ -72,25 +72,61 @@ __global__ void small_scan_kernel(const uint32_t* __restrict__ cnt, int len,
   if (threadIdx.x == 1023) off[len] = part[1023];
 }
 
+// Writes the rows of one round of copies for a warp: lane j of the warp
+// has a copy to place (has) at row pos of out, with the contents of its
+// record, staged in shared memory at rec + (rec0 + j) * KT.  The warp writes
+// 32 / KT rows per store, each row as KT consecutive 8-byte words, so a
+// store covers whole rows instead of one word of 32 scattered rows.
+__device__ __forceinline__ void warp_write_rows(const uint64_t* rec, int rec0, int KT,
+                                                bool has, uint32_t pos,
+                                                uint64_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int per = 32 / KT;
+  const int wr = lane / KT, ww = lane - wr * KT;
+  for (int r0 = 0; r0 < 32; r0 += per) {
+    const int src = r0 + wr;
+    const uint32_t p = __shfl_sync(0xffffffffu, pos, src);
+    const int h = __shfl_sync(0xffffffffu, has ? 1 : 0, src);
+    if (h) out[int64_t(p) * KT + ww] = rec[(rec0 + src) * KT + ww];
+  }
+}
+
+// Stages rows [i0, i0 + blockDim.x) (K words each, zero words up to KT) in
+// shared memory.
+__device__ __forceinline__ void stage_rows(const uint64_t* __restrict__ rows, int64_t n,
+                                           int stride, int K, int KT, int64_t i0,
+                                           uint64_t* rec) {
+  const int nb = blockDim.x;
+  for (int e = threadIdx.x; e < nb * KT; e += nb) {
+    const int r = e / KT, q = e - r * KT;
+    rec[e] = (i0 + r < n && q < K) ? rows[(i0 + r) * stride + q] : 0ull;
+  }
+}
+
 // Copies row i into the group of every item it contains.  A block first
 // counts its copies per item in shared memory, reserves one range per item
-// in the group with a single global atomic, then places its copies with
+// in the group with a single global atomic, and places its copies with
 // shared-memory atomics only (the order inside a group does not matter).
-constexpr int kScatterThreads = 256;
-
-__global__ void __launch_bounds__(kScatterThreads)
-    multi_scatter_kernel(const uint64_t* __restrict__ rows, int64_t n, int stride, int K, int KT,
-                         int L, const uint32_t* __restrict__ off, uint32_t* __restrict__ cursor,
-                         uint64_t* __restrict__ out, uint32_t* __restrict__ ids) {
-  extern __shared__ uint32_t sh[];
-  uint32_t* cnt = sh;       // [L]
-  uint32_t* base = sh + L;  // [L]
+// The copies are written a round at a time per warp -- round t places the
+// t-th item of each of the warp's records -- as whole rows (warp_write_rows).
+// Shared memory: blockDim.x * KT words of rows, then 2 * L counters.
+__global__ void multi_scatter_kernel(const uint64_t* __restrict__ rows, int64_t n, int stride,
+                                     int K, int KT, int L, const uint32_t* __restrict__ off,
+                                     uint32_t* __restrict__ cursor, uint64_t* __restrict__ out,
+                                     uint32_t* __restrict__ ids) {
+  extern __shared__ uint64_t shm[];
+  uint64_t* rec = shm;
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(rec + blockDim.x * KT);  // [L]
+  uint32_t* base = cnt + L;                                            // [L]
+  const int64_t i0 = int64_t(blockIdx.x) * blockDim.x;
+  stage_rows(rows, n, stride, K, KT, i0, rec);
   for (int l = threadIdx.x; l < L; l += blockDim.x) cnt[l] = 0;
   __syncthreads();
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const bool valid = i < n;
-  for (int k = 0; valid && k < K; ++k) {
-    uint64_t x = rows[i * stride + k];
+  const uint64_t* my = rec + threadIdx.x * KT;
+  int n_items = 0;
+  for (int k = 0; k < K; ++k) {
+    uint64_t x = my[k];
+    n_items += __popcll(x);
     while (x) {
       const int b = __ffsll(static_cast<long long>(x)) - 1;
       x &= x - 1;
@@ -104,62 +140,87 @@ __global__ void __launch_bounds__(kScatterThreads)
     cnt[l] = 0;
   }
   __syncthreads();
-  if (!valid) return;
-  uint64_t w[IG_MAX_KT_WORDS];
-  for (int q = 0; q < KT; ++q) w[q] = q < K ? rows[i * stride + q] : 0ull;
-  for (int k = 0; k < K; ++k) {
-    uint64_t x = w[k];
-    while (x) {
+  int rounds = n_items;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) rounds = max(rounds, __shfl_xor_sync(0xffffffffu, rounds, o));
+  const int rec0 = threadIdx.x & ~31;
+  int k = 0;
+  uint64_t x = K > 0 ? my[0] : 0ull;
+  for (int t = 0; t < rounds; ++t) {
+    const bool has = t < n_items;
+    uint32_t pos = 0;
+    if (has) {
+      while (x == 0ull) x = my[++k];
       const int b = __ffsll(static_cast<long long>(x)) - 1;
       x &= x - 1;
       const int l = k * 64 + b;
-      const uint32_t pos = base[l] + atomicAdd(&cnt[l], 1u);
-      for (int q = 0; q < KT; ++q) out[int64_t(pos) * KT + q] = w[q];
-      ids[pos] = uint32_t(i);
+      pos = base[l] + atomicAdd(&cnt[l], 1u);
+      ids[pos] = uint32_t(i0 + threadIdx.x);
     }
+    warp_write_rows(rec, rec0, KT, has, pos, out);
   }
 }
 
 // key[i] = the item of row i with the smallest freq (lowest item on ties),
-// or L when one of its items has freq 0 (or the row is empty).
+// or L when one of its items has freq 0 (or the row is empty); kcount[g]
+// counts the rows keyed to g.  freq is read from a shared copy and the
+// counts are aggregated per block: popular keys would otherwise take one
+// global atomic per row on a few addresses.  Shared memory: 2 * L + 1
+// counters.
 __global__ void key_item_kernel(const uint64_t* __restrict__ rows, int64_t n, int stride, int K,
                                 int L, const uint32_t* __restrict__ freq,
                                 uint32_t* __restrict__ key, uint32_t* __restrict__ kcount) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint32_t best = 0xffffffffu;
-  int best_l = L;
-  for (int k = 0; k < K; ++k) {
-    uint64_t x = rows[i * stride + k];
-    while (x) {
-      const int b = __ffsll(static_cast<long long>(x)) - 1;
-      x &= x - 1;
-      const int l = k * 64 + b;
-      const uint32_t f = freq[l];
-      if (f < best) {
-        best = f;
-        best_l = l;
-      }
-    }
-  }
-  if (best == 0u) best_l = L;
-  key[i] = uint32_t(best_l);
-  atomicAdd(kcount + best_l, 1u);
-}
-
-// Files row i under its key (block-aggregated like multi_scatter_kernel).
-__global__ void __launch_bounds__(kScatterThreads)
-    keyed_scatter_kernel(const uint64_t* __restrict__ rows, int64_t n, int stride, int K, int KT,
-                         int groups, const uint32_t* __restrict__ key,
-                         const uint32_t* __restrict__ off, uint32_t* __restrict__ cursor,
-                         uint64_t* __restrict__ out, uint32_t* __restrict__ ids,
-                         const uint64_t* __restrict__ payload, uint64_t* __restrict__ payload_out) {
-  extern __shared__ uint32_t sh[];
-  uint32_t* cnt = sh;            // [groups]
-  uint32_t* base = sh + groups;  // [groups]
-  for (int l = threadIdx.x; l < groups; l += blockDim.x) cnt[l] = 0;
+  extern __shared__ uint32_t shk[];
+  uint32_t* f_s = shk;          // [L]
+  uint32_t* c_s = shk + L;      // [L + 1]
+  for (int l = threadIdx.x; l < L; l += blockDim.x) f_s[l] = freq[l];
+  for (int l = threadIdx.x; l <= L; l += blockDim.x) c_s[l] = 0;
   __syncthreads();
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) {
+    uint32_t best = 0xffffffffu;
+    int best_l = L;
+    for (int k = 0; k < K; ++k) {
+      uint64_t x = rows[i * stride + k];
+      while (x) {
+        const int b = __ffsll(static_cast<long long>(x)) - 1;
+        x &= x - 1;
+        const int l = k * 64 + b;
+        const uint32_t f = f_s[l];
+        if (f < best) {
+          best = f;
+          best_l = l;
+        }
+      }
+    }
+    if (best == 0u) best_l = L;
+    key[i] = uint32_t(best_l);
+    atomicAdd(&c_s[best_l], 1u);
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l <= L; l += blockDim.x)
+    if (c_s[l]) atomicAdd(kcount + l, c_s[l]);
+}
+
+// Files row i under its key (block-aggregated like multi_scatter_kernel;
+// rows written whole by warp_write_rows).  Shared memory: blockDim.x * KT
+// words of rows, then 2 * groups counters.
+__global__ void keyed_scatter_kernel(const uint64_t* __restrict__ rows, int64_t n, int stride,
+                                     int K, int KT, int groups, const uint32_t* __restrict__ key,
+                                     const uint32_t* __restrict__ off,
+                                     uint32_t* __restrict__ cursor, uint64_t* __restrict__ out,
+                                     uint32_t* __restrict__ ids,
+                                     const uint64_t* __restrict__ payload,
+                                     uint64_t* __restrict__ payload_out) {
+  extern __shared__ uint64_t shm[];
+  uint64_t* rec = shm;
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(rec + blockDim.x * KT);  // [groups]
+  uint32_t* base = cnt + groups;                                       // [groups]
+  const int64_t i0 = int64_t(blockIdx.x) * blockDim.x;
+  stage_rows(rows, n, stride, K, KT, i0, rec);
+  for (int l = threadIdx.x; l < groups; l += blockDim.x) cnt[l] = 0;
+  __syncthreads();
+  const int64_t i = i0 + threadIdx.x;
   const bool valid = i < n;
   const uint32_t l = valid ? key[i] : 0u;
   if (valid) atomicAdd(&cnt[l], 1u);
@@ -170,11 +231,19 @@ __global__ void __launch_bounds__(kScatterThreads)
     cnt[g] = 0;
   }
   __syncthreads();
-  if (!valid) return;
-  const uint32_t pos = base[l] + atomicAdd(&cnt[l], 1u);
-  for (int q = 0; q < KT; ++q) out[int64_t(pos) * KT + q] = q < K ? rows[i * stride + q] : 0ull;
-  ids[pos] = uint32_t(i);
-  if (payload) payload_out[pos] = payload[i];
+  uint32_t pos = 0;
+  if (valid) {
+    pos = base[l] + atomicAdd(&cnt[l], 1u);
+    ids[pos] = uint32_t(i);
+    if (payload) payload_out[pos] = payload[i];
+  }
+  warp_write_rows(rec, threadIdx.x & ~31, KT, valid, pos, out);
+}
+
+// Threads per block of the scatter kernels: small inputs use narrow blocks
+// so that they still spread over the SMs.
+static int scatter_threads(int64_t n) {
+  return n >= int64_t(num_sms()) * 4 * 256 ? 256 : (n >= int64_t(num_sms()) * 4 * 64 ? 64 : 32);
 }
 
 // ---- the grouped subset kernel ------------------------------------------------
@@ -420,8 +489,10 @@ cudaError_t launch_multi_scatter(const uint64_t* rows, int64_t n, int stride, in
                                  int L, const uint32_t* off, uint32_t* cursor, uint64_t* out,
                                  uint32_t* ids, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  multi_scatter_kernel<<<unsigned(ceil_div(n, kScatterThreads)), kScatterThreads,
-                         size_t(2) * L * 4, s>>>(rows, n, stride, K, KT, L, off, cursor, out, ids);
+  const int nb = scatter_threads(n);
+  const size_t smem = size_t(nb) * KT * 8 + size_t(2) * L * 4;
+  multi_scatter_kernel<<<unsigned(ceil_div(n, nb)), nb, smem, s>>>(rows, n, stride, K, KT, L, off,
+                                                                   cursor, out, ids);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -430,8 +501,8 @@ cudaError_t launch_key_item(const uint64_t* rows, int64_t n, int stride, int K, 
                             const uint32_t* freq, uint32_t* key, uint32_t* kcount,
                             cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  key_item_kernel<<<unsigned(ceil_div(n, 256)), 256, 0, s>>>(rows, n, stride, K, L, freq, key,
-                                                             kcount);
+  key_item_kernel<<<unsigned(ceil_div(n, 256)), 256, size_t(2 * L + 1) * 4, s>>>(
+      rows, n, stride, K, L, freq, key, kcount);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -441,9 +512,10 @@ cudaError_t launch_keyed_scatter(const uint64_t* rows, int64_t n, int stride, in
                                  uint32_t* cursor, uint64_t* out, uint32_t* ids,
                                  const uint64_t* payload, uint64_t* payload_out, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  keyed_scatter_kernel<<<unsigned(ceil_div(n, kScatterThreads)), kScatterThreads,
-                         size_t(2) * groups * 4, s>>>(rows, n, stride, K, KT, groups, key, off,
-                                                      cursor, out, ids, payload, payload_out);
+  const int nb = scatter_threads(n);
+  const size_t smem = size_t(nb) * KT * 8 + size_t(2) * groups * 4;
+  keyed_scatter_kernel<<<unsigned(ceil_div(n, nb)), nb, smem, s>>>(
+      rows, n, stride, K, KT, groups, key, off, cursor, out, ids, payload, payload_out);
   count_launches(1);
   return cudaGetLastError();
 }
