@@ -86,8 +86,17 @@ __device__ int table_insert(const PairTable& t, const uint64_t* __restrict__ X, 
       const uint64_t* ca = X + ((cur >> kIdxBits) & kIdxMask) * KT;
       const uint64_t* cb = X + (cur & kIdxMask) * KT;
       bool same = true;
+      if constexpr (KT >= 2) {
+        // Rows of KT >= 2 words are 16-byte aligned: two words per load.
 #pragma unroll
-      for (int w = 0; w < KT; ++w) same &= ((__ldg(ca + w) & __ldg(cb + w)) == key(w));
+        for (int w = 0; w < KT; w += 2) {
+          const ulonglong2 va = __ldg(reinterpret_cast<const ulonglong2*>(ca + w));
+          const ulonglong2 vb = __ldg(reinterpret_cast<const ulonglong2*>(cb + w));
+          same &= ((va.x & vb.x) == key(w)) & ((va.y & vb.y) == key(w + 1));
+        }
+      } else {
+        same = (__ldg(ca) & __ldg(cb)) == key(0);
+      }
       if (same) return 0;
     }
     slot = (slot + 1) & t.mask;

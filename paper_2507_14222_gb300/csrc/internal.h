@@ -60,6 +60,10 @@ cudaError_t launch_encode(const uint16_t* codes, int64_t n, int F,
                           const uint32_t* offsets, const uint16_t* cards,
                           uint64_t* out, int K, int* status, cudaStream_t s);
 
+// Exclusive scan of cnt[0..len) into off[0..len] (off[len] = total), one
+// block (prune.cu).
+cudaError_t launch_small_scan(const uint32_t* cnt, int len, uint32_t* off, cudaStream_t s);
+
 // Stable split of rows (stride K) by label into class arrays (stride KT):
 // normal rows to x0, attack rows to x1.  counts[0..1] receive the sizes.
 cudaError_t launch_split(const uint64_t* rows, const uint8_t* labels, int64_t n,
