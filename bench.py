@@ -72,7 +72,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel", type=int, default=0,
                     help="subset-test form: 0 default, 1 integer pipe, 2 tensor cores, "
-                         "3 item index")
+                         "3 item index, 4 item index on the tensor cores")
     return ap.parse_args()
 
 
@@ -255,7 +255,8 @@ def run_ours(args):
         "tests_per_step": tests,
         "patterns": {"attack": info["n_patterns"][1], "normal": info["n_patterns"][0],
                      "candidates": list(info["n_candidates"][::-1])},
-        "subset_kernel": {1: "lop3", 2: "tcgen05", 3: "item-index"}[info["subset_kernel"]],
+        "subset_kernel": {1: "lop3", 2: "tcgen05", 3: "item-index",
+                          4: "item-index-tcgen05"}[info["subset_kernel"]],
         "executed_tests_per_step": {
             "coherence": sum(info["coherence_tests"]),
             "support": sum(info["support_tests"]),
@@ -498,19 +499,23 @@ def stage_roofline(name, ms, launches, work, info, K, clocks, steps, workload=No
     coh_dense = sum(info["coherence_tests"]) * steps - coh_idx - coh_tc
     tests = {"coherence": coh_dense, "coherence_tc": coh_tc, "coherence_idx": coh_idx}
     executed = tests.get(name, work)
-    out = {"kernel": SINGLE_KERNEL_STAGES[name].replace("K,", f"{K},"), "stage": name,
+    kernel = SINGLE_KERNEL_STAGES[name]
+    index_tc = info.get("subset_kernel") == 4 and name.endswith("_idx")
+    if index_tc:  # item-index blocks run by the tensor-core kernel
+        kernel = kernel.replace("grouped_subset_kernel<K, ", "subset_tc_kernel<") + " (index blocks)"
+    out = {"kernel": kernel.replace("K,", f"{K},"), "stage": name,
            "launches": int(launches), "avg_launch_ms": ms / max(1, launches)}
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
     peaks = load_peaks()
     if name in ("coherence", "support", "evidence", "coherence_idx", "support_idx",
-                "evidence_idx"):
+                "evidence_idx") and not index_tc:
         achieved = executed * 2 * K / (ms * 1e-3) / 1e12
         peak = LOP3_PER_SM_PER_CLK * 152 * sm_max * 1e6 / 1e12
         out.update({"tests": int(executed), "bound": "alu", "achieved": achieved,
                     "peak": peak, "unit": "Tops/s (LOP3)", "frac": achieved / peak,
                     "peak_source": f"{LOP3_PER_SM_PER_CLK} LOP3/SM/clk (measured) x 152 SMs "
                                    f"x {sm_max:.0f} MHz"})
-    elif name in ("coherence_tc", "support_tc", "evidence_tc"):
+    elif name in ("coherence_tc", "support_tc", "evidence_tc") or index_tc:
         achieved = executed * 2 * 64 * K / (ms * 1e-3) / 1e12
         bf16 = (peaks or {}).get("bf16_tflops", FALLBACK_BF16_TFLOPS)
         peak = 2.0 * bf16

@@ -76,8 +76,9 @@ typedef struct {
    * is 2, 4 or 8, else 1; 3 = item index: each pattern is tested only
    * against the records holding its rarest item (exact), in integer-pipe
    * blocks, falling back to 2 when records are too dense for the index to
-   * pay off.  The choice is kept in the model and used by ig_score too.
-   * Results are identical for every choice. */
+   * pay off; 4 = item index with its blocks run as tcgen05 0/1 GEMMs (K
+   * rounded up to 2, 4 or 8; else as 3).  The choice is kept in the model
+   * and used by ig_score too.  Results are identical for every choice. */
   int32_t subset_kernel;
   /* Tiling of the item-index form (results never depend on them; 0 picks
    * the default): the most own rows per thread of a block (1, 2 or 4, i.e.
@@ -100,7 +101,8 @@ typedef struct {
   int64_t coherence_tests_tc[2]; /* ... of which on the tensor cores */
   int64_t coherence_tests_idx[2]; /* ... of which through the item index */
   int64_t support_tests[2];      /* subset tests the support step executed */
-  int32_t subset_kernel;       /* form in use: 1 integer pipe, 2 tensor cores, 3 item index */
+  int32_t subset_kernel;       /* form in use: 1 integer pipe, 2 tensor cores, 3 item index,
+                                  4 item index on the tensor cores */
   int32_t reserved;
 } ig_model_info_t;
 

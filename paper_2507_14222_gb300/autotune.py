@@ -19,13 +19,15 @@ import time
 from . import buildlib as _build
 
 # Candidate configurations: the item index with several block shapes and
-# orientation policies, the tensor-core GEMM, and the plain integer kernel.
+# orientation policies, the item index on the tensor cores, the tensor-core
+# GEMM, and the plain integer kernel.
 CANDIDATES = [
     {"subset_kernel": 3, "index_max_q": 4, "index_flip_factor": 2},
     {"subset_kernel": 3, "index_max_q": 2, "index_flip_factor": 2},
     {"subset_kernel": 3, "index_max_q": 1, "index_flip_factor": 2},
     {"subset_kernel": 3, "index_max_q": 4, "index_flip_factor": 1},
     {"subset_kernel": 3, "index_max_q": 4, "index_flip_factor": 1 << 20},
+    {"subset_kernel": 4},
     {"subset_kernel": 2},
     {"subset_kernel": 1},
 ]

@@ -7,11 +7,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <atomic>
 #include <condition_variable>
 #include <functional>
 #include <thread>
@@ -125,6 +125,33 @@ void prof_drain_locked() {
 }
 
 // ---- device buffers ---------------------------------------------------------
+// Freed stream-ordered memory stays cached in the device's default pool --
+// up to an eighth of the device's memory, at most 32 GiB -- instead of going
+// back to the driver at every synchronization: a fit allocates and frees its
+// buffers between several synchronizations, and remapping them each time
+// costs more than the kernels that use them.  Set once per device; a
+// property of this process's pool, not of the GPU.
+static void keep_pool_memory() {
+  static std::atomic<int> done[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  if (done[dev].load(std::memory_order_relaxed)) return;
+  done[dev].store(1, std::memory_order_relaxed);
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  uint64_t keep = std::min<uint64_t>(uint64_t(total_b) / 8, uint64_t(32) << 30);
+  if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess)
+    cudaGetLastError();
+}
+
 // Stream-ordered allocation; freed on the same stream when the owner goes
 // out of scope (or kept by release()).
 template <class T>
@@ -141,6 +168,7 @@ struct DevBuf {
   }
   cudaError_t alloc(size_t count, cudaStream_t stream) {
     reset();
+    keep_pool_memory();
     s = stream;
     if (count == 0) count = 1;
     return cudaMallocAsync(reinterpret_cast<void**>(&p), count * sizeof(T), stream);
@@ -359,7 +387,7 @@ struct ig_model {
   uint64_t* score[2] = {nullptr, nullptr};     // pad_rows entries
   int reg3 = 0;
   double mu = 0, sigma = 0, r = 0, thr = 0;
-  int subset_kernel = 1;                       // 1 integer pipe, 2 tensor cores, 3 item index
+  int subset_kernel = 1;  // 1 integer pipe, 2 tensor cores, 3 item index, 4 item index on tensor cores
   uint8_t* pat_img[2] = {nullptr, nullptr};    // tensor-core images of P^c
   int64_t coh_tests[2] = {0, 0};               // coherence tests executed
   int64_t coh_tests_tc[2] = {0, 0};            // ... of which on the tensor cores
@@ -594,7 +622,7 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
       prm.index_max_q != 4)
     return fail(IG_E_INVAL, "ig_fit: index_max_q must be 0, 1, 2 or 4");
   if (prm.index_flip_factor < 0) return fail(IG_E_INVAL, "ig_fit: negative index_flip_factor");
-  if (prm.subset_kernel < 0 || prm.subset_kernel > 3)
+  if (prm.subset_kernel < 0 || prm.subset_kernel > 4)
     return fail(IG_E_INVAL, "ig_fit: unknown subset_kernel %d", prm.subset_kernel);
   if (prm.reg3_enabled && !std::isfinite(prm.r))
     return fail(IG_E_INVAL, "ig_fit: Regulation 3 needs a finite r");
@@ -645,9 +673,11 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
   // Subset-test form: the item index (default, and where K allows it), the
   // tensor-core GEMM, or the plain integer-pipe kernel.  Dense steps of the
   // index form run on the tensor cores where K allows.
-  const bool pruned = (prm.subset_kernel == 0 || prm.subset_kernel == 3) && KT >= 2;
+  const bool pruned =
+      (prm.subset_kernel == 0 || prm.subset_kernel == 3 || prm.subset_kernel == 4) && KT >= 2;
   const bool tc = prm.subset_kernel != 1 && igk::tc_supported(KT);
-  m->subset_kernel = pruned ? 3 : (tc ? 2 : 1);
+  const bool index_tc = prm.subset_kernel == 4 && igk::tc_supported(KT);
+  m->subset_kernel = pruned ? (index_tc ? 4 : 3) : (tc ? 2 : 1);
   m->index_max_q = prm.index_max_q ? prm.index_max_q : 4;
   m->index_flip = prm.index_flip_factor ? prm.index_flip_factor : 2;
   // Item indexes of both classes' records: used by the other class's
@@ -752,6 +782,7 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
           a.prof_stage = S_COHERENCE_IDX;
           a.max_q = m->index_max_q;
           a.flip_factor = m->index_flip;
+          a.tc = m->subset_kernel == 4 ? 1 : 0;
           IG_CUDA(igk::indexed_subset(a, s), "ig_fit: coherence");
         }
         if (t >= 0) {
@@ -846,6 +877,7 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
         a.prof_stage = S_SUPPORT_IDX;
         a.max_q = m->index_max_q;
         a.flip_factor = m->index_flip;
+        a.tc = m->subset_kernel == 4 ? 1 : 0;
         IG_CUDA(igk::indexed_subset(a, s), "ig_fit: support");
       }
       if (t >= 0) {
@@ -967,6 +999,7 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
       a.prof_stage = S_EVIDENCE_IDX;
       a.max_q = m->index_max_q;
       a.flip_factor = m->index_flip;
+      a.tc = m->subset_kernel == 4 ? 1 : 0;
       IG_CUDA(igk::indexed_subset(a, s), "ig_fit: Regulation 3 evidence");
     }
     if (t_idx >= 0) {
@@ -1258,7 +1291,7 @@ int ig_score(const ig_model* m, const uint64_t* rows, int64_t n_rows, int64_t* A
   DevBuf<uint8_t> test_img;
   // The item index pays for its build (and its host round trips) only on
   // batches of some size; smaller batches stream the patterns densely.
-  const bool pruned = m->subset_kernel == 3 && n_rows >= kIndexMinRows;
+  const bool pruned = m->subset_kernel >= 3 && n_rows >= kIndexMinRows;
   bool tc = m->subset_kernel >= 2 && igk::tc_supported(m->KT) && m->pat_img[0] && m->pat_img[1];
   bool done[2] = {false, false};
   IndexHolder test_idx;
@@ -1279,7 +1312,8 @@ int ig_score(const ig_model* m, const uint64_t* rows, int64_t n_rows, int64_t* A
       if (m->pidx[c] && n_rows * 8 < m->n_pat[c]) {
         IG_CUDA(igk::indexed_subset_prebuilt(igk::MODE_SUM, test_idx.idx, *m->pidx[c], nullptr,
                                              c == 1 ? A.d : N.d, d_status.p, &t, S_EVIDENCE_IDX,
-                                             m->index_max_q, m->index_flip, s),
+                                             m->index_max_q, m->index_flip,
+                                             m->subset_kernel == 4 ? 1 : 0, s),
                 "ig_score: evidence");
         done[c] = true;
         igk::prof_add_work(S_EVIDENCE_IDX, t);
@@ -1299,6 +1333,7 @@ int ig_score(const ig_model* m, const uint64_t* rows, int64_t n_rows, int64_t* A
       a.prof_stage = S_EVIDENCE_IDX;
       a.max_q = m->index_max_q;
       a.flip_factor = m->index_flip;
+      a.tc = m->subset_kernel == 4 ? 1 : 0;
       IG_CUDA(igk::indexed_subset(a, s), "ig_score: evidence");
       done[c] = true;
       igk::prof_add_work(S_EVIDENCE_IDX, t);

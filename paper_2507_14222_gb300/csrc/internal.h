@@ -135,6 +135,21 @@ bool tc_supported(int KT);
 size_t tc_image_bytes(int64_t n, int KT, bool own_side);
 cudaError_t launch_expand(const uint64_t* rows, int64_t n, int stride, int KT, bool complement,
                           bool own_side, uint8_t* img, cudaStream_t s);
+// A 128-row image tile made from rows [begin, begin + count) of a grouped
+// row array (item index), and one block of work for the tensor-core kernel
+// on such tiles: own tile a_tile (own_count valid rows, the first being
+// grouped row own_first) against stream tiles b_tile .. b_tile + b_tiles - 1
+// (str_count valid rows, the first being grouped row str_first).
+struct TcTile {
+  int64_t begin;
+  int32_t count;
+  int32_t pad;
+};
+struct TcItem {
+  int64_t a_tile, b_tile, own_first, str_first;
+  int32_t own_count, b_tiles, str_count, pad;
+};
+
 struct TcArgs {
   int mode;
   int KT;
@@ -213,6 +228,7 @@ struct IndexedArgs {
   int prof_stage = -1;  // stage under which the grouped kernel is timed
   int max_q = 4;        // most own rows per thread of a block (1, 2, 4)
   int flip_factor = 2;  // side ratio before the non-result side goes to registers
+  int tc = 0;           // run the blocks on the tensor cores (KT 2, 4, 8)
 };
 cudaError_t indexed_subset(const IndexedArgs& a, cudaStream_t s);
 
@@ -232,11 +248,19 @@ cudaError_t build_keyed_index(const uint64_t* keyed, int64_t n, int stride, int 
                               const uint32_t* freq, const uint64_t* score, KeyedIndex* out,
                               cudaStream_t s);
 void release_keyed_index(KeyedIndex* k, cudaStream_t s);
+// The item-index test with its blocks run on the tensor cores (KT 2, 4, 8):
+// the result side -- patterns for MODE_ANY / MODE_COUNT, records for
+// MODE_SUM -- goes to resident 128-row tiles, the other side streams; both
+// are expanded to per-group tile images first.  Same results as the integer
+// grouped kernel; *tests_out as for indexed_subset_prebuilt.
+cudaError_t indexed_subset_tc(int mode, const RecordIndex& idx, const KeyedIndex& kx,
+                              uint32_t* out_u32, unsigned long long* out_u64, int* status,
+                              int64_t* tests_out, int prof_stage, cudaStream_t s);
 // indexed_subset with a prebuilt pattern side; no synchronization.
 cudaError_t indexed_subset_prebuilt(int mode, const RecordIndex& idx, const KeyedIndex& kx,
                                     uint32_t* out_u32, unsigned long long* out_u64, int* status,
                                     int64_t* tests_out, int prof_stage, int max_q,
-                                    int flip_factor, cudaStream_t s);
+                                    int flip_factor, int tc, cudaStream_t s);
 // freq[l] += number of the n rows holding item l (rows of stride `stride`, K words).
 cudaError_t launch_item_histogram(const uint64_t* rows, int64_t n, int stride, int K, int L,
                                   uint32_t* freq, cudaStream_t s);

@@ -744,10 +744,12 @@ cudaError_t build_keyed_index(const uint64_t* keyed, int64_t n, int stride, int 
 cudaError_t indexed_subset_prebuilt(int mode, const RecordIndex& idx, const KeyedIndex& kx,
                                     uint32_t* out_u32, unsigned long long* out_u64, int* status,
                                     int64_t* tests_out, int prof_stage, int max_q,
-                                    int flip_factor, cudaStream_t s) {
+                                    int flip_factor, int tc, cudaStream_t s) {
   *tests_out = 0;
   if (kx.n == 0 || idx.n_rows == 0) return cudaSuccess;
   const int L = idx.L, KT = idx.KT;
+  if (tc && tc_supported(KT))
+    return indexed_subset_tc(mode, idx, kx, out_u32, out_u64, status, tests_out, prof_stage, s);
   std::vector<WorkItem> items;
   int64_t tests = 0;
   build_work_items(kx.h_off.data(), idx.h_off.data(), L, grouped_own_per_cta(KT),
@@ -796,7 +798,7 @@ cudaError_t indexed_subset(const IndexedArgs& a, cudaStream_t s) {
                                     a.mode == MODE_SUM ? a.keyed_score : nullptr, &kx, s);
   if (e != cudaSuccess) return e;
   e = indexed_subset_prebuilt(a.mode, idx, kx, a.out_u32, a.out_u64, a.status, a.tests_out,
-                              a.prof_stage, a.max_q, a.flip_factor, s);
+                              a.prof_stage, a.max_q, a.flip_factor, a.tc, s);
   release_keyed_index(&kx, s);
   return e;
 }

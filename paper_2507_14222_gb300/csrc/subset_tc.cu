@@ -25,6 +25,10 @@
 // MMA reads (K-major, 128-byte swizzle: 8-row x 128-byte atoms, the 16-byte
 // chunk c of row r stored at chunk c ^ (r mod 8)), so every tile is one
 // contiguous bulk copy.  expand_kernel writes these images from packed rows.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -70,6 +74,42 @@ __global__ void expand_kernel(const uint64_t* __restrict__ rows, int64_t n, int 
   if (g < n) {
     const int word = k0 >> 6;
     uint64_t w = word < stride ? rows[g * stride + word] : 0ull;
+    if (complement) w = ~w;
+    bits = uint32_t((w >> (k0 & 63)) & 0xffffu);
+  }
+  uint32_t v[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint32_t x = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) x |= ((bits >> (4 * q + b)) & 1u) ? (0x38u << (8 * b)) : 0u;
+    v[q] = x;
+  }
+  *reinterpret_cast<uint4*>(img + tile * (int64_t(R) * KT * 64) + int64_t(katom) * R * 128 +
+                            r * 128 + pos * 16) = make_uint4(v[0], v[1], v[2], v[3]);
+}
+
+// The same images for tiles listed in a table: image tile t holds rows
+// [tiles[t].begin, tiles[t].begin + tiles[t].count) of `rows` (count <= R),
+// then zero rows.  Used for the item index, whose groups each start a tile.
+template <int KT>
+__global__ void expand_tiles_kernel(const uint64_t* __restrict__ rows, int stride,
+                                    int complement, int R, const TcTile* __restrict__ tiles,
+                                    int64_t ntiles, uint8_t* __restrict__ img) {
+  const int64_t chunks_per_tile = int64_t(R) * KT * 4;
+  const int64_t id = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (id >= ntiles * chunks_per_tile) return;
+  const int64_t tile = id / chunks_per_tile;
+  const int64_t rem = id - tile * chunks_per_tile;
+  const int katom = int(rem / (R * 8));
+  const int rem2 = int(rem - int64_t(katom) * R * 8);
+  const int r = rem2 >> 3, pos = rem2 & 7;
+  const int c = pos ^ (r & 7);
+  const int k0 = katom * 128 + c * 16;
+  const TcTile tt = tiles[tile];
+  uint32_t bits = 0;
+  if (r < tt.count) {
+    uint64_t w = rows[(tt.begin + r) * stride + (k0 >> 6)];
     if (complement) w = ~w;
     bits = uint32_t((w >> (k0 & 63)) & 0xffffu);
   }
@@ -164,6 +204,11 @@ struct TcParams {
   uint32_t* out_u32;
   unsigned long long* out_u64;
   int* status;
+  // Item-index blocks: when set, CTA b runs items[b] instead of the dense
+  // (own tile, stream split) grid; results go to out[own_ids[own row]] and
+  // score indexes the streamed rows of the index.
+  const TcItem* items;
+  const uint32_t* own_ids;
 };
 
 template <int KT, int MODE>
@@ -171,14 +216,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) subset_tc_kernel(TcParams p) {
   using S = TcShape<KT>;
   constexpr int STAGES = S::kStages;
   extern __shared__ uint8_t smem_raw[];
-  const int64_t n_own = p.n_own_dev ? int64_t(*p.n_own_dev) : p.n_own;
-  const int64_t own0 = int64_t(blockIdx.x) * kTcM;
-  if (own0 >= n_own) return;
-  const int64_t t_lo = int64_t(blockIdx.y) * p.tiles_per_split;
-  const int64_t total_tiles = ceil_div(p.n_stream, kTcN);
-  const int64_t t_hi = (t_lo + p.tiles_per_split < total_tiles) ? t_lo + p.tiles_per_split
-                                                                 : total_tiles;
-  const int ntiles = int(t_hi > t_lo ? t_hi - t_lo : 0);
+  // This CTA's work: own image tile a_tile (own_valid rows), stream image
+  // tiles b_first .. b_first + ntiles - 1 whose rows are str_first ..
+  // str_first + str_count - 1 of the stream (scores, masks).
+  int64_t a_tile, b_first, own0, str_first, str_count;
+  int own_valid, ntiles;
+  if (p.items) {
+    const TcItem it = p.items[blockIdx.x];
+    a_tile = it.a_tile;
+    b_first = it.b_tile;
+    ntiles = it.b_tiles;
+    own0 = it.own_first;
+    own_valid = it.own_count;
+    str_first = it.str_first;
+    str_count = it.str_count;
+  } else {
+    const int64_t n_own = p.n_own_dev ? int64_t(*p.n_own_dev) : p.n_own;
+    own0 = int64_t(blockIdx.x) * kTcM;
+    if (own0 >= n_own) return;
+    const int64_t t_lo = int64_t(blockIdx.y) * p.tiles_per_split;
+    const int64_t total_tiles = ceil_div(p.n_stream, kTcN);
+    const int64_t t_hi = (t_lo + p.tiles_per_split < total_tiles) ? t_lo + p.tiles_per_split
+                                                                   : total_tiles;
+    ntiles = int(t_hi > t_lo ? t_hi - t_lo : 0);
+    a_tile = blockIdx.x;
+    b_first = p.b_tile0 + t_lo;
+    own_valid = int(n_own - own0 < kTcM ? n_own - own0 : kTcM);
+    str_first = t_lo * kTcN;
+    str_count = p.n_stream - str_first;
+  }
 
   // 1024-byte aligned carve-up of dynamic shared memory.
   const uint32_t raw = smem_u32(smem_raw);
@@ -224,7 +290,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) subset_tc_kernel(TcParams p) {
     if (lane == 0) {
       // Producer: A once, then the B tiles through the ring.
       mbar_arrive_expect_tx(a_full, S::kABytes);
-      bulk_g2s(A_s, p.a_img + size_t(blockIdx.x) * S::kABytes, S::kABytes, a_full);
+      bulk_g2s(A_s, p.a_img + size_t(a_tile) * S::kABytes, S::kABytes, a_full);
       int issued = 0;
       for (int t = 0; t < ntiles; ++t) {
         const int s = t % STAGES;
@@ -233,8 +299,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) subset_tc_kernel(TcParams p) {
           break;
         }
         mbar_arrive_expect_tx(full + s, S::kBBytes);
-        bulk_g2s(B_s + size_t(s) * S::kBBytes,
-                 p.b_img + size_t(p.b_tile0 + t_lo + t) * S::kBBytes, S::kBBytes, full + s);
+        bulk_g2s(B_s + size_t(s) * S::kBBytes, p.b_img + size_t(b_first + t) * S::kBBytes,
+                 S::kBBytes, full + s);
         issued = t + 1;
       }
       // Copies must have landed before the CTA may finish.
@@ -276,8 +342,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) subset_tc_kernel(TcParams p) {
   } else {
     // Epilogue: warp w reads accumulator lanes 32*(w % 4) .. +32.
     const int quarter = warp & 3;
-    const int64_t row = own0 + quarter * 32 + lane;
-    const bool valid = row < n_own;
+    const int tile_row = quarter * 32 + lane;
+    const bool valid = tile_row < own_valid;
     bool cov = false;
     uint32_t cnt = 0;
     unsigned long long sum = 0;
@@ -289,8 +355,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) subset_tc_kernel(TcParams p) {
         break;
       }
       tc_fence_after();
-      const int64_t j0 = (t_lo + t) * kTcN;  // first stream row of this tile
-      const int nvalid = int((p.n_stream - j0) < kTcN ? (p.n_stream - j0) : kTcN);
+      const int64_t j0 = str_first + int64_t(t) * kTcN;  // first stream row of this tile
+      const int64_t left = str_count - int64_t(t) * kTcN;
+      const int nvalid = int(left < kTcN ? left : kTcN);
 #pragma unroll 1
       for (int c = 0; c < kTcN; c += 32) {
         uint32_t v[32];
@@ -310,6 +377,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) subset_tc_kernel(TcParams p) {
       if (lane == 0) mbar_arrive(acc_empty + b);
     }
     if (valid) {
+      const int64_t row = p.items ? int64_t(p.own_ids[own0 + tile_row]) : own0 + tile_row;
       if constexpr (MODE == MODE_ANY) {
         if (cov) p.out_u32[row] = 1u;
       }
@@ -357,8 +425,8 @@ static cudaError_t run_tc(const TcArgs& a, cudaStream_t s) {
   if (splits < 1) splits = 1;
   const int64_t per = ceil_div(stream_tiles, splits);
   splits = ceil_div(stream_tiles, per);
-  TcParams p{a.a_img, a.n_own, a.n_own_dev, a.b_img, a.b_tile0, a.n_stream, per,
-             a.score, a.out_u32, a.out_u64, a.status};
+  TcParams p{a.a_img,   a.n_own,   a.n_own_dev, a.b_img,   a.b_tile0, a.n_stream, per,
+             a.score,   a.out_u32, a.out_u64,   a.status,  nullptr,   nullptr};
   cudaError_t e = cudaFuncSetAttribute(subset_tc_kernel<KT, MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::kSmem));
   if (e != cudaSuccess) return e;
@@ -384,6 +452,177 @@ cudaError_t launch_expand(const uint64_t* rows, int64_t n, int stride, int KT, b
     case 8: return expand<8>(rows, n, stride, complement ? 1 : 0, R, img, s);
   }
   return cudaErrorInvalidValue;
+}
+
+// ---- item-index blocks on the tensor cores ----------------------------------
+
+template <int KT, int MODE>
+static cudaError_t run_tc_items(const TcParams& p, int64_t n_items, cudaStream_t s) {
+  using S = TcShape<KT>;
+  cudaError_t e = cudaFuncSetAttribute(subset_tc_kernel<KT, MODE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::kSmem));
+  if (e != cudaSuccess) return e;
+  subset_tc_kernel<KT, MODE><<<unsigned(n_items), kTcThreads, S::kSmem, s>>>(p);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <int KT>
+static cudaError_t expand_tiles(const uint64_t* rows, bool complement, const TcTile* tiles,
+                                int64_t ntiles, uint8_t* img, cudaStream_t s) {
+  const int64_t chunks = ntiles * int64_t(kTcM) * KT * 4;
+  if (chunks == 0) return cudaSuccess;
+  expand_tiles_kernel<KT><<<unsigned(ceil_div(chunks, 256)), 256, 0, s>>>(
+      rows, KT, complement ? 1 : 0, kTcM, tiles, ntiles, img);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+namespace {
+// Pinned staging for the tile tables and work items, one per host thread;
+// reused once the copy out of it (recorded by `done`) has finished.
+struct TcStaging {
+  uint8_t* buf = nullptr;
+  size_t cap = 0;
+  cudaEvent_t done = nullptr;
+};
+thread_local TcStaging g_tc_staging;
+}  // namespace
+
+cudaError_t indexed_subset_tc(int mode, const RecordIndex& idx, const KeyedIndex& kx,
+                              uint32_t* out_u32, unsigned long long* out_u64, int* status,
+                              int64_t* tests_out, int prof_stage, cudaStream_t s) {
+  static_assert(kTcM == kTcN, "own and stream tiles share one tile table layout");
+  *tests_out = 0;
+  const int L = idx.L, KT = idx.KT;
+  if (kx.n == 0 || idx.n_rows == 0 || !tc_supported(KT)) return cudaErrorInvalidValue;
+  // The result side is resident: patterns (keyed) for ANY / COUNT, records
+  // (multi, complemented) for SUM.
+  const bool own_multi = mode == MODE_SUM;
+  const uint32_t* own_off = own_multi ? idx.h_off.data() : kx.h_off.data();
+  const uint32_t* str_off = own_multi ? kx.h_off.data() : idx.h_off.data();
+  std::vector<TcTile> tiles;  // own tiles, then stream tiles
+  std::vector<TcItem> items;
+  std::vector<int64_t> a0(L, -1), b0(L, -1);
+  int64_t tests = 0, pair_tiles = 0;
+  for (int l = 0; l < L; ++l) {
+    const int64_t no = int64_t(own_off[l + 1]) - own_off[l];
+    const int64_t ns = int64_t(str_off[l + 1]) - str_off[l];
+    if (no == 0 || ns == 0) continue;
+    tests += no * ns;
+    pair_tiles += ceil_div(no, kTcM) * ceil_div(ns, kTcN);
+    a0[l] = int64_t(tiles.size());
+    for (int64_t r = 0; r < no; r += kTcM)
+      tiles.push_back(TcTile{int64_t(own_off[l]) + r, int32_t(std::min<int64_t>(kTcM, no - r)), 0});
+  }
+  const int64_t n_a = int64_t(tiles.size());
+  for (int l = 0; l < L; ++l) {
+    if (a0[l] < 0) continue;
+    const int64_t ns = int64_t(str_off[l + 1]) - str_off[l];
+    b0[l] = int64_t(tiles.size()) - n_a;
+    for (int64_t r = 0; r < ns; r += kTcN)
+      tiles.push_back(TcTile{int64_t(str_off[l]) + r, int32_t(std::min<int64_t>(kTcN, ns - r)), 0});
+  }
+  const int64_t n_b = int64_t(tiles.size()) - n_a;
+  *tests_out = tests;
+  if (n_a == 0) return cudaSuccess;
+  // About four blocks per SM: stream ranges of `per` tiles.
+  const int64_t per = std::max<int64_t>(1, pair_tiles / (int64_t(num_sms()) * 4));
+  for (int l = 0; l < L; ++l) {
+    if (a0[l] < 0) continue;
+    const int64_t no = int64_t(own_off[l + 1]) - own_off[l];
+    const int64_t ns = int64_t(str_off[l + 1]) - str_off[l];
+    const int64_t nb = ceil_div(ns, kTcN);
+    for (int64_t a = 0; a * kTcM < no; ++a)
+      for (int64_t b = 0; b < nb; b += per) {
+        TcItem it;
+        it.a_tile = a0[l] + a;
+        it.b_tile = b0[l] + b;
+        it.own_first = int64_t(own_off[l]) + a * kTcM;
+        it.str_first = int64_t(str_off[l]) + b * kTcN;
+        it.own_count = int32_t(std::min<int64_t>(kTcM, no - a * kTcM));
+        it.b_tiles = int32_t(std::min<int64_t>(per, nb - b));
+        it.str_count = int32_t(std::min<int64_t>(per * kTcN, ns - b * kTcN));
+        it.pad = 0;
+        items.push_back(it);
+      }
+  }
+  // One device buffer: tile table, items, then the two images.
+  const size_t row_bytes = size_t(KT) * 64;
+  const size_t tiles_bytes = ((tiles.size() * sizeof(TcTile) + 255) / 256) * 256;
+  const size_t items_bytes = ((items.size() * sizeof(TcItem) + 255) / 256) * 256;
+  const size_t a_bytes = size_t(n_a) * kTcM * row_bytes, b_bytes = size_t(n_b) * kTcN * row_bytes;
+  const size_t table_bytes = tiles_bytes + items_bytes;
+  TcStaging& st = g_tc_staging;
+  cudaError_t e;
+  if (st.done && (e = cudaEventSynchronize(st.done)) != cudaSuccess) return e;
+  if (st.cap < table_bytes) {
+    if (st.buf) cudaFreeHost(st.buf);
+    st.buf = nullptr;
+    st.cap = 0;
+    if ((e = cudaMallocHost(reinterpret_cast<void**>(&st.buf), table_bytes * 2)) != cudaSuccess)
+      return e;
+    st.cap = table_bytes * 2;
+  }
+  if (!st.done && (e = cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming)) != cudaSuccess)
+    return e;
+  std::memcpy(st.buf, tiles.data(), tiles.size() * sizeof(TcTile));
+  std::memcpy(st.buf + tiles_bytes, items.data(), items.size() * sizeof(TcItem));
+  void* mem = nullptr;
+  e = cudaMallocAsync(&mem, table_bytes + a_bytes + b_bytes, s);
+  if (e != cudaSuccess) return e;
+  uint8_t* m = static_cast<uint8_t*>(mem);
+  const TcTile* d_tiles = reinterpret_cast<const TcTile*>(m);
+  const TcItem* d_items = reinterpret_cast<const TcItem*>(m + tiles_bytes);
+  uint8_t* a_img = m + table_bytes;
+  uint8_t* b_img = a_img + a_bytes;
+  e = cudaMemcpyAsync(m, st.buf, table_bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaEventRecord(st.done, s);
+  const uint64_t* own_rows = own_multi ? idx.rows : kx.rows;
+  const uint64_t* str_rows = own_multi ? kx.rows : idx.rows;
+  // The images are timed with the index build, the GEMM under the caller's
+  // stage.
+  void* tok = e == cudaSuccess ? prof_begin(kStageIndexBuild, s) : nullptr;
+  if (e == cudaSuccess) {
+    switch (KT) {
+      case 2:
+        e = expand_tiles<2>(own_rows, own_multi, d_tiles, n_a, a_img, s);
+        if (e == cudaSuccess) e = expand_tiles<2>(str_rows, !own_multi, d_tiles + n_a, n_b, b_img, s);
+        break;
+      case 4:
+        e = expand_tiles<4>(own_rows, own_multi, d_tiles, n_a, a_img, s);
+        if (e == cudaSuccess) e = expand_tiles<4>(str_rows, !own_multi, d_tiles + n_a, n_b, b_img, s);
+        break;
+      case 8:
+        e = expand_tiles<8>(own_rows, own_multi, d_tiles, n_a, a_img, s);
+        if (e == cudaSuccess) e = expand_tiles<8>(str_rows, !own_multi, d_tiles + n_a, n_b, b_img, s);
+        break;
+    }
+  }
+  prof_end(tok);
+  tok = nullptr;
+  if (e == cudaSuccess) {
+    tok = prof_stage >= 0 ? prof_begin(prof_stage, s) : nullptr;
+    TcParams p{a_img,   int64_t(n_a) * kTcM, nullptr, b_img,  0,      int64_t(n_b) * kTcN, 0,
+               own_multi ? kx.score : nullptr, out_u32, out_u64, status, d_items,
+               own_multi ? idx.ids : kx.ids};
+    const int64_t n_items = int64_t(items.size());
+#define IG_TCI_CASE(KTV)                                                              \
+  case KTV:                                                                           \
+    e = mode == MODE_ANY     ? run_tc_items<KTV, MODE_ANY>(p, n_items, s)             \
+        : mode == MODE_COUNT ? run_tc_items<KTV, MODE_COUNT>(p, n_items, s)           \
+                             : run_tc_items<KTV, MODE_SUM>(p, n_items, s);            \
+    break;
+    switch (KT) {
+      IG_TCI_CASE(2)
+      IG_TCI_CASE(4)
+      IG_TCI_CASE(8)
+    }
+#undef IG_TCI_CASE
+  }
+  prof_end(tok);
+  cudaFreeAsync(mem, s);
+  return e;
 }
 
 cudaError_t launch_subset_tc(const TcArgs& a, cudaStream_t s) {

@@ -48,7 +48,7 @@ def host(t, dtype):
 
 # 1 = integer-pipe (LOP3) kernel, 2 = tensor-core (tcgen05) kernel,
 # 3 = item-index pruning (exact)
-KERNELS = [1, 2, 3]
+KERNELS = [1, 2, 3, 4]
 
 
 def gpu_fit(rows, labels, r=None, kernel=0):
@@ -264,7 +264,7 @@ def _workload_fit(w, r=None, kernel=0):
     d_codes = dev(w.train_codes)
     rows = ig.ig_encode(d_codes, w.cards)
     m = ig.ig_fit(rows, dev(w.train_labels), r=r, subset_kernel=kernel)
-    assert m.info()["subset_kernel"] == {0: 3, 1: 1, 2: 2, 3: 3}[kernel]
+    assert m.info()["subset_kernel"] == {0: 3, 1: 1, 2: 2, 3: 3, 4: 4}[kernel]
     return m, oracle.encode(w.train_codes, w.cards)
 
 
@@ -294,7 +294,7 @@ def nsl15k_oracle():
     return w, oracle.fit(rows, w.train_labels)
 
 
-@pytest.fixture(scope="module", params=KERNELS, ids=["lop3", "tcgen05", "index"])
+@pytest.fixture(scope="module", params=KERNELS, ids=["lop3", "tcgen05", "index", "index-tc"])
 def nsl15k(request, nsl15k_oracle):
     w, om = nsl15k_oracle
     m, _ = _workload_fit(w, kernel=request.param)
