@@ -267,6 +267,14 @@ int ig_prof_reset(void);
 int ig_prof_read(double* ms, int64_t* launches);
 const char* ig_prof_stage_name(int32_t stage);
 
+/* Timeline of the stages recorded since the last reset (which also records
+ * the reference point): for each of the first min(cap, *n_out) stage spans,
+ * its stage id, the stream it ran on (an opaque id), and its begin and end
+ * in milliseconds after the reset.  Synchronizes the recorded events.  Any
+ * output array may be NULL; *n_out receives the number of spans. */
+int ig_prof_timeline(int32_t* stage, uint64_t* stream, double* t0_ms, double* t1_ms,
+                     int64_t cap, int64_t* n_out);
+
 /* Subset tests executed per stage since the last reset, counted while
  * timing is enabled (support and evidence stages; coherence tests are
  * reported per model by ig_model_info). */

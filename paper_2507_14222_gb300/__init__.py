@@ -85,6 +85,7 @@ SIGNATURES = {
     "ig_prof_stage_name": (ctypes.c_char_p, [_I32]),
     "ig_launch_count": (ctypes.c_int64, []),
     "ig_prof_read_work": (ctypes.c_int, [_P]),
+    "ig_prof_timeline": (ctypes.c_int, [_P, _P, _P, _P, _I64, _P]),
     "ig_score_noalloc": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P]),
     "ig_fit_batched": (ctypes.c_int, [_P, _I32, _P, _I32, _P, _P]),
     "ig_model_from_patterns": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P]),
@@ -468,6 +469,22 @@ def prof_read() -> dict:
     _check(lib.ig_prof_read_work(w))
     return {lib.ig_prof_stage_name(i).decode(): (ms[i], n[i], w[i])
             for i in range(PROF_STAGES)}
+
+
+def prof_timeline() -> list:
+    """Stage spans since the last prof_reset(): [(stage name, stream id,
+    begin ms, end ms)], in the order they were recorded."""
+    lib = load()
+    n = ctypes.c_int64()
+    _check(lib.ig_prof_timeline(None, None, None, None, 0, ctypes.byref(n)))
+    k = n.value
+    st = np.zeros(max(k, 1), np.int32)
+    sid = np.zeros(max(k, 1), np.uint64)
+    t0 = np.zeros(max(k, 1), np.float64)
+    t1 = np.zeros(max(k, 1), np.float64)
+    _check(lib.ig_prof_timeline(_ptr(st), _ptr(sid), _ptr(t0), _ptr(t1), k, ctypes.byref(n)))
+    return [(lib.ig_prof_stage_name(int(st[i])).decode(), int(sid[i]), float(t0[i]), float(t1[i]))
+            for i in range(k)]
 
 
 def launch_count() -> int:

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -79,10 +80,20 @@ struct Prof {
   int64_t work[IG_PROF_STAGES] = {};
   struct Pending {
     int stage;
+    cudaStream_t s;
     cudaEvent_t a, b;
   };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
+  // Timeline since the last reset: begin and end of every recorded stage,
+  // in ms after the reference event recorded by the reset.
+  cudaEvent_t ref = nullptr;
+  struct Span {
+    int stage;
+    cudaStream_t s;
+    double t0, t1;
+  };
+  std::vector<Span> spans;
 };
 Prof g_prof;
 
@@ -117,7 +128,11 @@ void prof_drain_locked() {
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
       g_prof.ms[p.stage] += ms;
       g_prof.launches[p.stage] += 1;
+      float t0 = 0.f;
+      if (g_prof.ref && cudaEventElapsedTime(&t0, g_prof.ref, p.a) == cudaSuccess)
+        g_prof.spans.push_back({p.stage, p.s, double(t0), double(t0) + double(ms)});
     }
+    cudaGetLastError();
     g_prof.pool.push_back(p.a);
     g_prof.pool.push_back(p.b);
   }
@@ -359,7 +374,7 @@ void igk::prof_end(void* token) {
   std::lock_guard<std::mutex> lk(g_prof.mu);
   cudaEvent_t b = prof_event();
   cudaEventRecord(b, t->s);
-  g_prof.pending.push_back({t->stage, t->a, b});
+  g_prof.pending.push_back({t->stage, t->s, t->a, b});
   delete t;
 }
 
@@ -377,6 +392,30 @@ int igk::num_sms() {
   }
   return cached[dev];
 }
+
+namespace {
+// A second stream for work that can overlap the caller's, with the two
+// events that join it: one per host thread and device, created on first use
+// and kept for the life of the process.
+struct AuxStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t ready = nullptr, done = nullptr;
+  cudaError_t error = cudaSuccess;
+};
+AuxStream& aux_stream() {
+  static thread_local AuxStream per_dev[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  AuxStream& a = per_dev[dev];
+  if (!a.s && a.error == cudaSuccess) {
+    a.error = cudaStreamCreateWithFlags(&a.s, cudaStreamNonBlocking);
+    if (a.error == cudaSuccess)
+      a.error = cudaEventCreateWithFlags(&a.ready, cudaEventDisableTiming);
+    if (a.error == cudaSuccess) a.error = cudaEventCreateWithFlags(&a.done, cudaEventDisableTiming);
+  }
+  return a;
+}
+}  // namespace
 
 struct ig_model {
   int K = 0, KT = 0;
@@ -474,6 +513,49 @@ struct TableCounters {
 // table.  At the load factors used (at most one half) linear probing
 // almost never comes near it.
 constexpr uint64_t kMaxProbe = 512;
+
+// Hand-over between the two class threads of a fit: each prepares its own
+// side (record index, image), records an event on its stream and marks
+// itself ready; a thread that needs the other side waits for that mark
+// (bounded) and orders its stream after the event.  A thread that fails
+// before it is ready marks itself failed, so the other never waits in vain.
+struct SideSync {
+  std::mutex mu;
+  std::condition_variable cv;
+  int state[2] = {0, 0};  // 0 pending, 1 ready, -1 failed
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  ~SideSync() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+  void mark(int c, int st) {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      if (state[c] == 0) state[c] = st;
+    }
+    cv.notify_all();
+  }
+  int wait(int c, cudaStream_t s) {
+    std::unique_lock<std::mutex> lk(mu);
+    if (!cv.wait_for(lk, std::chrono::seconds(600), [&] { return state[c] != 0; }))
+      return fail(IG_E_TIMEOUT, "ig_fit: the other class's record index never came");
+    if (state[c] < 0) return fail(IG_E_INTERNAL, "ig_fit: the other class failed");
+    IG_CUDA(cudaStreamWaitEvent(s, ev[c], 0), "ig_fit");
+    return IG_OK;
+  }
+};
+
+struct SideSignal {
+  SideSync* sync;
+  int c;
+  cudaError_t ready(cudaStream_t s) {
+    cudaError_t e = cudaEventCreateWithFlags(&sync->ev[c], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(sync->ev[c], s);
+    sync->mark(c, e == cudaSuccess ? 1 : -1);
+    return e;
+  }
+  ~SideSignal() { sync->mark(c, -1); }  // no effect once ready
+};
 
 int build_candidates(const uint64_t* X, int64_t n, int KT, cudaStream_t s, int* d_status,
                      TableCounters* h_counters, DevBuf<uint64_t>& cand, int64_t* U_out) {
@@ -681,35 +763,36 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
   m->index_max_q = prm.index_max_q ? prm.index_max_q : 4;
   m->index_flip = prm.index_flip_factor ? prm.index_flip_factor : 2;
   // Item indexes of both classes' records: used by the other class's
-  // coherence, this class's support and (normal class) Regulation 3.
+  // coherence, this class's support and (normal class) Regulation 3.  And
+  // complemented images of the records for the tensor cores: the stream
+  // operand of the other class's coherence and of this class's support, and
+  // the own operand of the Regulation 3 evidence; with the item index they
+  // are only needed where an index could not be used.  Each class thread
+  // prepares its own side first, then tells the other (side_ready).
   IndexHolder rec_idx[2];
-  if (pruned) {
-    for (int c = 0; c < 2; ++c) {
-      rec_idx[c].s = s;
-      IG_CUDA(igk::build_record_index(X[c].p, nc[c], KT, K, KT, 0.25, &rec_idx[c].idx, s),
-              "ig_fit: record index");
-    }
-  }
-  // Complemented images of both classes' records for the tensor cores: the
-  // stream operand of the other class's coherence and of this class's
-  // support, and the own operand of the Regulation 3 evidence.  With the
-  // item index they are only needed where an index could not be used.
   DevBuf<uint8_t> rec_img[2];
-  if (tc) {
-    for (int c = 0; c < 2; ++c) {
-      if (pruned && rec_idx[c].idx.usable) continue;
-      IG_CUDA(rec_img[c].alloc(igk::tc_image_bytes(nc[c], KT, false), s), "ig_fit: images");
-      ProfScope ps(S_EXPAND, s);
-      IG_CUDA(igk::launch_expand(X[c].p, nc[c], KT, KT, true, false, rec_img[c].p, s),
-              "ig_fit: expand");
-    }
-  }
+  SideSync side_sync;
 
   // The two classes are fitted concurrently, each on its own stream (class
   // + on a worker thread, class - on the calling thread), so that the
   // kernels of one class run while the other waits for a size read-back.
   auto fit_class = [&](int c, cudaStream_t s) -> int {
     const int o = 1 - c;
+    SideSignal signal{&side_sync, c};
+    // This class's record index and image, for both classes' later steps.
+    if (pruned) {
+      rec_idx[c].s = s;
+      IG_CUDA(igk::build_record_index(X[c].p, nc[c], KT, K, KT, 0.25, &rec_idx[c].idx, s),
+              "ig_fit: record index");
+    }
+    if (tc && !(pruned && rec_idx[c].idx.usable)) {
+      IG_CUDA(rec_img[c].alloc(igk::tc_image_bytes(nc[c], KT, false), s), "ig_fit: images");
+      ProfScope ps(S_EXPAND, s);
+      IG_CUDA(igk::launch_expand(X[c].p, nc[c], KT, KT, true, false, rec_img[c].p, s),
+              "ig_fit: expand");
+    }
+    IG_CUDA(signal.ready(s), "ig_fit");
+    bool other_ready = false;
     unsigned long long* h_pinned = thread_pinned();
     if (!h_pinned) return fail(IG_E_CUDA, "ig_fit: pinned host allocation failed");
     TableCounters* h_counters = reinterpret_cast<TableCounters*>(h_pinned + 4);
@@ -752,6 +835,11 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
       const bool pruned_round = pruned && lo == pruned_from;
       const bool tc_round = !pruned && tc && lo >= tc_from;
       if (pruned_round || tc_round) hi = nc[o];
+      if ((pruned_round || tc_round) && !other_ready) {
+        // The other class's record index / image, prepared by its thread.
+        IG_CHECK(side_sync.wait(o, s));
+        other_ready = true;
+      }
       unsigned long long* kept = d_kept.p + rounds;
       round_tests[rounds] = -1;
       IG_CUDA(cudaMemsetAsync(covered.p, 0, sizeof(uint32_t) * U, s), "ig_fit");
@@ -937,6 +1025,31 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
                                   cudaMemcpyDeviceToDevice, s),
                 "ig_fit");
     }
+    // Scoring's pattern index of this class, keyed by the item counts of
+    // both classes' training records (from the two record indexes).
+    if (pruned && P) {
+      if (!other_ready) {
+        IG_CHECK(side_sync.wait(o, s));
+        other_ready = true;
+      }
+      if (rec_idx[0].idx.usable && rec_idx[1].idx.usable) {
+        const int L = 64 * K;
+        std::vector<uint32_t> f(L);
+        for (int l = 0; l < L; ++l)
+          f[l] = (rec_idx[0].idx.h_off[l + 1] - rec_idx[0].idx.h_off[l]) +
+                 (rec_idx[1].idx.h_off[l + 1] - rec_idx[1].idx.h_off[l]);
+        DevBuf<uint32_t> d_f;
+        IG_CUDA(d_f.alloc(L, s), "ig_fit");
+        IG_CUDA(cudaMemcpyAsync(d_f.p, f.data(), sizeof(uint32_t) * L, cudaMemcpyHostToDevice, s),
+                "ig_fit");
+        igk::KeyedIndex* k = new igk::KeyedIndex;
+        const cudaError_t e = igk::build_keyed_index(m->words_kt[c], P, KT, K, KT, d_f.p,
+                                                     m->score[c], k, s);
+        if (e != cudaSuccess) delete k;
+        IG_CUDA(e, "ig_fit: pattern index");
+        m->pidx[c] = k;
+      }
+    }
     return IG_OK;
   };
   {
@@ -968,13 +1081,21 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
       cudaEventRecord(ev[i], cs[i]);
       cudaStreamWaitEvent(s, ev[i], 0);
       cudaStreamDestroy(cs[i]);
+      // What the class streams allocated for later steps is freed on s.
+      rec_idx[i].s = s;
+      rec_img[i].s = s;
     }
     for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
+    // Report a class's own failure before one that only saw the other fail.
+    int first = -1;
     for (int i = 1; i >= 0; --i)
-      if (rc[i] != IG_OK) {
-        g_last_error = msg[i];
-        return rc[i];
-      }
+      if (rc[i] != IG_OK && (first < 0 || msg[first].find("the other class failed") !=
+                                              std::string::npos))
+        first = i;
+    if (first >= 0) {
+      g_last_error = msg[first];
+      return rc[first];
+    }
   }
 
   // Regulation 3: mean and population std of N over the training normals,
@@ -1033,19 +1154,6 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
     m->r = prm.r;
     const double scaled = prm.r * m->sigma;
     m->thr = m->mu - scaled;
-  }
-  // Scoring's pattern index, keyed by the training records' item counts.
-  if (pruned && rec_idx[0].idx.usable && rec_idx[1].idx.usable) {
-    const int L = 64 * K;
-    std::vector<uint32_t> f(L);
-    for (int l = 0; l < L; ++l)
-      f[l] = (rec_idx[0].idx.h_off[l + 1] - rec_idx[0].idx.h_off[l]) +
-             (rec_idx[1].idx.h_off[l + 1] - rec_idx[1].idx.h_off[l]);
-    DevBuf<uint32_t> d_f;
-    IG_CUDA(d_f.alloc(L, s), "ig_fit");
-    IG_CUDA(cudaMemcpyAsync(d_f.p, f.data(), sizeof(uint32_t) * L, cudaMemcpyHostToDevice, s),
-            "ig_fit");
-    IG_CUDA(build_pattern_indexes(m, d_f.p, s), "ig_fit: pattern index");
   }
   IG_CHECK(read_status(d_status.p, s, "ig_fit"));
   guard.m = nullptr;
@@ -1300,11 +1408,18 @@ int ig_score(const ig_model* m, const uint64_t* rows, int64_t n_rows, int64_t* A
     IG_CUDA(igk::build_record_index(in.d, n_rows, m->K, m->K, m->KT, 0.25, &test_idx.idx, s),
             "ig_score: record index");
   if (pruned && test_idx.idx.usable) {
+    // A (class 1) on the caller's stream and N (class 0) on this thread's
+    // auxiliary stream, concurrently: both only read the indexes.
+    AuxStream& aux = aux_stream();
+    IG_CUDA(aux.error, "ig_score: auxiliary stream");
+    IG_CUDA(cudaEventRecord(aux.ready, s), "ig_score");
+    IG_CUDA(cudaStreamWaitEvent(aux.s, aux.ready, 0), "ig_score");
     for (int c = 1; c >= 0; --c) {
       if (m->n_pat[c] == 0) {
         done[c] = true;
         continue;
       }
+      const cudaStream_t sc = c == 1 ? s : aux.s;
       int64_t t = 0;
       // Small batches reuse the model's pattern index; larger ones re-key
       // the patterns by the batch's own item counts (fewer tests, and
@@ -1313,7 +1428,7 @@ int ig_score(const ig_model* m, const uint64_t* rows, int64_t n_rows, int64_t* A
         IG_CUDA(igk::indexed_subset_prebuilt(igk::MODE_SUM, test_idx.idx, *m->pidx[c], nullptr,
                                              c == 1 ? A.d : N.d, d_status.p, &t, S_EVIDENCE_IDX,
                                              m->index_max_q, m->index_flip,
-                                             m->subset_kernel == 4 ? 1 : 0, s),
+                                             m->subset_kernel == 4 ? 1 : 0, sc),
                 "ig_score: evidence");
         done[c] = true;
         igk::prof_add_work(S_EVIDENCE_IDX, t);
@@ -1334,10 +1449,12 @@ int ig_score(const ig_model* m, const uint64_t* rows, int64_t n_rows, int64_t* A
       a.max_q = m->index_max_q;
       a.flip_factor = m->index_flip;
       a.tc = m->subset_kernel == 4 ? 1 : 0;
-      IG_CUDA(igk::indexed_subset(a, s), "ig_score: evidence");
+      IG_CUDA(igk::indexed_subset(a, sc), "ig_score: evidence");
       done[c] = true;
       igk::prof_add_work(S_EVIDENCE_IDX, t);
     }
+    IG_CUDA(cudaEventRecord(aux.done, aux.s), "ig_score");
+    IG_CUDA(cudaStreamWaitEvent(s, aux.done, 0), "ig_score");
   }
   if (done[0] && done[1]) tc = false;
   if (tc) {
@@ -1511,6 +1628,28 @@ int ig_prof_reset(void) {
     g_prof.ms[i] = 0;
     g_prof.launches[i] = 0;
     g_prof.work[i] = 0;
+  }
+  g_prof.spans.clear();
+  if (!g_prof.ref && cudaEventCreate(&g_prof.ref) != cudaSuccess) {
+    g_prof.ref = nullptr;
+    cudaGetLastError();
+  }
+  if (g_prof.ref && cudaEventRecord(g_prof.ref, nullptr) != cudaSuccess) cudaGetLastError();
+  return IG_OK;
+}
+
+int ig_prof_timeline(int32_t* stage, uint64_t* stream, double* t0_ms, double* t1_ms,
+                     int64_t cap, int64_t* n_out) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  prof_drain_locked();
+  const int64_t n = int64_t(g_prof.spans.size());
+  if (n_out) *n_out = n;
+  for (int64_t i = 0; i < n && i < cap; ++i) {
+    const auto& sp = g_prof.spans[size_t(i)];
+    if (stage) stage[i] = sp.stage;
+    if (stream) stream[i] = uint64_t(reinterpret_cast<uintptr_t>(sp.s));
+    if (t0_ms) t0_ms[i] = sp.t0;
+    if (t1_ms) t1_ms[i] = sp.t1;
   }
   return IG_OK;
 }

@@ -56,10 +56,10 @@ struct TcShape {
 // img tile t holds rows [t*R, t*R + R): byte offset of item k of tile row r is
 //   (k / 128) * (R * 128) + r * 128 + (((k % 128) / 16) ^ (r % 8)) * 16 + k % 16.
 // One thread writes one 16-byte chunk.  Rows >= n are zero.
-template <int KT>
+template <int KT, int R>
 __global__ void expand_kernel(const uint64_t* __restrict__ rows, int64_t n, int stride,
-                              int complement, int R, int64_t ntiles, uint8_t* __restrict__ img) {
-  const int64_t chunks_per_tile = int64_t(R) * KT * 4;
+                              int complement, int64_t ntiles, uint8_t* __restrict__ img) {
+  constexpr int64_t chunks_per_tile = int64_t(R) * KT * 4;
   const int64_t id = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (id >= ntiles * chunks_per_tile) return;
   const int64_t tile = id / chunks_per_tile;
@@ -94,9 +94,10 @@ __global__ void expand_kernel(const uint64_t* __restrict__ rows, int64_t n, int 
 // then zero rows.  Used for the item index, whose groups each start a tile.
 template <int KT>
 __global__ void expand_tiles_kernel(const uint64_t* __restrict__ rows, int stride,
-                                    int complement, int R, const TcTile* __restrict__ tiles,
+                                    int complement, const TcTile* __restrict__ tiles,
                                     int64_t ntiles, uint8_t* __restrict__ img) {
-  const int64_t chunks_per_tile = int64_t(R) * KT * 4;
+  constexpr int R = kTcM;  // a power of two: the index arithmetic is shifts
+  constexpr int64_t chunks_per_tile = int64_t(R) * KT * 4;
   const int64_t id = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (id >= ntiles * chunks_per_tile) return;
   const int64_t tile = id / chunks_per_tile;
@@ -404,11 +405,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) subset_tc_kernel(TcParams p) {
 template <int KT>
 static cudaError_t expand(const uint64_t* rows, int64_t n, int stride, int complement, int R,
                           uint8_t* img, cudaStream_t s) {
-  const int64_t ntiles = ceil_div(n, R);
-  const int64_t chunks = ntiles * int64_t(R) * KT * 4;
+  static_assert(kTcM == kTcN, "one tile height for both operands");
+  if (R != kTcM) return cudaErrorInvalidValue;
+  const int64_t ntiles = ceil_div(n, kTcM);
+  const int64_t chunks = ntiles * int64_t(kTcM) * KT * 4;
   if (chunks == 0) return cudaSuccess;
-  expand_kernel<KT><<<unsigned(ceil_div(chunks, 256)), 256, 0, s>>>(rows, n, stride, complement,
-                                                                    R, ntiles, img);
+  expand_kernel<KT, kTcM><<<unsigned(ceil_div(chunks, 256)), 256, 0, s>>>(
+      rows, n, stride, complement, ntiles, img);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -473,7 +476,7 @@ static cudaError_t expand_tiles(const uint64_t* rows, bool complement, const TcT
   const int64_t chunks = ntiles * int64_t(kTcM) * KT * 4;
   if (chunks == 0) return cudaSuccess;
   expand_tiles_kernel<KT><<<unsigned(ceil_div(chunks, 256)), 256, 0, s>>>(
-      rows, KT, complement ? 1 : 0, kTcM, tiles, ntiles, img);
+      rows, KT, complement ? 1 : 0, tiles, ntiles, img);
   count_launches(1);
   return cudaGetLastError();
 }
