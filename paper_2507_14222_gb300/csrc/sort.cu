@@ -82,7 +82,19 @@ struct SortArrays {
   uint32_t* idx;
 };
 
-// Bitonic network over a tile of kSortTile elements in shared memory.
+// Bitonic network over a tile of kSortTile elements in shared memory.  The
+// tile holds keys [base, base + kSortTile) (this is the first pass, so the
+// element of key i carries index i); with KT <= 8 words those keys are
+// staged in shared memory too, so that elements whose prefixes tie are
+// compared there rather than by loads from global memory that every thread
+// of the block would wait for at the next barrier.
+template <int KT>
+constexpr bool kSortStageKeys = KT <= 8;
+template <int KT>
+constexpr size_t sort_stage_bytes() {
+  return kSortStageKeys<KT> ? size_t(kSortTile) * KT * 8 : 0;
+}
+
 template <int KT>
 __global__ void __launch_bounds__(kSortBlockThreads)
     block_sort_kernel(const uint64_t* __restrict__ keys, int64_t n, SortArrays in,
@@ -90,8 +102,12 @@ __global__ void __launch_bounds__(kSortBlockThreads)
   __shared__ uint64_t s0[kSortTile];
   __shared__ uint64_t s1[kSortTile];
   __shared__ uint32_t si[kSortTile];
+  extern __shared__ uint64_t tile_keys[];  // [kSortTile][KT] when staged
   const int64_t base = int64_t(blockIdx.x) * kSortTile;
   const int nv = int((n - base) < kSortTile ? (n - base) : kSortTile);
+  if constexpr (kSortStageKeys<KT>) {
+    for (int e = threadIdx.x; e < nv * KT; e += blockDim.x) tile_keys[e] = keys[base * KT + e];
+  }
   for (int r = threadIdx.x; r < kSortTile; r += blockDim.x) {
     if (r < nv) {
       s0[r] = in.p0[base + r];
@@ -107,7 +123,14 @@ __global__ void __launch_bounds__(kSortBlockThreads)
   auto greater = [&](int x, int y) -> bool {
     if (si[x] == 0xffffffffu) return si[y] != 0xffffffffu;
     if (si[y] == 0xffffffffu) return false;
-    return elem_less<KT>(keys, s0[y], s1[y], si[y], s0[x], s1[x], si[x]);
+    if constexpr (kSortStageKeys<KT>) {
+      if (s0[y] != s0[x]) return s0[y] < s0[x];
+      if (s1[y] != s1[x]) return s1[y] < s1[x];
+      return key_less<KT>(tile_keys + int64_t(si[y] - base) * KT,
+                          tile_keys + int64_t(si[x] - base) * KT);
+    } else {
+      return elem_less<KT>(keys, s0[y], s1[y], si[y], s0[x], s1[x], si[x]);
+    }
   };
   for (int k = 2; k <= kSortTile; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
@@ -197,8 +220,17 @@ static cudaError_t sort_t(const uint64_t* keys, int64_t n, uint64_t* keys_out, c
   const unsigned g = unsigned(ceil_div(n, 256));
   prefix_kernel<KT><<<g, 256, 0, s>>>(keys, n, A.p0, A.p1, A.idx);
   count_launches(1);
-  block_sort_kernel<KT><<<unsigned(ceil_div(n, kSortTile)), kSortBlockThreads, 0, s>>>(keys, n, A,
-                                                                                       B);
+  constexpr size_t stage = sort_stage_bytes<KT>();
+  if (stage > 0) {
+    e = cudaFuncSetAttribute(block_sort_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(stage));
+    if (e != cudaSuccess) {
+      cudaFreeAsync(mem, s);
+      return e;
+    }
+  }
+  block_sort_kernel<KT><<<unsigned(ceil_div(n, kSortTile)), kSortBlockThreads, stage, s>>>(
+      keys, n, A, B);
   count_launches(1);
   SortArrays cur = B, other = A;
   for (int64_t run = kSortTile; run < n; run *= 2) {
