@@ -103,36 +103,34 @@ __device__ __forceinline__ void stage_rows(const uint64_t* __restrict__ rows, in
   }
 }
 
-// Copies row i into the group of every item it contains.  A block first
-// counts its copies per item in shared memory, reserves one range per item
-// in the group with a single global atomic, and places its copies with
-// shared-memory atomics only (the order inside a group does not matter).
-// The copies are written a round at a time per warp -- round t places the
-// t-th item of each of the warp's records -- as whole rows (warp_write_rows).
-// Shared memory: blockDim.x * KT words of rows, then 2 * L counters.
+// Copies row i into the group of every item it contains, one warp per row:
+// the lanes test the row's item positions 32 at a time, each set position
+// takes a slot in its group, and the warp writes the row to those slots as
+// whole rows (32 / KT rows per store).  A block first counts its copies per
+// item in shared memory and reserves one range per item in the group with a
+// single global atomic, so the slots come from shared-memory atomics (the
+// order inside a group does not matter).  Shared memory: one staged row per
+// warp, then 2 * L counters.
 __global__ void multi_scatter_kernel(const uint64_t* __restrict__ rows, int64_t n, int stride,
                                      int K, int KT, int L, const uint32_t* __restrict__ off,
                                      uint32_t* __restrict__ cursor, uint64_t* __restrict__ out,
                                      uint32_t* __restrict__ ids) {
   extern __shared__ uint64_t shm[];
-  uint64_t* rec = shm;
-  uint32_t* cnt = reinterpret_cast<uint32_t*>(rec + blockDim.x * KT);  // [L]
-  uint32_t* base = cnt + L;                                            // [L]
-  const int64_t i0 = int64_t(blockIdx.x) * blockDim.x;
-  stage_rows(rows, n, stride, K, KT, i0, rec);
+  const int warps = int(blockDim.x >> 5);
+  const int warp = int(threadIdx.x >> 5), lane = int(threadIdx.x & 31);
+  uint64_t* rec = shm;                                             // [warps][KT]
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(rec + warps * KT);  // [L]
+  uint32_t* base = cnt + L;                                        // [L]
+  const int64_t r0 = int64_t(blockIdx.x) * warps;
+  for (int e = threadIdx.x; e < warps * KT; e += blockDim.x) {
+    const int r = e / KT, q = e - r * KT;
+    rec[e] = (r0 + r < n && q < K) ? rows[(r0 + r) * stride + q] : 0ull;
+  }
   for (int l = threadIdx.x; l < L; l += blockDim.x) cnt[l] = 0;
   __syncthreads();
-  const uint64_t* my = rec + threadIdx.x * KT;
-  int n_items = 0;
-  for (int k = 0; k < K; ++k) {
-    uint64_t x = my[k];
-    n_items += __popcll(x);
-    while (x) {
-      const int b = __ffsll(static_cast<long long>(x)) - 1;
-      x &= x - 1;
-      atomicAdd(&cnt[k * 64 + b], 1u);
-    }
-  }
+  const uint64_t* my = rec + warp * KT;
+  for (int l = lane; l < L; l += 32)
+    if ((my[l >> 6] >> (l & 63)) & 1ull) atomicAdd(&cnt[l], 1u);
   __syncthreads();
   for (int l = threadIdx.x; l < L; l += blockDim.x) {
     const uint32_t c = cnt[l];
@@ -140,24 +138,26 @@ __global__ void multi_scatter_kernel(const uint64_t* __restrict__ rows, int64_t 
     cnt[l] = 0;
   }
   __syncthreads();
-  int rounds = n_items;
-#pragma unroll
-  for (int o = 16; o; o >>= 1) rounds = max(rounds, __shfl_xor_sync(0xffffffffu, rounds, o));
-  const int rec0 = threadIdx.x & ~31;
-  int k = 0;
-  uint64_t x = K > 0 ? my[0] : 0ull;
-  for (int t = 0; t < rounds; ++t) {
-    const bool has = t < n_items;
+  const int64_t i = r0 + warp;
+  const int per = 32 / KT;                   // rows per store
+  const int g = lane / KT, ww = lane - g * KT;  // this lane writes word ww of the g-th row
+  for (int l0 = 0; l0 < L; l0 += 32) {
+    const int l = l0 + lane;
+    const bool has = l < L && ((my[l >> 6] >> (l & 63)) & 1ull);
     uint32_t pos = 0;
     if (has) {
-      while (x == 0ull) x = my[++k];
-      const int b = __ffsll(static_cast<long long>(x)) - 1;
-      x &= x - 1;
-      const int l = k * 64 + b;
       pos = base[l] + atomicAdd(&cnt[l], 1u);
-      ids[pos] = uint32_t(i0 + threadIdx.x);
+      ids[pos] = uint32_t(i);
     }
-    warp_write_rows(rec, rec0, KT, has, pos, out);
+    unsigned m = __ballot_sync(0xffffffffu, has);
+    while (m) {
+      unsigned b = m;
+      for (int k = 0; k < g && b; ++k) b &= b - 1u;  // the g-th set lane of m
+      const int src = b ? __ffs(int(b)) - 1 : 0;
+      const uint32_t p = __shfl_sync(0xffffffffu, pos, src);
+      if (b) out[int64_t(p) * KT + ww] = my[ww];
+      for (int k = 0; k < per && m; ++k) m &= m - 1u;
+    }
   }
 }
 
@@ -489,10 +489,12 @@ cudaError_t launch_multi_scatter(const uint64_t* rows, int64_t n, int stride, in
                                  int L, const uint32_t* off, uint32_t* cursor, uint64_t* out,
                                  uint32_t* ids, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  const int nb = scatter_threads(n);
-  const size_t smem = size_t(nb) * KT * 8 + size_t(2) * L * 4;
-  multi_scatter_kernel<<<unsigned(ceil_div(n, nb)), nb, smem, s>>>(rows, n, stride, K, KT, L, off,
-                                                                   cursor, out, ids);
+  // One warp per row; large inputs take wide blocks, so that popular items
+  // get few global reservations.
+  const int warps = n >= int64_t(num_sms()) * 32 * 4 ? 32 : 8;
+  const size_t smem = size_t(warps) * KT * 8 + size_t(2) * L * 4;
+  multi_scatter_kernel<<<unsigned(ceil_div(n, warps)), warps * 32, smem, s>>>(
+      rows, n, stride, K, KT, L, off, cursor, out, ids);
   count_launches(1);
   return cudaGetLastError();
 }

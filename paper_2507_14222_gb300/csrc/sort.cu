@@ -132,11 +132,14 @@ __global__ void __launch_bounds__(kSortBlockThreads)
       return elem_less<KT>(keys, s0[y], s1[y], si[y], s0[x], s1[x], si[x]);
     }
   };
-  for (int k = 2; k <= kSortTile; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
+  // k = 2^lk, j = 2^lj: pair t compares i = (t with a zero bit inserted at
+  // lj) and l = i + j, in ascending order where bit lk of i is 0.
+  for (int lk = 1; (1 << lk) <= kSortTile; ++lk) {
+    for (int lj = lk - 1; lj >= 0; --lj) {
+      const int j = 1 << lj;
       for (int t = threadIdx.x; t < kSortTile / 2; t += blockDim.x) {
-        const int i = (t / j) * 2 * j + (t % j), l = i + j;
-        const bool up = (i & k) == 0;
+        const int i = ((t >> lj) << (lj + 1)) | (t & (j - 1)), l = i + j;
+        const bool up = ((i >> lk) & 1) == 0;
         if (up ? greater(i, l) : greater(l, i)) {
           const uint64_t a0 = s0[i], a1 = s1[i];
           const uint32_t ai = si[i];
