@@ -70,7 +70,8 @@ typedef struct {
    * double precision in record order. */
   double r;
   int32_t reg3_enabled;
-  /* Subset-test form: 0 = library default (3 where K > 1, else 1);
+  /* Subset-test form: 0 = library default (4 where K rounds up to 2, 4 or
+   * 8; 3 where it rounds up to 16; 1 for K = 1);
    * 1 = integer-pipe kernel (LOP3) on every pair; 2 = tensor-core kernel
    * (tcgen05 0/1 GEMM) on every pair, where K (rounded up to a power of two)
    * is 2, 4 or 8, else 1; 3 = item index: each pattern is tested only

@@ -758,7 +758,8 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
   const bool pruned =
       (prm.subset_kernel == 0 || prm.subset_kernel == 3 || prm.subset_kernel == 4) && KT >= 2;
   const bool tc = prm.subset_kernel != 1 && igk::tc_supported(KT);
-  const bool index_tc = prm.subset_kernel == 4 && igk::tc_supported(KT);
+  const bool index_tc =
+      (prm.subset_kernel == 0 || prm.subset_kernel == 4) && igk::tc_supported(KT);
   m->subset_kernel = pruned ? (index_tc ? 4 : 3) : (tc ? 2 : 1);
   m->index_max_q = prm.index_max_q ? prm.index_max_q : 4;
   m->index_flip = prm.index_flip_factor ? prm.index_flip_factor : 2;

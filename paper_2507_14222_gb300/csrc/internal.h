@@ -135,18 +135,12 @@ bool tc_supported(int KT);
 size_t tc_image_bytes(int64_t n, int KT, bool own_side);
 cudaError_t launch_expand(const uint64_t* rows, int64_t n, int stride, int KT, bool complement,
                           bool own_side, uint8_t* img, cudaStream_t s);
-// A 128-row image tile made from rows [begin, begin + count) of a grouped
-// row array (item index), and one block of work for the tensor-core kernel
-// on such tiles: own tile a_tile (own_count valid rows, the first being
-// grouped row own_first) against stream tiles b_tile .. b_tile + b_tiles - 1
-// (str_count valid rows, the first being grouped row str_first).
-struct TcTile {
-  int64_t begin;
-  int32_t count;
-  int32_t pad;
-};
+// One block of work for the tensor-core kernel on the item index: the
+// resident rows own_first .. own_first + own_count - 1 (at most 128) of a
+// group against its streamed rows str_first .. str_first + str_count - 1, in
+// b_tiles tiles of 128 rows (grouped row numbers).
 struct TcItem {
-  int64_t a_tile, b_tile, own_first, str_first;
+  int64_t own_first, str_first;
   int32_t own_count, b_tiles, str_count, pad;
 };
 
@@ -250,9 +244,10 @@ cudaError_t build_keyed_index(const uint64_t* keyed, int64_t n, int stride, int 
 void release_keyed_index(KeyedIndex* k, cudaStream_t s);
 // The item-index test with its blocks run on the tensor cores (KT 2, 4, 8):
 // the result side -- patterns for MODE_ANY / MODE_COUNT, records for
-// MODE_SUM -- goes to resident 128-row tiles, the other side streams; both
-// are expanded to per-group tile images first.  Same results as the integer
-// grouped kernel; *tests_out as for indexed_subset_prebuilt.
+// MODE_SUM -- goes to resident 128-row tiles, the other side streams; packed
+// rows are expanded to operand tiles in shared memory by a persistent kernel.
+// Same results as the integer grouped kernel; *tests_out as for
+// indexed_subset_prebuilt.
 cudaError_t indexed_subset_tc(int mode, const RecordIndex& idx, const KeyedIndex& kx,
                               uint32_t* out_u32, unsigned long long* out_u64, int* status,
                               int64_t* tests_out, int prof_stage, cudaStream_t s);

@@ -89,43 +89,6 @@ __global__ void expand_kernel(const uint64_t* __restrict__ rows, int64_t n, int 
                             r * 128 + pos * 16) = make_uint4(v[0], v[1], v[2], v[3]);
 }
 
-// The same images for tiles listed in a table: image tile t holds rows
-// [tiles[t].begin, tiles[t].begin + tiles[t].count) of `rows` (count <= R),
-// then zero rows.  Used for the item index, whose groups each start a tile.
-template <int KT>
-__global__ void expand_tiles_kernel(const uint64_t* __restrict__ rows, int stride,
-                                    int complement, const TcTile* __restrict__ tiles,
-                                    int64_t ntiles, uint8_t* __restrict__ img) {
-  constexpr int R = kTcM;  // a power of two: the index arithmetic is shifts
-  constexpr int64_t chunks_per_tile = int64_t(R) * KT * 4;
-  const int64_t id = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (id >= ntiles * chunks_per_tile) return;
-  const int64_t tile = id / chunks_per_tile;
-  const int64_t rem = id - tile * chunks_per_tile;
-  const int katom = int(rem / (R * 8));
-  const int rem2 = int(rem - int64_t(katom) * R * 8);
-  const int r = rem2 >> 3, pos = rem2 & 7;
-  const int c = pos ^ (r & 7);
-  const int k0 = katom * 128 + c * 16;
-  const TcTile tt = tiles[tile];
-  uint32_t bits = 0;
-  if (r < tt.count) {
-    uint64_t w = rows[(tt.begin + r) * stride + (k0 >> 6)];
-    if (complement) w = ~w;
-    bits = uint32_t((w >> (k0 & 63)) & 0xffffu);
-  }
-  uint32_t v[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    uint32_t x = 0;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) x |= ((bits >> (4 * q + b)) & 1u) ? (0x38u << (8 * b)) : 0u;
-    v[q] = x;
-  }
-  *reinterpret_cast<uint4*>(img + tile * (int64_t(R) * KT * 64) + int64_t(katom) * R * 128 +
-                            r * 128 + pos * 16) = make_uint4(v[0], v[1], v[2], v[3]);
-}
-
 // ---- tcgen05 wrappers ---------------------------------------------------------
 
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, atoms of
@@ -205,11 +168,6 @@ struct TcParams {
   uint32_t* out_u32;
   unsigned long long* out_u64;
   int* status;
-  // Item-index blocks: when set, CTA b runs items[b] instead of the dense
-  // (own tile, stream split) grid; results go to out[own_ids[own row]] and
-  // score indexes the streamed rows of the index.
-  const TcItem* items;
-  const uint32_t* own_ids;
 };
 
 template <int KT, int MODE>
@@ -217,35 +175,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) subset_tc_kernel(TcParams p) {
   using S = TcShape<KT>;
   constexpr int STAGES = S::kStages;
   extern __shared__ uint8_t smem_raw[];
-  // This CTA's work: own image tile a_tile (own_valid rows), stream image
-  // tiles b_first .. b_first + ntiles - 1 whose rows are str_first ..
-  // str_first + str_count - 1 of the stream (scores, masks).
-  int64_t a_tile, b_first, own0, str_first, str_count;
-  int own_valid, ntiles;
-  if (p.items) {
-    const TcItem it = p.items[blockIdx.x];
-    a_tile = it.a_tile;
-    b_first = it.b_tile;
-    ntiles = it.b_tiles;
-    own0 = it.own_first;
-    own_valid = it.own_count;
-    str_first = it.str_first;
-    str_count = it.str_count;
-  } else {
-    const int64_t n_own = p.n_own_dev ? int64_t(*p.n_own_dev) : p.n_own;
-    own0 = int64_t(blockIdx.x) * kTcM;
-    if (own0 >= n_own) return;
-    const int64_t t_lo = int64_t(blockIdx.y) * p.tiles_per_split;
-    const int64_t total_tiles = ceil_div(p.n_stream, kTcN);
-    const int64_t t_hi = (t_lo + p.tiles_per_split < total_tiles) ? t_lo + p.tiles_per_split
-                                                                   : total_tiles;
-    ntiles = int(t_hi > t_lo ? t_hi - t_lo : 0);
-    a_tile = blockIdx.x;
-    b_first = p.b_tile0 + t_lo;
-    own_valid = int(n_own - own0 < kTcM ? n_own - own0 : kTcM);
-    str_first = t_lo * kTcN;
-    str_count = p.n_stream - str_first;
-  }
+  const int64_t n_own = p.n_own_dev ? int64_t(*p.n_own_dev) : p.n_own;
+  const int64_t own0 = int64_t(blockIdx.x) * kTcM;
+  if (own0 >= n_own) return;
+  const int64_t t_lo = int64_t(blockIdx.y) * p.tiles_per_split;
+  const int64_t total_tiles = ceil_div(p.n_stream, kTcN);
+  const int64_t t_hi = (t_lo + p.tiles_per_split < total_tiles) ? t_lo + p.tiles_per_split
+                                                                 : total_tiles;
+  const int ntiles = int(t_hi > t_lo ? t_hi - t_lo : 0);
+  const int own_valid = int(n_own - own0 < kTcM ? n_own - own0 : kTcM);
+  const int64_t str_first = t_lo * kTcN;            // stream rows of this CTA's tiles
+  const int64_t str_count = p.n_stream - str_first;
 
   // 1024-byte aligned carve-up of dynamic shared memory.
   const uint32_t raw = smem_u32(smem_raw);
@@ -291,7 +231,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) subset_tc_kernel(TcParams p) {
     if (lane == 0) {
       // Producer: A once, then the B tiles through the ring.
       mbar_arrive_expect_tx(a_full, S::kABytes);
-      bulk_g2s(A_s, p.a_img + size_t(a_tile) * S::kABytes, S::kABytes, a_full);
+      bulk_g2s(A_s, p.a_img + size_t(blockIdx.x) * S::kABytes, S::kABytes, a_full);
       int issued = 0;
       for (int t = 0; t < ntiles; ++t) {
         const int s = t % STAGES;
@@ -300,8 +240,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) subset_tc_kernel(TcParams p) {
           break;
         }
         mbar_arrive_expect_tx(full + s, S::kBBytes);
-        bulk_g2s(B_s + size_t(s) * S::kBBytes, p.b_img + size_t(b_first + t) * S::kBBytes,
-                 S::kBBytes, full + s);
+        bulk_g2s(B_s + size_t(s) * S::kBBytes,
+                 p.b_img + size_t(p.b_tile0 + t_lo + t) * S::kBBytes, S::kBBytes, full + s);
         issued = t + 1;
       }
       // Copies must have landed before the CTA may finish.
@@ -378,7 +318,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) subset_tc_kernel(TcParams p) {
       if (lane == 0) mbar_arrive(acc_empty + b);
     }
     if (valid) {
-      const int64_t row = p.items ? int64_t(p.own_ids[own0 + tile_row]) : own0 + tile_row;
+      const int64_t row = own0 + tile_row;
       if constexpr (MODE == MODE_ANY) {
         if (cov) p.out_u32[row] = 1u;
       }
@@ -428,8 +368,8 @@ static cudaError_t run_tc(const TcArgs& a, cudaStream_t s) {
   if (splits < 1) splits = 1;
   const int64_t per = ceil_div(stream_tiles, splits);
   splits = ceil_div(stream_tiles, per);
-  TcParams p{a.a_img,   a.n_own,   a.n_own_dev, a.b_img,   a.b_tile0, a.n_stream, per,
-             a.score,   a.out_u32, a.out_u64,   a.status,  nullptr,   nullptr};
+  TcParams p{a.a_img, a.n_own, a.n_own_dev, a.b_img,   a.b_tile0, a.n_stream, per,
+             a.score, a.out_u32, a.out_u64,   a.status};
   cudaError_t e = cudaFuncSetAttribute(subset_tc_kernel<KT, MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::kSmem));
   if (e != cudaSuccess) return e;
@@ -458,31 +398,327 @@ cudaError_t launch_expand(const uint64_t* rows, int64_t n, int stride, int KT, b
 }
 
 // ---- item-index blocks on the tensor cores ----------------------------------
+//
+// subset_tc_fused_kernel: the same 0/1 GEMM on the item index's blocks, with
+// no operand images in global memory.  Packed 64*KT-bit rows are copied by
+// TMA into shared staging, and four expander warps write the E4M3 bytes
+// (swizzled as the MMA reads them) straight into shared memory.  The grid is
+// persistent: CTA b runs work items b, b + gridDim.x, ... with its tensor
+// memory allocated once, and expands the next item's own tile as soon as
+// the MMAs on the previous one are done.  Warp roles:
+//   warp 0    lane 0 issues the bulk copies of packed rows (own, then stream);
+//   warp 1    allocates tensor memory; lane 0 issues the MMAs and commits;
+//   warps 2-5 epilogue, as in subset_tc_kernel;
+//   warps 6-21 expand packed tiles into operand tiles.
+// Every wait is bounded; a timeout sets the status and an abort flag that
+// every role checks.
 
-template <int KT, int MODE>
-static cudaError_t run_tc_items(const TcParams& p, int64_t n_items, cudaStream_t s) {
-  using S = TcShape<KT>;
-  cudaError_t e = cudaFuncSetAttribute(subset_tc_kernel<KT, MODE>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::kSmem));
-  if (e != cudaSuccess) return e;
-  subset_tc_kernel<KT, MODE><<<unsigned(n_items), kTcThreads, S::kSmem, s>>>(p);
-  count_launches(1);
-  return cudaGetLastError();
-}
+constexpr int kExpandThreads = 512;
+constexpr int kFusedThreads = 192 + kExpandThreads;
 
 template <int KT>
-static cudaError_t expand_tiles(const uint64_t* rows, bool complement, const TcTile* tiles,
-                                int64_t ntiles, uint8_t* img, cudaStream_t s) {
-  const int64_t chunks = ntiles * int64_t(kTcM) * KT * 4;
-  if (chunks == 0) return cudaSuccess;
-  expand_tiles_kernel<KT><<<unsigned(ceil_div(chunks, 256)), 256, 0, s>>>(
-      rows, KT, complement ? 1 : 0, tiles, ntiles, img);
-  count_launches(1);
-  return cudaGetLastError();
+struct FusedShape {
+  static constexpr uint32_t kImgBytes = uint32_t(128) * KT * 64;  // one expanded tile
+  static constexpr uint32_t kPkBytes = uint32_t(128) * KT * 8;    // one packed tile
+  static constexpr int kFit = (225 * 1024 - 2048 - int(kImgBytes) - int(kPkBytes)) /
+                              int(kImgBytes + kPkBytes);
+  static constexpr int kStages = kFit > 4 ? 4 : kFit;
+  static constexpr size_t kSmem =
+      1024 + kImgBytes + kPkBytes + size_t(kStages) * (kImgBytes + kPkBytes) + 512;
+};
+
+struct FusedParams {
+  const TcItem* items;
+  int64_t n_items;
+  const uint64_t* own_rows;  // grouped rows of the resident side (stride KT)
+  const uint64_t* str_rows;  // grouped rows of the streamed side (stride KT)
+  int own_complement;        // 1: the resident side is the record side
+  const uint32_t* own_ids;   // original id of each grouped resident row
+  const uint64_t* score;     // MODE_SUM: S of each grouped streamed row
+  uint32_t* out_u32;
+  unsigned long long* out_u64;
+  int* status;
+};
+
+// One E4M3 byte (0x38 = 1.0, or 0) per bit of a 4-bit group: the multiply
+// places bit b of n at bit 8b (the four shifted copies of n do not overlap),
+// the mask keeps those bits, the second multiply turns each into 0x38.
+__device__ __forceinline__ uint32_t spread_nibble(uint32_t n) {
+  return ((n * 0x00204081u) & 0x01010101u) * 0x38u;
 }
 
+// Expands `count` packed rows (the rest zero) into one 128-row operand tile
+// in the swizzled K-major layout of expand_kernel.  Thread e of n handles
+// 16-byte chunks e, e + n, ...; consecutive threads write consecutive chunks.
+template <int KT>
+__device__ __forceinline__ void expand_tile_smem(const uint64_t* pk, int count, bool complement,
+                                                 uint8_t* dst, int e, int n) {
+  constexpr int kChunks = 128 * KT * 4;
+#pragma unroll 4
+  for (int id = e; id < kChunks; id += n) {
+    const int katom = id >> 10, r = (id >> 3) & 127, pos = id & 7;
+    const int k0 = katom * 128 + ((pos ^ (r & 7)) << 4);
+    uint32_t bits = 0;
+    if (r < count) {
+      uint64_t w = pk[r * KT + (k0 >> 6)];
+      if (complement) w = ~w;
+      bits = uint32_t(w >> (k0 & 63)) & 0xffffu;
+    }
+    *reinterpret_cast<uint4*>(dst + katom * 16384 + r * 128 + pos * 16) =
+        make_uint4(spread_nibble(bits & 15u), spread_nibble((bits >> 4) & 15u),
+                   spread_nibble((bits >> 8) & 15u), spread_nibble(bits >> 12));
+  }
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+template <int KT, int MODE>
+__global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(FusedParams p) {
+  using S = FusedShape<KT>;
+  constexpr int STAGES = S::kStages;
+  constexpr int PKW = 128 * KT;  // words of one packed tile
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* base = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+  uint8_t* A_x = base;
+  uint8_t* B_x = A_x + S::kImgBytes;
+  uint64_t* A_pk = reinterpret_cast<uint64_t*>(B_x + size_t(STAGES) * S::kImgBytes);
+  uint64_t* B_pk = A_pk + PKW;
+  uint64_t* bars = B_pk + size_t(STAGES) * PKW;
+  uint64_t* a_pk_full = bars;
+  uint64_t* a_pk_empty = bars + 1;
+  uint64_t* a_x_full = bars + 2;
+  uint64_t* a_x_empty = bars + 3;
+  uint64_t* b_pk_full = bars + 4;
+  uint64_t* b_pk_empty = b_pk_full + STAGES;
+  uint64_t* b_x_full = b_pk_empty + STAGES;
+  uint64_t* b_x_empty = b_x_full + STAGES;
+  uint64_t* acc_full = b_x_empty + STAGES;
+  uint64_t* acc_empty = acc_full + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t G = gridDim.x;
+  if (threadIdx.x == 0) {
+    mbar_init(a_pk_full, 1);
+    mbar_init(a_pk_empty, kExpandThreads / 32);
+    mbar_init(a_x_full, kExpandThreads / 32);
+    mbar_init(a_x_empty, 1);
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(b_pk_full + s, 1);
+      mbar_init(b_pk_empty + s, kExpandThreads / 32);
+      mbar_init(b_x_full + s, kExpandThreads / 32);
+      mbar_init(b_x_empty + s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(acc_full + b, 1);
+      mbar_init(acc_empty + b, 4);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // Producer of packed tiles.
+      int64_t tt = 0, ii = 0, issued_b = 0;
+      bool issued_a = false;
+      for (int64_t it = blockIdx.x; it < p.n_items && !*abort_flag; it += G, ++ii) {
+        const TcItem w = p.items[it];
+        if (!mbar_wait(a_pk_empty, uint32_t((ii & 1) ^ 1), p.status)) {
+          *abort_flag = 1;
+          break;
+        }
+        const uint32_t abytes = uint32_t(w.own_count) * KT * 8;
+        mbar_arrive_expect_tx(a_pk_full, abytes);
+        bulk_g2s(A_pk, p.own_rows + w.own_first * KT, abytes, a_pk_full);
+        issued_a = true;
+        for (int t = 0; t < w.b_tiles; ++t, ++tt) {
+          const int s = int(tt % STAGES);
+          if (!mbar_wait(b_pk_empty + s, uint32_t(((tt / STAGES) & 1) ^ 1), p.status) ||
+              *abort_flag) {
+            *abort_flag = 1;
+            break;
+          }
+          const int64_t left = int64_t(w.str_count) - int64_t(t) * 128;
+          const uint32_t bytes = uint32_t(left < 128 ? left : 128) * KT * 8;
+          mbar_arrive_expect_tx(b_pk_full + s, bytes);
+          bulk_g2s(B_pk + size_t(s) * PKW, p.str_rows + (w.str_first + int64_t(t) * 128) * KT,
+                   bytes, b_pk_full + s);
+          issued_b = tt + 1;
+        }
+      }
+      if (*abort_flag) {
+        // Copies in flight must land before the CTA may finish.
+        if (issued_a) mbar_wait(a_pk_full, uint32_t((ii - (ii > 0 ? 1 : 0)) & 1), p.status);
+        for (int64_t t = (issued_b > STAGES ? issued_b - STAGES : 0); t < issued_b; ++t)
+          mbar_wait(b_pk_full + (t % STAGES), uint32_t((t / STAGES) & 1), p.status);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer.
+      int64_t tt = 0, ii = 0, last = -1;
+      bool ok = true;
+      const uint32_t a_base = smem_u32(A_x);
+      for (int64_t it = blockIdx.x; it < p.n_items && ok; it += G, ++ii) {
+        const int b_tiles = p.items[it].b_tiles;
+        if (!mbar_wait(a_x_full, uint32_t(ii & 1), p.status) || *abort_flag) {
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        for (int t = 0; t < b_tiles; ++t, ++tt) {
+          const int s = int(tt % STAGES), b = int(tt & 1);
+          if (!mbar_wait(b_x_full + s, uint32_t((tt / STAGES) & 1), p.status) ||
+              !mbar_wait(acc_empty + b, uint32_t(((tt >> 1) & 1) ^ 1), p.status) ||
+              *abort_flag) {
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t b_base = smem_u32(B_x + size_t(s) * S::kImgBytes);
+          const uint32_t d = tmem + uint32_t(b * kTcN);
+#pragma unroll 4
+          for (int k = 0; k < KT * 2; ++k) {
+            const uint32_t off = uint32_t(k >> 2) * (128 * 128) + uint32_t(k & 3) * 32;
+            tc_mma(d, sw128_desc(a_base + off), sw128_desc(b_base + off), k > 0 ? 1u : 0u);
+          }
+          tc_commit(b_x_empty + s);
+          tc_commit(acc_full + b);
+          last = tt;
+        }
+        if (!ok) break;
+        tc_commit(a_x_empty);  // the own tile is free once this item's MMAs are done
+      }
+      if (last >= 0) mbar_wait(acc_full + (last & 1), uint32_t((last >> 1) & 1), p.status);
+    }
+  } else if (warp < 6) {
+    // Epilogue: warp w reads accumulator lanes 32*(w % 4) .. +32.
+    const int quarter = warp & 3;
+    const int tile_row = quarter * 32 + lane;
+    int64_t tt = 0;
+    bool ok = true;
+    for (int64_t it = blockIdx.x; it < p.n_items && ok; it += G) {
+      const TcItem w = p.items[it];
+      bool cov = false;
+      uint32_t cnt = 0;
+      unsigned long long sum = 0;
+      for (int t = 0; t < w.b_tiles; ++t, ++tt) {
+        const int b = int(tt & 1);
+        const bool got = mbar_wait(acc_full + b, uint32_t((tt >> 1) & 1), p.status);
+        if (!__all_sync(0xffffffffu, got) || *abort_flag) {
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const int64_t j0 = w.str_first + int64_t(t) * 128;
+        const int64_t left = int64_t(w.str_count) - int64_t(t) * 128;
+        const int nvalid = int(left < 128 ? left : 128);
+#pragma unroll 1
+        for (int c = 0; c < 128; c += 32) {
+          uint32_t v[32];
+          tmem_ld32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * kTcN + c), v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const bool hit = v[i] == 0u && (c + i) < nvalid;
+            if constexpr (MODE == MODE_ANY) cov |= hit;
+            if constexpr (MODE == MODE_COUNT) cnt += hit ? 1u : 0u;
+            if constexpr (MODE == MODE_SUM) {
+              if (hit) sum += p.score[j0 + c + i];
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acc_empty + b);
+      }
+      if (!ok) break;
+      if (tile_row < w.own_count) {
+        const int64_t row = int64_t(p.own_ids[w.own_first + tile_row]);
+        if constexpr (MODE == MODE_ANY) {
+          if (cov) p.out_u32[row] = 1u;
+        }
+        if constexpr (MODE == MODE_COUNT) {
+          if (cnt) atomicAdd(p.out_u32 + row, cnt);
+        }
+        if constexpr (MODE == MODE_SUM) {
+          if (sum) atomicAdd(p.out_u64 + row, sum);
+        }
+      }
+    }
+  } else {
+    // Expanders.
+    const int e = threadIdx.x - 6 * 32;
+    int64_t tt = 0, ii = 0;
+    bool ok = true;
+    for (int64_t it = blockIdx.x; it < p.n_items && ok; it += G, ++ii) {
+      const TcItem w = p.items[it];
+      bool got = mbar_wait(a_pk_full, uint32_t(ii & 1), p.status) &&
+                 mbar_wait(a_x_empty, uint32_t((ii & 1) ^ 1), p.status);
+      if (!__all_sync(0xffffffffu, got) || *abort_flag) {
+        *abort_flag = 1;
+        break;
+      }
+      expand_tile_smem<KT>(A_pk, w.own_count, p.own_complement != 0, A_x, e, kExpandThreads);
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(a_pk_empty);
+        mbar_arrive(a_x_full);
+      }
+      for (int t = 0; t < w.b_tiles; ++t, ++tt) {
+        const int s = int(tt % STAGES);
+        const uint32_t ph = uint32_t((tt / STAGES) & 1);
+        got = mbar_wait(b_pk_full + s, ph, p.status) && mbar_wait(b_x_empty + s, ph ^ 1, p.status);
+        if (!__all_sync(0xffffffffu, got) || *abort_flag) {
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        const int64_t left = int64_t(w.str_count) - int64_t(t) * 128;
+        expand_tile_smem<KT>(B_pk + size_t(s) * PKW, int(left < 128 ? left : 128),
+                             p.own_complement == 0, B_x + size_t(s) * S::kImgBytes, e,
+                             kExpandThreads);
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(b_pk_empty + s);
+          mbar_arrive(b_x_full + s);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+
+
 namespace {
-// Pinned staging for the tile tables and work items, one per host thread;
+// Pinned staging for the work items, one per host thread;
 // reused once the copy out of it (recorded by `done`) has finished.
 struct TcStaging {
   uint8_t* buf = nullptr;
@@ -492,10 +728,21 @@ struct TcStaging {
 thread_local TcStaging g_tc_staging;
 }  // namespace
 
+template <int KT, int MODE>
+static cudaError_t run_fused(const FusedParams& p, cudaStream_t s) {
+  using S = FusedShape<KT>;
+  cudaError_t e = cudaFuncSetAttribute(subset_tc_fused_kernel<KT, MODE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::kSmem));
+  if (e != cudaSuccess) return e;
+  const int64_t grid = std::min<int64_t>(p.n_items, int64_t(num_sms()));
+  subset_tc_fused_kernel<KT, MODE><<<unsigned(grid), kFusedThreads, S::kSmem, s>>>(p);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t indexed_subset_tc(int mode, const RecordIndex& idx, const KeyedIndex& kx,
                               uint32_t* out_u32, unsigned long long* out_u64, int* status,
                               int64_t* tests_out, int prof_stage, cudaStream_t s) {
-  static_assert(kTcM == kTcN, "own and stream tiles share one tile table layout");
   *tests_out = 0;
   const int L = idx.L, KT = idx.KT;
   if (kx.n == 0 || idx.n_rows == 0 || !tc_supported(KT)) return cudaErrorInvalidValue;
@@ -504,9 +751,7 @@ cudaError_t indexed_subset_tc(int mode, const RecordIndex& idx, const KeyedIndex
   const bool own_multi = mode == MODE_SUM;
   const uint32_t* own_off = own_multi ? idx.h_off.data() : kx.h_off.data();
   const uint32_t* str_off = own_multi ? kx.h_off.data() : idx.h_off.data();
-  std::vector<TcTile> tiles;  // own tiles, then stream tiles
   std::vector<TcItem> items;
-  std::vector<int64_t> a0(L, -1), b0(L, -1);
   int64_t tests = 0, pair_tiles = 0;
   for (int l = 0; l < L; ++l) {
     const int64_t no = int64_t(own_off[l + 1]) - own_off[l];
@@ -514,33 +759,20 @@ cudaError_t indexed_subset_tc(int mode, const RecordIndex& idx, const KeyedIndex
     if (no == 0 || ns == 0) continue;
     tests += no * ns;
     pair_tiles += ceil_div(no, kTcM) * ceil_div(ns, kTcN);
-    a0[l] = int64_t(tiles.size());
-    for (int64_t r = 0; r < no; r += kTcM)
-      tiles.push_back(TcTile{int64_t(own_off[l]) + r, int32_t(std::min<int64_t>(kTcM, no - r)), 0});
   }
-  const int64_t n_a = int64_t(tiles.size());
-  for (int l = 0; l < L; ++l) {
-    if (a0[l] < 0) continue;
-    const int64_t ns = int64_t(str_off[l + 1]) - str_off[l];
-    b0[l] = int64_t(tiles.size()) - n_a;
-    for (int64_t r = 0; r < ns; r += kTcN)
-      tiles.push_back(TcTile{int64_t(str_off[l]) + r, int32_t(std::min<int64_t>(kTcN, ns - r)), 0});
-  }
-  const int64_t n_b = int64_t(tiles.size()) - n_a;
   *tests_out = tests;
-  if (n_a == 0) return cudaSuccess;
-  // About four blocks per SM: stream ranges of `per` tiles.
-  const int64_t per = std::max<int64_t>(1, pair_tiles / (int64_t(num_sms()) * 4));
+  if (pair_tiles == 0) return cudaSuccess;
+  // Stream ranges of `per` tiles (about eight items per SM), largest items
+  // first: the persistent CTAs take items round-robin.
+  const int64_t per = std::max<int64_t>(1, pair_tiles / (int64_t(num_sms()) * 8));
   for (int l = 0; l < L; ++l) {
-    if (a0[l] < 0) continue;
     const int64_t no = int64_t(own_off[l + 1]) - own_off[l];
     const int64_t ns = int64_t(str_off[l + 1]) - str_off[l];
+    if (no == 0 || ns == 0) continue;
     const int64_t nb = ceil_div(ns, kTcN);
     for (int64_t a = 0; a * kTcM < no; ++a)
       for (int64_t b = 0; b < nb; b += per) {
         TcItem it;
-        it.a_tile = a0[l] + a;
-        it.b_tile = b0[l] + b;
         it.own_first = int64_t(own_off[l]) + a * kTcM;
         it.str_first = int64_t(str_off[l]) + b * kTcN;
         it.own_count = int32_t(std::min<int64_t>(kTcM, no - a * kTcM));
@@ -550,81 +782,54 @@ cudaError_t indexed_subset_tc(int mode, const RecordIndex& idx, const KeyedIndex
         items.push_back(it);
       }
   }
-  // One device buffer: tile table, items, then the two images.
-  const size_t row_bytes = size_t(KT) * 64;
-  const size_t tiles_bytes = ((tiles.size() * sizeof(TcTile) + 255) / 256) * 256;
-  const size_t items_bytes = ((items.size() * sizeof(TcItem) + 255) / 256) * 256;
-  const size_t a_bytes = size_t(n_a) * kTcM * row_bytes, b_bytes = size_t(n_b) * kTcN * row_bytes;
-  const size_t table_bytes = tiles_bytes + items_bytes;
+  std::stable_sort(items.begin(), items.end(),
+                   [](const TcItem& x, const TcItem& y) { return x.b_tiles > y.b_tiles; });
+  const size_t bytes = items.size() * sizeof(TcItem);
   TcStaging& st = g_tc_staging;
   cudaError_t e;
   if (st.done && (e = cudaEventSynchronize(st.done)) != cudaSuccess) return e;
-  if (st.cap < table_bytes) {
+  if (st.cap < bytes) {
     if (st.buf) cudaFreeHost(st.buf);
     st.buf = nullptr;
     st.cap = 0;
-    if ((e = cudaMallocHost(reinterpret_cast<void**>(&st.buf), table_bytes * 2)) != cudaSuccess)
-      return e;
-    st.cap = table_bytes * 2;
+    if ((e = cudaMallocHost(reinterpret_cast<void**>(&st.buf), bytes * 2)) != cudaSuccess) return e;
+    st.cap = bytes * 2;
   }
   if (!st.done && (e = cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming)) != cudaSuccess)
     return e;
-  std::memcpy(st.buf, tiles.data(), tiles.size() * sizeof(TcTile));
-  std::memcpy(st.buf + tiles_bytes, items.data(), items.size() * sizeof(TcItem));
-  void* mem = nullptr;
-  e = cudaMallocAsync(&mem, table_bytes + a_bytes + b_bytes, s);
+  std::memcpy(st.buf, items.data(), bytes);
+  TcItem* d_items = nullptr;
+  e = cudaMallocAsync(reinterpret_cast<void**>(&d_items), bytes, s);
   if (e != cudaSuccess) return e;
-  uint8_t* m = static_cast<uint8_t*>(mem);
-  const TcTile* d_tiles = reinterpret_cast<const TcTile*>(m);
-  const TcItem* d_items = reinterpret_cast<const TcItem*>(m + tiles_bytes);
-  uint8_t* a_img = m + table_bytes;
-  uint8_t* b_img = a_img + a_bytes;
-  e = cudaMemcpyAsync(m, st.buf, table_bytes, cudaMemcpyHostToDevice, s);
+  e = cudaMemcpyAsync(d_items, st.buf, bytes, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaEventRecord(st.done, s);
-  const uint64_t* own_rows = own_multi ? idx.rows : kx.rows;
-  const uint64_t* str_rows = own_multi ? kx.rows : idx.rows;
-  // The images are timed with the index build, the GEMM under the caller's
-  // stage.
-  void* tok = e == cudaSuccess ? prof_begin(kStageIndexBuild, s) : nullptr;
   if (e == cudaSuccess) {
-    switch (KT) {
-      case 2:
-        e = expand_tiles<2>(own_rows, own_multi, d_tiles, n_a, a_img, s);
-        if (e == cudaSuccess) e = expand_tiles<2>(str_rows, !own_multi, d_tiles + n_a, n_b, b_img, s);
-        break;
-      case 4:
-        e = expand_tiles<4>(own_rows, own_multi, d_tiles, n_a, a_img, s);
-        if (e == cudaSuccess) e = expand_tiles<4>(str_rows, !own_multi, d_tiles + n_a, n_b, b_img, s);
-        break;
-      case 8:
-        e = expand_tiles<8>(own_rows, own_multi, d_tiles, n_a, a_img, s);
-        if (e == cudaSuccess) e = expand_tiles<8>(str_rows, !own_multi, d_tiles + n_a, n_b, b_img, s);
-        break;
-    }
-  }
-  prof_end(tok);
-  tok = nullptr;
-  if (e == cudaSuccess) {
-    tok = prof_stage >= 0 ? prof_begin(prof_stage, s) : nullptr;
-    TcParams p{a_img,   int64_t(n_a) * kTcM, nullptr, b_img,  0,      int64_t(n_b) * kTcN, 0,
-               own_multi ? kx.score : nullptr, out_u32, out_u64, status, d_items,
-               own_multi ? idx.ids : kx.ids};
-    const int64_t n_items = int64_t(items.size());
-#define IG_TCI_CASE(KTV)                                                              \
-  case KTV:                                                                           \
-    e = mode == MODE_ANY     ? run_tc_items<KTV, MODE_ANY>(p, n_items, s)             \
-        : mode == MODE_COUNT ? run_tc_items<KTV, MODE_COUNT>(p, n_items, s)           \
-                             : run_tc_items<KTV, MODE_SUM>(p, n_items, s);            \
+    FusedParams p{d_items,
+                  int64_t(items.size()),
+                  own_multi ? idx.rows : kx.rows,
+                  own_multi ? kx.rows : idx.rows,
+                  own_multi ? 1 : 0,
+                  own_multi ? idx.ids : kx.ids,
+                  own_multi ? kx.score : nullptr,
+                  out_u32,
+                  out_u64,
+                  status};
+    void* tok = prof_stage >= 0 ? prof_begin(prof_stage, s) : nullptr;
+#define IG_TCF_CASE(KTV)                                                   \
+  case KTV:                                                                \
+    e = mode == MODE_ANY     ? run_fused<KTV, MODE_ANY>(p, s)              \
+        : mode == MODE_COUNT ? run_fused<KTV, MODE_COUNT>(p, s)            \
+                             : run_fused<KTV, MODE_SUM>(p, s);             \
     break;
     switch (KT) {
-      IG_TCI_CASE(2)
-      IG_TCI_CASE(4)
-      IG_TCI_CASE(8)
+      IG_TCF_CASE(2)
+      IG_TCF_CASE(4)
+      IG_TCF_CASE(8)
     }
-#undef IG_TCI_CASE
+#undef IG_TCF_CASE
+    prof_end(tok);
   }
-  prof_end(tok);
-  cudaFreeAsync(mem, s);
+  cudaFreeAsync(d_items, s);
   return e;
 }
 

@@ -264,7 +264,7 @@ def _workload_fit(w, r=None, kernel=0):
     d_codes = dev(w.train_codes)
     rows = ig.ig_encode(d_codes, w.cards)
     m = ig.ig_fit(rows, dev(w.train_labels), r=r, subset_kernel=kernel)
-    assert m.info()["subset_kernel"] == {0: 3, 1: 1, 2: 2, 3: 3, 4: 4}[kernel]
+    assert m.info()["subset_kernel"] == {0: 4, 1: 1, 2: 2, 3: 3, 4: 4}[kernel]
     return m, oracle.encode(w.train_codes, w.cards)
 
 
