@@ -202,32 +202,61 @@ __global__ void rehash_kernel(const uint64_t* __restrict__ X, const uint64_t* __
   if (threadIdx.x == 0 && n_new != 0) atomicAdd(to.count, (unsigned long long)n_new);
 }
 
-// Warp-aggregated append of every stored key, recomputed from its pair.
+// Appends every stored key, recomputed from its pair.  Each block takes a
+// contiguous range of slots: it first counts the stored keys there and
+// reserves room for them with one atomic on the global count, then places
+// them through a shared-memory cursor -- one global atomic per block rather
+// than per warp, all on one address.  (The order of the output does not
+// matter: it is sorted into canonical order later.)
 template <int KT>
 __global__ void compact_kernel(const uint64_t* __restrict__ X, const uint64_t* __restrict__ slots,
                                uint64_t cap, uint64_t* __restrict__ out, int64_t out_rows,
                                unsigned long long* out_count, int* status) {
+  __shared__ unsigned int blk_count, blk_cursor;
+  __shared__ unsigned long long blk_base;
   const int lane = threadIdx.x & 31;
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31);
-       base < int64_t(cap); base += stride) {
-    int64_t s = base + lane;
-    const uint64_t v = s < int64_t(cap) ? slots[s] : 0ull;
-    unsigned m = __ballot_sync(0xffffffffu, v != 0ull);
-    if (m == 0) continue;
-    unsigned long long pos0 = 0;
-    if (lane == 0) pos0 = atomicAdd(out_count, (unsigned long long)__popc(m));
-    pos0 = __shfl_sync(0xffffffffu, pos0, 0);
-    if (v != 0ull) {
-      uint64_t pos = pos0 + __popc(m & ((1u << lane) - 1u));
-      if (pos >= uint64_t(out_rows)) {
-        set_status(status, ST_COUNT);
-        continue;
-      }
-      uint64_t b[KT];
-      pair_key<KT>(X, v, b);
+  const int64_t per = ((int64_t(cap) + gridDim.x - 1) / gridDim.x + 31) & ~int64_t(31);
+  const int64_t lo = int64_t(blockIdx.x) * per;
+  const int64_t hi = lo + per < int64_t(cap) ? lo + per : int64_t(cap);
+  if (threadIdx.x == 0) {
+    blk_count = 0;
+    blk_cursor = 0;
+  }
+  __syncthreads();
+  unsigned int mine = 0;
+  for (int64_t s = lo + threadIdx.x; s < hi; s += blockDim.x) mine += slots[s] != 0ull ? 1u : 0u;
 #pragma unroll
-      for (int k = 0; k < KT; ++k) out[pos * KT + k] = b[k];
+  for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+  if (lane == 0 && mine) atomicAdd(&blk_count, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) blk_base = blk_count ? atomicAdd(out_count, (unsigned long long)blk_count) : 0ull;
+  __syncthreads();
+  for (int64_t base = lo + (threadIdx.x & ~31); base < hi; base += blockDim.x) {
+    const int64_t s = base + lane;
+    const uint64_t v = s < hi ? slots[s] : 0ull;
+    const unsigned m = __ballot_sync(0xffffffffu, v != 0ull);
+    if (m == 0) continue;
+    unsigned int p0 = 0;
+    if (lane == 0) p0 = atomicAdd(&blk_cursor, unsigned(__popc(m)));
+    p0 = __shfl_sync(0xffffffffu, p0, 0);
+    if (v == 0ull) continue;
+    const uint64_t pos = blk_base + p0 + unsigned(__popc(m & ((1u << lane) - 1u)));
+    if (pos >= uint64_t(out_rows)) {
+      set_status(status, ST_COUNT);
+      continue;
+    }
+    const uint64_t* a = X + ((v >> kIdxBits) & kIdxMask) * KT;
+    const uint64_t* b = X + (v & kIdxMask) * KT;
+    if constexpr (KT >= 2) {
+#pragma unroll
+      for (int k = 0; k < KT; k += 2) {
+        const ulonglong2 va = __ldg(reinterpret_cast<const ulonglong2*>(a + k));
+        const ulonglong2 vb = __ldg(reinterpret_cast<const ulonglong2*>(b + k));
+        *reinterpret_cast<ulonglong2*>(out + pos * KT + k) =
+            make_ulonglong2(va.x & vb.x, va.y & vb.y);
+      }
+    } else {
+      out[pos] = __ldg(a) & __ldg(b);
     }
   }
 }
@@ -254,8 +283,10 @@ cudaError_t launch_rehash(const uint64_t* X, const uint64_t* from, uint64_t from
 cudaError_t launch_compact(const uint64_t* X, const uint64_t* slots, uint64_t cap, int KT,
                            uint64_t* out, int64_t out_rows, unsigned long long* out_count,
                            int* status, cudaStream_t s) {
-  int64_t blocks = ceil_div(int64_t(cap), 256);
-  if (blocks > 8 * 1024) blocks = 8 * 1024;
+  // Ranges of at least 4,096 slots, at most 16 blocks per SM.
+  int64_t blocks = ceil_div(int64_t(cap), 4096);
+  if (blocks > int64_t(num_sms()) * 16) blocks = int64_t(num_sms()) * 16;
+  if (blocks < 1) blocks = 1;
   IG_DISPATCH_KT(KT, (compact_kernel<KTC><<<unsigned(blocks), 256, 0, s>>>(
                          X, slots, cap, out, out_rows, out_count, status)));
   count_launches(1);

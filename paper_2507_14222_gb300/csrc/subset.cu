@@ -247,20 +247,39 @@ __global__ void select_unflagged_kernel(const uint64_t* __restrict__ rows, int64
                                         uint64_t* __restrict__ out,
                                         unsigned long long* out_count,
                                         const unsigned long long* n_dev) {
+  // Each block takes a contiguous range of rows: it counts the unflagged
+  // ones, reserves room for them with one atomic on the global count, and
+  // places them through a shared-memory cursor (one global atomic per block).
+  __shared__ unsigned int blk_count, blk_cursor;
+  __shared__ unsigned long long blk_base;
   if (n_dev) n = int64_t(*n_dev);
   const int lane = threadIdx.x & 31;
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31);
-       base < n; base += stride) {
-    int64_t i = base + lane;
-    bool keep = i < n && flag[i] == 0u;
-    unsigned m = __ballot_sync(0xffffffffu, keep);
+  const int64_t per = ((n + gridDim.x - 1) / gridDim.x + 31) & ~int64_t(31);
+  const int64_t lo = int64_t(blockIdx.x) * per;
+  const int64_t hi = lo + per < n ? lo + per : n;
+  if (threadIdx.x == 0) {
+    blk_count = 0;
+    blk_cursor = 0;
+  }
+  __syncthreads();
+  unsigned int mine = 0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) mine += flag[i] == 0u ? 1u : 0u;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+  if (lane == 0 && mine) atomicAdd(&blk_count, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) blk_base = blk_count ? atomicAdd(out_count, (unsigned long long)blk_count) : 0ull;
+  __syncthreads();
+  for (int64_t base = lo + (threadIdx.x & ~31); base < hi; base += blockDim.x) {
+    const int64_t i = base + lane;
+    const bool keep = i < hi && flag[i] == 0u;
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
     if (m == 0) continue;
-    unsigned long long pos0 = 0;
-    if (lane == 0) pos0 = atomicAdd(out_count, (unsigned long long)__popc(m));
-    pos0 = __shfl_sync(0xffffffffu, pos0, 0);
+    unsigned int p0 = 0;
+    if (lane == 0) p0 = atomicAdd(&blk_cursor, unsigned(__popc(m)));
+    p0 = __shfl_sync(0xffffffffu, p0, 0);
     if (keep) {
-      uint64_t pos = pos0 + __popc(m & ((1u << lane) - 1u));
+      const uint64_t pos = blk_base + p0 + unsigned(__popc(m & ((1u << lane) - 1u)));
 #pragma unroll
       for (int k = 0; k < KT; ++k) out[pos * KT + k] = rows[i * KT + k];
     }
@@ -272,8 +291,11 @@ cudaError_t launch_select_unflagged(const uint64_t* rows, int64_t n, int KT,
                                     unsigned long long* out_count, cudaStream_t s,
                                     const unsigned long long* n_dev) {
   if (n == 0) return cudaSuccess;
-  int64_t blocks = ceil_div(n, 256);
-  if (blocks > 8 * 1024) blocks = 8 * 1024;
+  // Ranges of at least 2,048 rows, at most 16 blocks per SM (n is an upper
+  // bound when the count is on the device).
+  int64_t blocks = ceil_div(n, 2048);
+  if (blocks > int64_t(num_sms()) * 16) blocks = int64_t(num_sms()) * 16;
+  if (blocks < 1) blocks = 1;
   IG_DISPATCH_KT(KT, (select_unflagged_kernel<KTC><<<unsigned(blocks), 256, 0, s>>>(
                          rows, n, flag, out, out_count, n_dev)));
   count_launches(1);
