@@ -501,8 +501,8 @@ def stage_roofline(name, ms, launches, work, info, K, clocks, steps, workload=No
     executed = tests.get(name, work)
     kernel = SINGLE_KERNEL_STAGES[name]
     index_tc = info.get("subset_kernel") == 4 and name.endswith("_idx")
-    if index_tc:  # item-index blocks run by the tensor-core kernel
-        kernel = kernel.replace("grouped_subset_kernel<K, ", "subset_tc_kernel<") + " (index blocks)"
+    if index_tc:  # item-index blocks run by the fused tensor-core kernel
+        kernel = kernel.replace("grouped_subset_kernel<", "subset_tc_fused_kernel<")
     out = {"kernel": kernel.replace("K,", f"{K},"), "stage": name,
            "launches": int(launches), "avg_launch_ms": ms / max(1, launches)}
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
