@@ -118,6 +118,16 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t
       : "memory");
 }
 
+__device__ __forceinline__ void tc_mma_desc(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -401,30 +411,45 @@ cudaError_t launch_expand(const uint64_t* rows, int64_t n, int stride, int KT, b
 //
 // subset_tc_fused_kernel: the same 0/1 GEMM on the item index's blocks, with
 // no operand images in global memory.  Packed 64*KT-bit rows are copied by
-// TMA into shared staging, and four expander warps write the E4M3 bytes
-// (swizzled as the MMA reads them) straight into shared memory.  The grid is
-// persistent: CTA b runs work items b, b + gridDim.x, ... with its tensor
-// memory allocated once, and expands the next item's own tile as soon as
-// the MMAs on the previous one are done.  Warp roles:
-//   warp 0    lane 0 issues the bulk copies of packed rows (own, then stream);
+// TMA into shared staging, and expander warps write the E4M3 bytes (swizzled
+// as the MMA reads them) straight into shared memory.  A work item holds up
+// to 256 resident rows of one item group, as two M = 128 halves that share
+// every expanded stream tile (64 rows, N = 64), so that the expansion --
+// integer work that sets this kernel's pace -- is spent once for two MMAs;
+// that pays where groups are large (evidence, resident side = records),
+// while coherence and support keep one half and 128-row stream tiles.  The grid
+// is persistent: CTA b runs items b, b + gridDim.x, ... with its tensor
+// memory allocated once, and expands the next item's resident rows as soon
+// as the MMAs on the previous one are done.  Warp roles:
+//   warp 0    lane 0 issues the bulk copies of packed rows;
 //   warp 1    allocates tensor memory; lane 0 issues the MMAs and commits;
-//   warps 2-5 epilogue, as in subset_tc_kernel;
-//   warps 6-21 expand packed tiles into operand tiles.
+//   warps 2-5 epilogue: lanes of TMEM quarter w % 4, both halves;
+//   warps 6-  expand packed tiles into operand tiles.
 // Every wait is bounded; a timeout sets the status and an abort flag that
 // every role checks.
 
 constexpr int kExpandThreads = 512;
 constexpr int kFusedThreads = 192 + kExpandThreads;
+// Resident halves and stream-tile rows per work item, by mode.
+constexpr int fused_halves(int mode) { return mode == MODE_SUM ? 2 : 1; }
+constexpr int fused_n(int mode) { return mode == MODE_SUM ? 64 : 128; }
 
-template <int KT>
+template <int KT, int MODE>
 struct FusedShape {
-  static constexpr uint32_t kImgBytes = uint32_t(128) * KT * 64;  // one expanded tile
-  static constexpr uint32_t kPkBytes = uint32_t(128) * KT * 8;    // one packed tile
-  static constexpr int kFit = (225 * 1024 - 2048 - int(kImgBytes) - int(kPkBytes)) /
-                              int(kImgBytes + kPkBytes);
+  static constexpr int kHalves = fused_halves(MODE);
+  static constexpr int kN = fused_n(MODE);                          // stream rows per tile
+  static constexpr int kOwn = 128 * kHalves;                        // resident rows per item
+  static constexpr uint32_t kImgA = uint32_t(128) * KT * 64;       // one expanded half
+  static constexpr uint32_t kImgB = uint32_t(kN) * KT * 64;        // one expanded stream tile
+  static constexpr uint32_t kPkA = uint32_t(kOwn) * KT * 8;        // packed resident rows
+  static constexpr uint32_t kPkB = uint32_t(kN) * KT * 8;          // one packed stream tile
+  static constexpr int kFit =
+      (225 * 1024 - 2048 - kHalves * int(kImgA) - int(kPkA)) / int(kImgB + kPkB);
   static constexpr int kStages = kFit > 4 ? 4 : kFit;
   static constexpr size_t kSmem =
-      1024 + kImgBytes + kPkBytes + size_t(kStages) * (kImgBytes + kPkBytes) + 512;
+      1024 + kHalves * kImgA + kPkA + size_t(kStages) * (kImgB + kPkB) + 512;
+  static constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) |
+                                     (uint32_t(kN >> 3) << 17) | (uint32_t(128 >> 4) << 24);
 };
 
 struct FusedParams {
@@ -447,16 +472,18 @@ __device__ __forceinline__ uint32_t spread_nibble(uint32_t n) {
   return ((n * 0x00204081u) & 0x01010101u) * 0x38u;
 }
 
-// Expands `count` packed rows (the rest zero) into one 128-row operand tile
-// in the swizzled K-major layout of expand_kernel.  Thread e of n handles
-// 16-byte chunks e, e + n, ...; consecutive threads write consecutive chunks.
-template <int KT>
+// Expands `count` packed rows (the rest zero) into one R-row operand tile in
+// the swizzled K-major layout of expand_kernel (atoms of R rows x 128 bytes).
+// Thread e of n handles 16-byte chunks e, e + n, ...; consecutive threads
+// write consecutive chunks.
+template <int KT, int R>
 __device__ __forceinline__ void expand_tile_smem(const uint64_t* pk, int count, bool complement,
                                                  uint8_t* dst, int e, int n) {
-  constexpr int kChunks = 128 * KT * 4;
+  constexpr int kChunks = R * KT * 4;
+  constexpr int kAtomShift = R == 128 ? 10 : 9;  // log2(R * 8)
 #pragma unroll 4
   for (int id = e; id < kChunks; id += n) {
-    const int katom = id >> 10, r = (id >> 3) & 127, pos = id & 7;
+    const int katom = id >> kAtomShift, r = (id >> 3) & (R - 1), pos = id & 7;
     const int k0 = katom * 128 + ((pos ^ (r & 7)) << 4);
     uint32_t bits = 0;
     if (r < count) {
@@ -464,7 +491,7 @@ __device__ __forceinline__ void expand_tile_smem(const uint64_t* pk, int count, 
       if (complement) w = ~w;
       bits = uint32_t(w >> (k0 & 63)) & 0xffffu;
     }
-    *reinterpret_cast<uint4*>(dst + katom * 16384 + r * 128 + pos * 16) =
+    *reinterpret_cast<uint4*>(dst + katom * (R * 128) + r * 128 + pos * 16) =
         make_uint4(spread_nibble(bits & 15u), spread_nibble((bits >> 4) & 15u),
                    spread_nibble((bits >> 8) & 15u), spread_nibble(bits >> 12));
   }
@@ -476,17 +503,19 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 
 template <int KT, int MODE>
 __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(FusedParams p) {
-  using S = FusedShape<KT>;
+  using S = FusedShape<KT, MODE>;
   constexpr int STAGES = S::kStages;
-  constexpr int PKW = 128 * KT;  // words of one packed tile
+  constexpr int kN = S::kN, kOwn = S::kOwn;
+  constexpr int PKB = kN * KT;  // words of one packed stream tile
+  constexpr int NX = kExpandThreads / 32;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* base = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
-  uint8_t* A_x = base;
-  uint8_t* B_x = A_x + S::kImgBytes;
-  uint64_t* A_pk = reinterpret_cast<uint64_t*>(B_x + size_t(STAGES) * S::kImgBytes);
-  uint64_t* B_pk = A_pk + PKW;
-  uint64_t* bars = B_pk + size_t(STAGES) * PKW;
+  uint8_t* A_x = base;                          // kHalves halves of kImgA
+  uint8_t* B_x = A_x + S::kHalves * S::kImgA;   // STAGES tiles of kImgB
+  uint64_t* A_pk = reinterpret_cast<uint64_t*>(B_x + size_t(STAGES) * S::kImgB);
+  uint64_t* B_pk = A_pk + kOwn * KT;
+  uint64_t* bars = B_pk + size_t(STAGES) * PKB;
   uint64_t* a_pk_full = bars;
   uint64_t* a_pk_empty = bars + 1;
   uint64_t* a_x_full = bars + 2;
@@ -504,13 +533,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
   const int64_t G = gridDim.x;
   if (threadIdx.x == 0) {
     mbar_init(a_pk_full, 1);
-    mbar_init(a_pk_empty, kExpandThreads / 32);
-    mbar_init(a_x_full, kExpandThreads / 32);
+    mbar_init(a_pk_empty, NX);
+    mbar_init(a_x_full, NX);
     mbar_init(a_x_empty, 1);
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(b_pk_full + s, 1);
-      mbar_init(b_pk_empty + s, kExpandThreads / 32);
-      mbar_init(b_x_full + s, kExpandThreads / 32);
+      mbar_init(b_pk_empty + s, NX);
+      mbar_init(b_x_full + s, NX);
       mbar_init(b_x_empty + s, 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -554,11 +583,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
             *abort_flag = 1;
             break;
           }
-          const int64_t left = int64_t(w.str_count) - int64_t(t) * 128;
-          const uint32_t bytes = uint32_t(left < 128 ? left : 128) * KT * 8;
+          const int64_t left = int64_t(w.str_count) - int64_t(t) * kN;
+          const uint32_t bytes = uint32_t(left < kN ? left : kN) * KT * 8;
           mbar_arrive_expect_tx(b_pk_full + s, bytes);
-          bulk_g2s(B_pk + size_t(s) * PKW, p.str_rows + (w.str_first + int64_t(t) * 128) * KT,
-                   bytes, b_pk_full + s);
+          bulk_g2s(B_pk + size_t(s) * PKB,
+                   p.str_rows + (w.str_first + int64_t(t) * kN) * KT, bytes, b_pk_full + s);
           issued_b = tt + 1;
         }
       }
@@ -571,18 +600,19 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // MMA issuer.
+      // MMA issuer: per stream tile, one MMA chain per resident half.
       int64_t tt = 0, ii = 0, last = -1;
       bool ok = true;
       const uint32_t a_base = smem_u32(A_x);
       for (int64_t it = blockIdx.x; it < p.n_items && ok; it += G, ++ii) {
-        const int b_tiles = p.items[it].b_tiles;
+        const TcItem w = p.items[it];
+        const int halves = w.own_count > 128 ? 2 : 1;
         if (!mbar_wait(a_x_full, uint32_t(ii & 1), p.status) || *abort_flag) {
           *abort_flag = 1;
           ok = false;
           break;
         }
-        for (int t = 0; t < b_tiles; ++t, ++tt) {
+        for (int t = 0; t < w.b_tiles; ++t, ++tt) {
           const int s = int(tt % STAGES), b = int(tt & 1);
           if (!mbar_wait(b_x_full + s, uint32_t((tt / STAGES) & 1), p.status) ||
               !mbar_wait(acc_empty + b, uint32_t(((tt >> 1) & 1) ^ 1), p.status) ||
@@ -592,33 +622,40 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
             break;
           }
           tc_fence_after();
-          const uint32_t b_base = smem_u32(B_x + size_t(s) * S::kImgBytes);
-          const uint32_t d = tmem + uint32_t(b * kTcN);
+          const uint32_t b_base = smem_u32(B_x + size_t(s) * S::kImgB);
+          for (int h = 0; h < halves; ++h) {
+            const uint32_t d = tmem + uint32_t(b * 128 + h * kN);
+            const uint32_t ah = a_base + uint32_t(h) * S::kImgA;
 #pragma unroll 4
-          for (int k = 0; k < KT * 2; ++k) {
-            const uint32_t off = uint32_t(k >> 2) * (128 * 128) + uint32_t(k & 3) * 32;
-            tc_mma(d, sw128_desc(a_base + off), sw128_desc(b_base + off), k > 0 ? 1u : 0u);
+            for (int k = 0; k < KT * 2; ++k) {
+              const uint32_t aoff = uint32_t(k >> 2) * (128 * 128) + uint32_t(k & 3) * 32;
+              const uint32_t boff = uint32_t(k >> 2) * (kN * 128) + uint32_t(k & 3) * 32;
+              tc_mma_desc(d, sw128_desc(ah + aoff), sw128_desc(b_base + boff), S::kIdesc,
+                          k > 0 ? 1u : 0u);
+            }
           }
           tc_commit(b_x_empty + s);
           tc_commit(acc_full + b);
           last = tt;
         }
         if (!ok) break;
-        tc_commit(a_x_empty);  // the own tile is free once this item's MMAs are done
+        tc_commit(a_x_empty);  // the resident rows are free once this item's MMAs are done
       }
       if (last >= 0) mbar_wait(acc_full + (last & 1), uint32_t((last >> 1) & 1), p.status);
     }
   } else if (warp < 6) {
-    // Epilogue: warp w reads accumulator lanes 32*(w % 4) .. +32.
+    // Epilogue: warp w reads accumulator lanes 32*(w % 4) .. +32 of both
+    // halves, i.e. resident rows quarter*32 + lane and 128 + that.
     const int quarter = warp & 3;
     const int tile_row = quarter * 32 + lane;
     int64_t tt = 0;
     bool ok = true;
     for (int64_t it = blockIdx.x; it < p.n_items && ok; it += G) {
       const TcItem w = p.items[it];
-      bool cov = false;
-      uint32_t cnt = 0;
-      unsigned long long sum = 0;
+      const int halves = w.own_count > 128 ? 2 : 1;
+      bool cov[2] = {false, false};
+      uint32_t cnt[2] = {0, 0};
+      unsigned long long sum[2] = {0, 0};
       for (int t = 0; t < w.b_tiles; ++t, ++tt) {
         const int b = int(tt & 1);
         const bool got = mbar_wait(acc_full + b, uint32_t((tt >> 1) & 1), p.status);
@@ -628,20 +665,23 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
           break;
         }
         tc_fence_after();
-        const int64_t j0 = w.str_first + int64_t(t) * 128;
-        const int64_t left = int64_t(w.str_count) - int64_t(t) * 128;
-        const int nvalid = int(left < 128 ? left : 128);
+        const int64_t j0 = w.str_first + int64_t(t) * kN;
+        const int64_t left = int64_t(w.str_count) - int64_t(t) * kN;
+        const int nvalid = int(left < kN ? left : kN);
+        for (int h = 0; h < halves; ++h) {
 #pragma unroll 1
-        for (int c = 0; c < 128; c += 32) {
-          uint32_t v[32];
-          tmem_ld32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * kTcN + c), v);
+          for (int c = 0; c < kN; c += 32) {
+            uint32_t v[32];
+            tmem_ld32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * 128 + h * kN + c),
+                      v);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const bool hit = v[i] == 0u && (c + i) < nvalid;
-            if constexpr (MODE == MODE_ANY) cov |= hit;
-            if constexpr (MODE == MODE_COUNT) cnt += hit ? 1u : 0u;
-            if constexpr (MODE == MODE_SUM) {
-              if (hit) sum += p.score[j0 + c + i];
+            for (int i = 0; i < 32; ++i) {
+              const bool hit = v[i] == 0u && (c + i) < nvalid;
+              if constexpr (MODE == MODE_ANY) cov[h] |= hit;
+              if constexpr (MODE == MODE_COUNT) cnt[h] += hit ? 1u : 0u;
+              if constexpr (MODE == MODE_SUM) {
+                if (hit) sum[h] += p.score[j0 + c + i];
+              }
             }
           }
         }
@@ -650,16 +690,18 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
         if (lane == 0) mbar_arrive(acc_empty + b);
       }
       if (!ok) break;
-      if (tile_row < w.own_count) {
-        const int64_t row = int64_t(p.own_ids[w.own_first + tile_row]);
+      for (int h = 0; h < halves; ++h) {
+        const int r = h * 128 + tile_row;
+        if (r >= w.own_count) continue;
+        const int64_t row = int64_t(p.own_ids[w.own_first + r]);
         if constexpr (MODE == MODE_ANY) {
-          if (cov) p.out_u32[row] = 1u;
+          if (cov[h]) p.out_u32[row] = 1u;
         }
         if constexpr (MODE == MODE_COUNT) {
-          if (cnt) atomicAdd(p.out_u32 + row, cnt);
+          if (cnt[h]) atomicAdd(p.out_u32 + row, cnt[h]);
         }
         if constexpr (MODE == MODE_SUM) {
-          if (sum) atomicAdd(p.out_u64 + row, sum);
+          if (sum[h]) atomicAdd(p.out_u64 + row, sum[h]);
         }
       }
     }
@@ -676,7 +718,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
         *abort_flag = 1;
         break;
       }
-      expand_tile_smem<KT>(A_pk, w.own_count, p.own_complement != 0, A_x, e, kExpandThreads);
+      expand_tile_smem<KT, 128>(A_pk, w.own_count < 128 ? w.own_count : 128,
+                                p.own_complement != 0, A_x, e, kExpandThreads);
+      if (w.own_count > 128)
+        expand_tile_smem<KT, 128>(A_pk + 128 * KT, w.own_count - 128, p.own_complement != 0,
+                                  A_x + S::kImgA, e, kExpandThreads);
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {
@@ -692,10 +738,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
           ok = false;
           break;
         }
-        const int64_t left = int64_t(w.str_count) - int64_t(t) * 128;
-        expand_tile_smem<KT>(B_pk + size_t(s) * PKW, int(left < 128 ? left : 128),
-                             p.own_complement == 0, B_x + size_t(s) * S::kImgBytes, e,
-                             kExpandThreads);
+        const int64_t left = int64_t(w.str_count) - int64_t(t) * kN;
+        expand_tile_smem<KT, kN>(B_pk + size_t(s) * PKB,
+                                      int(left < kN ? left : kN),
+                                      p.own_complement == 0, B_x + size_t(s) * S::kImgB, e,
+                                      kExpandThreads);
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) {
@@ -715,22 +762,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
   }
 }
 
-
-
-namespace {
-// Pinned staging for the work items, one per host thread;
-// reused once the copy out of it (recorded by `done`) has finished.
-struct TcStaging {
-  uint8_t* buf = nullptr;
-  size_t cap = 0;
-  cudaEvent_t done = nullptr;
-};
-thread_local TcStaging g_tc_staging;
-}  // namespace
-
 template <int KT, int MODE>
 static cudaError_t run_fused(const FusedParams& p, cudaStream_t s) {
-  using S = FusedShape<KT>;
+  using S = FusedShape<KT, MODE>;
   cudaError_t e = cudaFuncSetAttribute(subset_tc_fused_kernel<KT, MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::kSmem));
   if (e != cudaSuccess) return e;
@@ -739,6 +773,17 @@ static cudaError_t run_fused(const FusedParams& p, cudaStream_t s) {
   count_launches(1);
   return cudaGetLastError();
 }
+
+namespace {
+// Pinned staging for the work items, one per host thread; reused once the
+// copy out of it (recorded by `done`) has finished.
+struct TcStaging {
+  uint8_t* buf = nullptr;
+  size_t cap = 0;
+  cudaEvent_t done = nullptr;
+};
+thread_local TcStaging g_tc_staging;
+}  // namespace
 
 cudaError_t indexed_subset_tc(int mode, const RecordIndex& idx, const KeyedIndex& kx,
                               uint32_t* out_u32, unsigned long long* out_u64, int* status,
@@ -752,13 +797,14 @@ cudaError_t indexed_subset_tc(int mode, const RecordIndex& idx, const KeyedIndex
   const uint32_t* own_off = own_multi ? idx.h_off.data() : kx.h_off.data();
   const uint32_t* str_off = own_multi ? kx.h_off.data() : idx.h_off.data();
   std::vector<TcItem> items;
+  const int64_t own_rows = 128 * fused_halves(mode), n_rows = fused_n(mode);
   int64_t tests = 0, pair_tiles = 0;
   for (int l = 0; l < L; ++l) {
     const int64_t no = int64_t(own_off[l + 1]) - own_off[l];
     const int64_t ns = int64_t(str_off[l + 1]) - str_off[l];
     if (no == 0 || ns == 0) continue;
     tests += no * ns;
-    pair_tiles += ceil_div(no, kTcM) * ceil_div(ns, kTcN);
+    pair_tiles += ceil_div(no, own_rows) * ceil_div(ns, n_rows);
   }
   *tests_out = tests;
   if (pair_tiles == 0) return cudaSuccess;
@@ -769,15 +815,15 @@ cudaError_t indexed_subset_tc(int mode, const RecordIndex& idx, const KeyedIndex
     const int64_t no = int64_t(own_off[l + 1]) - own_off[l];
     const int64_t ns = int64_t(str_off[l + 1]) - str_off[l];
     if (no == 0 || ns == 0) continue;
-    const int64_t nb = ceil_div(ns, kTcN);
-    for (int64_t a = 0; a * kTcM < no; ++a)
+    const int64_t nb = ceil_div(ns, n_rows);
+    for (int64_t a = 0; a * own_rows < no; ++a)
       for (int64_t b = 0; b < nb; b += per) {
         TcItem it;
-        it.own_first = int64_t(own_off[l]) + a * kTcM;
-        it.str_first = int64_t(str_off[l]) + b * kTcN;
-        it.own_count = int32_t(std::min<int64_t>(kTcM, no - a * kTcM));
+        it.own_first = int64_t(own_off[l]) + a * own_rows;
+        it.str_first = int64_t(str_off[l]) + b * n_rows;
+        it.own_count = int32_t(std::min<int64_t>(own_rows, no - a * own_rows));
         it.b_tiles = int32_t(std::min<int64_t>(per, nb - b));
-        it.str_count = int32_t(std::min<int64_t>(per * kTcN, ns - b * kTcN));
+        it.str_count = int32_t(std::min<int64_t>(per * n_rows, ns - b * n_rows));
         it.pad = 0;
         items.push_back(it);
       }
