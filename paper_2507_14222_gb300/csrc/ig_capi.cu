@@ -417,6 +417,30 @@ AuxStream& aux_stream() {
 }
 }  // namespace
 
+namespace {
+// The two class streams of a fit and the three events that fork and join
+// them, one set per host thread and device, created on first use and kept
+// for the life of the process.
+struct FitStreams {
+  cudaStream_t cs[2] = {nullptr, nullptr};
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  cudaError_t error = cudaSuccess;
+};
+FitStreams& fit_streams() {
+  static thread_local FitStreams per_dev[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  FitStreams& f = per_dev[dev];
+  if (!f.cs[0] && f.error == cudaSuccess) {
+    for (int i = 0; i < 2 && f.error == cudaSuccess; ++i)
+      f.error = cudaStreamCreateWithFlags(&f.cs[i], cudaStreamNonBlocking);
+    for (int i = 0; i < 3 && f.error == cudaSuccess; ++i)
+      f.error = cudaEventCreateWithFlags(&f.ev[i], cudaEventDisableTiming);
+  }
+  return f;
+}
+}  // namespace
+
 struct ig_model {
   int K = 0, KT = 0;
   int64_t n_train[2] = {0, 0}, n_cand[2] = {0, 0}, n_pat[2] = {0, 0}, n_pairs[2] = {0, 0};
@@ -1056,12 +1080,10 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
   {
     int dev = 0;
     IG_CUDA(cudaGetDevice(&dev), "ig_fit");
-    cudaStream_t cs[2] = {nullptr, nullptr};
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-    for (int i = 0; i < 2; ++i)
-      IG_CUDA(cudaStreamCreateWithFlags(&cs[i], cudaStreamNonBlocking), "ig_fit");
-    for (int i = 0; i < 3; ++i)
-      IG_CUDA(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming), "ig_fit");
+    FitStreams& fs = fit_streams();
+    IG_CUDA(fs.error, "ig_fit: class streams");
+    cudaStream_t* cs = fs.cs;
+    cudaEvent_t* ev = fs.ev;
     IG_CUDA(cudaEventRecord(ev[2], s), "ig_fit");
     for (int i = 0; i < 2; ++i) IG_CUDA(cudaStreamWaitEvent(cs[i], ev[2], 0), "ig_fit");
     int rc[2] = {IG_OK, IG_OK};
@@ -1081,12 +1103,10 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
     for (int i = 0; i < 2; ++i) {
       cudaEventRecord(ev[i], cs[i]);
       cudaStreamWaitEvent(s, ev[i], 0);
-      cudaStreamDestroy(cs[i]);
       // What the class streams allocated for later steps is freed on s.
       rec_idx[i].s = s;
       rec_img[i].s = s;
     }
-    for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
     // Report a class's own failure before one that only saw the other fail.
     int first = -1;
     for (int i = 1; i >= 0; --i)
