@@ -412,7 +412,8 @@ cudaError_t launch_expand(const uint64_t* rows, int64_t n, int stride, int KT, b
 // subset_tc_fused_kernel: the same 0/1 GEMM on the item index's blocks, with
 // no operand images in global memory.  Packed 64*KT-bit rows are copied by
 // TMA into shared staging, and expander warps write the E4M3 bytes (swizzled
-// as the MMA reads them) straight into shared memory.  A work item holds up
+// as the MMA reads them; 0x08 = 2^-6 per set bit, which takes one multiply
+// fewer to spread than 1.0) straight into shared memory.  A work item holds up
 // to 256 resident rows of one item group, as two M = 128 halves that share
 // every expanded stream tile (64 rows, N = 64), so that the expansion --
 // integer work that sets this kernel's pace -- is spent once for two MMAs;
@@ -423,7 +424,9 @@ cudaError_t launch_expand(const uint64_t* rows, int64_t n, int stride, int KT, b
 // as the MMAs on the previous one are done.  Warp roles:
 //   warp 0    lane 0 issues the bulk copies of packed rows;
 //   warp 1    allocates tensor memory; lane 0 issues the MMAs and commits;
-//   warps 2-5 epilogue: lanes of TMEM quarter w % 4, both halves;
+//   warps 2-5 epilogue: lanes of TMEM quarter w % 4, both halves; a min
+//             over 32 columns for "any", a bit mask of the hits and a loop
+//             over its set bits for the score-weighted sum;
 //   warps 6-  expand packed tiles into operand tiles.
 // Every wait is bounded; a timeout sets the status and an abort flag that
 // every role checks.
@@ -443,11 +446,20 @@ struct FusedShape {
   static constexpr uint32_t kImgB = uint32_t(kN) * KT * 64;        // one expanded stream tile
   static constexpr uint32_t kPkA = uint32_t(kOwn) * KT * 8;        // packed resident rows
   static constexpr uint32_t kPkB = uint32_t(kN) * KT * 8;          // one packed stream tile
-  static constexpr int kFit =
-      (225 * 1024 - 2048 - kHalves * int(kImgA) - int(kPkA)) / int(kImgB + kPkB);
-  static constexpr int kStages = kFit > 4 ? 4 : kFit;
+  static constexpr size_t kScores = MODE == MODE_SUM ? size_t(4) * kN * 8 : 0;
+  // Alignment slack, barriers, scores and the resident tiles; the rest of
+  // 227 KB goes to the rings of expanded (up to 4) and packed (up to 8)
+  // stream tiles.  Packed tiles are small, so their ring runs deeper and
+  // keeps more bulk copies in flight than the expanded ring.
+  static constexpr int kFixed = 1024 + 512 + int(kScores) + kHalves * int(kImgA) + int(kPkA);
+  static constexpr int kBudget = 227 * 1024;
+  static constexpr int kXFit = (kBudget - kFixed - 2 * int(kPkB)) / int(kImgB);
+  static constexpr int kXStages = kXFit > 4 ? 4 : kXFit;
+  static constexpr int kPkFit = (kBudget - kFixed - kXStages * int(kImgB)) / int(kPkB);
+  static constexpr int kPkStages = kPkFit > 8 ? 8 : kPkFit;
+  static_assert(kXStages >= 2 && kPkStages >= 2, "shared memory too small for two stages");
   static constexpr size_t kSmem =
-      1024 + kHalves * kImgA + kPkA + size_t(kStages) * (kImgB + kPkB) + 512;
+      size_t(kFixed) + size_t(kXStages) * kImgB + size_t(kPkStages) * kPkB;
   static constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) |
                                      (uint32_t(kN >> 3) << 17) | (uint32_t(128 >> 4) << 24);
 };
@@ -465,35 +477,42 @@ struct FusedParams {
   int* status;
 };
 
-// One E4M3 byte (0x38 = 1.0, or 0) per bit of a 4-bit group: the multiply
-// places bit b of n at bit 8b (the four shifted copies of n do not overlap),
-// the mask keeps those bits, the second multiply turns each into 0x38.
+// One E4M3 byte per bit of a 4-bit group (n < 16): 0x08 (2^-6) for a set
+// bit, 0 otherwise.  The multiply places bit b of n at bit 8b + 3 (the four
+// shifted copies of n, at bits 3-6, 10-13, 17-20 and 24-27, do not overlap)
+// and the mask keeps those bits.  A product of two such bytes is 2^-12 and a
+// row's at most 512 of them add up exactly in FP32, so D == 0 still means
+// "no item in common".
 __device__ __forceinline__ uint32_t spread_nibble(uint32_t n) {
-  return ((n * 0x00204081u) & 0x01010101u) * 0x38u;
+  return (n * 0x01020408u) & 0x08080808u;
 }
 
 // Expands `count` packed rows (the rest zero) into one R-row operand tile in
-// the swizzled K-major layout of expand_kernel (atoms of R rows x 128 bytes).
-// Thread e of n handles 16-byte chunks e, e + n, ...; consecutive threads
-// write consecutive chunks.
+// the swizzled K-major layout of expand_kernel (atoms of R rows x 128 bytes;
+// chunk `pos` of row r in every atom holds the 16 items of logical chunk
+// pos ^ (r mod 8)).  Thread e of n handles the (row, chunk) pairs e, e + n,
+// ... of the R x 8 grid, in every atom: the source half-word and its shift
+// are the same for all atoms of a pair, and the atoms' items sit 128 bits
+// apart in the packed row.  Consecutive threads write consecutive chunks.
 template <int KT, int R>
 __device__ __forceinline__ void expand_tile_smem(const uint64_t* pk, int count, bool complement,
                                                  uint8_t* dst, int e, int n) {
-  constexpr int kChunks = R * KT * 4;
-  constexpr int kAtomShift = R == 128 ? 10 : 9;  // log2(R * 8)
-#pragma unroll 4
-  for (int id = e; id < kChunks; id += n) {
-    const int katom = id >> kAtomShift, r = (id >> 3) & (R - 1), pos = id & 7;
-    const int k0 = katom * 128 + ((pos ^ (r & 7)) << 4);
-    uint32_t bits = 0;
-    if (r < count) {
-      uint64_t w = pk[r * KT + (k0 >> 6)];
-      if (complement) w = ~w;
-      bits = uint32_t(w >> (k0 & 63)) & 0xffffu;
+  const uint32_t flip = complement ? 0xffffffffu : 0u;
+#pragma unroll 1
+  for (int id = e; id < R * 8; id += n) {
+    const int r = id >> 3, pos = id & 7;
+    const int sw = pos ^ (r & 7);
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(pk + r * KT) + (sw >> 1);
+    const int sh = (sw & 1) * 16;
+    uint8_t* d = dst + r * 128 + pos * 16;
+    const bool live = r < count;
+#pragma unroll
+    for (int a = 0; a < KT / 2; ++a) {
+      const uint32_t bits = live ? ((src[4 * a] ^ flip) >> sh) : 0u;
+      *reinterpret_cast<uint4*>(d + a * (R * 128)) =
+          make_uint4(spread_nibble(bits & 15u), spread_nibble((bits >> 4) & 15u),
+                     spread_nibble((bits >> 8) & 15u), spread_nibble((bits >> 12) & 15u));
     }
-    *reinterpret_cast<uint4*>(dst + katom * (R * 128) + r * 128 + pos * 16) =
-        make_uint4(spread_nibble(bits & 15u), spread_nibble((bits >> 4) & 15u),
-                   spread_nibble((bits >> 8) & 15u), spread_nibble(bits >> 12));
   }
 }
 
@@ -501,10 +520,11 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+
 template <int KT, int MODE>
 __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(FusedParams p) {
   using S = FusedShape<KT, MODE>;
-  constexpr int STAGES = S::kStages;
+  constexpr int XS = S::kXStages, PKS = S::kPkStages;
   constexpr int kN = S::kN, kOwn = S::kOwn;
   constexpr int PKB = kN * KT;  // words of one packed stream tile
   constexpr int NX = kExpandThreads / 32;
@@ -512,33 +532,38 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* base = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
   uint8_t* A_x = base;                          // kHalves halves of kImgA
-  uint8_t* B_x = A_x + S::kHalves * S::kImgA;   // STAGES tiles of kImgB
-  uint64_t* A_pk = reinterpret_cast<uint64_t*>(B_x + size_t(STAGES) * S::kImgB);
+  uint8_t* B_x = A_x + S::kHalves * S::kImgA;   // XS tiles of kImgB
+  uint64_t* A_pk = reinterpret_cast<uint64_t*>(B_x + size_t(XS) * S::kImgB);
   uint64_t* B_pk = A_pk + kOwn * KT;
-  uint64_t* bars = B_pk + size_t(STAGES) * PKB;
+  uint64_t* bars = B_pk + size_t(PKS) * PKB;
   uint64_t* a_pk_full = bars;
   uint64_t* a_pk_empty = bars + 1;
   uint64_t* a_x_full = bars + 2;
   uint64_t* a_x_empty = bars + 3;
   uint64_t* b_pk_full = bars + 4;
-  uint64_t* b_pk_empty = b_pk_full + STAGES;
-  uint64_t* b_x_full = b_pk_empty + STAGES;
-  uint64_t* b_x_empty = b_x_full + STAGES;
-  uint64_t* acc_full = b_x_empty + STAGES;
+  uint64_t* b_pk_empty = b_pk_full + PKS;
+  uint64_t* b_x_full = b_pk_empty + PKS;
+  uint64_t* b_x_empty = b_x_full + XS;
+  uint64_t* acc_full = b_x_empty + XS;
   uint64_t* acc_empty = acc_full + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t G = gridDim.x;
+  // MODE_SUM: the scores of the current stream tile, one copy per epilogue
+  // warp (after the barriers' 512 bytes).
+  unsigned long long* sc = reinterpret_cast<unsigned long long*>(bars + 64) + (warp & 3) * kN;
   if (threadIdx.x == 0) {
     mbar_init(a_pk_full, 1);
     mbar_init(a_pk_empty, NX);
     mbar_init(a_x_full, NX);
     mbar_init(a_x_empty, 1);
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < PKS; ++s) {
       mbar_init(b_pk_full + s, 1);
       mbar_init(b_pk_empty + s, NX);
+    }
+    for (int s = 0; s < XS; ++s) {
       mbar_init(b_x_full + s, NX);
       mbar_init(b_x_empty + s, 1);
     }
@@ -566,6 +591,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
       // Producer of packed tiles.
       int64_t tt = 0, ii = 0, issued_b = 0;
       bool issued_a = false;
+      auto tile_src = [&](const TcItem& w, int t) {
+        return p.str_rows + (w.str_first + int64_t(t) * kN) * KT;
+      };
+      auto tile_bytes = [&](const TcItem& w, int t) {
+        const int64_t left = int64_t(w.str_count) - int64_t(t) * kN;
+        return uint32_t(left < kN ? left : kN) * KT * 8;
+      };
       for (int64_t it = blockIdx.x; it < p.n_items && !*abort_flag; it += G, ++ii) {
         const TcItem w = p.items[it];
         if (!mbar_wait(a_pk_empty, uint32_t((ii & 1) ^ 1), p.status)) {
@@ -577,25 +609,23 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
         bulk_g2s(A_pk, p.own_rows + w.own_first * KT, abytes, a_pk_full);
         issued_a = true;
         for (int t = 0; t < w.b_tiles; ++t, ++tt) {
-          const int s = int(tt % STAGES);
-          if (!mbar_wait(b_pk_empty + s, uint32_t(((tt / STAGES) & 1) ^ 1), p.status) ||
+          const int s = int(tt % PKS);
+          if (!mbar_wait(b_pk_empty + s, uint32_t(((tt / PKS) & 1) ^ 1), p.status) ||
               *abort_flag) {
             *abort_flag = 1;
             break;
           }
-          const int64_t left = int64_t(w.str_count) - int64_t(t) * kN;
-          const uint32_t bytes = uint32_t(left < kN ? left : kN) * KT * 8;
+          const uint32_t bytes = tile_bytes(w, t);
           mbar_arrive_expect_tx(b_pk_full + s, bytes);
-          bulk_g2s(B_pk + size_t(s) * PKB,
-                   p.str_rows + (w.str_first + int64_t(t) * kN) * KT, bytes, b_pk_full + s);
+          bulk_g2s(B_pk + size_t(s) * PKB, tile_src(w, t), bytes, b_pk_full + s);
           issued_b = tt + 1;
         }
       }
       if (*abort_flag) {
         // Copies in flight must land before the CTA may finish.
         if (issued_a) mbar_wait(a_pk_full, uint32_t((ii - (ii > 0 ? 1 : 0)) & 1), p.status);
-        for (int64_t t = (issued_b > STAGES ? issued_b - STAGES : 0); t < issued_b; ++t)
-          mbar_wait(b_pk_full + (t % STAGES), uint32_t((t / STAGES) & 1), p.status);
+        for (int64_t t = (issued_b > PKS ? issued_b - PKS : 0); t < issued_b; ++t)
+          mbar_wait(b_pk_full + (t % PKS), uint32_t((t / PKS) & 1), p.status);
       }
     }
   } else if (warp == 1) {
@@ -613,8 +643,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
           break;
         }
         for (int t = 0; t < w.b_tiles; ++t, ++tt) {
-          const int s = int(tt % STAGES), b = int(tt & 1);
-          if (!mbar_wait(b_x_full + s, uint32_t((tt / STAGES) & 1), p.status) ||
+          const int s = int(tt % XS), b = int(tt & 1);
+          if (!mbar_wait(b_x_full + s, uint32_t((tt / XS) & 1), p.status) ||
               !mbar_wait(acc_empty + b, uint32_t(((tt >> 1) & 1) ^ 1), p.status) ||
               *abort_flag) {
             *abort_flag = 1;
@@ -656,8 +686,27 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
       bool cov[2] = {false, false};
       uint32_t cnt[2] = {0, 0};
       unsigned long long sum[2] = {0, 0};
+      // MODE_SUM: each tile's scores are loaded into registers one tile
+      // ahead and copied to this warp's shared slots when the tile starts.
+      unsigned long long nx[kN / 32];
+      auto load_scores = [&](int t) {
+        const int64_t j0 = w.str_first + int64_t(t) * kN;
+        const int64_t left = int64_t(w.str_count) - int64_t(t) * kN;
+#pragma unroll
+        for (int q = 0; q < kN / 32; ++q)
+          nx[q] = lane + 32 * q < left ? p.score[j0 + lane + 32 * q] : 0ull;
+      };
+      if constexpr (MODE == MODE_SUM) load_scores(0);
       for (int t = 0; t < w.b_tiles; ++t, ++tt) {
         const int b = int(tt & 1);
+        const int64_t left = int64_t(w.str_count) - int64_t(t) * kN;
+        const int nvalid = int(left < kN ? left : kN);
+        if constexpr (MODE == MODE_SUM) {
+#pragma unroll
+          for (int q = 0; q < kN / 32; ++q) sc[lane + 32 * q] = nx[q];
+          __syncwarp();
+          if (t + 1 < w.b_tiles) load_scores(t + 1);
+        }
         const bool got = mbar_wait(acc_full + b, uint32_t((tt >> 1) & 1), p.status);
         if (!__all_sync(0xffffffffu, got) || *abort_flag) {
           *abort_flag = 1;
@@ -665,22 +714,36 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
           break;
         }
         tc_fence_after();
-        const int64_t j0 = w.str_first + int64_t(t) * kN;
-        const int64_t left = int64_t(w.str_count) - int64_t(t) * kN;
-        const int nvalid = int(left < kN ? left : kN);
         for (int h = 0; h < halves; ++h) {
 #pragma unroll 1
           for (int c = 0; c < kN; c += 32) {
             uint32_t v[32];
             tmem_ld32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * 128 + h * kN + c),
                       v);
+            // Columns past the tile's rows (zero rows, D = 0) are made misses.
+            if (c + 32 > nvalid) {
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const bool hit = v[i] == 0u && (c + i) < nvalid;
-              if constexpr (MODE == MODE_ANY) cov[h] |= hit;
-              if constexpr (MODE == MODE_COUNT) cnt[h] += hit ? 1u : 0u;
-              if constexpr (MODE == MODE_SUM) {
-                if (hit) sum[h] += p.score[j0 + c + i];
+              for (int i = 0; i < 32; ++i)
+                if (c + i >= nvalid) v[i] = 1u;
+            }
+            if constexpr (MODE == MODE_ANY) {
+              uint32_t mn = v[0];
+#pragma unroll
+              for (int i = 1; i < 32; ++i) mn = min(mn, v[i]);
+              cov[h] |= mn == 0u;
+            }
+            if constexpr (MODE == MODE_COUNT) {
+#pragma unroll
+              for (int i = 0; i < 32; ++i) cnt[h] += v[i] == 0u ? 1u : 0u;
+            }
+            if constexpr (MODE == MODE_SUM) {
+              uint32_t m = 0;
+#pragma unroll
+              for (int i = 0; i < 32; ++i) m |= (v[i] == 0u ? 1u : 0u) << i;
+              while (m) {
+                const int i = __ffs(m) - 1;
+                m &= m - 1u;
+                sum[h] += sc[c + i];
               }
             }
           }
@@ -730,24 +793,23 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
         mbar_arrive(a_x_full);
       }
       for (int t = 0; t < w.b_tiles; ++t, ++tt) {
-        const int s = int(tt % STAGES);
-        const uint32_t ph = uint32_t((tt / STAGES) & 1);
-        got = mbar_wait(b_pk_full + s, ph, p.status) && mbar_wait(b_x_empty + s, ph ^ 1, p.status);
+        const int sp = int(tt % PKS), sx = int(tt % XS);
+        got = mbar_wait(b_pk_full + sp, uint32_t((tt / PKS) & 1), p.status) &&
+              mbar_wait(b_x_empty + sx, uint32_t(((tt / XS) & 1) ^ 1), p.status);
         if (!__all_sync(0xffffffffu, got) || *abort_flag) {
           *abort_flag = 1;
           ok = false;
           break;
         }
         const int64_t left = int64_t(w.str_count) - int64_t(t) * kN;
-        expand_tile_smem<KT, kN>(B_pk + size_t(s) * PKB,
-                                      int(left < kN ? left : kN),
-                                      p.own_complement == 0, B_x + size_t(s) * S::kImgB, e,
-                                      kExpandThreads);
+        expand_tile_smem<KT, kN>(B_pk + size_t(sp) * PKB, int(left < kN ? left : kN),
+                                 p.own_complement == 0, B_x + size_t(sx) * S::kImgB, e,
+                                 kExpandThreads);
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) {
-          mbar_arrive(b_pk_empty + s);
-          mbar_arrive(b_x_full + s);
+          mbar_arrive(b_pk_empty + sp);
+          mbar_arrive(b_x_full + sx);
         }
       }
     }
