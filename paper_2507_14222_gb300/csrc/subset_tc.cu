@@ -164,6 +164,37 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// This thread's lane, 32 consecutive columns from registers.  Completion is
+// awaited with tmem_wait_st.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+      "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]),
+      "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]),
+      "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// D (+)= A * B^T with A (M = 128 rows, one per lane, 4 E4M3 items per
+// column in item order) in tensor memory and B described in shared memory.
+__device__ __forceinline__ void tc_mma_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
+                                              uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // ---- the kernel -------------------------------------------------------------
 
 struct TcParams {
@@ -442,27 +473,38 @@ struct FusedShape {
   static constexpr int kHalves = fused_halves(MODE);
   static constexpr int kN = fused_n(MODE);                          // stream rows per tile
   static constexpr int kOwn = 128 * kHalves;                        // resident rows per item
-  static constexpr uint32_t kImgA = uint32_t(128) * KT * 64;       // one expanded half
   static constexpr uint32_t kImgB = uint32_t(kN) * KT * 64;        // one expanded stream tile
   static constexpr uint32_t kPkA = uint32_t(kOwn) * KT * 8;        // packed resident rows
   static constexpr uint32_t kPkB = uint32_t(kN) * KT * 8;          // one packed stream tile
   static constexpr size_t kScores = MODE == MODE_SUM ? size_t(4) * kN * 8 : 0;
-  // Alignment slack, barriers, scores and the resident tiles; the rest of
-  // 227 KB goes to the rings of expanded (up to 4) and packed (up to 8)
-  // stream tiles.  Packed tiles are small, so their ring runs deeper and
+  // Tensor memory (512 columns): two accumulator buffers of 128 columns,
+  // then the resident operand, 16*KT columns (4 items each) per half, twice
+  // where it fits, so that the next item's rows can be written while the
+  // MMAs still read the current ones.
+  static constexpr int kACols = 16 * KT;
+  static constexpr int kAccCols = 256;
+  static constexpr int kABufs = kAccCols + 2 * kHalves * kACols <= 512 ? 2 : 1;
+  // Alignment slack, barriers, scores and the packed resident rows; the
+  // rest of 227 KB goes to the rings of expanded (up to 4) and packed (up to
+  // 8) stream tiles.  Packed tiles are small, so their ring runs deeper and
   // keeps more bulk copies in flight than the expanded ring.
-  static constexpr int kFixed = 1024 + 512 + int(kScores) + kHalves * int(kImgA) + int(kPkA);
+  static constexpr int kFixed = 1024 + 512 + int(kScores) + int(kPkA);
   static constexpr int kBudget = 227 * 1024;
   static constexpr int kXFit = (kBudget - kFixed - 2 * int(kPkB)) / int(kImgB);
   static constexpr int kXStages = kXFit > 4 ? 4 : kXFit;
   static constexpr int kPkFit = (kBudget - kFixed - kXStages * int(kImgB)) / int(kPkB);
   static constexpr int kPkStages = kPkFit > 8 ? 8 : kPkFit;
   static_assert(kXStages >= 2 && kPkStages >= 2, "shared memory too small for two stages");
-  static constexpr size_t kSmem =
+  // At least 120 KB, so that no two CTAs (which each take all 512 tensor
+  // memory columns) share an SM.
+  static constexpr size_t kUsed =
       size_t(kFixed) + size_t(kXStages) * kImgB + size_t(kPkStages) * kPkB;
+  static constexpr size_t kSmem = kUsed > 120 * 1024 ? kUsed : 120 * 1024;
   static constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) |
                                      (uint32_t(kN >> 3) << 17) | (uint32_t(128 >> 4) << 24);
 };
+
+constexpr uint32_t kFusedTmemCols = 512;
 
 struct FusedParams {
   const TcItem* items;
@@ -531,16 +573,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* base = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
-  uint8_t* A_x = base;                          // kHalves halves of kImgA
-  uint8_t* B_x = A_x + S::kHalves * S::kImgA;   // XS tiles of kImgB
+  uint8_t* B_x = base;                          // XS tiles of kImgB
   uint64_t* A_pk = reinterpret_cast<uint64_t*>(B_x + size_t(XS) * S::kImgB);
   uint64_t* B_pk = A_pk + kOwn * KT;
   uint64_t* bars = B_pk + size_t(PKS) * PKB;
   uint64_t* a_pk_full = bars;
   uint64_t* a_pk_empty = bars + 1;
-  uint64_t* a_x_full = bars + 2;
-  uint64_t* a_x_empty = bars + 3;
-  uint64_t* b_pk_full = bars + 4;
+  uint64_t* a_x_full = bars + 2;   // [kABufs]
+  uint64_t* a_x_empty = bars + 4;  // [kABufs]
+  uint64_t* b_pk_full = bars + 6;
   uint64_t* b_pk_empty = b_pk_full + PKS;
   uint64_t* b_x_full = b_pk_empty + PKS;
   uint64_t* b_x_empty = b_x_full + XS;
@@ -557,8 +598,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
   if (threadIdx.x == 0) {
     mbar_init(a_pk_full, 1);
     mbar_init(a_pk_empty, NX);
-    mbar_init(a_x_full, NX);
-    mbar_init(a_x_empty, 1);
+    for (int b = 0; b < S::kABufs; ++b) {
+      mbar_init(a_x_full + b, NX);
+      mbar_init(a_x_empty + b, 1);
+    }
     for (int s = 0; s < PKS; ++s) {
       mbar_init(b_pk_full + s, 1);
       mbar_init(b_pk_empty + s, NX);
@@ -577,7 +620,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(kTmemCols)
+                 "r"(kFusedTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -630,18 +673,22 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // MMA issuer: per stream tile, one MMA chain per resident half.
+      // MMA issuer: per stream tile, one MMA chain per resident half, the
+      // resident operand read from tensor memory.
       int64_t tt = 0, ii = 0, last = -1;
       bool ok = true;
-      const uint32_t a_base = smem_u32(A_x);
       for (int64_t it = blockIdx.x; it < p.n_items && ok; it += G, ++ii) {
         const TcItem w = p.items[it];
         const int halves = w.own_count > 128 ? 2 : 1;
-        if (!mbar_wait(a_x_full, uint32_t(ii & 1), p.status) || *abort_flag) {
+        const int ab = S::kABufs == 2 ? int(ii & 1) : 0;
+        const uint32_t aph = uint32_t((S::kABufs == 2 ? (ii >> 1) : ii) & 1);
+        if (!mbar_wait(a_x_full + ab, aph, p.status) || *abort_flag) {
           *abort_flag = 1;
           ok = false;
           break;
         }
+        tc_fence_after();
+        const uint32_t a_tm = tmem + uint32_t(S::kAccCols + ab * S::kHalves * S::kACols);
         for (int t = 0; t < w.b_tiles; ++t, ++tt) {
           const int s = int(tt % XS), b = int(tt & 1);
           if (!mbar_wait(b_x_full + s, uint32_t((tt / XS) & 1), p.status) ||
@@ -655,13 +702,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
           const uint32_t b_base = smem_u32(B_x + size_t(s) * S::kImgB);
           for (int h = 0; h < halves; ++h) {
             const uint32_t d = tmem + uint32_t(b * 128 + h * kN);
-            const uint32_t ah = a_base + uint32_t(h) * S::kImgA;
+            const uint32_t ah = a_tm + uint32_t(h * S::kACols);
 #pragma unroll 4
             for (int k = 0; k < KT * 2; ++k) {
-              const uint32_t aoff = uint32_t(k >> 2) * (128 * 128) + uint32_t(k & 3) * 32;
+              // K step k: items 32k .. 32k + 31, resident columns 8k .. 8k + 7.
               const uint32_t boff = uint32_t(k >> 2) * (kN * 128) + uint32_t(k & 3) * 32;
-              tc_mma_desc(d, sw128_desc(ah + aoff), sw128_desc(b_base + boff), S::kIdesc,
-                          k > 0 ? 1u : 0u);
+              tc_mma_tmem_a(d, ah + uint32_t(8 * k), sw128_desc(b_base + boff), S::kIdesc,
+                            k > 0 ? 1u : 0u);
             }
           }
           tc_commit(b_x_empty + s);
@@ -669,7 +716,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
           last = tt;
         }
         if (!ok) break;
-        tc_commit(a_x_empty);  // the resident rows are free once this item's MMAs are done
+        tc_commit(a_x_empty + ab);  // the resident rows are free once this item's MMAs are done
       }
       if (last >= 0) mbar_wait(acc_full + (last & 1), uint32_t((last >> 1) & 1), p.status);
     }
@@ -775,22 +822,47 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
     bool ok = true;
     for (int64_t it = blockIdx.x; it < p.n_items && ok; it += G, ++ii) {
       const TcItem w = p.items[it];
+      const int ab = S::kABufs == 2 ? int(ii & 1) : 0;
+      const uint32_t aph = uint32_t((S::kABufs == 2 ? (ii >> 1) : ii) & 1);
       bool got = mbar_wait(a_pk_full, uint32_t(ii & 1), p.status) &&
-                 mbar_wait(a_x_empty, uint32_t((ii & 1) ^ 1), p.status);
+                 mbar_wait(a_x_empty + ab, aph ^ 1u, p.status);
       if (!__all_sync(0xffffffffu, got) || *abort_flag) {
         *abort_flag = 1;
         break;
       }
-      expand_tile_smem<KT, 128>(A_pk, w.own_count < 128 ? w.own_count : 128,
-                                p.own_complement != 0, A_x, e, kExpandThreads);
-      if (w.own_count > 128)
-        expand_tile_smem<KT, 128>(A_pk + 128 * KT, w.own_count - 128, p.own_complement != 0,
-                                  A_x + S::kImgA, e, kExpandThreads);
-      fence_proxy_async_smem();
+      tc_fence_after();
+      // Resident rows into tensor memory: warp w writes lanes 32*(w % 4)
+      // .. +32 (the rows of that quarter of each half), one 32-column block
+      // (128 items) at a time; the four warps of a quarter share its blocks.
+      {
+        const int quarter = warp & 3, wq = (warp - 6) >> 2;
+        constexpr int kBlocksPerHalf = KT / 2;
+        const uint32_t flip = p.own_complement ? 0xffffffffu : 0u;
+        for (int blk = wq; blk < S::kHalves * kBlocksPerHalf; blk += 4) {
+          const int h = blk / kBlocksPerHalf, cb = blk % kBlocksPerHalf;
+          const int r = h * 128 + quarter * 32 + lane;
+          uint32_t x[4] = {0u, 0u, 0u, 0u};
+          if (r < w.own_count) {
+            const uint4 q4 = *reinterpret_cast<const uint4*>(A_pk + r * KT + 2 * cb);
+            x[0] = q4.x ^ flip;
+            x[1] = q4.y ^ flip;
+            x[2] = q4.z ^ flip;
+            x[3] = q4.w ^ flip;
+          }
+          uint32_t v[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = spread_nibble((x[j >> 3] >> (4 * (j & 7))) & 15u);
+          tmem_st32(tmem + (uint32_t(quarter * 32) << 16) +
+                        uint32_t(S::kAccCols + (ab * S::kHalves + h) * S::kACols + cb * 32),
+                    v);
+        }
+        tmem_wait_st();
+      }
+      tc_fence_before();
       __syncwarp();
       if (lane == 0) {
         mbar_arrive(a_pk_empty);
-        mbar_arrive(a_x_full);
+        mbar_arrive(a_x_full + ab);
       }
       for (int t = 0; t < w.b_tiles; ++t, ++tt) {
         const int sp = int(tt % PKS), sx = int(tt % XS);
@@ -819,7 +891,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(kTmemCols)
+                 "r"(kFusedTmemCols)
                  : "memory");
   }
 }
