@@ -462,8 +462,7 @@ cudaError_t launch_expand(const uint64_t* rows, int64_t n, int stride, int KT, b
 // Every wait is bounded; a timeout sets the status and an abort flag that
 // every role checks.
 
-constexpr int kExpandThreads = 512;
-constexpr int kFusedThreads = 192 + kExpandThreads;
+constexpr int kFusedThreads = 704;  // 22 warps
 // Resident halves and stream-tile rows per work item, by mode.
 constexpr int fused_halves(int mode) { return mode == MODE_SUM ? 2 : 1; }
 constexpr int fused_n(int mode) { return mode == MODE_SUM ? 64 : 128; }
@@ -471,12 +470,17 @@ constexpr int fused_n(int mode) { return mode == MODE_SUM ? 64 : 128; }
 template <int KT, int MODE>
 struct FusedShape {
   static constexpr int kHalves = fused_halves(MODE);
+  // Epilogue warps (4 per resident half: one per 32-lane quarter of tensor
+  // memory) and expander warps (the rest of the 22 after the producer and
+  // the MMA issuer).
+  static constexpr int kEpiWarps = 4 * kHalves;
+  static constexpr int kExpWarps = kFusedThreads / 32 - 2 - kEpiWarps;
   static constexpr int kN = fused_n(MODE);                          // stream rows per tile
   static constexpr int kOwn = 128 * kHalves;                        // resident rows per item
   static constexpr uint32_t kImgB = uint32_t(kN) * KT * 64;        // one expanded stream tile
   static constexpr uint32_t kPkA = uint32_t(kOwn) * KT * 8;        // packed resident rows
   static constexpr uint32_t kPkB = uint32_t(kN) * KT * 8;          // one packed stream tile
-  static constexpr size_t kScores = MODE == MODE_SUM ? size_t(4) * kN * 8 : 0;
+  static constexpr size_t kScores = MODE == MODE_SUM ? size_t(kEpiWarps) * kN * 8 : 0;
   // Tensor memory (512 columns): two accumulator buffers of 128 columns,
   // then the resident operand, 16*KT columns (4 items each) per half, twice
   // where it fits, so that the next item's rows can be written while the
@@ -569,7 +573,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
   constexpr int XS = S::kXStages, PKS = S::kPkStages;
   constexpr int kN = S::kN, kOwn = S::kOwn;
   constexpr int PKB = kN * KT;  // words of one packed stream tile
-  constexpr int NX = kExpandThreads / 32;
+  constexpr int NX = S::kExpWarps, NE = S::kEpiWarps;
+  constexpr int kFirstExp = 2 + NE;  // first expander warp
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* base = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
@@ -594,7 +599,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
   const int64_t G = gridDim.x;
   // MODE_SUM: the scores of the current stream tile, one copy per epilogue
   // warp (after the barriers' 512 bytes).
-  unsigned long long* sc = reinterpret_cast<unsigned long long*>(bars + 64) + (warp & 3) * kN;
+  unsigned long long* sc =
+      reinterpret_cast<unsigned long long*>(bars + 64) + (warp >= 2 ? warp - 2 : 0) % NE * kN;
   if (threadIdx.x == 0) {
     mbar_init(a_pk_full, 1);
     mbar_init(a_pk_empty, NX);
@@ -612,7 +618,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(acc_full + b, 1);
-      mbar_init(acc_empty + b, 4);
+      mbar_init(acc_empty + b, NE);
     }
     *abort_flag = 0;
     fence_mbar_init();
@@ -720,11 +726,14 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
       }
       if (last >= 0) mbar_wait(acc_full + (last & 1), uint32_t((last >> 1) & 1), p.status);
     }
-  } else if (warp < 6) {
-    // Epilogue: warp w reads accumulator lanes 32*(w % 4) .. +32 of both
-    // halves, i.e. resident rows quarter*32 + lane and 128 + that.
+  } else if (warp < kFirstExp) {
+    // Epilogue: warp w reads accumulator lanes 32*(w % 4) .. +32, i.e.
+    // resident rows quarter*32 + lane of its half (h0 = (w - 2) / 4 when
+    // there is one group of four warps per half, else of both halves).
     const int quarter = warp & 3;
     const int tile_row = quarter * 32 + lane;
+    const int h0 = NE == 4 ? 0 : (warp - 2) >> 2;
+    const int hstep = NE == 4 ? 1 : 2;
     int64_t tt = 0;
     bool ok = true;
     for (int64_t it = blockIdx.x; it < p.n_items && ok; it += G) {
@@ -761,7 +770,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
           break;
         }
         tc_fence_after();
-        for (int h = 0; h < halves; ++h) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (h >= halves || (hstep == 2 && h != h0)) continue;
 #pragma unroll 1
           for (int c = 0; c < kN; c += 32) {
             uint32_t v[32];
@@ -800,7 +811,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
         if (lane == 0) mbar_arrive(acc_empty + b);
       }
       if (!ok) break;
-      for (int h = 0; h < halves; ++h) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (h >= halves || (hstep == 2 && h != h0)) continue;
         const int r = h * 128 + tile_row;
         if (r >= w.own_count) continue;
         const int64_t row = int64_t(p.own_ids[w.own_first + r]);
@@ -817,7 +830,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
     }
   } else {
     // Expanders.
-    const int e = threadIdx.x - 6 * 32;
+    const int e = threadIdx.x - kFirstExp * 32;
     int64_t tt = 0, ii = 0;
     bool ok = true;
     for (int64_t it = blockIdx.x; it < p.n_items && ok; it += G, ++ii) {
@@ -835,10 +848,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
       // .. +32 (the rows of that quarter of each half), one 32-column block
       // (128 items) at a time; the four warps of a quarter share its blocks.
       {
-        const int quarter = warp & 3, wq = (warp - 6) >> 2;
+        const int quarter = warp & 3, wq = (warp - kFirstExp) >> 2;
         constexpr int kBlocksPerHalf = KT / 2;
         const uint32_t flip = p.own_complement ? 0xffffffffu : 0u;
-        for (int blk = wq; blk < S::kHalves * kBlocksPerHalf; blk += 4) {
+        for (int blk = wq; blk < S::kHalves * kBlocksPerHalf; blk += NX / 4) {
           const int h = blk / kBlocksPerHalf, cb = blk % kBlocksPerHalf;
           const int r = h * 128 + quarter * 32 + lane;
           uint32_t x[4] = {0u, 0u, 0u, 0u};
@@ -876,7 +889,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
         const int64_t left = int64_t(w.str_count) - int64_t(t) * kN;
         expand_tile_smem<KT, kN>(B_pk + size_t(sp) * PKB, int(left < kN ? left : kN),
                                  p.own_complement == 0, B_x + size_t(sx) * S::kImgB, e,
-                                 kExpandThreads);
+                                 NX * 32);
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) {
