@@ -264,6 +264,11 @@ const char* ig_last_error(void);
  * reset.  Stage names are given by ig_prof_stage_name. */
 #define IG_PROF_STAGES 20
 int ig_prof_enable(int32_t on);
+/* Times only the stages s with bit s of stage_mask set (all stages until
+ * the first call); the others launch without events.  Executed-test counts
+ * (ig_prof_read_work) are kept for every stage while enabled.  Lets a
+ * caller time one stage without the cost of events around all the others. */
+int ig_prof_select(uint32_t stage_mask);
 int ig_prof_reset(void);
 int ig_prof_read(double* ms, int64_t* launches);
 const char* ig_prof_stage_name(int32_t stage);

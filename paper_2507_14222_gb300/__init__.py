@@ -80,6 +80,7 @@ SIGNATURES = {
     "ig_model_free": (None, [_P]),
     "ig_last_error": (ctypes.c_char_p, []),
     "ig_prof_enable": (ctypes.c_int, [_I32]),
+    "ig_prof_select": (ctypes.c_int, [ctypes.c_uint32]),
     "ig_prof_reset": (ctypes.c_int, []),
     "ig_prof_read": (ctypes.c_int, [_P, _P]),
     "ig_prof_stage_name": (ctypes.c_char_p, [_I32]),
@@ -453,6 +454,19 @@ def ig_model_load(path: str) -> Model:
 
 def prof_enable(on: bool = True):
     _check(load().ig_prof_enable(1 if on else 0))
+
+
+def prof_select(stages=None):
+    """Time only the named stages (all when None) while profiling is on."""
+    if stages is None:
+        mask = 0xFFFFFFFF
+    else:
+        lib = load()
+        names = {lib.ig_prof_stage_name(i).decode(): i for i in range(PROF_STAGES)}
+        mask = 0
+        for name in stages:
+            mask |= 1 << names[name]
+    _check(load().ig_prof_select(mask))
 
 
 def prof_reset():

@@ -75,6 +75,7 @@ enum Stage {
 struct Prof {
   std::mutex mu;
   bool on = false;
+  uint32_t mask = 0xffffffffu;  // stages whose launches are timed while on
   double ms[IG_PROF_STAGES] = {};
   int64_t launches[IG_PROF_STAGES] = {};
   int64_t work[IG_PROF_STAGES] = {};
@@ -357,7 +358,8 @@ std::atomic<long long> g_launches{0};
 
 void* igk::prof_begin(int stage, cudaStream_t s) {
   std::lock_guard<std::mutex> lk(g_prof.mu);
-  if (!g_prof.on) return nullptr;
+  if (!g_prof.on || stage < 0 || stage >= IG_PROF_STAGES || !((g_prof.mask >> stage) & 1u))
+    return nullptr;
   ProfToken* t = new ProfToken{stage, s, prof_event()};
   cudaEventRecord(t->a, s);
   return t;
@@ -1639,6 +1641,12 @@ void ig_model_free(ig_model* m) {
 int ig_prof_enable(int32_t on) {
   std::lock_guard<std::mutex> lk(g_prof.mu);
   g_prof.on = on != 0;
+  return IG_OK;
+}
+
+int ig_prof_select(uint32_t stage_mask) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  g_prof.mask = stage_mask;
   return IG_OK;
 }
 

@@ -62,3 +62,24 @@ def test_reset_clears_the_timeline(workload):
     ig.prof_reset()
     assert ig.prof_timeline() == []
     assert all(n == 0 for _, n, _ in ig.prof_read().values())
+
+
+def test_select_times_only_the_chosen_stage(workload):
+    rows, labels, test = workload
+    ig.prof_select(["pair_insert"])
+    try:
+        ig.prof_reset()
+        ig.prof_enable(True)
+        model = ig.ig_fit(rows, labels)
+        ig.ig_score(model, test)
+        torch.cuda.synchronize()
+        ig.prof_enable(False)
+        totals = ig.prof_read()
+        model.free()
+    finally:
+        ig.prof_select(None)
+    timed = {name for name, (_ms, n, _w) in totals.items() if n}
+    assert timed == {"pair_insert"}
+    assert totals["pair_insert"][1] == 2  # one launch per class
+    # Executed-test counts are kept for unselected stages too.
+    assert any(w > 0 for name, (_ms, _n, w) in totals.items() if name != "pair_insert")
