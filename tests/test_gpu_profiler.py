@@ -80,6 +80,6 @@ def test_select_times_only_the_chosen_stage(workload):
         ig.prof_select(None)
     timed = {name for name, (_ms, n, _w) in totals.items() if n}
     assert timed == {"pair_insert"}
-    assert totals["pair_insert"][1] == 2  # one launch per class
+    assert totals["pair_insert"][1] >= 2  # at least one launch per class
     # Executed-test counts are kept for unselected stages too.
     assert any(w > 0 for name, (_ms, _n, w) in totals.items() if name != "pair_insert")
