@@ -486,8 +486,10 @@ struct FusedShape {
   // where it fits, so that the next item's rows can be written while the
   // MMAs still read the current ones.
   static constexpr int kACols = 16 * KT;
-  static constexpr int kAccCols = 256;
+  static constexpr int kAccBufs = 2;                // accumulator buffers of 128 columns
+  static constexpr int kAccCols = 128 * kAccBufs;
   static constexpr int kABufs = kAccCols + 2 * kHalves * kACols <= 512 ? 2 : 1;
+  static_assert(kAccCols + kABufs * kHalves * kACols <= 512, "tensor memory overflow");
   // Alignment slack, barriers, scores and the packed resident rows; the
   // rest of 227 KB goes to the rings of expanded (up to 4) and packed (up to
   // 8) stream tiles.  Packed tiles are small, so their ring runs deeper and
@@ -591,8 +593,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
   uint64_t* b_x_full = b_pk_empty + PKS;
   uint64_t* b_x_empty = b_x_full + XS;
   uint64_t* acc_full = b_x_empty + XS;
-  uint64_t* acc_empty = acc_full + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  uint64_t* acc_empty = acc_full + S::kAccBufs;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + S::kAccBufs);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -616,7 +618,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
       mbar_init(b_x_full + s, NX);
       mbar_init(b_x_empty + s, 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < S::kAccBufs; ++b) {
       mbar_init(acc_full + b, 1);
       mbar_init(acc_empty + b, NE);
     }
@@ -696,24 +698,26 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
         tc_fence_after();
         const uint32_t a_tm = tmem + uint32_t(S::kAccCols + ab * S::kHalves * S::kACols);
         for (int t = 0; t < w.b_tiles; ++t, ++tt) {
-          const int s = int(tt % XS), b = int(tt & 1);
+          const int s = int(tt % XS), b = int(tt % S::kAccBufs);
           if (!mbar_wait(b_x_full + s, uint32_t((tt / XS) & 1), p.status) ||
-              !mbar_wait(acc_empty + b, uint32_t(((tt >> 1) & 1) ^ 1), p.status) ||
+              !mbar_wait(acc_empty + b, uint32_t(((tt / S::kAccBufs) & 1) ^ 1), p.status) ||
               *abort_flag) {
             *abort_flag = 1;
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t b_base = smem_u32(B_x + size_t(s) * S::kImgB);
+          // The descriptor's start address field is the byte address / 16, so
+          // a K step's offset is added to it directly.
+          const uint64_t bdesc = sw128_desc(smem_u32(B_x + size_t(s) * S::kImgB));
           for (int h = 0; h < halves; ++h) {
             const uint32_t d = tmem + uint32_t(b * 128 + h * kN);
             const uint32_t ah = a_tm + uint32_t(h * S::kACols);
-#pragma unroll 4
+#pragma unroll
             for (int k = 0; k < KT * 2; ++k) {
               // K step k: items 32k .. 32k + 31, resident columns 8k .. 8k + 7.
               const uint32_t boff = uint32_t(k >> 2) * (kN * 128) + uint32_t(k & 3) * 32;
-              tc_mma_tmem_a(d, ah + uint32_t(8 * k), sw128_desc(b_base + boff), S::kIdesc,
+              tc_mma_tmem_a(d, ah + uint32_t(8 * k), bdesc + uint64_t(boff >> 4), S::kIdesc,
                             k > 0 ? 1u : 0u);
             }
           }
@@ -724,7 +728,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
         if (!ok) break;
         tc_commit(a_x_empty + ab);  // the resident rows are free once this item's MMAs are done
       }
-      if (last >= 0) mbar_wait(acc_full + (last & 1), uint32_t((last >> 1) & 1), p.status);
+      if (last >= 0)
+        mbar_wait(acc_full + (last % S::kAccBufs), uint32_t((last / S::kAccBufs) & 1), p.status);
     }
   } else if (warp < kFirstExp) {
     // Epilogue: warp w reads accumulator lanes 32*(w % 4) .. +32, i.e.
@@ -754,7 +759,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
       };
       if constexpr (MODE == MODE_SUM) load_scores(0);
       for (int t = 0; t < w.b_tiles; ++t, ++tt) {
-        const int b = int(tt & 1);
+        const int b = int(tt % S::kAccBufs);
         const int64_t left = int64_t(w.str_count) - int64_t(t) * kN;
         const int nvalid = int(left < kN ? left : kN);
         if constexpr (MODE == MODE_SUM) {
@@ -763,13 +768,18 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
           __syncwarp();
           if (t + 1 < w.b_tiles) load_scores(t + 1);
         }
-        const bool got = mbar_wait(acc_full + b, uint32_t((tt >> 1) & 1), p.status);
+        const bool got = mbar_wait(acc_full + b, uint32_t((tt / S::kAccBufs) & 1), p.status);
         if (!__all_sync(0xffffffffu, got) || *abort_flag) {
           *abort_flag = 1;
           ok = false;
           break;
         }
         tc_fence_after();
+        // The accumulator buffer is handed back to the MMA issuer as soon as
+        // this warp's last load from it has completed, before that chunk is
+        // reduced.
+        const int h_last = hstep == 2 ? h0 : halves - 1;
+        bool released = false;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           if (h >= halves || (hstep == 2 && h != h0)) continue;
@@ -778,6 +788,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
             uint32_t v[32];
             tmem_ld32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * 128 + h * kN + c),
                       v);
+            if (h == h_last && c + 32 >= kN) {
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(acc_empty + b);
+              released = true;
+            }
             // Columns past the tile's rows (zero rows, D = 0) are made misses.
             if (c + 32 > nvalid) {
 #pragma unroll
@@ -806,9 +822,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
             }
           }
         }
-        tc_fence_before();
+        if (!released) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acc_empty + b);
+        }
         __syncwarp();
-        if (lane == 0) mbar_arrive(acc_empty + b);
       }
       if (!ok) break;
 #pragma unroll
