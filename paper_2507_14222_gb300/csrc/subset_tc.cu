@@ -164,6 +164,36 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Two loads of 32 columns each, then one wait for both.
+__device__ __forceinline__ void tmem_ld32x2(uint32_t taddr0, uint32_t taddr1,
+                                            uint32_t (&v)[32], uint32_t (&u)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+        "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+        "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+        "=r"(v[31])
+      : "r"(taddr0)
+      : "memory");
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]),
+        "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]),
+        "=r"(u[13]), "=r"(u[14]), "=r"(u[15]), "=r"(u[16]), "=r"(u[17]), "=r"(u[18]),
+        "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]), "=r"(u[24]),
+        "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]),
+        "=r"(u[31])
+      : "r"(taddr1)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // This thread's lane, 32 consecutive columns from registers.  Completion is
 // awaited with tmem_wait_st.
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
@@ -780,44 +810,87 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
         // reduced.
         const int h_last = hstep == 2 ? h0 : halves - 1;
         bool released = false;
+        if constexpr (MODE == MODE_SUM && kN == 64 && NE == 8) {
+          // This warp's half is two 32-column chunks: both are loaded, the
+          // buffer is handed back, then the hits of each are summed.
+          if (h0 < halves) {
+            uint32_t v[32], u[32];
+            const uint32_t ta =
+                tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * 128 + h0 * kN);
+            tmem_ld32x2(ta, ta + 32u, v, u);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty + b);
+            released = true;
+            uint32_t m0 = 0, m1 = 0;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (h >= halves || (hstep == 2 && h != h0)) continue;
+            for (int i = 0; i < 32; ++i) {
+              m0 |= (v[i] == 0u ? 1u : 0u) << i;
+              m1 |= (u[i] == 0u ? 1u : 0u) << i;
+            }
+            // Columns past the tile's rows (zero rows, D = 0) are not hits.
+            if (nvalid < 64) {
+              m0 &= nvalid >= 32 ? 0xffffffffu : (1u << nvalid) - 1u;
+              m1 &= nvalid <= 32 ? 0u : (1u << (nvalid - 32)) - 1u;
+            }
+            unsigned long long acc = 0;
+            while (m0) {
+              const int i = __ffs(m0) - 1;
+              m0 &= m0 - 1u;
+              acc += sc[i];
+            }
+            while (m1) {
+              const int i = __ffs(m1) - 1;
+              m1 &= m1 - 1u;
+              acc += sc[32 + i];
+            }
+            if (h0 == 0)
+              sum[0] += acc;
+            else
+              sum[1] += acc;
+          }
+        } else {
+          // 32 columns at a time; the buffer is handed back after this
+          // warp's last load from it, before that chunk is reduced.
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (h >= halves || (hstep == 2 && h != h0)) continue;
 #pragma unroll 1
-          for (int c = 0; c < kN; c += 32) {
-            uint32_t v[32];
-            tmem_ld32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * 128 + h * kN + c),
-                      v);
-            if (h == h_last && c + 32 >= kN) {
-              tc_fence_before();
-              __syncwarp();
-              if (lane == 0) mbar_arrive(acc_empty + b);
-              released = true;
-            }
-            // Columns past the tile's rows (zero rows, D = 0) are made misses.
-            if (c + 32 > nvalid) {
+            for (int c = 0; c < kN; c += 32) {
+              uint32_t v[32];
+              tmem_ld32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * 128 + h * kN + c),
+                        v);
+              if (h == h_last && c + 32 >= kN) {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acc_empty + b);
+                released = true;
+              }
+              // Columns past the tile's rows (zero rows, D = 0) are made misses.
+              if (c + 32 > nvalid) {
 #pragma unroll
-              for (int i = 0; i < 32; ++i)
-                if (c + i >= nvalid) v[i] = 1u;
-            }
-            if constexpr (MODE == MODE_ANY) {
-              uint32_t mn = v[0];
+                for (int i = 0; i < 32; ++i)
+                  if (c + i >= nvalid) v[i] = 1u;
+              }
+              if constexpr (MODE == MODE_ANY) {
+                uint32_t mn = v[0];
 #pragma unroll
-              for (int i = 1; i < 32; ++i) mn = min(mn, v[i]);
-              cov[h] |= mn == 0u;
-            }
-            if constexpr (MODE == MODE_COUNT) {
+                for (int i = 1; i < 32; ++i) mn = min(mn, v[i]);
+                cov[h] |= mn == 0u;
+              }
+              if constexpr (MODE == MODE_COUNT) {
 #pragma unroll
-              for (int i = 0; i < 32; ++i) cnt[h] += v[i] == 0u ? 1u : 0u;
-            }
-            if constexpr (MODE == MODE_SUM) {
-              uint32_t m = 0;
+                for (int i = 0; i < 32; ++i) cnt[h] += v[i] == 0u ? 1u : 0u;
+              }
+              if constexpr (MODE == MODE_SUM) {
+                uint32_t m = 0;
 #pragma unroll
-              for (int i = 0; i < 32; ++i) m |= (v[i] == 0u ? 1u : 0u) << i;
-              while (m) {
-                const int i = __ffs(m) - 1;
-                m &= m - 1u;
-                sum[h] += sc[c + i];
+                for (int i = 0; i < 32; ++i) m |= (v[i] == 0u ? 1u : 0u) << i;
+                while (m) {
+                  const int i = __ffs(m) - 1;
+                  m &= m - 1u;
+                  sum[h] += sc[c + i];
+                }
               }
             }
           }
