@@ -572,14 +572,17 @@ def dram_traffic(kernel, workload):
     except (OSError, ValueError):
         return None
     rec = table.get(kernel)
-    if not rec or rec.get("workload") != workload:
+    if not rec:
+        return None
+    per = (rec.get("by_workload") or {}).get(workload)
+    if per is None:
         return None
     src = os.path.join(ROOT, rec["source"])
     try:
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     except OSError:
         return None
-    return rec["bytes_per_launch"] if digest == rec["source_sha256_16"] else None
+    return per["bytes_per_launch"] if digest == rec["source_sha256_16"] else None
 
 
 def dominant_stage(stages):
