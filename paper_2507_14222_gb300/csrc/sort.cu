@@ -8,14 +8,15 @@
 //     items) and is represented by (prefix, index) while it is sorted, so the
 //     passes move 20 bytes per key and their searches run over arrays that
 //     fit in L2; full keys are read only when two prefixes tie;
-//  2. each block sorts a tile of 2,048 elements in shared memory with a
-//     bitonic network;
-//  3. merge passes double the sorted run length: every element finds its
+//  2. each block sorts a tile of 1,024 elements in shared memory with a
+//     bitonic network (one compare-exchange per thread and stage; two
+//     blocks fit an SM);
+//  3. merge passes quadruple the sorted run length: every element finds its
 //     output slot directly as (its index in its own run) + (number of
-//     partner-run elements before it), the latter by binary search --
-//     right-run elements count equal left-run elements as before them -- so
-//     the slots form a permutation without merge-path partitioning, also
-//     when keys repeat;
+//     elements of the three other runs of its group before it), by binary
+//     searches -- equal keys of lower runs count as before it -- so the
+//     slots form a permutation without merge-path partitioning, also when
+//     keys repeat;
 //  4. the keys are gathered in the final order.
 #include "common.cuh"
 #include "internal.h"
@@ -23,7 +24,7 @@
 namespace igk {
 
 constexpr int kSortBlockThreads = 512;
-constexpr int kSortTile = 2048;  // elements per block-sorted tile
+constexpr int kSortTile = 1024;  // elements per block-sorted tile (one pair per thread)
 
 template <int KT>
 __device__ __forceinline__ bool key_less(const uint64_t* a, const uint64_t* b) {
@@ -161,39 +162,54 @@ __global__ void __launch_bounds__(kSortBlockThreads)
   }
 }
 
-// Merge pass: element e of run r goes to (its index in its run) + (number
-// of partner-run elements before it); left-run elements go before equal
-// right-run elements, so the slots form a permutation even when keys repeat.
+// Merge pass over groups of four runs: element e of run q of its group
+// goes to (its index in its run) + (the number of elements of each other
+// run of the group that come before it).  Equal keys order by run (those of
+// lower runs first), so the slots form a permutation even when keys repeat.
+// The three binary searches advance in lockstep, so their loads overlap.
 template <int KT>
-__global__ void merge_pass_kernel(const uint64_t* __restrict__ keys, SortArrays in,
-                                  SortArrays out, int64_t n, int64_t run) {
+__global__ void merge4_pass_kernel(const uint64_t* __restrict__ keys, SortArrays in,
+                                   SortArrays out, int64_t n, int64_t run) {
   const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= n) return;
   const int64_t r = e / run;
   const int64_t own_lo = r * run;
-  const int64_t pair_lo = (r & ~int64_t(1)) * run;
-  const int64_t o_lo = (r ^ 1) * run;
-  const int64_t o_hi = o_lo + run < n ? o_lo + run : n;
+  const int64_t grp_lo = (r & ~int64_t(3)) * run;
+  const int q = int(r & 3);
   const uint64_t k0 = in.p0[e], k1 = in.p1[e];
   const uint32_t ki = in.idx[e];
-  const bool left = (r & 1) == 0;
-  int64_t below = 0;
-  if (o_lo < n) {
-    int64_t lo = o_lo, hi = o_hi;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi) >> 1;
-      const uint64_t m0 = in.p0[mid], m1 = in.p1[mid];
-      const uint32_t mi = in.idx[mid];
-      const bool before = left ? elem_less<KT>(keys, m0, m1, mi, k0, k1, ki)
-                               : !elem_less<KT>(keys, k0, k1, ki, m0, m1, mi);
-      if (before)
-        lo = mid + 1;
-      else
-        hi = mid;
-    }
-    below = lo - o_lo;
+  int64_t lo[3], hi[3], base[3];
+  bool before_eq[3];  // partner run lower than q: its equal keys come first
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const int qq = s < q ? s : s + 1;
+    const int64_t a = grp_lo + int64_t(qq) * run;
+    base[s] = a < n ? a : n;
+    lo[s] = base[s];
+    hi[s] = a + run < n ? a + run : n;
+    before_eq[s] = qq < q;
   }
-  const int64_t pos = pair_lo + (e - own_lo) + below;
+  bool more = true;
+  while (more) {
+    more = false;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      if (lo[s] < hi[s]) {
+        const int64_t mid = (lo[s] + hi[s]) >> 1;
+        const uint64_t m0 = in.p0[mid], m1 = in.p1[mid];
+        const uint32_t mi = in.idx[mid];
+        const bool before = before_eq[s] ? !elem_less<KT>(keys, k0, k1, ki, m0, m1, mi)
+                                         : elem_less<KT>(keys, m0, m1, mi, k0, k1, ki);
+        if (before)
+          lo[s] = mid + 1;
+        else
+          hi[s] = mid;
+        more |= lo[s] < hi[s];
+      }
+    }
+  }
+  const int64_t pos = grp_lo + (e - own_lo) + (lo[0] - base[0]) + (lo[1] - base[1]) +
+                      (lo[2] - base[2]);
   out.p0[pos] = k0;
   out.p1[pos] = k1;
   out.idx[pos] = ki;
@@ -236,8 +252,8 @@ static cudaError_t sort_t(const uint64_t* keys, int64_t n, uint64_t* keys_out, c
       keys, n, A, B);
   count_launches(1);
   SortArrays cur = B, other = A;
-  for (int64_t run = kSortTile; run < n; run *= 2) {
-    merge_pass_kernel<KT><<<g, 256, 0, s>>>(keys, cur, other, n, run);
+  for (int64_t run = kSortTile; run < n; run *= 4) {
+    merge4_pass_kernel<KT><<<g, 256, 0, s>>>(keys, cur, other, n, run);
     count_launches(1);
     const SortArrays t = cur;
     cur = other;
