@@ -208,10 +208,12 @@ __global__ void rehash_kernel(const uint64_t* __restrict__ X, const uint64_t* __
 // them through a shared-memory cursor -- one global atomic per block rather
 // than per warp, all on one address.  (The order of the output does not
 // matter: it is sorted into canonical order later.)
+constexpr int kCompactThreads = 256;
 template <int KT>
-__global__ void compact_kernel(const uint64_t* __restrict__ X, const uint64_t* __restrict__ slots,
-                               uint64_t cap, uint64_t* __restrict__ out, int64_t out_rows,
-                               unsigned long long* out_count, int* status) {
+__global__ void __launch_bounds__(kCompactThreads)
+    compact_kernel(const uint64_t* __restrict__ X, const uint64_t* __restrict__ slots,
+                   uint64_t cap, uint64_t* __restrict__ out, int64_t out_rows,
+                   unsigned long long* out_count, int* status) {
   __shared__ unsigned int blk_count, blk_cursor;
   __shared__ unsigned long long blk_base;
   const int lane = threadIdx.x & 31;
@@ -231,6 +233,12 @@ __global__ void compact_kernel(const uint64_t* __restrict__ X, const uint64_t* _
   __syncthreads();
   if (threadIdx.x == 0) blk_base = blk_count ? atomicAdd(out_count, (unsigned long long)blk_count) : 0ull;
   __syncthreads();
+  // The stored pairs of each 32-slot step are expanded by the whole warp,
+  // 32 / KT keys per instruction with consecutive lanes on consecutive words.
+  __shared__ uint64_t kept_v[kCompactThreads];
+  uint64_t* my_kept = kept_v + (threadIdx.x & ~31);
+  constexpr int kRowsPer = 32 / KT;
+  const int sub = lane / KT, word = lane % KT;
   for (int64_t base = lo + (threadIdx.x & ~31); base < hi; base += blockDim.x) {
     const int64_t s = base + lane;
     const uint64_t v = s < hi ? slots[s] : 0ull;
@@ -239,25 +247,20 @@ __global__ void compact_kernel(const uint64_t* __restrict__ X, const uint64_t* _
     unsigned int p0 = 0;
     if (lane == 0) p0 = atomicAdd(&blk_cursor, unsigned(__popc(m)));
     p0 = __shfl_sync(0xffffffffu, p0, 0);
-    if (v == 0ull) continue;
-    const uint64_t pos = blk_base + p0 + unsigned(__popc(m & ((1u << lane) - 1u)));
-    if (pos >= uint64_t(out_rows)) {
-      set_status(status, ST_COUNT);
-      continue;
-    }
-    const uint64_t* a = X + ((v >> kIdxBits) & kIdxMask) * KT;
-    const uint64_t* b = X + (v & kIdxMask) * KT;
-    if constexpr (KT >= 2) {
-#pragma unroll
-      for (int k = 0; k < KT; k += 2) {
-        const ulonglong2 va = __ldg(reinterpret_cast<const ulonglong2*>(a + k));
-        const ulonglong2 vb = __ldg(reinterpret_cast<const ulonglong2*>(b + k));
-        *reinterpret_cast<ulonglong2*>(out + pos * KT + k) =
-            make_ulonglong2(va.x & vb.x, va.y & vb.y);
+    if (v != 0ull) my_kept[__popc(m & ((1u << lane) - 1u))] = v;
+    __syncwarp();
+    const int nk = __popc(m);
+    for (int b = sub; b < nk; b += kRowsPer) {
+      const uint64_t pos = blk_base + p0 + unsigned(b);
+      if (pos >= uint64_t(out_rows)) {
+        set_status(status, ST_COUNT);
+        continue;
       }
-    } else {
-      out[pos] = __ldg(a) & __ldg(b);
+      const uint64_t kv = my_kept[b];
+      out[pos * KT + word] = __ldg(X + ((kv >> kIdxBits) & kIdxMask) * KT + word) &
+                             __ldg(X + (kv & kIdxMask) * KT + word);
     }
+    __syncwarp();
   }
 }
 
@@ -287,7 +290,7 @@ cudaError_t launch_compact(const uint64_t* X, const uint64_t* slots, uint64_t ca
   int64_t blocks = ceil_div(int64_t(cap), 4096);
   if (blocks > int64_t(num_sms()) * 16) blocks = int64_t(num_sms()) * 16;
   if (blocks < 1) blocks = 1;
-  IG_DISPATCH_KT(KT, (compact_kernel<KTC><<<unsigned(blocks), 256, 0, s>>>(
+  IG_DISPATCH_KT(KT, (compact_kernel<KTC><<<unsigned(blocks), kCompactThreads, 0, s>>>(
                          X, slots, cap, out, out_rows, out_count, status)));
   count_launches(1);
   return cudaGetLastError();

@@ -241,12 +241,12 @@ cudaError_t launch_subset(const SubsetArgs& a, cudaStream_t s) {
 }
 
 // Warp-aggregated append of the rows whose flag is zero.
+constexpr int kSelectThreads = 256;
 template <int KT>
-__global__ void select_unflagged_kernel(const uint64_t* __restrict__ rows, int64_t n,
-                                        const uint32_t* __restrict__ flag,
-                                        uint64_t* __restrict__ out,
-                                        unsigned long long* out_count,
-                                        const unsigned long long* n_dev) {
+__global__ void __launch_bounds__(kSelectThreads)
+    select_unflagged_kernel(const uint64_t* __restrict__ rows, int64_t n,
+                            const uint32_t* __restrict__ flag, uint64_t* __restrict__ out,
+                            unsigned long long* out_count, const unsigned long long* n_dev) {
   // Each block takes a contiguous range of rows: it counts the unflagged
   // ones, reserves room for them with one atomic on the global count, and
   // places them through a shared-memory cursor (one global atomic per block).
@@ -270,6 +270,12 @@ __global__ void select_unflagged_kernel(const uint64_t* __restrict__ rows, int64
   __syncthreads();
   if (threadIdx.x == 0) blk_base = blk_count ? atomicAdd(out_count, (unsigned long long)blk_count) : 0ull;
   __syncthreads();
+  // The kept rows of each 32-row step are copied by the whole warp, 32 / KT
+  // rows per instruction with consecutive lanes on consecutive words.
+  __shared__ int64_t kept_row[kSelectThreads];
+  int64_t* my_kept = kept_row + (threadIdx.x & ~31);
+  constexpr int kRowsPer = 32 / KT;
+  const int sub = lane / KT, word = lane % KT;
   for (int64_t base = lo + (threadIdx.x & ~31); base < hi; base += blockDim.x) {
     const int64_t i = base + lane;
     const bool keep = i < hi && flag[i] == 0u;
@@ -278,11 +284,14 @@ __global__ void select_unflagged_kernel(const uint64_t* __restrict__ rows, int64
     unsigned int p0 = 0;
     if (lane == 0) p0 = atomicAdd(&blk_cursor, unsigned(__popc(m)));
     p0 = __shfl_sync(0xffffffffu, p0, 0);
-    if (keep) {
-      const uint64_t pos = blk_base + p0 + unsigned(__popc(m & ((1u << lane) - 1u)));
-#pragma unroll
-      for (int k = 0; k < KT; ++k) out[pos * KT + k] = rows[i * KT + k];
+    if (keep) my_kept[__popc(m & ((1u << lane) - 1u))] = i;
+    __syncwarp();
+    const int nk = __popc(m);
+    for (int b = sub; b < nk; b += kRowsPer) {
+      const uint64_t pos = blk_base + p0 + unsigned(b);
+      out[pos * KT + word] = rows[my_kept[b] * KT + word];
     }
+    __syncwarp();
   }
 }
 
@@ -296,7 +305,7 @@ cudaError_t launch_select_unflagged(const uint64_t* rows, int64_t n, int KT,
   int64_t blocks = ceil_div(n, 2048);
   if (blocks > int64_t(num_sms()) * 16) blocks = int64_t(num_sms()) * 16;
   if (blocks < 1) blocks = 1;
-  IG_DISPATCH_KT(KT, (select_unflagged_kernel<KTC><<<unsigned(blocks), 256, 0, s>>>(
+  IG_DISPATCH_KT(KT, (select_unflagged_kernel<KTC><<<unsigned(blocks), kSelectThreads, 0, s>>>(
                          rows, n, flag, out, out_count, n_dev)));
   count_launches(1);
   return cudaGetLastError();
