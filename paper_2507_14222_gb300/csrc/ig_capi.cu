@@ -872,22 +872,15 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
       IG_CUDA(cudaMemsetAsync(covered.p, 0, sizeof(uint32_t) * U, s), "ig_fit");
       bool done_round = false;
       if (pruned_round) {
-        // The indexed round needs the exact number of candidates left.
-        int64_t n_cur = U;
-        if (cur_n_dev) {
-          IG_CUDA(cudaMemcpyAsync(h_pinned + 3, cur_n_dev, sizeof(unsigned long long),
-                                  cudaMemcpyDeviceToHost, s),
-                  "ig_fit");
-          IG_CUDA(cudaStreamSynchronize(s), "ig_fit");
-          n_cur = int64_t(h_pinned[3]);
-        }
+        // The candidates left are counted on the device (U bounds them).
         int64_t t = -1;
         if (rec_idx[o].idx.usable) {
           igk::IndexedArgs a;
           a.mode = igk::MODE_ANY;
           a.index = &rec_idx[o].idx;
           a.keyed = cur;
-          a.n_keyed = n_cur;
+          a.n_keyed = U;
+          a.n_keyed_dev = cur_n_dev;
           a.keyed_stride = KT;
           a.keyed_score = nullptr;
           a.out_u32 = covered.p;

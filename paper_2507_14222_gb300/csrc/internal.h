@@ -223,6 +223,9 @@ struct IndexedArgs {
   int max_q = 4;        // most own rows per thread of a block (1, 2, 4)
   int flip_factor = 2;  // side ratio before the non-result side goes to registers
   int tc = 0;           // run the blocks on the tensor cores (KT 2, 4, 8)
+  // Optional: the keyed row count on the device; n_keyed is then its upper
+  // bound (no host read-back is needed before the index is built).
+  const unsigned long long* n_keyed_dev = nullptr;
 };
 cudaError_t indexed_subset(const IndexedArgs& a, cudaStream_t s);
 
@@ -238,9 +241,11 @@ struct KeyedIndex {
   uint32_t* off = nullptr;    // group offsets, L + 2 entries
   std::vector<uint32_t> h_off;
 };
+// n_dev (optional): the number of rows on the device, at most n (an upper
+// bound then, used for sizes); out->n is the number filed.
 cudaError_t build_keyed_index(const uint64_t* keyed, int64_t n, int stride, int K, int KT,
                               const uint32_t* freq, const uint64_t* score, KeyedIndex* out,
-                              cudaStream_t s);
+                              cudaStream_t s, const unsigned long long* n_dev = nullptr);
 void release_keyed_index(KeyedIndex* k, cudaStream_t s);
 // The item-index test with its blocks run on the tensor cores (KT 2, 4, 8):
 // the result side -- patterns for MODE_ANY / MODE_COUNT, records for

@@ -169,8 +169,10 @@ __global__ void multi_scatter_kernel(const uint64_t* __restrict__ rows, int64_t 
 // counters.
 __global__ void key_item_kernel(const uint64_t* __restrict__ rows, int64_t n, int stride, int K,
                                 int L, const uint32_t* __restrict__ freq,
-                                uint32_t* __restrict__ key, uint32_t* __restrict__ kcount) {
+                                uint32_t* __restrict__ key, uint32_t* __restrict__ kcount,
+                                const unsigned long long* __restrict__ n_dev) {
   extern __shared__ uint32_t shk[];
+  if (n_dev && int64_t(*n_dev) < n) n = int64_t(*n_dev);
   uint32_t* f_s = shk;          // [L]
   uint32_t* c_s = shk + L;      // [L + 1]
   for (int l = threadIdx.x; l < L; l += blockDim.x) f_s[l] = freq[l];
@@ -211,8 +213,10 @@ __global__ void keyed_scatter_kernel(const uint64_t* __restrict__ rows, int64_t 
                                      uint32_t* __restrict__ cursor, uint64_t* __restrict__ out,
                                      uint32_t* __restrict__ ids,
                                      const uint64_t* __restrict__ payload,
-                                     uint64_t* __restrict__ payload_out) {
+                                     uint64_t* __restrict__ payload_out,
+                                     const unsigned long long* __restrict__ n_dev) {
   extern __shared__ uint64_t shm[];
+  if (n_dev && int64_t(*n_dev) < n) n = int64_t(*n_dev);
   uint64_t* rec = shm;
   uint32_t* cnt = reinterpret_cast<uint32_t*>(rec + blockDim.x * KT);  // [groups]
   uint32_t* base = cnt + groups;                                       // [groups]
@@ -501,10 +505,10 @@ cudaError_t launch_multi_scatter(const uint64_t* rows, int64_t n, int stride, in
 
 cudaError_t launch_key_item(const uint64_t* rows, int64_t n, int stride, int K, int L,
                             const uint32_t* freq, uint32_t* key, uint32_t* kcount,
-                            cudaStream_t s) {
+                            const unsigned long long* n_dev, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   key_item_kernel<<<unsigned(ceil_div(n, 256)), 256, size_t(2 * L + 1) * 4, s>>>(
-      rows, n, stride, K, L, freq, key, kcount);
+      rows, n, stride, K, L, freq, key, kcount, n_dev);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -512,12 +516,13 @@ cudaError_t launch_key_item(const uint64_t* rows, int64_t n, int stride, int K, 
 cudaError_t launch_keyed_scatter(const uint64_t* rows, int64_t n, int stride, int K, int KT,
                                  int groups, const uint32_t* key, const uint32_t* off,
                                  uint32_t* cursor, uint64_t* out, uint32_t* ids,
-                                 const uint64_t* payload, uint64_t* payload_out, cudaStream_t s) {
+                                 const uint64_t* payload, uint64_t* payload_out,
+                                 const unsigned long long* n_dev, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int nb = scatter_threads(n);
   const size_t smem = size_t(nb) * KT * 8 + size_t(2) * groups * 4;
   keyed_scatter_kernel<<<unsigned(ceil_div(n, nb)), nb, smem, s>>>(
-      rows, n, stride, K, KT, groups, key, off, cursor, out, ids, payload, payload_out);
+      rows, n, stride, K, KT, groups, key, off, cursor, out, ids, payload, payload_out, n_dev);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -703,7 +708,7 @@ void release_keyed_index(KeyedIndex* k, cudaStream_t s) {
 
 cudaError_t build_keyed_index(const uint64_t* keyed, int64_t n, int stride, int K, int KT,
                               const uint32_t* freq, const uint64_t* score, KeyedIndex* out,
-                              cudaStream_t s) {
+                              cudaStream_t s, const unsigned long long* n_dev) {
   *out = KeyedIndex();
   out->K = K;
   out->KT = KT;
@@ -729,14 +734,15 @@ cudaError_t build_keyed_index(const uint64_t* keyed, int64_t n, int stride, int 
   if (score)
     IG_K_TRY(cudaMallocAsync(reinterpret_cast<void**>(&out->score), size_t(n + 256) * 8, s));
   void* tok = prof_begin(kStageIndexBuild, s);
-  IG_K_TRY(launch_key_item(keyed, n, stride, K, L, freq, key, kcount, s));
+  IG_K_TRY(launch_key_item(keyed, n, stride, K, L, freq, key, kcount, n_dev, s));
   IG_K_TRY(launch_small_scan(kcount, groups, out->off, s));
   IG_K_TRY(launch_keyed_scatter(keyed, n, stride, K, KT, groups, key, out->off, kcount + groups,
-                                out->rows, out->ids, score, out->score, s));
+                                out->rows, out->ids, score, out->score, n_dev, s));
   prof_end(tok);
   out->h_off.assign(groups + 1, 0u);
   IG_K_TRY(cudaMemcpyAsync(out->h_off.data(), out->off, (groups + 1) * 4, cudaMemcpyDeviceToHost, s));
   IG_K_TRY(cudaStreamSynchronize(s));
+  out->n = int64_t(out->h_off[groups]);  // the rows filed: n, or *n_dev when given
   cudaFreeAsync(kcount, s);
   cudaFreeAsync(key, s);
 #undef IG_K_TRY
@@ -797,8 +803,13 @@ cudaError_t indexed_subset(const IndexedArgs& a, cudaStream_t s) {
   if (a.n_keyed == 0 || idx.n_rows == 0) return cudaSuccess;
   KeyedIndex kx;
   cudaError_t e = build_keyed_index(a.keyed, a.n_keyed, a.keyed_stride, idx.K, idx.KT, idx.freq,
-                                    a.mode == MODE_SUM ? a.keyed_score : nullptr, &kx, s);
+                                    a.mode == MODE_SUM ? a.keyed_score : nullptr, &kx, s,
+                                    a.n_keyed_dev);
   if (e != cudaSuccess) return e;
+  if (kx.n == 0) {  // no keyed rows left on the device: nothing to test
+    release_keyed_index(&kx, s);
+    return cudaSuccess;
+  }
   e = indexed_subset_prebuilt(a.mode, idx, kx, a.out_u32, a.out_u64, a.status, a.tests_out,
                               a.prof_stage, a.max_q, a.flip_factor, a.tc, s);
   release_keyed_index(&kx, s);
