@@ -472,30 +472,35 @@ cudaError_t launch_expand(const uint64_t* rows, int64_t n, int stride, int KT, b
 //
 // subset_tc_fused_kernel: the same 0/1 GEMM on the item index's blocks, with
 // no operand images in global memory.  Packed 64*KT-bit rows are copied by
-// TMA into shared staging, and expander warps write the E4M3 bytes (swizzled
-// as the MMA reads them; 0x08 = 2^-6 per set bit, which takes one multiply
-// fewer to spread than 1.0) straight into shared memory.  A work item holds up
-// to 256 resident rows of one item group, as two M = 128 halves that share
-// every expanded stream tile (64 rows, N = 64), so that the expansion --
-// integer work that sets this kernel's pace -- is spent once for two MMAs;
-// that pays where groups are large (evidence, resident side = records),
-// while coherence and support keep one half and 128-row stream tiles.  The grid
-// is persistent: CTA b runs items b, b + gridDim.x, ... with its tensor
-// memory allocated once, and expands the next item's resident rows as soon
-// as the MMAs on the previous one are done.  Warp roles:
-//   warp 0    lane 0 issues the bulk copies of packed rows;
-//   warp 1    allocates tensor memory; lane 0 issues the MMAs and commits;
-//   warps 2-5 epilogue: lanes of TMEM quarter w % 4, both halves; a min
-//             over 32 columns for "any", a bit mask of the hits and a loop
-//             over its set bits for the score-weighted sum;
-//   warps 6-  expand packed tiles into operand tiles.
+// TMA into shared staging.  The resident rows of a work item (one item
+// group's patterns for coherence and support, its records for evidence) are
+// expanded to E4M3 bytes (0x08 = 2^-6 per set bit, which takes one multiply
+// fewer to spread than 1.0) and written into tensor memory, where the MMA
+// reads its A operand; the streamed rows are expanded into swizzled
+// shared-memory tiles of 128 rows (the B operand).  Evidence keeps two
+// 128-row halves of records per item, so each expanded stream tile serves
+// two MMA chains.  Each chain (a "unit": one tile, one half) accumulates
+// into one of two 128-column slots of tensor memory, taken in turn, so the
+// epilogue of one unit overlaps the MMAs of the next.  The grid is
+// persistent: CTA b runs items b, b + gridDim.x, ... with its tensor memory
+// allocated once.  Warp roles:
+//   warp 0     lane 0 issues the bulk copies of packed rows;
+//   warp 1     allocates tensor memory; lane 0 issues the MMAs and commits;
+//   warps 2-5  epilogue (and 6-9 for evidence, a second group that takes
+//              every other unit): lanes of TMEM quarter w % 4; a min over
+//              32 columns for "any", a count of zeros for "count", a bit
+//              mask of the hits and a loop over its set bits for the
+//              score-weighted sum;
+//   the rest   expand packed tiles into operand tiles.
 // Every wait is bounded; a timeout sets the status and an abort flag that
 // every role checks.
 
 constexpr int kFusedThreads = 704;  // 22 warps
-// Resident halves and stream-tile rows per work item, by mode.
+// Resident halves and stream-tile rows per work item, by mode: evidence
+// keeps two 128-row halves of records, so that each expanded stream tile
+// serves two MMA chains.
 constexpr int fused_halves(int mode) { return mode == MODE_SUM ? 2 : 1; }
-constexpr int fused_n(int mode) { return mode == MODE_SUM ? 64 : 128; }
+constexpr int fused_n(int mode) { return 128; }
 
 template <int KT, int MODE>
 struct FusedShape {
@@ -650,7 +655,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
     }
     for (int b = 0; b < S::kAccBufs; ++b) {
       mbar_init(acc_full + b, 1);
-      mbar_init(acc_empty + b, NE);
+      mbar_init(acc_empty + b, 4);  // the four warps of the group that takes the unit
     }
     *abort_flag = 0;
     fence_mbar_init();
@@ -711,9 +716,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // MMA issuer: per stream tile, one MMA chain per resident half, the
-      // resident operand read from tensor memory.
-      int64_t tt = 0, ii = 0, last = -1;
+      // MMA issuer: per stream tile, one MMA chain per resident half (a
+      // "unit"), the resident operand read from tensor memory.  Units take
+      // the accumulator slots in turn, so the epilogue of one unit overlaps
+      // the MMAs of the next.
+      int64_t tt = 0, ii = 0, uu = 0;
       bool ok = true;
       for (int64_t it = blockIdx.x; it < p.n_items && ok; it += G, ++ii) {
         const TcItem w = p.items[it];
@@ -727,21 +734,26 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
         }
         tc_fence_after();
         const uint32_t a_tm = tmem + uint32_t(S::kAccCols + ab * S::kHalves * S::kACols);
-        for (int t = 0; t < w.b_tiles; ++t, ++tt) {
-          const int s = int(tt % XS), b = int(tt % S::kAccBufs);
-          if (!mbar_wait(b_x_full + s, uint32_t((tt / XS) & 1), p.status) ||
-              !mbar_wait(acc_empty + b, uint32_t(((tt / S::kAccBufs) & 1) ^ 1), p.status) ||
-              *abort_flag) {
+        for (int t = 0; t < w.b_tiles && ok; ++t, ++tt) {
+          const int s = int(tt % XS);
+          if (!mbar_wait(b_x_full + s, uint32_t((tt / XS) & 1), p.status) || *abort_flag) {
             *abort_flag = 1;
             ok = false;
             break;
           }
-          tc_fence_after();
           // The descriptor's start address field is the byte address / 16, so
           // a K step's offset is added to it directly.
           const uint64_t bdesc = sw128_desc(smem_u32(B_x + size_t(s) * S::kImgB));
-          for (int h = 0; h < halves; ++h) {
-            const uint32_t d = tmem + uint32_t(b * 128 + h * kN);
+          for (int h = 0; h < halves; ++h, ++uu) {
+            const int b = int(uu % S::kAccBufs);
+            if (!mbar_wait(acc_empty + b, uint32_t(((uu / S::kAccBufs) & 1) ^ 1), p.status) ||
+                *abort_flag) {
+              *abort_flag = 1;
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t d = tmem + uint32_t(b * 128);
             const uint32_t ah = a_tm + uint32_t(h * S::kACols);
 #pragma unroll
             for (int k = 0; k < KT * 2; ++k) {
@@ -750,122 +762,92 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
               tc_mma_tmem_a(d, ah + uint32_t(8 * k), bdesc + uint64_t(boff >> 4), S::kIdesc,
                             k > 0 ? 1u : 0u);
             }
+            tc_commit(acc_full + b);
           }
+          if (!ok) break;
           tc_commit(b_x_empty + s);
-          tc_commit(acc_full + b);
-          last = tt;
         }
         if (!ok) break;
         tc_commit(a_x_empty + ab);  // the resident rows are free once this item's MMAs are done
       }
-      if (last >= 0)
-        mbar_wait(acc_full + (last % S::kAccBufs), uint32_t((last / S::kAccBufs) & 1), p.status);
+      if (uu > 0)
+        mbar_wait(acc_full + ((uu - 1) % S::kAccBufs), uint32_t(((uu - 1) / S::kAccBufs) & 1),
+                  p.status);
     }
   } else if (warp < kFirstExp) {
-    // Epilogue: warp w reads accumulator lanes 32*(w % 4) .. +32, i.e.
-    // resident rows quarter*32 + lane of its half (h0 = (w - 2) / 4 when
-    // there is one group of four warps per half, else of both halves).
+    // Epilogue: warp w reads accumulator lanes 32*(w % 4) .. +32 (resident
+    // rows quarter*32 + lane of the unit's half).  With two groups of four
+    // warps (evidence), group g takes the units u with u % 2 == g, i.e. the
+    // accumulator slot g; with one group, every unit.
+    constexpr int NG = NE / 4;
     const int quarter = warp & 3;
     const int tile_row = quarter * 32 + lane;
-    const int h0 = NE == 4 ? 0 : (warp - 2) >> 2;
-    const int hstep = NE == 4 ? 1 : 2;
-    int64_t tt = 0;
+    const int grp = (warp - 2) >> 2;
+    int64_t uu = 0;
     bool ok = true;
     for (int64_t it = blockIdx.x; it < p.n_items && ok; it += G) {
       const TcItem w = p.items[it];
       const int halves = w.own_count > 128 ? 2 : 1;
-      bool cov[2] = {false, false};
-      uint32_t cnt[2] = {0, 0};
-      unsigned long long sum[2] = {0, 0};
-      // MODE_SUM: each tile's scores are loaded into registers one tile
-      // ahead and copied to this warp's shared slots when the tile starts.
-      unsigned long long nx[kN / 32];
-      auto load_scores = [&](int t) {
-        const int64_t j0 = w.str_first + int64_t(t) * kN;
-        const int64_t left = int64_t(w.str_count) - int64_t(t) * kN;
-#pragma unroll
-        for (int q = 0; q < kN / 32; ++q)
-          nx[q] = lane + 32 * q < left ? p.score[j0 + lane + 32 * q] : 0ull;
-      };
-      if constexpr (MODE == MODE_SUM) load_scores(0);
-      for (int t = 0; t < w.b_tiles; ++t, ++tt) {
-        const int b = int(tt % S::kAccBufs);
+      bool cov0 = false, cov1 = false;
+      uint32_t cnt0 = 0, cnt1 = 0;
+      unsigned long long sum0 = 0, sum1 = 0;
+      for (int t = 0; t < w.b_tiles && ok; ++t) {
         const int64_t left = int64_t(w.str_count) - int64_t(t) * kN;
         const int nvalid = int(left < kN ? left : kN);
-        if constexpr (MODE == MODE_SUM) {
+        bool staged = false;
+        for (int h = 0; h < halves; ++h, ++uu) {
+          if (int(uu % NG) != grp) continue;
+          const int b = int(uu % S::kAccBufs);
+          if constexpr (MODE == MODE_SUM) {
+            if (!staged) {
+              // This tile's scores, one copy per warp, fetched before the
+              // wait for the accumulator.
+              const int64_t j0 = w.str_first + int64_t(t) * kN;
 #pragma unroll
-          for (int q = 0; q < kN / 32; ++q) sc[lane + 32 * q] = nx[q];
-          __syncwarp();
-          if (t + 1 < w.b_tiles) load_scores(t + 1);
-        }
-        const bool got = mbar_wait(acc_full + b, uint32_t((tt / S::kAccBufs) & 1), p.status);
-        if (!__all_sync(0xffffffffu, got) || *abort_flag) {
-          *abort_flag = 1;
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        // The accumulator buffer is handed back to the MMA issuer as soon as
-        // this warp's last load from it has completed, before that chunk is
-        // reduced.
-        const int h_last = hstep == 2 ? h0 : halves - 1;
-        bool released = false;
-        if constexpr (MODE == MODE_SUM && kN == 64 && NE == 8) {
-          // This warp's half is two 32-column chunks: both are loaded, the
-          // buffer is handed back, then the hits of each are summed.
-          if (h0 < halves) {
-            uint32_t v[32], u[32];
-            const uint32_t ta =
-                tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * 128 + h0 * kN);
-            tmem_ld32x2(ta, ta + 32u, v, u);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acc_empty + b);
-            released = true;
-            uint32_t m0 = 0, m1 = 0;
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              m0 |= (v[i] == 0u ? 1u : 0u) << i;
-              m1 |= (u[i] == 0u ? 1u : 0u) << i;
+              for (int q = 0; q < kN / 32; ++q)
+                sc[lane + 32 * q] = lane + 32 * q < left ? p.score[j0 + lane + 32 * q] : 0ull;
+              __syncwarp();
+              staged = true;
             }
-            // Columns past the tile's rows (zero rows, D = 0) are not hits.
-            if (nvalid < 64) {
-              m0 &= nvalid >= 32 ? 0xffffffffu : (1u << nvalid) - 1u;
-              m1 &= nvalid <= 32 ? 0u : (1u << (nvalid - 32)) - 1u;
-            }
-            unsigned long long acc = 0;
-            while (m0) {
-              const int i = __ffs(m0) - 1;
-              m0 &= m0 - 1u;
-              acc += sc[i];
-            }
-            while (m1) {
-              const int i = __ffs(m1) - 1;
-              m1 &= m1 - 1u;
-              acc += sc[32 + i];
-            }
-            if (h0 == 0)
-              sum[0] += acc;
-            else
-              sum[1] += acc;
           }
-        } else {
-          // 32 columns at a time; the buffer is handed back after this
-          // warp's last load from it, before that chunk is reduced.
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            if (h >= halves || (hstep == 2 && h != h0)) continue;
+          const bool got =
+              mbar_wait(acc_full + b, uint32_t((uu / S::kAccBufs) & 1), p.status);
+          if (!__all_sync(0xffffffffu, got) || *abort_flag) {
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          bool cov = false;
+          uint32_t cnt = 0;
+          unsigned long long sum = 0;
+          // 32 columns per load; the slot is handed back to the MMA issuer as
+          // soon as the last load from it has completed, before that chunk
+          // is reduced.
 #pragma unroll 1
-            for (int c = 0; c < kN; c += 32) {
-              uint32_t v[32];
-              tmem_ld32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * 128 + h * kN + c),
-                        v);
-              if (h == h_last && c + 32 >= kN) {
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(acc_empty + b);
-                released = true;
+          for (int c = 0; c < kN; c += 32) {
+            uint32_t v[32];
+            tmem_ld32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * 128 + c), v);
+            if (c + 32 >= kN) {
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(acc_empty + b);
+            }
+            if constexpr (MODE == MODE_SUM) {
+              uint32_t m = 0;
+#pragma unroll
+              for (int i = 0; i < 32; ++i) m |= (v[i] == 0u ? 1u : 0u) << i;
+              // Columns past the tile's rows (zero rows, D = 0) are not hits.
+              if (c + 32 > nvalid) {
+                const int r = nvalid - c;
+                m &= r <= 0 ? 0u : (1u << r) - 1u;
               }
+              while (m) {
+                const int i = __ffs(m) - 1;
+                m &= m - 1u;
+                sum += sc[c + i];
+              }
+            } else {
               // Columns past the tile's rows (zero rows, D = 0) are made misses.
               if (c + 32 > nvalid) {
 #pragma unroll
@@ -876,47 +858,41 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
                 uint32_t mn = v[0];
 #pragma unroll
                 for (int i = 1; i < 32; ++i) mn = min(mn, v[i]);
-                cov[h] |= mn == 0u;
+                cov |= mn == 0u;
               }
               if constexpr (MODE == MODE_COUNT) {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) cnt[h] += v[i] == 0u ? 1u : 0u;
-              }
-              if constexpr (MODE == MODE_SUM) {
-                uint32_t m = 0;
-#pragma unroll
-                for (int i = 0; i < 32; ++i) m |= (v[i] == 0u ? 1u : 0u) << i;
-                while (m) {
-                  const int i = __ffs(m) - 1;
-                  m &= m - 1u;
-                  sum[h] += sc[c + i];
-                }
+                for (int i = 0; i < 32; ++i) cnt += v[i] == 0u ? 1u : 0u;
               }
             }
           }
-        }
-        if (!released) {
-          tc_fence_before();
+          if (h == 0) {
+            cov0 |= cov;
+            cnt0 += cnt;
+            sum0 += sum;
+          } else {
+            cov1 |= cov;
+            cnt1 += cnt;
+            sum1 += sum;
+          }
           __syncwarp();
-          if (lane == 0) mbar_arrive(acc_empty + b);
         }
-        __syncwarp();
       }
       if (!ok) break;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (h >= halves || (hstep == 2 && h != h0)) continue;
+      for (int h = 0; h < halves; ++h) {
         const int r = h * 128 + tile_row;
         if (r >= w.own_count) continue;
         const int64_t row = int64_t(p.own_ids[w.own_first + r]);
         if constexpr (MODE == MODE_ANY) {
-          if (cov[h]) p.out_u32[row] = 1u;
+          if (h == 0 ? cov0 : cov1) p.out_u32[row] = 1u;
         }
         if constexpr (MODE == MODE_COUNT) {
-          if (cnt[h]) atomicAdd(p.out_u32 + row, cnt[h]);
+          const uint32_t c = h == 0 ? cnt0 : cnt1;
+          if (c) atomicAdd(p.out_u32 + row, c);
         }
         if constexpr (MODE == MODE_SUM) {
-          if (sum[h]) atomicAdd(p.out_u64 + row, sum[h]);
+          const unsigned long long v = h == 0 ? sum0 : sum1;
+          if (v) atomicAdd(p.out_u64 + row, v);
         }
       }
     }
