@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="nsl15k",
+    ap.add_argument("--workload", default="nsl148k",
                     choices=sorted(igdata.WORKLOADS) + ["batched", "served"])
     ap.add_argument("--served-patterns", type=int, default=1_000_000,
                     help="patterns per class of the served workload")
@@ -253,6 +253,11 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return
 
+    executed = {
+        "coherence": sum(info["coherence_tests"]),
+        "support": sum(info["support_tests"]),
+        "evidence": sum(stages.get(k, (0, 0, 0))[2] for k in
+                        ("evidence_idx", "evidence_tc", "evidence")) // max(1, args.steps)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -270,12 +275,11 @@ def run_ours(args):
                      "candidates": list(info["n_candidates"][::-1])},
         "subset_kernel": {1: "lop3", 2: "tcgen05", 3: "item-index",
                           4: "item-index-tcgen05"}[info["subset_kernel"]],
-        "executed_tests_per_step": {
-            "coherence": sum(info["coherence_tests"]),
-            "support": sum(info["support_tests"]),
-            "evidence": stages.get("evidence_idx", (0, 0, 0))[2] // max(1, args.steps)
-                        + stages.get("evidence_tc", (0, 0, 0))[2] // max(1, args.steps)
-                        + stages.get("evidence", (0, 0, 0))[2] // max(1, args.steps)},
+        "executed_tests_per_step": executed,
+        # The same step's rate counted in executed subset tests (after the
+        # item index's exact pruning and the coherence windows' early drops)
+        # instead of the tests the definitions require.
+        "executed_value": sum(executed.values()) / (ms_per_step * 1e-3) / 1e9,
         "stages_ms_per_step": {k: round(v[0] / n_warm, 4) for k, v in warm.items() if v[1]},
         "stage_timing": f"stages: {n_warm} profiled warm-up step(s); timed steps: events "
                         f"around the {top} stage only",

@@ -289,6 +289,40 @@ int ig_prof_read_work(int64_t* tests);
 /* Number of kernels this library has launched in the process so far. */
 int64_t ig_launch_count(void);
 
+/* ---- Throughput probes --------------------------------------------------
+ * Measured rates of the hardware units the kernels above are bound by, for
+ * roofline denominators (instrumentation: the paper has no counterpart).
+ *   IG_PROBE_LOP3       LOP3 (three-input 32-bit logic) instructions per
+ *                       second over all SMs -- the integer-pipe subset test
+ *                       (Eq. 6 as acc |= p & ~r) takes one per half word;
+ *   IG_PROBE_L2_READ    bytes per second of coalesced 16-byte loads over a
+ *                       buffer of `arg` MiB (0 = 48) that stays in L2;
+ *   IG_PROBE_L2_RANDOM  bytes per second of 16-byte loads at random 16-byte
+ *                       offsets of such a buffer (the dedup table's access);
+ *   IG_PROBE_MMA_F8_SMEM, IG_PROBE_MMA_F8_TMEM
+ *                       flops per second of back-to-back tcgen05.mma
+ *                       kind::f8f6f4 chains (E4M3 operands, FP32
+ *                       accumulators), M = 128, N = arg & 0xfff (64, 128,
+ *                       or 256 with A in shared memory only), 16 MMAs of
+ *                       K = 32 per chain, A read from shared or tensor
+ *                       memory; one CTA per SM.  arg bit 12: a commit after
+ *                       every chain; bit 13: chains alternate between two
+ *                       accumulators and chain c waits for chain c - 2 to
+ *                       complete (an accumulator ring of two).
+ * A warm-up launch precedes the timed one.  *rate receives the rate, *ms the
+ * timed launch's device time, *cycles (MMA probes) the largest SM-clock count
+ * a CTA spent issuing and draining its chains; any may be NULL.  Runs on the
+ * current device on a stream of its own and synchronizes it.  IG_E_INVAL for
+ * an unknown probe or shape. */
+enum {
+  IG_PROBE_LOP3 = 0,
+  IG_PROBE_L2_READ = 1,
+  IG_PROBE_L2_RANDOM = 2,
+  IG_PROBE_MMA_F8_SMEM = 3,
+  IG_PROBE_MMA_F8_TMEM = 4
+};
+int ig_probe(int32_t probe, int32_t arg, double* rate, double* ms, double* cycles);
+
 #ifdef __cplusplus
 }
 #endif

@@ -89,6 +89,7 @@ SIGNATURES = {
     "ig_prof_timeline": (ctypes.c_int, [_P, _P, _P, _P, _I64, _P]),
     "ig_score_noalloc": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P]),
     "ig_fit_batched": (ctypes.c_int, [_P, _I32, _P, _I32, _P, _P]),
+    "ig_probe": (ctypes.c_int, [_I32, _I32, _P, _P, _P]),
     "ig_model_from_patterns": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P]),
     "ig_server_create": (ctypes.c_int, [_P, _P, _P]),
     "ig_server_submit": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P]),
@@ -315,10 +316,28 @@ def ig_fit_batched(problems, r: float | None = None, subset_kernel: int = 0,
     return [Model(ctypes.c_void_p(outs[i])) for i in range(len(problems))]
 
 
+def _check_score_rows(model: Model, rows):
+    """Scoring reads m x K 8-byte words with K from the model: reject rows of
+    another width or element size before anything is launched."""
+    m, K = _rows_shape(rows)
+    if _is_torch(rows):
+        import torch
+        ok = rows.dtype in (torch.int64, torch.uint64) if hasattr(torch, "uint64") \
+            else rows.dtype == torch.int64
+    else:
+        ok = np.asarray(rows).dtype.itemsize == 8
+    if not ok:
+        raise ValueError("rows must hold 64-bit words (torch.int64 / numpy.uint64)")
+    mk = model.info()["K"]
+    if K != mk:
+        raise ValueError(f"rows have {K} words per record but the model has K = {mk}")
+    return m, K
+
+
 def ig_score(model: Model, rows, stream=None):
     """IG inference (Eq. 4, Regulations 1-3): returns (A, N, labels)."""
     lib = load()
-    m, K = _rows_shape(rows)
+    m, K = _check_score_rows(model, rows)
     if _is_torch(rows):
         import torch
         A = torch.empty(m, dtype=torch.int64, device=rows.device)
@@ -348,7 +367,7 @@ def ig_score_noalloc(model: Model, rows, stream=None):
     import torch
     if not _is_torch(rows) or not rows.is_cuda:
         raise ValueError("ig_score_noalloc takes CUDA tensors only")
-    m, _ = _rows_shape(rows)
+    m, _ = _check_score_rows(model, rows)
     A = torch.empty(m, dtype=torch.int64, device=rows.device)
     N = torch.empty(m, dtype=torch.int64, device=rows.device)
     lab = torch.empty(m, dtype=torch.uint8, device=rows.device)
@@ -499,6 +518,18 @@ def prof_timeline() -> list:
     _check(lib.ig_prof_timeline(_ptr(st), _ptr(sid), _ptr(t0), _ptr(t1), k, ctypes.byref(n)))
     return [(lib.ig_prof_stage_name(int(st[i])).decode(), int(sid[i]), float(t0[i]), float(t1[i]))
             for i in range(k)]
+
+
+PROBES = {"lop3": 0, "l2_read": 1, "l2_random": 2, "mma_f8_smem": 3, "mma_f8_tmem": 4}
+
+
+def probe(name: str, arg: int = 0) -> dict:
+    """One throughput probe of the current GPU (ig_probe): {"rate": per second,
+    "ms": timed launch, "cycles": SM clocks of the slowest CTA (MMA probes)}."""
+    rate, ms, cyc = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().ig_probe(PROBES[name], int(arg), ctypes.byref(rate), ctypes.byref(ms),
+                           ctypes.byref(cyc)))
+    return {"rate": rate.value, "ms": ms.value, "cycles": cyc.value}
 
 
 def launch_count() -> int:

@@ -21,7 +21,7 @@ LIB = os.path.join(BUILD, "libig_gb300.so")
 
 SOURCES = ["encode.cu", "dedup.cu", "subset.cu", "sort.cu", "ig_capi.cu",
            "score_noalloc.cu", "subset_tc.cu",
-           "prune.cu", "server.cu", "helpers.cu"]
+           "prune.cu", "server.cu", "helpers.cu", "probe.cu"]
 HEADERS = ["common.cuh", "internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Host code is compiled without floating-point contraction, so that its

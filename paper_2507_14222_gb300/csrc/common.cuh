@@ -21,10 +21,14 @@ enum : int {
   ST_COUNT = 8,       // a table held more keys than its count (nothing written past it)
 };
 
-// Upper bounds on spin loops.  Each mbarrier poll is a try_wait, which
-// itself suspends the thread for a hardware-defined interval, so the bound
-// below corresponds to well over a second of waiting.
-constexpr uint32_t kMbarPollLimit = 1u << 22;
+// Upper bounds on spin loops.  Each mbarrier poll is a try_wait that
+// suspends the thread until the phase completes or about kMbarSuspendNs
+// nanoseconds pass, so the bound below is about two seconds of waiting.  The
+// suspension keeps waiting warps (the tensor-core kernels' producer,
+// expander and epilogue roles spend much of their time waiting) from
+// spending issue slots that the working warps of the SM need.
+constexpr uint32_t kMbarSuspendNs = 2000;
+constexpr uint32_t kMbarPollLimit = 1u << 20;
 constexpr uint32_t kSlotSpinLimit = 1u << 22;
 
 __device__ __forceinline__ void set_status(int* status, int bits) {
@@ -60,10 +64,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "n"(kMbarSuspendNs)
       : "memory");
   return ok != 0;
 }

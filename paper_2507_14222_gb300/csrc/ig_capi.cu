@@ -196,9 +196,6 @@ struct DevBuf {
   }
 };
 
-// True for CUDA device (or managed) memory; the calling thread's current
-// device is then switched to the device that owns it, so that every later
-// allocation and launch of the call happens there.
 // Pinned host words for size read-backs, one block per host thread.
 unsigned long long* thread_pinned() {
   static thread_local unsigned long long* p = nullptr;
@@ -275,21 +272,6 @@ struct IndexHolder {
   ~IndexHolder() { igk::release_record_index(&idx, s); }
 };
 
-bool is_device_pointer(const void* p) {
-  if (!p) return false;
-  cudaPointerAttributes attr;
-  cudaError_t e = cudaPointerGetAttributes(&attr, p);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) return false;
-  int cur = -1;
-  if (cudaGetDevice(&cur) == cudaSuccess && cur != attr.device && attr.device >= 0)
-    cudaSetDevice(attr.device);
-  return true;
-}
-
 // An input array as a device pointer: either the caller's own device array,
 // or a stream-ordered device copy of the caller's host array.
 template <class T>
@@ -301,7 +283,7 @@ struct InputView {
       d = p;
       return IG_OK;
     }
-    if (is_device_pointer(p)) {
+    if (igk::is_device_pointer(p)) {
       d = p;
       return IG_OK;
     }
@@ -324,7 +306,7 @@ struct OutputView {
   int bind(T* p, size_t n, cudaStream_t s, const char* what) {
     user = p;
     count = n;
-    if (p && is_device_pointer(p)) {
+    if (p && igk::is_device_pointer(p)) {
       d = p;
       return IG_OK;
     }
@@ -383,16 +365,40 @@ void igk::prof_end(void* token) {
 void igk::count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 int igk::num_sms() {
-  static int cached[64] = {0};
+  // Filled by whichever thread asks first; concurrent fillers store the same
+  // value (relaxed atomics: the class and server threads call this too).
+  static std::atomic<int> cached[64];
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return 148;
-  if (!cached[dev]) {
-    int v = 0;
+  int v = cached[dev].load(std::memory_order_relaxed);
+  if (!v) {
     cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    cached[dev] = v > 0 ? v : 148;
+    if (v <= 0) v = 148;
+    cached[dev].store(v, std::memory_order_relaxed);
   }
-  return cached[dev];
+  return v;
+}
+
+bool igk::device_of(const void* p, int* dev) {
+  if (!p) return false;
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) return false;
+  if (attr.device < 0) return false;
+  *dev = attr.device;
+  return true;
+}
+
+bool igk::is_device_pointer(const void* p) {
+  int owner = -1;
+  if (!device_of(p, &owner)) return false;
+  int cur = -1;
+  if (cudaGetDevice(&cur) == cudaSuccess && cur != owner) cudaSetDevice(owner);
+  return true;
 }
 
 namespace {
@@ -460,6 +466,7 @@ struct ig_model {
   int64_t sup_tests[2] = {0, 0};               // support tests executed
   igk::KeyedIndex* pidx[2] = {nullptr, nullptr};  // patterns by key item, for scoring
   int index_max_q = 4, index_flip = 2;            // item-index tiling
+  uint64_t score_max[2] = {~uint64_t(0), ~uint64_t(0)};  // largest S per class (bound)
 };
 
 static void model_release(ig_model* m) {
@@ -682,6 +689,7 @@ const char* ig_last_error(void) { return g_last_error.c_str(); }
 
 int ig_encode(const uint16_t* codes, int64_t n, int32_t F, const uint16_t* cards,
               uint64_t* words_out, int32_t K, ig_stream_t stream) {
+  igk::DeviceRestore restore_device;  // the caller's device, put back on return
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (n < 0 || F <= 0 || !cards || (n > 0 && (!codes || !words_out)))
     return fail(IG_E_INVAL, "ig_encode: bad arguments");
@@ -718,6 +726,7 @@ int ig_encode(const uint16_t* codes, int64_t n, int32_t F, const uint16_t* cards
 
 int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
            const ig_params* params, ig_model** out, ig_stream_t stream) {
+  igk::DeviceRestore restore_device;  // the caller's device, put back on return
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (!out) return fail(IG_E_INVAL, "ig_fit: out is NULL");
   *out = nullptr;
@@ -751,6 +760,8 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
   static thread_local unsigned long long* h_pinned = nullptr;
   if (!h_pinned) IG_CUDA(cudaMallocHost(&h_pinned, 8 * sizeof(unsigned long long)), "ig_fit");
   TableCounters* h_counters = reinterpret_cast<TableCounters*>(h_pinned + 4);
+  // [2 + c]: the largest score of class c, copied back by its class stream.
+  unsigned long long* const h_smax = h_pinned + 2;
 
   // Section 3.2: class-stacked row matrices (normal -> X[0], attack -> X[1]).
   DevBuf<uint64_t> X[2];
@@ -1029,9 +1040,16 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
             "ig_fit: scores");
     IG_CUDA(cudaMemsetAsync(m->score[c], 0, sizeof(uint64_t) * npad, s), "ig_fit");
     {
+      DevBuf<unsigned long long> d_smax;
+      IG_CUDA(d_smax.alloc(1, s), "ig_fit");
+      IG_CUDA(cudaMemsetAsync(d_smax.p, 0, sizeof(unsigned long long), s), "ig_fit");
       ProfScope ps(S_PSCORE, s);
-      IG_CUDA(igk::launch_pattern_score(m->words_kt[c], P, KT, m->support[c], m->score[c], s),
+      IG_CUDA(igk::launch_pattern_score(m->words_kt[c], P, KT, m->support[c], m->score[c], s,
+                                        d_smax.p),
               "ig_fit: score");
+      IG_CUDA(cudaMemcpyAsync(h_smax + c, d_smax.p, sizeof(unsigned long long),
+                              cudaMemcpyDeviceToHost, s),
+              "ig_fit");
     }
     if (K == KT) {
       m->words[c] = m->words_kt[c];
@@ -1172,6 +1190,7 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
     m->thr = m->mu - scaled;
   }
   IG_CHECK(read_status(d_status.p, s, "ig_fit"));
+  for (int c = 0; c < 2; ++c) m->score_max[c] = h_smax[c];
   guard.m = nullptr;
   *out = m;
   return IG_OK;
@@ -1256,6 +1275,7 @@ int ig_fit_batched(const ig_problem* problems, int32_t n_problems, const ig_para
 
 int ig_model_from_patterns(int32_t K, const uint64_t* const* words, const uint32_t* const* support,
                            const int64_t* n_patterns, ig_model** out, ig_stream_t stream) {
+  igk::DeviceRestore restore_device;  // the caller's device, put back on return
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (!out || !words || !support || !n_patterns)
     return fail(IG_E_INVAL, "ig_model_from_patterns: NULL argument");
@@ -1312,8 +1332,15 @@ int ig_model_from_patterns(int32_t K, const uint64_t* const* words, const uint32
     IG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&m->score[c]), sizeof(uint64_t) * npad, s),
             "ig_model_from_patterns");
     IG_CUDA(cudaMemsetAsync(m->score[c], 0, sizeof(uint64_t) * npad, s), "ig_model_from_patterns");
-    IG_CUDA(igk::launch_pattern_score(m->words_kt[c], P, KT, m->support[c], m->score[c], s),
+    DevBuf<unsigned long long> d_smax;
+    IG_CUDA(d_smax.alloc(1, s), "ig_model_from_patterns");
+    IG_CUDA(cudaMemsetAsync(d_smax.p, 0, sizeof(unsigned long long), s), "ig_model_from_patterns");
+    IG_CUDA(igk::launch_pattern_score(m->words_kt[c], P, KT, m->support[c], m->score[c], s,
+                                      d_smax.p),
             "ig_model_from_patterns: score");
+    unsigned long long smax = 0;
+    IG_CUDA(cudaMemcpyAsync(&smax, d_smax.p, sizeof(smax), cudaMemcpyDeviceToHost, s),
+            "ig_model_from_patterns");
     if (K == KT) {
       m->words[c] = m->words_kt[c];
     } else {
@@ -1326,6 +1353,7 @@ int ig_model_from_patterns(int32_t K, const uint64_t* const* words, const uint32
                 "ig_model_from_patterns");
     }
     IG_CHECK(read_status(d_status.p, s, "ig_model_from_patterns"));
+    m->score_max[c] = smax;
   }
   m->subset_kernel = KT >= 2 ? 3 : 1;
   if (KT >= 2) {
@@ -1397,6 +1425,7 @@ int ig_model_copy_patterns(const ig_model* m, int32_t cls, uint64_t* words_out,
 
 int ig_score(const ig_model* m, const uint64_t* rows, int64_t n_rows, int64_t* A_out,
              int64_t* N_out, uint8_t* label_out, ig_stream_t stream) {
+  igk::DeviceRestore restore_device;  // the caller's device, put back on return
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (!m || n_rows < 0 || (n_rows > 0 && !rows)) return fail(IG_E_INVAL, "ig_score: bad arguments");
   if (n_rows == 0) return IG_OK;
@@ -1420,9 +1449,39 @@ int ig_score(const ig_model* m, const uint64_t* rows, int64_t n_rows, int64_t* A
   bool done[2] = {false, false};
   IndexHolder test_idx;
   test_idx.s = s;
-  if (pruned)
+  DevBuf<uint64_t> sorted_rows;
+  DevBuf<uint32_t> perm;
+  if (pruned && m->subset_kernel == 4) {
+    // The tensor-core evidence kernel reads records in canonical order: the
+    // neighbouring rows of an item group then hold similar itemsets, so the
+    // patterns inside them fall into fewer 32 x 32 accumulator chunks, and
+    // its epilogue skips every chunk without one.  The index files each copy
+    // under the caller's row number (perm), so results land in place.
+    const int KT = m->KT;
+    const uint64_t* keys = in.d;
+    DevBuf<uint64_t> padded;
+    if (m->K != KT) {
+      IG_CUDA(padded.alloc(size_t(n_rows) * KT, s), "ig_score");
+      IG_CUDA(cudaMemsetAsync(padded.p, 0, sizeof(uint64_t) * n_rows * KT, s), "ig_score");
+      IG_CUDA(cudaMemcpy2DAsync(padded.p, KT * 8, in.d, m->K * 8, m->K * 8, n_rows,
+                                cudaMemcpyDeviceToDevice, s),
+              "ig_score");
+      keys = padded.p;
+    }
+    IG_CUDA(sorted_rows.alloc(size_t(n_rows) * KT, s), "ig_score");
+    IG_CUDA(perm.alloc(size_t(n_rows), s), "ig_score");
+    {
+      ProfScope ps(igk::kStageIndexBuild, s);
+      IG_CUDA(igk::canonical_sort(keys, n_rows, KT, sorted_rows.p, nullptr, s, perm.p),
+              "ig_score: record order");
+    }
+    IG_CUDA(igk::build_record_index(sorted_rows.p, n_rows, KT, m->K, KT, 0.25, &test_idx.idx, s,
+                                    perm.p),
+            "ig_score: record index");
+  } else if (pruned) {
     IG_CUDA(igk::build_record_index(in.d, n_rows, m->K, m->K, m->KT, 0.25, &test_idx.idx, s),
             "ig_score: record index");
+  }
   if (pruned && test_idx.idx.usable) {
     // A (class 1) on the caller's stream and N (class 0) on this thread's
     // auxiliary stream, concurrently: both only read the indexes.
@@ -1444,7 +1503,7 @@ int ig_score(const ig_model* m, const uint64_t* rows, int64_t n_rows, int64_t* A
         IG_CUDA(igk::indexed_subset_prebuilt(igk::MODE_SUM, test_idx.idx, *m->pidx[c], nullptr,
                                              c == 1 ? A.d : N.d, d_status.p, &t, S_EVIDENCE_IDX,
                                              m->index_max_q, m->index_flip,
-                                             m->subset_kernel == 4 ? 1 : 0, sc),
+                                             m->subset_kernel == 4 ? 1 : 0, sc, m->score_max[c]),
                 "ig_score: evidence");
         done[c] = true;
         igk::prof_add_work(S_EVIDENCE_IDX, t);
@@ -1462,6 +1521,7 @@ int ig_score(const ig_model* m, const uint64_t* rows, int64_t n_rows, int64_t* A
       a.status = d_status.p;
       a.tests_out = &t;
       a.prof_stage = S_EVIDENCE_IDX;
+      a.score_max = m->score_max[c];
       a.max_q = m->index_max_q;
       a.flip_factor = m->index_flip;
       a.tc = m->subset_kernel == 4 ? 1 : 0;
@@ -1584,6 +1644,7 @@ int ig_model_load(const char* path, ig_model** out) {
     get(sup.data(), sup.size() * 4);
     get(sc.data(), size_t(P) * 8);
     if (!ok) break;
+    m->score_max[c] = P ? *std::max_element(sc.begin(), sc.begin() + P) : 0;
     for (int64_t i = 0; i < P; ++i)
       for (int k = 0; k < m->K; ++k) wk[size_t(i) * m->KT + k] = w[size_t(i) * m->K + k];
     bool cu = cudaMalloc(&m->words_kt[c], wk.size() * 8) == cudaSuccess &&

@@ -24,6 +24,30 @@ inline int64_t pad_rows(int64_t n) { return ((n + kRowPad - 1) / kRowPad) * kRow
 
 int num_sms();
 
+// Device pointers.  device_of: true if p is CUDA device (or managed) memory,
+// with *dev set to the device that owns it.  is_device_pointer: the same
+// test, and the calling thread's current device is switched to the owner,
+// so that the rest of the call allocates and launches there; entry points
+// that call it hold a DeviceRestore, which puts the caller's device back
+// when the call returns.
+bool device_of(const void* p, int* dev);
+bool is_device_pointer(const void* p);
+struct DeviceRestore {
+  int dev = -1;
+  DeviceRestore() {
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+      cudaGetLastError();
+      dev = -1;
+    }
+  }
+  ~DeviceRestore() {
+    int cur = -1;
+    if (dev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != dev) cudaSetDevice(dev);
+  }
+  DeviceRestore(const DeviceRestore&) = delete;
+  DeviceRestore& operator=(const DeviceRestore&) = delete;
+};
+
 // Stage timing (ig_prof_*): prof_begin records a CUDA event on s when timing
 // is on and returns a token (nullptr otherwise); prof_end records the
 // closing event and files the pair under the stage.
@@ -35,6 +59,9 @@ constexpr int kStageIndexBuild = 19;
 
 // Adds n to the library's count of kernel launches (ig_launch_count).
 void count_launches(int n);
+
+// probe.cu: one throughput probe (ig_probe).
+int probe_run(int probe, int arg, double* rate, double* ms, double* cycles);
 
 // Read-only view of a fitted model's device arrays (for entry points defined
 // outside ig_capi.cu).
@@ -198,8 +225,11 @@ struct RecordIndex {
   uint32_t* off = nullptr;
   std::vector<uint32_t> h_off;
 };
+// id_map (optional, n entries): the id filed for row i is id_map[i] instead
+// of i (rows given in another order than the caller's).
 cudaError_t build_record_index(const uint64_t* rows, int64_t n, int stride, int K, int KT,
-                               double max_fill, RecordIndex* idx, cudaStream_t s);
+                               double max_fill, RecordIndex* idx, cudaStream_t s,
+                               const uint32_t* id_map = nullptr);
 void release_record_index(RecordIndex* idx, cudaStream_t s);
 
 // A subset test of "keyed" rows (patterns: MODE_ANY / MODE_COUNT own rows,
@@ -226,6 +256,7 @@ struct IndexedArgs {
   // Optional: the keyed row count on the device; n_keyed is then its upper
   // bound (no host read-back is needed before the index is built).
   const unsigned long long* n_keyed_dev = nullptr;
+  uint64_t score_max = ~uint64_t(0);  // MODE_SUM: an upper bound of keyed_score
 };
 cudaError_t indexed_subset(const IndexedArgs& a, cudaStream_t s);
 
@@ -253,14 +284,18 @@ void release_keyed_index(KeyedIndex* k, cudaStream_t s);
 // rows are expanded to operand tiles in shared memory by a persistent kernel.
 // Same results as the integer grouped kernel; *tests_out as for
 // indexed_subset_prebuilt.
+// score_max (MODE_SUM): an upper bound of the keyed rows' scores; below
+// 2^26 the kernel sums hits per record in 32-bit shared partial sums.
 cudaError_t indexed_subset_tc(int mode, const RecordIndex& idx, const KeyedIndex& kx,
                               uint32_t* out_u32, unsigned long long* out_u64, int* status,
-                              int64_t* tests_out, int prof_stage, cudaStream_t s);
+                              int64_t* tests_out, int prof_stage, uint64_t score_max,
+                              cudaStream_t s);
 // indexed_subset with a prebuilt pattern side; no synchronization.
 cudaError_t indexed_subset_prebuilt(int mode, const RecordIndex& idx, const KeyedIndex& kx,
                                     uint32_t* out_u32, unsigned long long* out_u64, int* status,
                                     int64_t* tests_out, int prof_stage, int max_q,
-                                    int flip_factor, int tc, cudaStream_t s);
+                                    int flip_factor, int tc, cudaStream_t s,
+                                    uint64_t score_max = ~uint64_t(0));
 // freq[l] += number of the n rows holding item l (rows of stride `stride`, K words).
 cudaError_t launch_item_histogram(const uint64_t* rows, int64_t n, int stride, int K, int L,
                                   uint32_t* freq, cudaStream_t s);
@@ -273,9 +308,11 @@ cudaError_t launch_select_unflagged(const uint64_t* rows, int64_t n, int KT,
                                     unsigned long long* out_count, cudaStream_t s,
                                     const unsigned long long* n_dev = nullptr);
 
-// S = f * popcount(row)^2 (Eq. 2).
+// S = f * popcount(row)^2 (Eq. 2); smax (optional, must start at 0)
+// receives the largest S.
 cudaError_t launch_pattern_score(const uint64_t* rows, int64_t n, int KT,
-                                 const uint32_t* f, uint64_t* S, cudaStream_t s);
+                                 const uint32_t* f, uint64_t* S, cudaStream_t s,
+                                 unsigned long long* smax = nullptr);
 
 // Regulations 1-3 -> label (1 attack).
 cudaError_t launch_labels(const unsigned long long* A, const unsigned long long* N,
@@ -286,9 +323,10 @@ cudaError_t launch_labels(const unsigned long long* A, const unsigned long long*
 // Canonical order of n keys (stride KT): ascending as KT-word unsigned
 // integers, word KT-1 most significant; equal keys may repeat.  keys_out (n
 // rows) receives the sorted rows and must not overlap keys; `work` is
-// unused (the sort allocates its own 40 bytes per key).
+// unused (the sort allocates its own 40 bytes per key).  perm_out (optional,
+// n entries): the input row of each sorted row.
 cudaError_t canonical_sort(const uint64_t* keys, int64_t n, int KT, uint64_t* keys_out,
-                           uint64_t* work, cudaStream_t s);
+                           uint64_t* work, cudaStream_t s, uint32_t* perm_out = nullptr);
 
 // payload_sorted[pos of keys[i] in sorted] = payload[i] (binary search;
 // ST_BAD_INPUT if a key is missing).  sorted and keys: n rows, stride KT.

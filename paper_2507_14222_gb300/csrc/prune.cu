@@ -114,7 +114,8 @@ __device__ __forceinline__ void stage_rows(const uint64_t* __restrict__ rows, in
 __global__ void multi_scatter_kernel(const uint64_t* __restrict__ rows, int64_t n, int stride,
                                      int K, int KT, int L, const uint32_t* __restrict__ off,
                                      uint32_t* __restrict__ cursor, uint64_t* __restrict__ out,
-                                     uint32_t* __restrict__ ids) {
+                                     uint32_t* __restrict__ ids,
+                                     const uint32_t* __restrict__ id_map) {
   extern __shared__ uint64_t shm[];
   const int warps = int(blockDim.x >> 5);
   const int warp = int(threadIdx.x >> 5), lane = int(threadIdx.x & 31);
@@ -139,6 +140,7 @@ __global__ void multi_scatter_kernel(const uint64_t* __restrict__ rows, int64_t 
   }
   __syncthreads();
   const int64_t i = r0 + warp;
+  const uint32_t my_id = i < n ? (id_map ? id_map[i] : uint32_t(i)) : 0u;
   const int per = 32 / KT;                   // rows per store
   const int g = lane / KT, ww = lane - g * KT;  // this lane writes word ww of the g-th row
   for (int l0 = 0; l0 < L; l0 += 32) {
@@ -147,7 +149,7 @@ __global__ void multi_scatter_kernel(const uint64_t* __restrict__ rows, int64_t 
     uint32_t pos = 0;
     if (has) {
       pos = base[l] + atomicAdd(&cnt[l], 1u);
-      ids[pos] = uint32_t(i);
+      ids[pos] = my_id;
     }
     unsigned m = __ballot_sync(0xffffffffu, has);
     while (m) {
@@ -491,14 +493,14 @@ cudaError_t launch_small_scan(const uint32_t* cnt, int len, uint32_t* off, cudaS
 
 cudaError_t launch_multi_scatter(const uint64_t* rows, int64_t n, int stride, int K, int KT,
                                  int L, const uint32_t* off, uint32_t* cursor, uint64_t* out,
-                                 uint32_t* ids, cudaStream_t s) {
+                                 uint32_t* ids, const uint32_t* id_map, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   // One warp per row; large inputs take wide blocks, so that popular items
   // get few global reservations.
   const int warps = n >= int64_t(num_sms()) * 32 * 4 ? 32 : 8;
   const size_t smem = size_t(warps) * KT * 8 + size_t(2) * L * 4;
   multi_scatter_kernel<<<unsigned(ceil_div(n, warps)), warps * 32, smem, s>>>(
-      rows, n, stride, K, KT, L, off, cursor, out, ids);
+      rows, n, stride, K, KT, L, off, cursor, out, ids, id_map);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -641,7 +643,8 @@ void release_record_index(RecordIndex* idx, cudaStream_t s) {
 }
 
 cudaError_t build_record_index(const uint64_t* rows, int64_t n, int stride, int K, int KT,
-                               double max_fill, RecordIndex* idx, cudaStream_t s) {
+                               double max_fill, RecordIndex* idx, cudaStream_t s,
+                               const uint32_t* id_map) {
   *idx = RecordIndex();
   idx->K = K;
   idx->KT = KT;
@@ -678,7 +681,7 @@ cudaError_t build_record_index(const uint64_t* rows, int64_t n, int stride, int 
   IG_I_TRY(cudaMallocAsync(reinterpret_cast<void**>(&idx->ids), size_t(idx->n_copies) * 4, s));
   void* tok = prof_begin(kStageIndexBuild, s);
   IG_I_TRY(launch_multi_scatter(rows, n, stride, K, KT, L, idx->off, cursor, idx->rows, idx->ids,
-                                s));
+                                id_map, s));
   prof_end(tok);
 #undef IG_I_TRY
   return cudaSuccess;
@@ -752,12 +755,14 @@ cudaError_t build_keyed_index(const uint64_t* keyed, int64_t n, int stride, int 
 cudaError_t indexed_subset_prebuilt(int mode, const RecordIndex& idx, const KeyedIndex& kx,
                                     uint32_t* out_u32, unsigned long long* out_u64, int* status,
                                     int64_t* tests_out, int prof_stage, int max_q,
-                                    int flip_factor, int tc, cudaStream_t s) {
+                                    int flip_factor, int tc, cudaStream_t s,
+                                    uint64_t score_max) {
   *tests_out = 0;
   if (kx.n == 0 || idx.n_rows == 0) return cudaSuccess;
   const int L = idx.L, KT = idx.KT;
   if (tc && tc_supported(KT))
-    return indexed_subset_tc(mode, idx, kx, out_u32, out_u64, status, tests_out, prof_stage, s);
+    return indexed_subset_tc(mode, idx, kx, out_u32, out_u64, status, tests_out, prof_stage,
+                             score_max, s);
   std::vector<WorkItem> items;
   int64_t tests = 0;
   build_work_items(kx.h_off.data(), idx.h_off.data(), L, grouped_own_per_cta(KT),
@@ -811,7 +816,7 @@ cudaError_t indexed_subset(const IndexedArgs& a, cudaStream_t s) {
     return cudaSuccess;
   }
   e = indexed_subset_prebuilt(a.mode, idx, kx, a.out_u32, a.out_u64, a.status, a.tests_out,
-                              a.prof_stage, a.max_q, a.flip_factor, a.tc, s);
+                              a.prof_stage, a.max_q, a.flip_factor, a.tc, s, a.score_max);
   release_keyed_index(&kx, s);
   return e;
 }

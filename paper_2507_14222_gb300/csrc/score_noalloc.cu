@@ -58,19 +58,6 @@ int scratch_address(unsigned long long** out) {
   return IG_OK;
 }
 
-// True if p is device memory; makes its device current.
-bool on_device(const void* p) {
-  cudaPointerAttributes attr;
-  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) return false;
-  int cur = -1;
-  if (cudaGetDevice(&cur) == cudaSuccess && cur != attr.device) cudaSetDevice(attr.device);
-  return true;
-}
-
 int cuda_fail(cudaError_t e) {
   static thread_local char buf[256];
   snprintf(buf, sizeof(buf), "ig_score_noalloc: %s", cudaGetErrorString(e));
@@ -89,10 +76,34 @@ extern "C" int ig_score_noalloc(const ig_model* model, const uint64_t* rows, int
     return igk::report_error(
         IG_E_INVAL, "ig_score_noalloc: more rows than IG_SCORE_NOALLOC_MAX_ROWS (262144) in one call");
   if (m == 0) return IG_OK;
-  if (!on_device(rows) || (A_out && !on_device(A_out)) || (N_out && !on_device(N_out)) ||
-      (label_out && !on_device(label_out)))
+  // Every array must be device memory of one GPU, the one holding the
+  // model; that GPU is made current for the call and the caller's device is
+  // put back on return.
+  igk::ModelView v;
+  igk::model_view(model, &v);
+  int dev = -1;
+  if (!igk::device_of(rows, &dev))
     return igk::report_error(IG_E_INVAL,
                              "ig_score_noalloc: rows and outputs must be device memory");
+  const void* more[3] = {A_out, N_out, label_out};
+  for (const void* p : more) {
+    int d = -1;
+    if (p && (!igk::device_of(p, &d) || d != dev))
+      return igk::report_error(
+          IG_E_INVAL, "ig_score_noalloc: rows and outputs must be device memory of one GPU");
+  }
+  for (int c = 0; c < 2; ++c) {
+    int d = -1;
+    if (v.n_pat[c] && (!igk::device_of(v.words_kt[c], &d) || d != dev))
+      return igk::report_error(IG_E_INVAL,
+                               "ig_score_noalloc: the model lives on another GPU than the rows");
+  }
+  igk::DeviceRestore restore_device;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != dev) {
+    cudaError_t e = cudaSetDevice(dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
   unsigned long long* scratch = nullptr;
   int rc = scratch_address(&scratch);
   if (rc != IG_OK) return rc;
@@ -100,8 +111,6 @@ extern "C" int ig_score_noalloc(const ig_model* model, const uint64_t* rows, int
   unsigned long long* A = scratch + kStatusWords;
   unsigned long long* N = A + kMaxRows;
 
-  igk::ModelView v;
-  igk::model_view(model, &v);
   cudaError_t e;
   if ((e = cudaMemsetAsync(d_status, 0, sizeof(int), s)) != cudaSuccess) return cuda_fail(e);
   if ((e = cudaMemsetAsync(A, 0, sizeof(unsigned long long) * m, s)) != cudaSuccess) return cuda_fail(e);

@@ -226,7 +226,8 @@ __global__ void gather_rows_kernel(const uint64_t* __restrict__ keys, int KT,
 }
 
 template <int KT>
-static cudaError_t sort_t(const uint64_t* keys, int64_t n, uint64_t* keys_out, cudaStream_t s) {
+static cudaError_t sort_t(const uint64_t* keys, int64_t n, uint64_t* keys_out, uint32_t* perm_out,
+                          cudaStream_t s) {
   // Two sets of (p0, p1, idx) arrays, ping-ponged by the passes.
   void* mem = nullptr;
   cudaError_t e = cudaMallocAsync(&mem, size_t(n) * 40, s);
@@ -263,6 +264,8 @@ static cudaError_t sort_t(const uint64_t* keys, int64_t n, uint64_t* keys_out, c
                                                                      keys_out);
   count_launches(1);
   e = cudaGetLastError();
+  if (e == cudaSuccess && perm_out)
+    e = cudaMemcpyAsync(perm_out, cur.idx, size_t(n) * 4, cudaMemcpyDeviceToDevice, s);
   cudaFreeAsync(mem, s);
   return e;
 }
@@ -329,10 +332,10 @@ cudaError_t launch_check_strict(const uint64_t* sorted, int64_t n, int KT, int* 
 }
 
 cudaError_t canonical_sort(const uint64_t* keys, int64_t n, int KT, uint64_t* keys_out,
-                           uint64_t* /*work*/, cudaStream_t s) {
+                           uint64_t* /*work*/, cudaStream_t s, uint32_t* perm_out) {
   if (n == 0) return cudaSuccess;
   if (n >= int64_t(0xffffffffll)) return cudaErrorInvalidValue;
-  IG_DISPATCH_KT(KT, return sort_t<KTC>(keys, n, keys_out, s));
+  IG_DISPATCH_KT(KT, return sort_t<KTC>(keys, n, keys_out, perm_out, s));
   return cudaErrorInvalidValue;
 }
 

@@ -314,18 +314,32 @@ cudaError_t launch_select_unflagged(const uint64_t* rows, int64_t n, int KT,
 // Eq. 2: S = f * |b|^2, |b| the number of items of b.
 __global__ void pattern_score_kernel(const uint64_t* __restrict__ rows, int64_t n,
                                      int KT, const uint32_t* __restrict__ f,
-                                     uint64_t* __restrict__ S) {
+                                     uint64_t* __restrict__ S,
+                                     unsigned long long* __restrict__ smax) {
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint64_t items = 0;
-  for (int k = 0; k < KT; ++k) items += __popcll(rows[i * KT + k]);
-  S[i] = uint64_t(f[i]) * items * items;
+  unsigned long long v = 0;
+  if (i < n) {
+    uint64_t items = 0;
+    for (int k = 0; k < KT; ++k) items += __popcll(rows[i * KT + k]);
+    v = uint64_t(f[i]) * items * items;
+    S[i] = v;
+  }
+  if (smax) {
+    // Largest score of the warp, then one atomic per warp.
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, d);
+      v = o > v ? o : v;
+    }
+    if ((threadIdx.x & 31) == 0 && v) atomicMax(smax, v);
+  }
 }
 
 cudaError_t launch_pattern_score(const uint64_t* rows, int64_t n, int KT,
-                                 const uint32_t* f, uint64_t* S, cudaStream_t s) {
+                                 const uint32_t* f, uint64_t* S, cudaStream_t s,
+                                 unsigned long long* smax) {
   if (n == 0) return cudaSuccess;
-  pattern_score_kernel<<<unsigned(ceil_div(n, 256)), 256, 0, s>>>(rows, n, KT, f, S);
+  pattern_score_kernel<<<unsigned(ceil_div(n, 256)), 256, 0, s>>>(rows, n, KT, f, S, smax);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -26,6 +26,7 @@
 // chunk c of row r stored at chunk c ^ (r mod 8)), so every tile is one
 // contiguous bulk copy.  expand_kernel writes these images from packed rows.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -164,32 +165,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Two loads of 32 columns each, then one wait for both.
-__device__ __forceinline__ void tmem_ld32x2(uint32_t taddr0, uint32_t taddr1,
-                                            uint32_t (&v)[32], uint32_t (&u)[32]) {
+// 32 consecutive accumulator columns of this thread's lane, with their
+// minimum as unsigned words (tcgen05.ld.red.min): the accumulators hold
+// non-negative FP32 counts, so the minimum word is 0 exactly when one of the
+// 32 counts is 0.
+__device__ __forceinline__ void tmem_ld32_min(uint32_t taddr, uint32_t (&v)[32], uint32_t& mn) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "tcgen05.ld.red.sync.aligned.32x32b.x32.min.u32 "
       "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, %32, [%33];"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
         "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
         "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
         "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
         "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
-        "=r"(v[31])
-      : "r"(taddr0)
-      : "memory");
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]),
-        "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]),
-        "=r"(u[13]), "=r"(u[14]), "=r"(u[15]), "=r"(u[16]), "=r"(u[17]), "=r"(u[18]),
-        "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]), "=r"(u[24]),
-        "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]),
-        "=r"(u[31])
-      : "r"(taddr1)
+        "=r"(v[31]), "=r"(mn)
+      : "r"(taddr)
       : "memory");
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -497,7 +488,7 @@ cudaError_t launch_expand(const uint64_t* rows, int64_t n, int stride, int KT, b
 
 constexpr int kFusedThreads = 704;  // 22 warps
 // Resident halves and stream-tile rows per work item, by mode: evidence
-// keeps two 128-row halves of records, so that each expanded stream tile
+// keeps two 128-row halves of patterns, so that each expanded stream tile
 // serves two MMA chains.
 constexpr int fused_halves(int mode) { return mode == MODE_SUM ? 2 : 1; }
 constexpr int fused_n(int mode) { return 128; }
@@ -505,9 +496,9 @@ constexpr int fused_n(int mode) { return 128; }
 template <int KT, int MODE>
 struct FusedShape {
   static constexpr int kHalves = fused_halves(MODE);
-  // Epilogue warps (4 per resident half: one per 32-lane quarter of tensor
-  // memory) and expander warps (the rest of the 22 after the producer and
-  // the MMA issuer).
+  // Epilogue warps (4 per group, one per 32-lane quarter of tensor memory;
+  // evidence has two groups, which split every unit's columns) and expander
+  // warps (the rest of the 22 after the producer and the MMA issuer).
   static constexpr int kEpiWarps = 4 * kHalves;
   static constexpr int kExpWarps = kFusedThreads / 32 - 2 - kEpiWarps;
   static constexpr int kN = fused_n(MODE);                          // stream rows per tile
@@ -515,7 +506,10 @@ struct FusedShape {
   static constexpr uint32_t kImgB = uint32_t(kN) * KT * 64;        // one expanded stream tile
   static constexpr uint32_t kPkA = uint32_t(kOwn) * KT * 8;        // packed resident rows
   static constexpr uint32_t kPkB = uint32_t(kN) * KT * 8;          // one packed stream tile
-  static constexpr size_t kScores = MODE == MODE_SUM ? size_t(kEpiWarps) * kN * 8 : 0;
+  // MODE_SUM: each epilogue warp stages the record ids of its columns of
+  // the current stream tile.
+  static constexpr size_t kScores =
+      MODE == MODE_SUM ? size_t(kEpiWarps) * (kN / (kEpiWarps / 4)) * 4 : 0;
   // Tensor memory (512 columns): two accumulator buffers of 128 columns,
   // then the resident operand, 16*KT columns (4 items each) per half, twice
   // where it fits, so that the next item's rows can be written while the
@@ -554,7 +548,12 @@ struct FusedParams {
   const uint64_t* str_rows;  // grouped rows of the streamed side (stride KT)
   int own_complement;        // 1: the resident side is the record side
   const uint32_t* own_ids;   // original id of each grouped resident row
-  const uint64_t* score;     // MODE_SUM: S of each grouped streamed row
+  const uint64_t* score;     // MODE_SUM: S of each grouped resident row (pattern)
+  const uint32_t* str_ids;   // MODE_SUM: original id of each grouped streamed row (record)
+  // MODE_SUM: 1 when every score is below 2^27, so that the sum of one
+  // column's hits over a warp's 32 patterns fits in 32 bits; 0: every hit
+  // goes to its record by its own 64-bit atomic.
+  int narrow;
   uint32_t* out_u32;
   unsigned long long* out_u64;
   int* status;
@@ -634,10 +633,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t G = gridDim.x;
-  // MODE_SUM: the scores of the current stream tile, one copy per epilogue
-  // warp (after the barriers' 512 bytes).
-  unsigned long long* sc =
-      reinterpret_cast<unsigned long long*>(bars + 64) + (warp >= 2 ? warp - 2 : 0) % NE * kN;
+  // MODE_SUM: this warp's record ids for its columns of the current stream
+  // tile (after the barriers' 512 bytes).
+  constexpr int NG = NE / 4;      // epilogue groups; each takes kCols columns of every unit
+  constexpr int kCols = kN / NG;
+  uint32_t* sid = reinterpret_cast<uint32_t*>(bars + 64) + (warp >= 2 ? warp - 2 : 0) % NE * kCols;
   if (threadIdx.x == 0) {
     mbar_init(a_pk_full, 1);
     mbar_init(a_pk_empty, NX);
@@ -655,7 +655,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
     }
     for (int b = 0; b < S::kAccBufs; ++b) {
       mbar_init(acc_full + b, 1);
-      mbar_init(acc_empty + b, 4);  // the four warps of the group that takes the unit
+      mbar_init(acc_empty + b, NE);  // every epilogue warp reads every unit
     }
     *abort_flag = 0;
     fence_mbar_init();
@@ -776,40 +776,49 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
     }
   } else if (warp < kFirstExp) {
     // Epilogue: warp w reads accumulator lanes 32*(w % 4) .. +32 (resident
-    // rows quarter*32 + lane of the unit's half).  With two groups of four
-    // warps (evidence), group g takes the units u with u % 2 == g, i.e. the
-    // accumulator slot g; with one group, every unit.
-    constexpr int NG = NE / 4;
+    // rows quarter*32 + lane of the unit's half).  The NG groups of four
+    // warps split every unit's columns -- group g reads columns [g*kCols,
+    // (g+1)*kCols) -- so that each warp holds an accumulator slot for fewer
+    // loads and the slot returns to the MMA issuer sooner.
     const int quarter = warp & 3;
     const int tile_row = quarter * 32 + lane;
     const int grp = (warp - 2) >> 2;
+    const int col0 = grp * kCols;
     int64_t uu = 0;
     bool ok = true;
     for (int64_t it = blockIdx.x; it < p.n_items && ok; it += G) {
       const TcItem w = p.items[it];
       const int halves = w.own_count > 128 ? 2 : 1;
+      // This lane's resident row in each half; rows past the item's are zero
+      // operands (D = 0 against everything) and take no part.
+      bool live[2];
+      unsigned long long own_s[2] = {0ull, 0ull};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        live[h] = h < halves && h * 128 + tile_row < w.own_count;
+        if constexpr (MODE == MODE_SUM)
+          if (live[h]) own_s[h] = p.score[w.own_first + h * 128 + tile_row];
+      }
       bool cov0 = false, cov1 = false;
       uint32_t cnt0 = 0, cnt1 = 0;
-      unsigned long long sum0 = 0, sum1 = 0;
       for (int t = 0; t < w.b_tiles && ok; ++t) {
         const int64_t left = int64_t(w.str_count) - int64_t(t) * kN;
         const int nvalid = int(left < kN ? left : kN);
-        bool staged = false;
-        for (int h = 0; h < halves; ++h, ++uu) {
-          if (int(uu % NG) != grp) continue;
-          const int b = int(uu % S::kAccBufs);
-          if constexpr (MODE == MODE_SUM) {
-            if (!staged) {
-              // This tile's scores, one copy per warp, fetched before the
-              // wait for the accumulator.
-              const int64_t j0 = w.str_first + int64_t(t) * kN;
+        // MODE_SUM: record ids of this warp's columns of the tile, fetched
+        // before the wait for the accumulator (once every lane is done with
+        // the last tile's).
+        if constexpr (MODE == MODE_SUM) {
+          __syncwarp();
+          const int64_t j0 = w.str_first + int64_t(t) * kN + col0;
 #pragma unroll
-              for (int q = 0; q < kN / 32; ++q)
-                sc[lane + 32 * q] = lane + 32 * q < left ? p.score[j0 + lane + 32 * q] : 0ull;
-              __syncwarp();
-              staged = true;
-            }
+          for (int q = 0; q < kCols / 32; ++q) {
+            const int j = lane + 32 * q;
+            sid[j] = col0 + j < nvalid ? p.str_ids[j0 + j] : 0u;
           }
+          __syncwarp();
+        }
+        for (int h = 0; h < halves; ++h, ++uu) {
+          const int b = int(uu % S::kAccBufs);
           const bool got =
               mbar_wait(acc_full + b, uint32_t((uu / S::kAccBufs) & 1), p.status);
           if (!__all_sync(0xffffffffu, got) || *abort_flag) {
@@ -820,79 +829,111 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
           tc_fence_after();
           bool cov = false;
           uint32_t cnt = 0;
-          unsigned long long sum = 0;
-          // 32 columns per load; the slot is handed back to the MMA issuer as
-          // soon as the last load from it has completed, before that chunk
-          // is reduced.
+          // 32 columns per load, with their minimum; the slot is handed back
+          // to the MMA issuer as soon as this warp's last load from it has
+          // completed, before that chunk is reduced.  A chunk whose minimum
+          // is non-zero holds no hit (no count is 0) and needs no further
+          // work unless it runs past the tile's rows (zero rows, D = 0, are
+          // not hits).  Hits are rare (about one test in 600 at NSL-KDD
+          // shape), so most chunks take only the load.
 #pragma unroll 1
-          for (int c = 0; c < kN; c += 32) {
-            uint32_t v[32];
-            tmem_ld32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * 128 + c), v);
-            if (c + 32 >= kN) {
+          for (int c = col0; c < col0 + kCols; c += 32) {
+            uint32_t v[32], mn;
+            __syncwarp();  // the lanes of the last chunk's hits rejoin before the load
+            tmem_ld32_min(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * 128 + c), v, mn);
+            if (c + 32 >= col0 + kCols) {
               tc_fence_before();
               __syncwarp();
               if (lane == 0) mbar_arrive(acc_empty + b);
             }
+            const bool tail = c + 32 > nvalid;
+            if constexpr (MODE == MODE_ANY) {
+              if (!live[h] || (mn != 0u && !tail)) continue;
+              if (!tail) {
+                cov = true;
+                continue;
+              }
+            }
+            // This lane's hits among the chunk's columns (none unless its row
+            // is live and the chunk holds a zero count or runs past the
+            // tile's rows, whose zero rows give D = 0 but are not hits).
+            const bool need = live[h] && (mn == 0u || tail);
             if constexpr (MODE == MODE_SUM) {
-              uint32_t m = 0;
+              if (!__any_sync(0xffffffffu, need)) continue;
+            } else {
+              if (!need) continue;
+            }
+            uint32_t m = 0;
+            if (need) {
 #pragma unroll
               for (int i = 0; i < 32; ++i) m |= (v[i] == 0u ? 1u : 0u) << i;
-              // Columns past the tile's rows (zero rows, D = 0) are not hits.
-              if (c + 32 > nvalid) {
+              if (tail) {
                 const int r = nvalid - c;
                 m &= r <= 0 ? 0u : (1u << r) - 1u;
               }
-              while (m) {
-                const int i = __ffs(m) - 1;
-                m &= m - 1u;
-                sum += sc[c + i];
-              }
-            } else {
-              // Columns past the tile's rows (zero rows, D = 0) are made misses.
-              if (c + 32 > nvalid) {
+            }
+            if constexpr (MODE == MODE_ANY) cov |= m != 0u;
+            if constexpr (MODE == MODE_COUNT) cnt += uint32_t(__popc(m));
+            if constexpr (MODE == MODE_SUM) {
+              // Eq. 4: every record holding a pattern gains its score.
+              const unsigned long long sv = own_s[h];
+              if (p.narrow) {
+                // Per column that any lane hit, the warp sums its patterns'
+                // scores, and lane i adds column i's total to its record:
+                // one atomic per (record, chunk) instead of one per hit, so
+                // that the patterns of a record do not queue on its address.
+                uint32_t cols = __reduce_or_sync(0xffffffffu, m);
+                uint32_t mine = 0;
+                while (cols) {
+                  const int i = __ffs(cols) - 1;
+                  cols &= cols - 1u;
+                  const uint32_t tot =
+                      __reduce_add_sync(0xffffffffu, ((m >> i) & 1u) ? uint32_t(sv) : 0u);
+                  mine = lane == i ? tot : mine;
+                }
+                if (mine) atomicAdd(p.out_u64 + sid[c - col0 + lane], (unsigned long long)mine);
+              } else {
+                // Straight to the records, four hits per round so that their
+                // id loads and atomics overlap.
+                const uint32_t* ids = sid + (c - col0);
+                while (m) {
+                  int i[4];
 #pragma unroll
-                for (int i = 0; i < 32; ++i)
-                  if (c + i >= nvalid) v[i] = 1u;
-              }
-              if constexpr (MODE == MODE_ANY) {
-                uint32_t mn = v[0];
+                  for (int q = 0; q < 4; ++q) {
+                    i[q] = m ? __ffs(m) - 1 : -1;
+                    m &= m - 1u;
+                  }
+                  uint32_t r[4];
 #pragma unroll
-                for (int i = 1; i < 32; ++i) mn = min(mn, v[i]);
-                cov |= mn == 0u;
-              }
-              if constexpr (MODE == MODE_COUNT) {
+                  for (int q = 0; q < 4; ++q) r[q] = i[q] >= 0 ? ids[i[q]] : 0u;
 #pragma unroll
-                for (int i = 0; i < 32; ++i) cnt += v[i] == 0u ? 1u : 0u;
+                  for (int q = 0; q < 4; ++q)
+                    if (i[q] >= 0) atomicAdd(p.out_u64 + r[q], sv);
+                }
               }
             }
           }
           if (h == 0) {
             cov0 |= cov;
             cnt0 += cnt;
-            sum0 += sum;
           } else {
             cov1 |= cov;
             cnt1 += cnt;
-            sum1 += sum;
           }
-          __syncwarp();
         }
       }
       if (!ok) break;
-      for (int h = 0; h < halves; ++h) {
-        const int r = h * 128 + tile_row;
-        if (r >= w.own_count) continue;
-        const int64_t row = int64_t(p.own_ids[w.own_first + r]);
-        if constexpr (MODE == MODE_ANY) {
-          if (h == 0 ? cov0 : cov1) p.out_u32[row] = 1u;
-        }
-        if constexpr (MODE == MODE_COUNT) {
-          const uint32_t c = h == 0 ? cnt0 : cnt1;
-          if (c) atomicAdd(p.out_u32 + row, c);
-        }
-        if constexpr (MODE == MODE_SUM) {
-          const unsigned long long v = h == 0 ? sum0 : sum1;
-          if (v) atomicAdd(p.out_u64 + row, v);
+      if constexpr (MODE != MODE_SUM) {
+        for (int h = 0; h < halves; ++h) {
+          if (!live[h]) continue;
+          const int64_t row = int64_t(p.own_ids[w.own_first + h * 128 + tile_row]);
+          if constexpr (MODE == MODE_ANY) {
+            if (h == 0 ? cov0 : cov1) p.out_u32[row] = 1u;
+          }
+          if constexpr (MODE == MODE_COUNT) {
+            const uint32_t c = h == 0 ? cnt0 : cnt1;
+            if (c) atomicAdd(p.out_u32 + row, c);
+          }
         }
       }
     }
@@ -990,6 +1031,15 @@ static cudaError_t run_fused(const FusedParams& p, cudaStream_t s) {
 }
 
 namespace {
+// Test hook: IG_EVIDENCE_WIDE_SUMS=1 in the environment makes the evidence
+// kernel add every hit to its record with a 64-bit atomic even where the
+// scores would allow 32-bit warp sums per record, so that tests can check
+// that path on ordinary data (both give the same sums).
+bool force_wide_sums() {
+  const char* v = std::getenv("IG_EVIDENCE_WIDE_SUMS");
+  return v && v[0] == '1';
+}
+
 // Pinned staging for the work items, one per host thread; reused once the
 // copy out of it (recorded by `done`) has finished.
 struct TcStaging {
@@ -1002,13 +1052,18 @@ thread_local TcStaging g_tc_staging;
 
 cudaError_t indexed_subset_tc(int mode, const RecordIndex& idx, const KeyedIndex& kx,
                               uint32_t* out_u32, unsigned long long* out_u64, int* status,
-                              int64_t* tests_out, int prof_stage, cudaStream_t s) {
+                              int64_t* tests_out, int prof_stage, uint64_t score_max,
+                              cudaStream_t s) {
   *tests_out = 0;
   const int L = idx.L, KT = idx.KT;
   if (kx.n == 0 || idx.n_rows == 0 || !tc_supported(KT)) return cudaErrorInvalidValue;
-  // The result side is resident: patterns (keyed) for ANY / COUNT, records
-  // (multi, complemented) for SUM.
-  const bool own_multi = mode == MODE_SUM;
+  // Patterns (keyed) are resident and records (multi, complemented) stream,
+  // in every mode: an item group holds far fewer patterns than records, so
+  // items are long (about 90 stream tiles at NSL-KDD shape, against 6-9 with
+  // the records resident) and the resident rows are expanded 10-15x less
+  // often.  ANY / COUNT results stay per resident row; SUM adds each
+  // pattern's score to the records containing it, per hit.
+  const bool own_multi = false;
   const uint32_t* own_off = own_multi ? idx.h_off.data() : kx.h_off.data();
   const uint32_t* str_off = own_multi ? kx.h_off.data() : idx.h_off.data();
   std::vector<TcItem> items;
@@ -1071,7 +1126,9 @@ cudaError_t indexed_subset_tc(int mode, const RecordIndex& idx, const KeyedIndex
                   own_multi ? kx.rows : idx.rows,
                   own_multi ? 1 : 0,
                   own_multi ? idx.ids : kx.ids,
-                  own_multi ? kx.score : nullptr,
+                  mode == MODE_SUM ? kx.score : nullptr,
+                  idx.ids,
+                  mode == MODE_SUM && score_max < (uint64_t(1) << 27) && !force_wide_sums() ? 1 : 0,
                   out_u32,
                   out_u64,
                   status};

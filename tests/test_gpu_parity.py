@@ -312,6 +312,19 @@ def test_nsl15k_score_parity(nsl15k):
     assert_scores_equal(m, om, oracle.encode(w.test_codes, w.cards))
 
 
+def test_evidence_wide_sums_path(nsl15k_oracle, monkeypatch):
+    # The tensor-core evidence kernel sums a warp's hits per record in 32-bit
+    # shared partial sums when every score is below 2^26 (always true at
+    # these shapes), and otherwise adds each hit with its own 64-bit atomic;
+    # the test hook forces the second path on the same data.
+    w, om = nsl15k_oracle
+    m, _ = _workload_fit(w, kernel=4)
+    test = oracle.encode(w.test_codes, w.cards)
+    assert_scores_equal(m, om, test)
+    monkeypatch.setenv("IG_EVIDENCE_WIDE_SUMS", "1")
+    assert_scores_equal(m, om, test)
+
+
 def test_nsl15k_deterministic_and_permutation_invariant(nsl15k):
     w, m, om = nsl15k
     perm = np.random.default_rng(5).permutation(w.train_codes.shape[0])

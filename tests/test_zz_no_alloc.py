@@ -58,3 +58,43 @@ def test_limits_are_rejected(model_and_rows):
     rc = lib.ig_score_noalloc(model.handle, ctypes.c_void_p(host_rows.ctypes.data),
                               host_rows.shape[0], None, None, None, None)
     assert rc == -1 and b"device memory" in lib.ig_last_error()
+
+
+@pytest.mark.parametrize("n_items", [150, 300, 420])   # K = 3, 5, 7: row stride < padded width
+def test_odd_word_counts_match_oracle(n_items):
+    # A record of K words is read with its own stride K while the kernels
+    # work on the padded width (4 or 8 words); the words past K must read
+    # as zero.  Two calls in a row again, against the CPU oracle.
+    import oracle
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ig.build()
+    rng = np.random.default_rng(n_items)
+    rows = igdata.random_words(rng, 260, n_items, "three_quarters")
+    labels = np.zeros(260, np.uint8)
+    labels[rng.permutation(260)[:120]] = 1
+    model = ig.ig_fit(torch.from_numpy(rows.view(np.int64)).cuda(),
+                      torch.from_numpy(labels).cuda())
+    om = oracle.fit(rows, labels)
+    # Random records (mostly no pattern inside) and training records (their
+    # own patterns inside), a different mix in each call.
+    for test in (np.concatenate([igdata.random_words(rng, 200, n_items, "three_quarters"),
+                                 rows[:133]]),
+                 rows[130:221]):
+        A, N, lab = ig.ig_score_noalloc(model, torch.from_numpy(test.view(np.int64)).cuda())
+        oA, oN, olab = oracle.score(om, test)
+        assert np.array_equal(A.cpu().numpy(), oA) and np.array_equal(N.cpu().numpy(), oN)
+        assert np.array_equal(lab.cpu().numpy(), olab)
+        assert int((A > 0).sum()) + int((N > 0).sum()) > 0
+
+
+def test_width_mismatch_rejected_before_launch(model_and_rows):
+    model, test, _ = model_and_rows
+    launches = ig.launch_count()
+    with pytest.raises(ValueError, match="words per record"):
+        ig.ig_score_noalloc(model, test[:, :2].contiguous())
+    with pytest.raises(ValueError, match="64-bit words"):
+        ig.ig_score_noalloc(model, test.to(torch.int32))
+    with pytest.raises(ValueError, match="words per record"):
+        ig.ig_score(model, test[:, :3].contiguous())
+    assert ig.launch_count() == launches
