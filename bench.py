@@ -51,9 +51,9 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 FALLBACK_BF16_TFLOPS = 1900.0
 # Integer-pipe peak of the subset test: LOP3 instructions per SM per clock
-# (4 sub-partitions x 16 lanes; a LOP3 throughput probe on GB300 measured
-# 60.8 per SM per clock against the 2,070 MHz attribute clock while the SM
-# ran near 1,995 MHz) x 152 SMs x the maximum SM clock.
+# (4 sub-partitions x 16 lanes) x 152 SMs x the maximum SM clock.  The
+# library's LOP3 probe (ig_probe, run at the start of every bench) measured
+# 2.01e13 per second on GB300, the same figure at 2,070 MHz.
 LOP3_PER_SM_PER_CLK = 64
 
 
@@ -167,6 +167,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     ig.build()
     ig.load()
+    probes = run_probes(ig)
     if args.workload == "batched":
         return run_batched(args, ig, torch, rank, world, local)
     if args.workload == "served":
@@ -285,6 +286,9 @@ def run_ours(args):
                         f"around the {top} stage only",
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
+        "probes": {k: (round(v / 1e12, 2) if isinstance(v, float) else v)
+                   for k, v in probes.items()},
+        "probes_unit": "1e12 per second (LOP3 instructions, bytes of L2 loads, MMA flops)",
     }
     kt = 1
     while kt < w.n_words:
@@ -546,12 +550,27 @@ def stage_roofline(name, ms, launches, work, info, K, clocks, steps, workload=No
                     "peak": peak, "unit": "TFLOP/s (FP8 0/1 GEMM)", "frac": achieved / peak,
                     "peak_source": ("measured bf16 burst x 2 (nominal FP8/BF16 ratio)"
                                     if peaks else "fallback bf16 x 2")})
+    elif name == "pair_insert" and PROBED.get("l2_random"):
+        # The dedup table (8 bytes a slot) and the records stay in L2; each
+        # pair (the records of Eq. 1 included: i = j) probes one slot at a
+        # hashed address and each distinct key claims one: random L2
+        # accesses, rated against this GPU's measured rate of random
+        # 16-byte L2 loads (ig_probe, run by this bench before timing).
+        U = sum(info["n_candidates"]) * steps
+        pairs = (sum(info["n_pairs"]) + sum(info["n_train"])) * steps
+        acc = pairs + U
+        achieved = acc / (ms * 1e-3) / 1e9
+        peak = PROBED["l2_random"] / 16 / 1e9
+        out.update({"bound": "l2", "achieved": achieved, "peak": peak,
+                    "unit": "G random L2 accesses/s", "frac": achieved / peak,
+                    "algorithmic_accesses_per_launch": acc // max(1, launches),
+                    "peak_source": "measured: ig_probe L2_RANDOM (16-byte loads at random "
+                                   "offsets of a 48 MiB buffer) on this GPU"})
     else:
         # Byte models (per timed step x steps) of the memory-bound stages:
-        #   pair_insert: a hash set of K-word keys -- every pair compares its
-        #     key with one stored key (8K B) and every distinct key is
-        #     written once (8K B); the pairs include each record with itself
-        #     (the records of Eq. 1);
+        #   pair_insert (without a probed L2 rate): a hash set of K-word
+        #     keys -- every pair compares its key with one stored key (8K B)
+        #     and every distinct key is written once (8K B);
         #   compact: every distinct key written once (8K B).
         U = sum(info["n_candidates"]) * steps
         pairs = (sum(info["n_pairs"]) + sum(info["n_train"])) * steps
@@ -563,6 +582,26 @@ def stage_roofline(name, ms, launches, work, info, K, clocks, steps, workload=No
                     "algorithmic_bytes_per_launch": nbytes // max(1, launches),
                     "peak_source": "measured" if peaks else "fallback"})
     out["traffic"] = dram_traffic(out["kernel"], workload)
+    return out
+
+
+# Rates measured by ig_probe on this GPU at the start of the run.
+PROBED = {}
+
+
+def run_probes(ig):
+    """Throughput probes of the units the kernels are bound by (ig_probe):
+    LOP3 rate, L2 streaming and random 16-byte loads, FP8 tcgen05 MMA rate."""
+    out = {}
+    for name, arg in (("lop3", 0), ("l2_read", 48), ("l2_random", 48),
+                      ("mma_f8_tmem", 128), ("mma_f8_tmem", 128 | (2 << 12))):
+        key = name if name != "mma_f8_tmem" or arg == 128 else "mma_f8_tmem_ring2"
+        try:
+            out[key] = ig.probe(name, arg)["rate"]
+        except Exception as e:  # a probe that fails leaves its figure out
+            out[key + "_error"] = str(e)[:120]
+    PROBED.clear()
+    PROBED.update({k: v for k, v in out.items() if not k.endswith("_error")})
     return out
 
 

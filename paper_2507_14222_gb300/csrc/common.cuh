@@ -73,10 +73,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Waits for the given phase parity; false (and ST_TIMEOUT set) if the poll
-// limit is reached first.
+// limit (kMbarPollLimit unless given) is reached first.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
-                                          int* status) {
-  for (uint32_t it = 0; it < kMbarPollLimit; ++it)
+                                          int* status, uint32_t limit = kMbarPollLimit) {
+  for (uint32_t it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   set_status(status, ST_TIMEOUT);
   return false;

@@ -554,6 +554,13 @@ struct FusedParams {
   // column's hits over a warp's 32 patterns fits in 32 bits; 0: every hit
   // goes to its record by its own 64-bit atomic.
   int narrow;
+  // Polls a wait for a full stage, a free stage or an accumulator may take
+  // (0: kMbarPollLimit); the waits for copies and MMAs in flight before the
+  // CTA ends always take the full limit.  And, for tests of the timeout
+  // path, the unit before whose MMAs the issuer waits on a barrier that
+  // never completes (-1: none).
+  uint32_t poll_limit;
+  int64_t stall_unit;
   uint32_t* out_u32;
   unsigned long long* out_u64;
   int* status;
@@ -628,11 +635,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
   uint64_t* b_x_empty = b_x_full + XS;
   uint64_t* acc_full = b_x_empty + XS;
   uint64_t* acc_empty = acc_full + S::kAccBufs;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + S::kAccBufs);
+  uint64_t* never = acc_empty + S::kAccBufs;  // no thread ever arrives on it
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t G = gridDim.x;
+  const uint32_t lim = p.poll_limit ? p.poll_limit : kMbarPollLimit;
   // MODE_SUM: this warp's record ids for its columns of the current stream
   // tile (after the barriers' 512 bytes).
   constexpr int NG = NE / 4;      // epilogue groups; each takes kCols columns of every unit
@@ -657,6 +666,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
       mbar_init(acc_full + b, 1);
       mbar_init(acc_empty + b, NE);  // every epilogue warp reads every unit
     }
+    mbar_init(never, 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -675,8 +685,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
   if (warp == 0) {
     if (lane == 0) {
       // Producer of packed tiles.
-      int64_t tt = 0, ii = 0, issued_b = 0;
-      bool issued_a = false;
+      int64_t tt = 0, ii = 0, issued_b = 0, issued_a = 0;
       auto tile_src = [&](const TcItem& w, int t) {
         return p.str_rows + (w.str_first + int64_t(t) * kN) * KT;
       };
@@ -686,17 +695,17 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
       };
       for (int64_t it = blockIdx.x; it < p.n_items && !*abort_flag; it += G, ++ii) {
         const TcItem w = p.items[it];
-        if (!mbar_wait(a_pk_empty, uint32_t((ii & 1) ^ 1), p.status)) {
+        if (!mbar_wait(a_pk_empty, uint32_t((ii & 1) ^ 1), p.status, lim)) {
           *abort_flag = 1;
           break;
         }
         const uint32_t abytes = uint32_t(w.own_count) * KT * 8;
         mbar_arrive_expect_tx(a_pk_full, abytes);
         bulk_g2s(A_pk, p.own_rows + w.own_first * KT, abytes, a_pk_full);
-        issued_a = true;
+        ++issued_a;
         for (int t = 0; t < w.b_tiles; ++t, ++tt) {
           const int s = int(tt % PKS);
-          if (!mbar_wait(b_pk_empty + s, uint32_t(((tt / PKS) & 1) ^ 1), p.status) ||
+          if (!mbar_wait(b_pk_empty + s, uint32_t(((tt / PKS) & 1) ^ 1), p.status, lim) ||
               *abort_flag) {
             *abort_flag = 1;
             break;
@@ -708,8 +717,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
         }
       }
       if (*abort_flag) {
-        // Copies in flight must land before the CTA may finish.
-        if (issued_a) mbar_wait(a_pk_full, uint32_t((ii - (ii > 0 ? 1 : 0)) & 1), p.status);
+        // Copies in flight must land before the CTA may finish: the last
+        // resident copy (the k-th completes phase k of a_pk_full) and the
+        // stream copies of the last PKS tiles (earlier ones have been
+        // consumed, or their stage could not have been reused).
+        if (issued_a) mbar_wait(a_pk_full, uint32_t((issued_a - 1) & 1), p.status);
         for (int64_t t = (issued_b > PKS ? issued_b - PKS : 0); t < issued_b; ++t)
           mbar_wait(b_pk_full + (t % PKS), uint32_t((t / PKS) & 1), p.status);
       }
@@ -721,13 +733,14 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
       // the accumulator slots in turn, so the epilogue of one unit overlaps
       // the MMAs of the next.
       int64_t tt = 0, ii = 0, uu = 0;
+      int64_t bx_last = -1, ax_last = -1;  // last tile / item whose stage / rows were released
       bool ok = true;
       for (int64_t it = blockIdx.x; it < p.n_items && ok; it += G, ++ii) {
         const TcItem w = p.items[it];
         const int halves = w.own_count > 128 ? 2 : 1;
         const int ab = S::kABufs == 2 ? int(ii & 1) : 0;
         const uint32_t aph = uint32_t((S::kABufs == 2 ? (ii >> 1) : ii) & 1);
-        if (!mbar_wait(a_x_full + ab, aph, p.status) || *abort_flag) {
+        if (!mbar_wait(a_x_full + ab, aph, p.status, lim) || *abort_flag) {
           *abort_flag = 1;
           ok = false;
           break;
@@ -736,7 +749,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
         const uint32_t a_tm = tmem + uint32_t(S::kAccCols + ab * S::kHalves * S::kACols);
         for (int t = 0; t < w.b_tiles && ok; ++t, ++tt) {
           const int s = int(tt % XS);
-          if (!mbar_wait(b_x_full + s, uint32_t((tt / XS) & 1), p.status) || *abort_flag) {
+          if (!mbar_wait(b_x_full + s, uint32_t((tt / XS) & 1), p.status, lim) || *abort_flag) {
             *abort_flag = 1;
             ok = false;
             break;
@@ -746,7 +759,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
           const uint64_t bdesc = sw128_desc(smem_u32(B_x + size_t(s) * S::kImgB));
           for (int h = 0; h < halves; ++h, ++uu) {
             const int b = int(uu % S::kAccBufs);
-            if (!mbar_wait(acc_empty + b, uint32_t(((uu / S::kAccBufs) & 1) ^ 1), p.status) ||
+            if ((uu == p.stall_unit && !mbar_wait(never, 0, p.status, lim)) ||
+                !mbar_wait(acc_empty + b, uint32_t(((uu / S::kAccBufs) & 1) ^ 1), p.status, lim) ||
                 *abort_flag) {
               *abort_flag = 1;
               ok = false;
@@ -766,13 +780,23 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
           }
           if (!ok) break;
           tc_commit(b_x_empty + s);
+          bx_last = tt;
         }
         if (!ok) break;
         tc_commit(a_x_empty + ab);  // the resident rows are free once this item's MMAs are done
+        ax_last = ii;
       }
+      // Before the CTA may finish, every MMA must be done (the last commit
+      // to an accumulator) and every commit's arrival must have landed on
+      // its barrier (the last stage and resident releases).
       if (uu > 0)
         mbar_wait(acc_full + ((uu - 1) % S::kAccBufs), uint32_t(((uu - 1) / S::kAccBufs) & 1),
                   p.status);
+      if (bx_last >= 0)
+        mbar_wait(b_x_empty + (bx_last % XS), uint32_t((bx_last / XS) & 1), p.status);
+      if (ax_last >= 0)
+        mbar_wait(a_x_empty + (S::kABufs == 2 ? int(ax_last & 1) : 0),
+                  uint32_t((S::kABufs == 2 ? (ax_last >> 1) : ax_last) & 1), p.status);
     }
   } else if (warp < kFirstExp) {
     // Epilogue: warp w reads accumulator lanes 32*(w % 4) .. +32 (resident
@@ -820,7 +844,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
         for (int h = 0; h < halves; ++h, ++uu) {
           const int b = int(uu % S::kAccBufs);
           const bool got =
-              mbar_wait(acc_full + b, uint32_t((uu / S::kAccBufs) & 1), p.status);
+              mbar_wait(acc_full + b, uint32_t((uu / S::kAccBufs) & 1), p.status, lim);
           if (!__all_sync(0xffffffffu, got) || *abort_flag) {
             *abort_flag = 1;
             ok = false;
@@ -946,8 +970,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
       const TcItem w = p.items[it];
       const int ab = S::kABufs == 2 ? int(ii & 1) : 0;
       const uint32_t aph = uint32_t((S::kABufs == 2 ? (ii >> 1) : ii) & 1);
-      bool got = mbar_wait(a_pk_full, uint32_t(ii & 1), p.status) &&
-                 mbar_wait(a_x_empty + ab, aph ^ 1u, p.status);
+      bool got = mbar_wait(a_pk_full, uint32_t(ii & 1), p.status, lim) &&
+                 mbar_wait(a_x_empty + ab, aph ^ 1u, p.status, lim);
       if (!__all_sync(0xffffffffu, got) || *abort_flag) {
         *abort_flag = 1;
         break;
@@ -988,8 +1012,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
       }
       for (int t = 0; t < w.b_tiles; ++t, ++tt) {
         const int sp = int(tt % PKS), sx = int(tt % XS);
-        got = mbar_wait(b_pk_full + sp, uint32_t((tt / PKS) & 1), p.status) &&
-              mbar_wait(b_x_empty + sx, uint32_t(((tt / XS) & 1) ^ 1), p.status);
+        got = mbar_wait(b_pk_full + sp, uint32_t((tt / PKS) & 1), p.status, lim) &&
+              mbar_wait(b_x_empty + sx, uint32_t(((tt / XS) & 1) ^ 1), p.status, lim);
         if (!__all_sync(0xffffffffu, got) || *abort_flag) {
           *abort_flag = 1;
           ok = false;
@@ -1038,6 +1062,20 @@ namespace {
 bool force_wide_sums() {
   const char* v = std::getenv("IG_EVIDENCE_WIDE_SUMS");
   return v && v[0] == '1';
+}
+
+// Test hook for the timeout path: IG_TEST_STALL_UNIT=u makes every CTA of
+// the fused kernel wait, before the MMAs of its u-th unit, on a barrier that
+// never completes, with the stage and accumulator waits limited to a few
+// polls, so that the kernel reports ST_TIMEOUT, drains the copies and MMAs
+// it has in flight and ends.  Unset (the default): no stall.
+void test_stall(uint32_t* poll_limit, int64_t* stall_unit) {
+  *poll_limit = 0;
+  *stall_unit = -1;
+  const char* v = std::getenv("IG_TEST_STALL_UNIT");
+  if (!v || !*v) return;
+  *stall_unit = std::strtoll(v, nullptr, 10);
+  *poll_limit = 64;
 }
 
 // Pinned staging for the work items, one per host thread; reused once the
@@ -1129,9 +1167,12 @@ cudaError_t indexed_subset_tc(int mode, const RecordIndex& idx, const KeyedIndex
                   mode == MODE_SUM ? kx.score : nullptr,
                   idx.ids,
                   mode == MODE_SUM && score_max < (uint64_t(1) << 27) && !force_wide_sums() ? 1 : 0,
+                  0u,
+                  -1,
                   out_u32,
                   out_u64,
                   status};
+    test_stall(&p.poll_limit, &p.stall_unit);
     void* tok = prof_stage >= 0 ? prof_begin(prof_stage, s) : nullptr;
 #define IG_TCF_CASE(KTV)                                                   \
   case KTV:                                                                \

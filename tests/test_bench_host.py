@@ -80,6 +80,21 @@ def test_pair_insert_byte_model(fixed_peaks):
     assert r["peak"] == PEAKS["hbm_gbs"]
 
 
+def test_pair_insert_l2_accesses(fixed_peaks, monkeypatch):
+    # With a probed random-L2 rate: one slot access per pair and one claim
+    # per distinct key, against the probed 16-byte loads per second.
+    monkeypatch.setattr(bench, "PROBED", {"l2_random": 16.0e12})
+    i = info()
+    r = bench.stage_roofline("pair_insert", 1.0, 2, 0, i, 8, None, 3)
+    pairs = (45 + 190 + 10 + 20) * 3
+    keys = (100 + 200) * 3
+    assert r["bound"] == "l2"
+    assert r["algorithmic_accesses_per_launch"] == (pairs + keys) // 2
+    assert r["achieved"] == pytest.approx((pairs + keys) / 1e-3 / 1e9)
+    assert r["peak"] == pytest.approx(1000.0)
+    assert r["frac"] == pytest.approx(r["achieved"] / 1000.0)
+
+
 def test_roofline_head_from_timed_steps_breakdown_from_warmup(fixed_peaks):
     warm = {"pair_insert": (4.0, 4, 0), "evidence_idx": (2.0, 4, 10**9)}
     timed = {"pair_insert": (3.0, 6, 0), "evidence_idx": (0.0, 0, 10**9)}
