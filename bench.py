@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--served-flows", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="leave out the batched and served comparisons of the default line")
     ap.add_argument("--kernel", type=int, default=0,
                     help="subset-test form: 0 default, 1 integer pipe, 2 tensor cores, "
                          "3 item index, 4 item index on the tensor cores")
@@ -297,6 +299,11 @@ def run_ours(args):
                                 warm=warm, warm_steps=n_warm)
     if not args.no_e2e:
         line["e2e"] = e2e_host_buffers(ig, w, tests, max(2, min(args.steps, 5)))
+    if not args.no_extras and world == 1:
+        # The batched and served forms against their plain counterparts, on
+        # the same GPU in the same run (config 4 and config 5 shapes).
+        line["batched"] = measure_batched(args, ig, torch, local, 3, 1)
+        line["served"] = measure_served(args, ig, torch, local)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line), flush=True)
@@ -304,14 +311,12 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def run_batched(args, ig, torch, rank, world, local):
-    """64 independent problems per step: batched fit vs one ig_fit per problem.
-
-    Both forms run in the same process on the same inputs; their models must
-    be byte-identical.  Scoring runs per problem in both.
-    """
-    from paper_2507_14222_gb300 import replicas
-    probs = igdata.batched(igdata.BATCHED_PROBLEMS, replicas.replica_seed(2000, rank))
+def measure_batched(args, ig, torch, local, steps, warmup, seed=2000):
+    """64 independent problems per step: one ig_fit_batched call against one
+    ig_fit per problem (the plain per-problem launch), same inputs, same
+    process; scoring runs per problem in both.  The models must be
+    byte-identical.  Returns the measurements (ms per step of each form)."""
+    probs = igdata.batched(igdata.BATCHED_PROBLEMS, seed)
     dev = []
     for w in probs:
         dev.append((torch.from_numpy(w.train_codes.view(np.int16)).cuda(),
@@ -324,7 +329,7 @@ def run_batched(args, ig, torch, rank, world, local):
         return [(ig.ig_encode(c, cards), lab, ig.ig_encode(t, cards)) for c, lab, t, cards in dev]
 
     # Tiling and subset-test form per (K, size) group, tuned once per GPU
-    # (cached), outside the timed region.
+    # (cached), outside the timed region; both forms use the same choices.
     from paper_2507_14222_gb300 import autotune
     tuner = autotune.Autotuner()
     enc0 = encode_all()
@@ -340,14 +345,24 @@ def run_batched(args, ig, torch, rank, world, local):
                                        subset_kernel=args.kernel,
                                        per_problem_params=per_params)
         else:
-            models = [ig.ig_fit(r, lab, subset_kernel=args.kernel) for r, lab, _ in enc]
+            models = []
+            for (r, lab, _), pp in zip(enc, per_params):
+                if pp is None:
+                    models.append(ig.ig_fit(r, lab, subset_kernel=args.kernel))
+                else:
+                    models.append(ig.ig_fit(r, lab, subset_kernel=pp.subset_kernel,
+                                            index_max_q=pp.index_max_q,
+                                            index_flip_factor=pp.index_flip_factor))
         for mdl, (_, _, te) in zip(models, enc):
             ig.ig_score(mdl, te)
         return models
 
-    def timed(batched, steps):
-        ms = []
-        for _ in range(steps):
+    def timed(batched, n):
+        ms, last = [], None
+        for _ in range(n):
+            if last:
+                for mdl in last:
+                    mdl.free()
             flush.zero_()
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
@@ -359,25 +374,16 @@ def run_batched(args, ig, torch, rank, world, local):
             last = models
         return ms, last
 
-    # The last warm-up step carries stage events (the breakdown); the timed
-    # steps of both forms run without them.
-    for i in range(args.warmup):
-        if i == args.warmup - 1:
-            ig.prof_select(None)
-            ig.prof_reset()
-            ig.prof_enable(True)
-        for mdl in step(True):
-            mdl.free()
+    for _ in range(warmup):
+        for form in (True, False):
+            for mdl in step(form):
+                mdl.free()
     torch.cuda.synchronize()
-    ig.prof_enable(False)
-    stages = ig.prof_read()
     launches0 = ig.launch_count()
-    replicas.barrier()
-    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        ms_b, models_b = timed(True, args.steps)
-    launches = ig.launch_count() - launches0
-    ms_s, models_s = timed(False, max(1, min(args.steps, 3)))
+        ms_b, models_b = timed(True, steps)
+    launches = (ig.launch_count() - launches0) // max(1, steps)
+    ms_s, models_s = timed(False, steps)
     identical = True
     total_tests = 0
     for w, mb, ms_ in zip(probs, models_b, models_s):
@@ -388,43 +394,57 @@ def run_batched(args, ig, torch, rank, world, local):
                                                                    ms_.patterns(cls)))
         mb.free()
         ms_.free()
-    total_ms, job_tests = replicas.job_totals(sum(ms_b), total_tests, device="cuda")
+    return {"problems": len(probs), "ms_per_step": statistics.median(ms_b),
+            "per_problem_ms_per_step": statistics.median(ms_s),
+            "speedup_vs_per_problem": statistics.median(ms_s) / statistics.median(ms_b),
+            "identical_to_per_problem": bool(identical), "tests_per_step": int(total_tests),
+            "value": total_tests / (statistics.median(ms_b) * 1e-3) / 1e9, "unit": UNIT,
+            "steps": steps, "gpu_launches_per_step": int(launches), "autotuned": tuned,
+            "records": [int(w.train_codes.shape[0] + w.test_codes.shape[0]) for w in probs],
+            "l2": "flushed before every timed step (512 MiB write)",
+            "clocks": clk.summary()}
+
+
+def run_batched(args, ig, torch, rank, world, local):
+    """The batched workload as its own bench line."""
+    from paper_2507_14222_gb300 import replicas
+    r = measure_batched(args, ig, torch, local, args.steps, args.warmup,
+                        replicas.replica_seed(2000, rank))
+    total_ms, job_tests = replicas.job_totals(r["ms_per_step"] * args.steps,
+                                              r["tests_per_step"] * args.steps, device="cuda")
     ms_per_step = total_ms / args.steps
     if rank != 0:
         return
     line = {
-        "metric": METRIC, "value": job_tests / (ms_per_step * 1e-3) / 1e9,
+        "metric": METRIC, "value": job_tests / args.steps / (ms_per_step * 1e-3) / 1e9,
         "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": f"ig-batched-{len(probs)}-problems",
-                   "records": [int(w.train_codes.shape[0] + w.test_codes.shape[0])
-                               for w in probs][:8] + ["..."],
-                   "l2": "flushed before every timed step (512 MiB write)"},
-        "per_problem_launch_ms_per_step": statistics.median(ms_s),
-        "speedup_vs_per_problem": statistics.median(ms_s) / statistics.median(ms_b),
-        "identical_to_per_problem": bool(identical),
-        "autotuned": tuned,
-        "stages_ms_per_step (summed over concurrent lanes; profiled warm-up step)":
-            {k: round(v[0], 3) for k, v in stages.items() if v[1]},
-        "gpu_launches": int(launches), "clocks": clk.summary(),
+        "config": {"workload": f"ig-batched-{r['problems']}-problems",
+                   "records": r["records"][:8] + ["..."], "l2": r["l2"]},
+        "per_problem_launch_ms_per_step": r["per_problem_ms_per_step"],
+        "speedup_vs_per_problem": r["speedup_vs_per_problem"],
+        "identical_to_per_problem": r["identical_to_per_problem"],
+        "autotuned": r["autotuned"], "gpu_launches": r["gpu_launches_per_step"] * args.steps,
+        "clocks": r["clocks"],
     }
     print(json.dumps(line), flush=True)
 
 
-def run_served(args, ig, torch, rank, world, local):
-    """Served scoring: a continuous-batching server over resident pattern sets.
+def measure_served(args, ig, torch, local, seed=1005):
+    """Served scoring of one Poisson request stream, two ways:
 
-    1. Saturated throughput: every request submitted at once.
-    2. A Poisson request stream at 0.8x that rate, replayed in real time:
-       flows/s and per-request latency (submission -> results in host memory).
-    Every flow's (A, N, label) is checked against one ig_score call over all
-    flows.
-    """
+    1. the continuous-batching server (ig_server_*): requests are submitted
+       at their arrival times and batched as slots and memory free up;
+    2. plain: one ig_score call per request, in arrival order, on one host
+       thread (each request waits for the ones before it).
+
+    The arrival rate is 0.8x the server's saturated rate (every request
+    submitted at once), measured first.  Latency runs from a request's
+    arrival to its results being in host memory.  Every flow's (A, N, label)
+    from both ways is checked against one ig_score call over all flows."""
     import threading
-    from paper_2507_14222_gb300 import replicas
-    sw = igdata.served(args.served_patterns, args.served_flows,
-                       replicas.replica_seed(1005, rank))
+    sw = igdata.served(args.served_patterns, args.served_flows, seed)
     words = [ig.ig_encode(torch.from_numpy(sw.patterns[c].view(np.int16)).cuda(), sw.cards)
              for c in (0, 1)]
     model = ig.ig_model_from_patterns(words[0], sw.support[0], words[1], sw.support[1])
@@ -460,39 +480,74 @@ def run_served(args, ig, torch, rank, world, local):
         th.join()
         return out, time.perf_counter() - t0
 
+    def run_plain(gaps_s):
+        out, lat = [], []
+        t0 = time.perf_counter()
+        due = t0
+        for i, r in enumerate(reqs):
+            due += gaps_s[i]
+            delay = due - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            A, N, lab = ig.ig_score(model, r)
+            lat.append((time.perf_counter() - due) * 1e3)
+            out.append((A, N, lab))
+        return out, lat, time.perf_counter() - t0
+
     run(None)                                   # warm-up pass
     sat, sat_s = run(None)
-    sat_fps = sw.request_sizes.sum() / sat_s
+    flows_done = int(sw.request_sizes.sum())
+    sat_fps = flows_done / sat_s
     rate_req = 0.8 * sat_fps / sw.request_sizes.mean()
+    gaps = sw.unit_gaps / rate_req
     b0, f0 = server.stats()
     with ClockSampler(local) as clk:
-        paced, paced_s = run(sw.unit_gaps / rate_req)
+        paced, paced_s = run(gaps)
     b1, f1 = server.stats()
     lat = np.array([o[3] for o in paced])
     got = [np.concatenate([o[k] for o in paced]) for k in range(3)]
     identical = all(np.array_equal(g, r) for g, r in zip(got, ref))
     server.close()
-    flows_done = int(sw.request_sizes.sum())
-    paced_ms, job_flows = replicas.job_totals(paced_s * 1e3, flows_done, device="cuda")
-    paced_s = paced_ms * 1e-3
+    plain, plain_lat, plain_s = run_plain(gaps)
+    got = [np.concatenate([o[k] for o in plain]) for k in range(3)]
+    plain_identical = all(np.array_equal(g, r) for g, r in zip(got, ref))
+    plain_lat = np.array(plain_lat)
+    return {"workload": sw.name, "patterns_per_class": args.served_patterns,
+            "flows": flows_done, "requests": int(len(reqs)),
+            "request_sizes": "log-uniform in [1, 4096]",
+            "arrivals": "Poisson at 0.8x the server's saturated rate",
+            "server": {"slots": 3, "max_batch_flows": 65536, "memory_budget_bytes": 1 << 30},
+            "flows_per_s": flows_done / paced_s, "seconds": paced_s,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "saturated_flows_per_s": sat_fps,
+            "saturated_p50_ms": float(np.percentile([o[3] for o in sat], 50)),
+            "batches": int(b1 - b0), "mean_flows_per_batch": (f1 - f0) / max(1, b1 - b0),
+            "identical_to_one_shot": bool(identical),
+            "plain": {"form": "one ig_score per request in arrival order, host buffers",
+                      "flows_per_s": flows_done / plain_s, "seconds": plain_s,
+                      "p50_ms": float(np.percentile(plain_lat, 50)),
+                      "p99_ms": float(np.percentile(plain_lat, 99)),
+                      "identical_to_one_shot": bool(plain_identical)},
+            "clocks": clk.summary()}
+
+
+def run_served(args, ig, torch, rank, world, local):
+    """The served workload as its own bench line."""
+    from paper_2507_14222_gb300 import replicas
+    r = measure_served(args, ig, torch, local, replicas.replica_seed(1005, rank))
+    paced_ms, job_flows = replicas.job_totals(r["seconds"] * 1e3, r["flows"], device="cuda")
     if rank != 0:
         return
     line = {
-        "metric": METRIC, "value": job_flows / paced_s, "unit": "flows/s",
+        "metric": METRIC, "value": job_flows / (paced_ms * 1e-3), "unit": "flows/s",
         "n_gpus": world, "steps": 1, "warmup": 1,
-        "ms_per_step": paced_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": paced_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": sw.name, "patterns_per_class": args.served_patterns,
-                   "flows": flows_done, "requests": int(len(reqs)),
-                   "request_sizes": "log-uniform in [1, 4096]",
-                   "arrivals": "Poisson at 0.8x the saturated rate",
-                   "server": {"slots": 3, "max_batch_flows": 65536,
-                              "memory_budget_bytes": 1 << 30}},
-        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-        "saturated_flows_per_s": sat_fps,
-        "saturated_p50_ms": float(np.percentile([o[3] for o in sat], 50)),
-        "batches": int(b1 - b0), "mean_flows_per_batch": (f1 - f0) / max(1, b1 - b0),
-        "identical_to_one_shot": bool(identical), "clocks": clk.summary(),
+        "config": {k: r[k] for k in ("workload", "patterns_per_class", "flows", "requests",
+                                     "request_sizes", "arrivals", "server")},
+        **{k: r[k] for k in ("p50_ms", "p99_ms", "saturated_flows_per_s", "saturated_p50_ms",
+                             "batches", "mean_flows_per_batch", "identical_to_one_shot",
+                             "plain", "clocks")},
     }
     print(json.dumps(line), flush=True)
 

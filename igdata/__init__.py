@@ -315,6 +315,16 @@ class ServedWorkload:
     meta: dict = field(default_factory=dict)
 
 
+def _unique_rows(a: np.ndarray) -> np.ndarray:
+    """np.unique(a, axis=0) for a uint16 matrix -- the distinct rows in
+    ascending lexicographic order -- computed on one byte string per row
+    (big-endian, so that byte order is numeric order), which sorts much
+    faster than the column-wise row comparison."""
+    a = np.ascontiguousarray(a, dtype=np.uint16)
+    keys = np.ascontiguousarray(a.astype(">u2")).view(np.dtype((np.void, 2 * a.shape[1])))
+    return np.unique(keys.ravel()).view(">u2").reshape(-1, a.shape[1]).astype(np.uint16)
+
+
 def served(per_class: int = 1_000_000, total_flows: int = 1_000_000, seed: int = 1005,
            keep_frac: float = 0.5, max_request: int = 4096) -> ServedWorkload:
     """The served-scoring workload (NSL-KDD-shaped, K = 8).
@@ -339,7 +349,7 @@ def served(per_class: int = 1_000_000, total_flows: int = 1_000_000, seed: int =
             keep = rng.random(codes.shape) < keep_frac
             keep[np.arange(need), rng.integers(0, codes.shape[1], need)] = True
             codes = np.where(keep, codes, np.uint16(MISSING)).astype(np.uint16)
-            have = np.unique(np.concatenate([have, codes]), axis=0)
+            have = _unique_rows(np.concatenate([have, codes]))
         patterns[c] = np.ascontiguousarray(have[rng.permutation(have.shape[0])[:per_class]])
         support[c] = rng.integers(1, 1001, size=per_class).astype(np.uint32)
     n_normal = int(round(0.53 * total_flows))

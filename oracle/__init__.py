@@ -68,6 +68,7 @@ def _load():
         "oracle_coherent": (None, [P, I64, P, I64, I32, P, ctypes.c_int]),
         "oracle_support": (None, [P, I64, P, I64, I32, P, P, ctypes.c_int]),
         "oracle_evidence": (None, [P, P, I64, P, I64, I32, P, ctypes.c_int]),
+        "oracle_pattern_score": (None, [P, I64, I32, P, P]),
         "oracle_reg3_stats": (None, [P, I64, P, P]),
         "oracle_labels": (None, [P, P, I64, ctypes.c_int, D, P]),
         "oracle_reg3_threshold": (D, [D, D, D]),
@@ -144,6 +145,32 @@ def support(patterns, same, threads: int | None = None):
     _load().oracle_support(_ptr(patterns), P, _ptr(same), same.shape[0], K,
                            _ptr(f), _ptr(S), threads or default_threads())
     return f, S
+
+
+def pattern_score(patterns, f) -> np.ndarray:
+    """Eq. 2 for given supports: S(b) = f(b) * |b|^2 for every pattern b."""
+    patterns = _rows(patterns)
+    f = np.ascontiguousarray(f, dtype=np.uint32)
+    S = np.zeros(patterns.shape[0], dtype=np.uint64)
+    _load().oracle_pattern_score(_ptr(patterns), patterns.shape[0], patterns.shape[1],
+                                 _ptr(f), _ptr(S))
+    return S
+
+
+def model_from_patterns(patterns: dict, support: dict) -> "Model":
+    """A model holding given dictionaries P^- (class 0) and P^+ (class 1)
+    with their supports: canonical order (ascending, word K-1 most
+    significant) and the scores of Eq. 2."""
+    K = None
+    pats, sups, scos = {}, {}, {}
+    for c in (NORMAL, ATTACK):
+        P = _rows(patterns[c])
+        K = P.shape[1]
+        order = np.lexsort(P.T) if P.shape[0] else np.zeros(0, np.int64)
+        pats[c] = np.ascontiguousarray(P[order])
+        sups[c] = np.ascontiguousarray(np.asarray(support[c], np.uint32)[order])
+        scos[c] = pattern_score(pats[c], sups[c])
+    return Model(K, pats, sups, scos, {NORMAL: 0, ATTACK: 0}, None)
 
 
 def evidence(patterns, S, rows, threads: int | None = None) -> np.ndarray:

@@ -209,6 +209,16 @@ void oracle_support(const uint64_t* pat, int64_t P, const uint64_t* same,
   });
 }
 
+// Eq. 2 for given supports: S(b) = f(b) * |b|^2 (patterns learned elsewhere,
+// e.g. a dictionary to be served).
+void oracle_pattern_score(const uint64_t* pat, int64_t P, int32_t K, const uint32_t* f,
+                          uint64_t* S) {
+  for (int64_t p = 0; p < P; ++p) {
+    uint64_t size = uint64_t(items_in_row(pat + p * K, K));
+    S[p] = uint64_t(f[p]) * size * size;
+  }
+}
+
 // Eq. 4: evidence(x) = sum over patterns b of S(b) * [b contained in x].
 // Called once with P^+ (giving A) and once with P^- (giving N).
 void oracle_evidence(const uint64_t* pat, const uint64_t* S, int64_t P,

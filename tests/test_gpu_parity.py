@@ -357,42 +357,66 @@ def test_save_load_roundtrip(nsl15k, tmp_path):
     assert_scores_equal(m2, om, test)
 
 
-def test_nsl148k_parity_sampled_scores():
-    # Full-size fit compared in full; scores on a seeded sample of the
-    # 133,200 test records (the oracle's evidence loop is the slow part).
-    # Library default kernel, as the benchmark runs it.
-    w = igdata.nsl148k()
-    m, rows = _workload_fit(w)
-    om = oracle.fit(rows, w.train_labels)
-    assert_model_equal(m, om)
-    test_rows = ig.ig_encode(dev(w.test_codes), w.cards)
+def _golden_digests():
+    """The oracle's digests of the full-size workloads, and the digest
+    function that wrote them (tests/golden/make_digests.py)."""
+    import importlib.util
+    import json
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_digests",
+                                                  os.path.join(here, "make_digests.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    with open(os.path.join(here, "oracle_digests.json")) as f:
+        return json.load(f)["workloads"], mod.digest
+
+
+def _gpu_digest(digest, m, test_rows):
+    info = m.info()
+    pats = {c: m.patterns(c) for c in (0, 1)}
     A, N, lab = ig.ig_score(m, test_rows)
-    idx = np.random.default_rng(7).choice(w.test_codes.shape[0], 1500, replace=False)
-    oA, oN, olab = oracle.score(om, oracle.encode(w.test_codes[idx], w.cards))
-    assert np.array_equal(host(A, np.int64)[idx], oA)
-    assert np.array_equal(host(N, np.int64)[idx], oN)
-    assert np.array_equal(host(lab, np.uint8)[idx], olab)
+    return digest(info["n_candidates"], {c: pats[c][0] for c in (0, 1)},
+                  {c: pats[c][1] for c in (0, 1)}, {c: pats[c][2] for c in (0, 1)},
+                  host(A, np.int64), host(N, np.int64), host(lab, np.uint8)), info
+
+
+def test_nsl148k_full_parity():
+    # Full-size fit and all 133,200 test records' scores against the
+    # oracle's digest of the same workload (library default kernel, as the
+    # benchmark runs it).
+    golden, digest = _golden_digests()
+    w = igdata.nsl148k()
+    m, _ = _workload_fit(w)
+    got, info = _gpu_digest(digest, m, ig.ig_encode(dev(w.test_codes), w.cards))
+    want = golden[w.name]
+    assert list(info["n_patterns"]) == want["n_patterns"]
+    assert list(info["n_candidates"]) == want["n_candidates"]
+    assert got == want["sha256"], "148k output differs from the oracle's"
 
 
 # ---- batched problems -------------------------------------------------------
 
-def test_batched_fit_matches_single_fits_and_oracle():
-    probs = igdata.batched(14)
+def test_batched_fit_all_problems_match_single_fits_and_oracle():
+    # All 64 problems of the batched workload in one ig_fit_batched call:
+    # each model equals its own ig_fit, and each problem's whole output
+    # (model and test scores) equals the oracle's digest.
+    golden, digest = _golden_digests()
+    probs = igdata.batched(igdata.BATCHED_PROBLEMS)
     enc = []
     for w in probs:
         enc.append((ig.ig_encode(dev(w.train_codes), w.cards), dev(w.train_labels)))
-    batched = ig.ig_fit_batched(enc, lanes=5)
+    batched = ig.ig_fit_batched(enc)
     widths = set()
     for i, (w, mb) in enumerate(zip(probs, batched)):
         single = ig.ig_fit(*enc[i])
         for cls in (0, 1):
             assert all(np.array_equal(x, y) for x, y in zip(mb.patterns(cls), single.patterns(cls)))
+        single.free()
+        got, _ = _gpu_digest(digest, mb, ig.ig_encode(dev(w.test_codes), w.cards))
+        assert got == golden[w.name]["sha256"], f"problem {i} differs from the oracle"
         widths.add(w.meta["width"])
-        if w.train_codes.shape[0] <= 2500:          # oracle on the smaller problems
-            om = oracle.fit(oracle.encode(w.train_codes, w.cards), w.train_labels)
-            assert_model_equal(mb, om)
-            assert_scores_equal(mb, om, oracle.encode(w.test_codes, w.cards))
-    assert len(widths) >= 3
+        mb.free()
+    assert len(widths) == 4
 
 
 def test_batched_fit_reports_failing_problem():

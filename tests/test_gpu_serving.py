@@ -29,20 +29,47 @@ def served():
 
 
 def test_model_from_patterns_matches_oracle(served):
+    # The oracle's model is built from the generator's codes alone (its own
+    # encoding, canonical order and Eq. 2 scores); so are the test records.
     sw, words, model, flows = served
-    pats, sups, scos = {}, {}, {}
+    om = oracle.model_from_patterns({c: oracle.encode(sw.patterns[c], sw.cards) for c in (0, 1)},
+                                    sw.support)
     for c in (0, 1):
-        order = np.lexsort(words[c].T)   # canonical: word K-1 most significant
         w, f, s = model.patterns(c)
-        assert np.array_equal(w, words[c][order])
-        assert np.array_equal(f, sw.support[c][order])
-        items = np.unpackbits(w.view(np.uint8), axis=1).sum(1).astype(np.uint64)
-        assert np.array_equal(s, f.astype(np.uint64) * items * items)     # Eq. 2
-        pats[c], sups[c], scos[c] = w, f, s
-    om = oracle.Model(8, pats, sups, scos, {0: 0, 1: 0}, None)
-    A, N, lab = ig.ig_score(model, flows[:3000])
-    oA, oN, olab = oracle.score(om, flows[:3000])
+        assert np.array_equal(w, om.patterns[c])
+        assert np.array_equal(f, om.support[c]) and np.array_equal(s, om.score[c])
+    test = oracle.encode(sw.flow_codes[:3000], sw.cards)
+    A, N, lab = ig.ig_score(model, test)
+    oA, oN, olab = oracle.score(om, test)
     assert np.array_equal(A, oA) and np.array_equal(N, oN) and np.array_equal(lab, olab)
+
+
+def test_served_full_size(served):
+    # The served workload at its full size: 1M normal + 1M attack patterns,
+    # 10^6 flows in 1,972 requests.  The one-shot ig_score of a seeded
+    # sample of flows equals the oracle's; every flow the server returns, in
+    # a burst of all requests at once, equals the one-shot ig_score of all
+    # flows.
+    sw = igdata.served()
+    words = [ig.ig_encode(torch.from_numpy(sw.patterns[c].view(np.int16)).cuda(), sw.cards)
+             for c in (0, 1)]
+    model = ig.ig_model_from_patterns(words[0], sw.support[0], words[1], sw.support[1])
+    om = oracle.model_from_patterns({c: oracle.encode(sw.patterns[c], sw.cards) for c in (0, 1)},
+                                    sw.support)
+    idx = np.random.default_rng(9).choice(sw.flow_codes.shape[0], 1500, replace=False)
+    sample = oracle.encode(sw.flow_codes[idx], sw.cards)
+    A, N, lab = ig.ig_score(model, sample)
+    oA, oN, olab = oracle.score(om, sample)
+    assert np.array_equal(A, oA) and np.array_equal(N, oN) and np.array_equal(lab, olab)
+    assert int((oA > 0).sum()) > 0 and int((oN > 0).sum()) > 0
+    flows = ig.ig_encode(sw.flow_codes, sw.cards)
+    ref = ig.ig_score(model, flows)
+    offs = np.concatenate([[0], np.cumsum(sw.request_sizes)])
+    reqs = [flows[offs[i]:offs[i + 1]] for i in range(len(sw.request_sizes))]
+    outs, (batches, n_flows) = _serve(model, reqs, 0.0, cap=65536, budget=1 << 30)
+    assert n_flows == flows.shape[0] and batches < len(reqs)
+    for k in range(3):
+        assert np.array_equal(np.concatenate([o[k] for o in outs]), ref[k])
 
 
 def test_model_from_patterns_rejects_duplicates():

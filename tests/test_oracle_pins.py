@@ -267,3 +267,29 @@ def test_reg3_statistics_closed_form():
     mu, sigma = oracle.reg3_stats(np.array([5, 5, 5]))
     assert (mu, sigma) == (5.0, 0.0)
     assert oracle.reg3_threshold(2.5, 0.5, 3.0) == 1.0
+
+
+def test_pattern_score_for_given_supports():
+    # Eq. 2 with the supports given: |b| counts items in every word (an item
+    # in word 0 and one in the top bit of word 1 make |b| = 2).
+    P = np.array([[0b10110, 0], [1, 1 << 63], [0, 0b111]], np.uint64)
+    f = np.array([5, 2, 7], np.uint32)
+    assert oracle.pattern_score(P, f).tolist() == [5 * 9, 2 * 4, 7 * 9]
+    # The same scores as the support step's own (brute-force pinned) ones.
+    rng = np.random.default_rng(21)
+    same = igdata.random_words(rng, 60, 150, "half")
+    pats = same[rng.integers(0, 60, size=25)] & same[rng.integers(0, 60, size=25)]
+    pats = pats[np.any(pats != 0, axis=1)]
+    fs, S = oracle.support(pats, same)
+    assert np.array_equal(oracle.pattern_score(pats, fs), S)
+
+
+def test_model_from_patterns_canonical_order():
+    # Given dictionaries come back ascending as K-word integers (word K-1
+    # most significant), supports following their patterns.
+    P = np.array([[5, 1], [7, 0], [1, 1], [2, 0]], np.uint64)
+    m = oracle.model_from_patterns({0: P, 1: P[:2]}, {0: [10, 20, 30, 40], 1: [1, 2]})
+    assert m.patterns[0].tolist() == [[2, 0], [7, 0], [1, 1], [5, 1]]
+    assert m.support[0].tolist() == [40, 20, 30, 10]
+    assert m.score[0].tolist() == [40 * 1, 20 * 9, 30 * 4, 10 * 9]
+    assert m.patterns[1].tolist() == [[7, 0], [5, 1]]
