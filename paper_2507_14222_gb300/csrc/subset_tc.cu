@@ -510,12 +510,18 @@ struct FusedShape {
   // the current stream tile.
   static constexpr size_t kScores =
       MODE == MODE_SUM ? size_t(kEpiWarps) * (kN / (kEpiWarps / 4)) * 4 : 0;
-  // Tensor memory (512 columns): two accumulator buffers of 128 columns,
-  // then the resident operand, 16*KT columns (4 items each) per half, twice
-  // where it fits, so that the next item's rows can be written while the
-  // MMAs still read the current ones.
+  // Tensor memory (512 columns): accumulator buffers of 128 columns, then
+  // the resident operand, 16*KT columns (4 items each) per half, twice where
+  // it fits, so that the next item's rows can be written while the MMAs
+  // still read the current ones.
+  // Three accumulator buffers where they fit beside two resident buffers
+  // (each buffer more gives the epilogue a whole unit of MMA time before
+  // the issuer needs its slot back; a second resident buffer lets the next
+  // item's rows be written while the MMAs still read the current ones,
+  // which matters more where items are short), else two; then the second
+  // resident buffer where the rest allows.
   static constexpr int kACols = 16 * KT;
-  static constexpr int kAccBufs = 2;                // accumulator buffers of 128 columns
+  static constexpr int kAccBufs = 3 * 128 + 2 * kHalves * kACols <= 512 ? 3 : 2;
   static constexpr int kAccCols = 128 * kAccBufs;
   static constexpr int kABufs = kAccCols + 2 * kHalves * kACols <= 512 ? 2 : 1;
   static_assert(kAccCols + kABufs * kHalves * kACols <= 512, "tensor memory overflow");
@@ -749,7 +755,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
         const uint32_t a_tm = tmem + uint32_t(S::kAccCols + ab * S::kHalves * S::kACols);
         for (int t = 0; t < w.b_tiles && ok; ++t, ++tt) {
           const int s = int(tt % XS);
-          if (!mbar_wait(b_x_full + s, uint32_t((tt / XS) & 1), p.status, lim) || *abort_flag) {
+          // (The abort flag is read only at item boundaries: on an abort the
+          // other roles stop, so this issuer's own bounded waits end too.)
+          if (!mbar_wait(b_x_full + s, uint32_t((tt / XS) & 1), p.status, lim)) {
             *abort_flag = 1;
             ok = false;
             break;
@@ -760,8 +768,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
           for (int h = 0; h < halves; ++h, ++uu) {
             const int b = int(uu % S::kAccBufs);
             if ((uu == p.stall_unit && !mbar_wait(never, 0, p.status, lim)) ||
-                !mbar_wait(acc_empty + b, uint32_t(((uu / S::kAccBufs) & 1) ^ 1), p.status, lim) ||
-                *abort_flag) {
+                !mbar_wait(acc_empty + b, uint32_t(((uu / S::kAccBufs) & 1) ^ 1), p.status, lim)) {
               *abort_flag = 1;
               ok = false;
               break;
@@ -828,18 +835,27 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
       for (int t = 0; t < w.b_tiles && ok; ++t) {
         const int64_t left = int64_t(w.str_count) - int64_t(t) * kN;
         const int nvalid = int(left < kN ? left : kN);
-        // MODE_SUM: record ids of this warp's columns of the tile, fetched
-        // before the wait for the accumulator (once every lane is done with
-        // the last tile's).
+        // MODE_SUM: record ids of this warp's columns of the tile, lane i
+        // holding those of columns col0 + i + 32q (which it adds to when the
+        // warp sums a column's hits): loads issued before the wait for the
+        // accumulator and first needed only by a hit, so their latency hides
+        // behind the wait.  With wide sums (scores beyond 2^27) any lane may
+        // need any column's id: those are staged in shared memory (once
+        // every lane is done with the last tile's).
+        uint32_t rid[kCols / 32];
         if constexpr (MODE == MODE_SUM) {
-          __syncwarp();
           const int64_t j0 = w.str_first + int64_t(t) * kN + col0;
 #pragma unroll
           for (int q = 0; q < kCols / 32; ++q) {
             const int j = lane + 32 * q;
-            sid[j] = col0 + j < nvalid ? p.str_ids[j0 + j] : 0u;
+            rid[q] = col0 + j < nvalid ? p.str_ids[j0 + j] : 0u;
           }
-          __syncwarp();
+          if (!p.narrow) {
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < kCols / 32; ++q) sid[lane + 32 * q] = rid[q];
+            __syncwarp();
+          }
         }
         for (int h = 0; h < halves; ++h, ++uu) {
           const int b = int(uu % S::kAccBufs);
@@ -851,88 +867,100 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
             break;
           }
           tc_fence_after();
-          bool cov = false;
-          uint32_t cnt = 0;
-          // 32 columns per load, with their minimum; the slot is handed back
-          // to the MMA issuer as soon as this warp's last load from it has
-          // completed, before that chunk is reduced.  A chunk whose minimum
-          // is non-zero holds no hit (no count is 0) and needs no further
-          // work unless it runs past the tile's rows (zero rows, D = 0, are
-          // not hits).  Hits are rare (about one test in 600 at NSL-KDD
-          // shape), so most chunks take only the load.
-#pragma unroll 1
-          for (int c = col0; c < col0 + kCols; c += 32) {
+          // Two phases.  While the unit holds its accumulator slot: per 32
+          // columns one load with the columns' minimum and, where a lane's
+          // chunk holds a hit, that lane's 32-bit hit mask -- a chunk whose
+          // minimum is non-zero holds no hit (no count is 0), and columns
+          // past the tile's rows (zero rows give D = 0) are not hits.  The
+          // slot goes back to the MMA issuer after this warp's last load;
+          // the masks are reduced after that, so that the sums and atomics
+          // of the hits (about one test in 600 at NSL-KDD shape) do not
+          // hold the slot.
+          constexpr int NQ = kCols / 32;
+          uint32_t hm[NQ];
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) {
+            const int c = col0 + 32 * q;
             uint32_t v[32], mn;
-            __syncwarp();  // the lanes of the last chunk's hits rejoin before the load
+            __syncwarp();  // the lanes that built a mask rejoin before the load
             tmem_ld32_min(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * 128 + c), v, mn);
-            if (c + 32 >= col0 + kCols) {
+            if (q == NQ - 1) {
               tc_fence_before();
               __syncwarp();
               if (lane == 0) mbar_arrive(acc_empty + b);
             }
             const bool tail = c + 32 > nvalid;
-            if constexpr (MODE == MODE_ANY) {
-              if (!live[h] || (mn != 0u && !tail)) continue;
-              if (!tail) {
-                cov = true;
-                continue;
-              }
-            }
-            // This lane's hits among the chunk's columns (none unless its row
-            // is live and the chunk holds a zero count or runs past the
-            // tile's rows, whose zero rows give D = 0 but are not hits).
-            const bool need = live[h] && (mn == 0u || tail);
-            if constexpr (MODE == MODE_SUM) {
-              if (!__any_sync(0xffffffffu, need)) continue;
-            } else {
-              if (!need) continue;
-            }
             uint32_t m = 0;
-            if (need) {
+            if (live[h] && (mn == 0u || tail)) {
+              if (MODE == MODE_ANY && !tail) {
+                m = 1u;  // a hit somewhere: all that coherence needs
+              } else {
 #pragma unroll
-              for (int i = 0; i < 32; ++i) m |= (v[i] == 0u ? 1u : 0u) << i;
-              if (tail) {
-                const int r = nvalid - c;
-                m &= r <= 0 ? 0u : (1u << r) - 1u;
+                for (int i = 0; i < 32; ++i) m |= (v[i] == 0u ? 1u : 0u) << i;
+                if (tail) {
+                  const int r = nvalid - c;
+                  m &= r <= 0 ? 0u : (1u << r) - 1u;
+                }
               }
             }
+            hm[q] = m;
+          }
+          __syncwarp();
+          bool cov = false;
+          uint32_t cnt = 0;
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) {
+            const uint32_t m = hm[q];
             if constexpr (MODE == MODE_ANY) cov |= m != 0u;
             if constexpr (MODE == MODE_COUNT) cnt += uint32_t(__popc(m));
             if constexpr (MODE == MODE_SUM) {
               // Eq. 4: every record holding a pattern gains its score.
+              if (!__any_sync(0xffffffffu, m != 0u)) continue;
+              const int c = col0 + 32 * q;
               const unsigned long long sv = own_s[h];
               if (p.narrow) {
                 // Per column that any lane hit, the warp sums its patterns'
                 // scores, and lane i adds column i's total to its record:
                 // one atomic per (record, chunk) instead of one per hit, so
                 // that the patterns of a record do not queue on its address.
+                // Four columns per round: their warp sums are independent and
+                // overlap.
                 uint32_t cols = __reduce_or_sync(0xffffffffu, m);
                 uint32_t mine = 0;
                 while (cols) {
-                  const int i = __ffs(cols) - 1;
-                  cols &= cols - 1u;
-                  const uint32_t tot =
-                      __reduce_add_sync(0xffffffffu, ((m >> i) & 1u) ? uint32_t(sv) : 0u);
-                  mine = lane == i ? tot : mine;
+                  int i[4];
+#pragma unroll
+                  for (int k = 0; k < 4; ++k) {
+                    i[k] = cols ? __ffs(cols) - 1 : 32;
+                    cols &= cols - 1u;
+                  }
+                  uint32_t tot[4];
+#pragma unroll
+                  for (int k = 0; k < 4; ++k)
+                    tot[k] = __reduce_add_sync(
+                        0xffffffffu, (i[k] < 32 && ((m >> i[k]) & 1u)) ? uint32_t(sv) : 0u);
+#pragma unroll
+                  for (int k = 0; k < 4; ++k) mine = lane == i[k] ? tot[k] : mine;
                 }
-                if (mine) atomicAdd(p.out_u64 + sid[c - col0 + lane], (unsigned long long)mine);
+                if (mine) atomicAdd(p.out_u64 + rid[q], (unsigned long long)mine);
               } else {
                 // Straight to the records, four hits per round so that their
                 // id loads and atomics overlap.
                 const uint32_t* ids = sid + (c - col0);
-                while (m) {
+                uint32_t mm = m;
+                while (mm) {
                   int i[4];
 #pragma unroll
-                  for (int q = 0; q < 4; ++q) {
-                    i[q] = m ? __ffs(m) - 1 : -1;
-                    m &= m - 1u;
+                  for (int k = 0; k < 4; ++k) {
+                    i[k] = mm ? __ffs(mm) - 1 : -1;
+                    mm &= mm - 1u;
                   }
                   uint32_t r[4];
 #pragma unroll
-                  for (int q = 0; q < 4; ++q) r[q] = i[q] >= 0 ? ids[i[q]] : 0u;
+                  for (int k = 0; k < 4; ++k) r[k] = i[k] >= 0 ? ids[i[k]] : 0u;
 #pragma unroll
-                  for (int q = 0; q < 4; ++q)
-                    if (i[q] >= 0) atomicAdd(p.out_u64 + r[q], sv);
+                  for (int k = 0; k < 4; ++k)
+                    if (i[k] >= 0) atomicAdd(p.out_u64 + r[k], sv);
                 }
               }
             }
