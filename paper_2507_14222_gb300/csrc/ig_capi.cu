@@ -1482,7 +1482,39 @@ int ig_score(const ig_model* m, const uint64_t* rows, int64_t n_rows, int64_t* A
     IG_CUDA(igk::build_record_index(in.d, n_rows, m->K, m->K, m->KT, 0.25, &test_idx.idx, s),
             "ig_score: record index");
   }
-  if (pruned && test_idx.idx.usable) {
+  if (pruned && test_idx.idx.usable && m->subset_kernel == 4 && igk::tc_supported(m->KT)) {
+    // Tensor-core form: both classes' patterns against the batch's records
+    // in one launch of the fused kernel (one schedule, one tail).  Small
+    // batches reuse the model's pattern index; larger ones re-key the
+    // patterns by the batch's own item counts.
+    igk::KeyedIndex own[2];
+    const igk::KeyedIndex* kx[2];
+    unsigned long long* outs[2];
+    uint64_t smax[2];
+    int n = 0;
+    int64_t t[2] = {0, 0};
+    cudaError_t e = cudaSuccess;
+    for (int c = 1; c >= 0 && e == cudaSuccess; --c) {
+      done[c] = true;
+      if (m->n_pat[c] == 0) continue;
+      if (m->pidx[c] && n_rows * 8 < m->n_pat[c]) {
+        kx[n] = m->pidx[c];
+      } else {
+        e = igk::build_keyed_index(m->words_kt[c], m->n_pat[c], m->KT, m->K, m->KT,
+                                   test_idx.idx.freq, m->score[c], &own[n], s);
+        kx[n] = &own[n];
+      }
+      outs[n] = c == 1 ? A.d : N.d;
+      smax[n] = m->score_max[c];
+      ++n;
+    }
+    if (e == cudaSuccess && n > 0)
+      e = igk::indexed_subset_tc_classes(igk::MODE_SUM, test_idx.idx, kx, n, nullptr, outs,
+                                         d_status.p, t, S_EVIDENCE_IDX, smax, s);
+    for (int i = 0; i < 2; ++i) igk::release_keyed_index(&own[i], s);
+    IG_CUDA(e, "ig_score: evidence");
+    igk::prof_add_work(S_EVIDENCE_IDX, t[0] + t[1]);
+  } else if (pruned && test_idx.idx.usable) {
     // A (class 1) on the caller's stream and N (class 0) on this thread's
     // auxiliary stream, concurrently: both only read the indexes.
     AuxStream& aux = aux_stream();

@@ -285,7 +285,17 @@ void release_keyed_index(KeyedIndex* k, cudaStream_t s);
 // Same results as the integer grouped kernel; *tests_out as for
 // indexed_subset_prebuilt.
 // score_max (MODE_SUM): an upper bound of the keyed rows' scores; below
-// 2^26 the kernel sums hits per record in 32-bit shared partial sums.
+// 2^27 the kernel sums each hit column's scores over a warp in 32 bits
+// before adding them to the record.
+//
+// indexed_subset_tc_classes: the same for n_cls keyed indexes (1, or 2 with
+// MODE_SUM: both classes' patterns against one record index in one launch,
+// class c's sums into out_sum[c]); tests_out and score_max have n_cls entries.
+cudaError_t indexed_subset_tc_classes(int mode, const RecordIndex& idx, const KeyedIndex* const* kx,
+                                      int n_cls, uint32_t* out_u32,
+                                      unsigned long long* const* out_sum, int* status,
+                                      int64_t* tests_out, int prof_stage,
+                                      const uint64_t* score_max, cudaStream_t s);
 cudaError_t indexed_subset_tc(int mode, const RecordIndex& idx, const KeyedIndex& kx,
                               uint32_t* out_u32, unsigned long long* out_u64, int* status,
                               int64_t* tests_out, int prof_stage, uint64_t score_max,

@@ -548,18 +548,26 @@ struct FusedShape {
 constexpr uint32_t kFusedTmemCols = 512;
 
 struct FusedParams {
-  const TcItem* items;
+  const TcItem* items;        // grouped by CTA: CTA b runs items [cta_off[b], cta_off[b + 1])
   int64_t n_items;
-  const uint64_t* own_rows;  // grouped rows of the resident side (stride KT)
+  const int64_t* cta_off;     // gridDim.x + 1 entries
+  // Per class of resident rows (an item's class is its `pad` field: one
+  // launch can score the records against both classes' patterns):
+  const uint64_t* own_rows0;  // grouped rows of the resident side (stride KT)
+  const uint64_t* own_rows1;
+  const uint32_t* own_ids0;   // original id of each grouped resident row
+  const uint32_t* own_ids1;
+  const uint64_t* score0;     // MODE_SUM: S of each grouped resident row (pattern)
+  const uint64_t* score1;
+  unsigned long long* sum0;   // MODE_SUM: per-record sums (Eq. 4: A or N)
+  unsigned long long* sum1;
+  // MODE_SUM: 1 when every score of the class is below 2^27, so that the
+  // sum of one column's hits over a warp's 32 patterns fits in 32 bits; 0:
+  // every hit goes to its record by its own 64-bit atomic.
+  int narrow0, narrow1;
   const uint64_t* str_rows;  // grouped rows of the streamed side (stride KT)
   int own_complement;        // 1: the resident side is the record side
-  const uint32_t* own_ids;   // original id of each grouped resident row
-  const uint64_t* score;     // MODE_SUM: S of each grouped resident row (pattern)
   const uint32_t* str_ids;   // MODE_SUM: original id of each grouped streamed row (record)
-  // MODE_SUM: 1 when every score is below 2^27, so that the sum of one
-  // column's hits over a warp's 32 patterns fits in 32 bits; 0: every hit
-  // goes to its record by its own 64-bit atomic.
-  int narrow;
   // Polls a wait for a full stage, a free stage or an accumulator may take
   // (0: kMbarPollLimit); the waits for copies and MMAs in flight before the
   // CTA ends always take the full limit.  And, for tests of the timeout
@@ -567,8 +575,7 @@ struct FusedParams {
   // never completes (-1: none).
   uint32_t poll_limit;
   int64_t stall_unit;
-  uint32_t* out_u32;
-  unsigned long long* out_u64;
+  uint32_t* out_u32;          // MODE_ANY / MODE_COUNT (one class)
   int* status;
 };
 
@@ -646,7 +653,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t G = gridDim.x;
+  const int64_t it_lo = p.cta_off[blockIdx.x], it_hi = p.cta_off[blockIdx.x + 1];
   const uint32_t lim = p.poll_limit ? p.poll_limit : kMbarPollLimit;
   // MODE_SUM: this warp's record ids for its columns of the current stream
   // tile (after the barriers' 512 bytes).
@@ -699,7 +706,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
         const int64_t left = int64_t(w.str_count) - int64_t(t) * kN;
         return uint32_t(left < kN ? left : kN) * KT * 8;
       };
-      for (int64_t it = blockIdx.x; it < p.n_items && !*abort_flag; it += G, ++ii) {
+      for (int64_t it = it_lo; it < it_hi && !*abort_flag; ++it, ++ii) {
         const TcItem w = p.items[it];
         if (!mbar_wait(a_pk_empty, uint32_t((ii & 1) ^ 1), p.status, lim)) {
           *abort_flag = 1;
@@ -707,7 +714,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
         }
         const uint32_t abytes = uint32_t(w.own_count) * KT * 8;
         mbar_arrive_expect_tx(a_pk_full, abytes);
-        bulk_g2s(A_pk, p.own_rows + w.own_first * KT, abytes, a_pk_full);
+        bulk_g2s(A_pk, (w.pad ? p.own_rows1 : p.own_rows0) + w.own_first * KT, abytes,
+                 a_pk_full);
         ++issued_a;
         for (int t = 0; t < w.b_tiles; ++t, ++tt) {
           const int s = int(tt % PKS);
@@ -741,7 +749,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
       int64_t tt = 0, ii = 0, uu = 0;
       int64_t bx_last = -1, ax_last = -1;  // last tile / item whose stage / rows were released
       bool ok = true;
-      for (int64_t it = blockIdx.x; it < p.n_items && ok; it += G, ++ii) {
+      for (int64_t it = it_lo; it < it_hi && ok; ++it, ++ii) {
         const TcItem w = p.items[it];
         const int halves = w.own_count > 128 ? 2 : 1;
         const int ab = S::kABufs == 2 ? int(ii & 1) : 0;
@@ -817,9 +825,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
     const int col0 = grp * kCols;
     int64_t uu = 0;
     bool ok = true;
-    for (int64_t it = blockIdx.x; it < p.n_items && ok; it += G) {
+    for (int64_t it = it_lo; it < it_hi && ok; ++it) {
       const TcItem w = p.items[it];
       const int halves = w.own_count > 128 ? 2 : 1;
+      const bool narrow = w.pad ? p.narrow1 != 0 : p.narrow0 != 0;
+      unsigned long long* const out_sum = w.pad ? p.sum1 : p.sum0;
       // This lane's resident row in each half; rows past the item's are zero
       // operands (D = 0 against everything) and take no part.
       bool live[2];
@@ -828,7 +838,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
       for (int h = 0; h < 2; ++h) {
         live[h] = h < halves && h * 128 + tile_row < w.own_count;
         if constexpr (MODE == MODE_SUM)
-          if (live[h]) own_s[h] = p.score[w.own_first + h * 128 + tile_row];
+          if (live[h]) own_s[h] = (w.pad ? p.score1 : p.score0)[w.own_first + h * 128 + tile_row];
       }
       bool cov0 = false, cov1 = false;
       uint32_t cnt0 = 0, cnt1 = 0;
@@ -850,7 +860,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
             const int j = lane + 32 * q;
             rid[q] = col0 + j < nvalid ? p.str_ids[j0 + j] : 0u;
           }
-          if (!p.narrow) {
+          if (!narrow) {
             __syncwarp();
 #pragma unroll
             for (int q = 0; q < kCols / 32; ++q) sid[lane + 32 * q] = rid[q];
@@ -918,7 +928,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
               if (!__any_sync(0xffffffffu, m != 0u)) continue;
               const int c = col0 + 32 * q;
               const unsigned long long sv = own_s[h];
-              if (p.narrow) {
+              if (narrow) {
                 // Per column that any lane hit, the warp sums its patterns'
                 // scores, and lane i adds column i's total to its record:
                 // one atomic per (record, chunk) instead of one per hit, so
@@ -942,7 +952,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
 #pragma unroll
                   for (int k = 0; k < 4; ++k) mine = lane == i[k] ? tot[k] : mine;
                 }
-                if (mine) atomicAdd(p.out_u64 + rid[q], (unsigned long long)mine);
+                if (mine) atomicAdd(out_sum + rid[q], (unsigned long long)mine);
               } else {
                 // Straight to the records, four hits per round so that their
                 // id loads and atomics overlap.
@@ -960,7 +970,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
                   for (int k = 0; k < 4; ++k) r[k] = i[k] >= 0 ? ids[i[k]] : 0u;
 #pragma unroll
                   for (int k = 0; k < 4; ++k)
-                    if (i[k] >= 0) atomicAdd(p.out_u64 + r[k], sv);
+                    if (i[k] >= 0) atomicAdd(out_sum + r[k], sv);
                 }
               }
             }
@@ -978,7 +988,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
       if constexpr (MODE != MODE_SUM) {
         for (int h = 0; h < halves; ++h) {
           if (!live[h]) continue;
-          const int64_t row = int64_t(p.own_ids[w.own_first + h * 128 + tile_row]);
+          const int64_t row =
+              int64_t((w.pad ? p.own_ids1 : p.own_ids0)[w.own_first + h * 128 + tile_row]);
           if constexpr (MODE == MODE_ANY) {
             if (h == 0 ? cov0 : cov1) p.out_u32[row] = 1u;
           }
@@ -994,7 +1005,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) subset_tc_fused_kernel(Fused
     const int e = threadIdx.x - kFirstExp * 32;
     int64_t tt = 0, ii = 0;
     bool ok = true;
-    for (int64_t it = blockIdx.x; it < p.n_items && ok; it += G, ++ii) {
+    for (int64_t it = it_lo; it < it_hi && ok; ++it, ++ii) {
       const TcItem w = p.items[it];
       const int ab = S::kABufs == 2 ? int(ii & 1) : 0;
       const uint32_t aph = uint32_t((S::kABufs == 2 ? (ii >> 1) : ii) & 1);
@@ -1076,6 +1087,7 @@ static cudaError_t run_fused(const FusedParams& p, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(subset_tc_fused_kernel<KT, MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::kSmem));
   if (e != cudaSuccess) return e;
+  // As many CTAs as the items' CTA lists (cta_off) were made for.
   const int64_t grid = std::min<int64_t>(p.n_items, int64_t(num_sms()));
   subset_tc_fused_kernel<KT, MODE><<<unsigned(grid), kFusedThreads, S::kSmem, s>>>(p);
   count_launches(1);
@@ -1116,57 +1128,87 @@ struct TcStaging {
 thread_local TcStaging g_tc_staging;
 }  // namespace
 
-cudaError_t indexed_subset_tc(int mode, const RecordIndex& idx, const KeyedIndex& kx,
-                              uint32_t* out_u32, unsigned long long* out_u64, int* status,
-                              int64_t* tests_out, int prof_stage, uint64_t score_max,
-                              cudaStream_t s) {
-  *tests_out = 0;
+cudaError_t indexed_subset_tc_classes(int mode, const RecordIndex& idx, const KeyedIndex* const* kx,
+                                      int n_cls, uint32_t* out_u32,
+                                      unsigned long long* const* out_sum, int* status,
+                                      int64_t* tests_out, int prof_stage,
+                                      const uint64_t* score_max, cudaStream_t s) {
   const int L = idx.L, KT = idx.KT;
-  if (kx.n == 0 || idx.n_rows == 0 || !tc_supported(KT)) return cudaErrorInvalidValue;
+  if (n_cls < 1 || n_cls > 2 || (n_cls == 2 && mode != MODE_SUM)) return cudaErrorInvalidValue;
+  for (int c = 0; c < n_cls; ++c) tests_out[c] = 0;
+  if (idx.n_rows == 0 || !tc_supported(KT)) return cudaErrorInvalidValue;
   // Patterns (keyed) are resident and records (multi, complemented) stream,
   // in every mode: an item group holds far fewer patterns than records, so
   // items are long (about 90 stream tiles at NSL-KDD shape, against 6-9 with
   // the records resident) and the resident rows are expanded 10-15x less
   // often.  ANY / COUNT results stay per resident row; SUM adds each
-  // pattern's score to the records containing it, per hit.
-  const bool own_multi = false;
-  const uint32_t* own_off = own_multi ? idx.h_off.data() : kx.h_off.data();
-  const uint32_t* str_off = own_multi ? kx.h_off.data() : idx.h_off.data();
+  // pattern's score to the records containing it.  With two classes (SUM),
+  // both classes' items share one launch, one schedule and one tail.
+  const uint32_t* str_off = idx.h_off.data();
   std::vector<TcItem> items;
   const int64_t own_rows = 128 * fused_halves(mode), n_rows = fused_n(mode);
-  int64_t tests = 0, pair_tiles = 0;
-  for (int l = 0; l < L; ++l) {
-    const int64_t no = int64_t(own_off[l + 1]) - own_off[l];
-    const int64_t ns = int64_t(str_off[l + 1]) - str_off[l];
-    if (no == 0 || ns == 0) continue;
-    tests += no * ns;
-    pair_tiles += ceil_div(no, own_rows) * ceil_div(ns, n_rows);
+  int64_t pair_tiles = 0;
+  for (int c = 0; c < n_cls; ++c) {
+    if (kx[c]->n == 0) continue;
+    const uint32_t* own_off = kx[c]->h_off.data();
+    for (int l = 0; l < L; ++l) {
+      const int64_t no = int64_t(own_off[l + 1]) - own_off[l];
+      const int64_t ns = int64_t(str_off[l + 1]) - str_off[l];
+      if (no == 0 || ns == 0) continue;
+      tests_out[c] += no * ns;
+      pair_tiles += ceil_div(no, own_rows) * ceil_div(ns, n_rows);
+    }
   }
-  *tests_out = tests;
   if (pair_tiles == 0) return cudaSuccess;
-  // Stream ranges of `per` tiles (about eight items per SM), largest items
-  // first: the persistent CTAs take items round-robin.
+  // Stream ranges of `per` tiles (about eight items per SM).
   const int64_t per = std::max<int64_t>(1, pair_tiles / (int64_t(num_sms()) * 8));
-  for (int l = 0; l < L; ++l) {
-    const int64_t no = int64_t(own_off[l + 1]) - own_off[l];
-    const int64_t ns = int64_t(str_off[l + 1]) - str_off[l];
-    if (no == 0 || ns == 0) continue;
-    const int64_t nb = ceil_div(ns, n_rows);
-    for (int64_t a = 0; a * own_rows < no; ++a)
-      for (int64_t b = 0; b < nb; b += per) {
-        TcItem it;
-        it.own_first = int64_t(own_off[l]) + a * own_rows;
-        it.str_first = int64_t(str_off[l]) + b * n_rows;
-        it.own_count = int32_t(std::min<int64_t>(own_rows, no - a * own_rows));
-        it.b_tiles = int32_t(std::min<int64_t>(per, nb - b));
-        it.str_count = int32_t(std::min<int64_t>(per * n_rows, ns - b * n_rows));
-        it.pad = 0;
-        items.push_back(it);
-      }
+  for (int c = 0; c < n_cls; ++c) {
+    if (kx[c]->n == 0) continue;
+    const uint32_t* own_off = kx[c]->h_off.data();
+    for (int l = 0; l < L; ++l) {
+      const int64_t no = int64_t(own_off[l + 1]) - own_off[l];
+      const int64_t ns = int64_t(str_off[l + 1]) - str_off[l];
+      if (no == 0 || ns == 0) continue;
+      const int64_t nb = ceil_div(ns, n_rows);
+      for (int64_t a = 0; a * own_rows < no; ++a)
+        for (int64_t b = 0; b < nb; b += per) {
+          TcItem it;
+          it.own_first = int64_t(own_off[l]) + a * own_rows;
+          it.str_first = int64_t(str_off[l]) + b * n_rows;
+          it.own_count = int32_t(std::min<int64_t>(own_rows, no - a * own_rows));
+          it.b_tiles = int32_t(std::min<int64_t>(per, nb - b));
+          it.str_count = int32_t(std::min<int64_t>(per * n_rows, ns - b * n_rows));
+          it.pad = c;
+          items.push_back(it);
+        }
+    }
   }
+  // Items to CTAs in snake order over the items sorted longest first
+  // (CTAs 0 .. G-1, then G-1 .. 0, ...), which evens out the CTAs' totals
+  // far better than plain round-robin; a CTA's items are contiguous and it
+  // runs them largest first.  An item costs its MMA units plus about two
+  // units for its resident rows.
+  const int64_t grid = std::min<int64_t>(int64_t(items.size()), int64_t(num_sms()));
+  auto cost = [](const TcItem& w) {
+    return int64_t(w.b_tiles) * (w.own_count > 128 ? 2 : 1) + 2;
+  };
   std::stable_sort(items.begin(), items.end(),
-                   [](const TcItem& x, const TcItem& y) { return x.b_tiles > y.b_tiles; });
-  const size_t bytes = items.size() * sizeof(TcItem);
+                   [&](const TcItem& x, const TcItem& y) { return cost(x) > cost(y); });
+  auto cta_of = [&](size_t i) {
+    const int64_t round = int64_t(i) / grid, k = int64_t(i) % grid;
+    return (round & 1) ? grid - 1 - k : k;
+  };
+  std::vector<int64_t> cta_off(size_t(grid) + 1, 0);
+  for (size_t i = 0; i < items.size(); ++i) ++cta_off[size_t(cta_of(i)) + 1];
+  for (int64_t b = 0; b < grid; ++b) cta_off[size_t(b) + 1] += cta_off[size_t(b)];
+  {
+    std::vector<TcItem> by_cta(items.size());
+    std::vector<int64_t> pos(cta_off.begin(), cta_off.end() - 1);
+    for (size_t i = 0; i < items.size(); ++i) by_cta[size_t(pos[size_t(cta_of(i))]++)] = items[i];
+    items.swap(by_cta);
+  }
+  const size_t item_bytes = items.size() * sizeof(TcItem);
+  const size_t bytes = item_bytes + cta_off.size() * sizeof(int64_t);
   TcStaging& st = g_tc_staging;
   cudaError_t e;
   if (st.done && (e = cudaEventSynchronize(st.done)) != cudaSuccess) return e;
@@ -1179,26 +1221,39 @@ cudaError_t indexed_subset_tc(int mode, const RecordIndex& idx, const KeyedIndex
   }
   if (!st.done && (e = cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming)) != cudaSuccess)
     return e;
-  std::memcpy(st.buf, items.data(), bytes);
+  std::memcpy(st.buf, items.data(), item_bytes);
+  std::memcpy(st.buf + item_bytes, cta_off.data(), cta_off.size() * sizeof(int64_t));
   TcItem* d_items = nullptr;
   e = cudaMallocAsync(reinterpret_cast<void**>(&d_items), bytes, s);
   if (e != cudaSuccess) return e;
   e = cudaMemcpyAsync(d_items, st.buf, bytes, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaEventRecord(st.done, s);
   if (e == cudaSuccess) {
+    const KeyedIndex& k0 = *kx[0];
+    const KeyedIndex& k1 = *kx[n_cls - 1];
+    auto narrow = [&](int c) {
+      return mode == MODE_SUM && score_max[c] < (uint64_t(1) << 27) && !force_wide_sums() ? 1 : 0;
+    };
     FusedParams p{d_items,
                   int64_t(items.size()),
-                  own_multi ? idx.rows : kx.rows,
-                  own_multi ? kx.rows : idx.rows,
-                  own_multi ? 1 : 0,
-                  own_multi ? idx.ids : kx.ids,
-                  mode == MODE_SUM ? kx.score : nullptr,
+                  reinterpret_cast<const int64_t*>(reinterpret_cast<const uint8_t*>(d_items) +
+                                                   item_bytes),
+                  k0.rows,
+                  k1.rows,
+                  k0.ids,
+                  k1.ids,
+                  mode == MODE_SUM ? k0.score : nullptr,
+                  mode == MODE_SUM ? k1.score : nullptr,
+                  mode == MODE_SUM ? out_sum[0] : nullptr,
+                  mode == MODE_SUM ? out_sum[n_cls - 1] : nullptr,
+                  narrow(0),
+                  narrow(n_cls - 1),
+                  idx.rows,
+                  0,
                   idx.ids,
-                  mode == MODE_SUM && score_max < (uint64_t(1) << 27) && !force_wide_sums() ? 1 : 0,
                   0u,
                   -1,
                   out_u32,
-                  out_u64,
                   status};
     test_stall(&p.poll_limit, &p.stall_unit);
     void* tok = prof_stage >= 0 ? prof_begin(prof_stage, s) : nullptr;
@@ -1218,6 +1273,18 @@ cudaError_t indexed_subset_tc(int mode, const RecordIndex& idx, const KeyedIndex
   }
   cudaFreeAsync(d_items, s);
   return e;
+}
+
+cudaError_t indexed_subset_tc(int mode, const RecordIndex& idx, const KeyedIndex& kx,
+                              uint32_t* out_u32, unsigned long long* out_u64, int* status,
+                              int64_t* tests_out, int prof_stage, uint64_t score_max,
+                              cudaStream_t s) {
+  *tests_out = 0;
+  if (kx.n == 0 || idx.n_rows == 0 || !tc_supported(idx.KT)) return cudaErrorInvalidValue;
+  const KeyedIndex* kxs[1] = {&kx};
+  unsigned long long* sums[1] = {out_u64};
+  return indexed_subset_tc_classes(mode, idx, kxs, 1, out_u32, sums, status, tests_out,
+                                   prof_stage, &score_max, s);
 }
 
 cudaError_t launch_subset_tc(const TcArgs& a, cudaStream_t s) {
