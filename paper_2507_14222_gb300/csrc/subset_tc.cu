@@ -464,24 +464,28 @@ cudaError_t launch_expand(const uint64_t* rows, int64_t n, int stride, int KT, b
 // subset_tc_fused_kernel: the same 0/1 GEMM on the item index's blocks, with
 // no operand images in global memory.  Packed 64*KT-bit rows are copied by
 // TMA into shared staging.  The resident rows of a work item (one item
-// group's patterns for coherence and support, its records for evidence) are
-// expanded to E4M3 bytes (0x08 = 2^-6 per set bit, which takes one multiply
-// fewer to spread than 1.0) and written into tensor memory, where the MMA
-// reads its A operand; the streamed rows are expanded into swizzled
-// shared-memory tiles of 128 rows (the B operand).  Evidence keeps two
-// 128-row halves of records per item, so each expanded stream tile serves
-// two MMA chains.  Each chain (a "unit": one tile, one half) accumulates
-// into one of two 128-column slots of tensor memory, taken in turn, so the
-// epilogue of one unit overlaps the MMAs of the next.  The grid is
-// persistent: CTA b runs items b, b + gridDim.x, ... with its tensor memory
-// allocated once.  Warp roles:
+// group's patterns, in every mode) are expanded to E4M3 bytes (0x08 = 2^-6
+// per set bit, which takes one multiply fewer to spread than 1.0) and
+// written into tensor memory, where the MMA reads its A operand; the
+// streamed rows (the other class's records for coherence, the own class's
+// records for support, the scored records for evidence) are expanded into
+// swizzled shared-memory tiles of 128 rows (the B operand).  Evidence keeps
+// two 128-row halves of patterns per item, so each expanded stream tile
+// serves two MMA chains.  Each chain (a "unit": one tile, one half)
+// accumulates into one of the 128-column slots of tensor memory, taken in
+// turn, so the epilogue of one unit overlaps the MMAs of the next.  The grid
+// is persistent: CTA b runs the items [cta_off[b], cta_off[b + 1]), lists
+// balanced by the host, with its tensor memory allocated once; an item's
+// class (its pad field) picks the resident rows, scores and outputs, so one
+// launch scores records against both classes.  Warp roles:
 //   warp 0     lane 0 issues the bulk copies of packed rows;
 //   warp 1     allocates tensor memory; lane 0 issues the MMAs and commits;
-//   warps 2-5  epilogue (and 6-9 for evidence, a second group that takes
-//              every other unit): lanes of TMEM quarter w % 4; a min over
-//              32 columns for "any", a count of zeros for "count", a bit
-//              mask of the hits and a loop over its set bits for the
-//              score-weighted sum;
+//   warps 2-5  epilogue (and 6-9 for evidence, a second group; the groups
+//              split every unit's columns): lanes of TMEM quarter w % 4;
+//              per 32 columns one load that also returns their minimum,
+//              then hit masks, the slot handed back, and the reduction: an
+//              "any" for coherence, a count of zeros for support, and for
+//              evidence a warp sum of the patterns' scores per hit record;
 //   the rest   expand packed tiles into operand tiles.
 // Every wait is bounded; a timeout sets the status and an abort flag that
 // every role checks.
