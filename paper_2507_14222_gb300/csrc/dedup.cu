@@ -22,9 +22,12 @@
 // probe keeps lookups exact: slots are written once and never cleared, so a
 // stored key sits within `max_probe` slots of its home, before any empty one.
 //
-// Each CTA counts the keys it adds in shared memory and adds that to the
-// table's count once, when it ends: a per-key atomic on one global counter
-// would serialise every new key in one L2 slice.
+// Warps count the keys they add in registers and add them to the table's
+// count every few hundred keys at most (and their CTA once when it ends): a
+// per-key atomic on one global counter would serialise every new key in one
+// L2 slice.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -47,14 +50,8 @@ __device__ __forceinline__ void pair_key(const uint64_t* __restrict__ X, uint64_
   for (int w = 0; w < KT; ++w) k[w] = __ldg(a + w) & __ldg(b + w);
 }
 
-// A key given as the AND of two rows, read word by word where it is needed
-// instead of being held in registers: rows in shared memory (pair tiles) or
-// in global memory (rehash).
-struct SharedPairKey {
-  const uint64_t* a;
-  const uint64_t* b;
-  __device__ __forceinline__ uint64_t operator()(int w) const { return a[w] & b[w]; }
-};
+// A key held in registers (pair tiles), or given as the AND of two rows of
+// global memory and read word by word where it is needed (rehash).
 template <int KT>
 struct RegKey {
   const uint64_t (&w)[KT];
@@ -115,21 +112,40 @@ constexpr int kPairThreads = 256;
 // more resident CTAs would not help anyway, since their shared memory comes
 // out of the L1 that caches the class's records, which every key comparison
 // reads.
+//
+// Overflow is watched during the tile, not only at its start: warps add
+// their new keys to the table's count every `t.flush` keys, and a warp whose
+// addition takes the count to the limit records its band and stops its
+// whole tile (its band is replayed on the grown table).  Every warp that
+// adds keys learns of the overflow at its next addition, so inserts stop
+// within one flush interval; without the watch, tiles that started before
+// the table filled kept inserting into an ever fuller table, every insert
+// probing up to max_probe slots.  (Polling the count instead cost 0.1-0.4 ms
+// per 148k fit: the poll's latency on that one hot line stalled its warp.)
 template <int KT>
-__global__ void __launch_bounds__(kPairThreads)
-    pair_insert_kernel(const uint64_t* __restrict__ X, int64_t n, int64_t band_lo,
-                       PairTable t, int* status) {
+struct PairSmem {
+  uint64_t A[kPairTile * (KT + 1)];
+  uint64_t B[kPairTile * (KT + 1)];
+  unsigned int n_new;
+  int table_full;
+  volatile int stop_tile;
+};
+
+// One pair tile (bi, bj), bj >= bi, of the records X[0, n): run by the whole
+// CTA, which may run several in turn (the shared state is reset here).
+template <int KT>
+__device__ __forceinline__ void pair_tile(const uint64_t* __restrict__ X, int64_t n, int64_t bi,
+                                          int64_t bj, const PairTable& t, int* status,
+                                          PairSmem<KT>& sm) {
   constexpr int T = kPairTile;
   constexpr int SKT = KT + 1;
-  __shared__ uint64_t A[T * SKT];
-  __shared__ uint64_t B[T * SKT];
-  __shared__ unsigned int n_new;
-  __shared__ int table_full;
-  const int64_t bi = band_lo + blockIdx.y, bj = blockIdx.x;
-  if (bj < bi) return;
+  uint64_t* const A = sm.A;
+  uint64_t* const B = sm.B;
+  __syncthreads();  // every thread is done with the previous tile's state
   if (threadIdx.x == 0) {
-    n_new = 0;
-    table_full = ld_relaxed_u64(reinterpret_cast<const uint64_t*>(t.count)) >= t.limit;
+    sm.n_new = 0;
+    sm.stop_tile = 0;
+    sm.table_full = ld_relaxed_u64(reinterpret_cast<const uint64_t*>(t.count)) >= t.limit;
   }
   const int64_t i0 = bi * T, j0 = bj * T;
   for (int e = threadIdx.x; e < T * KT; e += kPairThreads) {
@@ -138,14 +154,15 @@ __global__ void __launch_bounds__(kPairThreads)
     B[r * SKT + k] = (j0 + r < n) ? X[(j0 + r) * KT + k] : 0ull;
   }
   __syncthreads();
-  if (table_full) {  // uniform: the whole tile waits for the grown table
+  if (sm.table_full) {  // uniform: the whole tile waits for the grown table
     if (threadIdx.x == 0) atomicMin(t.failed_band, int(bi));
     return;
   }
   const int lane = threadIdx.x & 31;
+  unsigned int wnew = 0;  // keys this warp added and has not yet counted (same in every lane)
   for (int p = threadIdx.x; p < T * T; p += kPairThreads) {
     const int i = p / T, j = p - (p / T) * T;
-    bool valid = (i0 + i < n) && (j0 + j < n) && (bi < bj || i <= j);
+    const bool valid = (i0 + i < n) && (j0 + j < n) && (bi < bj || i <= j);
     uint64_t kw[KT];
     uint64_t any = 0;
     uint64_t h = hash_begin();
@@ -155,31 +172,103 @@ __global__ void __launch_bounds__(kPairThreads)
       any |= kw[k];
       h = hash_word(h, kw[k]);
     }
-    const RegKey<KT> key{kw};
     h = hash_end(h);
-    bool has = valid && any != 0;
-    unsigned active = __ballot_sync(0xffffffffu, has);
-    if (!has) continue;
-    // Lanes holding the same key insert it once: the lowest lane of each
-    // group of equal hashes is its leader; a lane whose key equals its
-    // leader's skips the insert.
-    // Most hashes are unique in the warp, and those lanes skip the compare.
-    const unsigned peers = __match_any_sync(active, h);
-    if (__popc(peers) > 1) {
-      const int leader = __ffs(peers) - 1;
-      bool same = true;
+    bool pending = valid && any != 0;
+    const unsigned active = __ballot_sync(0xffffffffu, pending);
+    if (pending) {
+      // Lanes holding the same key insert it once: the lowest lane of each
+      // group of equal hashes is its leader; a lane whose key equals its
+      // leader's skips the insert.  Most hashes are unique in the warp, and
+      // those lanes skip the compare.
+      const unsigned peers = __match_any_sync(active, h);
+      if (__popc(peers) > 1) {
+        const int leader = __ffs(peers) - 1;
+        bool same = true;
 #pragma unroll
-      for (int k = 0; k < KT; ++k) {
-        const uint64_t w = key(k);
-        same &= (__shfl_sync(peers, w, leader) == w);
+        for (int k = 0; k < KT; ++k) same &= (__shfl_sync(peers, kw[k], leader) == kw[k]);
+        if (leader != lane && same) pending = false;
       }
-      if (leader != lane && same) continue;
     }
-    if (table_insert<KT>(t, X, key, h, uint32_t(i0 + i), uint32_t(j0 + j), int(bi), status) == 1)
-      atomicAdd(&n_new, 1u);
+    bool added = false;
+    if (pending)
+      added = table_insert<KT>(t, X, RegKey<KT>{kw}, h, uint32_t(i0 + i), uint32_t(j0 + j),
+                               int(bi), status) == 1;
+    wnew += unsigned(__popc(__ballot_sync(0xffffffffu, added)));
+    if (t.flush && wnew >= t.flush) {
+      if (lane == 0) {
+        const unsigned long long before = atomicAdd(t.count, (unsigned long long)wnew);
+        if (before + wnew >= t.limit) {
+          atomicMin(t.failed_band, int(bi));
+          sm.stop_tile = 1;
+        }
+      }
+      wnew = 0;
+    }
+    if (__shfl_sync(0xffffffffu, lane == 0 ? sm.stop_tile : 0, 0)) break;
   }
+  if (lane == 0 && wnew) atomicAdd(&sm.n_new, wnew);
   __syncthreads();
-  if (threadIdx.x == 0 && n_new != 0) atomicAdd(t.count, (unsigned long long)n_new);
+  if (threadIdx.x == 0 && sm.n_new != 0) atomicAdd(t.count, (unsigned long long)sm.n_new);
+}
+
+template <int KT>
+__global__ void __launch_bounds__(kPairThreads)
+    pair_insert_kernel(const uint64_t* __restrict__ X, int64_t n, int64_t band_lo,
+                       PairTable t, int* status) {
+  __shared__ PairSmem<KT> sm;
+  const int64_t bi = band_lo + blockIdx.y, bj = blockIdx.x;
+  if (bj < bi) return;
+  pair_tile<KT>(X, n, bi, bj, t, status, sm);
+}
+
+// Many tables in one launch (independent problems and classes): a
+// persistent grid takes pair tiles from one device-side queue, the tiles of
+// job j numbered [tile_off[j], tile_off[j + 1]) band by band from the job's
+// band_lo.  Each CTA draws its next tile with one atomic, so large and small
+// jobs share the SMs without a launch per job.
+template <int KT>
+__global__ void __launch_bounds__(kPairThreads, KT >= 16 ? 3 : 5)
+    pair_insert_multi_kernel(const PairJob* __restrict__ jobs, int n_jobs,
+                             const int64_t* __restrict__ tile_off,
+                             unsigned long long* next_tile, int* status) {
+  __shared__ PairSmem<KT> sm;
+  __shared__ int64_t tile[3];  // job, bi, bj
+  __shared__ PairJob job;      // the current tile's job (read from here, not held in registers)
+  const int64_t total = tile_off[n_jobs];
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int64_t q = int64_t(atomicAdd(next_tile, 1ull));
+      tile[0] = -1;
+      if (q < total) {
+        // The job holding tile q, then its band: band b of a job with nt
+        // tile rows starts after sum_{x = band_lo}^{b - 1} (nt - x) tiles.
+        int lo = 0, hi = n_jobs - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (tile_off[mid] <= q) lo = mid; else hi = mid - 1;
+        }
+        const PairJob& jb = jobs[lo];
+        const int64_t nt = ceil_div(jb.n, kPairTile), b0 = jb.band_lo;
+        const int64_t r = q - tile_off[lo];
+        auto before = [&](int64_t b) {  // tiles of the bands [b0, b)
+          return (b - b0) * nt - (b * (b - 1) / 2 - b0 * (b0 - 1) / 2);
+        };
+        int64_t blo = b0, bhi = nt - 1;
+        while (blo < bhi) {
+          const int64_t mid = (blo + bhi + 1) >> 1;
+          if (before(mid) <= r) blo = mid; else bhi = mid - 1;
+        }
+        job = jb;
+        tile[0] = lo;
+        tile[1] = blo;
+        tile[2] = blo + (r - before(blo));
+      }
+    }
+    __syncthreads();
+    const int64_t j = tile[0], bi = tile[1], bj = tile[2];
+    if (j < 0) break;
+    pair_tile<KT>(job.X, job.n, bi, bj, job.t, status, sm);
+  }
 }
 
 template <int KT>
@@ -269,10 +358,39 @@ cudaError_t launch_pair_insert(const uint64_t* X, int64_t n, int KT, int64_t ban
   int64_t nt = ceil_div(n, kPairTile);
   if (band_lo >= nt) return cudaSuccess;
   dim3 grid{unsigned(nt), unsigned(nt - band_lo), 1u};
+  // Warps count their new keys into the table every `flush` keys, often
+  // enough that the count lags the table by at most about a quarter of the
+  // limit over all warps in flight (at most 8 CTAs of 8 warps per SM).
+  const int64_t tiles = (nt - band_lo) * (nt - band_lo + 1) / 2;
+  const int64_t warps = std::min<int64_t>(tiles, int64_t(num_sms()) * 8) * (kPairThreads / 32);
+  t.flush = uint32_t(std::max<int64_t>(1, std::min<int64_t>(256, int64_t(t.limit) / (4 * warps))));
   IG_DISPATCH_KT(KT, (pair_insert_kernel<KTC><<<grid, kPairThreads, 0, s>>>(X, n, band_lo, t,
                                                                              status)));
   count_launches(1);
   return cudaGetLastError();
+}
+
+cudaError_t launch_pair_insert_multi(const PairJob* jobs, int n_jobs, const int64_t* tile_off,
+                                     unsigned long long* next_tile, int KT, int* status,
+                                     cudaStream_t s) {
+  if (n_jobs <= 0) return cudaSuccess;
+  int per_sm = 0;
+  cudaError_t e = cudaSuccess;
+  IG_DISPATCH_KT(KT, (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                          &per_sm, pair_insert_multi_kernel<KTC>, kPairThreads, 0)));
+  if (e != cudaSuccess) return e;
+  const unsigned grid = unsigned(std::max(1, per_sm) * num_sms());
+  IG_DISPATCH_KT(KT, (pair_insert_multi_kernel<KTC><<<grid, kPairThreads, 0, s>>>(
+                         jobs, n_jobs, tile_off, next_tile, status)));
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+int pair_multi_grid_warps(int KT) {
+  int per_sm = 0;
+  IG_DISPATCH_KT(KT, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                         &per_sm, pair_insert_multi_kernel<KTC>, kPairThreads, 0)));
+  return std::max(1, per_sm) * num_sms() * (kPairThreads / 32);
 }
 
 cudaError_t launch_rehash(const uint64_t* X, const uint64_t* from, uint64_t from_cap,

@@ -15,6 +15,7 @@
 #include <cstring>
 #include <condition_variable>
 #include <functional>
+#include <memory>
 #include <thread>
 #include <mutex>
 #include <string>
@@ -590,83 +591,84 @@ struct SideSignal {
   ~SideSignal() { sync->mark(c, -1); }  // no effect once ready
 };
 
-int build_candidates(const uint64_t* X, int64_t n, int KT, cudaStream_t s, int* d_status,
-                     TableCounters* h_counters, DevBuf<uint64_t>& cand, int64_t* U_out) {
-  if (n > int64_t(65535) * igk::kPairTile)
-    return fail(IG_E_OVERFLOW, "ig_fit: more than 4,194,240 records in one class");
-  const int64_t pairs = n * (n + 1) / 2;
-  uint64_t cap = 1u << 12;
-  const int64_t guess = std::max<int64_t>(pairs / 8, 16 * n);
-  while (cap < uint64_t(2 * guess)) cap <<= 1;
+constexpr int kNoBand = 0x7f7f7f7f;  // failed_band after a 0x7f byte fill
 
+// One class's hash set of candidate keys (Eq. 1) between its pair stage and
+// its compaction.
+struct CandTable {
   DevBuf<uint64_t> slots;
-  DevBuf<TableCounters> ctr;
-  IG_CUDA(ctr.alloc(1, s), "ig_fit: table counters");
-  IG_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(TableCounters), s), "ig_fit");
-  IG_CUDA(slots.alloc(cap, s), "ig_fit: hash table");
-  IG_CUDA(cudaMemsetAsync(slots.p, 0, cap * sizeof(uint64_t), s), "ig_fit");
-  auto table = [&](uint64_t* sl, uint64_t c, TableCounters* t, uint64_t max_probe) {
-    igk::PairTable pt;
-    pt.slots = sl;
-    pt.mask = c - 1;
-    pt.count = &t->count;
-    pt.limit = c / 2;
-    pt.max_probe = max_probe;
-    pt.failed_band = &t->failed_band;
-    return pt;
-  };
-  const int kNoBand = 0x7f7f7f7f;  // failed_band after a 0x7f byte fill
-  int64_t band_lo = 0;
-  for (;;) {
-    // failed_band = none, then insert the bands.
-    IG_CUDA(cudaMemsetAsync(&ctr.p->failed_band, 0x7f, sizeof(int), s), "ig_fit");
-    {
-      ProfScope ps(S_PAIR, s);
-      IG_CUDA(igk::launch_pair_insert(X, n, KT, band_lo, table(slots.p, cap, ctr.p, kMaxProbe),
-                                      d_status, s),
-              "ig_fit: pair intersection");
-    }
-    IG_CUDA(cudaMemcpyAsync(h_counters, ctr.p, sizeof(TableCounters), cudaMemcpyDeviceToHost, s),
-            "ig_fit");
-    IG_CUDA(cudaStreamSynchronize(s), "ig_fit");
-    if (h_counters->failed_band == kNoBand) break;
-    // Grow, then replay from the first band that ran out of room.  The bands
-    // before it held `pairs_before` pairs and gave `count` keys; the new table
-    // is sized for twice the count projected at that rate over all pairs
-    // (at least doubling), so that one growth is usually enough.
-    const int64_t failed = h_counters->failed_band;
-    const int64_t T = igk::kPairTile, nt = igk::ceil_div(n, T);
-    int64_t pairs_before = 0, pairs_all = 0;  // tile-granular pair counts
-    for (int64_t r = 0; r < nt; ++r) {
-      const int64_t band = (nt - r) * T * T;
-      pairs_all += band;
-      if (r < failed) pairs_before += band;
-    }
-    const double rate = double(h_counters->count) / double(std::max<int64_t>(1, pairs_before));
-    const double projected = std::min(double(pairs), rate * double(pairs_all)) * 1.25;
-    uint64_t ncap = cap << 1;
-    while (double(ncap) < 2.0 * projected && ncap < (uint64_t(1) << 36)) ncap <<= 1;
-    DevBuf<uint64_t> nslots;
-    DevBuf<TableCounters> nctr;
-    IG_CUDA(nslots.alloc(ncap, s), "ig_fit: hash table");
-    IG_CUDA(nctr.alloc(1, s), "ig_fit: table counters");
-    IG_CUDA(cudaMemsetAsync(nslots.p, 0, ncap * sizeof(uint64_t), s), "ig_fit");
-    IG_CUDA(cudaMemsetAsync(nctr.p, 0, sizeof(TableCounters), s), "ig_fit");
-    {
-      ProfScope ps(S_REHASH, s);
-      // The grown table is at most a quarter full: every rehashed key finds
-      // a slot (probing is unbounded here).
-      IG_CUDA(igk::launch_rehash(X, slots.p, cap, table(nslots.p, ncap, nctr.p, ncap), KT,
-                                 d_status, s),
-              "ig_fit: rehash");
-    }
-    std::swap(slots.p, nslots.p);
-    std::swap(ctr.p, nctr.p);
-    cap = ncap;
-    band_lo = h_counters->failed_band;
+  uint64_t cap = 0;
+};
+
+igk::PairTable make_table(uint64_t* slots, uint64_t cap, TableCounters* t, uint64_t max_probe) {
+  igk::PairTable pt;
+  pt.slots = slots;
+  pt.mask = cap - 1;
+  pt.count = &t->count;
+  pt.limit = cap / 2;
+  pt.max_probe = max_probe;
+  pt.failed_band = &t->failed_band;
+  return pt;
+}
+
+// The table's first capacity: twice a guess of |B^c| (an eighth of the
+// pairs, at least 16 keys per record), a power of two.
+uint64_t initial_cap(int64_t n) {
+  const int64_t pairs = n * (n + 1) / 2;
+  const int64_t guess = std::max<int64_t>(pairs / 8, 16 * n);
+  uint64_t cap = 1u << 12;
+  while (cap < uint64_t(2 * guess)) cap <<= 1;
+  return cap;
+}
+
+cudaError_t alloc_table(CandTable& tab, uint64_t cap, cudaStream_t s) {
+  tab.cap = cap;
+  cudaError_t e = tab.slots.alloc(cap, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tab.slots.p, 0, cap * sizeof(uint64_t), s);
+  return e;
+}
+
+// After a pair launch whose band `failed` ran out of room: a larger table,
+// rehashed from the old one.  The bands before the failed one held
+// `pairs_before` pairs and gave `count` keys; the new table is sized for
+// twice the count projected at that rate over all pairs (at least doubling),
+// so that one growth is usually enough.  The table's counters (d_ctr) are
+// reused: they count the rehashed keys, and failed_band must be reset
+// before the replay.
+int grow_table(const uint64_t* X, int64_t n, int KT, CandTable& tab, TableCounters* d_ctr,
+               int64_t failed, unsigned long long count, int* d_status, cudaStream_t s) {
+  const int64_t pairs = n * (n + 1) / 2;
+  const int64_t T = igk::kPairTile, nt = igk::ceil_div(n, T);
+  int64_t pairs_before = 0, pairs_all = 0;  // tile-granular pair counts
+  for (int64_t r = 0; r < nt; ++r) {
+    const int64_t band = (nt - r) * T * T;
+    pairs_all += band;
+    if (r < failed) pairs_before += band;
   }
-  IG_CHECK(read_status(d_status, s, "ig_fit: candidate generation"));
-  const int64_t U = int64_t(h_counters->count);
+  const double rate = double(count) / double(std::max<int64_t>(1, pairs_before));
+  const double projected = std::min(double(pairs), rate * double(pairs_all)) * 1.25;
+  uint64_t ncap = tab.cap << 1;
+  while (double(ncap) < 2.0 * projected && ncap < (uint64_t(1) << 36)) ncap <<= 1;
+  CandTable grown;
+  IG_CUDA(alloc_table(grown, ncap, s), "ig_fit: hash table");
+  IG_CUDA(cudaMemsetAsync(d_ctr, 0, sizeof(TableCounters), s), "ig_fit");
+  {
+    ProfScope ps(S_REHASH, s);
+    // The grown table is at most a quarter full: every rehashed key finds
+    // a slot (probing is unbounded here).
+    IG_CUDA(igk::launch_rehash(X, tab.slots.p, tab.cap, make_table(grown.slots.p, ncap, d_ctr, ncap),
+                               KT, d_status, s),
+            "ig_fit: rehash");
+  }
+  std::swap(tab.slots.p, grown.slots.p);  // the old slots are freed (after the rehash) on s
+  tab.cap = ncap;
+  return IG_OK;
+}
+
+// Appends the U keys of a finished table to `cand` (canonical order comes
+// later) and frees the table.
+int compact_table(const uint64_t* X, int KT, CandTable& tab, int64_t U, int* d_status,
+                  DevBuf<uint64_t>& cand, cudaStream_t s) {
   if (U > int64_t(0xffffffffll)) return fail(IG_E_OVERFLOW, "ig_fit: too many candidates");
   IG_CUDA(cand.alloc(size_t(igk::pad_rows(U)) * KT, s), "ig_fit: candidates");
   DevBuf<unsigned long long> out_count;
@@ -674,12 +676,62 @@ int build_candidates(const uint64_t* X, int64_t n, int KT, cudaStream_t s, int* 
   IG_CUDA(cudaMemsetAsync(out_count.p, 0, sizeof(unsigned long long), s), "ig_fit");
   {
     ProfScope ps(S_COMPACT, s);
-    IG_CUDA(igk::launch_compact(X, slots.p, cap, KT, cand.p, U, out_count.p, d_status, s),
+    IG_CUDA(igk::launch_compact(X, tab.slots.p, tab.cap, KT, cand.p, U, out_count.p, d_status, s),
             "ig_fit: compact");
   }
+  tab.slots.s = s;
+  tab.slots.reset();
+  return IG_OK;
+}
+
+// Candidate generation (Eq. 1) for one class, deduplicated on the device.
+// One launch covers every pair band; if the table runs out of room the
+// launch records the lowest band that failed, and the table is grown,
+// rehashed and the bands from that one on are replayed (inserts are
+// idempotent).  Typical workloads need one launch.
+int build_candidates(const uint64_t* X, int64_t n, int KT, cudaStream_t s, int* d_status,
+                     TableCounters* h_counters, DevBuf<uint64_t>& cand, int64_t* U_out) {
+  if (n > int64_t(65535) * igk::kPairTile)
+    return fail(IG_E_OVERFLOW, "ig_fit: more than 4,194,240 records in one class");
+  CandTable tab;
+  DevBuf<TableCounters> ctr;
+  IG_CUDA(ctr.alloc(1, s), "ig_fit: table counters");
+  IG_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(TableCounters), s), "ig_fit");
+  IG_CUDA(alloc_table(tab, initial_cap(n), s), "ig_fit: hash table");
+  int64_t band_lo = 0;
+  for (;;) {
+    // failed_band = none, then insert the bands.
+    IG_CUDA(cudaMemsetAsync(&ctr.p->failed_band, 0x7f, sizeof(int), s), "ig_fit");
+    {
+      ProfScope ps(S_PAIR, s);
+      IG_CUDA(igk::launch_pair_insert(X, n, KT, band_lo,
+                                      make_table(tab.slots.p, tab.cap, ctr.p, kMaxProbe), d_status,
+                                      s),
+              "ig_fit: pair intersection");
+    }
+    IG_CUDA(cudaMemcpyAsync(h_counters, ctr.p, sizeof(TableCounters), cudaMemcpyDeviceToHost, s),
+            "ig_fit");
+    IG_CUDA(cudaStreamSynchronize(s), "ig_fit");
+    if (h_counters->failed_band == kNoBand) break;
+    band_lo = h_counters->failed_band;
+    IG_CHECK(grow_table(X, n, KT, tab, ctr.p, band_lo, h_counters->count, d_status, s));
+  }
+  IG_CHECK(read_status(d_status, s, "ig_fit: candidate generation"));
+  const int64_t U = int64_t(h_counters->count);
+  IG_CHECK(compact_table(X, KT, tab, U, d_status, cand, s));
   *U_out = U;
   return IG_OK;
 }
+
+// What the batched candidate stage hands to a problem's fit: its class
+// matrices and, per class, the finished table of candidate keys.
+struct FitPrep {
+  bool ready = false;
+  DevBuf<uint64_t> X[2];
+  int64_t nc[2] = {0, 0};
+  CandTable tab[2];
+  int64_t count[2] = {0, 0};
+};
 
 }  // namespace
 
@@ -724,10 +776,15 @@ int ig_encode(const uint16_t* codes, int64_t n, int32_t F, const uint16_t* cards
   return read_status(d_status.p, s, "ig_encode");
 }
 
-int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
-           const ig_params* params, ig_model** out, ig_stream_t stream) {
-  igk::DeviceRestore restore_device;  // the caller's device, put back on return
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+}  // extern "C"
+
+namespace {
+
+// ig_fit's body.  With `prep` (from ig_fit_batched's candidate stage) the
+// class matrices and the candidate tables are already built: the split and
+// the pair stage are skipped and each class starts at its compaction.
+int fit_impl(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
+             const ig_params* params, ig_model** out, cudaStream_t s, FitPrep* prep) {
   if (!out) return fail(IG_E_INVAL, "ig_fit: out is NULL");
   *out = nullptr;
   if (!rows || !labels || n < 2) return fail(IG_E_INVAL, "ig_fit: need at least two records");
@@ -747,39 +804,50 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
 
   InputView<uint64_t> in_rows;
   InputView<uint8_t> in_lab;
-  IG_CHECK(in_rows.bind(rows, size_t(n) * K, s, "ig_fit: rows"));
-  IG_CHECK(in_lab.bind(labels, size_t(n), s, "ig_fit: labels"));
+  if (!prep) {
+    IG_CHECK(in_rows.bind(rows, size_t(n) * K, s, "ig_fit: rows"));
+    IG_CHECK(in_lab.bind(labels, size_t(n), s, "ig_fit: labels"));
+  }
 
   DevBuf<int> d_status;
   DevBuf<unsigned long long> d_counts;
   IG_CUDA(d_status.alloc(1, s), "ig_fit");
   IG_CUDA(d_counts.alloc(2, s), "ig_fit");
   IG_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), s), "ig_fit");
-  // Pinned host words for size read-backs: [0..1] class counts, [2] scratch,
-  // [4..7] hash-table counters.
+  // Pinned host words for size read-backs: [0..1] class counts, [2..3] the
+  // classes' largest scores.
   static thread_local unsigned long long* h_pinned = nullptr;
   if (!h_pinned) IG_CUDA(cudaMallocHost(&h_pinned, 8 * sizeof(unsigned long long)), "ig_fit");
-  TableCounters* h_counters = reinterpret_cast<TableCounters*>(h_pinned + 4);
   // [2 + c]: the largest score of class c, copied back by its class stream.
   unsigned long long* const h_smax = h_pinned + 2;
 
   // Section 3.2: class-stacked row matrices (normal -> X[0], attack -> X[1]).
   DevBuf<uint64_t> X[2];
-  // One spare tile of rows beyond the padding: record windows of the
-  // coherence rounds may start at any multiple of 32 rows.
-  for (int c = 0; c < 2; ++c)
-    IG_CUDA(X[c].alloc(size_t(igk::pad_rows(n) + igk::kRowPad) * KT, s), "ig_fit: rows");
-  {
-    ProfScope ps(S_SPLIT, s);
-    IG_CUDA(igk::launch_split(in_rows.d, in_lab.d, n, K, KT, X[0].p, X[1].p, d_counts.p,
-                              d_status.p, s),
-            "ig_fit: split");
+  int64_t nc[2];
+  if (prep) {
+    for (int c = 0; c < 2; ++c) {
+      X[c].p = prep->X[c].release();
+      X[c].s = s;
+      nc[c] = prep->nc[c];
+    }
+  } else {
+    // One spare tile of rows beyond the padding: record windows of the
+    // coherence rounds may start at any multiple of 32 rows.
+    for (int c = 0; c < 2; ++c)
+      IG_CUDA(X[c].alloc(size_t(igk::pad_rows(n) + igk::kRowPad) * KT, s), "ig_fit: rows");
+    {
+      ProfScope ps(S_SPLIT, s);
+      IG_CUDA(igk::launch_split(in_rows.d, in_lab.d, n, K, KT, X[0].p, X[1].p, d_counts.p,
+                                d_status.p, s),
+              "ig_fit: split");
+    }
+    IG_CUDA(cudaMemcpyAsync(h_pinned, d_counts.p, 2 * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, s),
+            "ig_fit");
+    IG_CHECK(read_status(d_status.p, s, "ig_fit: labels"));
+    nc[0] = int64_t(h_pinned[0]);
+    nc[1] = int64_t(h_pinned[1]);
   }
-  IG_CUDA(cudaMemcpyAsync(h_pinned, d_counts.p, 2 * sizeof(unsigned long long),
-                          cudaMemcpyDeviceToHost, s),
-          "ig_fit");
-  IG_CHECK(read_status(d_status.p, s, "ig_fit: labels"));
-  const int64_t nc[2] = {int64_t(h_pinned[0]), int64_t(h_pinned[1])};
   if (nc[0] == 0 || nc[1] == 0) return fail(IG_E_INVAL, "ig_fit: both classes must be non-empty");
 
   ig_model* m = new ig_model;
@@ -839,7 +907,12 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
     // Eq. 1: B^c, deduplicated on the device.
     DevBuf<uint64_t> cand;
     int64_t U = 0;
-    IG_CHECK(build_candidates(X[c].p, nc[c], KT, s, d_status.p, h_counters, cand, &U));
+    if (prep) {
+      U = prep->count[c];
+      IG_CHECK(compact_table(X[c].p, KT, prep->tab[c], U, d_status.p, cand, s));
+    } else {
+      IG_CHECK(build_candidates(X[c].p, nc[c], KT, s, d_status.p, h_counters, cand, &U));
+    }
     m->n_cand[c] = U;
     // Eq. 3 (tested as Eq. 6): drop candidates inside any opposite record.
     // The opposite records are tested in growing windows; after each window
@@ -1196,6 +1269,192 @@ int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
   return IG_OK;
 }
 
+// Pinned host scratch of at least `bytes`, one block per host thread.
+void* pinned_scratch(size_t bytes) {
+  static thread_local void* p = nullptr;
+  static thread_local size_t cap = 0;
+  if (bytes > cap) {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    if (cudaMallocHost(&p, bytes) != cudaSuccess) return nullptr;
+    cap = bytes;
+  }
+  return p;
+}
+
+// The candidate stage (Eq. 1) of every problem of a batch at once: the
+// class split of every problem, one read-back of all class sizes, then the
+// pair tiles of every class of every problem in one launch per word count
+// (a persistent grid drawing tiles from a device-side queue), one read-back
+// of all tables' counters, and replays of the tables that ran out of room
+// (grown and rehashed one by one, replayed together).  A problem that this
+// stage cannot prepare (bad arguments, bad labels, an empty class) is left
+// unprepared: its own fit then runs every step and reports the error.
+int batched_candidates(const ig_problem* problems, int32_t np, const ig_params* params,
+                       std::vector<FitPrep>& prep, cudaStream_t s) {
+  struct Inputs {
+    InputView<uint64_t> rows;
+    InputView<uint8_t> lab;
+  };
+  std::unique_ptr<Inputs[]> in(new Inputs[np]);
+  std::vector<char> ok(np, 0);
+  DevBuf<unsigned long long> d_counts;
+  DevBuf<int> d_status;
+  IG_CUDA(d_counts.alloc(size_t(2) * np, s), "ig_fit_batched");
+  // Status words: one per problem (its split), and one for the pair stage.
+  IG_CUDA(d_status.alloc(size_t(np) + 1, s), "ig_fit_batched");
+  IG_CUDA(cudaMemsetAsync(d_counts.p, 0, sizeof(unsigned long long) * 2 * np, s), "ig_fit_batched");
+  IG_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int) * (np + 1), s), "ig_fit_batched");
+  int* const pair_status = d_status.p + np;
+  for (int32_t i = 0; i < np; ++i) {
+    const ig_problem& pr = problems[i];
+    const ig_params* prm = pr.params ? pr.params : params;
+    if (!pr.rows || !pr.labels || pr.n < 2 || pr.K < 1 || pr.K > IG_MAX_WORDS ||
+        pr.n > int64_t(0x7fffffff) || (prm && prm->subset_kernel < 0))
+      continue;
+    const int KT = igk::padded_words(pr.K);
+    if (in[i].rows.bind(pr.rows, size_t(pr.n) * pr.K, s, "ig_fit_batched: rows") != IG_OK ||
+        in[i].lab.bind(pr.labels, size_t(pr.n), s, "ig_fit_batched: labels") != IG_OK)
+      continue;
+    for (int c = 0; c < 2; ++c)
+      IG_CUDA(prep[i].X[c].alloc(size_t(igk::pad_rows(pr.n) + igk::kRowPad) * KT, s),
+              "ig_fit_batched: rows");
+    {
+      ProfScope ps(S_SPLIT, s);
+      IG_CUDA(igk::launch_split(in[i].rows.d, in[i].lab.d, pr.n, pr.K, KT, prep[i].X[0].p,
+                                prep[i].X[1].p, d_counts.p + 2 * i, d_status.p + i, s),
+              "ig_fit_batched: split");
+    }
+    ok[i] = 1;
+  }
+  const size_t n_ctr = size_t(2) * np;
+  char* h = static_cast<char*>(pinned_scratch(n_ctr * sizeof(TableCounters) +
+                                              n_ctr * sizeof(unsigned long long) +
+                                              (size_t(np) + 1) * sizeof(int)));
+  if (!h) return fail(IG_E_CUDA, "ig_fit_batched: pinned host allocation failed");
+  TableCounters* h_ctr = reinterpret_cast<TableCounters*>(h);
+  unsigned long long* h_counts = reinterpret_cast<unsigned long long*>(h_ctr + n_ctr);
+  int* h_status = reinterpret_cast<int*>(h_counts + n_ctr);
+  IG_CUDA(cudaMemcpyAsync(h_counts, d_counts.p, sizeof(unsigned long long) * n_ctr,
+                          cudaMemcpyDeviceToHost, s),
+          "ig_fit_batched");
+  IG_CUDA(cudaMemcpyAsync(h_status, d_status.p, sizeof(int) * np, cudaMemcpyDeviceToHost, s),
+          "ig_fit_batched");
+  IG_CUDA(cudaStreamSynchronize(s), "ig_fit_batched");
+
+  // Tables of the problems whose split succeeded with both classes present.
+  struct Job {
+    int32_t i;
+    int c;
+    int KT;
+  };
+  std::vector<Job> jobs;
+  for (int32_t i = 0; i < np; ++i) {
+    if (!ok[i]) continue;
+    const int64_t nc[2] = {int64_t(h_counts[2 * i]), int64_t(h_counts[2 * i + 1])};
+    if (h_status[i] != 0 || nc[0] == 0 || nc[1] == 0 ||
+        std::max(nc[0], nc[1]) > int64_t(65535) * igk::kPairTile) {
+      ok[i] = 0;
+      continue;
+    }
+    for (int c = 0; c < 2; ++c) {
+      prep[i].nc[c] = nc[c];
+      IG_CUDA(alloc_table(prep[i].tab[c], initial_cap(nc[c]), s), "ig_fit_batched: hash table");
+      jobs.push_back(Job{i, c, igk::padded_words(problems[i].K)});
+    }
+  }
+  DevBuf<TableCounters> d_ctr;
+  IG_CUDA(d_ctr.alloc(std::max<size_t>(1, jobs.size()), s), "ig_fit_batched");
+  for (size_t k = 0; k < jobs.size(); ++k) h_ctr[k] = TableCounters{0ull, kNoBand, 0};
+  IG_CUDA(cudaMemcpyAsync(d_ctr.p, h_ctr, sizeof(TableCounters) * jobs.size(),
+                          cudaMemcpyHostToDevice, s),
+          "ig_fit_batched");
+  std::vector<int64_t> band_lo(jobs.size(), 0);
+  std::vector<size_t> todo(jobs.size());
+  for (size_t k = 0; k < jobs.size(); ++k) todo[k] = k;
+  DevBuf<igk::PairJob> d_jobs;
+  DevBuf<int64_t> d_off;
+  DevBuf<unsigned long long> d_next;
+  while (!todo.empty()) {
+    // One launch per word count over the tables still to do.
+    for (int KT : {1, 2, 4, 8, 16}) {
+      std::vector<igk::PairJob> pj;
+      std::vector<int64_t> off{0};
+      const int warps = igk::pair_multi_grid_warps(KT);
+      for (size_t k : todo) {
+        const Job& jb = jobs[k];
+        if (jb.KT != KT) continue;
+        FitPrep& pp = prep[jb.i];
+        igk::PairJob j;
+        j.X = pp.X[jb.c].p;
+        j.n = pp.nc[jb.c];
+        j.band_lo = band_lo[k];
+        j.t = make_table(pp.tab[jb.c].slots.p, pp.tab[jb.c].cap, d_ctr.p + k, kMaxProbe);
+        // Warps add their keys to the count often enough that it lags the
+        // table by at most about a quarter of the limit over the whole grid.
+        j.t.flush = uint32_t(std::max<int64_t>(
+            1, std::min<int64_t>(256, int64_t(j.t.limit) / (4 * int64_t(warps)))));
+        const int64_t nt = igk::ceil_div(j.n, igk::kPairTile), rows = nt - j.band_lo;
+        pj.push_back(j);
+        off.push_back(off.back() + rows * (rows + 1) / 2);
+      }
+      if (pj.empty()) continue;
+      // Buffers of the previous launch are freed in stream order first.
+      IG_CUDA(d_jobs.alloc(pj.size(), s), "ig_fit_batched");
+      IG_CUDA(d_off.alloc(off.size(), s), "ig_fit_batched");
+      IG_CUDA(d_next.alloc(1, s), "ig_fit_batched");
+      IG_CUDA(cudaMemcpyAsync(d_jobs.p, pj.data(), sizeof(igk::PairJob) * pj.size(),
+                              cudaMemcpyHostToDevice, s),
+              "ig_fit_batched");
+      IG_CUDA(cudaMemcpyAsync(d_off.p, off.data(), sizeof(int64_t) * off.size(),
+                              cudaMemcpyHostToDevice, s),
+              "ig_fit_batched");
+      IG_CUDA(cudaMemsetAsync(d_next.p, 0, sizeof(unsigned long long), s), "ig_fit_batched");
+      ProfScope ps(S_PAIR, s);
+      IG_CUDA(igk::launch_pair_insert_multi(d_jobs.p, int(pj.size()), d_off.p, d_next.p, KT,
+                                            pair_status, s),
+              "ig_fit_batched: pair intersection");
+    }
+    IG_CUDA(cudaMemcpyAsync(h_ctr, d_ctr.p, sizeof(TableCounters) * jobs.size(),
+                            cudaMemcpyDeviceToHost, s),
+            "ig_fit_batched");
+    IG_CUDA(cudaStreamSynchronize(s), "ig_fit_batched");
+    std::vector<size_t> again;
+    for (size_t k : todo) {
+      if (h_ctr[k].failed_band == kNoBand) continue;
+      const Job& jb = jobs[k];
+      FitPrep& pp = prep[jb.i];
+      band_lo[k] = h_ctr[k].failed_band;
+      IG_CHECK(grow_table(pp.X[jb.c].p, pp.nc[jb.c], jb.KT, pp.tab[jb.c], d_ctr.p + k, band_lo[k],
+                          h_ctr[k].count, pair_status, s));
+      IG_CUDA(cudaMemsetAsync(&d_ctr.p[k].failed_band, 0x7f, sizeof(int), s), "ig_fit_batched");
+      again.push_back(k);
+    }
+    todo.swap(again);
+  }
+  IG_CUDA(cudaMemcpyAsync(h_status, d_status.p, sizeof(int) * (np + 1), cudaMemcpyDeviceToHost,
+                          s),
+          "ig_fit_batched");
+  IG_CUDA(cudaStreamSynchronize(s), "ig_fit_batched");
+  for (size_t k = 0; k < jobs.size(); ++k) prep[jobs[k].i].count[jobs[k].c] = int64_t(h_ctr[k].count);
+  // A pair-stage status (which no table should raise) leaves every problem
+  // to its own fit.
+  for (int32_t i = 0; i < np; ++i) prep[i].ready = ok[i] && h_status[i] == 0 && h_status[np] == 0;
+  return IG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
+           const ig_params* params, ig_model** out, ig_stream_t stream) {
+  igk::DeviceRestore restore_device;  // the caller's device, put back on return
+  return fit_impl(rows, labels, n, K, params, out, reinterpret_cast<cudaStream_t>(stream),
+                  nullptr);
+}
+
 int ig_fit_batched(const ig_problem* problems, int32_t n_problems, const ig_params* params,
                    int32_t lanes, ig_model** out, ig_stream_t stream) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -1213,6 +1472,8 @@ int ig_fit_batched(const ig_problem* problems, int32_t n_problems, const ig_para
   });
   int dev = 0;
   IG_CUDA(cudaGetDevice(&dev), "ig_fit_batched");
+  std::vector<FitPrep> prep(n_problems);
+  IG_CHECK(batched_candidates(problems, n_problems, params, prep, s));
   cudaEvent_t ready = nullptr;
   IG_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming), "ig_fit_batched");
   IG_CUDA(cudaEventRecord(ready, s), "ig_fit_batched");
@@ -1233,8 +1494,9 @@ int ig_fit_batched(const ig_problem* problems, int32_t n_problems, const ig_para
       const int32_t k = next.fetch_add(1);
       if (k >= n_problems) break;
       const ig_problem& pr = problems[order[k]];
-      const int rc = ig_fit(pr.rows, pr.labels, pr.n, pr.K, pr.params ? pr.params : params,
-                            &out[order[k]], reinterpret_cast<ig_stream_t>(ls[l]));
+      FitPrep* pp = prep[order[k]].ready ? &prep[order[k]] : nullptr;
+      const int rc = fit_impl(pr.rows, pr.labels, pr.n, pr.K, pr.params ? pr.params : params,
+                              &out[order[k]], ls[l], pp);
       if (rc != IG_OK) {
         std::lock_guard<std::mutex> lk(err_mu);
         if (first_rc == IG_OK) {
