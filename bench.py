@@ -312,10 +312,11 @@ def run_ours(args):
 
 
 def measure_batched(args, ig, torch, local, steps, warmup, seed=2000):
-    """64 independent problems per step: one ig_fit_batched call against one
-    ig_fit per problem (the plain per-problem launch), same inputs, same
-    process; scoring runs per problem in both.  The models must be
-    byte-identical.  Returns the measurements (ms per step of each form)."""
+    """64 independent problems per step, each fitted and its test records
+    scored: one ig_fit_batched and one ig_score_batched call against one
+    ig_fit and one ig_score per problem (the plain per-problem launches),
+    same inputs, same process.  Models and scores must be identical.
+    Returns the measurements (ms per step of each form)."""
     probs = igdata.batched(igdata.BATCHED_PROBLEMS, seed)
     dev = []
     for w in probs:
@@ -344,6 +345,8 @@ def measure_batched(args, ig, torch, local, steps, warmup, seed=2000):
             models = ig.ig_fit_batched([(r, lab) for r, lab, _ in enc],
                                        subset_kernel=args.kernel,
                                        per_problem_params=per_params)
+            scores = ig.ig_score_batched([(mdl, te) for mdl, (_, _, te) in zip(models, enc)])
+            return models, scores
         else:
             models = []
             for (r, lab, _), pp in zip(enc, per_params):
@@ -353,9 +356,8 @@ def measure_batched(args, ig, torch, local, steps, warmup, seed=2000):
                     models.append(ig.ig_fit(r, lab, subset_kernel=pp.subset_kernel,
                                             index_max_q=pp.index_max_q,
                                             index_flip_factor=pp.index_flip_factor))
-        for mdl, (_, _, te) in zip(models, enc):
-            ig.ig_score(mdl, te)
-        return models
+        scores = [ig.ig_score(mdl, te) for mdl, (_, _, te) in zip(models, enc)]
+        return models, scores
 
     def timed(batched, n):
         ms, last = [], None
@@ -367,31 +369,32 @@ def measure_batched(args, ig, torch, local, steps, warmup, seed=2000):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            models = step(batched)
+            models, scores = step(batched)
             b.record(stream)
             torch.cuda.synchronize()
             ms.append(a.elapsed_time(b))
             last = models
-        return ms, last
+        return ms, last, scores
 
     for _ in range(warmup):
         for form in (True, False):
-            for mdl in step(form):
+            for mdl in step(form)[0]:
                 mdl.free()
     torch.cuda.synchronize()
     launches0 = ig.launch_count()
     with ClockSampler(local) as clk:
-        ms_b, models_b = timed(True, steps)
+        ms_b, models_b, scores_b = timed(True, steps)
     launches = (ig.launch_count() - launches0) // max(1, steps)
-    ms_s, models_s = timed(False, steps)
+    ms_s, models_s, scores_s = timed(False, steps)
     identical = True
     total_tests = 0
-    for w, mb, ms_ in zip(probs, models_b, models_s):
+    for w, mb, ms_, sb, ss in zip(probs, models_b, models_s, scores_b, scores_s):
         ib = mb.info()
         total_tests += nominal_tests(ib, w.test_codes.shape[0])["total"]
         for cls in (0, 1):
             identical &= all(np.array_equal(x, y) for x, y in zip(mb.patterns(cls),
                                                                    ms_.patterns(cls)))
+        identical &= all(bool(torch.equal(x, y)) for x, y in zip(sb, ss))
         mb.free()
         ms_.free()
     return {"problems": len(probs), "ms_per_step": statistics.median(ms_b),

@@ -155,6 +155,29 @@ typedef struct {
 int ig_fit_batched(const ig_problem* problems, int32_t n_problems, const ig_params* p,
                    int32_t lanes, ig_model** out, ig_stream_t stream);
 
+/* One job of a batched scoring call: records of the model's width K and
+ * the outputs, exactly as for ig_score. */
+typedef struct {
+  const ig_model* model;
+  const uint64_t* rows;  /* uint64[m][K], device or host */
+  int64_t m;
+  int64_t* A_out;        /* int64[m], device or host */
+  int64_t* N_out;        /* int64[m] */
+  uint8_t* label_out;    /* uint8[m] */
+} ig_score_job;
+
+/* Batched IG inference: n_jobs independent scoring calls (evidence of Eq. 4
+ * and the labels of Regulations 1-3, each exactly as ig_score computes it;
+ * jobs may share a model) run concurrently on up to `lanes` streams (0 = 8),
+ * the largest batches first, every lane pulling the next job when it
+ * finishes one -- the batch-level scheduling of Section 3.3 applied across
+ * independent problems.  Work is ordered after what `stream` holds when the
+ * call starts and before what is enqueued on it afterwards; the call
+ * returns when every result is in place.  On an error the first error is
+ * reported (naming the job); the other jobs' outputs are then unspecified. */
+int ig_score_batched(const ig_score_job* jobs, int32_t n_jobs, int32_t lanes,
+                     ig_stream_t stream);
+
 /* Builds a model from given pattern sets (Section 3.1's dictionaries P^-
  * and P^+, learned elsewhere), e.g. to serve them: for class c (0 = normal,
  * 1 = attack) words[c] is uint64[n_patterns[c]][K] (any order; non-empty,

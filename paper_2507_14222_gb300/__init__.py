@@ -89,6 +89,7 @@ SIGNATURES = {
     "ig_prof_timeline": (ctypes.c_int, [_P, _P, _P, _P, _I64, _P]),
     "ig_score_noalloc": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P]),
     "ig_fit_batched": (ctypes.c_int, [_P, _I32, _P, _I32, _P, _P]),
+    "ig_score_batched": (ctypes.c_int, [_P, _I32, _I32, _P]),
     "ig_probe": (ctypes.c_int, [_I32, _I32, _P, _P, _P]),
     "ig_model_from_patterns": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P]),
     "ig_server_create": (ctypes.c_int, [_P, _P, _P]),
@@ -314,6 +315,40 @@ def ig_fit_batched(problems, r: float | None = None, subset_kernel: int = 0,
     _check(lib.ig_fit_batched(arr, len(problems), ctypes.byref(prm), int(lanes), outs,
                               _stream(stream) if any_torch else None))
     return [Model(ctypes.c_void_p(outs[i])) for i in range(len(problems))]
+
+
+class ig_score_job(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_void_p), ("rows", ctypes.c_void_p), ("m", ctypes.c_int64),
+                ("A_out", ctypes.c_void_p), ("N_out", ctypes.c_void_p),
+                ("label_out", ctypes.c_void_p)]
+
+
+def ig_score_batched(jobs, lanes: int = 0, stream=None) -> list:
+    """Scores independent batches [(model, rows), ...] concurrently, each
+    exactly as ig_score would; returns [(A, N, labels), ...] in order."""
+    lib = load()
+    arr = (ig_score_job * max(1, len(jobs)))()
+    keep, outs = [], []
+    any_torch = False
+    for i, (model, rows) in enumerate(jobs):
+        m, _ = _check_score_rows(model, rows)
+        if _is_torch(rows):
+            import torch
+            any_torch = True
+            A = torch.empty(m, dtype=torch.int64, device=rows.device)
+            N = torch.empty(m, dtype=torch.int64, device=rows.device)
+            lab = torch.empty(m, dtype=torch.uint8, device=rows.device)
+        else:
+            rows = np.ascontiguousarray(rows, dtype=np.uint64)
+            A = np.empty(m, np.int64)
+            N = np.empty(m, np.int64)
+            lab = np.empty(m, np.uint8)
+        keep.append(rows)
+        outs.append((A, N, lab))
+        arr[i] = ig_score_job(model.handle, _ptr(rows), m, _ptr(A), _ptr(N), _ptr(lab))
+    _check(lib.ig_score_batched(arr, len(jobs), int(lanes),
+                                _stream(stream) if any_torch else None))
+    return outs
 
 
 def _check_score_rows(model: Model, rows):

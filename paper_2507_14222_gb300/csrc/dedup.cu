@@ -27,6 +27,7 @@
 // per-key atomic on one global counter would serialise every new key in one
 // L2 slice.
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 #include "internal.h"
@@ -221,17 +222,25 @@ __global__ void __launch_bounds__(kPairThreads)
   pair_tile<KT>(X, n, bi, bj, t, status, sm);
 }
 
-// Many tables in one launch (independent problems and classes): a
-// persistent grid takes pair tiles from one device-side queue, the tiles of
-// job j numbered [tile_off[j], tile_off[j + 1]) band by band from the job's
-// band_lo.  Each CTA draws its next tile with one atomic, so large and small
-// jobs share the SMs without a launch per job.
-template <int KT>
-__global__ void __launch_bounds__(kPairThreads, KT >= 16 ? 3 : 5)
+// Many tables in one launch (independent problems and classes, of any word
+// count): a persistent grid takes pair tiles from one device-side queue,
+// the tiles of job j numbered [tile_off[j], tile_off[j + 1]) band by band
+// from the job's band_lo.  Each CTA draws its next tile with one atomic, so
+// large and small jobs share the SMs without a launch per job; a tile runs
+// the code of its job's word count in shared memory sized for the largest.
+union PairSmemAny {
+  PairSmem<1> k1;
+  PairSmem<2> k2;
+  PairSmem<4> k4;
+  PairSmem<8> k8;
+  PairSmem<16> k16;
+};
+
+__global__ void __launch_bounds__(kPairThreads, 4)
     pair_insert_multi_kernel(const PairJob* __restrict__ jobs, int n_jobs,
                              const int64_t* __restrict__ tile_off,
                              unsigned long long* next_tile, int* status) {
-  __shared__ PairSmem<KT> sm;
+  __shared__ PairSmemAny sm;
   __shared__ int64_t tile[3];  // job, bi, bj
   __shared__ PairJob job;      // the current tile's job (read from here, not held in registers)
   const int64_t total = tile_off[n_jobs];
@@ -267,7 +276,13 @@ __global__ void __launch_bounds__(kPairThreads, KT >= 16 ? 3 : 5)
     __syncthreads();
     const int64_t j = tile[0], bi = tile[1], bj = tile[2];
     if (j < 0) break;
-    pair_tile<KT>(job.X, job.n, bi, bj, job.t, status, sm);
+    switch (job.KT) {  // uniform
+      case 1: pair_tile<1>(job.X, job.n, bi, bj, job.t, status, sm.k1); break;
+      case 2: pair_tile<2>(job.X, job.n, bi, bj, job.t, status, sm.k2); break;
+      case 4: pair_tile<4>(job.X, job.n, bi, bj, job.t, status, sm.k4); break;
+      case 8: pair_tile<8>(job.X, job.n, bi, bj, job.t, status, sm.k8); break;
+      default: pair_tile<16>(job.X, job.n, bi, bj, job.t, status, sm.k16); break;
+    }
   }
 }
 
@@ -371,26 +386,25 @@ cudaError_t launch_pair_insert(const uint64_t* X, int64_t n, int KT, int64_t ban
 }
 
 cudaError_t launch_pair_insert_multi(const PairJob* jobs, int n_jobs, const int64_t* tile_off,
-                                     unsigned long long* next_tile, int KT, int* status,
-                                     cudaStream_t s) {
+                                     unsigned long long* next_tile, int* status, cudaStream_t s) {
   if (n_jobs <= 0) return cudaSuccess;
-  int per_sm = 0;
-  cudaError_t e = cudaSuccess;
-  IG_DISPATCH_KT(KT, (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                          &per_sm, pair_insert_multi_kernel<KTC>, kPairThreads, 0)));
-  if (e != cudaSuccess) return e;
-  const unsigned grid = unsigned(std::max(1, per_sm) * num_sms());
-  IG_DISPATCH_KT(KT, (pair_insert_multi_kernel<KTC><<<grid, kPairThreads, 0, s>>>(
-                         jobs, n_jobs, tile_off, next_tile, status)));
+  pair_insert_multi_kernel<<<unsigned(pair_multi_grid_warps() / (kPairThreads / 32)),
+                             kPairThreads, 0, s>>>(jobs, n_jobs, tile_off, next_tile, status);
   count_launches(1);
   return cudaGetLastError();
 }
 
-int pair_multi_grid_warps(int KT) {
-  int per_sm = 0;
-  IG_DISPATCH_KT(KT, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                         &per_sm, pair_insert_multi_kernel<KTC>, kPairThreads, 0)));
-  return std::max(1, per_sm) * num_sms() * (kPairThreads / 32);
+int pair_multi_grid_warps() {
+  static std::atomic<int> per_sm{0};
+  int v = per_sm.load(std::memory_order_relaxed);
+  if (v == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, pair_insert_multi_kernel, kPairThreads,
+                                                      0) != cudaSuccess ||
+        v < 1)
+      v = 1;
+    per_sm.store(v, std::memory_order_relaxed);
+  }
+  return v * num_sms() * (kPairThreads / 32);
 }
 
 cudaError_t launch_rehash(const uint64_t* X, const uint64_t* from, uint64_t from_cap,

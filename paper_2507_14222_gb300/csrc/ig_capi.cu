@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <condition_variable>
 #include <functional>
@@ -1360,8 +1361,34 @@ int batched_candidates(const ig_problem* problems, int32_t np, const ig_params* 
     }
     for (int c = 0; c < 2; ++c) {
       prep[i].nc[c] = nc[c];
-      IG_CUDA(alloc_table(prep[i].tab[c], initial_cap(nc[c]), s), "ig_fit_batched: hash table");
       jobs.push_back(Job{i, c, igk::padded_words(problems[i].K)});
+    }
+  }
+  // Table sizes.  A table with room for every pair (a key per pair at half
+  // load) never has to grow, so the stage needs one launch; that is the
+  // size while all tables together stay within an eighth of the device's
+  // memory, and the usual guess (which may grow) otherwise.
+  {
+    size_t free_b = 0, total_b = 0;
+    IG_CUDA(cudaMemGetInfo(&free_b, &total_b), "ig_fit_batched");
+    uint64_t room = 0;
+    std::vector<uint64_t> cap(jobs.size());
+    for (size_t k = 0; k < jobs.size(); ++k) {
+      const int64_t n = prep[jobs[k].i].nc[jobs[k].c];
+      const uint64_t pairs = uint64_t(n) * uint64_t(n + 1) / 2;
+      uint64_t c = 1u << 12;
+      while (c < 2 * pairs) c <<= 1;
+      cap[k] = c;
+      room += c * sizeof(uint64_t);
+    }
+    // IG_TEST_SMALL_TABLES=1 (a test hook) takes the usual guess always, so
+    // that tables grow and their bands are replayed.
+    const char* small = std::getenv("IG_TEST_SMALL_TABLES");
+    const bool roomy = room <= total_b / 8 && !(small && small[0] == '1');
+    for (size_t k = 0; k < jobs.size(); ++k) {
+      const int64_t n = prep[jobs[k].i].nc[jobs[k].c];
+      IG_CUDA(alloc_table(prep[jobs[k].i].tab[jobs[k].c], roomy ? cap[k] : initial_cap(n), s),
+              "ig_fit_batched: hash table");
     }
   }
   DevBuf<TableCounters> d_ctr;
@@ -1376,43 +1403,42 @@ int batched_candidates(const ig_problem* problems, int32_t np, const ig_params* 
   DevBuf<igk::PairJob> d_jobs;
   DevBuf<int64_t> d_off;
   DevBuf<unsigned long long> d_next;
+  const int warps = igk::pair_multi_grid_warps();
   while (!todo.empty()) {
-    // One launch per word count over the tables still to do.
-    for (int KT : {1, 2, 4, 8, 16}) {
-      std::vector<igk::PairJob> pj;
-      std::vector<int64_t> off{0};
-      const int warps = igk::pair_multi_grid_warps(KT);
-      for (size_t k : todo) {
-        const Job& jb = jobs[k];
-        if (jb.KT != KT) continue;
-        FitPrep& pp = prep[jb.i];
-        igk::PairJob j;
-        j.X = pp.X[jb.c].p;
-        j.n = pp.nc[jb.c];
-        j.band_lo = band_lo[k];
-        j.t = make_table(pp.tab[jb.c].slots.p, pp.tab[jb.c].cap, d_ctr.p + k, kMaxProbe);
-        // Warps add their keys to the count often enough that it lags the
-        // table by at most about a quarter of the limit over the whole grid.
-        j.t.flush = uint32_t(std::max<int64_t>(
-            1, std::min<int64_t>(256, int64_t(j.t.limit) / (4 * int64_t(warps)))));
-        const int64_t nt = igk::ceil_div(j.n, igk::kPairTile), rows = nt - j.band_lo;
-        pj.push_back(j);
-        off.push_back(off.back() + rows * (rows + 1) / 2);
-      }
-      if (pj.empty()) continue;
-      // Buffers of the previous launch are freed in stream order first.
-      IG_CUDA(d_jobs.alloc(pj.size(), s), "ig_fit_batched");
-      IG_CUDA(d_off.alloc(off.size(), s), "ig_fit_batched");
-      IG_CUDA(d_next.alloc(1, s), "ig_fit_batched");
-      IG_CUDA(cudaMemcpyAsync(d_jobs.p, pj.data(), sizeof(igk::PairJob) * pj.size(),
-                              cudaMemcpyHostToDevice, s),
-              "ig_fit_batched");
-      IG_CUDA(cudaMemcpyAsync(d_off.p, off.data(), sizeof(int64_t) * off.size(),
-                              cudaMemcpyHostToDevice, s),
-              "ig_fit_batched");
-      IG_CUDA(cudaMemsetAsync(d_next.p, 0, sizeof(unsigned long long), s), "ig_fit_batched");
+    // One launch over every table still to do.
+    std::vector<igk::PairJob> pj;
+    std::vector<int64_t> off{0};
+    for (size_t k : todo) {
+      const Job& jb = jobs[k];
+      FitPrep& pp = prep[jb.i];
+      igk::PairJob j;
+      j.X = pp.X[jb.c].p;
+      j.n = pp.nc[jb.c];
+      j.band_lo = band_lo[k];
+      j.KT = jb.KT;
+      j.t = make_table(pp.tab[jb.c].slots.p, pp.tab[jb.c].cap, d_ctr.p + k, kMaxProbe);
+      // Warps add their keys to the count often enough that it lags the
+      // table by at most about a quarter of the limit over the whole grid.
+      j.t.flush = uint32_t(
+          std::max<int64_t>(1, std::min<int64_t>(256, int64_t(j.t.limit) / (4 * int64_t(warps)))));
+      const int64_t nt = igk::ceil_div(j.n, igk::kPairTile), rows = nt - j.band_lo;
+      pj.push_back(j);
+      off.push_back(off.back() + rows * (rows + 1) / 2);
+    }
+    // Buffers of the previous launch are freed in stream order first.
+    IG_CUDA(d_jobs.alloc(pj.size(), s), "ig_fit_batched");
+    IG_CUDA(d_off.alloc(off.size(), s), "ig_fit_batched");
+    IG_CUDA(d_next.alloc(1, s), "ig_fit_batched");
+    IG_CUDA(cudaMemcpyAsync(d_jobs.p, pj.data(), sizeof(igk::PairJob) * pj.size(),
+                            cudaMemcpyHostToDevice, s),
+            "ig_fit_batched");
+    IG_CUDA(cudaMemcpyAsync(d_off.p, off.data(), sizeof(int64_t) * off.size(),
+                            cudaMemcpyHostToDevice, s),
+            "ig_fit_batched");
+    IG_CUDA(cudaMemsetAsync(d_next.p, 0, sizeof(unsigned long long), s), "ig_fit_batched");
+    {
       ProfScope ps(S_PAIR, s);
-      IG_CUDA(igk::launch_pair_insert_multi(d_jobs.p, int(pj.size()), d_off.p, d_next.p, KT,
+      IG_CUDA(igk::launch_pair_insert_multi(d_jobs.p, int(pj.size()), d_off.p, d_next.p,
                                             pair_status, s),
               "ig_fit_batched: pair intersection");
     }
@@ -1444,39 +1470,23 @@ int batched_candidates(const ig_problem* problems, int32_t np, const ig_params* 
   return IG_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
-           const ig_params* params, ig_model** out, ig_stream_t stream) {
-  igk::DeviceRestore restore_device;  // the caller's device, put back on return
-  return fit_impl(rows, labels, n, K, params, out, reinterpret_cast<cudaStream_t>(stream),
-                  nullptr);
-}
-
-int ig_fit_batched(const ig_problem* problems, int32_t n_problems, const ig_params* params,
-                   int32_t lanes, ig_model** out, ig_stream_t stream) {
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (n_problems < 0 || (n_problems > 0 && (!problems || !out)))
-    return fail(IG_E_INVAL, "ig_fit_batched: bad arguments");
-  for (int32_t i = 0; i < n_problems; ++i) out[i] = nullptr;
-  if (n_problems == 0) return IG_OK;
+// Runs fn(k, stream) for k = order[0], order[1], ... on `lanes` streams,
+// each with a host thread pulling the next item when it finishes one.  The
+// streams start after what `s` holds and `s` waits for all of them.  The
+// first failure (by the order in which lanes saw them) is kept, its message
+// prefixed with `what` and the item's number.
+template <class Fn>
+int run_lanes(const std::vector<int32_t>& order, int lanes, cudaStream_t s, const char* what,
+              Fn fn) {
+  const int32_t n = int32_t(order.size());
+  if (n == 0) return IG_OK;
   if (lanes <= 0) lanes = 8;
-  if (lanes > n_problems) lanes = n_problems;
-  // Largest problems first (pairs grow as n^2), each lane pulling the next.
-  std::vector<int32_t> order(n_problems);
-  for (int32_t i = 0; i < n_problems; ++i) order[i] = i;
-  std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-    return problems[a].n > problems[b].n || (problems[a].n == problems[b].n && a < b);
-  });
+  if (lanes > n) lanes = n;
   int dev = 0;
-  IG_CUDA(cudaGetDevice(&dev), "ig_fit_batched");
-  std::vector<FitPrep> prep(n_problems);
-  IG_CHECK(batched_candidates(problems, n_problems, params, prep, s));
+  IG_CUDA(cudaGetDevice(&dev), what);
   cudaEvent_t ready = nullptr;
-  IG_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming), "ig_fit_batched");
-  IG_CUDA(cudaEventRecord(ready, s), "ig_fit_batched");
+  IG_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming), what);
+  IG_CUDA(cudaEventRecord(ready, s), what);
   std::atomic<int32_t> next{0};
   std::mutex err_mu;
   int first_rc = IG_OK;
@@ -1484,24 +1494,21 @@ int ig_fit_batched(const ig_problem* problems, int32_t n_problems, const ig_para
   std::vector<cudaStream_t> ls(lanes, nullptr);
   std::vector<cudaEvent_t> done(lanes, nullptr);
   for (int l = 0; l < lanes; ++l) {
-    IG_CUDA(cudaStreamCreateWithFlags(&ls[l], cudaStreamNonBlocking), "ig_fit_batched");
-    IG_CUDA(cudaEventCreateWithFlags(&done[l], cudaEventDisableTiming), "ig_fit_batched");
-    IG_CUDA(cudaStreamWaitEvent(ls[l], ready, 0), "ig_fit_batched");
+    IG_CUDA(cudaStreamCreateWithFlags(&ls[l], cudaStreamNonBlocking), what);
+    IG_CUDA(cudaEventCreateWithFlags(&done[l], cudaEventDisableTiming), what);
+    IG_CUDA(cudaStreamWaitEvent(ls[l], ready, 0), what);
   }
   auto lane = [&](int l) {
     cudaSetDevice(dev);
     for (;;) {
       const int32_t k = next.fetch_add(1);
-      if (k >= n_problems) break;
-      const ig_problem& pr = problems[order[k]];
-      FitPrep* pp = prep[order[k]].ready ? &prep[order[k]] : nullptr;
-      const int rc = fit_impl(pr.rows, pr.labels, pr.n, pr.K, pr.params ? pr.params : params,
-                              &out[order[k]], ls[l], pp);
+      if (k >= n) break;
+      const int rc = fn(order[k], ls[l]);
       if (rc != IG_OK) {
         std::lock_guard<std::mutex> lk(err_mu);
         if (first_rc == IG_OK) {
           first_rc = rc;
-          first_msg = std::string("problem ") + std::to_string(order[k]) + ": " + g_last_error;
+          first_msg = std::string(what) + " " + std::to_string(order[k]) + ": " + g_last_error;
         }
       }
     }
@@ -1524,15 +1531,67 @@ int ig_fit_batched(const ig_problem* problems, int32_t n_problems, const ig_para
     cudaStreamDestroy(ls[l]);
   }
   cudaEventDestroy(ready);
-  if (first_rc != IG_OK) {
+  if (first_rc != IG_OK) g_last_error = first_msg;
+  return first_rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
+           const ig_params* params, ig_model** out, ig_stream_t stream) {
+  igk::DeviceRestore restore_device;  // the caller's device, put back on return
+  return fit_impl(rows, labels, n, K, params, out, reinterpret_cast<cudaStream_t>(stream),
+                  nullptr);
+}
+
+int ig_fit_batched(const ig_problem* problems, int32_t n_problems, const ig_params* params,
+                   int32_t lanes, ig_model** out, ig_stream_t stream) {
+  igk::DeviceRestore restore_device;  // the caller's device, put back on return
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (n_problems < 0 || (n_problems > 0 && (!problems || !out)))
+    return fail(IG_E_INVAL, "ig_fit_batched: bad arguments");
+  for (int32_t i = 0; i < n_problems; ++i) out[i] = nullptr;
+  if (n_problems == 0) return IG_OK;
+  // Largest problems first (pairs grow as n^2), each lane pulling the next.
+  std::vector<int32_t> order(n_problems);
+  for (int32_t i = 0; i < n_problems; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return problems[a].n > problems[b].n || (problems[a].n == problems[b].n && a < b);
+  });
+  std::vector<FitPrep> prep(n_problems);
+  IG_CHECK(batched_candidates(problems, n_problems, params, prep, s));
+  const int rc = run_lanes(order, lanes, s, "problem", [&](int32_t k, cudaStream_t ls) {
+    const ig_problem& pr = problems[k];
+    return fit_impl(pr.rows, pr.labels, pr.n, pr.K, pr.params ? pr.params : params, &out[k], ls,
+                    prep[k].ready ? &prep[k] : nullptr);
+  });
+  if (rc != IG_OK) {
     for (int32_t i = 0; i < n_problems; ++i) {
       ig_model_free(out[i]);
       out[i] = nullptr;
     }
-    g_last_error = first_msg;
-    return first_rc;
   }
-  return IG_OK;
+  return rc;
+}
+
+int ig_score_batched(const ig_score_job* jobs, int32_t n_jobs, int32_t lanes,
+                     ig_stream_t stream) {
+  igk::DeviceRestore restore_device;  // the caller's device, put back on return
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(IG_E_INVAL, "ig_score_batched: bad arguments");
+  // Largest batches first, each lane pulling the next.
+  std::vector<int32_t> order(n_jobs);
+  for (int32_t i = 0; i < n_jobs; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return jobs[a].m > jobs[b].m || (jobs[a].m == jobs[b].m && a < b);
+  });
+  return run_lanes(order, lanes, s, "job", [&](int32_t k, cudaStream_t ls) {
+    const ig_score_job& j = jobs[k];
+    return ig_score(j.model, j.rows, j.m, j.A_out, j.N_out, j.label_out,
+                    reinterpret_cast<ig_stream_t>(ls));
+  });
 }
 
 int ig_model_from_patterns(int32_t K, const uint64_t* const* words, const uint32_t* const* support,

@@ -118,24 +118,24 @@ constexpr int kPairTile = 64;  // records per side of a pair tile (one band = on
 // the upper triangle; one launch.
 cudaError_t launch_pair_insert(const uint64_t* X, int64_t n, int KT, int64_t band_lo,
                                PairTable t, int* status, cudaStream_t s);
-// One table of a multi-table pair launch: the records X[0, n) (stride KT),
-// the bands [band_lo, ceil(n / kPairTile)) and the table (its flush set by
-// the caller, see pair_multi_grid_warps).
+// One table of a multi-table pair launch: the records X[0, n) (KT words
+// per row), the bands [band_lo, ceil(n / kPairTile)) and the table (its
+// flush set by the caller, see pair_multi_grid_warps).
 struct PairJob {
   const uint64_t* X = nullptr;
   int64_t n = 0;
   int64_t band_lo = 0;
+  int KT = 0;
   PairTable t;
 };
-// The pair tiles of every job in one launch of a persistent grid drawing
-// tiles from a device-side queue: tile_off[j] (device, n_jobs + 1 entries)
-// numbers job j's tiles band by band; next_tile (device) must start at 0.
-// All jobs have KT words per row.
+// The pair tiles of every job, of any word counts, in one launch of a
+// persistent grid drawing tiles from a device-side queue: tile_off[j]
+// (device, n_jobs + 1 entries) numbers job j's tiles band by band;
+// next_tile (device) must start at 0.
 cudaError_t launch_pair_insert_multi(const PairJob* jobs, int n_jobs, const int64_t* tile_off,
-                                     unsigned long long* next_tile, int KT, int* status,
-                                     cudaStream_t s);
+                                     unsigned long long* next_tile, int* status, cudaStream_t s);
 // Warps of the multi-table launch's grid (for the jobs' flush intervals).
-int pair_multi_grid_warps(int KT);
+int pair_multi_grid_warps();
 // Re-inserts every key of the table `from` (from_cap slots) into `to`.
 cudaError_t launch_rehash(const uint64_t* X, const uint64_t* from, uint64_t from_cap,
                           PairTable to, int KT, int* status, cudaStream_t s);

@@ -419,6 +419,90 @@ def test_batched_fit_all_problems_match_single_fits_and_oracle():
     assert len(widths) == 4
 
 
+def test_batched_pair_stage_with_table_growth(monkeypatch):
+    # The batched candidate stage with the usual (small) first tables: the
+    # distinct-heavy batched problems overflow them, so tables grow, are
+    # rehashed and their bands replayed in further launches.  Every model
+    # still equals its problem's oracle digest.
+    monkeypatch.setenv("IG_TEST_SMALL_TABLES", "1")
+    golden, digest = _golden_digests()
+    probs = igdata.batched(igdata.BATCHED_PROBLEMS)[:24]
+    enc = [(ig.ig_encode(dev(w.train_codes), w.cards), dev(w.train_labels)) for w in probs]
+    launches0 = ig.launch_count()
+    ig.prof_enable(True)
+    ig.prof_reset()
+    try:
+        batched = ig.ig_fit_batched(enc)
+        torch.cuda.synchronize()
+        stages = ig.prof_read()
+    finally:
+        ig.prof_enable(False)
+    assert ig.launch_count() > launches0
+    assert stages["rehash"][1] > 0          # some table grew
+    for w, mb in zip(probs, batched):
+        got, _ = _gpu_digest(digest, mb, ig.ig_encode(dev(w.test_codes), w.cards))
+        assert got == golden[w.name]["sha256"], f"{w.name} differs from the oracle"
+        mb.free()
+
+
+def test_batched_pair_stage_is_one_launch():
+    # With room for every pair, no table grows: the pair tiles of every
+    # class of every problem (all word counts) run in one launch.
+    probs = igdata.batched(igdata.BATCHED_PROBLEMS)
+    enc = [(ig.ig_encode(dev(w.train_codes), w.cards), dev(w.train_labels)) for w in probs]
+    ig.prof_enable(True)
+    ig.prof_reset()
+    try:
+        models = ig.ig_fit_batched(enc)
+        torch.cuda.synchronize()
+        stages = ig.prof_read()
+    finally:
+        ig.prof_enable(False)
+    assert stages["pair_insert"][1] == 1
+    assert stages["rehash"][1] == 0
+    assert len({int(r.shape[1]) for r, _ in enc}) == 4
+    for m in models:
+        m.free()
+
+
+def _as_np(x):
+    return x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)
+
+
+def test_batched_scoring_matches_single_calls():
+    # ig_score_batched over independent (model, rows) jobs -- device and host
+    # arrays, jobs sharing a model, an empty batch -- equals one ig_score per
+    # job; a failing job is reported by number.
+    probs = igdata.batched(igdata.BATCHED_PROBLEMS)[:12]
+    enc = [(ig.ig_encode(dev(w.train_codes), w.cards), dev(w.train_labels)) for w in probs]
+    models = ig.ig_fit_batched(enc)
+    jobs = [(m, ig.ig_encode(dev(w.test_codes), w.cards)) for w, m in zip(probs, models)]
+    jobs.append((models[0], jobs[0][1][:0]))                             # empty
+    jobs.append((models[1], jobs[1][1].cpu().numpy().view(np.uint64)))   # host arrays
+    jobs.append((models[1], jobs[1][1][:17]))                            # shared model
+    got = ig.ig_score_batched(jobs, lanes=4)
+    for (m, rows), (A, N, lab) in zip(jobs, got):
+        rA, rN, rlab = ig.ig_score(m, rows)
+        assert np.array_equal(_as_np(A), _as_np(rA))
+        assert np.array_equal(_as_np(N), _as_np(rN))
+        assert np.array_equal(_as_np(lab), _as_np(rlab))
+    assert any(int(_as_np(A).max(initial=0)) > 0 for A, _, _ in got)
+    lib = ig.load()
+    rows = jobs[0][1]
+    bufs = [torch.empty(rows.shape[0], dtype=torch.int64, device=rows.device) for _ in range(4)]
+    labs = [torch.empty(rows.shape[0], dtype=torch.uint8, device=rows.device) for _ in range(2)]
+    arr = (ig.ig_score_job * 2)()
+    arr[0] = ig.ig_score_job(models[0].handle, rows.data_ptr(), rows.shape[0], bufs[0].data_ptr(),
+                             bufs[1].data_ptr(), labs[0].data_ptr())
+    arr[1] = ig.ig_score_job(None, rows.data_ptr(), rows.shape[0], bufs[2].data_ptr(),
+                             bufs[3].data_ptr(), labs[1].data_ptr())
+    assert lib.ig_score_batched(arr, 2, 2, None) != 0
+    assert b"job 1" in lib.ig_last_error()
+    torch.cuda.synchronize()
+    for m in models:
+        m.free()
+
+
 def test_batched_fit_reports_failing_problem():
     good = (np.array([[1], [2], [3]], np.uint64), np.array([1, 0, 1], np.uint8))
     bad = (np.array([[1], [2]], np.uint64), np.array([1, 1], np.uint8))   # one class only
