@@ -4,27 +4,35 @@
 // across runs (the paper's requirement that GPU and CPU pattern evidence
 // agree exactly, Section 4).
 //
-//  1. every key gets an order-preserving 128-bit prefix (its ten highest
-//     items) and is represented by (prefix, index) while it is sorted, so the
+//  1. every key is represented while it is sorted by (prefix, index): an
+//     order-preserving 128-bit prefix (its ten highest items), so the merge
 //     passes move 20 bytes per key and their searches run over arrays that
 //     fit in L2; full keys are read only when two prefixes tie;
-//  2. each block sorts a tile of 1,024 elements in shared memory with a
-//     bitonic network (one compare-exchange per thread and stage; two
-//     blocks fit an SM);
-//  3. merge passes quadruple the sorted run length: every element finds its
-//     output slot directly as (its index in its own run) + (number of
-//     elements of the three other runs of its group before it), by binary
-//     searches -- equal keys of lower runs count as before it -- so the
-//     slots form a permutation without merge-path partitioning, also when
-//     keys repeat;
+//  2. each CTA sorts a tile of kSortTile keys with a bitonic network whose
+//     elements stay in registers (thread t holds tile positions t,
+//     t + 1024, ...), exchanged by warp shuffles where the partner is less
+//     than 32 positions away and through shared memory otherwise; the
+//     tile's keys are staged in shared memory (K <= 8 words) for prefix
+//     ties.  The prefixes are computed here, from the staged keys;
+//  3. merge passes multiply the sorted run length by kMergeFan (4): every
+//     element finds its output slot directly as (its index in its own run)
+//     + (the number of elements of each other run of its group before it),
+//     by binary searches advanced in lockstep so that their loads overlap;
+//     equal keys of lower runs count as before it, so the slots form a
+//     permutation without merge-path partitioning, also when keys repeat;
 //  4. the keys are gathered in the final order.
 #include "common.cuh"
 #include "internal.h"
 
 namespace igk {
 
-constexpr int kSortBlockThreads = 512;
-constexpr int kSortTile = 1024;  // elements per block-sorted tile (one pair per thread)
+constexpr int kSortThreads = 1024;
+constexpr int kSortPerThread = 1;                             // tile positions per thread
+constexpr int kSortTile = kSortThreads * kSortPerThread;      // elements per block-sorted tile
+// Runs merged per pass.  Eight runs per pass (two passes fewer at 148k)
+// measured slower than four: seven lockstep searches per element cost more
+// than the passes they save.
+constexpr int kMergeFan = 4;
 
 template <int KT>
 __device__ __forceinline__ bool key_less(const uint64_t* a, const uint64_t* b) {
@@ -42,17 +50,14 @@ __device__ __forceinline__ bool key_less(const uint64_t* a, const uint64_t* b) {
 // (word KT-1 most significant): two keys first differ at the highest bit
 // where one has an item and the other not, and that is the first position
 // where their descending item lists differ.  Keys with equal prefixes are
-// compared in full.
+// compared in full.  Every prefix word is below 2^60.
 template <int KT>
-__global__ void prefix_kernel(const uint64_t* __restrict__ keys, int64_t n,
-                              uint64_t* __restrict__ p0, uint64_t* __restrict__ p1,
-                              uint32_t* __restrict__ idx) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint64_t a = 0, b = 0;
+__device__ __forceinline__ void key_prefix(const uint64_t* key, uint64_t& a, uint64_t& b) {
+  a = 0;
+  b = 0;
   int taken = 0;
   for (int w = KT - 1; w >= 0 && taken < 10; --w) {
-    uint64_t x = keys[i * KT + w];
+    uint64_t x = key[w];
     while (x && taken < 10) {
       const int bit = 63 - __clzll(static_cast<long long>(x));
       x &= ~(1ull << bit);
@@ -64,9 +69,6 @@ __global__ void prefix_kernel(const uint64_t* __restrict__ keys, int64_t n,
       ++taken;
     }
   }
-  p0[i] = a;
-  p1[i] = b;
-  idx[i] = uint32_t(i);
 }
 
 template <int KT>
@@ -83,105 +85,151 @@ struct SortArrays {
   uint32_t* idx;
 };
 
-// Bitonic network over a tile of kSortTile elements in shared memory.  The
-// tile holds keys [base, base + kSortTile) (this is the first pass, so the
-// element of key i carries index i); with KT <= 8 words those keys are
-// staged in shared memory too, so that elements whose prefixes tie are
-// compared there rather than by loads from global memory that every thread
-// of the block would wait for at the next barrier.
+// Keys staged in shared memory for the block sort's prefix ties where they
+// fit beside the exchange arrays.
 template <int KT>
 constexpr bool kSortStageKeys = KT <= 8;
 template <int KT>
-constexpr size_t sort_stage_bytes() {
-  return kSortStageKeys<KT> ? size_t(kSortTile) * KT * 8 : 0;
+constexpr size_t sort_smem_bytes() {
+  return size_t(kSortTile) * (8 + 8 + 4) + (kSortStageKeys<KT> ? size_t(kSortTile) * KT * 8 : 0);
 }
 
+// One element of the block sort's network, in registers: its prefix, its
+// key's index and the tile slot of its staged key.  Tile positions past the
+// keys hold +inf (prefix words of all ones, above every real prefix).
+struct Elem {
+  uint64_t p0, p1;
+  uint32_t idx;
+};
+
+// The element that position `pos` keeps from its comparator with position
+// q: the smaller one at the lower position, the larger at the upper, in the
+// order of (prefix, key, index), which is strict for distinct elements.  Keys
+// are read at kbase + (index - base) * KT: the staged tile when kbase is
+// the shared copy, else global memory.
 template <int KT>
-__global__ void __launch_bounds__(kSortBlockThreads)
-    block_sort_kernel(const uint64_t* __restrict__ keys, int64_t n, SortArrays in,
-                      SortArrays out) {
-  __shared__ uint64_t s0[kSortTile];
-  __shared__ uint64_t s1[kSortTile];
-  __shared__ uint32_t si[kSortTile];
-  extern __shared__ uint64_t tile_keys[];  // [kSortTile][KT] when staged
-  const int64_t base = int64_t(blockIdx.x) * kSortTile;
-  const int nv = int((n - base) < kSortTile ? (n - base) : kSortTile);
+__device__ __forceinline__ Elem keep(const Elem& mine, const Elem& other, bool lower,
+                                     const uint64_t* kbase, int64_t base) {
+  bool other_first;
+  if (other.p0 != mine.p0) {
+    other_first = other.p0 < mine.p0;
+  } else if (other.p1 != mine.p1) {
+    other_first = other.p1 < mine.p1;
+  } else if (other.idx == 0xffffffffu || mine.idx == 0xffffffffu) {
+    other_first = mine.idx == 0xffffffffu && other.idx != 0xffffffffu;
+  } else {
+    // Equal keys order by index: the comparator must be strict, or both
+    // positions would keep the same element.
+    const uint64_t* ko = kbase + (int64_t(other.idx) - base) * KT;
+    const uint64_t* km = kbase + (int64_t(mine.idx) - base) * KT;
+    other_first = key_less<KT>(ko, km) || (!key_less<KT>(km, ko) && other.idx < mine.idx);
+  }
+  return lower == other_first ? other : mine;
+}
+
+// Sorts tile blockIdx.x (keys [base, base + kSortTile)) and writes its
+// elements (prefix, index) in order.  The network: for each block size
+// k = 2, 4, ..., kSortTile, a "flip" step pairs position i with its mirror
+// i ^ (k - 1) in its k-block, then "disperse" steps pair i with i ^ j for
+// j = k/4, ..., 1; every comparator puts the smaller element at the lower
+// position, so the +inf positions past the tile's keys never move.
+template <int KT>
+__global__ void __launch_bounds__(kSortThreads, 1)
+    block_sort_kernel(const uint64_t* __restrict__ keys, int64_t n, SortArrays out) {
+  constexpr int E = kSortPerThread, T = kSortThreads, C = kSortTile;
+  extern __shared__ __align__(16) uint8_t sh_raw[];
+  uint64_t* x0 = reinterpret_cast<uint64_t*>(sh_raw);  // exchange arrays [C]
+  uint64_t* x1 = x0 + C;
+  uint64_t* sk = x1 + C;                                // staged keys [C][KT] (K <= 8)
+  uint32_t* xi = reinterpret_cast<uint32_t*>(sk + (kSortStageKeys<KT> ? size_t(C) * KT : 0));
+  const int64_t base = int64_t(blockIdx.x) * C;
+  const int nv = int((n - base) < C ? (n - base) : C);
+  const uint64_t* kbase = keys + base * KT;
   if constexpr (kSortStageKeys<KT>) {
-    for (int e = threadIdx.x; e < nv * KT; e += blockDim.x) tile_keys[e] = keys[base * KT + e];
+    for (int q = threadIdx.x; q < nv * KT; q += T) sk[q] = kbase[q];
+    __syncthreads();
+    kbase = sk;
   }
-  for (int r = threadIdx.x; r < kSortTile; r += blockDim.x) {
-    if (r < nv) {
-      s0[r] = in.p0[base + r];
-      s1[r] = in.p1[base + r];
-      si[r] = in.idx[base + r];
-    } else {  // +infinity: after every key
-      s0[r] = ~0ull;
-      s1[r] = ~0ull;
-      si[r] = 0xffffffffu;
-    }
-  }
-  __syncthreads();
-  auto greater = [&](int x, int y) -> bool {
-    if (si[x] == 0xffffffffu) return si[y] != 0xffffffffu;
-    if (si[y] == 0xffffffffu) return false;
-    if constexpr (kSortStageKeys<KT>) {
-      if (s0[y] != s0[x]) return s0[y] < s0[x];
-      if (s1[y] != s1[x]) return s1[y] < s1[x];
-      return key_less<KT>(tile_keys + int64_t(si[y] - base) * KT,
-                          tile_keys + int64_t(si[x] - base) * KT);
+  Elem el[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int pos = threadIdx.x + e * T;
+    if (pos < nv) {
+      key_prefix<KT>(kbase + int64_t(pos) * KT, el[e].p0, el[e].p1);
+      el[e].idx = uint32_t(base + pos);
     } else {
-      return elem_less<KT>(keys, s0[y], s1[y], si[y], s0[x], s1[x], si[x]);
-    }
-  };
-  // k = 2^lk, j = 2^lj: pair t compares i = (t with a zero bit inserted at
-  // lj) and l = i + j, in ascending order where bit lk of i is 0.
-  for (int lk = 1; (1 << lk) <= kSortTile; ++lk) {
-    for (int lj = lk - 1; lj >= 0; --lj) {
-      const int j = 1 << lj;
-      for (int t = threadIdx.x; t < kSortTile / 2; t += blockDim.x) {
-        const int i = ((t >> lj) << (lj + 1)) | (t & (j - 1)), l = i + j;
-        const bool up = ((i >> lk) & 1) == 0;
-        if (up ? greater(i, l) : greater(l, i)) {
-          const uint64_t a0 = s0[i], a1 = s1[i];
-          const uint32_t ai = si[i];
-          s0[i] = s0[l];
-          s1[i] = s1[l];
-          si[i] = si[l];
-          s0[l] = a0;
-          s1[l] = a1;
-          si[l] = ai;
-        }
-      }
-      __syncthreads();
+      el[e].p0 = ~0ull;
+      el[e].p1 = ~0ull;
+      el[e].idx = 0xffffffffu;
     }
   }
-  for (int r = threadIdx.x; r < nv; r += blockDim.x) {
-    out.p0[base + r] = s0[r];
-    out.p1[base + r] = s1[r];
-    out.idx[base + r] = si[r];
+  const int lane = threadIdx.x & 31;
+  for (int k = 2; k <= C; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const int d = j == (k >> 1) ? k - 1 : j;  // partner = position ^ d
+      if (d < 32) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          Elem o;
+          o.p0 = __shfl_xor_sync(0xffffffffu, el[e].p0, d);
+          o.p1 = __shfl_xor_sync(0xffffffffu, el[e].p1, d);
+          o.idx = __shfl_xor_sync(0xffffffffu, el[e].idx, d);
+          el[e] = keep<KT>(el[e], o, lane < (lane ^ d), kbase, base);
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int pos = threadIdx.x + e * T;
+          x0[pos] = el[e].p0;
+          x1[pos] = el[e].p1;
+          xi[pos] = el[e].idx;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int pos = threadIdx.x + e * T, q = pos ^ d;
+          Elem o;
+          o.p0 = x0[q];
+          o.p1 = x1[q];
+          o.idx = xi[q];
+          el[e] = keep<KT>(el[e], o, pos < q, kbase, base);
+        }
+        __syncthreads();
+      }
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int pos = threadIdx.x + e * T;
+    if (pos < nv) {
+      out.p0[base + pos] = el[e].p0;
+      out.p1[base + pos] = el[e].p1;
+      out.idx[base + pos] = el[e].idx;
+    }
   }
 }
 
-// Merge pass over groups of four runs: element e of run q of its group
+// Merge pass over groups of kMergeFan runs: element e of run q of its group
 // goes to (its index in its run) + (the number of elements of each other
 // run of the group that come before it).  Equal keys order by run (those of
 // lower runs first), so the slots form a permutation even when keys repeat.
-// The three binary searches advance in lockstep, so their loads overlap.
+// The binary searches advance in lockstep, so their loads overlap.
 template <int KT>
-__global__ void merge4_pass_kernel(const uint64_t* __restrict__ keys, SortArrays in,
-                                   SortArrays out, int64_t n, int64_t run) {
+__global__ void merge_pass_kernel(const uint64_t* __restrict__ keys, SortArrays in,
+                                  SortArrays out, int64_t n, int64_t run) {
+  constexpr int F = kMergeFan;
   const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= n) return;
   const int64_t r = e / run;
   const int64_t own_lo = r * run;
-  const int64_t grp_lo = (r & ~int64_t(3)) * run;
-  const int q = int(r & 3);
+  const int64_t grp_lo = (r / F) * F * run;
+  const int q = int(r % F);
   const uint64_t k0 = in.p0[e], k1 = in.p1[e];
   const uint32_t ki = in.idx[e];
-  int64_t lo[3], hi[3], base[3];
-  bool before_eq[3];  // partner run lower than q: its equal keys come first
+  int64_t lo[F - 1], hi[F - 1], base[F - 1];
+  bool before_eq[F - 1];  // partner run lower than q: its equal keys come first
 #pragma unroll
-  for (int s = 0; s < 3; ++s) {
+  for (int s = 0; s < F - 1; ++s) {
     const int qq = s < q ? s : s + 1;
     const int64_t a = grp_lo + int64_t(qq) * run;
     base[s] = a < n ? a : n;
@@ -193,7 +241,7 @@ __global__ void merge4_pass_kernel(const uint64_t* __restrict__ keys, SortArrays
   while (more) {
     more = false;
 #pragma unroll
-    for (int s = 0; s < 3; ++s) {
+    for (int s = 0; s < F - 1; ++s) {
       if (lo[s] < hi[s]) {
         const int64_t mid = (lo[s] + hi[s]) >> 1;
         const uint64_t m0 = in.p0[mid], m1 = in.p1[mid];
@@ -208,8 +256,9 @@ __global__ void merge4_pass_kernel(const uint64_t* __restrict__ keys, SortArrays
       }
     }
   }
-  const int64_t pos = grp_lo + (e - own_lo) + (lo[0] - base[0]) + (lo[1] - base[1]) +
-                      (lo[2] - base[2]);
+  int64_t pos = grp_lo + (e - own_lo);
+#pragma unroll
+  for (int s = 0; s < F - 1; ++s) pos += lo[s] - base[s];
   out.p0[pos] = k0;
   out.p1[pos] = k1;
   out.idx[pos] = ki;
@@ -237,24 +286,19 @@ static cudaError_t sort_t(const uint64_t* keys, int64_t n, uint64_t* keys_out, u
                reinterpret_cast<uint32_t*>(m + 32 * n)};
   SortArrays B{reinterpret_cast<uint64_t*>(m + 16 * n), reinterpret_cast<uint64_t*>(m + 24 * n),
                reinterpret_cast<uint32_t*>(m + 36 * n)};
-  const unsigned g = unsigned(ceil_div(n, 256));
-  prefix_kernel<KT><<<g, 256, 0, s>>>(keys, n, A.p0, A.p1, A.idx);
-  count_launches(1);
-  constexpr size_t stage = sort_stage_bytes<KT>();
-  if (stage > 0) {
-    e = cudaFuncSetAttribute(block_sort_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(stage));
-    if (e != cudaSuccess) {
-      cudaFreeAsync(mem, s);
-      return e;
-    }
+  constexpr size_t smem = sort_smem_bytes<KT>();
+  e = cudaFuncSetAttribute(block_sort_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(smem));
+  if (e != cudaSuccess) {
+    cudaFreeAsync(mem, s);
+    return e;
   }
-  block_sort_kernel<KT><<<unsigned(ceil_div(n, kSortTile)), kSortBlockThreads, stage, s>>>(
-      keys, n, A, B);
+  block_sort_kernel<KT><<<unsigned(ceil_div(n, kSortTile)), kSortThreads, smem, s>>>(keys, n, A);
   count_launches(1);
-  SortArrays cur = B, other = A;
-  for (int64_t run = kSortTile; run < n; run *= 4) {
-    merge4_pass_kernel<KT><<<g, 256, 0, s>>>(keys, cur, other, n, run);
+  SortArrays cur = A, other = B;
+  const unsigned g = unsigned(ceil_div(n, 256));
+  for (int64_t run = kSortTile; run < n; run *= kMergeFan) {
+    merge_pass_kernel<KT><<<g, 256, 0, s>>>(keys, cur, other, n, run);
     count_launches(1);
     const SortArrays t = cur;
     cur = other;
