@@ -815,12 +815,17 @@ int fit_impl(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
   IG_CUDA(d_status.alloc(1, s), "ig_fit");
   IG_CUDA(d_counts.alloc(2, s), "ig_fit");
   IG_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), s), "ig_fit");
-  // Pinned host words for size read-backs: [0..1] class counts, [2..3] the
-  // classes' largest scores.
+  // Pinned host words for read-backs: [0..1] class counts, [2..3] the
+  // classes' largest scores, [4..5] and [6..7] the coherence and support
+  // tests of the item-index rounds (the tensor-core form copies them when
+  // its stream gets there), [8] those of the Regulation 3 evidence.
   static thread_local unsigned long long* h_pinned = nullptr;
-  if (!h_pinned) IG_CUDA(cudaMallocHost(&h_pinned, 8 * sizeof(unsigned long long)), "ig_fit");
+  if (!h_pinned) IG_CUDA(cudaMallocHost(&h_pinned, 16 * sizeof(unsigned long long)), "ig_fit");
   // [2 + c]: the largest score of class c, copied back by its class stream.
   unsigned long long* const h_smax = h_pinned + 2;
+  int64_t* const h_tests = reinterpret_cast<int64_t*>(h_pinned + 4);
+  for (int i = 0; i < 5; ++i) h_tests[i] = 0;
+  bool sup_idx_ran[2] = {false, false};
 
   // Section 3.2: class-stacked row matrices (normal -> X[0], attack -> X[1]).
   DevBuf<uint64_t> X[2];
@@ -958,7 +963,6 @@ int fit_impl(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
       bool done_round = false;
       if (pruned_round) {
         // The candidates left are counted on the device (U bounds them).
-        int64_t t = -1;
         if (rec_idx[o].idx.usable) {
           igk::IndexedArgs a;
           a.mode = igk::MODE_ANY;
@@ -971,15 +975,13 @@ int fit_impl(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
           a.out_u32 = covered.p;
           a.out_u64 = nullptr;
           a.status = d_status.p;
-          a.tests_out = &t;
+          a.tests_out = h_tests + c;  // read after the round's read-back below
           a.prof_stage = S_COHERENCE_IDX;
           a.max_q = m->index_max_q;
           a.flip_factor = m->index_flip;
           a.tc = m->subset_kernel == 4 ? 1 : 0;
           IG_CUDA(igk::indexed_subset(a, s), "ig_fit: coherence");
-        }
-        if (t >= 0) {
-          round_tests[rounds] = t;
+          round_tests[rounds] = -2;  // in h_tests[c]
           done_round = true;
         }
       }
@@ -1022,9 +1024,9 @@ int fit_impl(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
     h_pinned[2] = kept_h[rounds - 1];
     m->coh_tests[c] = m->coh_tests_tc[c] = m->coh_tests_pruned[c] = 0;
     for (int r = 0; r < rounds; ++r) {
-      if (round_tests[r] >= 0) {
-        m->coh_tests[c] += round_tests[r];
-        m->coh_tests_pruned[c] += round_tests[r];
+      if (round_tests[r] == -2) {
+        m->coh_tests[c] += h_tests[c];
+        m->coh_tests_pruned[c] += h_tests[c];
         continue;
       }
       const int64_t t = int64_t(r == 0 ? U : kept_h[r - 1]) * (win_hi[r] - win_lo[r]);
@@ -1054,7 +1056,6 @@ int fit_impl(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
     bool support_done = false;
     m->sup_tests[c] = P * nc[c];
     if (pruned) {
-      int64_t t = -1;
       if (rec_idx[c].idx.usable) {
         igk::IndexedArgs a;
         a.mode = igk::MODE_COUNT;
@@ -1066,17 +1067,14 @@ int fit_impl(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
         a.out_u32 = m->support[c];
         a.out_u64 = nullptr;
         a.status = d_status.p;
-        a.tests_out = &t;
+        a.tests_out = h_tests + 2 + c;  // read after the fit's last read-back
         a.prof_stage = S_SUPPORT_IDX;
         a.max_q = m->index_max_q;
         a.flip_factor = m->index_flip;
         a.tc = m->subset_kernel == 4 ? 1 : 0;
         IG_CUDA(igk::indexed_subset(a, s), "ig_fit: support");
-      }
-      if (t >= 0) {
         support_done = true;
-        m->sup_tests[c] = t;
-        igk::prof_add_work(S_SUPPORT_IDX, t);
+        sup_idx_ran[c] = true;
       }
     }
     if (support_done) {
@@ -1155,8 +1153,12 @@ int fit_impl(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
         IG_CUDA(cudaMemcpyAsync(d_f.p, f.data(), sizeof(uint32_t) * L, cudaMemcpyHostToDevice, s),
                 "ig_fit");
         igk::KeyedIndex* k = new igk::KeyedIndex;
+        // The tensor-core scoring builds its work items on the device and
+        // needs no host offsets (and this fit no read-back).
         const cudaError_t e = igk::build_keyed_index(m->words_kt[c], P, KT, K, KT, d_f.p,
-                                                     m->score[c], k, s);
+                                                     m->score[c], k, s, nullptr,
+                                                     !(m->subset_kernel == 4 &&
+                                                       igk::tc_supported(KT)));
         if (e != cudaSuccess) delete k;
         IG_CUDA(e, "ig_fit: pattern index");
         m->pidx[c] = k;
@@ -1212,7 +1214,7 @@ int fit_impl(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
     DevBuf<unsigned long long> d_n;
     IG_CUDA(d_n.alloc(size_t(nc[0]), s), "ig_fit");
     IG_CUDA(cudaMemsetAsync(d_n.p, 0, sizeof(unsigned long long) * nc[0], s), "ig_fit");
-    int64_t t_idx = -1;
+    bool done_idx = false;
     if (pruned && m->n_pat[0] && rec_idx[0].idx.usable) {
       igk::IndexedArgs a;
       a.mode = igk::MODE_SUM;
@@ -1224,14 +1226,15 @@ int fit_impl(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
       a.out_u32 = nullptr;
       a.out_u64 = d_n.p;
       a.status = d_status.p;
-      a.tests_out = &t_idx;
+      a.tests_out = h_tests + 4;
       a.prof_stage = S_EVIDENCE_IDX;
       a.max_q = m->index_max_q;
       a.flip_factor = m->index_flip;
       a.tc = m->subset_kernel == 4 ? 1 : 0;
       IG_CUDA(igk::indexed_subset(a, s), "ig_fit: Regulation 3 evidence");
+      done_idx = true;
     }
-    if (t_idx >= 0) {
+    if (done_idx) {
     } else if (tc && m->n_pat[0] && rec_img[0].p && m->pat_img[0]) {
       ProfScope ps(S_EVIDENCE_TC, s);
       igk::TcArgs a{igk::MODE_SUM, KT,           rec_img[0].p, nc[0],   nullptr, m->pat_img[0],
@@ -1264,7 +1267,13 @@ int fit_impl(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
     m->thr = m->mu - scaled;
   }
   IG_CHECK(read_status(d_status.p, s, "ig_fit"));
-  for (int c = 0; c < 2; ++c) m->score_max[c] = h_smax[c];
+  for (int c = 0; c < 2; ++c) {
+    m->score_max[c] = h_smax[c];
+    if (sup_idx_ran[c]) {
+      m->sup_tests[c] = h_tests[2 + c];
+      igk::prof_add_work(S_SUPPORT_IDX, h_tests[2 + c]);
+    }
+  }
   guard.m = nullptr;
   *out = m;
   return IG_OK;
@@ -1749,6 +1758,10 @@ int ig_score(const ig_model* m, const uint64_t* rows, int64_t n_rows, int64_t* A
   igk::DeviceRestore restore_device;  // the caller's device, put back on return
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (!m || n_rows < 0 || (n_rows > 0 && !rows)) return fail(IG_E_INVAL, "ig_score: bad arguments");
+  // Pinned words for the tensor-core evidence's executed tests (one pair
+  // per host thread), copied when the stream gets there.
+  static thread_local int64_t* h_tests = nullptr;
+  int tc_tests = 0;
   if (n_rows == 0) return IG_OK;
   InputView<uint64_t> in;
   IG_CHECK(in.bind(rows, size_t(n_rows) * m->K, s, "ig_score: rows"));
@@ -1813,28 +1826,31 @@ int ig_score(const ig_model* m, const uint64_t* rows, int64_t n_rows, int64_t* A
     unsigned long long* outs[2];
     uint64_t smax[2];
     int n = 0;
-    int64_t t[2] = {0, 0};
     cudaError_t e = cudaSuccess;
+    if (!h_tests) e = cudaMallocHost(&h_tests, 2 * sizeof(int64_t));
     for (int c = 1; c >= 0 && e == cudaSuccess; --c) {
       done[c] = true;
       if (m->n_pat[c] == 0) continue;
       if (m->pidx[c] && n_rows * 8 < m->n_pat[c]) {
         kx[n] = m->pidx[c];
       } else {
+        // Work items are built on the device: no host offsets, no read-back.
         e = igk::build_keyed_index(m->words_kt[c], m->n_pat[c], m->KT, m->K, m->KT,
-                                   test_idx.idx.freq, m->score[c], &own[n], s);
+                                   test_idx.idx.freq, m->score[c], &own[n], s, nullptr, false);
         kx[n] = &own[n];
       }
       outs[n] = c == 1 ? A.d : N.d;
       smax[n] = m->score_max[c];
       ++n;
     }
-    if (e == cudaSuccess && n > 0)
+    if (e == cudaSuccess && n > 0) {
+      h_tests[0] = h_tests[1] = 0;
       e = igk::indexed_subset_tc_classes(igk::MODE_SUM, test_idx.idx, kx, n, nullptr, outs,
-                                         d_status.p, t, S_EVIDENCE_IDX, smax, s);
+                                         d_status.p, h_tests, S_EVIDENCE_IDX, smax, s);
+      tc_tests = n;  // counted after the last read-back below
+    }
     for (int i = 0; i < 2; ++i) igk::release_keyed_index(&own[i], s);
     IG_CUDA(e, "ig_score: evidence");
-    igk::prof_add_work(S_EVIDENCE_IDX, t[0] + t[1]);
   } else if (pruned && test_idx.idx.usable) {
     // A (class 1) on the caller's stream and N (class 0) on this thread's
     // auxiliary stream, concurrently: both only read the indexes.
@@ -1914,7 +1930,9 @@ int ig_score(const ig_model* m, const uint64_t* rows, int64_t n_rows, int64_t* A
   IG_CHECK(A.finish(s, "ig_score"));
   IG_CHECK(N.finish(s, "ig_score"));
   if (label_out) IG_CHECK(lab.finish(s, "ig_score"));
-  return read_status(d_status.p, s, "ig_score");
+  const int rc = read_status(d_status.p, s, "ig_score");
+  if (rc == IG_OK && tc_tests) igk::prof_add_work(S_EVIDENCE_IDX, h_tests[0] + h_tests[1]);
+  return rc;
 }
 
 // ---- persistence ------------------------------------------------------------

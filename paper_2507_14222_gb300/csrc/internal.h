@@ -268,7 +268,8 @@ struct IndexedArgs {
   uint32_t* out_u32;
   unsigned long long* out_u64;
   int* status;
-  int64_t* tests_out;   // subset tests executed
+  int64_t* tests_out;   // subset tests executed (tensor-core form: pinned host memory,
+                        // written when the stream gets there)
   int prof_stage = -1;  // stage under which the grouped kernel is timed
   int max_q = 4;        // most own rows per thread of a block (1, 2, 4)
   int flip_factor = 2;  // side ratio before the non-result side goes to registers
@@ -293,17 +294,23 @@ struct KeyedIndex {
   std::vector<uint32_t> h_off;
 };
 // n_dev (optional): the number of rows on the device, at most n (an upper
-// bound then, used for sizes); out->n is the number filed.
+// bound then, used for sizes); out->n is the number filed.  With
+// host_offsets false nothing is read back and the stream is not
+// synchronized: h_off stays empty and out->n is the bound n (for the
+// tensor-core form, which builds its work items on the device).
 cudaError_t build_keyed_index(const uint64_t* keyed, int64_t n, int stride, int K, int KT,
                               const uint32_t* freq, const uint64_t* score, KeyedIndex* out,
-                              cudaStream_t s, const unsigned long long* n_dev = nullptr);
+                              cudaStream_t s, const unsigned long long* n_dev = nullptr,
+                              bool host_offsets = true);
 void release_keyed_index(KeyedIndex* k, cudaStream_t s);
 // The item-index test with its blocks run on the tensor cores (KT 2, 4, 8):
-// the result side -- patterns for MODE_ANY / MODE_COUNT, records for
-// MODE_SUM -- goes to resident 128-row tiles, the other side streams; packed
-// rows are expanded to operand tiles in shared memory by a persistent kernel.
-// Same results as the integer grouped kernel; *tests_out as for
-// indexed_subset_prebuilt.
+// the patterns go to resident tiles, the records stream; packed rows are
+// expanded to operand tiles by a persistent kernel whose work items are
+// built on the device from the indexes' device offsets (the keyed indexes
+// need no host offsets).  Same results as the integer grouped kernel.
+// tests_out (optional) must be pinned host memory: the executed tests are
+// copied there when the stream reaches this point (valid after the caller's
+// next synchronization).
 // score_max (MODE_SUM): an upper bound of the keyed rows' scores; below
 // 2^27 the kernel sums each hit column's scores over a warp in 32 bits
 // before adding them to the record.
@@ -320,7 +327,9 @@ cudaError_t indexed_subset_tc(int mode, const RecordIndex& idx, const KeyedIndex
                               uint32_t* out_u32, unsigned long long* out_u64, int* status,
                               int64_t* tests_out, int prof_stage, uint64_t score_max,
                               cudaStream_t s);
-// indexed_subset with a prebuilt pattern side; no synchronization.
+// indexed_subset with a prebuilt pattern side; no synchronization.  The
+// tensor-core form writes *tests_out asynchronously (pinned host memory,
+// valid after the caller's next synchronization), the integer form at once.
 cudaError_t indexed_subset_prebuilt(int mode, const RecordIndex& idx, const KeyedIndex& kx,
                                     uint32_t* out_u32, unsigned long long* out_u64, int* status,
                                     int64_t* tests_out, int prof_stage, int max_q,

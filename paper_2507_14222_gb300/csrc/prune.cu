@@ -711,7 +711,7 @@ void release_keyed_index(KeyedIndex* k, cudaStream_t s) {
 
 cudaError_t build_keyed_index(const uint64_t* keyed, int64_t n, int stride, int K, int KT,
                               const uint32_t* freq, const uint64_t* score, KeyedIndex* out,
-                              cudaStream_t s, const unsigned long long* n_dev) {
+                              cudaStream_t s, const unsigned long long* n_dev, bool host_offsets) {
   *out = KeyedIndex();
   out->K = K;
   out->KT = KT;
@@ -742,10 +742,12 @@ cudaError_t build_keyed_index(const uint64_t* keyed, int64_t n, int stride, int 
   IG_K_TRY(launch_keyed_scatter(keyed, n, stride, K, KT, groups, key, out->off, kcount + groups,
                                 out->rows, out->ids, score, out->score, n_dev, s));
   prof_end(tok);
-  out->h_off.assign(groups + 1, 0u);
-  IG_K_TRY(cudaMemcpyAsync(out->h_off.data(), out->off, (groups + 1) * 4, cudaMemcpyDeviceToHost, s));
-  IG_K_TRY(cudaStreamSynchronize(s));
-  out->n = int64_t(out->h_off[groups]);  // the rows filed: n, or *n_dev when given
+  if (host_offsets) {
+    out->h_off.assign(groups + 1, 0u);
+    IG_K_TRY(cudaMemcpyAsync(out->h_off.data(), out->off, (groups + 1) * 4, cudaMemcpyDeviceToHost, s));
+    IG_K_TRY(cudaStreamSynchronize(s));
+    out->n = int64_t(out->h_off[groups]);  // the rows filed: n, or *n_dev when given
+  }
   cudaFreeAsync(kcount, s);
   cudaFreeAsync(key, s);
 #undef IG_K_TRY
@@ -760,7 +762,7 @@ cudaError_t indexed_subset_prebuilt(int mode, const RecordIndex& idx, const Keye
   *tests_out = 0;
   if (kx.n == 0 || idx.n_rows == 0) return cudaSuccess;
   const int L = idx.L, KT = idx.KT;
-  if (tc && tc_supported(KT))
+  if (tc && tc_supported(KT))  // work items built on the device; *tests_out written later
     return indexed_subset_tc(mode, idx, kx, out_u32, out_u64, status, tests_out, prof_stage,
                              score_max, s);
   std::vector<WorkItem> items;
@@ -807,9 +809,11 @@ cudaError_t indexed_subset(const IndexedArgs& a, cudaStream_t s) {
   const RecordIndex& idx = *a.index;
   if (a.n_keyed == 0 || idx.n_rows == 0) return cudaSuccess;
   KeyedIndex kx;
+  // The tensor-core form builds its work items on the device: no read-back.
+  const bool device_items = a.tc && tc_supported(idx.KT);
   cudaError_t e = build_keyed_index(a.keyed, a.n_keyed, a.keyed_stride, idx.K, idx.KT, idx.freq,
                                     a.mode == MODE_SUM ? a.keyed_score : nullptr, &kx, s,
-                                    a.n_keyed_dev);
+                                    a.n_keyed_dev, !device_items);
   if (e != cudaSuccess) return e;
   if (kx.n == 0) {  // no keyed rows left on the device: nothing to test
     release_keyed_index(&kx, s);

@@ -1091,9 +1091,8 @@ static cudaError_t run_fused(const FusedParams& p, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(subset_tc_fused_kernel<KT, MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::kSmem));
   if (e != cudaSuccess) return e;
-  // As many CTAs as the items' CTA lists (cta_off) were made for.
-  const int64_t grid = std::min<int64_t>(p.n_items, int64_t(num_sms()));
-  subset_tc_fused_kernel<KT, MODE><<<unsigned(grid), kFusedThreads, S::kSmem, s>>>(p);
+  // One CTA per SM: the items' CTA lists (cta_off) are made for that many.
+  subset_tc_fused_kernel<KT, MODE><<<unsigned(num_sms()), kFusedThreads, S::kSmem, s>>>(p);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -1122,15 +1121,172 @@ void test_stall(uint32_t* poll_limit, int64_t* stall_unit) {
   *poll_limit = 64;
 }
 
-// Pinned staging for the work items, one per host thread; reused once the
-// copy out of it (recorded by `done`) has finished.
-struct TcStaging {
-  uint8_t* buf = nullptr;
-  size_t cap = 0;
-  cudaEvent_t done = nullptr;
-};
-thread_local TcStaging g_tc_staging;
 }  // namespace
+
+// ---- work items, built on the device --------------------------------------
+//
+// The fused kernel's work items are (class, item group, resident tile of
+// own_rows patterns, range of `per` stream tiles of 128 records), `per` set
+// so that there are about eight items per SM.  One CTA builds them from the
+// indexes' group offsets on the device -- no read-back, no host work, no
+// copy -- and deals them to the CTAs of the persistent grid: sorted by cost
+// (stream tiles x halves + 2, in kCostBuckets classes, largest first), in
+// snake order (CTAs 0 .. G-1, then G-1 .. 0, ...), so that every CTA runs a
+// contiguous list, largest items first, with about equal totals.  The order
+// of the items does not change any result (flags, counts and sums are
+// order-independent integers).
+constexpr int kItemThreads = 1024;
+constexpr int kItemMaxL = 1024;   // items per index (64 K, K <= 16)
+constexpr int kItemMaxGrid = 1024;
+constexpr int kCostBuckets = 64;
+
+struct ItemBuild {
+  const uint32_t* own_off[2];  // keyed (pattern) group offsets per class
+  const uint32_t* str_off;     // record group offsets
+  int n_cls, L, own_rows, grid;
+  int64_t max_items;
+  TcItem* items;               // [max_items]
+  int64_t* cta_off;            // [grid + 1]
+  unsigned long long* tests;   // [n_cls]: (pattern, record) pairs met, per class
+  int* status;
+};
+
+__device__ __forceinline__ int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Exclusive scan of v[0, n) in place (v[n] = total), by one block: a chunk
+// of consecutive entries per thread, then a scan of the chunk sums.
+template <class V>
+__device__ void block_exclusive_scan(V* v, int n, V* part) {
+  const int T = blockDim.x, t = threadIdx.x;
+  const int chunk = (n + T - 1) / T;
+  const int lo = t * chunk, hi = lo + chunk < n ? lo + chunk : n;
+  V sum = 0;
+  for (int i = lo; i < hi; ++i) sum += v[i];
+  part[t] = sum;
+  __syncthreads();
+  for (int d = 1; d < T; d <<= 1) {
+    const V x = t >= d ? part[t - d] : V(0);
+    __syncthreads();
+    part[t] += x;
+    __syncthreads();
+  }
+  V run = part[t] - sum;
+  for (int i = lo; i < hi; ++i) {
+    const V x = v[i];
+    v[i] = run;
+    run += x;
+  }
+  __syncthreads();
+  if (t == T - 1) v[n] = part[T - 1];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kItemThreads) tc_items_kernel(ItemBuild b) {
+  __shared__ uint32_t s_no[2][kItemMaxL];
+  __shared__ uint32_t s_ns[kItemMaxL];
+  __shared__ int64_t s_off[2 * kItemMaxL + 1];
+  __shared__ int64_t s_cta[kItemMaxGrid + 1];
+  __shared__ int64_t s_part[kItemThreads];
+  __shared__ uint32_t s_hist[kCostBuckets + 1], s_cnt2[kCostBuckets];
+  __shared__ unsigned long long s_tiles, s_tests[2];
+  const int L = b.L, G = b.grid, t = threadIdx.x, T = blockDim.x;
+  const int own_rows = b.own_rows, ng = b.n_cls * L;
+  if (t == 0) {
+    s_tiles = 0;
+    s_tests[0] = s_tests[1] = 0;
+  }
+  for (int i = t; i < kCostBuckets; i += T) s_hist[i] = s_cnt2[i] = 0;
+  __syncthreads();
+  unsigned long long tiles = 0, tests[2] = {0, 0};
+  for (int l = t; l < L; l += T) {
+    const uint32_t ns = b.str_off[l + 1] - b.str_off[l];
+    s_ns[l] = ns;
+    for (int c = 0; c < b.n_cls; ++c) {
+      const uint32_t no = b.own_off[c][l + 1] - b.own_off[c][l];
+      s_no[c][l] = no;
+      if (no && ns) {
+        tiles += uint64_t(div_up(no, own_rows)) * uint64_t(div_up(ns, 128));
+        tests[c] += uint64_t(no) * ns;
+      }
+    }
+  }
+  if (tiles) atomicAdd(&s_tiles, tiles);
+  if (tests[0]) atomicAdd(&s_tests[0], tests[0]);
+  if (tests[1]) atomicAdd(&s_tests[1], tests[1]);
+  __syncthreads();
+  const int64_t per_raw = int64_t(s_tiles) / (int64_t(G) * 8);
+  const int64_t per = per_raw > 1 ? per_raw : 1;
+  for (int g = t; g < ng; g += T) {
+    const int c = g / L, l = g - c * L;
+    const int64_t no = s_no[c][l], ns = s_ns[l];
+    s_off[g] = (no && ns) ? div_up(no, own_rows) * div_up(div_up(ns, 128), per) : 0;
+  }
+  __syncthreads();
+  block_exclusive_scan(s_off, ng, s_part);
+  const int64_t n_items = s_off[ng];
+  if (n_items > b.max_items) {  // cannot happen with the host's bound; no item is written
+    if (t == 0) set_status(b.status, ST_COUNT);
+    for (int i = t; i <= G; i += T) b.cta_off[i] = 0;
+    return;
+  }
+  // Item k: its (class, group) by a binary search of the scanned counts,
+  // then its resident tile and stream range.
+  auto item_of = [&](int64_t k, TcItem& it) {
+    int lo = 0, hi = ng - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_off[mid] <= k) lo = mid; else hi = mid - 1;
+    }
+    const int c = lo / L, l = lo - c * L;
+    const int64_t no = s_no[c][l], ns = s_ns[l], nb = div_up(ns, 128);
+    const int64_t nbp = div_up(nb, per), j = k - s_off[lo];
+    const int64_t a = j / nbp, bs = (j - a * nbp) * per;
+    it.own_first = int64_t(b.own_off[c][l]) + a * own_rows;
+    it.str_first = int64_t(b.str_off[l]) + bs * 128;
+    it.own_count = int32_t(min(int64_t(own_rows), no - a * own_rows));
+    it.b_tiles = int32_t(min(per, nb - bs));
+    it.str_count = int32_t(min(per * 128, ns - bs * 128));
+    it.pad = c;
+  };
+  const int64_t cmax = 2 * per + 2;
+  auto bucket_of = [&](const TcItem& it) {
+    const int64_t cost = int64_t(it.b_tiles) * (it.own_count > 128 ? 2 : 1) + 2;
+    return int((cmax - cost) * kCostBuckets / (cmax + 1));
+  };
+  for (int64_t k = t; k < n_items; k += T) {
+    TcItem it;
+    item_of(k, it);
+    atomicAdd(&s_hist[bucket_of(it)], 1u);
+  }
+  __syncthreads();
+  if (t == 0) {
+    uint32_t run = 0;
+    for (int i = 0; i < kCostBuckets; ++i) {
+      const uint32_t x = s_hist[i];
+      s_hist[i] = run;
+      run += x;
+    }
+  }
+  // CTA lists: the sorted item s goes to round s / G, CTA s % G in even
+  // rounds and G - 1 - s % G in odd ones; a CTA's list holds one item per
+  // round it takes part in.
+  const int64_t R = n_items / G, rem = n_items - R * G;
+  for (int g = t; g < G; g += T)
+    s_cta[g] = R + (((R & 1) == 0) ? (g < rem ? 1 : 0) : (g >= G - rem ? 1 : 0));
+  __syncthreads();
+  block_exclusive_scan(s_cta, G, s_part);
+  for (int64_t k = t; k < n_items; k += T) {
+    TcItem it;
+    item_of(k, it);
+    const int bk = bucket_of(it);
+    const int64_t sp = int64_t(s_hist[bk]) + atomicAdd(&s_cnt2[bk], 1u);
+    const int64_t round = sp / G, kk = sp - round * G;
+    const int64_t cta = (round & 1) ? G - 1 - kk : kk;
+    b.items[s_cta[cta] + round] = it;
+  }
+  for (int i = t; i <= G; i += T) b.cta_off[i] = s_cta[i];
+  if (t < b.n_cls) b.tests[t] = s_tests[t];
+}
 
 cudaError_t indexed_subset_tc_classes(int mode, const RecordIndex& idx, const KeyedIndex* const* kx,
                                       int n_cls, uint32_t* out_u32,
@@ -1139,8 +1295,7 @@ cudaError_t indexed_subset_tc_classes(int mode, const RecordIndex& idx, const Ke
                                       const uint64_t* score_max, cudaStream_t s) {
   const int L = idx.L, KT = idx.KT;
   if (n_cls < 1 || n_cls > 2 || (n_cls == 2 && mode != MODE_SUM)) return cudaErrorInvalidValue;
-  for (int c = 0; c < n_cls; ++c) tests_out[c] = 0;
-  if (idx.n_rows == 0 || !tc_supported(KT)) return cudaErrorInvalidValue;
+  if (idx.n_rows == 0 || !tc_supported(KT) || L > kItemMaxL) return cudaErrorInvalidValue;
   // Patterns (keyed) are resident and records (multi, complemented) stream,
   // in every mode: an item group holds far fewer patterns than records, so
   // items are long (about 90 stream tiles at NSL-KDD shape, against 6-9 with
@@ -1148,90 +1303,36 @@ cudaError_t indexed_subset_tc_classes(int mode, const RecordIndex& idx, const Ke
   // often.  ANY / COUNT results stay per resident row; SUM adds each
   // pattern's score to the records containing it.  With two classes (SUM),
   // both classes' items share one launch, one schedule and one tail.
-  const uint32_t* str_off = idx.h_off.data();
-  std::vector<TcItem> items;
-  const int64_t own_rows = 128 * fused_halves(mode), n_rows = fused_n(mode);
-  int64_t pair_tiles = 0;
-  for (int c = 0; c < n_cls; ++c) {
-    if (kx[c]->n == 0) continue;
-    const uint32_t* own_off = kx[c]->h_off.data();
-    for (int l = 0; l < L; ++l) {
-      const int64_t no = int64_t(own_off[l + 1]) - own_off[l];
-      const int64_t ns = int64_t(str_off[l + 1]) - str_off[l];
-      if (no == 0 || ns == 0) continue;
-      tests_out[c] += no * ns;
-      pair_tiles += ceil_div(no, own_rows) * ceil_div(ns, n_rows);
-    }
-  }
-  if (pair_tiles == 0) return cudaSuccess;
-  // Stream ranges of `per` tiles (about eight items per SM).
-  const int64_t per = std::max<int64_t>(1, pair_tiles / (int64_t(num_sms()) * 8));
-  for (int c = 0; c < n_cls; ++c) {
-    if (kx[c]->n == 0) continue;
-    const uint32_t* own_off = kx[c]->h_off.data();
-    for (int l = 0; l < L; ++l) {
-      const int64_t no = int64_t(own_off[l + 1]) - own_off[l];
-      const int64_t ns = int64_t(str_off[l + 1]) - str_off[l];
-      if (no == 0 || ns == 0) continue;
-      const int64_t nb = ceil_div(ns, n_rows);
-      for (int64_t a = 0; a * own_rows < no; ++a)
-        for (int64_t b = 0; b < nb; b += per) {
-          TcItem it;
-          it.own_first = int64_t(own_off[l]) + a * own_rows;
-          it.str_first = int64_t(str_off[l]) + b * n_rows;
-          it.own_count = int32_t(std::min<int64_t>(own_rows, no - a * own_rows));
-          it.b_tiles = int32_t(std::min<int64_t>(per, nb - b));
-          it.str_count = int32_t(std::min<int64_t>(per * n_rows, ns - b * n_rows));
-          it.pad = c;
-          items.push_back(it);
-        }
-    }
-  }
-  // Items to CTAs in snake order over the items sorted longest first
-  // (CTAs 0 .. G-1, then G-1 .. 0, ...), which evens out the CTAs' totals
-  // far better than plain round-robin; a CTA's items are contiguous and it
-  // runs them largest first.  An item costs its MMA units plus about two
-  // units for its resident rows.
-  const int64_t grid = std::min<int64_t>(int64_t(items.size()), int64_t(num_sms()));
-  auto cost = [](const TcItem& w) {
-    return int64_t(w.b_tiles) * (w.own_count > 128 ? 2 : 1) + 2;
-  };
-  std::stable_sort(items.begin(), items.end(),
-                   [&](const TcItem& x, const TcItem& y) { return cost(x) > cost(y); });
-  auto cta_of = [&](size_t i) {
-    const int64_t round = int64_t(i) / grid, k = int64_t(i) % grid;
-    return (round & 1) ? grid - 1 - k : k;
-  };
-  std::vector<int64_t> cta_off(size_t(grid) + 1, 0);
-  for (size_t i = 0; i < items.size(); ++i) ++cta_off[size_t(cta_of(i)) + 1];
-  for (int64_t b = 0; b < grid; ++b) cta_off[size_t(b) + 1] += cta_off[size_t(b)];
-  {
-    std::vector<TcItem> by_cta(items.size());
-    std::vector<int64_t> pos(cta_off.begin(), cta_off.end() - 1);
-    for (size_t i = 0; i < items.size(); ++i) by_cta[size_t(pos[size_t(cta_of(i))]++)] = items[i];
-    items.swap(by_cta);
-  }
-  const size_t item_bytes = items.size() * sizeof(TcItem);
-  const size_t bytes = item_bytes + cta_off.size() * sizeof(int64_t);
-  TcStaging& st = g_tc_staging;
-  cudaError_t e;
-  if (st.done && (e = cudaEventSynchronize(st.done)) != cudaSuccess) return e;
-  if (st.cap < bytes) {
-    if (st.buf) cudaFreeHost(st.buf);
-    st.buf = nullptr;
-    st.cap = 0;
-    if ((e = cudaMallocHost(reinterpret_cast<void**>(&st.buf), bytes * 2)) != cudaSuccess) return e;
-    st.cap = bytes * 2;
-  }
-  if (!st.done && (e = cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming)) != cudaSuccess)
-    return e;
-  std::memcpy(st.buf, items.data(), item_bytes);
-  std::memcpy(st.buf + item_bytes, cta_off.data(), cta_off.size() * sizeof(int64_t));
-  TcItem* d_items = nullptr;
-  e = cudaMallocAsync(reinterpret_cast<void**>(&d_items), bytes, s);
+  const int G = num_sms();
+  if (G > kItemMaxGrid) return cudaErrorInvalidValue;
+  const int64_t own_rows = 128 * fused_halves(mode);
+  // At most 16 G items beyond one per (class, group, resident tile).
+  int64_t max_items = 16 * int64_t(G);
+  for (int c = 0; c < n_cls; ++c) max_items += ceil_div(kx[c]->n, own_rows) + L + 1;
+  const size_t item_bytes = size_t(max_items) * sizeof(TcItem);
+  const size_t bytes = item_bytes + size_t(G + 1) * 8 + size_t(n_cls) * 8;
+  uint8_t* blk = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&blk), bytes, s);
   if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(d_items, st.buf, bytes, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaEventRecord(st.done, s);
+  TcItem* d_items = reinterpret_cast<TcItem*>(blk);
+  int64_t* d_cta = reinterpret_cast<int64_t*>(blk + item_bytes);
+  unsigned long long* d_tests = reinterpret_cast<unsigned long long*>(d_cta + G + 1);
+  ItemBuild ib;
+  ib.own_off[0] = kx[0]->off;
+  ib.own_off[1] = kx[n_cls - 1]->off;
+  ib.str_off = idx.off;
+  ib.n_cls = n_cls;
+  ib.L = L;
+  ib.own_rows = int(own_rows);
+  ib.grid = G;
+  ib.max_items = max_items;
+  ib.items = d_items;
+  ib.cta_off = d_cta;
+  ib.tests = d_tests;
+  ib.status = status;
+  tc_items_kernel<<<1, kItemThreads, 0, s>>>(ib);
+  count_launches(1);
+  e = cudaGetLastError();
   if (e == cudaSuccess) {
     const KeyedIndex& k0 = *kx[0];
     const KeyedIndex& k1 = *kx[n_cls - 1];
@@ -1239,9 +1340,8 @@ cudaError_t indexed_subset_tc_classes(int mode, const RecordIndex& idx, const Ke
       return mode == MODE_SUM && score_max[c] < (uint64_t(1) << 27) && !force_wide_sums() ? 1 : 0;
     };
     FusedParams p{d_items,
-                  int64_t(items.size()),
-                  reinterpret_cast<const int64_t*>(reinterpret_cast<const uint8_t*>(d_items) +
-                                                   item_bytes),
+                  max_items,
+                  d_cta,
                   k0.rows,
                   k1.rows,
                   k0.ids,
@@ -1275,7 +1375,10 @@ cudaError_t indexed_subset_tc_classes(int mode, const RecordIndex& idx, const Ke
 #undef IG_TCF_CASE
     prof_end(tok);
   }
-  cudaFreeAsync(d_items, s);
+  // The tests, into the caller's pinned words when the stream gets here.
+  if (e == cudaSuccess && tests_out)
+    e = cudaMemcpyAsync(tests_out, d_tests, size_t(n_cls) * 8, cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(blk, s);
   return e;
 }
 
@@ -1283,8 +1386,7 @@ cudaError_t indexed_subset_tc(int mode, const RecordIndex& idx, const KeyedIndex
                               uint32_t* out_u32, unsigned long long* out_u64, int* status,
                               int64_t* tests_out, int prof_stage, uint64_t score_max,
                               cudaStream_t s) {
-  *tests_out = 0;
-  if (kx.n == 0 || idx.n_rows == 0 || !tc_supported(idx.KT)) return cudaErrorInvalidValue;
+  if (idx.n_rows == 0 || !tc_supported(idx.KT)) return cudaErrorInvalidValue;
   const KeyedIndex* kxs[1] = {&kx};
   unsigned long long* sums[1] = {out_u64};
   return indexed_subset_tc_classes(mode, idx, kxs, 1, out_u32, sums, status, tests_out,
