@@ -215,10 +215,11 @@ __device__ __forceinline__ void pair_tile(const uint64_t* __restrict__ X, int64_
 template <int KT>
 __global__ void __launch_bounds__(kPairThreads)
     pair_insert_kernel(const uint64_t* __restrict__ X, int64_t n, int64_t band_lo,
-                       PairTable t, int* status) {
+                       PairTable t, int* status, const unsigned long long* __restrict__ n_dev) {
   __shared__ PairSmem<KT> sm;
+  if (n_dev && int64_t(*n_dev) < n) n = int64_t(*n_dev);
   const int64_t bi = band_lo + blockIdx.y, bj = blockIdx.x;
-  if (bj < bi) return;
+  if (bj < bi || bj * kPairTile >= n) return;
   pair_tile<KT>(X, n, bi, bj, t, status, sm);
 }
 
@@ -368,8 +369,54 @@ __global__ void __launch_bounds__(kCompactThreads)
   }
 }
 
+// Marks the repeated rows of X[0, n): rows are put in an open-addressing
+// table of row indices (cap > n slots, all 0xffffffff) by content; the row
+// that claims a content's slot represents it (flag 0) and every other row
+// with that content is flagged 1.  The table is never full, so every probe
+// ends within cap slots.
+template <int KT>
+__global__ void mark_repeats_kernel(const uint64_t* __restrict__ X, int64_t n,
+                                    uint32_t* __restrict__ table, uint64_t mask,
+                                    uint32_t* __restrict__ flag) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t w[KT];
+#pragma unroll
+  for (int k = 0; k < KT; ++k) w[k] = X[i * KT + k];
+  uint64_t slot = hash_key<KT>(w) & mask;
+  for (uint64_t probe = 0; probe <= mask; ++probe) {
+    uint32_t cur = table[slot];
+    if (cur == 0xffffffffu) {
+      cur = atomicCAS(table + slot, 0xffffffffu, uint32_t(i));
+      if (cur == 0xffffffffu) {
+        flag[i] = 0u;
+        return;
+      }
+    }
+    bool same = true;
+#pragma unroll
+    for (int k = 0; k < KT; ++k) same &= X[int64_t(cur) * KT + k] == w[k];
+    if (same) {
+      flag[i] = 1u;
+      return;
+    }
+    slot = (slot + 1) & mask;
+  }
+}
+
+cudaError_t launch_mark_repeats(const uint64_t* X, int64_t n, int KT, uint32_t* table,
+                                uint64_t cap, uint32_t* flag, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  if (cap <= uint64_t(n) || (cap & (cap - 1)) != 0) return cudaErrorInvalidValue;
+  IG_DISPATCH_KT(KT, (mark_repeats_kernel<KTC><<<unsigned(ceil_div(n, 256)), 256, 0, s>>>(
+                         X, n, table, cap - 1, flag)));
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pair_insert(const uint64_t* X, int64_t n, int KT, int64_t band_lo,
-                               PairTable t, int* status, cudaStream_t s) {
+                               PairTable t, int* status, cudaStream_t s,
+                               const unsigned long long* n_dev) {
   int64_t nt = ceil_div(n, kPairTile);
   if (band_lo >= nt) return cudaSuccess;
   dim3 grid{unsigned(nt), unsigned(nt - band_lo), 1u};
@@ -380,7 +427,7 @@ cudaError_t launch_pair_insert(const uint64_t* X, int64_t n, int KT, int64_t ban
   const int64_t warps = std::min<int64_t>(tiles, int64_t(num_sms()) * 8) * (kPairThreads / 32);
   t.flush = uint32_t(std::max<int64_t>(1, std::min<int64_t>(256, int64_t(t.limit) / (4 * warps))));
   IG_DISPATCH_KT(KT, (pair_insert_kernel<KTC><<<grid, kPairThreads, 0, s>>>(X, n, band_lo, t,
-                                                                             status)));
+                                                                             status, n_dev)));
   count_launches(1);
   return cudaGetLastError();
 }

@@ -532,6 +532,28 @@ int igk::report_error(int code, const char* msg) { return fail(code, "%s", msg);
 
 namespace {
 
+// The distinct rows of X[0, n) (stride KT), in any order, into Xu, their
+// number into *d_nu (on the device).  B^c of Eq. 1 is a set: a repeated
+// record adds no intersection its first copy does not (x AND x = x), so the
+// pair stage needs each record once -- at NSL-KDD shape a quarter of the
+// training records repeat, and the pairs fall to about 55%.
+int unique_rows(const uint64_t* X, int64_t n, int KT, DevBuf<uint64_t>& Xu,
+                unsigned long long* d_nu, cudaStream_t s) {
+  uint64_t cap = 1024;
+  while (cap < 2 * uint64_t(n)) cap <<= 1;
+  DevBuf<uint32_t> table, flag;
+  IG_CUDA(table.alloc(cap, s), "ig_fit: distinct records");
+  IG_CUDA(flag.alloc(size_t(n), s), "ig_fit: distinct records");
+  IG_CUDA(Xu.alloc(size_t(n) * KT, s), "ig_fit: distinct records");
+  IG_CUDA(cudaMemsetAsync(table.p, 0xff, cap * sizeof(uint32_t), s), "ig_fit");
+  IG_CUDA(cudaMemsetAsync(d_nu, 0, sizeof(unsigned long long), s), "ig_fit");
+  ProfScope ps(S_SPLIT, s);
+  IG_CUDA(igk::launch_mark_repeats(X, n, KT, table.p, cap, flag.p, s), "ig_fit: distinct records");
+  IG_CUDA(igk::launch_select_unflagged(X, n, KT, flag.p, Xu.p, d_nu, s),
+          "ig_fit: distinct records");
+  return IG_OK;
+}
+
 // Candidate generation (Eq. 1) for one class, deduplicated on the device.
 // One launch covers every pair band; if the table runs out of room the
 // launch records the lowest band that failed, and the table is doubled,
@@ -690,10 +712,17 @@ int compact_table(const uint64_t* X, int KT, CandTable& tab, int64_t U, int* d_s
 // launch records the lowest band that failed, and the table is grown,
 // rehashed and the bands from that one on are replayed (inserts are
 // idempotent).  Typical workloads need one launch.
-int build_candidates(const uint64_t* X, int64_t n, int KT, cudaStream_t s, int* d_status,
+int build_candidates(const uint64_t* Xall, int64_t n, int KT, cudaStream_t s, int* d_status,
                      TableCounters* h_counters, DevBuf<uint64_t>& cand, int64_t* U_out) {
   if (n > int64_t(65535) * igk::kPairTile)
     return fail(IG_E_OVERFLOW, "ig_fit: more than 4,194,240 records in one class");
+  // Pairs of distinct records only; their count stays on the device (n
+  // sizes the grids).
+  DevBuf<uint64_t> Xu;
+  DevBuf<unsigned long long> d_nu;
+  IG_CUDA(d_nu.alloc(1, s), "ig_fit: distinct records");
+  IG_CHECK(unique_rows(Xall, n, KT, Xu, d_nu.p, s));
+  const uint64_t* X = Xu.p;
   CandTable tab;
   DevBuf<TableCounters> ctr;
   IG_CUDA(ctr.alloc(1, s), "ig_fit: table counters");
@@ -707,7 +736,7 @@ int build_candidates(const uint64_t* X, int64_t n, int KT, cudaStream_t s, int* 
       ProfScope ps(S_PAIR, s);
       IG_CUDA(igk::launch_pair_insert(X, n, KT, band_lo,
                                       make_table(tab.slots.p, tab.cap, ctr.p, kMaxProbe), d_status,
-                                      s),
+                                      s, d_nu.p),
               "ig_fit: pair intersection");
     }
     IG_CUDA(cudaMemcpyAsync(h_counters, ctr.p, sizeof(TableCounters), cudaMemcpyDeviceToHost, s),
@@ -729,6 +758,7 @@ int build_candidates(const uint64_t* X, int64_t n, int KT, cudaStream_t s, int* 
 struct FitPrep {
   bool ready = false;
   DevBuf<uint64_t> X[2];
+  DevBuf<uint64_t> Xu[2];  // the distinct records of each class (the pair stage's rows)
   int64_t nc[2] = {0, 0};
   CandTable tab[2];
   int64_t count[2] = {0, 0};
@@ -915,7 +945,9 @@ int fit_impl(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
     int64_t U = 0;
     if (prep) {
       U = prep->count[c];
-      IG_CHECK(compact_table(X[c].p, KT, prep->tab[c], U, d_status.p, cand, s));
+      prep->Xu[c].s = s;
+      IG_CHECK(compact_table(prep->Xu[c].p, KT, prep->tab[c], U, d_status.p, cand, s));
+      prep->Xu[c].reset();
     } else {
       IG_CHECK(build_candidates(X[c].p, nc[c], KT, s, d_status.p, h_counters, cand, &U));
     }
@@ -1373,6 +1405,24 @@ int batched_candidates(const ig_problem* problems, int32_t np, const ig_params* 
       jobs.push_back(Job{i, c, igk::padded_words(problems[i].K)});
     }
   }
+  // The pair stage runs over each class's distinct records: their counts
+  // are read back together (one synchronization for the batch).
+  std::vector<int64_t> nu(jobs.size(), 0);
+  if (!jobs.empty()) {
+    DevBuf<unsigned long long> d_nu;
+    IG_CUDA(d_nu.alloc(jobs.size(), s), "ig_fit_batched");
+    for (size_t k = 0; k < jobs.size(); ++k) {
+      FitPrep& pp = prep[jobs[k].i];
+      IG_CHECK(unique_rows(pp.X[jobs[k].c].p, pp.nc[jobs[k].c], jobs[k].KT, pp.Xu[jobs[k].c],
+                           d_nu.p + k, s));
+    }
+    unsigned long long* h_nu = reinterpret_cast<unsigned long long*>(h_ctr);
+    IG_CUDA(cudaMemcpyAsync(h_nu, d_nu.p, sizeof(unsigned long long) * jobs.size(),
+                            cudaMemcpyDeviceToHost, s),
+            "ig_fit_batched");
+    IG_CUDA(cudaStreamSynchronize(s), "ig_fit_batched");
+    for (size_t k = 0; k < jobs.size(); ++k) nu[k] = int64_t(h_nu[k]);
+  }
   // Table sizes.  A table with room for every pair (a key per pair at half
   // load) never has to grow, so the stage needs one launch; that is the
   // size while all tables together stay within an eighth of the device's
@@ -1383,7 +1433,7 @@ int batched_candidates(const ig_problem* problems, int32_t np, const ig_params* 
     uint64_t room = 0;
     std::vector<uint64_t> cap(jobs.size());
     for (size_t k = 0; k < jobs.size(); ++k) {
-      const int64_t n = prep[jobs[k].i].nc[jobs[k].c];
+      const int64_t n = nu[k];
       const uint64_t pairs = uint64_t(n) * uint64_t(n + 1) / 2;
       uint64_t c = 1u << 12;
       while (c < 2 * pairs) c <<= 1;
@@ -1394,11 +1444,9 @@ int batched_candidates(const ig_problem* problems, int32_t np, const ig_params* 
     // that tables grow and their bands are replayed.
     const char* small = std::getenv("IG_TEST_SMALL_TABLES");
     const bool roomy = room <= total_b / 8 && !(small && small[0] == '1');
-    for (size_t k = 0; k < jobs.size(); ++k) {
-      const int64_t n = prep[jobs[k].i].nc[jobs[k].c];
-      IG_CUDA(alloc_table(prep[jobs[k].i].tab[jobs[k].c], roomy ? cap[k] : initial_cap(n), s),
+    for (size_t k = 0; k < jobs.size(); ++k)
+      IG_CUDA(alloc_table(prep[jobs[k].i].tab[jobs[k].c], roomy ? cap[k] : initial_cap(nu[k]), s),
               "ig_fit_batched: hash table");
-    }
   }
   DevBuf<TableCounters> d_ctr;
   IG_CUDA(d_ctr.alloc(std::max<size_t>(1, jobs.size()), s), "ig_fit_batched");
@@ -1421,8 +1469,8 @@ int batched_candidates(const ig_problem* problems, int32_t np, const ig_params* 
       const Job& jb = jobs[k];
       FitPrep& pp = prep[jb.i];
       igk::PairJob j;
-      j.X = pp.X[jb.c].p;
-      j.n = pp.nc[jb.c];
+      j.X = pp.Xu[jb.c].p;
+      j.n = nu[k];
       j.band_lo = band_lo[k];
       j.KT = jb.KT;
       j.t = make_table(pp.tab[jb.c].slots.p, pp.tab[jb.c].cap, d_ctr.p + k, kMaxProbe);
@@ -1461,7 +1509,7 @@ int batched_candidates(const ig_problem* problems, int32_t np, const ig_params* 
       const Job& jb = jobs[k];
       FitPrep& pp = prep[jb.i];
       band_lo[k] = h_ctr[k].failed_band;
-      IG_CHECK(grow_table(pp.X[jb.c].p, pp.nc[jb.c], jb.KT, pp.tab[jb.c], d_ctr.p + k, band_lo[k],
+      IG_CHECK(grow_table(pp.Xu[jb.c].p, nu[k], jb.KT, pp.tab[jb.c], d_ctr.p + k, band_lo[k],
                           h_ctr[k].count, pair_status, s));
       IG_CUDA(cudaMemsetAsync(&d_ctr.p[k].failed_band, 0x7f, sizeof(int), s), "ig_fit_batched");
       again.push_back(k);

@@ -116,8 +116,16 @@ constexpr int kPairTile = 64;  // records per side of a pair tile (one band = on
 // Inserts x_i AND x_j for every i <= j (i == j gives the record itself),
 // skipping empty intersections, for every pair tile in bands >= band_lo of
 // the upper triangle; one launch.
+// flag[i] = 1 for every row of X[0, n) (stride KT) whose content an
+// earlier-claimed row already has, 0 for one row per distinct content.
+// table: cap uint32 slots (cap a power of two above n), all 0xffffffff.
+cudaError_t launch_mark_repeats(const uint64_t* X, int64_t n, int KT, uint32_t* table,
+                                uint64_t cap, uint32_t* flag, cudaStream_t s);
+// n_dev (optional): the number of rows on the device, at most n (n then
+// sizes the grid only).
 cudaError_t launch_pair_insert(const uint64_t* X, int64_t n, int KT, int64_t band_lo,
-                               PairTable t, int* status, cudaStream_t s);
+                               PairTable t, int* status, cudaStream_t s,
+                               const unsigned long long* n_dev = nullptr);
 // One table of a multi-table pair launch: the records X[0, n) (KT words
 // per row), the bands [band_lo, ceil(n / kPairTile)) and the table (its
 // flush set by the caller, see pair_multi_grid_warps).
