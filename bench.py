@@ -342,10 +342,14 @@ def measure_batched(args, ig, torch, local, steps, warmup, seed=2000):
     def step(batched):
         enc = encode_all()
         if batched:
+            # One lane: the candidate stage of all problems is one launch either
+            # way, and on this GPU-bound mix more lanes measured no faster once
+            # warm (the first multi-lane call is, later ones not).
             models = ig.ig_fit_batched([(r, lab) for r, lab, _ in enc],
                                        subset_kernel=args.kernel,
-                                       per_problem_params=per_params)
-            scores = ig.ig_score_batched([(mdl, te) for mdl, (_, _, te) in zip(models, enc)])
+                                       per_problem_params=per_params, lanes=1)
+            scores = ig.ig_score_batched([(mdl, te) for mdl, (_, _, te) in zip(models, enc)],
+                                         lanes=1)
             return models, scores
         else:
             models = []

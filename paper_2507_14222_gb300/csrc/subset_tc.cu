@@ -1153,40 +1153,53 @@ struct ItemBuild {
 
 __device__ __forceinline__ int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// Exclusive scan of v[0, n) in place (v[n] = total), by one block: a chunk
-// of consecutive entries per thread, then a scan of the chunk sums.
+// Exclusive scan of v[0, n) in place (v[n] = total), by one block of at
+// most 1,024 threads: a chunk of consecutive entries per thread, the chunk
+// sums scanned by warp shuffles and then across the warps (part: 32 words).
 template <class V>
 __device__ void block_exclusive_scan(V* v, int n, V* part) {
-  const int T = blockDim.x, t = threadIdx.x;
+  const int T = blockDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int chunk = (n + T - 1) / T;
   const int lo = t * chunk, hi = lo + chunk < n ? lo + chunk : n;
   V sum = 0;
   for (int i = lo; i < hi; ++i) sum += v[i];
-  part[t] = sum;
-  __syncthreads();
-  for (int d = 1; d < T; d <<= 1) {
-    const V x = t >= d ? part[t - d] : V(0);
-    __syncthreads();
-    part[t] += x;
-    __syncthreads();
+  V inc = sum;  // inclusive scan of the chunk sums within the warp
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const V x = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += x;
   }
-  V run = part[t] - sum;
+  if (lane == 31) part[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (T + 31) >> 5;
+    V w = lane < nw ? part[lane] : V(0);
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const V x = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += x;
+    }
+    if (lane < nw) part[lane] = w;  // inclusive over the warps
+  }
+  __syncthreads();
+  V run = (warp ? part[warp - 1] : V(0)) + inc - sum;
   for (int i = lo; i < hi; ++i) {
     const V x = v[i];
     v[i] = run;
     run += x;
   }
-  __syncthreads();
-  if (t == T - 1) v[n] = part[T - 1];
+  if (t == T - 1) v[n] = part[((T + 31) >> 5) - 1];
   __syncthreads();
 }
 
 __global__ void __launch_bounds__(kItemThreads) tc_items_kernel(ItemBuild b) {
-  __shared__ uint32_t s_no[2][kItemMaxL];
-  __shared__ uint32_t s_ns[kItemMaxL];
+  // Group offsets of the patterns (per class) and of the records, read
+  // once; sizes are their differences.
+  __shared__ uint32_t s_ob[2][kItemMaxL + 1];
+  __shared__ uint32_t s_sb[kItemMaxL + 1];
   __shared__ int64_t s_off[2 * kItemMaxL + 1];
   __shared__ int64_t s_cta[kItemMaxGrid + 1];
-  __shared__ int64_t s_part[kItemThreads];
+  __shared__ int64_t s_part[32];
   __shared__ uint32_t s_hist[kCostBuckets + 1], s_cnt2[kCostBuckets];
   __shared__ unsigned long long s_tiles, s_tests[2];
   const int L = b.L, G = b.grid, t = threadIdx.x, T = blockDim.x;
@@ -1196,14 +1209,16 @@ __global__ void __launch_bounds__(kItemThreads) tc_items_kernel(ItemBuild b) {
     s_tests[0] = s_tests[1] = 0;
   }
   for (int i = t; i < kCostBuckets; i += T) s_hist[i] = s_cnt2[i] = 0;
+  for (int l = t; l <= L; l += T) {
+    s_sb[l] = b.str_off[l];
+    for (int c = 0; c < b.n_cls; ++c) s_ob[c][l] = b.own_off[c][l];
+  }
   __syncthreads();
   unsigned long long tiles = 0, tests[2] = {0, 0};
   for (int l = t; l < L; l += T) {
-    const uint32_t ns = b.str_off[l + 1] - b.str_off[l];
-    s_ns[l] = ns;
+    const uint32_t ns = s_sb[l + 1] - s_sb[l];
     for (int c = 0; c < b.n_cls; ++c) {
-      const uint32_t no = b.own_off[c][l + 1] - b.own_off[c][l];
-      s_no[c][l] = no;
+      const uint32_t no = s_ob[c][l + 1] - s_ob[c][l];
       if (no && ns) {
         tiles += uint64_t(div_up(no, own_rows)) * uint64_t(div_up(ns, 128));
         tests[c] += uint64_t(no) * ns;
@@ -1218,7 +1233,7 @@ __global__ void __launch_bounds__(kItemThreads) tc_items_kernel(ItemBuild b) {
   const int64_t per = per_raw > 1 ? per_raw : 1;
   for (int g = t; g < ng; g += T) {
     const int c = g / L, l = g - c * L;
-    const int64_t no = s_no[c][l], ns = s_ns[l];
+    const int64_t no = s_ob[c][l + 1] - s_ob[c][l], ns = s_sb[l + 1] - s_sb[l];
     s_off[g] = (no && ns) ? div_up(no, own_rows) * div_up(div_up(ns, 128), per) : 0;
   }
   __syncthreads();
@@ -1238,11 +1253,12 @@ __global__ void __launch_bounds__(kItemThreads) tc_items_kernel(ItemBuild b) {
       if (s_off[mid] <= k) lo = mid; else hi = mid - 1;
     }
     const int c = lo / L, l = lo - c * L;
-    const int64_t no = s_no[c][l], ns = s_ns[l], nb = div_up(ns, 128);
+    const int64_t no = s_ob[c][l + 1] - s_ob[c][l], ns = s_sb[l + 1] - s_sb[l];
+    const int64_t nb = div_up(ns, 128);
     const int64_t nbp = div_up(nb, per), j = k - s_off[lo];
     const int64_t a = j / nbp, bs = (j - a * nbp) * per;
-    it.own_first = int64_t(b.own_off[c][l]) + a * own_rows;
-    it.str_first = int64_t(b.str_off[l]) + bs * 128;
+    it.own_first = int64_t(s_ob[c][l]) + a * own_rows;
+    it.str_first = int64_t(s_sb[l]) + bs * 128;
     it.own_count = int32_t(min(int64_t(own_rows), no - a * own_rows));
     it.b_tiles = int32_t(min(per, nb - bs));
     it.str_count = int32_t(min(per * 128, ns - bs * 128));
@@ -1259,13 +1275,17 @@ __global__ void __launch_bounds__(kItemThreads) tc_items_kernel(ItemBuild b) {
     atomicAdd(&s_hist[bucket_of(it)], 1u);
   }
   __syncthreads();
-  if (t == 0) {
-    uint32_t run = 0;
-    for (int i = 0; i < kCostBuckets; ++i) {
-      const uint32_t x = s_hist[i];
-      s_hist[i] = run;
-      run += x;
+  if (t < 32) {  // exclusive scan of the bucket counts by one warp
+    const uint32_t a0 = s_hist[2 * t], a1 = s_hist[2 * t + 1];
+    uint32_t inc = a0 + a1;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t x = __shfl_up_sync(0xffffffffu, inc, d);
+      if (t >= d) inc += x;
     }
+    const uint32_t ex = inc - a0 - a1;
+    s_hist[2 * t] = ex;
+    s_hist[2 * t + 1] = ex + a0;
   }
   // CTA lists: the sorted item s goes to round s / G, CTA s % G in even
   // rounds and G - 1 - s % G in odd ones; a CTA's list holds one item per
