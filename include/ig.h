@@ -227,8 +227,9 @@ int ig_score(const ig_model* model, const uint64_t* rows, int64_t m,
  * fixed device array inside the library (about 4 MiB, held on every GPU that
  * loads the library until the process exits); it is cleared by each call, and
  * calls whose work overlaps on the GPU race on it.  The first call on each
- * device looks up that array's device address; make that first call before
- * any stream capture.  Synchronizes `stream` before returning. */
+ * device looks up that array's device address.  Synchronizes `stream` before
+ * returning (to read the status word), so a call cannot be captured into a
+ * CUDA graph. */
 #define IG_SCORE_NOALLOC_MAX_ROWS 262144
 int ig_score_noalloc(const ig_model* model, const uint64_t* rows, int64_t m,
                      int64_t* A_out, int64_t* N_out, uint8_t* label_out,
