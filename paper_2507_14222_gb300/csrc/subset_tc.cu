@@ -1127,9 +1127,11 @@ void test_stall(uint32_t* poll_limit, int64_t* stall_unit) {
 //
 // The fused kernel's work items are (class, item group, resident tile of
 // own_rows patterns, range of `per` stream tiles of 128 records), `per` set
-// so that there are about eight items per SM.  One CTA builds them from the
-// indexes' group offsets on the device -- no read-back, no host work, no
-// copy -- and deals them to the CTAs of the persistent grid: sorted by cost
+// so that there are about eight items per SM.  Two kernels build them from
+// the indexes' group offsets on the device -- no read-back, no host work,
+// no copy: one CTA plans (sizes, offsets, cost classes, CTA lists), then one
+// thread per item places it.  Items are dealt to the CTAs of the persistent
+// grid: sorted by cost
 // (stream tiles x halves + 2, in kCostBuckets classes, largest first), in
 // snake order (CTAs 0 .. G-1, then G-1 .. 0, ...), so that every CTA runs a
 // contiguous list, largest items first, with about equal totals.  The order
@@ -1149,7 +1151,19 @@ struct ItemBuild {
   int64_t* cta_off;            // [grid + 1]
   unsigned long long* tests;   // [n_cls]: (pattern, record) pairs met, per class
   int* status;
+  // Passed from the plan kernel to the placement kernel:
+  int64_t* goff;               // [2 L + 1] first item of each (class, group)
+  uint32_t* boff;              // [kCostBuckets] first sorted position of each cost class
+  uint32_t* bcnt;              // [kCostBuckets] positions taken so far
+  int64_t* meta;               // [2]: item count, stream tiles per range (per)
 };
+
+// Cost class of an item (stream tiles x halves + 2, largest first).
+__device__ __forceinline__ int cost_bucket(int64_t b_tiles, int64_t own_count, int64_t per) {
+  const int64_t cmax = 2 * per + 2;
+  const int64_t cost = b_tiles * (own_count > 128 ? 2 : 1) + 2;
+  return int((cmax - cost) * kCostBuckets / (cmax + 1));
+}
 
 __device__ __forceinline__ int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -1192,15 +1206,17 @@ __device__ void block_exclusive_scan(V* v, int n, V* part) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kItemThreads) tc_items_kernel(ItemBuild b) {
-  // Group offsets of the patterns (per class) and of the records, read
-  // once; sizes are their differences.
+// The plan, by one CTA: sizes, the items of each (class, group) and their
+// offsets, the cost classes' sizes (per group in closed form: only a
+// group's last resident tile and last stream range differ from the others)
+// and offsets, and the CTA lists' offsets.
+__global__ void __launch_bounds__(kItemThreads) tc_items_plan_kernel(ItemBuild b) {
   __shared__ uint32_t s_ob[2][kItemMaxL + 1];
   __shared__ uint32_t s_sb[kItemMaxL + 1];
   __shared__ int64_t s_off[2 * kItemMaxL + 1];
   __shared__ int64_t s_cta[kItemMaxGrid + 1];
   __shared__ int64_t s_part[32];
-  __shared__ uint32_t s_hist[kCostBuckets + 1], s_cnt2[kCostBuckets];
+  __shared__ uint32_t s_hist[kCostBuckets];
   __shared__ unsigned long long s_tiles, s_tests[2];
   const int L = b.L, G = b.grid, t = threadIdx.x, T = blockDim.x;
   const int own_rows = b.own_rows, ng = b.n_cls * L;
@@ -1208,7 +1224,10 @@ __global__ void __launch_bounds__(kItemThreads) tc_items_kernel(ItemBuild b) {
     s_tiles = 0;
     s_tests[0] = s_tests[1] = 0;
   }
-  for (int i = t; i < kCostBuckets; i += T) s_hist[i] = s_cnt2[i] = 0;
+  for (int i = t; i < kCostBuckets; i += T) {
+    s_hist[i] = 0;
+    b.bcnt[i] = 0;
+  }
   for (int l = t; l <= L; l += T) {
     s_sb[l] = b.str_off[l];
     for (int c = 0; c < b.n_cls; ++c) s_ob[c][l] = b.own_off[c][l];
@@ -1234,48 +1253,24 @@ __global__ void __launch_bounds__(kItemThreads) tc_items_kernel(ItemBuild b) {
   for (int g = t; g < ng; g += T) {
     const int c = g / L, l = g - c * L;
     const int64_t no = s_ob[c][l + 1] - s_ob[c][l], ns = s_sb[l + 1] - s_sb[l];
-    s_off[g] = (no && ns) ? div_up(no, own_rows) * div_up(div_up(ns, 128), per) : 0;
+    int64_t items = 0;
+    if (no && ns) {
+      const int64_t A = div_up(no, own_rows), nb = div_up(ns, 128), nbp = div_up(nb, per);
+      items = A * nbp;
+      const int64_t rem_o = no - (A - 1) * own_rows, rem_b = nb - (nbp - 1) * per;
+      if (A > 1 && nbp > 1)
+        atomicAdd(&s_hist[cost_bucket(per, own_rows, per)], uint32_t((A - 1) * (nbp - 1)));
+      if (A > 1) atomicAdd(&s_hist[cost_bucket(rem_b, own_rows, per)], uint32_t(A - 1));
+      if (nbp > 1) atomicAdd(&s_hist[cost_bucket(per, rem_o, per)], uint32_t(nbp - 1));
+      atomicAdd(&s_hist[cost_bucket(rem_b, rem_o, per)], 1u);
+    }
+    s_off[g] = items;
   }
   __syncthreads();
   block_exclusive_scan(s_off, ng, s_part);
   const int64_t n_items = s_off[ng];
-  if (n_items > b.max_items) {  // cannot happen with the host's bound; no item is written
-    if (t == 0) set_status(b.status, ST_COUNT);
-    for (int i = t; i <= G; i += T) b.cta_off[i] = 0;
-    return;
-  }
-  // Item k: its (class, group) by a binary search of the scanned counts,
-  // then its resident tile and stream range.
-  auto item_of = [&](int64_t k, TcItem& it) {
-    int lo = 0, hi = ng - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (s_off[mid] <= k) lo = mid; else hi = mid - 1;
-    }
-    const int c = lo / L, l = lo - c * L;
-    const int64_t no = s_ob[c][l + 1] - s_ob[c][l], ns = s_sb[l + 1] - s_sb[l];
-    const int64_t nb = div_up(ns, 128);
-    const int64_t nbp = div_up(nb, per), j = k - s_off[lo];
-    const int64_t a = j / nbp, bs = (j - a * nbp) * per;
-    it.own_first = int64_t(s_ob[c][l]) + a * own_rows;
-    it.str_first = int64_t(s_sb[l]) + bs * 128;
-    it.own_count = int32_t(min(int64_t(own_rows), no - a * own_rows));
-    it.b_tiles = int32_t(min(per, nb - bs));
-    it.str_count = int32_t(min(per * 128, ns - bs * 128));
-    it.pad = c;
-  };
-  const int64_t cmax = 2 * per + 2;
-  auto bucket_of = [&](const TcItem& it) {
-    const int64_t cost = int64_t(it.b_tiles) * (it.own_count > 128 ? 2 : 1) + 2;
-    return int((cmax - cost) * kCostBuckets / (cmax + 1));
-  };
-  for (int64_t k = t; k < n_items; k += T) {
-    TcItem it;
-    item_of(k, it);
-    atomicAdd(&s_hist[bucket_of(it)], 1u);
-  }
-  __syncthreads();
-  if (t < 32) {  // exclusive scan of the bucket counts by one warp
+  const bool fits = n_items <= b.max_items;  // always, with the host's bound
+  if (t < 32) {  // exclusive scan of the cost classes' sizes by one warp
     const uint32_t a0 = s_hist[2 * t], a1 = s_hist[2 * t + 1];
     uint32_t inc = a0 + a1;
 #pragma unroll
@@ -1284,28 +1279,58 @@ __global__ void __launch_bounds__(kItemThreads) tc_items_kernel(ItemBuild b) {
       if (t >= d) inc += x;
     }
     const uint32_t ex = inc - a0 - a1;
-    s_hist[2 * t] = ex;
-    s_hist[2 * t + 1] = ex + a0;
+    b.boff[2 * t] = ex;
+    b.boff[2 * t + 1] = ex + a0;
   }
   // CTA lists: the sorted item s goes to round s / G, CTA s % G in even
   // rounds and G - 1 - s % G in odd ones; a CTA's list holds one item per
   // round it takes part in.
-  const int64_t R = n_items / G, rem = n_items - R * G;
+  const int64_t R = fits ? n_items / G : 0, rem = fits ? n_items - R * G : 0;
   for (int g = t; g < G; g += T)
     s_cta[g] = R + (((R & 1) == 0) ? (g < rem ? 1 : 0) : (g >= G - rem ? 1 : 0));
   __syncthreads();
   block_exclusive_scan(s_cta, G, s_part);
-  for (int64_t k = t; k < n_items; k += T) {
-    TcItem it;
-    item_of(k, it);
-    const int bk = bucket_of(it);
-    const int64_t sp = int64_t(s_hist[bk]) + atomicAdd(&s_cnt2[bk], 1u);
-    const int64_t round = sp / G, kk = sp - round * G;
-    const int64_t cta = (round & 1) ? G - 1 - kk : kk;
-    b.items[s_cta[cta] + round] = it;
-  }
   for (int i = t; i <= G; i += T) b.cta_off[i] = s_cta[i];
+  for (int i = t; i <= ng; i += T) b.goff[i] = s_off[i];
   if (t < b.n_cls) b.tests[t] = s_tests[t];
+  if (t == 0) {
+    if (!fits) set_status(b.status, ST_COUNT);
+    b.meta[0] = fits ? n_items : 0;  // nothing is placed past the bound
+    b.meta[1] = per;
+  }
+}
+
+// The placement, one thread per item: item k of its (class, group), its
+// position among the items sorted by cost class, and its place in its CTA's
+// list.
+__global__ void tc_items_place_kernel(ItemBuild b) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t n_items = b.meta[0];
+  if (k >= n_items) return;
+  const int64_t per = b.meta[1];
+  const int L = b.L, G = b.grid, own_rows = b.own_rows, ng = b.n_cls * L;
+  int lo = 0, hi = ng - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (b.goff[mid] <= k) lo = mid; else hi = mid - 1;
+  }
+  const int c = lo / L, l = lo - c * L;
+  const int64_t o0 = b.own_off[c][l], s0 = b.str_off[l];
+  const int64_t no = int64_t(b.own_off[c][l + 1]) - o0, ns = int64_t(b.str_off[l + 1]) - s0;
+  const int64_t nb = div_up(ns, 128), nbp = div_up(nb, per), j = k - b.goff[lo];
+  const int64_t a = j / nbp, bs = (j - a * nbp) * per;
+  TcItem it;
+  it.own_first = o0 + a * own_rows;
+  it.str_first = s0 + bs * 128;
+  it.own_count = int32_t(min(int64_t(own_rows), no - a * own_rows));
+  it.b_tiles = int32_t(min(per, nb - bs));
+  it.str_count = int32_t(min(per * 128, ns - bs * 128));
+  it.pad = c;
+  const int bk = cost_bucket(it.b_tiles, it.own_count, per);
+  const int64_t sp = int64_t(b.boff[bk]) + atomicAdd(b.bcnt + bk, 1u);
+  const int64_t round = sp / G, kk = sp - round * G;
+  const int64_t cta = (round & 1) ? G - 1 - kk : kk;
+  b.items[b.cta_off[cta] + round] = it;
 }
 
 cudaError_t indexed_subset_tc_classes(int mode, const RecordIndex& idx, const KeyedIndex* const* kx,
@@ -1330,13 +1355,17 @@ cudaError_t indexed_subset_tc_classes(int mode, const RecordIndex& idx, const Ke
   int64_t max_items = 16 * int64_t(G);
   for (int c = 0; c < n_cls; ++c) max_items += ceil_div(kx[c]->n, own_rows) + L + 1;
   const size_t item_bytes = size_t(max_items) * sizeof(TcItem);
-  const size_t bytes = item_bytes + size_t(G + 1) * 8 + size_t(n_cls) * 8;
+  const size_t bytes = item_bytes + size_t(G + 1) * 8 + size_t(n_cls) * 8 +
+                       size_t(2 * L + 1) * 8 + 2 * 8 + 2 * size_t(kCostBuckets) * 4;
   uint8_t* blk = nullptr;
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&blk), bytes, s);
   if (e != cudaSuccess) return e;
   TcItem* d_items = reinterpret_cast<TcItem*>(blk);
   int64_t* d_cta = reinterpret_cast<int64_t*>(blk + item_bytes);
   unsigned long long* d_tests = reinterpret_cast<unsigned long long*>(d_cta + G + 1);
+  int64_t* d_goff = reinterpret_cast<int64_t*>(d_tests + n_cls);
+  int64_t* d_meta = d_goff + (2 * L + 1);
+  uint32_t* d_boff = reinterpret_cast<uint32_t*>(d_meta + 2);
   ItemBuild ib;
   ib.own_off[0] = kx[0]->off;
   ib.own_off[1] = kx[n_cls - 1]->off;
@@ -1350,8 +1379,13 @@ cudaError_t indexed_subset_tc_classes(int mode, const RecordIndex& idx, const Ke
   ib.cta_off = d_cta;
   ib.tests = d_tests;
   ib.status = status;
-  tc_items_kernel<<<1, kItemThreads, 0, s>>>(ib);
-  count_launches(1);
+  ib.goff = d_goff;
+  ib.meta = d_meta;
+  ib.boff = d_boff;
+  ib.bcnt = d_boff + kCostBuckets;
+  tc_items_plan_kernel<<<1, kItemThreads, 0, s>>>(ib);
+  tc_items_place_kernel<<<unsigned(ceil_div(max_items, 256)), 256, 0, s>>>(ib);
+  count_launches(2);
   e = cudaGetLastError();
   if (e == cudaSuccess) {
     const KeyedIndex& k0 = *kx[0];
