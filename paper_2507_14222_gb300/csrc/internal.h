@@ -291,7 +291,8 @@ cudaError_t indexed_subset(const IndexedArgs& a, cudaStream_t s);
 
 // The pattern side of the item index, built once and reusable: patterns
 // filed under their key item (the item with the smallest `freq`; group L
-// holds patterns with an item of freq 0).  Synchronizes the stream once.
+// holds patterns with an item of freq 0).  Synchronizes the stream once to
+// read the group offsets back, unless built without host offsets.
 struct KeyedIndex {
   int K = 0, KT = 0, L = 0;
   int64_t n = 0;

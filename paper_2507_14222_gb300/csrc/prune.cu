@@ -15,8 +15,10 @@
 // k(p)), and no pair outside a common group can have p inside r, so counts,
 // flags and score sums are the same as from the full product.
 //
-// Work items are (group, own tile, stream range) blocks; the host builds the
-// list from the group sizes and balances the stream ranges across the GPU.
+// Work items are (group, own tile, stream range) blocks.  For the integer
+// grouped kernel here the host builds the list from the group sizes (read
+// back) and balances the stream ranges across the GPU; the tensor-core form
+// builds its items on the device (subset_tc.cu).
 #include <algorithm>
 #include <vector>
 
