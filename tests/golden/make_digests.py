@@ -6,7 +6,10 @@ the oracle on the GPU host:
   * ig-nsl-148k-10/90 (14,800 training records; all 133,200 test records
     scored);
   * every one of the 64 batched problems (each fitted on its own, its test
-    records scored).
+    records scored);
+  * the served workload: 1M + 1M given patterns (a model built from them,
+    canonical order and Eq. 2 scores) and all 10^6 flows scored (about half
+    an hour on 8 cores; run with the argument "served").
 
 Per problem the digest covers, for class 0 (normal) then 1 (attack), the
 number of candidates |B^c| (Eq. 1) as a little-endian uint64, then the
@@ -62,6 +65,19 @@ def oracle_entry(w) -> dict:
             "oracle_s": round(time.time() - t0, 1)}
 
 
+def served_entry(sw) -> dict:
+    """A model from given patterns has no candidate stage: |B^c| = 0."""
+    t0 = time.time()
+    m = oracle.model_from_patterns({c: oracle.encode(sw.patterns[c], sw.cards) for c in (0, 1)},
+                                   sw.support)
+    A, N, lab = oracle.score(m, oracle.encode(sw.flow_codes, sw.cards))
+    return {"sha256": digest(m.n_candidates, m.patterns, m.support, m.score, A, N, lab),
+            "n_candidates": [int(m.n_candidates[0]), int(m.n_candidates[1])],
+            "n_patterns": [int(m.patterns[0].shape[0]), int(m.patterns[1].shape[0])],
+            "flows": int(sw.flow_codes.shape[0]),
+            "oracle_s": round(time.time() - t0, 1)}
+
+
 def main():
     out = {"about": "SHA-256 of the CPU oracle's output per workload; written by "
                     "tests/golden/make_digests.py (see its docstring for the byte layout)",
@@ -79,6 +95,10 @@ def main():
             out["workloads"][w.name] = oracle_entry(w)
             print(w.name, out["workloads"][w.name], flush=True)
             json.dump(out, open(OUT, "w"), indent=1)
+    if "served" in which:
+        sw = igdata.served()
+        out["workloads"][sw.name] = served_entry(sw)
+        print(sw.name, out["workloads"][sw.name], flush=True)
     json.dump(out, open(OUT, "w"), indent=1)
 
 

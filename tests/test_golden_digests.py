@@ -8,34 +8,17 @@ oracle alone, the digest of every batched problem with at most 1,500
 training records (about half of the 64) and checks it, together with the
 recorded sizes, against the stored file.
 """
-import importlib.util
-import json
-import os
-
 import pytest
 
 import igdata
-
-HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-
-
-def _make_digests():
-    spec = importlib.util.spec_from_file_location("make_digests",
-                                                  os.path.join(HERE, "make_digests.py"))
-    mod = importlib.util.module_from_spec(spec)
-    spec.loader.exec_module(mod)
-    return mod
-
-
-def _stored():
-    with open(os.path.join(HERE, "oracle_digests.json")) as f:
-        return json.load(f)["workloads"]
+from tests.golden_digests import stored as _stored, writer as _make_digests
 
 
 def test_every_workload_has_a_digest():
     stored = _stored()
     names = {igdata.batched_problem(i).name for i in range(igdata.BATCHED_PROBLEMS)}
     names.add(igdata.nsl148k().name)
+    names.add("ig-served-1000000x2-patterns-1000000-flows")   # igdata.served() at its defaults
     assert names <= set(stored)
     for entry in stored.values():
         assert len(entry["sha256"]) == 64 and int(entry["sha256"], 16) >= 0

@@ -15,6 +15,7 @@ import pytest
 import igdata
 import oracle
 from tests import brute
+from tests import golden_digests
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -360,15 +361,7 @@ def test_save_load_roundtrip(nsl15k, tmp_path):
 def _golden_digests():
     """The oracle's digests of the full-size workloads, and the digest
     function that wrote them (tests/golden/make_digests.py)."""
-    import importlib.util
-    import json
-    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-    spec = importlib.util.spec_from_file_location("make_digests",
-                                                  os.path.join(here, "make_digests.py"))
-    mod = importlib.util.module_from_spec(spec)
-    spec.loader.exec_module(mod)
-    with open(os.path.join(here, "oracle_digests.json")) as f:
-        return json.load(f)["workloads"], mod.digest
+    return golden_digests.stored(), golden_digests.writer().digest
 
 
 def _gpu_digest(digest, m, test_rows):

@@ -9,6 +9,7 @@ import pytest
 
 import igdata
 import oracle
+from tests import golden_digests
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -47,9 +48,10 @@ def test_model_from_patterns_matches_oracle(served):
 def test_served_full_size(served):
     # The served workload at its full size: 1M normal + 1M attack patterns,
     # 10^6 flows in 1,972 requests.  The one-shot ig_score of a seeded
-    # sample of flows equals the oracle's; every flow the server returns, in
-    # a burst of all requests at once, equals the one-shot ig_score of all
-    # flows.
+    # sample of flows equals the oracle's; the model and the one-shot
+    # ig_score of all flows equal the oracle's digest of the same workload;
+    # every flow the server returns, in a burst of all requests at once,
+    # equals the one-shot ig_score of all flows.
     sw = igdata.served()
     words = [ig.ig_encode(torch.from_numpy(sw.patterns[c].view(np.int16)).cuda(), sw.cards)
              for c in (0, 1)]
@@ -64,6 +66,14 @@ def test_served_full_size(served):
     assert int((oA > 0).sum()) > 0 and int((oN > 0).sum()) > 0
     flows = ig.ig_encode(sw.flow_codes, sw.cards)
     ref = ig.ig_score(model, flows)
+    want = golden_digests.stored()[sw.name]
+    info = model.info()
+    pats = {c: model.patterns(c) for c in (0, 1)}
+    got = golden_digests.writer().digest(
+        info["n_candidates"], {c: pats[c][0] for c in (0, 1)}, {c: pats[c][1] for c in (0, 1)},
+        {c: pats[c][2] for c in (0, 1)}, ref[0], ref[1], ref[2])
+    assert list(info["n_patterns"]) == want["n_patterns"]
+    assert got == want["sha256"], "served output differs from the oracle's"
     offs = np.concatenate([[0], np.cumsum(sw.request_sizes)])
     reqs = [flows[offs[i]:offs[i + 1]] for i in range(len(sw.request_sizes))]
     outs, (batches, n_flows) = _serve(model, reqs, 0.0, cap=65536, budget=1 << 30)
