@@ -116,6 +116,11 @@ def test_confusion_hand_example():
     assert m["accuracy"] == 3 / 5 and m["precision"] == 2 / 3
     assert m["recall"] == 2 / 3 and m["f1"] == 4 / 6
     assert math.isnan(m["auc"])
+    # fp != fn, so precision and recall differ: tp 1, fp 3, tn 1, fn 2
+    m = H.evaluate([1, 1, 1, 0, 0, 0, 0], [1, 0, 0, 1, 1, 1, 0])
+    assert (m["tp"], m["fp"], m["tn"], m["fn"]) == (1, 3, 1, 2)
+    assert m["accuracy"] == 2 / 7 and m["precision"] == 1 / 4
+    assert m["recall"] == 1 / 3 and m["f1"] == 2 / 7
     e = H.evaluate([0, 0], [0, 0], [1, 2], [0, 0])
     assert math.isnan(e["precision"]) and math.isnan(e["recall"]) and math.isnan(e["auc"])
 
