@@ -1,0 +1,52 @@
+"""bench.py --impl reference: the CPU oracle timed on the host's cores.
+
+It needs no GPU, so the CPU suite runs it as the benchmark does: one JSON line on
+rank 0 with the benchmark's metric, unit and workload, a cpu_baseline that
+describes the run, and an e2e with no copies; any other rank exits 0 without
+work or output.
+"""
+import importlib.util
+import json
+import os
+import subprocess
+import sys
+
+import igdata
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+_spec = importlib.util.spec_from_file_location("ig_bench", os.path.join(ROOT, "bench.py"))
+bench = importlib.util.module_from_spec(_spec)
+_spec.loader.exec_module(bench)
+
+
+def _run(extra_env=None, *args):
+    env = dict(os.environ, **(extra_env or {}))
+    p = subprocess.run([sys.executable, "bench.py", "--impl", "reference", *args],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return p.returncode, p.stdout, p.stderr
+
+
+def test_reference_arm_prints_one_line_on_the_default_workload():
+    rc, out, err = _run(None, "--steps", "3", "--warmup", "3")
+    assert rc == 0, err[-2000:]
+    lines = [l for l in out.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["higher_is_better"] is True and d["vs_baseline"] is None
+    assert (d["n_gpus"], d["steps"], d["warmup"]) == (1, 3, 3)
+    assert d["config"]["workload"] == igdata.nsl148k().name
+    assert d["value"] > 0 and d["ms_per_step"] > 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["unit"] == d["unit"]
+    assert cb["cores"] == (os.cpu_count() or 1) and cb["sample"] == d["config"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"],
+                        "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_do_no_work():
+    rc, out, err = _run({"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"},
+                        "--steps", "3", "--warmup", "3")
+    assert rc == 0, err[-2000:]
+    assert out.strip() == ""
