@@ -1542,19 +1542,31 @@ int run_lanes(const std::vector<int32_t>& order, int lanes, cudaStream_t s, cons
   int dev = 0;
   IG_CUDA(cudaGetDevice(&dev), what);
   cudaEvent_t ready = nullptr;
-  IG_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming), what);
-  IG_CUDA(cudaEventRecord(ready, s), what);
+  std::vector<cudaStream_t> ls(lanes, nullptr);
+  std::vector<cudaEvent_t> done(lanes, nullptr);
+  // Destroys what was created (a stream is released once its work is done).
+  auto release = [&] {
+    for (int l = 0; l < lanes; ++l) {
+      if (done[l]) cudaEventDestroy(done[l]);
+      if (ls[l]) cudaStreamDestroy(ls[l]);
+    }
+    if (ready) cudaEventDestroy(ready);
+  };
+  cudaError_t e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ready, s);
+  for (int l = 0; l < lanes && e == cudaSuccess; ++l) {
+    e = cudaStreamCreateWithFlags(&ls[l], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[l], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ls[l], ready, 0);
+  }
+  if (e != cudaSuccess) {
+    release();
+    return fail_cuda(e, what);
+  }
   std::atomic<int32_t> next{0};
   std::mutex err_mu;
   int first_rc = IG_OK;
   std::string first_msg;
-  std::vector<cudaStream_t> ls(lanes, nullptr);
-  std::vector<cudaEvent_t> done(lanes, nullptr);
-  for (int l = 0; l < lanes; ++l) {
-    IG_CUDA(cudaStreamCreateWithFlags(&ls[l], cudaStreamNonBlocking), what);
-    IG_CUDA(cudaEventCreateWithFlags(&done[l], cudaEventDisableTiming), what);
-    IG_CUDA(cudaStreamWaitEvent(ls[l], ready, 0), what);
-  }
   auto lane = [&](int l) {
     cudaSetDevice(dev);
     for (;;) {
@@ -1582,12 +1594,8 @@ int run_lanes(const std::vector<int32_t>& order, int lanes, cudaStream_t s, cons
     w->wait();
     release_worker(w);
   }
-  for (int l = 0; l < lanes; ++l) {
-    cudaStreamWaitEvent(s, done[l], 0);
-    cudaEventDestroy(done[l]);
-    cudaStreamDestroy(ls[l]);
-  }
-  cudaEventDestroy(ready);
+  for (int l = 0; l < lanes; ++l) cudaStreamWaitEvent(s, done[l], 0);
+  release();
   if (first_rc != IG_OK) g_last_error = first_msg;
   return first_rc;
 }
