@@ -935,9 +935,9 @@ int fit_impl(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
     }
     IG_CUDA(signal.ready(s), "ig_fit");
     bool other_ready = false;
-    unsigned long long* h_pinned = thread_pinned();
-    if (!h_pinned) return fail(IG_E_CUDA, "ig_fit: pinned host allocation failed");
-    TableCounters* h_counters = reinterpret_cast<TableCounters*>(h_pinned + 4);
+    unsigned long long* h_own = thread_pinned();  // this class thread's pinned words
+    if (!h_own) return fail(IG_E_CUDA, "ig_fit: pinned host allocation failed");
+    TableCounters* h_counters = reinterpret_cast<TableCounters*>(h_own + 4);
     m->n_train[c] = nc[c];
     m->n_pairs[c] = nc[c] * (nc[c] - 1) / 2;
     // Eq. 1: B^c, deduplicated on the device.
@@ -1053,7 +1053,7 @@ int fit_impl(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
                             cudaMemcpyDeviceToHost, s),
             "ig_fit");
     IG_CHECK(read_status(d_status.p, s, "ig_fit: coherence"));
-    h_pinned[2] = kept_h[rounds - 1];
+    h_own[2] = kept_h[rounds - 1];
     m->coh_tests[c] = m->coh_tests_tc[c] = m->coh_tests_pruned[c] = 0;
     for (int r = 0; r < rounds; ++r) {
       if (round_tests[r] == -2) {
@@ -1065,7 +1065,7 @@ int fit_impl(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
       m->coh_tests[c] += t;
       if (tc && win_lo[r] >= (pruned ? pruned_from : tc_from)) m->coh_tests_tc[c] += t;
     }
-    const int64_t P = int64_t(h_pinned[2]);
+    const int64_t P = int64_t(h_own[2]);
     m->n_pat[c] = P;
     covered.reset();
     // Canonical order of P^c (the other buffer serves as sort workspace).
