@@ -145,9 +145,15 @@ typedef struct {
 } ig_problem;
 
 /* Batched IG training: fits n_problems independent problems (each exactly
- * as ig_fit would, Section 3.1), of any sizes and word counts, concurrently
- * on up to `lanes` streams (0 = 8); the largest problems start first and
- * every lane pulls the next problem when it finishes one.  out[i] receives
+ * as ig_fit would, Section 3.1), of any sizes and word counts.  The
+ * candidate stage (Eq. 1) of every class of every problem runs first, in one
+ * launch of a persistent kernel whose blocks draw (problem, class, pair
+ * tile) work from a device-side queue (further launches only for tables
+ * that run out of room).  The remaining steps of each fit then run
+ * concurrently on up to `lanes` streams (0 = 8); the largest problems start
+ * first and every lane pulls the next problem when it finishes one.  The
+ * batch-level scheduling of Section 3.3 (batch size as a tunable parameter)
+ * applied across independent problems.  out[i] receives
  * problem i's model.  Work is ordered after what `stream` holds when the
  * call starts and before what is enqueued on it afterwards; the call returns
  * when all models are complete.  On an error every model is freed, out[] is

@@ -1327,7 +1327,7 @@ void* pinned_scratch(size_t bytes) {
 
 // The candidate stage (Eq. 1) of every problem of a batch at once: the
 // class split of every problem, one read-back of all class sizes, then the
-// pair tiles of every class of every problem in one launch per word count
+// pair tiles of every class of every problem, all word counts, in one launch
 // (a persistent grid drawing tiles from a device-side queue), one read-back
 // of all tables' counters, and replays of the tables that ran out of room
 // (grown and rehashed one by one, replayed together).  A problem that this
