@@ -50,3 +50,16 @@ def test_reference_arm_other_ranks_do_no_work():
                         "--steps", "3", "--warmup", "3")
     assert rc == 0, err[-2000:]
     assert out.strip() == ""
+
+
+def test_own_arm_without_a_gpu_fails_loudly():
+    # No CPU fallback: without a CUDA device the benchmark exits non-zero and
+    # prints no result line.
+    import pytest
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    p = subprocess.run([sys.executable, "bench.py", "--steps", "3", "--warmup", "3"], cwd=ROOT,
+                       capture_output=True, text=True, timeout=600)
+    assert p.returncode != 0
+    assert not [l for l in p.stdout.splitlines() if l.lstrip().startswith("{")]
