@@ -3,7 +3,8 @@
 It needs no GPU, so the CPU suite runs it as the benchmark does: one JSON line on
 rank 0 with the benchmark's metric, unit and workload, a cpu_baseline that
 describes the run, and an e2e with no copies; any other rank exits 0 without
-work or output.
+work or output.  The benchmark's own arm, on a host without a GPU, exits
+non-zero without a result line.
 """
 import importlib.util
 import json
