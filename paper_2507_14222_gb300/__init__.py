@@ -170,6 +170,37 @@ def _rows_shape(rows):
     return int(rows.shape[0]), int(rows.shape[1])
 
 
+# Element types a tensor may have where the library reads 8-byte words,
+# 2-byte codes, 1-byte labels and 4-byte supports (names missing from the
+# installed torch are skipped).
+_WORD_TYPES = ("int64", "uint64")
+_CODE_TYPES = ("int16", "uint16")
+_LABEL_TYPES = ("uint8", "int8", "bool")
+_SUPPORT_TYPES = ("int32", "uint32")
+
+
+def _torch_type_ok(x, names) -> bool:
+    import torch
+    return any(getattr(torch, name, None) == x.dtype for name in names)
+
+
+def _check_words(rows, what="rows"):
+    """[n, K] packed rows: the library reads n x K 8-byte words, so a tensor
+    of another element size is rejected before anything is launched."""
+    n, K = _rows_shape(rows)
+    if _is_torch(rows) and not _torch_type_ok(rows, _WORD_TYPES):
+        raise ValueError(f"{what} must hold 64-bit words (torch.int64 / numpy.uint64)")
+    return n, K
+
+
+def _check_vector(x, n: int, names, what: str):
+    """A [n] array the library reads n elements of."""
+    if x.ndim != 1 or int(x.shape[0]) != n:
+        raise ValueError(f"{what} must have shape [{n}], not {tuple(x.shape)}")
+    if _is_torch(x) and not _torch_type_ok(x, names):
+        raise ValueError(f"{what}: element type {x.dtype} is not one of {', '.join(names)}")
+
+
 def ig_encode(codes, cards, stream=None):
     """One-hot packing (Section 3.1, Eq. 5) of codes[n, F] with cards[F].
 
@@ -179,7 +210,13 @@ def ig_encode(codes, cards, stream=None):
     """
     lib = load()
     cards = np.ascontiguousarray(np.asarray(cards, dtype=np.uint16))
+    if codes.ndim != 2:
+        raise ValueError("codes must be [n, F]")
+    if _is_torch(codes) and not _torch_type_ok(codes, _CODE_TYPES):
+        raise ValueError("codes must hold 16-bit codes (torch.int16 / numpy.uint16)")
     n, F = int(codes.shape[0]), int(codes.shape[1])
+    if cards.ndim != 1 or int(cards.shape[0]) != F:
+        raise ValueError(f"cards must have shape [{F}]")
     K = (int(cards.astype(np.int64).sum()) + 63) // 64
     if _is_torch(codes):
         import torch
@@ -264,11 +301,12 @@ def ig_fit(rows, labels, r: float | None = None, subset_kernel: int = 0,
     labels: [n] uint8, 1 = attack, 0 = normal.
     """
     lib = load()
-    n, K = _rows_shape(rows)
+    n, K = _check_words(rows)
     if not _is_torch(rows):
         rows = np.ascontiguousarray(rows, dtype=np.uint64)
     if not _is_torch(labels):
         labels = np.ascontiguousarray(labels, dtype=np.uint8)
+    _check_vector(labels, n, _LABEL_TYPES, "labels")
     prm = make_params(r, subset_kernel, index_max_q, index_flip_factor)
     h = ctypes.c_void_p()
     _check(lib.ig_fit(_ptr(rows), _ptr(labels), n, K, ctypes.byref(prm),
@@ -296,13 +334,14 @@ def ig_fit_batched(problems, r: float | None = None, subset_kernel: int = 0,
     arr = (ig_problem * max(1, len(problems)))()
     any_torch = False
     for i, (rows, labels) in enumerate(problems):
-        n, K = _rows_shape(rows)
+        n, K = _check_words(rows, f"problem {i}: rows")
         if _is_torch(rows):
             any_torch = True
         else:
             rows = np.ascontiguousarray(rows, dtype=np.uint64)
         if not _is_torch(labels):
             labels = np.ascontiguousarray(labels, dtype=np.uint8)
+        _check_vector(labels, n, _LABEL_TYPES, f"problem {i}: labels")
         keep.append((rows, labels))
         pp = per_problem_params[i] if per_problem_params else None
         if pp is not None:
@@ -354,14 +393,8 @@ def ig_score_batched(jobs, lanes: int = 0, stream=None) -> list:
 def _check_score_rows(model: Model, rows):
     """Scoring reads m x K 8-byte words with K from the model: reject rows of
     another width or element size before anything is launched."""
-    m, K = _rows_shape(rows)
-    if _is_torch(rows):
-        import torch
-        ok = rows.dtype in (torch.int64, torch.uint64) if hasattr(torch, "uint64") \
-            else rows.dtype == torch.int64
-    else:
-        ok = np.asarray(rows).dtype.itemsize == 8
-    if not ok:
+    m, K = _check_words(rows)
+    if not _is_torch(rows) and np.asarray(rows).dtype.itemsize != 8:
         raise ValueError("rows must hold 64-bit words (torch.int64 / numpy.uint64)")
     mk = model.info()["K"]
     if K != mk:
@@ -422,16 +455,20 @@ def ig_model_from_patterns(words_normal, support_normal, words_attack, support_a
     lib = load()
     ws, fs = [], []
     any_torch = False
-    for w, f in ((words_normal, support_normal), (words_attack, support_attack)):
+    for c, (w, f) in enumerate(((words_normal, support_normal), (words_attack, support_attack))):
         if _is_torch(w):
             any_torch = True
         else:
             w = np.ascontiguousarray(w, dtype=np.uint64)
+        P, _ = _check_words(w, f"class {c}: words")
         if not _is_torch(f):
             f = np.ascontiguousarray(f, dtype=np.uint32)
+        _check_vector(f, P, _SUPPORT_TYPES, f"class {c}: support")
         ws.append(w)
         fs.append(f)
-    K = int(ws[0].shape[1]) if ws[0].ndim == 2 else int(ws[1].shape[1])
+    if int(ws[0].shape[1]) != int(ws[1].shape[1]):
+        raise ValueError("both classes' words must have the same K")
+    K = int(ws[0].shape[1])
     wp = (ctypes.c_void_p * 2)(*[_ptr(w).value for w in ws])
     fp = (ctypes.c_void_p * 2)(*[_ptr(f).value for f in fs])
     n = (ctypes.c_int64 * 2)(int(ws[0].shape[0]), int(ws[1].shape[0]))
