@@ -502,7 +502,7 @@ class Server:
 
     def submit(self, rows) -> int:
         rows = np.ascontiguousarray(rows, dtype=np.uint64)
-        m = rows.shape[0]
+        m, _ = _check_score_rows(self.model, rows)   # the server reads m x K words
         A = np.empty(m, np.int64)
         N = np.empty(m, np.int64)
         lab = np.empty(m, np.uint8)
