@@ -498,11 +498,14 @@ class Server:
         h = ctypes.c_void_p()
         _check(load().ig_server_create(model.handle, ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h
+        self._K = int(model.info()["K"])
         self._pending = {}
 
     def submit(self, rows) -> int:
         rows = np.ascontiguousarray(rows, dtype=np.uint64)
-        m, _ = _check_score_rows(self.model, rows)   # the server reads m x K words
+        if rows.ndim != 2 or int(rows.shape[1]) != self._K:   # the server reads m x K words
+            raise ValueError(f"rows must be [m, {self._K}] (the model's K), not {rows.shape}")
+        m = int(rows.shape[0])
         A = np.empty(m, np.int64)
         N = np.empty(m, np.int64)
         lab = np.empty(m, np.uint8)
