@@ -14,6 +14,7 @@ import re
 import shutil
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 import pytest
 
@@ -143,17 +144,33 @@ def test_control_copy_passes_every_pin(tmp_path, pin_file):
     assert rc == 0, out[-3000:]
 
 
-@pytest.mark.parametrize("name,fname,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_planted_mistake_fails_a_pin(tmp_path, name, fname, old, new):
-    dst = str(tmp_path)
+def _run_mutant(dst, fname, old, new):
+    """Plants one mistake in a fresh copy under dst, builds it and runs its pins."""
     _copy_tree(dst)
     path = os.path.join(dst, "oracle", fname)
     with open(path) as f:
         src = f.read()
-    assert src.count(old) == 1, f"{name}: the text to replace must occur exactly once"
+    if src.count(old) != 1:
+        return None, "the text to replace must occur exactly once"
     with open(path, "w") as f:
         f.write(src.replace(old, new))
     _build_oracle(dst)
-    rc, out = _run_pins(dst, PINS[fname])
+    return _run_pins(dst, PINS[fname])
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    """Every mutant's (return code, output), the copies built and pinned
+    concurrently (each is an independent scratch tree and process)."""
+    with ThreadPoolExecutor(max_workers=max(1, os.cpu_count() or 1)) as ex:
+        futs = {m[0]: ex.submit(_run_mutant, str(tmp_path_factory.mktemp(m[0])), *m[1:])
+                for m in MUTANTS}
+        return {name: f.result() for name, f in futs.items()}
+
+
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+def test_planted_mistake_fails_a_pin(outcomes, name):
+    rc, out = outcomes[name]
+    assert rc is not None, f"{name}: {out}"
     caught = re.findall(r"^FAILED (\S+)", out, re.M)
     assert rc == 1 and caught, f"{name} was not caught by any pin (rc {rc}):\n{out[-3000:]}"
