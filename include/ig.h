@@ -194,19 +194,26 @@ int ig_score_batched(const ig_score_job* jobs, int32_t n_jobs, int32_t lanes,
 int ig_model_from_patterns(int32_t K, const uint64_t* const* words, const uint32_t* const* support,
                            const int64_t* n_patterns, ig_model** out, ig_stream_t stream);
 
-/* Sizes and statistics of a fitted model. */
+/* Sizes and statistics of a fitted model (see ig_model_info_t): per class
+ * the training records, |B^c| (Eq. 1), |P^c| (Eq. 3) and the subset tests
+ * executed, plus Regulation 3's mu_N, sigma_N, r and threshold.  Host only;
+ * IG_E_INVAL if m or info is NULL. */
 int ig_model_info(const ig_model* m, ig_model_info_t* info);
 
-/* Device pointers to class `cls` (1 = attack P+, 0 = normal P-) of a model:
- * words uint64[n_patterns][K] in canonical order, support uint32[n_patterns],
- * score uint64[n_patterns].  Any output pointer may be NULL.  The arrays are
- * owned by the model. */
+/* Device pointers to class `cls` (1 = attack P+, 0 = normal P-) of a model,
+ * the dictionary of Section 3.1 (coherent patterns, Eq. 3) with the supports
+ * f_c and scores S_c of Eq. 2: words uint64[n_patterns][K] in canonical
+ * order, support uint32[n_patterns], score uint64[n_patterns].  Any output
+ * pointer may be NULL.  The arrays are owned by the model and live until
+ * ig_model_free.  IG_E_INVAL for a NULL model or cls not 0 or 1. */
 int ig_model_patterns(const ig_model* m, int32_t cls, const uint64_t** words,
                       const uint32_t** support, const uint64_t** score);
 
-/* Copies class `cls` of a model into caller arrays (device or host; any may
- * be NULL): words_out uint64[n_patterns][K], support_out uint32[n_patterns],
- * score_out uint64[n_patterns].  Returns after the copies have completed. */
+/* Copies class `cls` of a model (its patterns, Eq. 3, with f_c and S_c of
+ * Eq. 2) into caller arrays (device or host; any may be NULL): words_out
+ * uint64[n_patterns][K], support_out uint32[n_patterns], score_out
+ * uint64[n_patterns].  Returns after the copies have completed.  IG_E_INVAL
+ * for a NULL model or cls not 0 or 1; IG_E_CUDA if a copy fails. */
 int ig_model_copy_patterns(const ig_model* m, int32_t cls, uint64_t* words_out,
                            uint32_t* support_out, uint64_t* score_out,
                            ig_stream_t stream);
@@ -303,7 +310,8 @@ int ig_prof_reset(void);
 int ig_prof_read(double* ms, int64_t* launches);
 const char* ig_prof_stage_name(int32_t stage);
 
-/* Timeline of the stages recorded since the last reset (which also records
+/* Instrumentation (no counterpart in the paper).  Timeline of the stages
+ * recorded since the last reset (which also records
  * the reference point): for each of the first min(cap, *n_out) stage spans,
  * its stage id, the stream it ran on (an opaque id), and its begin and end
  * in milliseconds after the reset.  Synchronizes the recorded events.  Any
