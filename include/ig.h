@@ -267,26 +267,42 @@ typedef struct {
                                    quarter of the free memory at creation) */
 } ig_server_config;
 
-/* The model must outlive the server.  cfg may be NULL. */
+/* Continuous-batching scoring server: the inference of Section 3.3 (the
+ * evidence of Eq. 4 and the labels of Regulations 1-3, exactly as ig_score)
+ * served per flow as the abstract sets out.  Requests that arrive while
+ * others run are admitted into batches as slots and the memory budget allow;
+ * admitted batches run concurrently, one stream per slot, and every flow's
+ * result equals ig_score's.  The model must outlive the server.  cfg may be
+ * NULL.  IG_E_INVAL for a NULL model or out; IG_E_NOMEM if its device or
+ * pinned buffers cannot be allocated. */
 int ig_server_create(const ig_model* model, const ig_server_config* cfg, ig_server** out);
 /* Queues a request: rows uint64[m][K] on the host (read when the request is
  * batched), results written to the host arrays A_out, N_out (int64[m]) and
  * label_out (uint8[m]; any may be NULL) before the request completes.  The
- * arrays must stay valid until ig_server_wait returns for *ticket. */
+ * arrays must stay valid until ig_server_wait returns for *ticket.
+ * IG_E_INVAL for a NULL server, rows or ticket, m <= 0, or m above the
+ * batch cap. */
 int ig_server_submit(ig_server* sv, const uint64_t* rows, int64_t m, int64_t* A_out,
                      int64_t* N_out, uint8_t* label_out, uint64_t* ticket);
 /* Blocks until the request completes; *latency_ms (may be NULL) receives the
- * time from its submission to its completion.  Each ticket is waited once. */
+ * time from its submission to its completion.  Each ticket is waited once.
+ * Returns the request's own status (a scoring error is reported here), or
+ * IG_E_INVAL for a NULL server or an unknown ticket. */
 int ig_server_wait(ig_server* sv, uint64_t ticket, double* latency_ms);
-/* Batches run and flows scored so far. */
+/* Batches run and flows scored so far.  IG_E_INVAL for a NULL server. */
 int ig_server_stats(ig_server* sv, int64_t* batches, int64_t* flows);
 /* Stops the server after the batches in flight; requests still queued are
  * dropped (destroy only once every submitted request has been waited). */
 void ig_server_destroy(ig_server* sv);
 
-/* Model persistence: a flat little-endian file (magic, version, K, counts,
- * Regulation 3 statistics, then per class the canonical words, supports and
- * scores).  ig_model_load places the model on the current device. */
+/* Model persistence (no counterpart in the paper): a flat little-endian file
+ * (magic, version, K, counts, Regulation 3 statistics, then per class the
+ * canonical words, supports and scores of Eq. 2).  ig_model_load places the
+ * model on the current device.  Errors: IG_E_INVAL for NULL arguments;
+ * IG_E_IO for a file that cannot be opened or written, has another magic,
+ * version or K out of range, or whose pattern counts do not account for its
+ * size exactly (checked before anything is allocated); IG_E_CUDA for a
+ * failed device allocation or copy. */
 int ig_model_save(const ig_model* m, const char* path);
 int ig_model_load(const char* path, ig_model** out);
 void ig_model_free(ig_model* m);

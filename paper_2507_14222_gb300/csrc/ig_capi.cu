@@ -5,6 +5,7 @@
 // Every step of the computation runs in the kernels of encode.cu, dedup.cu,
 // subset.cu and sort.cu; this file only sizes buffers and launches them.
 #include <cuda_runtime.h>
+#include <sys/types.h>
 
 #include <algorithm>
 #include <atomic>
@@ -2054,6 +2055,24 @@ int ig_model_load(const char* path, ig_model** out) {
     fclose(f);
     model_release(m);
     return fail(IG_E_IO, "ig_model_load: %s is not an IG model file", path);
+  }
+  {
+    // The pattern counts must account for the rest of the file exactly
+    // (words, supports and scores of both classes) before anything is sized
+    // by them: a damaged header must not drive a huge allocation.
+    const off_t here = ftello(f);
+    bool sized = here >= 0 && fseeko(f, 0, SEEK_END) == 0;
+    const off_t end = sized ? ftello(f) : off_t(-1);
+    const int64_t per = 8 * int64_t(hdr[1]) + 4 + 8;
+    const int64_t left = int64_t(end) - int64_t(here);
+    sized = sized && end >= here && m->n_pat[0] <= left / per && m->n_pat[1] <= left / per &&
+            (m->n_pat[0] + m->n_pat[1]) * per == left && fseeko(f, here, SEEK_SET) == 0;
+    if (!sized) {
+      fclose(f);
+      model_release(m);
+      return fail(IG_E_IO, "ig_model_load: %s is truncated or its counts do not match its size",
+                  path);
+    }
   }
   m->K = int(hdr[1]);
   m->KT = igk::padded_words(m->K);
