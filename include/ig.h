@@ -28,7 +28,9 @@
  *    (pattern lists) belong to the library's ig_model and live until
  *    ig_model_free.
  *  * Every function returns IG_OK (0) or a negative status; the calling
- *    thread's last error message is then readable via ig_last_error().
+ *    thread's last error message is then readable via ig_last_error().  No
+ *    C++ exception leaves the library: a failed host allocation inside a
+ *    call is reported as IG_E_NOMEM, any other exception as IG_E_INTERNAL.
  *    There is no CPU fallback: without a usable GPU every compute call
  *    returns IG_E_CUDA.
  */
@@ -48,7 +50,7 @@ typedef struct CUstream_st* ig_stream_t;
 enum {
   IG_OK = 0,
   IG_E_INVAL = -1,     /* bad argument (size, K, label or code out of range) */
-  IG_E_NOMEM = -2,     /* device allocation failed */
+  IG_E_NOMEM = -2,     /* device or host allocation failed */
   IG_E_CUDA = -3,      /* CUDA runtime error (message has the CUDA text) */
   IG_E_TIMEOUT = -4,   /* a bounded device-side wait ran out */
   IG_E_OVERFLOW = -5,  /* a count exceeded the library's index range */

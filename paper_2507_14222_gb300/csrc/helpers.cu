@@ -110,155 +110,163 @@ constexpr int64_t kMaxEvalRows = int64_t(1) << 31;  // keeps 2U below 2^63
 extern "C" int ig_discretize(const double* fit_values, int64_t n_fit, const double* values,
                              int64_t n, int32_t F, const uint8_t* categorical, int32_t p,
                              uint16_t* codes_out, uint16_t* cards_out) {
-  if (n_fit < 0 || n < 0 || F <= 0 || p < 0 || p > 9 || !categorical || !cards_out ||
-      (n_fit > 0 && !fit_values) || (n > 0 && (!values || !codes_out)))
-    return fail(IG_E_INVAL, "ig_discretize: bad arguments");
-  double scale = 1.0;
-  for (int k = 0; k < p; ++k) scale *= 10.0;
-  std::vector<double> tok;
-  for (int32_t f = 0; f < F; ++f) {
-    Column col;
-    col.categorical = categorical[f] != 0;
-    col.scale = scale;
-    if (!col.categorical) {
-      // Population statistics over the column's present fit values, summed
-      // in row order.
-      double sum = 0.0;
-      int64_t cnt = 0;
-      for (int64_t i = 0; i < n_fit; ++i) {
-        const double x = fit_values[i * F + f];
-        if (std::isfinite(x)) {
-          sum += x;
-          ++cnt;
-        }
-      }
-      if (cnt > 0) {
-        col.mu = sum / double(cnt);
-        double ss = 0.0;
+  return igk::guarded("ig_discretize", [&]() -> int {
+    if (n_fit < 0 || n < 0 || F <= 0 || p < 0 || p > 9 || !categorical || !cards_out ||
+        (n_fit > 0 && !fit_values) || (n > 0 && (!values || !codes_out)))
+      return fail(IG_E_INVAL, "ig_discretize: bad arguments");
+    double scale = 1.0;
+    for (int k = 0; k < p; ++k) scale *= 10.0;
+    std::vector<double> tok;
+    for (int32_t f = 0; f < F; ++f) {
+      Column col;
+      col.categorical = categorical[f] != 0;
+      col.scale = scale;
+      if (!col.categorical) {
+        // Population statistics over the column's present fit values, summed
+        // in row order.
+        double sum = 0.0;
+        int64_t cnt = 0;
         for (int64_t i = 0; i < n_fit; ++i) {
           const double x = fit_values[i * F + f];
           if (std::isfinite(x)) {
-            const double d = x - col.mu;
-            ss += d * d;
+            sum += x;
+            ++cnt;
           }
         }
-        col.sigma = std::sqrt(ss / double(cnt));
+        if (cnt > 0) {
+          col.mu = sum / double(cnt);
+          double ss = 0.0;
+          for (int64_t i = 0; i < n_fit; ++i) {
+            const double x = fit_values[i * F + f];
+            if (std::isfinite(x)) {
+              const double d = x - col.mu;
+              ss += d * d;
+            }
+          }
+          col.sigma = std::sqrt(ss / double(cnt));
+        }
+      }
+      // Vocabulary: the distinct tokens of the fit rows, ascending.
+      tok.clear();
+      bool overflow = false;
+      for (int64_t i = 0; i < n_fit; ++i) {
+        double t;
+        if (col.token(fit_values[i * F + f], &t, &overflow)) tok.push_back(t);
+      }
+      if (overflow)
+        return fail(IG_E_OVERFLOW, "ig_discretize: column " + std::to_string(f) +
+                                       ": a z-score token exceeds 2^62");
+      std::sort(tok.begin(), tok.end());
+      tok.erase(std::unique(tok.begin(), tok.end()), tok.end());
+      if (tok.size() > 65535u)
+        return fail(IG_E_OVERFLOW, "ig_discretize: column " + std::to_string(f) +
+                                       " has more than 65535 distinct tokens");
+      cards_out[f] = uint16_t(tok.size());
+      for (int64_t i = 0; i < n; ++i) {
+        double t;
+        bool ovf = false;
+        uint16_t code = kMissing;
+        if (col.token(values[i * F + f], &t, &ovf)) {
+          auto it = std::lower_bound(tok.begin(), tok.end(), t);
+          if (it != tok.end() && *it == t) code = uint16_t(it - tok.begin());
+        }
+        codes_out[i * F + f] = code;  // missing, unseen or out-of-range tokens: no item
       }
     }
-    // Vocabulary: the distinct tokens of the fit rows, ascending.
-    tok.clear();
-    bool overflow = false;
-    for (int64_t i = 0; i < n_fit; ++i) {
-      double t;
-      if (col.token(fit_values[i * F + f], &t, &overflow)) tok.push_back(t);
-    }
-    if (overflow)
-      return fail(IG_E_OVERFLOW, "ig_discretize: column " + std::to_string(f) +
-                                     ": a z-score token exceeds 2^62");
-    std::sort(tok.begin(), tok.end());
-    tok.erase(std::unique(tok.begin(), tok.end()), tok.end());
-    if (tok.size() > 65535u)
-      return fail(IG_E_OVERFLOW, "ig_discretize: column " + std::to_string(f) +
-                                     " has more than 65535 distinct tokens");
-    cards_out[f] = uint16_t(tok.size());
-    for (int64_t i = 0; i < n; ++i) {
-      double t;
-      bool ovf = false;
-      uint16_t code = kMissing;
-      if (col.token(values[i * F + f], &t, &ovf)) {
-        auto it = std::lower_bound(tok.begin(), tok.end(), t);
-        if (it != tok.end() && *it == t) code = uint16_t(it - tok.begin());
-      }
-      codes_out[i * F + f] = code;  // missing, unseen or out-of-range tokens: no item
-    }
-  }
-  return IG_OK;
+    return IG_OK;
+  });
 }
 
 extern "C" int ig_filter_contradictions(const uint64_t* rows, const uint8_t* labels, int64_t n,
                                         int32_t K, int32_t mode, uint8_t* keep_out,
                                         int64_t* n_kept_out) {
-  if (n < 0 || K < 1 || K > IG_MAX_WORDS || (mode != 0 && mode != 1) ||
-      (n > 0 && (!rows || !labels || !keep_out)))
-    return fail(IG_E_INVAL, "ig_filter_contradictions: bad arguments");
-  if (!labels_ok(labels, n)) return fail(IG_E_INVAL, "ig_filter_contradictions: label > 1");
-  // Group equal itemsets: sort record indices by their words, ties by index,
-  // so that each group lists its records in record order.
-  std::vector<int64_t> order(static_cast<size_t>(n));
-  std::iota(order.begin(), order.end(), int64_t(0));
-  auto less = [&](int64_t a, int64_t b) {
-    const uint64_t* ra = rows + a * K;
-    const uint64_t* rb = rows + b * K;
-    for (int w = 0; w < K; ++w)
-      if (ra[w] != rb[w]) return ra[w] < rb[w];
-    return a < b;
-  };
-  std::sort(order.begin(), order.end(), less);
-  auto same = [&](int64_t a, int64_t b) {
-    return std::equal(rows + a * K, rows + a * K + K, rows + b * K);
-  };
-  int64_t kept = 0;
-  for (int64_t g0 = 0; g0 < n;) {
-    int64_t g1 = g0 + 1;
-    while (g1 < n && same(order[g0], order[g1])) ++g1;
-    int64_t n_att = 0, n_nor = 0;
-    for (int64_t k = g0; k < g1; ++k) (labels[order[k]] ? n_att : n_nor)++;
-    int64_t drop_att = 0, drop_nor = 0;
-    if (mode == 0) {
-      drop_att = drop_nor = std::min(n_att, n_nor);
-    } else if (n_att > 0 && n_nor > 0) {
-      drop_att = n_att;
-      drop_nor = n_nor;
-    }
-    for (int64_t k = g0; k < g1; ++k) {
-      const int64_t i = order[k];
-      int64_t& left = labels[i] ? drop_att : drop_nor;
-      if (left > 0) {
-        --left;
-        keep_out[i] = 0;
-      } else {
-        keep_out[i] = 1;
-        ++kept;
+  return igk::guarded("ig_filter_contradictions", [&]() -> int {
+    if (n < 0 || K < 1 || K > IG_MAX_WORDS || (mode != 0 && mode != 1) ||
+        (n > 0 && (!rows || !labels || !keep_out)))
+      return fail(IG_E_INVAL, "ig_filter_contradictions: bad arguments");
+    if (!labels_ok(labels, n)) return fail(IG_E_INVAL, "ig_filter_contradictions: label > 1");
+    // Group equal itemsets: sort record indices by their words, ties by index,
+    // so that each group lists its records in record order.
+    std::vector<int64_t> order(static_cast<size_t>(n));
+    std::iota(order.begin(), order.end(), int64_t(0));
+    auto less = [&](int64_t a, int64_t b) {
+      const uint64_t* ra = rows + a * K;
+      const uint64_t* rb = rows + b * K;
+      for (int w = 0; w < K; ++w)
+        if (ra[w] != rb[w]) return ra[w] < rb[w];
+      return a < b;
+    };
+    std::sort(order.begin(), order.end(), less);
+    auto same = [&](int64_t a, int64_t b) {
+      return std::equal(rows + a * K, rows + a * K + K, rows + b * K);
+    };
+    int64_t kept = 0;
+    for (int64_t g0 = 0; g0 < n;) {
+      int64_t g1 = g0 + 1;
+      while (g1 < n && same(order[g0], order[g1])) ++g1;
+      int64_t n_att = 0, n_nor = 0;
+      for (int64_t k = g0; k < g1; ++k) (labels[order[k]] ? n_att : n_nor)++;
+      int64_t drop_att = 0, drop_nor = 0;
+      if (mode == 0) {
+        drop_att = drop_nor = std::min(n_att, n_nor);
+      } else if (n_att > 0 && n_nor > 0) {
+        drop_att = n_att;
+        drop_nor = n_nor;
       }
+      for (int64_t k = g0; k < g1; ++k) {
+        const int64_t i = order[k];
+        int64_t& left = labels[i] ? drop_att : drop_nor;
+        if (left > 0) {
+          --left;
+          keep_out[i] = 0;
+        } else {
+          keep_out[i] = 1;
+          ++kept;
+        }
+      }
+      g0 = g1;
     }
-    g0 = g1;
-  }
-  if (n_kept_out) *n_kept_out = kept;
-  return IG_OK;
+    if (n_kept_out) *n_kept_out = kept;
+    return IG_OK;
+  });
 }
 
 extern "C" int ig_evaluate(const uint8_t* y_true, const uint8_t* y_pred, const int64_t* A,
                            const int64_t* N, int64_t m, ig_metrics_t* out) {
-  if (m < 0 || !out || (m > 0 && (!y_true || !y_pred)) || ((A == nullptr) != (N == nullptr)))
-    return fail(IG_E_INVAL, "ig_evaluate: bad arguments");
-  if (m > kMaxEvalRows) return fail(IG_E_OVERFLOW, "ig_evaluate: more than 2^31 records");
-  if (!labels_ok(y_true, m) || !labels_ok(y_pred, m))
-    return fail(IG_E_INVAL, "ig_evaluate: label > 1");
-  fill_counts(y_true, y_pred, m, out);
-  out->auc = (A && m > 0) ? auc_of(y_true, A, N, m) : std::nan("");
-  return IG_OK;
+  return igk::guarded("ig_evaluate", [&]() -> int {
+    if (m < 0 || !out || (m > 0 && (!y_true || !y_pred)) || ((A == nullptr) != (N == nullptr)))
+      return fail(IG_E_INVAL, "ig_evaluate: bad arguments");
+    if (m > kMaxEvalRows) return fail(IG_E_OVERFLOW, "ig_evaluate: more than 2^31 records");
+    if (!labels_ok(y_true, m) || !labels_ok(y_pred, m))
+      return fail(IG_E_INVAL, "ig_evaluate: label > 1");
+    fill_counts(y_true, y_pred, m, out);
+    out->auc = (A && m > 0) ? auc_of(y_true, A, N, m) : std::nan("");
+    return IG_OK;
+  });
 }
 
 extern "C" int ig_reg3_sweep(const int64_t* A, const int64_t* N, const uint8_t* y_true,
                              int64_t m, double mu, double sigma, const double* r, int32_t n_r,
                              ig_metrics_t* out) {
-  if (m < 0 || n_r < 0 || (n_r > 0 && (!r || !out)) || (m > 0 && (!A || !N || !y_true)))
-    return fail(IG_E_INVAL, "ig_reg3_sweep: bad arguments");
-  if (m > kMaxEvalRows) return fail(IG_E_OVERFLOW, "ig_reg3_sweep: more than 2^31 records");
-  if (!labels_ok(y_true, m)) return fail(IG_E_INVAL, "ig_reg3_sweep: label > 1");
-  const double auc = m > 0 ? auc_of(y_true, A, N, m) : std::nan("");
-  std::vector<uint8_t> pred(static_cast<size_t>(m));
-  for (int32_t k = 0; k < n_r; ++k) {
-    const double scaled = r[k] * sigma;
-    const double thr = mu - scaled;
-    for (int64_t i = 0; i < m; ++i) {
-      const bool r1 = A[i] >= N[i];
-      const bool r2 = A[i] == 0 && N[i] == 0;
-      const bool r3 = double(N[i]) < thr;
-      pred[i] = uint8_t(r1 || r2 || r3);
+  return igk::guarded("ig_reg3_sweep", [&]() -> int {
+    if (m < 0 || n_r < 0 || (n_r > 0 && (!r || !out)) || (m > 0 && (!A || !N || !y_true)))
+      return fail(IG_E_INVAL, "ig_reg3_sweep: bad arguments");
+    if (m > kMaxEvalRows) return fail(IG_E_OVERFLOW, "ig_reg3_sweep: more than 2^31 records");
+    if (!labels_ok(y_true, m)) return fail(IG_E_INVAL, "ig_reg3_sweep: label > 1");
+    const double auc = m > 0 ? auc_of(y_true, A, N, m) : std::nan("");
+    std::vector<uint8_t> pred(static_cast<size_t>(m));
+    for (int32_t k = 0; k < n_r; ++k) {
+      const double scaled = r[k] * sigma;
+      const double thr = mu - scaled;
+      for (int64_t i = 0; i < m; ++i) {
+        const bool r1 = A[i] >= N[i];
+        const bool r2 = A[i] == 0 && N[i] == 0;
+        const bool r3 = double(N[i]) < thr;
+        pred[i] = uint8_t(r1 || r2 || r3);
+      }
+      fill_counts(y_true, pred.data(), m, out + k);
+      out[k].auc = auc;
     }
-    fill_counts(y_true, pred.data(), m, out + k);
-    out[k].auc = auc;
-  }
-  return IG_OK;
+    return IG_OK;
+  });
 }

@@ -531,6 +531,16 @@ void igk::model_view(const ig_model* m, igk::ModelView* v) {
 
 int igk::report_error(int code, const char* msg) { return fail(code, "%s", msg); }
 
+int igk::report_exception(const char* where, bool out_of_memory) noexcept {
+  const int code = out_of_memory ? IG_E_NOMEM : IG_E_INTERNAL;
+  try {
+    return fail(code, "%s: %s", where,
+                out_of_memory ? "host memory allocation failed" : "unexpected host exception");
+  } catch (...) {
+    return code;
+  }
+}
+
 namespace {
 
 // The distinct rows of X[0, n) (stride KT), in any order, into Xu, their
@@ -773,39 +783,41 @@ const char* ig_last_error(void) { return g_last_error.c_str(); }
 
 int ig_encode(const uint16_t* codes, int64_t n, int32_t F, const uint16_t* cards,
               uint64_t* words_out, int32_t K, ig_stream_t stream) {
-  igk::DeviceRestore restore_device;  // the caller's device, put back on return
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (n < 0 || F <= 0 || !cards || (n > 0 && (!codes || !words_out)))
-    return fail(IG_E_INVAL, "ig_encode: bad arguments");
-  std::vector<uint32_t> offsets(F + 1, 0);
-  for (int f = 0; f < F; ++f) {
-    if (cards[f] == 0) return fail(IG_E_INVAL, "ig_encode: feature %d has cardinality 0", f);
-    offsets[f + 1] = offsets[f] + cards[f];
-  }
-  const int64_t L = offsets[F];
-  if (K != int32_t((L + 63) / 64))
-    return fail(IG_E_INVAL, "ig_encode: K = %d but ceil(L/64) = %lld", K, (long long)((L + 63) / 64));
-  if (K < 1 || K > IG_MAX_WORDS) return fail(IG_E_INVAL, "ig_encode: K = %d out of range", K);
-  if (n == 0) return IG_OK;
-  InputView<uint16_t> in;
-  IG_CHECK(in.bind(codes, size_t(n) * F, s, "ig_encode: codes"));
-  OutputView<uint64_t> out;
-  IG_CHECK(out.bind(words_out, size_t(n) * K, s, "ig_encode: output"));
-  DevBuf<uint32_t> d_off;
-  DevBuf<int> d_status;
-  IG_CUDA(d_off.alloc(F + 1, s), "ig_encode");
-  IG_CUDA(d_status.alloc(1, s), "ig_encode");
-  IG_CUDA(cudaMemcpyAsync(d_off.p, offsets.data(), sizeof(uint32_t) * (F + 1),
-                          cudaMemcpyHostToDevice, s),
-          "ig_encode");
-  IG_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), s), "ig_encode");
-  {
-    ProfScope ps(S_ENCODE, s);
-    IG_CUDA(igk::launch_encode(in.d, n, F, d_off.p, nullptr, out.d, K, d_status.p, s),
-            "ig_encode: kernel");
-  }
-  IG_CHECK(out.finish(s, "ig_encode: copy back"));
-  return read_status(d_status.p, s, "ig_encode");
+  return igk::guarded("ig_encode", [&]() -> int {
+    igk::DeviceRestore restore_device;  // the caller's device, put back on return
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (n < 0 || F <= 0 || !cards || (n > 0 && (!codes || !words_out)))
+      return fail(IG_E_INVAL, "ig_encode: bad arguments");
+    std::vector<uint32_t> offsets(F + 1, 0);
+    for (int f = 0; f < F; ++f) {
+      if (cards[f] == 0) return fail(IG_E_INVAL, "ig_encode: feature %d has cardinality 0", f);
+      offsets[f + 1] = offsets[f] + cards[f];
+    }
+    const int64_t L = offsets[F];
+    if (K != int32_t((L + 63) / 64))
+      return fail(IG_E_INVAL, "ig_encode: K = %d but ceil(L/64) = %lld", K, (long long)((L + 63) / 64));
+    if (K < 1 || K > IG_MAX_WORDS) return fail(IG_E_INVAL, "ig_encode: K = %d out of range", K);
+    if (n == 0) return IG_OK;
+    InputView<uint16_t> in;
+    IG_CHECK(in.bind(codes, size_t(n) * F, s, "ig_encode: codes"));
+    OutputView<uint64_t> out;
+    IG_CHECK(out.bind(words_out, size_t(n) * K, s, "ig_encode: output"));
+    DevBuf<uint32_t> d_off;
+    DevBuf<int> d_status;
+    IG_CUDA(d_off.alloc(F + 1, s), "ig_encode");
+    IG_CUDA(d_status.alloc(1, s), "ig_encode");
+    IG_CUDA(cudaMemcpyAsync(d_off.p, offsets.data(), sizeof(uint32_t) * (F + 1),
+                            cudaMemcpyHostToDevice, s),
+            "ig_encode");
+    IG_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), s), "ig_encode");
+    {
+      ProfScope ps(S_ENCODE, s);
+      IG_CUDA(igk::launch_encode(in.d, n, F, d_off.p, nullptr, out.d, K, d_status.p, s),
+              "ig_encode: kernel");
+    }
+    IG_CHECK(out.finish(s, "ig_encode: copy back"));
+    return read_status(d_status.p, s, "ig_encode");
+  });
 }
 
 }  // extern "C"
@@ -1214,11 +1226,19 @@ int fit_impl(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
       Worker* w = acquire_worker();
       w->run([&] {
         cudaSetDevice(dev);
-        rc[1] = fit_class(1, cs[1]);
-        if (rc[1] != IG_OK) msg[1] = g_last_error;
+        rc[1] = igk::guarded("ig_fit", [&]() -> int {
+          const int r = fit_class(1, cs[1]);
+          if (r != IG_OK) msg[1] = g_last_error;
+          return r;
+        });
       });
-      rc[0] = fit_class(0, cs[0]);
-      if (rc[0] != IG_OK) msg[0] = g_last_error;
+      // Guarded on this thread too: nothing may unwind this frame while the
+      // helper thread still uses it.
+      rc[0] = igk::guarded("ig_fit", [&]() -> int {
+        const int r = fit_class(0, cs[0]);
+        if (r != IG_OK) msg[0] = g_last_error;
+        return r;
+      });
       w->wait();
       release_worker(w);
     }
@@ -1573,12 +1593,15 @@ int run_lanes(const std::vector<int32_t>& order, int lanes, cudaStream_t s, cons
     for (;;) {
       const int32_t k = next.fetch_add(1);
       if (k >= n) break;
-      const int rc = fn(order[k], ls[l]);
+      const int rc = igk::guarded(what, [&]() -> int { return fn(order[k], ls[l]); });
       if (rc != IG_OK) {
         std::lock_guard<std::mutex> lk(err_mu);
         if (first_rc == IG_OK) {
           first_rc = rc;
-          first_msg = std::string(what) + " " + std::to_string(order[k]) + ": " + g_last_error;
+          try {
+            first_msg = std::string(what) + " " + std::to_string(order[k]) + ": " + g_last_error;
+          } catch (...) {
+          }
         }
       }
     }
@@ -1607,151 +1630,159 @@ extern "C" {
 
 int ig_fit(const uint64_t* rows, const uint8_t* labels, int64_t n, int32_t K,
            const ig_params* params, ig_model** out, ig_stream_t stream) {
-  igk::DeviceRestore restore_device;  // the caller's device, put back on return
-  return fit_impl(rows, labels, n, K, params, out, reinterpret_cast<cudaStream_t>(stream),
-                  nullptr);
+  return igk::guarded("ig_fit", [&]() -> int {
+    igk::DeviceRestore restore_device;  // the caller's device, put back on return
+    return fit_impl(rows, labels, n, K, params, out, reinterpret_cast<cudaStream_t>(stream),
+                    nullptr);
+  });
 }
 
 int ig_fit_batched(const ig_problem* problems, int32_t n_problems, const ig_params* params,
                    int32_t lanes, ig_model** out, ig_stream_t stream) {
-  igk::DeviceRestore restore_device;  // the caller's device, put back on return
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (n_problems < 0 || (n_problems > 0 && (!problems || !out)))
-    return fail(IG_E_INVAL, "ig_fit_batched: bad arguments");
-  for (int32_t i = 0; i < n_problems; ++i) out[i] = nullptr;
-  if (n_problems == 0) return IG_OK;
-  // Largest problems first (pairs grow as n^2), each lane pulling the next.
-  std::vector<int32_t> order(n_problems);
-  for (int32_t i = 0; i < n_problems; ++i) order[i] = i;
-  std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-    return problems[a].n > problems[b].n || (problems[a].n == problems[b].n && a < b);
-  });
-  std::vector<FitPrep> prep(n_problems);
-  IG_CHECK(batched_candidates(problems, n_problems, params, prep, s));
-  const int rc = run_lanes(order, lanes, s, "problem", [&](int32_t k, cudaStream_t ls) {
-    const ig_problem& pr = problems[k];
-    return fit_impl(pr.rows, pr.labels, pr.n, pr.K, pr.params ? pr.params : params, &out[k], ls,
-                    prep[k].ready ? &prep[k] : nullptr);
-  });
-  if (rc != IG_OK) {
-    for (int32_t i = 0; i < n_problems; ++i) {
-      ig_model_free(out[i]);
-      out[i] = nullptr;
+  return igk::guarded("ig_fit_batched", [&]() -> int {
+    igk::DeviceRestore restore_device;  // the caller's device, put back on return
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (n_problems < 0 || (n_problems > 0 && (!problems || !out)))
+      return fail(IG_E_INVAL, "ig_fit_batched: bad arguments");
+    for (int32_t i = 0; i < n_problems; ++i) out[i] = nullptr;
+    if (n_problems == 0) return IG_OK;
+    // Largest problems first (pairs grow as n^2), each lane pulling the next.
+    std::vector<int32_t> order(n_problems);
+    for (int32_t i = 0; i < n_problems; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+      return problems[a].n > problems[b].n || (problems[a].n == problems[b].n && a < b);
+    });
+    std::vector<FitPrep> prep(n_problems);
+    IG_CHECK(batched_candidates(problems, n_problems, params, prep, s));
+    const int rc = run_lanes(order, lanes, s, "problem", [&](int32_t k, cudaStream_t ls) {
+      const ig_problem& pr = problems[k];
+      return fit_impl(pr.rows, pr.labels, pr.n, pr.K, pr.params ? pr.params : params, &out[k], ls,
+                      prep[k].ready ? &prep[k] : nullptr);
+    });
+    if (rc != IG_OK) {
+      for (int32_t i = 0; i < n_problems; ++i) {
+        ig_model_free(out[i]);
+        out[i] = nullptr;
+      }
     }
-  }
-  return rc;
+    return rc;
+  });
 }
 
 int ig_score_batched(const ig_score_job* jobs, int32_t n_jobs, int32_t lanes,
                      ig_stream_t stream) {
-  igk::DeviceRestore restore_device;  // the caller's device, put back on return
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(IG_E_INVAL, "ig_score_batched: bad arguments");
-  // Largest batches first, each lane pulling the next.
-  std::vector<int32_t> order(n_jobs);
-  for (int32_t i = 0; i < n_jobs; ++i) order[i] = i;
-  std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-    return jobs[a].m > jobs[b].m || (jobs[a].m == jobs[b].m && a < b);
-  });
-  return run_lanes(order, lanes, s, "job", [&](int32_t k, cudaStream_t ls) {
-    const ig_score_job& j = jobs[k];
-    return ig_score(j.model, j.rows, j.m, j.A_out, j.N_out, j.label_out,
-                    reinterpret_cast<ig_stream_t>(ls));
+  return igk::guarded("ig_score_batched", [&]() -> int {
+    igk::DeviceRestore restore_device;  // the caller's device, put back on return
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(IG_E_INVAL, "ig_score_batched: bad arguments");
+    // Largest batches first, each lane pulling the next.
+    std::vector<int32_t> order(n_jobs);
+    for (int32_t i = 0; i < n_jobs; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+      return jobs[a].m > jobs[b].m || (jobs[a].m == jobs[b].m && a < b);
+    });
+    return run_lanes(order, lanes, s, "job", [&](int32_t k, cudaStream_t ls) {
+      const ig_score_job& j = jobs[k];
+      return ig_score(j.model, j.rows, j.m, j.A_out, j.N_out, j.label_out,
+                      reinterpret_cast<ig_stream_t>(ls));
+    });
   });
 }
 
 int ig_model_from_patterns(int32_t K, const uint64_t* const* words, const uint32_t* const* support,
                            const int64_t* n_patterns, ig_model** out, ig_stream_t stream) {
-  igk::DeviceRestore restore_device;  // the caller's device, put back on return
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (!out || !words || !support || !n_patterns)
-    return fail(IG_E_INVAL, "ig_model_from_patterns: NULL argument");
-  *out = nullptr;
-  if (K < 1 || K > IG_MAX_WORDS)
-    return fail(IG_E_INVAL, "ig_model_from_patterns: K = %d out of range", K);
-  const int KT = igk::padded_words(K);
-  ig_model* m = new ig_model;
-  struct ModelGuard {
-    ig_model* m;
-    ~ModelGuard() { model_release(m); }
-  } guard{m};
-  m->K = K;
-  m->KT = KT;
-  DevBuf<int> d_status;
-  IG_CUDA(d_status.alloc(1, s), "ig_model_from_patterns");
-  IG_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), s), "ig_model_from_patterns");
-  for (int c = 0; c < 2; ++c) {
-    const int64_t P = n_patterns[c];
-    if (P < 0 || (P > 0 && (!words[c] || !support[c])))
-      return fail(IG_E_INVAL, "ig_model_from_patterns: bad class %d arrays", c);
-    if (P > int64_t(0xffffffffll)) return fail(IG_E_OVERFLOW, "ig_model_from_patterns: too many");
-    m->n_pat[c] = P;
-    const size_t npad = size_t(std::max<int64_t>(1, igk::pad_rows(P)));
-    InputView<uint64_t> in_w;
-    InputView<uint32_t> in_f;
-    IG_CHECK(in_w.bind(words[c], size_t(P) * K, s, "ig_model_from_patterns: words"));
-    IG_CHECK(in_f.bind(support[c], size_t(P), s, "ig_model_from_patterns: supports"));
-    DevBuf<uint64_t> raw, work;
-    IG_CUDA(raw.alloc(npad * KT, s), "ig_model_from_patterns");
-    IG_CUDA(work.alloc(npad * KT, s), "ig_model_from_patterns");
-    IG_CUDA(cudaMemsetAsync(raw.p, 0, npad * KT * 8, s), "ig_model_from_patterns");
-    if (P)
-      IG_CUDA(cudaMemcpy2DAsync(raw.p, KT * 8, in_w.d, K * 8, K * 8, P, cudaMemcpyDeviceToDevice, s),
-              "ig_model_from_patterns");
-    IG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&m->words_kt[c]), npad * KT * 8, s),
-            "ig_model_from_patterns");
-    IG_CUDA(cudaMemsetAsync(m->words_kt[c], 0, npad * KT * 8, s), "ig_model_from_patterns");
-    IG_CUDA(cudaMemcpyAsync(work.p, raw.p, npad * KT * 8, cudaMemcpyDeviceToDevice, s),
-            "ig_model_from_patterns");
-    {
-      ProfScope ps(S_SORT, s);
-      IG_CUDA(igk::canonical_sort(work.p, P, KT, m->words_kt[c], work.p, s),
-              "ig_model_from_patterns: sort");
-    }
-    IG_CUDA(igk::launch_check_strict(m->words_kt[c], P, KT, d_status.p, s),
-            "ig_model_from_patterns");
-    IG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&m->support[c]),
-                            sizeof(uint32_t) * std::max<int64_t>(1, P), s),
-            "ig_model_from_patterns");
-    IG_CUDA(igk::launch_place_payload(m->words_kt[c], P, KT, raw.p, in_f.d, m->support[c],
-                                      d_status.p, s),
-            "ig_model_from_patterns");
-    IG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&m->score[c]), sizeof(uint64_t) * npad, s),
-            "ig_model_from_patterns");
-    IG_CUDA(cudaMemsetAsync(m->score[c], 0, sizeof(uint64_t) * npad, s), "ig_model_from_patterns");
-    DevBuf<unsigned long long> d_smax;
-    IG_CUDA(d_smax.alloc(1, s), "ig_model_from_patterns");
-    IG_CUDA(cudaMemsetAsync(d_smax.p, 0, sizeof(unsigned long long), s), "ig_model_from_patterns");
-    IG_CUDA(igk::launch_pattern_score(m->words_kt[c], P, KT, m->support[c], m->score[c], s,
-                                      d_smax.p),
-            "ig_model_from_patterns: score");
-    unsigned long long smax = 0;
-    IG_CUDA(cudaMemcpyAsync(&smax, d_smax.p, sizeof(smax), cudaMemcpyDeviceToHost, s),
-            "ig_model_from_patterns");
-    if (K == KT) {
-      m->words[c] = m->words_kt[c];
-    } else {
-      IG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&m->words[c]),
-                              sizeof(uint64_t) * std::max<int64_t>(1, P) * K, s),
-              "ig_model_from_patterns");
+  return igk::guarded("ig_model_from_patterns", [&]() -> int {
+    igk::DeviceRestore restore_device;  // the caller's device, put back on return
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!out || !words || !support || !n_patterns)
+      return fail(IG_E_INVAL, "ig_model_from_patterns: NULL argument");
+    *out = nullptr;
+    if (K < 1 || K > IG_MAX_WORDS)
+      return fail(IG_E_INVAL, "ig_model_from_patterns: K = %d out of range", K);
+    const int KT = igk::padded_words(K);
+    ig_model* m = new ig_model;
+    struct ModelGuard {
+      ig_model* m;
+      ~ModelGuard() { model_release(m); }
+    } guard{m};
+    m->K = K;
+    m->KT = KT;
+    DevBuf<int> d_status;
+    IG_CUDA(d_status.alloc(1, s), "ig_model_from_patterns");
+    IG_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), s), "ig_model_from_patterns");
+    for (int c = 0; c < 2; ++c) {
+      const int64_t P = n_patterns[c];
+      if (P < 0 || (P > 0 && (!words[c] || !support[c])))
+        return fail(IG_E_INVAL, "ig_model_from_patterns: bad class %d arrays", c);
+      if (P > int64_t(0xffffffffll)) return fail(IG_E_OVERFLOW, "ig_model_from_patterns: too many");
+      m->n_pat[c] = P;
+      const size_t npad = size_t(std::max<int64_t>(1, igk::pad_rows(P)));
+      InputView<uint64_t> in_w;
+      InputView<uint32_t> in_f;
+      IG_CHECK(in_w.bind(words[c], size_t(P) * K, s, "ig_model_from_patterns: words"));
+      IG_CHECK(in_f.bind(support[c], size_t(P), s, "ig_model_from_patterns: supports"));
+      DevBuf<uint64_t> raw, work;
+      IG_CUDA(raw.alloc(npad * KT, s), "ig_model_from_patterns");
+      IG_CUDA(work.alloc(npad * KT, s), "ig_model_from_patterns");
+      IG_CUDA(cudaMemsetAsync(raw.p, 0, npad * KT * 8, s), "ig_model_from_patterns");
       if (P)
-        IG_CUDA(cudaMemcpy2DAsync(m->words[c], K * 8, m->words_kt[c], KT * 8, K * 8, P,
-                                  cudaMemcpyDeviceToDevice, s),
+        IG_CUDA(cudaMemcpy2DAsync(raw.p, KT * 8, in_w.d, K * 8, K * 8, P, cudaMemcpyDeviceToDevice, s),
                 "ig_model_from_patterns");
+      IG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&m->words_kt[c]), npad * KT * 8, s),
+              "ig_model_from_patterns");
+      IG_CUDA(cudaMemsetAsync(m->words_kt[c], 0, npad * KT * 8, s), "ig_model_from_patterns");
+      IG_CUDA(cudaMemcpyAsync(work.p, raw.p, npad * KT * 8, cudaMemcpyDeviceToDevice, s),
+              "ig_model_from_patterns");
+      {
+        ProfScope ps(S_SORT, s);
+        IG_CUDA(igk::canonical_sort(work.p, P, KT, m->words_kt[c], work.p, s),
+                "ig_model_from_patterns: sort");
+      }
+      IG_CUDA(igk::launch_check_strict(m->words_kt[c], P, KT, d_status.p, s),
+              "ig_model_from_patterns");
+      IG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&m->support[c]),
+                              sizeof(uint32_t) * std::max<int64_t>(1, P), s),
+              "ig_model_from_patterns");
+      IG_CUDA(igk::launch_place_payload(m->words_kt[c], P, KT, raw.p, in_f.d, m->support[c],
+                                        d_status.p, s),
+              "ig_model_from_patterns");
+      IG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&m->score[c]), sizeof(uint64_t) * npad, s),
+              "ig_model_from_patterns");
+      IG_CUDA(cudaMemsetAsync(m->score[c], 0, sizeof(uint64_t) * npad, s), "ig_model_from_patterns");
+      DevBuf<unsigned long long> d_smax;
+      IG_CUDA(d_smax.alloc(1, s), "ig_model_from_patterns");
+      IG_CUDA(cudaMemsetAsync(d_smax.p, 0, sizeof(unsigned long long), s), "ig_model_from_patterns");
+      IG_CUDA(igk::launch_pattern_score(m->words_kt[c], P, KT, m->support[c], m->score[c], s,
+                                        d_smax.p),
+              "ig_model_from_patterns: score");
+      unsigned long long smax = 0;
+      IG_CUDA(cudaMemcpyAsync(&smax, d_smax.p, sizeof(smax), cudaMemcpyDeviceToHost, s),
+              "ig_model_from_patterns");
+      if (K == KT) {
+        m->words[c] = m->words_kt[c];
+      } else {
+        IG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&m->words[c]),
+                                sizeof(uint64_t) * std::max<int64_t>(1, P) * K, s),
+                "ig_model_from_patterns");
+        if (P)
+          IG_CUDA(cudaMemcpy2DAsync(m->words[c], K * 8, m->words_kt[c], KT * 8, K * 8, P,
+                                    cudaMemcpyDeviceToDevice, s),
+                  "ig_model_from_patterns");
+      }
+      IG_CHECK(read_status(d_status.p, s, "ig_model_from_patterns"));
+      m->score_max[c] = smax;
     }
-    IG_CHECK(read_status(d_status.p, s, "ig_model_from_patterns"));
-    m->score_max[c] = smax;
-  }
-  m->subset_kernel = KT >= 2 ? 3 : 1;
-  if (KT >= 2) {
-    DevBuf<uint32_t> d_f;
-    IG_CUDA(d_f.alloc(64 * K, s), "ig_model_from_patterns");
-    IG_CUDA(pattern_item_freq(m, d_f.p, s), "ig_model_from_patterns");
-    IG_CUDA(build_pattern_indexes(m, d_f.p, s), "ig_model_from_patterns: pattern index");
-  }
-  guard.m = nullptr;
-  *out = m;
-  return IG_OK;
+    m->subset_kernel = KT >= 2 ? 3 : 1;
+    if (KT >= 2) {
+      DevBuf<uint32_t> d_f;
+      IG_CUDA(d_f.alloc(64 * K, s), "ig_model_from_patterns");
+      IG_CUDA(pattern_item_freq(m, d_f.p, s), "ig_model_from_patterns");
+      IG_CUDA(build_pattern_indexes(m, d_f.p, s), "ig_model_from_patterns: pattern index");
+    }
+    guard.m = nullptr;
+    *out = m;
+    return IG_OK;
+  });
 }
 
 int ig_model_info(const ig_model* m, ig_model_info_t* info) {
@@ -1793,203 +1824,207 @@ int ig_model_patterns(const ig_model* m, int32_t cls, const uint64_t** words,
 int ig_model_copy_patterns(const ig_model* m, int32_t cls, uint64_t* words_out,
                            uint32_t* support_out, uint64_t* score_out,
                            ig_stream_t stream) {
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (!m || (cls != 0 && cls != 1)) return fail(IG_E_INVAL, "ig_model_copy_patterns: bad arguments");
-  const int64_t P = m->n_pat[cls];
-  if (P == 0) return IG_OK;
-  if (words_out)
-    IG_CUDA(cudaMemcpyAsync(words_out, m->words[cls], sizeof(uint64_t) * P * m->K,
-                            cudaMemcpyDefault, s), "ig_model_copy_patterns");
-  if (support_out)
-    IG_CUDA(cudaMemcpyAsync(support_out, m->support[cls], sizeof(uint32_t) * P,
-                            cudaMemcpyDefault, s), "ig_model_copy_patterns");
-  if (score_out)
-    IG_CUDA(cudaMemcpyAsync(score_out, m->score[cls], sizeof(uint64_t) * P, cudaMemcpyDefault, s),
-            "ig_model_copy_patterns");
-  IG_CUDA(cudaStreamSynchronize(s), "ig_model_copy_patterns");
-  return IG_OK;
+  return igk::guarded("ig_model_copy_patterns", [&]() -> int {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!m || (cls != 0 && cls != 1)) return fail(IG_E_INVAL, "ig_model_copy_patterns: bad arguments");
+    const int64_t P = m->n_pat[cls];
+    if (P == 0) return IG_OK;
+    if (words_out)
+      IG_CUDA(cudaMemcpyAsync(words_out, m->words[cls], sizeof(uint64_t) * P * m->K,
+                              cudaMemcpyDefault, s), "ig_model_copy_patterns");
+    if (support_out)
+      IG_CUDA(cudaMemcpyAsync(support_out, m->support[cls], sizeof(uint32_t) * P,
+                              cudaMemcpyDefault, s), "ig_model_copy_patterns");
+    if (score_out)
+      IG_CUDA(cudaMemcpyAsync(score_out, m->score[cls], sizeof(uint64_t) * P, cudaMemcpyDefault, s),
+              "ig_model_copy_patterns");
+    IG_CUDA(cudaStreamSynchronize(s), "ig_model_copy_patterns");
+    return IG_OK;
+  });
 }
 
 int ig_score(const ig_model* m, const uint64_t* rows, int64_t n_rows, int64_t* A_out,
              int64_t* N_out, uint8_t* label_out, ig_stream_t stream) {
-  igk::DeviceRestore restore_device;  // the caller's device, put back on return
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (!m || n_rows < 0 || (n_rows > 0 && !rows)) return fail(IG_E_INVAL, "ig_score: bad arguments");
-  // Pinned words for the tensor-core evidence's executed tests (one pair
-  // per host thread), copied when the stream gets there.
-  static thread_local int64_t* h_tests = nullptr;
-  int tc_tests = 0;
-  if (n_rows == 0) return IG_OK;
-  InputView<uint64_t> in;
-  IG_CHECK(in.bind(rows, size_t(n_rows) * m->K, s, "ig_score: rows"));
-  OutputView<unsigned long long> A, N;
-  OutputView<uint8_t> lab;
-  IG_CHECK(A.bind(reinterpret_cast<unsigned long long*>(A_out), size_t(n_rows), s, "ig_score"));
-  IG_CHECK(N.bind(reinterpret_cast<unsigned long long*>(N_out), size_t(n_rows), s, "ig_score"));
-  if (label_out) IG_CHECK(lab.bind(label_out, size_t(n_rows), s, "ig_score"));
-  DevBuf<int> d_status;
-  IG_CUDA(d_status.alloc(1, s), "ig_score");
-  IG_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), s), "ig_score");
-  IG_CUDA(cudaMemsetAsync(A.d, 0, sizeof(unsigned long long) * n_rows, s), "ig_score");
-  IG_CUDA(cudaMemsetAsync(N.d, 0, sizeof(unsigned long long) * n_rows, s), "ig_score");
-  DevBuf<uint8_t> test_img;
-  // The item index pays for its build (and its host round trips) only on
-  // batches of some size; smaller batches stream the patterns densely.
-  const bool pruned = m->subset_kernel >= 3 && n_rows >= kIndexMinRows;
-  bool tc = m->subset_kernel >= 2 && igk::tc_supported(m->KT) && m->pat_img[0] && m->pat_img[1];
-  bool done[2] = {false, false};
-  IndexHolder test_idx;
-  test_idx.s = s;
-  DevBuf<uint64_t> sorted_rows;
-  DevBuf<uint32_t> perm;
-  if (pruned && m->subset_kernel == 4) {
-    // The tensor-core evidence kernel reads records in canonical order: the
-    // neighbouring rows of an item group then hold similar itemsets, so the
-    // patterns inside them fall into fewer 32 x 32 accumulator chunks, and
-    // its epilogue skips every chunk without one.  The index files each copy
-    // under the caller's row number (perm), so results land in place.
-    const int KT = m->KT;
-    const uint64_t* keys = in.d;
-    DevBuf<uint64_t> padded;
-    if (m->K != KT) {
-      IG_CUDA(padded.alloc(size_t(n_rows) * KT, s), "ig_score");
-      IG_CUDA(cudaMemsetAsync(padded.p, 0, sizeof(uint64_t) * n_rows * KT, s), "ig_score");
-      IG_CUDA(cudaMemcpy2DAsync(padded.p, KT * 8, in.d, m->K * 8, m->K * 8, n_rows,
-                                cudaMemcpyDeviceToDevice, s),
-              "ig_score");
-      keys = padded.p;
-    }
-    IG_CUDA(sorted_rows.alloc(size_t(n_rows) * KT, s), "ig_score");
-    IG_CUDA(perm.alloc(size_t(n_rows), s), "ig_score");
-    {
-      ProfScope ps(igk::kStageIndexBuild, s);
-      IG_CUDA(igk::canonical_sort(keys, n_rows, KT, sorted_rows.p, nullptr, s, perm.p),
-              "ig_score: record order");
-    }
-    IG_CUDA(igk::build_record_index(sorted_rows.p, n_rows, KT, m->K, KT, 0.25, &test_idx.idx, s,
-                                    perm.p),
-            "ig_score: record index");
-  } else if (pruned) {
-    IG_CUDA(igk::build_record_index(in.d, n_rows, m->K, m->K, m->KT, 0.25, &test_idx.idx, s),
-            "ig_score: record index");
-  }
-  if (pruned && test_idx.idx.usable && m->subset_kernel == 4 && igk::tc_supported(m->KT)) {
-    // Tensor-core form: both classes' patterns against the batch's records
-    // in one launch of the fused kernel (one schedule, one tail).  Small
-    // batches reuse the model's pattern index; larger ones re-key the
-    // patterns by the batch's own item counts.
-    igk::KeyedIndex own[2];
-    const igk::KeyedIndex* kx[2];
-    unsigned long long* outs[2];
-    uint64_t smax[2];
-    int n = 0;
-    cudaError_t e = cudaSuccess;
-    if (!h_tests) e = cudaMallocHost(&h_tests, 2 * sizeof(int64_t));
-    for (int c = 1; c >= 0 && e == cudaSuccess; --c) {
-      done[c] = true;
-      if (m->n_pat[c] == 0) continue;
-      if (m->pidx[c] && n_rows * 8 < m->n_pat[c]) {
-        kx[n] = m->pidx[c];
-      } else {
-        // Work items are built on the device: no host offsets, no read-back.
-        e = igk::build_keyed_index(m->words_kt[c], m->n_pat[c], m->KT, m->K, m->KT,
-                                   test_idx.idx.freq, m->score[c], &own[n], s, nullptr, false);
-        kx[n] = &own[n];
+  return igk::guarded("ig_score", [&]() -> int {
+    igk::DeviceRestore restore_device;  // the caller's device, put back on return
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!m || n_rows < 0 || (n_rows > 0 && !rows)) return fail(IG_E_INVAL, "ig_score: bad arguments");
+    // Pinned words for the tensor-core evidence's executed tests (one pair
+    // per host thread), copied when the stream gets there.
+    static thread_local int64_t* h_tests = nullptr;
+    int tc_tests = 0;
+    if (n_rows == 0) return IG_OK;
+    InputView<uint64_t> in;
+    IG_CHECK(in.bind(rows, size_t(n_rows) * m->K, s, "ig_score: rows"));
+    OutputView<unsigned long long> A, N;
+    OutputView<uint8_t> lab;
+    IG_CHECK(A.bind(reinterpret_cast<unsigned long long*>(A_out), size_t(n_rows), s, "ig_score"));
+    IG_CHECK(N.bind(reinterpret_cast<unsigned long long*>(N_out), size_t(n_rows), s, "ig_score"));
+    if (label_out) IG_CHECK(lab.bind(label_out, size_t(n_rows), s, "ig_score"));
+    DevBuf<int> d_status;
+    IG_CUDA(d_status.alloc(1, s), "ig_score");
+    IG_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), s), "ig_score");
+    IG_CUDA(cudaMemsetAsync(A.d, 0, sizeof(unsigned long long) * n_rows, s), "ig_score");
+    IG_CUDA(cudaMemsetAsync(N.d, 0, sizeof(unsigned long long) * n_rows, s), "ig_score");
+    DevBuf<uint8_t> test_img;
+    // The item index pays for its build (and its host round trips) only on
+    // batches of some size; smaller batches stream the patterns densely.
+    const bool pruned = m->subset_kernel >= 3 && n_rows >= kIndexMinRows;
+    bool tc = m->subset_kernel >= 2 && igk::tc_supported(m->KT) && m->pat_img[0] && m->pat_img[1];
+    bool done[2] = {false, false};
+    IndexHolder test_idx;
+    test_idx.s = s;
+    DevBuf<uint64_t> sorted_rows;
+    DevBuf<uint32_t> perm;
+    if (pruned && m->subset_kernel == 4) {
+      // The tensor-core evidence kernel reads records in canonical order: the
+      // neighbouring rows of an item group then hold similar itemsets, so the
+      // patterns inside them fall into fewer 32 x 32 accumulator chunks, and
+      // its epilogue skips every chunk without one.  The index files each copy
+      // under the caller's row number (perm), so results land in place.
+      const int KT = m->KT;
+      const uint64_t* keys = in.d;
+      DevBuf<uint64_t> padded;
+      if (m->K != KT) {
+        IG_CUDA(padded.alloc(size_t(n_rows) * KT, s), "ig_score");
+        IG_CUDA(cudaMemsetAsync(padded.p, 0, sizeof(uint64_t) * n_rows * KT, s), "ig_score");
+        IG_CUDA(cudaMemcpy2DAsync(padded.p, KT * 8, in.d, m->K * 8, m->K * 8, n_rows,
+                                  cudaMemcpyDeviceToDevice, s),
+                "ig_score");
+        keys = padded.p;
       }
-      outs[n] = c == 1 ? A.d : N.d;
-      smax[n] = m->score_max[c];
-      ++n;
+      IG_CUDA(sorted_rows.alloc(size_t(n_rows) * KT, s), "ig_score");
+      IG_CUDA(perm.alloc(size_t(n_rows), s), "ig_score");
+      {
+        ProfScope ps(igk::kStageIndexBuild, s);
+        IG_CUDA(igk::canonical_sort(keys, n_rows, KT, sorted_rows.p, nullptr, s, perm.p),
+                "ig_score: record order");
+      }
+      IG_CUDA(igk::build_record_index(sorted_rows.p, n_rows, KT, m->K, KT, 0.25, &test_idx.idx, s,
+                                      perm.p),
+              "ig_score: record index");
+    } else if (pruned) {
+      IG_CUDA(igk::build_record_index(in.d, n_rows, m->K, m->K, m->KT, 0.25, &test_idx.idx, s),
+              "ig_score: record index");
     }
-    if (e == cudaSuccess && n > 0) {
-      h_tests[0] = h_tests[1] = 0;
-      e = igk::indexed_subset_tc_classes(igk::MODE_SUM, test_idx.idx, kx, n, nullptr, outs,
-                                         d_status.p, h_tests, S_EVIDENCE_IDX, smax, s);
-      tc_tests = n;  // counted after the last read-back below
-    }
-    for (int i = 0; i < 2; ++i) igk::release_keyed_index(&own[i], s);
-    IG_CUDA(e, "ig_score: evidence");
-  } else if (pruned && test_idx.idx.usable) {
-    // A (class 1) on the caller's stream and N (class 0) on this thread's
-    // auxiliary stream, concurrently: both only read the indexes.
-    AuxStream& aux = aux_stream();
-    IG_CUDA(aux.error, "ig_score: auxiliary stream");
-    IG_CUDA(cudaEventRecord(aux.ready, s), "ig_score");
-    IG_CUDA(cudaStreamWaitEvent(aux.s, aux.ready, 0), "ig_score");
-    for (int c = 1; c >= 0; --c) {
-      if (m->n_pat[c] == 0) {
+    if (pruned && test_idx.idx.usable && m->subset_kernel == 4 && igk::tc_supported(m->KT)) {
+      // Tensor-core form: both classes' patterns against the batch's records
+      // in one launch of the fused kernel (one schedule, one tail).  Small
+      // batches reuse the model's pattern index; larger ones re-key the
+      // patterns by the batch's own item counts.
+      igk::KeyedIndex own[2];
+      const igk::KeyedIndex* kx[2];
+      unsigned long long* outs[2];
+      uint64_t smax[2];
+      int n = 0;
+      cudaError_t e = cudaSuccess;
+      if (!h_tests) e = cudaMallocHost(&h_tests, 2 * sizeof(int64_t));
+      for (int c = 1; c >= 0 && e == cudaSuccess; --c) {
         done[c] = true;
-        continue;
+        if (m->n_pat[c] == 0) continue;
+        if (m->pidx[c] && n_rows * 8 < m->n_pat[c]) {
+          kx[n] = m->pidx[c];
+        } else {
+          // Work items are built on the device: no host offsets, no read-back.
+          e = igk::build_keyed_index(m->words_kt[c], m->n_pat[c], m->KT, m->K, m->KT,
+                                     test_idx.idx.freq, m->score[c], &own[n], s, nullptr, false);
+          kx[n] = &own[n];
+        }
+        outs[n] = c == 1 ? A.d : N.d;
+        smax[n] = m->score_max[c];
+        ++n;
       }
-      const cudaStream_t sc = c == 1 ? s : aux.s;
-      int64_t t = 0;
-      // Small batches reuse the model's pattern index; larger ones re-key
-      // the patterns by the batch's own item counts (fewer tests, and
-      // patterns holding an item absent from the batch drop out at once).
-      if (m->pidx[c] && n_rows * 8 < m->n_pat[c]) {
-        IG_CUDA(igk::indexed_subset_prebuilt(igk::MODE_SUM, test_idx.idx, *m->pidx[c], nullptr,
-                                             c == 1 ? A.d : N.d, d_status.p, &t, S_EVIDENCE_IDX,
-                                             m->index_max_q, m->index_flip,
-                                             m->subset_kernel == 4 ? 1 : 0, sc, m->score_max[c]),
-                "ig_score: evidence");
+      if (e == cudaSuccess && n > 0) {
+        h_tests[0] = h_tests[1] = 0;
+        e = igk::indexed_subset_tc_classes(igk::MODE_SUM, test_idx.idx, kx, n, nullptr, outs,
+                                           d_status.p, h_tests, S_EVIDENCE_IDX, smax, s);
+        tc_tests = n;  // counted after the last read-back below
+      }
+      for (int i = 0; i < 2; ++i) igk::release_keyed_index(&own[i], s);
+      IG_CUDA(e, "ig_score: evidence");
+    } else if (pruned && test_idx.idx.usable) {
+      // A (class 1) on the caller's stream and N (class 0) on this thread's
+      // auxiliary stream, concurrently: both only read the indexes.
+      AuxStream& aux = aux_stream();
+      IG_CUDA(aux.error, "ig_score: auxiliary stream");
+      IG_CUDA(cudaEventRecord(aux.ready, s), "ig_score");
+      IG_CUDA(cudaStreamWaitEvent(aux.s, aux.ready, 0), "ig_score");
+      for (int c = 1; c >= 0; --c) {
+        if (m->n_pat[c] == 0) {
+          done[c] = true;
+          continue;
+        }
+        const cudaStream_t sc = c == 1 ? s : aux.s;
+        int64_t t = 0;
+        // Small batches reuse the model's pattern index; larger ones re-key
+        // the patterns by the batch's own item counts (fewer tests, and
+        // patterns holding an item absent from the batch drop out at once).
+        if (m->pidx[c] && n_rows * 8 < m->n_pat[c]) {
+          IG_CUDA(igk::indexed_subset_prebuilt(igk::MODE_SUM, test_idx.idx, *m->pidx[c], nullptr,
+                                               c == 1 ? A.d : N.d, d_status.p, &t, S_EVIDENCE_IDX,
+                                               m->index_max_q, m->index_flip,
+                                               m->subset_kernel == 4 ? 1 : 0, sc, m->score_max[c]),
+                  "ig_score: evidence");
+          done[c] = true;
+          igk::prof_add_work(S_EVIDENCE_IDX, t);
+          continue;
+        }
+        igk::IndexedArgs a;
+        a.mode = igk::MODE_SUM;
+        a.index = &test_idx.idx;
+        a.keyed = m->words_kt[c];
+        a.n_keyed = m->n_pat[c];
+        a.keyed_stride = m->KT;
+        a.keyed_score = m->score[c];
+        a.out_u32 = nullptr;
+        a.out_u64 = c == 1 ? A.d : N.d;
+        a.status = d_status.p;
+        a.tests_out = &t;
+        a.prof_stage = S_EVIDENCE_IDX;
+        a.score_max = m->score_max[c];
+        a.max_q = m->index_max_q;
+        a.flip_factor = m->index_flip;
+        a.tc = m->subset_kernel == 4 ? 1 : 0;
+        IG_CUDA(igk::indexed_subset(a, sc), "ig_score: evidence");
         done[c] = true;
         igk::prof_add_work(S_EVIDENCE_IDX, t);
-        continue;
       }
-      igk::IndexedArgs a;
-      a.mode = igk::MODE_SUM;
-      a.index = &test_idx.idx;
-      a.keyed = m->words_kt[c];
-      a.n_keyed = m->n_pat[c];
-      a.keyed_stride = m->KT;
-      a.keyed_score = m->score[c];
-      a.out_u32 = nullptr;
-      a.out_u64 = c == 1 ? A.d : N.d;
-      a.status = d_status.p;
-      a.tests_out = &t;
-      a.prof_stage = S_EVIDENCE_IDX;
-      a.score_max = m->score_max[c];
-      a.max_q = m->index_max_q;
-      a.flip_factor = m->index_flip;
-      a.tc = m->subset_kernel == 4 ? 1 : 0;
-      IG_CUDA(igk::indexed_subset(a, sc), "ig_score: evidence");
-      done[c] = true;
-      igk::prof_add_work(S_EVIDENCE_IDX, t);
+      IG_CUDA(cudaEventRecord(aux.done, aux.s), "ig_score");
+      IG_CUDA(cudaStreamWaitEvent(s, aux.done, 0), "ig_score");
     }
-    IG_CUDA(cudaEventRecord(aux.done, aux.s), "ig_score");
-    IG_CUDA(cudaStreamWaitEvent(s, aux.done, 0), "ig_score");
-  }
-  if (done[0] && done[1]) tc = false;
-  if (tc) {
-    IG_CUDA(test_img.alloc(igk::tc_image_bytes(n_rows, m->KT, true), s), "ig_score: images");
-    ProfScope pe(S_EXPAND, s);
-    IG_CUDA(igk::launch_expand(in.d, n_rows, m->K, m->KT, true, true, test_img.p, s),
-            "ig_score: expand");
-  }
-  for (int c = 1; c >= 0; --c) {  // A from P+, then N from P- (Eq. 4)
-    if (done[c]) continue;
-    igk::prof_add_work(tc && m->n_pat[c] ? S_EVIDENCE_TC : S_EVIDENCE, n_rows * m->n_pat[c]);
-    ProfScope ps(tc && m->n_pat[c] ? S_EVIDENCE_TC : S_EVIDENCE, s);
-    if (tc && m->n_pat[c]) {
-      igk::TcArgs a{igk::MODE_SUM, m->KT,      test_img.p,  n_rows,  nullptr,
-                    m->pat_img[c], 0,          m->n_pat[c], m->score[c], nullptr,
-                    c == 1 ? A.d : N.d,        d_status.p};
-      IG_CUDA(igk::launch_subset_tc(a, s), "ig_score: evidence");
-    } else {
-      igk::SubsetArgs a{igk::MODE_SUM, m->KT, in.d, n_rows, m->K, m->words_kt[c], m->score[c],
-                        m->n_pat[c], nullptr, c == 1 ? A.d : N.d, d_status.p};
-      IG_CUDA(igk::launch_subset(a, s), "ig_score: evidence");
+    if (done[0] && done[1]) tc = false;
+    if (tc) {
+      IG_CUDA(test_img.alloc(igk::tc_image_bytes(n_rows, m->KT, true), s), "ig_score: images");
+      ProfScope pe(S_EXPAND, s);
+      IG_CUDA(igk::launch_expand(in.d, n_rows, m->K, m->KT, true, true, test_img.p, s),
+              "ig_score: expand");
     }
-  }
-  if (label_out) {
-    ProfScope ps(S_LABELS, s);
-    IG_CUDA(igk::launch_labels(A.d, N.d, n_rows, m->reg3, m->thr, lab.d, s), "ig_score: labels");
-  }
-  IG_CHECK(A.finish(s, "ig_score"));
-  IG_CHECK(N.finish(s, "ig_score"));
-  if (label_out) IG_CHECK(lab.finish(s, "ig_score"));
-  const int rc = read_status(d_status.p, s, "ig_score");
-  if (rc == IG_OK && tc_tests) igk::prof_add_work(S_EVIDENCE_IDX, h_tests[0] + h_tests[1]);
-  return rc;
+    for (int c = 1; c >= 0; --c) {  // A from P+, then N from P- (Eq. 4)
+      if (done[c]) continue;
+      igk::prof_add_work(tc && m->n_pat[c] ? S_EVIDENCE_TC : S_EVIDENCE, n_rows * m->n_pat[c]);
+      ProfScope ps(tc && m->n_pat[c] ? S_EVIDENCE_TC : S_EVIDENCE, s);
+      if (tc && m->n_pat[c]) {
+        igk::TcArgs a{igk::MODE_SUM, m->KT,      test_img.p,  n_rows,  nullptr,
+                      m->pat_img[c], 0,          m->n_pat[c], m->score[c], nullptr,
+                      c == 1 ? A.d : N.d,        d_status.p};
+        IG_CUDA(igk::launch_subset_tc(a, s), "ig_score: evidence");
+      } else {
+        igk::SubsetArgs a{igk::MODE_SUM, m->KT, in.d, n_rows, m->K, m->words_kt[c], m->score[c],
+                          m->n_pat[c], nullptr, c == 1 ? A.d : N.d, d_status.p};
+        IG_CUDA(igk::launch_subset(a, s), "ig_score: evidence");
+      }
+    }
+    if (label_out) {
+      ProfScope ps(S_LABELS, s);
+      IG_CUDA(igk::launch_labels(A.d, N.d, n_rows, m->reg3, m->thr, lab.d, s), "ig_score: labels");
+    }
+    IG_CHECK(A.finish(s, "ig_score"));
+    IG_CHECK(N.finish(s, "ig_score"));
+    if (label_out) IG_CHECK(lab.finish(s, "ig_score"));
+    const int rc = read_status(d_status.p, s, "ig_score");
+    if (rc == IG_OK && tc_tests) igk::prof_add_work(S_EVIDENCE_IDX, h_tests[0] + h_tests[1]);
+    return rc;
+  });
 }
 
 // ---- persistence ------------------------------------------------------------
@@ -1997,139 +2032,143 @@ static const char kMagic[8] = {'I', 'G', 'G', 'B', '3', '0', '0', 0};
 static const uint32_t kVersion = 1;
 
 int ig_model_save(const ig_model* m, const char* path) {
-  if (!m || !path) return fail(IG_E_INVAL, "ig_model_save: NULL argument");
-  FILE* f = fopen(path, "wb");
-  if (!f) return fail(IG_E_IO, "ig_model_save: cannot open %s", path);
-  bool ok = true;
-  auto put = [&](const void* p, size_t n) { ok = ok && fwrite(p, 1, n, f) == n; };
-  uint32_t hdr[4] = {kVersion, uint32_t(m->K), uint32_t(m->reg3), 0};
-  double st[4] = {m->mu, m->sigma, m->r, m->thr};
-  put(kMagic, 8);
-  put(hdr, sizeof(hdr));
-  put(st, sizeof(st));
-  put(m->n_train, sizeof(m->n_train));
-  put(m->n_cand, sizeof(m->n_cand));
-  put(m->n_pairs, sizeof(m->n_pairs));
-  put(m->n_pat, sizeof(m->n_pat));
-  for (int c = 0; c < 2 && ok; ++c) {
-    const int64_t P = m->n_pat[c];
-    std::vector<uint64_t> w(size_t(P) * m->K);
-    std::vector<uint32_t> sup(static_cast<size_t>(P));
-    std::vector<uint64_t> sc(static_cast<size_t>(P));
-    if (P) {
-      if (cudaMemcpy(w.data(), m->words[c], w.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
-          cudaMemcpy(sup.data(), m->support[c], sup.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
-          cudaMemcpy(sc.data(), m->score[c], sc.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
-        fclose(f);
-        return fail(IG_E_CUDA, "ig_model_save: copy from device failed");
+  return igk::guarded("ig_model_save", [&]() -> int {
+    if (!m || !path) return fail(IG_E_INVAL, "ig_model_save: NULL argument");
+    FILE* f = fopen(path, "wb");
+    if (!f) return fail(IG_E_IO, "ig_model_save: cannot open %s", path);
+    bool ok = true;
+    auto put = [&](const void* p, size_t n) { ok = ok && fwrite(p, 1, n, f) == n; };
+    uint32_t hdr[4] = {kVersion, uint32_t(m->K), uint32_t(m->reg3), 0};
+    double st[4] = {m->mu, m->sigma, m->r, m->thr};
+    put(kMagic, 8);
+    put(hdr, sizeof(hdr));
+    put(st, sizeof(st));
+    put(m->n_train, sizeof(m->n_train));
+    put(m->n_cand, sizeof(m->n_cand));
+    put(m->n_pairs, sizeof(m->n_pairs));
+    put(m->n_pat, sizeof(m->n_pat));
+    for (int c = 0; c < 2 && ok; ++c) {
+      const int64_t P = m->n_pat[c];
+      std::vector<uint64_t> w(size_t(P) * m->K);
+      std::vector<uint32_t> sup(static_cast<size_t>(P));
+      std::vector<uint64_t> sc(static_cast<size_t>(P));
+      if (P) {
+        if (cudaMemcpy(w.data(), m->words[c], w.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(sup.data(), m->support[c], sup.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(sc.data(), m->score[c], sc.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+          fclose(f);
+          return fail(IG_E_CUDA, "ig_model_save: copy from device failed");
+        }
       }
+      put(w.data(), w.size() * 8);
+      put(sup.data(), sup.size() * 4);
+      put(sc.data(), sc.size() * 8);
     }
-    put(w.data(), w.size() * 8);
-    put(sup.data(), sup.size() * 4);
-    put(sc.data(), sc.size() * 8);
-  }
-  if (fclose(f) != 0) ok = false;
-  return ok ? IG_OK : fail(IG_E_IO, "ig_model_save: write to %s failed", path);
+    if (fclose(f) != 0) ok = false;
+    return ok ? IG_OK : fail(IG_E_IO, "ig_model_save: write to %s failed", path);
+  });
 }
 
 int ig_model_load(const char* path, ig_model** out) {
-  if (!path || !out) return fail(IG_E_INVAL, "ig_model_load: NULL argument");
-  *out = nullptr;
-  FILE* f = fopen(path, "rb");
-  if (!f) return fail(IG_E_IO, "ig_model_load: cannot open %s", path);
-  bool ok = true;
-  auto get = [&](void* p, size_t n) { ok = ok && fread(p, 1, n, f) == n; };
-  char magic[8];
-  uint32_t hdr[4];
-  double st[4];
-  ig_model* m = new ig_model;
-  get(magic, 8);
-  get(hdr, sizeof(hdr));
-  get(st, sizeof(st));
-  get(m->n_train, sizeof(m->n_train));
-  get(m->n_cand, sizeof(m->n_cand));
-  get(m->n_pairs, sizeof(m->n_pairs));
-  get(m->n_pat, sizeof(m->n_pat));
-  if (!ok || memcmp(magic, kMagic, 8) != 0 || hdr[0] != kVersion || hdr[1] < 1 ||
-      hdr[1] > IG_MAX_WORDS || m->n_pat[0] < 0 || m->n_pat[1] < 0) {
+  return igk::guarded("ig_model_load", [&]() -> int {
+    if (!path || !out) return fail(IG_E_INVAL, "ig_model_load: NULL argument");
+    *out = nullptr;
+    FILE* f = fopen(path, "rb");
+    if (!f) return fail(IG_E_IO, "ig_model_load: cannot open %s", path);
+    bool ok = true;
+    auto get = [&](void* p, size_t n) { ok = ok && fread(p, 1, n, f) == n; };
+    char magic[8];
+    uint32_t hdr[4];
+    double st[4];
+    ig_model* m = new ig_model;
+    get(magic, 8);
+    get(hdr, sizeof(hdr));
+    get(st, sizeof(st));
+    get(m->n_train, sizeof(m->n_train));
+    get(m->n_cand, sizeof(m->n_cand));
+    get(m->n_pairs, sizeof(m->n_pairs));
+    get(m->n_pat, sizeof(m->n_pat));
+    if (!ok || memcmp(magic, kMagic, 8) != 0 || hdr[0] != kVersion || hdr[1] < 1 ||
+        hdr[1] > IG_MAX_WORDS || m->n_pat[0] < 0 || m->n_pat[1] < 0) {
+      fclose(f);
+      model_release(m);
+      return fail(IG_E_IO, "ig_model_load: %s is not an IG model file", path);
+    }
+    {
+      // The pattern counts must account for the rest of the file exactly
+      // (words, supports and scores of both classes) before anything is sized
+      // by them: a damaged header must not drive a huge allocation.
+      const off_t here = ftello(f);
+      bool sized = here >= 0 && fseeko(f, 0, SEEK_END) == 0;
+      const off_t end = sized ? ftello(f) : off_t(-1);
+      const int64_t per = 8 * int64_t(hdr[1]) + 4 + 8;
+      const int64_t left = int64_t(end) - int64_t(here);
+      sized = sized && end >= here && m->n_pat[0] <= left / per && m->n_pat[1] <= left / per &&
+              (m->n_pat[0] + m->n_pat[1]) * per == left && fseeko(f, here, SEEK_SET) == 0;
+      if (!sized) {
+        fclose(f);
+        model_release(m);
+        return fail(IG_E_IO, "ig_model_load: %s is truncated or its counts do not match its size",
+                    path);
+      }
+    }
+    m->K = int(hdr[1]);
+    m->KT = igk::padded_words(m->K);
+    m->reg3 = int(hdr[2]);
+    m->mu = st[0];
+    m->sigma = st[1];
+    m->r = st[2];
+    m->thr = st[3];
+    for (int c = 0; c < 2 && ok; ++c) {
+      const int64_t P = m->n_pat[c];
+      std::vector<uint64_t> w(size_t(P) * m->K), wk(size_t(std::max<int64_t>(1, igk::pad_rows(P))) * m->KT, 0);
+      std::vector<uint32_t> sup(static_cast<size_t>(P));
+      std::vector<uint64_t> sc(size_t(std::max<int64_t>(1, igk::pad_rows(P))), 0);
+      get(w.data(), w.size() * 8);
+      get(sup.data(), sup.size() * 4);
+      get(sc.data(), size_t(P) * 8);
+      if (!ok) break;
+      m->score_max[c] = P ? *std::max_element(sc.begin(), sc.begin() + P) : 0;
+      for (int64_t i = 0; i < P; ++i)
+        for (int k = 0; k < m->K; ++k) wk[size_t(i) * m->KT + k] = w[size_t(i) * m->K + k];
+      bool cu = cudaMalloc(&m->words_kt[c], wk.size() * 8) == cudaSuccess &&
+                cudaMemcpy(m->words_kt[c], wk.data(), wk.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+                cudaMalloc(&m->support[c], std::max<size_t>(1, sup.size()) * 4) == cudaSuccess &&
+                (sup.empty() || cudaMemcpy(m->support[c], sup.data(), sup.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess) &&
+                cudaMalloc(&m->score[c], sc.size() * 8) == cudaSuccess &&
+                cudaMemcpy(m->score[c], sc.data(), sc.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+      if (cu && m->K == m->KT) {
+        m->words[c] = m->words_kt[c];
+      } else if (cu) {
+        cu = cudaMalloc(&m->words[c], std::max<size_t>(1, w.size()) * 8) == cudaSuccess &&
+             (w.empty() || cudaMemcpy(m->words[c], w.data(), w.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess);
+      }
+      if (!cu) {
+        fclose(f);
+        model_release(m);
+        return fail(IG_E_CUDA, "ig_model_load: device allocation or copy failed");
+      }
+    }
     fclose(f);
-    model_release(m);
-    return fail(IG_E_IO, "ig_model_load: %s is not an IG model file", path);
-  }
-  {
-    // The pattern counts must account for the rest of the file exactly
-    // (words, supports and scores of both classes) before anything is sized
-    // by them: a damaged header must not drive a huge allocation.
-    const off_t here = ftello(f);
-    bool sized = here >= 0 && fseeko(f, 0, SEEK_END) == 0;
-    const off_t end = sized ? ftello(f) : off_t(-1);
-    const int64_t per = 8 * int64_t(hdr[1]) + 4 + 8;
-    const int64_t left = int64_t(end) - int64_t(here);
-    sized = sized && end >= here && m->n_pat[0] <= left / per && m->n_pat[1] <= left / per &&
-            (m->n_pat[0] + m->n_pat[1]) * per == left && fseeko(f, here, SEEK_SET) == 0;
-    if (!sized) {
-      fclose(f);
+    if (!ok) {
       model_release(m);
-      return fail(IG_E_IO, "ig_model_load: %s is truncated or its counts do not match its size",
-                  path);
+      return fail(IG_E_IO, "ig_model_load: %s is truncated", path);
     }
-  }
-  m->K = int(hdr[1]);
-  m->KT = igk::padded_words(m->K);
-  m->reg3 = int(hdr[2]);
-  m->mu = st[0];
-  m->sigma = st[1];
-  m->r = st[2];
-  m->thr = st[3];
-  for (int c = 0; c < 2 && ok; ++c) {
-    const int64_t P = m->n_pat[c];
-    std::vector<uint64_t> w(size_t(P) * m->K), wk(size_t(std::max<int64_t>(1, igk::pad_rows(P))) * m->KT, 0);
-    std::vector<uint32_t> sup(static_cast<size_t>(P));
-    std::vector<uint64_t> sc(size_t(std::max<int64_t>(1, igk::pad_rows(P))), 0);
-    get(w.data(), w.size() * 8);
-    get(sup.data(), sup.size() * 4);
-    get(sc.data(), size_t(P) * 8);
-    if (!ok) break;
-    m->score_max[c] = P ? *std::max_element(sc.begin(), sc.begin() + P) : 0;
-    for (int64_t i = 0; i < P; ++i)
-      for (int k = 0; k < m->K; ++k) wk[size_t(i) * m->KT + k] = w[size_t(i) * m->K + k];
-    bool cu = cudaMalloc(&m->words_kt[c], wk.size() * 8) == cudaSuccess &&
-              cudaMemcpy(m->words_kt[c], wk.data(), wk.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMalloc(&m->support[c], std::max<size_t>(1, sup.size()) * 4) == cudaSuccess &&
-              (sup.empty() || cudaMemcpy(m->support[c], sup.data(), sup.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess) &&
-              cudaMalloc(&m->score[c], sc.size() * 8) == cudaSuccess &&
-              cudaMemcpy(m->score[c], sc.data(), sc.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess;
-    if (cu && m->K == m->KT) {
-      m->words[c] = m->words_kt[c];
-    } else if (cu) {
-      cu = cudaMalloc(&m->words[c], std::max<size_t>(1, w.size()) * 8) == cudaSuccess &&
-           (w.empty() || cudaMemcpy(m->words[c], w.data(), w.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess);
+    if (m->KT >= 2) {
+      uint32_t* d_f = nullptr;
+      cudaError_t e = cudaMalloc(&d_f, sizeof(uint32_t) * 64 * m->K);
+      if (e == cudaSuccess) e = pattern_item_freq(m, d_f, nullptr);
+      if (e == cudaSuccess) e = build_pattern_indexes(m, d_f, nullptr);
+      if (d_f) cudaFree(d_f);
+      if (e != cudaSuccess) {
+        model_release(m);
+        return fail_cuda(e, "ig_model_load: pattern index");
+      }
+      m->subset_kernel = 3;
     }
-    if (!cu) {
-      fclose(f);
-      model_release(m);
-      return fail(IG_E_CUDA, "ig_model_load: device allocation or copy failed");
-    }
-  }
-  fclose(f);
-  if (!ok) {
-    model_release(m);
-    return fail(IG_E_IO, "ig_model_load: %s is truncated", path);
-  }
-  if (m->KT >= 2) {
-    uint32_t* d_f = nullptr;
-    cudaError_t e = cudaMalloc(&d_f, sizeof(uint32_t) * 64 * m->K);
-    if (e == cudaSuccess) e = pattern_item_freq(m, d_f, nullptr);
-    if (e == cudaSuccess) e = build_pattern_indexes(m, d_f, nullptr);
-    if (d_f) cudaFree(d_f);
-    if (e != cudaSuccess) {
-      model_release(m);
-      return fail_cuda(e, "ig_model_load: pattern index");
-    }
-    m->subset_kernel = 3;
-  }
-  *out = m;
-  return IG_OK;
+    *out = m;
+    return IG_OK;
+  });
 }
 
 void ig_model_free(ig_model* m) {
@@ -2169,18 +2208,20 @@ int ig_prof_reset(void) {
 
 int ig_prof_timeline(int32_t* stage, uint64_t* stream, double* t0_ms, double* t1_ms,
                      int64_t cap, int64_t* n_out) {
-  std::lock_guard<std::mutex> lk(g_prof.mu);
-  prof_drain_locked();
-  const int64_t n = int64_t(g_prof.spans.size());
-  if (n_out) *n_out = n;
-  for (int64_t i = 0; i < n && i < cap; ++i) {
-    const auto& sp = g_prof.spans[size_t(i)];
-    if (stage) stage[i] = sp.stage;
-    if (stream) stream[i] = uint64_t(reinterpret_cast<uintptr_t>(sp.s));
-    if (t0_ms) t0_ms[i] = sp.t0;
-    if (t1_ms) t1_ms[i] = sp.t1;
-  }
-  return IG_OK;
+  return igk::guarded("ig_prof_timeline", [&]() -> int {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    prof_drain_locked();
+    const int64_t n = int64_t(g_prof.spans.size());
+    if (n_out) *n_out = n;
+    for (int64_t i = 0; i < n && i < cap; ++i) {
+      const auto& sp = g_prof.spans[size_t(i)];
+      if (stage) stage[i] = sp.stage;
+      if (stream) stream[i] = uint64_t(reinterpret_cast<uintptr_t>(sp.s));
+      if (t0_ms) t0_ms[i] = sp.t0;
+      if (t1_ms) t1_ms[i] = sp.t1;
+    }
+    return IG_OK;
+  });
 }
 
 int ig_prof_read_work(int64_t* tests) {

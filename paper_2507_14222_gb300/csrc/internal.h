@@ -6,9 +6,31 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <new>
 #include <vector>
 
+#include "../../include/ig.h"
+
 namespace igk {
+
+// The status of an entry point whose body threw (no C++ exception may cross
+// the C ABI): IG_E_NOMEM for a failed host allocation, IG_E_INTERNAL for any
+// other exception; the message names the entry point.
+int report_exception(const char* where, bool out_of_memory) noexcept;
+
+// Runs the body of an exported entry point, or work that one hands to a
+// helper thread, so that an exception becomes a status instead of ending the
+// caller's process.
+template <class Body>
+int guarded(const char* where, Body&& body) noexcept {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    return report_exception(where, true);
+  } catch (...) {
+    return report_exception(where, false);
+  }
+}
 
 // Rows of every internally staged row array are allocated in multiples of
 // this many rows, so that whole TMA tiles can always be copied in bounds.

@@ -69,70 +69,72 @@ int cuda_fail(cudaError_t e) {
 extern "C" int ig_score_noalloc(const ig_model* model, const uint64_t* rows, int64_t m,
                                 int64_t* A_out, int64_t* N_out, uint8_t* label_out,
                                 ig_stream_t stream) {
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (!model || m < 0 || (m > 0 && !rows))
-    return igk::report_error(IG_E_INVAL, "ig_score_noalloc: bad arguments");
-  if (m > kMaxRows)
-    return igk::report_error(
-        IG_E_INVAL, "ig_score_noalloc: more rows than IG_SCORE_NOALLOC_MAX_ROWS (262144) in one call");
-  if (m == 0) return IG_OK;
-  // Every array must be device memory of one GPU, the one holding the
-  // model; that GPU is made current for the call and the caller's device is
-  // put back on return.
-  igk::ModelView v;
-  igk::model_view(model, &v);
-  int dev = -1;
-  if (!igk::device_of(rows, &dev))
-    return igk::report_error(IG_E_INVAL,
-                             "ig_score_noalloc: rows and outputs must be device memory");
-  const void* more[3] = {A_out, N_out, label_out};
-  for (const void* p : more) {
-    int d = -1;
-    if (p && (!igk::device_of(p, &d) || d != dev))
+  return igk::guarded("ig_score_noalloc", [&]() -> int {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!model || m < 0 || (m > 0 && !rows))
+      return igk::report_error(IG_E_INVAL, "ig_score_noalloc: bad arguments");
+    if (m > kMaxRows)
       return igk::report_error(
-          IG_E_INVAL, "ig_score_noalloc: rows and outputs must be device memory of one GPU");
-  }
-  for (int c = 0; c < 2; ++c) {
-    int d = -1;
-    if (v.n_pat[c] && (!igk::device_of(v.words_kt[c], &d) || d != dev))
+          IG_E_INVAL, "ig_score_noalloc: more rows than IG_SCORE_NOALLOC_MAX_ROWS (262144) in one call");
+    if (m == 0) return IG_OK;
+    // Every array must be device memory of one GPU, the one holding the
+    // model; that GPU is made current for the call and the caller's device is
+    // put back on return.
+    igk::ModelView v;
+    igk::model_view(model, &v);
+    int dev = -1;
+    if (!igk::device_of(rows, &dev))
       return igk::report_error(IG_E_INVAL,
-                               "ig_score_noalloc: the model lives on another GPU than the rows");
-  }
-  igk::DeviceRestore restore_device;
-  int cur = -1;
-  if (cudaGetDevice(&cur) != cudaSuccess || cur != dev) {
-    cudaError_t e = cudaSetDevice(dev);
-    if (e != cudaSuccess) return cuda_fail(e);
-  }
-  unsigned long long* scratch = nullptr;
-  int rc = scratch_address(&scratch);
-  if (rc != IG_OK) return rc;
-  int* d_status = reinterpret_cast<int*>(scratch);
-  unsigned long long* A = scratch + kStatusWords;
-  unsigned long long* N = A + kMaxRows;
+                               "ig_score_noalloc: rows and outputs must be device memory");
+    const void* more[3] = {A_out, N_out, label_out};
+    for (const void* p : more) {
+      int d = -1;
+      if (p && (!igk::device_of(p, &d) || d != dev))
+        return igk::report_error(
+            IG_E_INVAL, "ig_score_noalloc: rows and outputs must be device memory of one GPU");
+    }
+    for (int c = 0; c < 2; ++c) {
+      int d = -1;
+      if (v.n_pat[c] && (!igk::device_of(v.words_kt[c], &d) || d != dev))
+        return igk::report_error(IG_E_INVAL,
+                                 "ig_score_noalloc: the model lives on another GPU than the rows");
+    }
+    igk::DeviceRestore restore_device;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != dev) {
+      cudaError_t e = cudaSetDevice(dev);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
+    unsigned long long* scratch = nullptr;
+    int rc = scratch_address(&scratch);
+    if (rc != IG_OK) return rc;
+    int* d_status = reinterpret_cast<int*>(scratch);
+    unsigned long long* A = scratch + kStatusWords;
+    unsigned long long* N = A + kMaxRows;
 
-  cudaError_t e;
-  if ((e = cudaMemsetAsync(d_status, 0, sizeof(int), s)) != cudaSuccess) return cuda_fail(e);
-  if ((e = cudaMemsetAsync(A, 0, sizeof(unsigned long long) * m, s)) != cudaSuccess) return cuda_fail(e);
-  if ((e = cudaMemsetAsync(N, 0, sizeof(unsigned long long) * m, s)) != cudaSuccess) return cuda_fail(e);
-  for (int c = 1; c >= 0; --c) {  // A from P+, N from P- (Eq. 4)
-    igk::SubsetArgs a{igk::MODE_SUM, v.KT, rows, m, v.K, v.words_kt[c], v.score[c],
-                      v.n_pat[c], nullptr, c == 1 ? A : N, d_status};
-    if ((e = igk::launch_subset(a, s)) != cudaSuccess) return cuda_fail(e);
-  }
-  if (label_out && (e = igk::launch_labels(A, N, m, v.reg3, v.thr, label_out, s)) != cudaSuccess)
-    return cuda_fail(e);
-  if (A_out && (e = cudaMemcpyAsync(A_out, A, sizeof(int64_t) * m, cudaMemcpyDeviceToDevice, s)) !=
-                   cudaSuccess)
-    return cuda_fail(e);
-  if (N_out && (e = cudaMemcpyAsync(N_out, N, sizeof(int64_t) * m, cudaMemcpyDeviceToDevice, s)) !=
-                   cudaSuccess)
-    return cuda_fail(e);
-  int st = 0;
-  if ((e = cudaMemcpyAsync(&st, d_status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-    return cuda_fail(e);
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e);
-  if (st & igk::ST_TIMEOUT)
-    return igk::report_error(IG_E_TIMEOUT, "ig_score_noalloc: a bounded device wait ran out");
-  return IG_OK;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(d_status, 0, sizeof(int), s)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemsetAsync(A, 0, sizeof(unsigned long long) * m, s)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemsetAsync(N, 0, sizeof(unsigned long long) * m, s)) != cudaSuccess) return cuda_fail(e);
+    for (int c = 1; c >= 0; --c) {  // A from P+, N from P- (Eq. 4)
+      igk::SubsetArgs a{igk::MODE_SUM, v.KT, rows, m, v.K, v.words_kt[c], v.score[c],
+                        v.n_pat[c], nullptr, c == 1 ? A : N, d_status};
+      if ((e = igk::launch_subset(a, s)) != cudaSuccess) return cuda_fail(e);
+    }
+    if (label_out && (e = igk::launch_labels(A, N, m, v.reg3, v.thr, label_out, s)) != cudaSuccess)
+      return cuda_fail(e);
+    if (A_out && (e = cudaMemcpyAsync(A_out, A, sizeof(int64_t) * m, cudaMemcpyDeviceToDevice, s)) !=
+                     cudaSuccess)
+      return cuda_fail(e);
+    if (N_out && (e = cudaMemcpyAsync(N_out, N, sizeof(int64_t) * m, cudaMemcpyDeviceToDevice, s)) !=
+                     cudaSuccess)
+      return cuda_fail(e);
+    int st = 0;
+    if ((e = cudaMemcpyAsync(&st, d_status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      return cuda_fail(e);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e);
+    if (st & igk::ST_TIMEOUT)
+      return igk::report_error(IG_E_TIMEOUT, "ig_score_noalloc: a bounded device wait ran out");
+    return IG_OK;
+  });
 }

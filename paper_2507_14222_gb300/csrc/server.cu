@@ -212,91 +212,97 @@ void scheduler_loop(ig_server* sv) {
 extern "C" {
 
 int ig_server_create(const ig_model* model, const ig_server_config* cfg, ig_server** out) {
-  if (!model || !out) return set_error("ig_server_create: NULL argument");
-  *out = nullptr;
-  ig_model_info_t info;
-  if (ig_model_info(model, &info) != IG_OK) return IG_E_INVAL;
-  ig_server* sv = new ig_server;
-  sv->model = model;
-  sv->K = info.K;
-  cudaGetDevice(&sv->device);
-  ig_server_config c{};
-  if (cfg) c = *cfg;
-  if (c.slots <= 0) c.slots = 3;
-  if (c.max_batch_flows <= 0) c.max_batch_flows = 65536;
-  // Device bytes per flow in flight: the packed row, A, N and label, plus
-  // the item index of a scoring call (at most a quarter of all item slots
-  // filled, each copy a padded row).
-  const int KT = igk::padded_words(sv->K);
-  sv->bytes_per_flow = int64_t(KT) * 8 * (1 + 64 * sv->K / 4) + 32;
-  if (c.memory_budget_bytes <= 0) {
-    size_t free_b = 0, total_b = 0;
-    cudaMemGetInfo(&free_b, &total_b);
-    c.memory_budget_bytes = int64_t(free_b / 4);
-  }
-  c.memory_budget_bytes = std::max<int64_t>(c.memory_budget_bytes, sv->bytes_per_flow);
-  sv->cfg = c;
-  sv->slots.resize(c.slots);
-  const int64_t cap = c.max_batch_flows;
-  for (Slot& s : sv->slots) {
-    bool ok = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaMalloc(&s.d_rows, sizeof(uint64_t) * cap * sv->K) == cudaSuccess &&
-              cudaMalloc(&s.d_A, sizeof(int64_t) * cap) == cudaSuccess &&
-              cudaMalloc(&s.d_N, sizeof(int64_t) * cap) == cudaSuccess &&
-              cudaMalloc(&s.d_lab, cap) == cudaSuccess &&
-              cudaMallocHost(&s.h_rows, sizeof(uint64_t) * cap * sv->K) == cudaSuccess &&
-              cudaMallocHost(&s.h_A, sizeof(int64_t) * cap) == cudaSuccess &&
-              cudaMallocHost(&s.h_N, sizeof(int64_t) * cap) == cudaSuccess &&
-              cudaMallocHost(&s.h_lab, cap) == cudaSuccess;
-    if (!ok) {
-      ig_server_destroy(sv);
-      return igk::report_error(IG_E_NOMEM, "ig_server_create: device or pinned allocation failed");
+  return igk::guarded("ig_server_create", [&]() -> int {
+    if (!model || !out) return set_error("ig_server_create: NULL argument");
+    *out = nullptr;
+    ig_model_info_t info;
+    if (ig_model_info(model, &info) != IG_OK) return IG_E_INVAL;
+    ig_server* sv = new ig_server;
+    sv->model = model;
+    sv->K = info.K;
+    cudaGetDevice(&sv->device);
+    ig_server_config c{};
+    if (cfg) c = *cfg;
+    if (c.slots <= 0) c.slots = 3;
+    if (c.max_batch_flows <= 0) c.max_batch_flows = 65536;
+    // Device bytes per flow in flight: the packed row, A, N and label, plus
+    // the item index of a scoring call (at most a quarter of all item slots
+    // filled, each copy a padded row).
+    const int KT = igk::padded_words(sv->K);
+    sv->bytes_per_flow = int64_t(KT) * 8 * (1 + 64 * sv->K / 4) + 32;
+    if (c.memory_budget_bytes <= 0) {
+      size_t free_b = 0, total_b = 0;
+      cudaMemGetInfo(&free_b, &total_b);
+      c.memory_budget_bytes = int64_t(free_b / 4);
     }
-  }
-  for (Slot& s : sv->slots) s.thread = std::thread(slot_loop, sv, &s);
-  sv->scheduler = std::thread(scheduler_loop, sv);
-  *out = sv;
-  return IG_OK;
+    c.memory_budget_bytes = std::max<int64_t>(c.memory_budget_bytes, sv->bytes_per_flow);
+    sv->cfg = c;
+    sv->slots.resize(c.slots);
+    const int64_t cap = c.max_batch_flows;
+    for (Slot& s : sv->slots) {
+      bool ok = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) == cudaSuccess &&
+                cudaMalloc(&s.d_rows, sizeof(uint64_t) * cap * sv->K) == cudaSuccess &&
+                cudaMalloc(&s.d_A, sizeof(int64_t) * cap) == cudaSuccess &&
+                cudaMalloc(&s.d_N, sizeof(int64_t) * cap) == cudaSuccess &&
+                cudaMalloc(&s.d_lab, cap) == cudaSuccess &&
+                cudaMallocHost(&s.h_rows, sizeof(uint64_t) * cap * sv->K) == cudaSuccess &&
+                cudaMallocHost(&s.h_A, sizeof(int64_t) * cap) == cudaSuccess &&
+                cudaMallocHost(&s.h_N, sizeof(int64_t) * cap) == cudaSuccess &&
+                cudaMallocHost(&s.h_lab, cap) == cudaSuccess;
+      if (!ok) {
+        ig_server_destroy(sv);
+        return igk::report_error(IG_E_NOMEM, "ig_server_create: device or pinned allocation failed");
+      }
+    }
+    for (Slot& s : sv->slots) s.thread = std::thread(slot_loop, sv, &s);
+    sv->scheduler = std::thread(scheduler_loop, sv);
+    *out = sv;
+    return IG_OK;
+  });
 }
 
 int ig_server_submit(ig_server* sv, const uint64_t* rows, int64_t m, int64_t* A_out,
                      int64_t* N_out, uint8_t* label_out, uint64_t* ticket) {
-  if (!sv || !ticket || m <= 0 || !rows) return set_error("ig_server_submit: bad arguments");
-  if (m > sv->cfg.max_batch_flows)
-    return set_error("ig_server_submit: request larger than the batch cap");
-  Request* r = new Request;
-  r->rows = rows;
-  r->m = m;
-  r->A = A_out;
-  r->N = N_out;
-  r->labels = label_out;
-  r->submitted = Clock::now();
-  {
-    std::lock_guard<std::mutex> lk(sv->mu);
-    r->ticket = sv->next_ticket++;
-    sv->live[r->ticket] = r;
-    sv->queue.push_back(r);
-  }
-  sv->cv.notify_all();
-  *ticket = r->ticket;
-  return IG_OK;
+  return igk::guarded("ig_server_submit", [&]() -> int {
+    if (!sv || !ticket || m <= 0 || !rows) return set_error("ig_server_submit: bad arguments");
+    if (m > sv->cfg.max_batch_flows)
+      return set_error("ig_server_submit: request larger than the batch cap");
+    Request* r = new Request;
+    r->rows = rows;
+    r->m = m;
+    r->A = A_out;
+    r->N = N_out;
+    r->labels = label_out;
+    r->submitted = Clock::now();
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      r->ticket = sv->next_ticket++;
+      sv->live[r->ticket] = r;
+      sv->queue.push_back(r);
+    }
+    sv->cv.notify_all();
+    *ticket = r->ticket;
+    return IG_OK;
+  });
 }
 
 int ig_server_wait(ig_server* sv, uint64_t ticket, double* latency_ms) {
-  if (!sv) return set_error("ig_server_wait: NULL server");
-  std::unique_lock<std::mutex> lk(sv->mu);
-  auto it = sv->live.find(ticket);
-  if (it == sv->live.end()) return set_error("ig_server_wait: unknown ticket");
-  Request* r = it->second;
-  sv->done_cv.wait(lk, [&] { return r->done; });
-  sv->live.erase(it);
-  const int rc = r->rc;
-  if (latency_ms)
-    *latency_ms = std::chrono::duration<double, std::milli>(r->completed - r->submitted).count();
-  std::string err = r->error;
-  delete r;
-  if (rc != IG_OK) return igk::report_error(rc, err.c_str());
-  return rc;
+  return igk::guarded("ig_server_wait", [&]() -> int {
+    if (!sv) return set_error("ig_server_wait: NULL server");
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->live.find(ticket);
+    if (it == sv->live.end()) return set_error("ig_server_wait: unknown ticket");
+    Request* r = it->second;
+    sv->done_cv.wait(lk, [&] { return r->done; });
+    sv->live.erase(it);
+    const int rc = r->rc;
+    if (latency_ms)
+      *latency_ms = std::chrono::duration<double, std::milli>(r->completed - r->submitted).count();
+    std::string err = r->error;
+    delete r;
+    if (rc != IG_OK) return igk::report_error(rc, err.c_str());
+    return rc;
+  });
 }
 
 int ig_server_stats(ig_server* sv, int64_t* batches, int64_t* flows) {
