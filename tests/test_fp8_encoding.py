@@ -11,8 +11,9 @@ accumulator in any order, and D = 0 only when no item is missing.
 Checked here from the E4M3 definition (1 sign, 4 exponent bits with bias 7,
 3 mantissa bits; subnormals at exponent 0) and IEEE float32 sums in numpy:
 the two operand bytes, the exactness of every count up to 512 under
-shuffled accumulation orders, and the complement identity on random
-itemsets.
+shuffled accumulation orders, the complement identity on random itemsets,
+and the fused kernel's spread of four items into four operand bytes by one
+multiply and one mask.
 """
 import numpy as np
 import pytest
@@ -63,3 +64,17 @@ def test_complement_counts_missing_items():
         missing = int((p & ~r).sum())
         assert D == np.float32(missing * 2.0 ** -12)
         assert (D == 0) == bool(np.all(~p | r))
+
+
+def spread_nibble(n: int) -> int:
+    """The fused kernel's expansion of 4 items into 4 E4M3 bytes (uint32)."""
+    return (n * 0x01020408) & 0x08080808 & 0xFFFFFFFF
+
+
+def test_nibble_spread_gives_one_byte_per_item():
+    for n in range(16):
+        v = spread_nibble(n)
+        assert [(v >> (8 * b)) & 0xFF for b in range(4)] == \
+            [0x08 if (n >> b) & 1 else 0x00 for b in range(4)]
+        # the shifted copies of n do not overlap, so the product has no carries
+        assert n * 0x01020408 == sum(n << s for s in (3, 10, 17, 24)) < 1 << 32
