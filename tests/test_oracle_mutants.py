@@ -56,6 +56,9 @@ MUTANTS = [
     ("evidence-transposed", CPP, "if (contained_in(pat + p * K, rows + t * K, K)) sum +=",
      "if (contained_in(rows + t * K, pat + p * K, K)) sum +="),
     ("evidence-counts-patterns", CPP, "sum += int64_t(S[p]);", "sum += 1;"),
+    ("evidence-32-bit-sum", CPP, "      int64_t sum = 0;", "      int32_t sum = 0;"),
+    ("threads-drop-last-row", CPP, "int64_t lo = t * chunk, hi = std::min<int64_t>(n, lo + chunk);",
+     "int64_t lo = t * chunk, hi = std::min<int64_t>(n - 1, lo + chunk);"),
     # Regulations 1-3
     ("reg1-strict", CPP, "(A[t] >= N[t]) ? 1 : 0", "(A[t] > N[t]) ? 1 : 0"),
     # (Dropping Regulation 2 outright changes nothing: A == N == 0 already
@@ -86,6 +89,7 @@ MUTANTS = [
     ("reg3-stats-over-attacks", PY, "evidence(pats[NORMAL], sco[NORMAL], X[NORMAL], threads)",
      "evidence(pats[NORMAL], sco[NORMAL], X[ATTACK], threads)"),
     ("given-order-word0-major", PY, "order = np.lexsort(P.T) if", "order = np.lexsort(P.T[::-1]) if"),
+    ("score-ignores-reg3", PY, "thr = None if model.reg3 is None else model.reg3[3]", "thr = None"),
     # host helpers: discretiser, contradiction filter, metrics, sweep
     ("stats-sample-std", HELP, "return mu, math.sqrt(ss / float(count))",
      "return mu, math.sqrt(ss / float(max(count - 1, 1)))"),

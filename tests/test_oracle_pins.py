@@ -293,3 +293,40 @@ def test_model_from_patterns_canonical_order():
     assert m.support[0].tolist() == [40, 20, 30, 10]
     assert m.score[0].tolist() == [40 * 1, 20 * 9, 30 * 4, 10 * 9]
     assert m.patterns[1].tolist() == [[7, 0], [5, 1]]
+
+
+def test_evidence_sums_beyond_32_bits():
+    # Eq. 4 closed form: a record holding every item of one word contains
+    # every pattern made of its items, so its evidence is the sum of all the
+    # patterns' scores.  2,081 patterns of 62-64 items with support 1,000
+    # score 3.8-4.1 million each: the sum is about 8e9, beyond 32 bits.
+    from itertools import combinations
+    full = (1 << 64) - 1
+    pats = [full] + [full ^ (1 << a) for a in range(64)] + \
+           [full ^ (1 << a) ^ (1 << b) for a, b in combinations(range(64), 2)]
+    P = np.array([[p] for p in pats], np.uint64)
+    f = np.full(len(pats), 1000, np.uint32)
+    S = oracle.pattern_score(P, f)
+    want = sum(1000 * bin(p).count("1") ** 2 for p in pats)
+    assert want > 2 ** 32 and int(S.astype(object).sum()) == want
+    got = oracle.evidence(P, S, np.array([[full], [full ^ 1]], np.uint64))
+    assert got.dtype == np.int64
+    # the second record lacks item 0: only patterns without it are inside
+    assert got.tolist() == [want, sum(1000 * bin(p).count("1") ** 2 for p in pats if not p & 1)]
+
+
+def test_score_applies_regulation3(tiny_fit):
+    # Scoring with a fitted Regulation 3: labels follow Regulations 1-3 with
+    # the model's threshold, applied here by hand to the oracle's (brute-force
+    # pinned) evidence, and some normal-by-Regulation-1 records do turn attack.
+    w, rows, _ = tiny_fit
+    m = oracle.fit(rows, w.train_labels, r=0.5)
+    test = oracle.encode(w.test_codes, w.cards)
+    A, N, lab = oracle.score(m, test)
+    assert np.array_equal(A, oracle.evidence(m.patterns[1], m.score[1], test))
+    assert np.array_equal(N, oracle.evidence(m.patterns[0], m.score[0], test))
+    thr = m.reg3[3]
+    want = [1 if (a >= n or (a == 0 and n == 0) or float(n) < thr) else 0
+            for a, n in zip(A.tolist(), N.tolist())]
+    assert lab.tolist() == want
+    assert sum(1 for a, n in zip(A.tolist(), N.tolist()) if a < n and float(n) < thr) > 0
