@@ -69,6 +69,8 @@ MUTANTS = [
     ("reg3-sample-std", CPP, "*sigma = std::sqrt(ss / double(n));",
      "*sigma = std::sqrt(ss / double(n > 1 ? n - 1 : 1));"),
     ("reg3-threshold-sign", CPP, "return mu - scaled;", "return mu + scaled;"),
+    ("reg3-mean-over-n-plus-1", CPP, "double mean = sum / double(n);",
+     "double mean = sum / double(n + 1);"),
     # Section 3.1 / Eq. 5 encoding
     ("encode-missing-keeps-offset", CPP, "        offset += cards[f];\n        continue;",
      "        continue;"),
@@ -90,6 +92,9 @@ MUTANTS = [
      "evidence(pats[NORMAL], sco[NORMAL], X[ATTACK], threads)"),
     ("given-order-word0-major", PY, "order = np.lexsort(P.T) if", "order = np.lexsort(P.T[::-1]) if"),
     ("score-ignores-reg3", PY, "thr = None if model.reg3 is None else model.reg3[3]", "thr = None"),
+    ("given-supports-not-reordered", PY,
+     "sups[c] = np.ascontiguousarray(np.asarray(support[c], np.uint32)[order])",
+     "sups[c] = np.ascontiguousarray(np.asarray(support[c], np.uint32))"),
     # host helpers: discretiser, contradiction filter, metrics, sweep
     ("stats-sample-std", HELP, "return mu, math.sqrt(ss / float(count))",
      "return mu, math.sqrt(ss / float(max(count - 1, 1)))"),
@@ -98,6 +103,13 @@ MUTANTS = [
     ("filter-drops-last-attacks", HELP, "dropped = normal[:k] + attack[:k]",
      "dropped = normal[:k] + attack[len(attack) - k:]"),
     ("filter-mode1-any-class", HELP, "if normal and attack else []", "if normal or attack else []"),
+    ("filter-pairs-by-max", HELP, "k = min(len(normal), len(attack))",
+     "k = max(len(normal), len(attack))"),
+    ("unseen-token-coded-0", HELP, "if t is not None and t in rank:\n                codes[i, f] = rank[t]",
+     "if t is not None:\n                codes[i, f] = rank.get(t, 0)"),
+    ("constant-column-token-1", HELP, "    if not sigma > 0.0:\n        return 0",
+     "    if not sigma > 0.0:\n        return 1"),
+    ("decimals-off-by-one", HELP, "scale = float(10 ** int(p))", "scale = float(10 ** (int(p) + 1))"),
     ("precision-uses-fn", HELP, '"precision": _ratio(tp, tp + fp)', '"precision": _ratio(tp, tp + fn)'),
     ("f1-halved", HELP, '"f1": _ratio(2 * tp, 2 * tp + fp + fn)', '"f1": _ratio(tp, tp + fp + fn)'),
     ("auc-ties-dropped", HELP, "two_u += 2 * below + (upto - below)", "two_u += 2 * below"),
