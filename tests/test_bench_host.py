@@ -1,6 +1,7 @@
 """Host-side bookkeeping of bench.py (no GPU): the test counts the metric is
 built on (Eq. 2, Eq. 3, Eq. 4), the choice of the dominant stage, the
-roofline arithmetic and the DRAM-traffic table's workload and hash checks."""
+roofline arithmetic, the DRAM-traffic table's workload and hash checks, and
+the parsing of the clock and throttle-reason samples."""
 import hashlib
 import importlib.util
 import json
@@ -133,3 +134,25 @@ def test_traffic_lookup_drops_a_changed_source(tmp_path, monkeypatch):
     assert bench.dram_traffic("k", "w") == 123
     src.write_text("kernel v2\n")
     assert bench.dram_traffic("k", "w") is None
+
+
+def test_clock_samples_parse_median_max_and_reasons(tmp_path):
+    # nvidia-smi rows (csv, no header, no units): index, clocks.sm,
+    # clocks.max.sm, power, active reasons, then the four reasons read.
+    rows = ["0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "0, 2055, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+            "0, 1980, 2070, 1400.2, 0x0000000000000008, Active, Not Active, Not Active, Active",
+            "garbage line",
+            "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    path = tmp_path / "clocks.csv"
+    path.write_text("\n".join(rows) + "\n")
+
+    class Done:
+        pass
+    s = bench.ClockSampler(0)
+    s.proc = Done()
+    s.tmp = open(path)
+    out = s.summary()
+    assert out["sm_mhz"] == 2055.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 3
+    assert out["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert bench.ClockSampler(0).summary()["reasons"] == ["unsampled"]
