@@ -156,3 +156,12 @@ def test_clock_samples_parse_median_max_and_reasons(tmp_path):
     assert out["sm_mhz"] == 2055.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 3
     assert out["reasons"] == ["hw_slowdown", "sw_power_cap"]
     assert bench.ClockSampler(0).summary()["reasons"] == ["unsampled"]
+
+
+def test_peaks_fall_back_when_unmeasured(monkeypatch):
+    # Without the measured peaks file the rooflines use the stated fallback
+    # figures and say so.
+    monkeypatch.setattr(bench, "load_peaks", lambda: None)
+    r = bench.stage_roofline("evidence_idx", 2.0, 2, 10**9, info(), 8, None, 1)
+    assert r["peak"] == pytest.approx(2 * bench.FALLBACK_BF16_TFLOPS)
+    assert "fallback" in r["peak_source"]
