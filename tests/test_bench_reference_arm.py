@@ -64,3 +64,24 @@ def test_own_arm_without_a_gpu_fails_loudly():
                        capture_output=True, text=True, timeout=600)
     assert p.returncode != 0
     assert not [l for l in p.stdout.splitlines() if l.lstrip().startswith("{")]
+
+
+def _line(out):
+    lines = [l for l in out.splitlines() if l.strip()]
+    assert len(lines) == 1
+    return json.loads(lines[0])
+
+
+def test_reference_arm_batched_and_served_workloads():
+    rc, out, err = _run(None, "--workload", "batched", "--steps", "3", "--warmup", "3")
+    assert rc == 0, err[-2000:]
+    d = _line(out)
+    assert d["unit"] == bench.UNIT and d["config"]["workload"] == "ig-batched-64-problems"
+    assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+    rc, out, err = _run(None, "--workload", "served", "--served-patterns", "3000",
+                        "--served-flows", "5000", "--steps", "3", "--warmup", "3")
+    assert rc == 0, err[-2000:]
+    d = _line(out)
+    assert d["unit"] == "flows/s" and d["value"] > 0
+    assert d["config"]["workload"] == "ig-served-3000x2-patterns-5000-flows"
+    assert d["e2e"]["unit"] == "flows/s"
