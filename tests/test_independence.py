@@ -75,7 +75,7 @@ def test_generator_imports_neither_side():
 
 
 def test_bench_and_entry_import_the_oracle_only_where_allowed():
-    allowed = {"bench.py": {"_oracle_pass", "cpu_baseline", "run_reference"},
+    allowed = {"bench.py": {"_oracle_pass", "cpu_baseline", "run_reference", "_reference_served"},
                "__graft_entry__.py": {"build", "smoke"}}
     for name, fns in allowed.items():
         where = {fn for m, fn in _imports(ast.parse(_read(os.path.join(ROOT, name))))
